@@ -1,0 +1,309 @@
+"""Pins of the CPU oracle against facts the paper and the mathematics fix (no GPU).
+
+Each test checks the oracle against something other than itself: adaptive quadrature, arbitrary-
+precision Bessel functions, closed forms, invariants stated in the paper, or exact solutions.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import integrate, special
+
+import workloads as wl
+from oracle import geometry as geo
+from oracle import kernels as ker
+from oracle import transforms as tr
+from oracle.fthms import Setup, run_oracle
+
+
+# ---- Chebyshev log-kernel identity (flat-arc identity of the weighted log kernel) ----------------
+
+def _log_moment_quad(t, k):
+    """int_{-1}^{1} log|t - s| T_k(s)/sqrt(1-s^2) ds by adaptive quadrature in s = cos(theta)."""
+    f = lambda th: math.log(abs(t - math.cos(th))) * math.cos(k * th)
+    if abs(t) < 1.0:
+        pts = [math.acos(t)]
+        return integrate.quad(f, 0.0, math.pi, points=pts, limit=400, epsabs=1e-14, epsrel=1e-13)[0]
+    return integrate.quad(f, 0.0, math.pi, limit=400, epsabs=1e-14, epsrel=1e-13)[0]
+
+
+@pytest.mark.parametrize("t,k", [(0.3, 0), (0.3, 1), (-0.71, 2), (0.9, 5), (0.05, 7)])
+def test_flat_arc_identity_by_quadrature(t, k):
+    """-1/(2pi) int log|t-s| T_k(s)/sqrt(1-s^2) ds = T_k(t)/(2k) (k >= 1), ln2/2 (k = 0)."""
+    val = -_log_moment_quad(t, k) / (2.0 * math.pi)
+    ref = math.log(2.0) / 2.0 if k == 0 else math.cos(k * math.acos(t)) / (2.0 * k)
+    assert abs(val - ref) < 1e-12
+
+
+@pytest.mark.parametrize("n", [4, 9, 33, 96])
+def test_rlog_self_reproduces_identity(n):
+    """The self weights integrate every T_k, k < n, exactly: sum_l Rlog_il T_k(t_l) = -(pi/k) T_k(t_i)."""
+    R = ker.rlog_self(n)
+    t = geo.cheb_nodes(n)
+    for k in range(n):
+        Tk = np.cos(k * np.arccos(t))
+        ref = -math.pi * math.log(2.0) * np.ones(n) if k == 0 else -(math.pi / k) * Tk
+        assert np.max(np.abs(R @ Tk - ref)) < 1e-12 * max(1.0, n / 10)
+
+
+@pytest.mark.parametrize("ts", [1.02, -1.3, 2.5, -2.9])
+def test_log_moments_outside_by_quadrature(ts):
+    lam = ker.log_moments_outside(np.array([ts]), 8)[0]
+    for k in range(8):
+        assert abs(lam[k] - _log_moment_quad(ts, k)) < 1e-11
+
+
+def test_rlog_outside_reproduces_moments():
+    n = 17
+    ts = np.array([1.05, -1.7, 2.9])
+    W = ker.rlog_outside(ts, n)
+    t = geo.cheb_nodes(n)
+    lam = ker.log_moments_outside(ts, n)
+    for k in range(n):
+        assert np.max(np.abs(W @ np.cos(k * np.arccos(t)) - lam[:, k])) < 1e-11
+
+
+# ---- Hankel function ---------------------------------------------------------------------------
+
+def test_hankel_against_mpmath_and_wronskian():
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    for z in [1e-3, 0.37, 1.0, 2.7, 4.5, 7.9, 12.3, 19.9, 26.0, 55.5, 140.0, 611.0]:
+        K = ker.phi_kernel(np.array([z]))[0]
+        ref = 0.25j * complex(mp.besselj(0, z) + 1j * mp.bessely(0, z))
+        assert abs(K - ref) <= 2e-16 * max(1.0, abs(ref)) * 8
+        w = special.j1(z) * special.y0(z) - special.j0(z) * special.y1(z)
+        assert abs(w - 2.0 / (math.pi * z)) < 1e-14 * max(1.0, 2.0 / (math.pi * z))
+
+
+# ---- Nystrom rule against brute-force quadrature ---------------------------------------------
+
+def _arc():
+    problem = wl.config2_reduced()
+    return geo.build_arcs(problem)[4]       # a kite arc: curved, non-uniform speed
+
+
+def _brute_single_layer(arc, kappa, y, phi_fun, tstar=None):
+    """int_{-1}^{1} Phi(y, x(s)) phi(s)/sqrt(1-s^2) ds, s = cos(theta), adaptive with the log
+    singularity split off at the target's parameter when it lies on the arc."""
+    def f(th, part):
+        s = math.cos(th)
+        x, _ = arc.point(np.array([s]))
+        r = float(np.linalg.norm(np.asarray(y) - x[0]))
+        K = 0.25j * (special.j0(kappa * r) + 1j * special.y0(kappa * r))
+        v = K * phi_fun(s)
+        return v.real if part == 0 else v.imag
+    pts = None
+    if tstar is not None and abs(tstar) < 1:
+        pts = [math.acos(tstar)]
+    re = integrate.quad(f, 0, math.pi, args=(0,), points=pts, limit=500, epsabs=1e-14, epsrel=1e-13)[0]
+    im = integrate.quad(f, 0, math.pi, args=(1,), points=pts, limit=500, epsabs=1e-14, epsrel=1e-13)[0]
+    return re + 1j * im
+
+
+def test_self_matrix_against_brute_force():
+    arc = _arc()
+    kappa = 7.3
+    n = 64
+    phi_fun = lambda s: math.exp(0.4 * s) * math.cos(1.3 * s) + 0.2j * s * s
+    t = geo.cheb_nodes(n)
+    A = ker.self_matrix(arc, n, kappa)
+    phi = np.array([phi_fun(s) for s in t])
+    got = A @ phi
+    X, _ = arc.point(t)
+    for i in [0, 5, 31, 50, 63]:
+        ref = _brute_single_layer(arc, kappa, X[i], phi_fun, tstar=t[i])
+        assert abs(got[i] - ref) < 1e-10 * max(1.0, abs(ref))
+
+
+def test_cross_rows_near_and_far_against_brute_force():
+    arc = _arc()
+    kappa = 5.1
+    n = 64
+    phi_fun = lambda s: 1.0 + 0.5 * s - 0.3j * s ** 3
+    t = geo.cheb_nodes(n)
+    phi = np.array([phi_fun(s) for s in t])
+    # near targets: points of the same curve just beyond each end of the arc
+    ts = np.array([1.03, -1.2, 1.5])
+    theta = arc.theta_c + arc.half * ts
+    ynear = geo.curve_eval(arc.curve, theta)[0]
+    E = ker.cross_rows(arc, n, kappa, ynear, ts, np.ones(3, dtype=bool))
+    for r in range(3):
+        ref = _brute_single_layer(arc, kappa, ynear[r], phi_fun)
+        assert abs(E[r] @ phi - ref) < 1e-9 * max(1.0, abs(ref))
+    yfar = np.array([[5.0, 4.0], [-3.0, 2.0]])
+    E = ker.cross_rows(arc, n, kappa, yfar, np.zeros(2), np.zeros(2, dtype=bool))
+    for r in range(2):
+        ref = _brute_single_layer(arc, kappa, yfar[r], phi_fun)
+        assert abs(E[r] @ phi - ref) < 1e-11 * max(1.0, abs(ref))
+
+
+def test_open_arc_manufactured_solution_converges():
+    """phi -> G by brute-force quadrature -> solve -> phi back; spectral in N."""
+    arc = _arc()
+    kappa = 3.0
+    phi_fun = lambda s: math.cos(0.7 * s) + 0.3j * math.sin(1.1 * s)
+    errs = []
+    for n in (24, 48):
+        t = geo.cheb_nodes(n)
+        X, _ = arc.point(t)
+        G = np.array([_brute_single_layer(arc, kappa, X[i], phi_fun, tstar=t[i]) for i in range(n)])
+        phi = np.linalg.solve(ker.self_matrix(arc, n, kappa), G)
+        errs.append(np.max(np.abs(phi - np.array([phi_fun(s) for s in t]))))
+    assert errs[1] < 1e-9 and errs[1] < errs[0]
+
+
+def test_restriction_is_interpolation():
+    nmax, n = 29, 17
+    R = ker.restriction(n, nmax)
+    tau, t = geo.cheb_nodes(nmax), geo.cheb_nodes(n)
+    f = lambda x: np.exp(x) * np.sin(3 * x)
+    assert np.max(np.abs(R @ f(tau) - f(t))) < 1e-12
+    assert np.max(np.abs(ker.restriction(nmax, nmax) - np.eye(nmax))) < 1e-13
+
+
+# ---- Partitions of unity ---------------------------------------------------------------------
+
+@pytest.mark.parametrize("cfg", ["c1", "c2"])
+def test_boundary_pou(cfg):
+    problem = wl.config1() if cfg == "c1" else wl.config2_reduced()
+    arcs = geo.build_arcs(problem)
+    for ci in range(len(problem["curves"])):
+        mine = [a for a in arcs if a.curve_index == ci]
+        theta = np.linspace(0, 2 * math.pi, 1001)
+        total = np.zeros_like(theta)
+        for a in mine:
+            ts = a.local_param(theta)
+            inside = np.abs(ts) <= 1.0
+            total[inside] += geo.chi(a, ts[inside])
+        assert np.max(np.abs(total - 1.0)) < 1e-13
+        for a in mine:      # chi_j vanishes on Gamma_j^0 next to both endpoints
+            assert np.all(geo.chi(a, np.array([0.9999, -0.9999])) == 0.0)
+
+
+def test_time_window_pou():
+    H, Q = 7.0, 4
+    s = np.array([1.5 * q * H for q in range(Q)])
+    t = np.linspace(-H / 2, s[-1] + H / 2, 4001)
+    tot = sum(tr.window(t - sq, H) for sq in s)
+    assert np.max(np.abs(tot - 1.0)) < 1e-15
+    assert np.all(tr.window(np.array([-H, H, -H - 1, H + 2]), H) == 0.0)
+
+
+# ---- Transforms ------------------------------------------------------------------------------
+
+def test_forward_transform_matches_closed_form():
+    sig = {"amp": 1.0, "carrier": 10.0, "centre": 6.0, "width": 2.0}
+    opts = {"W": 60.0, "L": 257, "Q": 1, "H": 40.0, "n_period": 2048}
+    g = tr.TimeGrid(opts)
+    G = g.forward(tr.signal_f(sig, g.t)[None, :])[0, 0]
+    ref = tr.signal_F(sig, g.omega) * np.exp(-1j * g.omega * g.s[0])
+    assert np.max(np.abs(G[1:] - ref[1:])) < 1e-12 * np.max(np.abs(ref))
+
+
+def test_inverse_transform_matches_signal():
+    sig = {"amp": 1.0, "carrier": 10.0, "centre": 6.0, "width": 2.0}
+    opts = {"W": 60.0, "L": 1025, "Q": 1, "H": 40.0, "n_period": 4096}
+    g = tr.TimeGrid(opts)
+    V = tr.signal_F(sig, g.omega)[None, None, :]          # one window with s_1 = 0
+    t = np.linspace(-5.0, 25.0, 301)
+    v = g.inverse_at(V, t)[0]
+    assert np.max(np.abs(v - tr.signal_f(sig, t))) < 1e-12
+    vg = g.inverse(V)[0]
+    assert np.max(np.abs(vg - tr.signal_f(sig, g.t))) < 1e-12
+
+
+def test_windowed_round_trip_multiple_windows():
+    """Forward per window then recentred inverse sums back to the signal (eqs. windowing, TDsol).
+    The solver drops omega = 0; adding that node's trapezoid term (weight h/2) back restores the
+    full rule, which reproduces the signal to rounding on [-H/2, s_Q + H/2]."""
+    sig = {"amp": 1.0, "carrier": 6.0, "centre": 14.0, "width": 5.0}
+    opts = {"W": 80.0, "L": 1281, "Q": 3, "H": 10.0, "n_period": 4096}
+    g = tr.TimeGrid(opts)
+    f = tr.signal_f(sig, g.t)
+    G = g.forward(f[None, :])
+    back = g.inverse(G)[0]
+    for q in range(g.Q):
+        valid = np.zeros(g.NT, dtype=bool)
+        valid[g.nlo[q]:g.nlo[q] + g.K] = True
+        back += np.where(valid, 0.5 * g.h * G[0, q, 0].real / math.pi, 0.0)
+    inside = (g.t >= -g.H / 2) & (g.t <= g.s[-1] + g.H / 2)
+    assert np.max(np.abs(back - f)[inside]) < 1e-12
+
+
+def test_point_source_field_against_quadrature_and_transform():
+    sig = {"kind": 0, "z0": [2.0, 0.5], "amp": 1.0, "carrier": 4.0, "centre": 4.0, "width": 1.5}
+    x = np.array([[1.0, 0.0], [-0.5, 0.8]])
+    t = np.array([3.0, 5.5, 7.25, 9.0])
+    u = tr.incident_field(sig, x, t)
+    for p in range(2):
+        r = float(np.linalg.norm(x[p] - np.array(sig["z0"])))
+        for n, tn in enumerate(t):
+            f = lambda v: tr.signal_f(sig, tn - r * math.cosh(v)) / (2 * math.pi)
+            ref = integrate.quad(f, 0.0, math.acosh((tn + 20.0) / r), limit=2000, epsabs=1e-16, epsrel=1e-14)[0]
+            assert abs(u[p, n] - ref) < 1e-14
+    # the slow transform of the field is F(omega) (i/4) H0(omega r): outgoing convention of
+    # Section 2.1 (a signal without DC content, so that the 2-D tail is negligible in the window)
+    sig = dict(sig, carrier=8.0)
+    opts = {"W": 24.0, "L": 257, "Q": 1, "H": 30.0, "n_period": 2048}
+    g = tr.TimeGrid(opts)
+    r = float(np.linalg.norm(x[0] - np.array(sig["z0"])))
+    U = g.forward(tr.incident_field(sig, x[:1], g.t))[0, 0]
+    ref = tr.signal_F(sig, g.omega[1:]) * ker.phi_kernel(g.omega[1:] * r) * np.exp(-1j * g.omega[1:] * g.s[0])
+    assert np.max(np.abs(U[1:] - ref)) < 1e-11 * np.max(np.abs(ref))
+
+
+# ---- End to end ------------------------------------------------------------------------------
+
+def test_config1_interior_point_source_exact_solution():
+    """Interior disk with boundary data = point-source field: u = u^i in D (config 1)."""
+    p = wl.config1()
+    r = run_oracle(p)
+    o = p["options"]
+    tout = o["tout0"] + o["dtout"] * np.arange(o["n_tout"])
+    ex = tr.incident_field(p["signal"], o["obs"], tout)
+    assert np.max(np.abs(r.traces - ex)) < 1.5e-4          # N = 96 single-patch discretisation
+
+
+def test_ms_horizon_theorem():
+    """u_M = u for t <= t_on + T(M) (Theorem equivalence-int): with M = 1 the sum matches the exact
+    field early and departs from it later; more steps extend the matching interval."""
+    errs = {}
+    for M in (1, 3):
+        p = wl.config1(L=129, M=M, N=64)
+        r = run_oracle(p)
+        o = p["options"]
+        tout = o["tout0"] + o["dtout"] * np.arange(o["n_tout"])
+        ex = tr.incident_field(p["signal"], o["obs"], tout)
+        errs[M] = np.max(np.abs(r.traces - ex), axis=0)
+    # time of first departure above 1e-3 of the field scale
+    def depart(e):
+        idx = np.nonzero(e > 1e-4)[0]
+        return idx[0] if idx.size else len(e)
+    assert depart(errs[3]) > depart(errs[1])
+
+
+def test_exterior_disk_mie_series():
+    """Sound-soft disk of radius a split into 3 arcs, plane-wave pulse: the multiple-scattering sum
+    matches the Mie series u_s = -sum_n i^n J_n(ka)/H_n(ka) H_n(kr) e^{in(theta-theta_inc)} F(omega)."""
+    a = 1.0
+    p = {"name": "mie", "curves": [wl.circle(a)], "arcs": wl.split_closed_curve(0, 3, 1.25, 0.3),
+         "signal": {"kind": 1, "z0": [0, 0], "dir": [1.0, 0.0], "sign": -1.0, "amp": 1.0,
+                    "carrier": 4.0, "centre": 6.0, "width": 1.5},
+         "options": {"W": 16.0, "L": 129, "N_fixed": 64, "N_min": 0, "N_off": 0, "N_ppw": 0.0,
+                     "M": 10, "Q": 1, "H": 20.0, "n_period": 1024, "interior": 0,
+                     "obs": np.array([[2.0, 0.5], [-1.5, -1.5]]), "tout0": 0.0, "dtout": 0.1, "n_tout": 101}}
+    r = run_oracle(p)
+    g = r.grid
+    Vm = np.zeros((2, 1, g.L), dtype=np.complex128)
+    for i, z in enumerate(p["options"]["obs"]):
+        rr, th = float(np.hypot(*z)), float(math.atan2(z[1], z[0]))
+        for l in range(1, g.L):
+            k = g.omega[l]
+            nn = np.arange(-80, 81)
+            terms = (1j ** nn) * special.jv(nn, k * a) / special.hankel1(nn, k * a) * special.hankel1(nn, k * rr) \
+                * np.exp(1j * nn * th)
+            Vm[i, 0, l] = -np.sum(terms) * tr.signal_F(p["signal"], k)
+    tout = np.arange(101) * 0.1
+    ref = g.inverse_at(Vm, tout)
+    assert np.max(np.abs(r.traces - ref)) < 2e-3 * np.max(np.abs(ref))

@@ -1,0 +1,183 @@
+"""Seeded synthetic FTH-MS problem descriptions shared by the oracle, the tests and the bench.
+
+This module only *describes* problems: curve coefficients, arc parameter intervals, signal and
+discretisation parameters, observation points.  It holds none of the method's arithmetic (no
+nodes, windows, kernels, transforms), so that the CPU oracle and the CUDA path can both consume
+the same inputs while sharing no computation.
+
+A problem is a plain dict:
+
+* ``curves``: list of trig-polynomial curves ``X(theta) = sum_k (ax[k] cos k theta + bx[k] sin k theta,
+  ay[k] cos k theta + by[k] sin k theta)``, k = 0..degree (the ``b[0]`` entries are unused).
+* ``arcs``: list of ``(curve_index, theta_a, theta_b)`` with ``theta_b > theta_a`` (may exceed 2 pi);
+  consecutive arcs of one closed curve overlap their neighbours only (Section 3.1).
+* ``signal``: incident field ``u^i``; ``kind`` 0 = point source at ``z0``, 1 = plane wave along ``dir``;
+  time signal ``f(t) = amp sin(carrier t) exp(-((t - centre)/width)^2)``; boundary data is
+  ``sign * u^i`` (``sign = -1`` for scattering, ``+1`` when the boundary carries the field itself).
+* ``options``: ``W`` (max frequency), ``L`` (frequencies ``omega_l = l W/(L-1)``, l = 0..L-1),
+  the per-arc node-count rule ``N = N_fixed`` if nonzero else
+  ``max(N_min, ceil(N_ppw * omega * arclength) + N_off)``, ``M`` multiple-scattering steps,
+  ``Q`` time windows of half-width ``H``, ``n_period`` time samples per period ``2 pi/h`` of the
+  uniform frequency grid, observation points and output times.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+__all__ = [
+    "circle", "ellipse", "kite", "star", "split_closed_curve", "config1", "config2",
+    "config2_reduced", "random_small", "problem_summary",
+]
+
+
+def circle(r, cx=0.0, cy=0.0):
+    return {"ax": [cx, r], "bx": [0.0, 0.0], "ay": [cy, 0.0], "by": [0.0, r]}
+
+
+def ellipse(a, b, cx=0.0, cy=0.0):
+    return {"ax": [cx, a], "bx": [0.0, 0.0], "ay": [cy, 0.0], "by": [0.0, b]}
+
+
+def kite(cx=0.0, cy=0.0):
+    # x(s) = cos s + 0.65 cos 2s - 0.65, y(s) = 1.5 sin s
+    return {"ax": [cx - 0.65, 1.0, 0.65], "bx": [0.0, 0.0, 0.0],
+            "ay": [cy, 0.0, 0.0], "by": [0.0, 1.5, 0.0]}
+
+
+def star(amp=0.3, lobes=5, phase=0.0, cx=0.0, cy=0.0):
+    """r(theta) = 1 + amp cos(lobes theta + phase), written as a trig polynomial of degree lobes+1."""
+    deg = lobes + 1
+    ax = [0.0] * (deg + 1); bx = [0.0] * (deg + 1); ay = [0.0] * (deg + 1); by = [0.0] * (deg + 1)
+    ax[0] += cx; ay[0] += cy
+    ax[1] += 1.0; by[1] += 1.0
+    # amp cos(n t + p) cos t = amp/2 [cos((n+1)t + p) + cos((n-1)t + p)]
+    # amp cos(n t + p) sin t = amp/2 [sin((n+1)t + p) - sin((n-1)t + p)]
+    c, s = math.cos(phase), math.sin(phase)
+    for m, sgn in ((lobes + 1, 1.0), (lobes - 1, -1.0)):
+        ax[m] += 0.5 * amp * c; bx[m] += -0.5 * amp * s
+        by[m] += sgn * 0.5 * amp * c; ay[m] += sgn * 0.5 * amp * s
+    return {"ax": ax, "bx": bx, "ay": ay, "by": by}
+
+
+def split_closed_curve(curve_index, n, span_factor=1.25, theta_off=0.0):
+    """n overlapping arcs of span span_factor*2pi/n centred at theta_off + 2 pi k/n."""
+    span = span_factor * 2.0 * math.pi / n
+    arcs = []
+    for k in range(n):
+        c = theta_off + 2.0 * math.pi * k / n
+        arcs.append((curve_index, c - 0.5 * span, c + 0.5 * span))
+    return arcs
+
+
+def _signal(kind, sign, amp, carrier, centre, width, z0=(0.0, 0.0), direction=(1.0, 0.0)):
+    return {"kind": int(kind), "z0": [float(z0[0]), float(z0[1])],
+            "dir": [float(direction[0]), float(direction[1])], "sign": float(sign),
+            "amp": float(amp), "carrier": float(carrier), "centre": float(centre), "width": float(width)}
+
+
+def _options(W, L, M, Q, H, n_period, obs, tout0, dtout, n_tout, N_fixed=0, N_min=0, N_off=0,
+             N_ppw=0.0, interior=0):
+    return {"W": float(W), "L": int(L), "N_fixed": int(N_fixed), "N_min": int(N_min), "N_off": int(N_off),
+            "N_ppw": float(N_ppw), "M": int(M), "Q": int(Q), "H": float(H), "n_period": int(n_period),
+            "interior": int(interior), "obs": np.asarray(obs, dtype=np.float64).reshape(-1, 2),
+            "tout0": float(tout0), "dtout": float(dtout), "n_tout": int(n_tout)}
+
+
+def config1(L=257, M=8, N=96):
+    """Unit disk, 3 arcs of 150 deg at 0/120/240 deg, interior point source at (2, 0.5),
+    f(t) = sin(4t) exp(-((t-4)/1.5)^2), boundary data = +field (exact interior solution = u^i),
+    N = 96, omega in [0, 24] with 257 points, M = 8, 5 interior observation points, t in [0, 10]."""
+    curves = [circle(1.0)]
+    arcs = split_closed_curve(0, 3, 1.25, 0.0)
+    signal = _signal(0, +1.0, 1.0, 4.0, 4.0, 1.5, z0=(2.0, 0.5))
+    obs = [(0.5, 0.0), (0.0, 0.0), (-0.3, 0.4), (0.2, -0.6), (-0.5, -0.2)]
+    options = _options(24.0, L, M, 1, 20.0, 2048, obs, 0.0, 0.05, 201, N_fixed=N, interior=1)
+    return {"name": "disk3-pointsource", "curves": curves, "arcs": arcs, "signal": signal, "options": options}
+
+
+def _min_gap(c1, c2, n=720):
+    th = np.linspace(0.0, 2.0 * math.pi, n, endpoint=False)
+
+    def pts(c):
+        x = np.zeros_like(th); y = np.zeros_like(th)
+        for k in range(len(c["ax"])):
+            x += c["ax"][k] * np.cos(k * th) + c["bx"][k] * np.sin(k * th)
+            y += c["ay"][k] * np.cos(k * th) + c["by"][k] * np.sin(k * th)
+        return np.stack([x, y], 1)
+
+    a, b = pts(c1), pts(c2)
+    return float(np.min(np.linalg.norm(a[:, None, :] - b[None, :, :], axis=2)))
+
+
+def config2(seed=2, L=1025, M=12, W=60.0, Q=1, H=40.0, n_period=4096, n_tout=201):
+    """Exterior problem, 4 obstacles (ellipses (1,0.6) and (0.8,0.5), kite, circle r=0.7) at seeded
+    positions with pairwise gap >= 0.5, each split into 2 overlapping arcs (8 arcs), plane-wave pulse
+    f(t) = sin(10t) exp(-((t-6)/2)^2) at a seeded angle, N = max(48, ceil(2 omega len/pi) + 16),
+    omega in [0, 60] with 1025 points, M = 12, outputs at 5 points on a circle of radius 6."""
+    rng = np.random.default_rng(seed)
+    makers = [lambda cx, cy: ellipse(1.0, 0.6, cx, cy), lambda cx, cy: ellipse(0.8, 0.5, cx, cy),
+              lambda cx, cy: kite(cx, cy), lambda cx, cy: circle(0.7, cx, cy)]
+    curves = []
+    for mk in makers:
+        for _ in range(10000):
+            cx, cy = rng.uniform(-2.5, 2.5, size=2)
+            c = mk(float(cx), float(cy))
+            if all(_min_gap(c, o) >= 0.5 for o in curves):
+                curves.append(c)
+                break
+        else:
+            raise RuntimeError("could not place obstacle")
+    arcs = []
+    for ci in range(len(curves)):
+        arcs += split_closed_curve(ci, 2, 1.25, 0.0)
+    ang = float(rng.uniform(0.0, 2.0 * math.pi))
+    signal = _signal(1, -1.0, 1.0, 10.0, 6.0, 2.0, direction=(math.cos(ang), math.sin(ang)))
+    ph = float(rng.uniform(0.0, 2.0 * math.pi))
+    obs = [(6.0 * math.cos(ph + 2 * math.pi * k / 5), 6.0 * math.sin(ph + 2 * math.pi * k / 5)) for k in range(5)]
+    options = _options(W, L, M, Q, H, n_period, obs, 0.0, 20.0 / (n_tout - 1), n_tout,
+                       N_min=48, N_off=16, N_ppw=2.0 / math.pi, interior=0)
+    return {"name": "4obstacles-planewave", "curves": curves, "arcs": arcs, "signal": signal, "options": options}
+
+
+def config2_reduced(seed=2, L=129, M=3, n_period=512):
+    """Config 2's geometry and node-count rule (N from 48 up to the full maximum at omega = 60) on a
+    coarser frequency grid and fewer steps, sized for the oracle to finish in seconds."""
+    return config2(seed=seed, L=L, M=M, n_period=n_period)
+
+
+def random_small(seed, n_arcs_per_curve=3, n_curves=1, L=33, M=2, Q=1, N_fixed=0, W=10.0, kind=None,
+                 H=8.0, n_period=256):
+    """Tiny seeded problems for edge-case parity (few frequencies, small N, ragged sizes)."""
+    rng = np.random.default_rng(seed)
+    curves = []
+    for ci in range(n_curves):
+        cx, cy = 4.0 * ci, 0.0
+        t = rng.integers(0, 3)
+        if t == 0:
+            curves.append(circle(float(rng.uniform(0.6, 1.2)), cx, cy))
+        elif t == 1:
+            curves.append(ellipse(float(rng.uniform(0.7, 1.2)), float(rng.uniform(0.4, 0.7)), cx, cy))
+        else:
+            curves.append(star(0.2, 5, float(rng.uniform(0, 2 * math.pi)), cx, cy))
+    arcs = []
+    for ci in range(n_curves):
+        arcs += split_closed_curve(ci, n_arcs_per_curve, 1.25, float(rng.uniform(0, 2 * math.pi)))
+    if kind is None:
+        kind = int(rng.integers(0, 2))
+    if kind == 0:
+        signal = _signal(0, -1.0, 1.0, float(rng.uniform(3, 6)), 2.5, 1.0, z0=(4.0 * (n_curves - 1) + 2.2, 0.8))
+    else:
+        a = float(rng.uniform(0, 2 * math.pi))
+        signal = _signal(1, -1.0, 1.0, float(rng.uniform(3, 6)), 2.5, 1.0, direction=(math.cos(a), math.sin(a)))
+    obs = [(0.0, 3.0), (4.0 * (n_curves - 1) + 3.0, 0.0)]
+    options = _options(W, L, M, Q, H, n_period, obs, 0.0, 0.1, 61,
+                       N_fixed=N_fixed, N_min=12, N_off=6, N_ppw=1.0 / math.pi)
+    return {"name": f"small-{seed}", "curves": curves, "arcs": arcs, "signal": signal, "options": options}
+
+
+def problem_summary(p):
+    o = p["options"]
+    return (f"{p['name']}: {len(p['curves'])} curves, {len(p['arcs'])} arcs, L={o['L']}, W={o['W']}, "
+            f"M={o['M']}, Q={o['Q']}, H={o['H']}, n_period={o['n_period']}")
