@@ -1,0 +1,193 @@
+/*
+ * fthms.h -- C ABI of the GB300 (sm_103a) FTH-MS open-arc hot path.
+ *
+ * The library runs the data-parallel core of the frequency-time hybrid multiple-scattering
+ * method of arxiv 2507.05725 (FTH-MS, Algorithm 1 and Sections 3.1-4.3): for every open arc
+ * Gamma_j and every frequency omega_l it assembles the log-split Chebyshev Nystrom matrix of the
+ * single-layer operator V_Gamma_j (eq. FDBIEk-interior), factors it once, and then for each
+ * multiple-scattering step m and time window q solves for the density, evaluates the arc's
+ * potential S_Gamma_j (eq. FDsolk-interior) on the other arcs and at observation points,
+ * synthesises it back to time with recentring (eq. TDsol), applies the partition-of-unity and
+ * overlap masks of eqs. criterion_int2 / vtilde and takes the windowed slow transform
+ * (eq. Fourierk) that is the next step's data.
+ *
+ * Conventions shared by every call:
+ *  - Plain C types only; every pointer argument is a HOST pointer unless its name ends in _dev.
+ *  - All inputs are copied before the call returns; the caller may free them immediately.
+ *  - Outputs go into caller-owned buffers whose capacity (in doubles) is passed; when it is too
+ *    small the call returns FTHMS_EINVAL and writes the required size to *needed if given.
+ *  - Errors are status codes only; fthms_last_error() returns a message for the calling thread.
+ *  - Complex values are interleaved (re, im) doubles.
+ *  - Wave speed c = 1, so kappa = omega.  Time convention of eqs. forwardFT/backwardFT:
+ *    G(omega) = int g(t) e^{i omega t} dt; the kernel is (i/4) H0^(1)(kappa |x - y|).
+ */
+#ifndef FTHMS_H
+#define FTHMS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FTHMS_OK = 0,
+  FTHMS_EINVAL = 1,   /* invalid argument, geometry or option (nothing was enqueued) */
+  FTHMS_ENOMEM = 2,   /* the job does not fit the context's HBM budget or device memory */
+  FTHMS_ENOCONV = 3,  /* reserved: iterative refinement did not reach its tolerance */
+  FTHMS_ETIMEOUT = 4, /* fthms_wait: the job did not finish within the timeout */
+  FTHMS_ECUDA = 5,    /* a CUDA runtime call failed; the message names it */
+  FTHMS_EBUSY = 6,    /* results requested before the job finished */
+  FTHMS_ENOTIMPL = 7  /* option value not implemented in this build */
+} fthms_status;
+
+typedef struct fthms_ctx fthms_ctx; /* device, stream, memory budget */
+typedef struct fthms_req fthms_req; /* one FTH-MS job and its device-resident state */
+
+/* Closed or open curve X(theta) = sum_{k=0}^{degree} (ax[k] cos k theta + bx[k] sin k theta,
+ * ay[k] cos k theta + by[k] sin k theta); each array has degree+1 entries (b[0] is ignored).
+ * Covers circles, ellipses, the kite and r = 1 + a cos(n theta + p) stars exactly. */
+typedef struct {
+  int degree;
+  const double* ax;
+  const double* bx;
+  const double* ay;
+  const double* by;
+} fthms_curve;
+
+/* Overlapping patch Gamma_j = X([theta_a, theta_b]) of curve `curve` (Section 3.1): theta_b >
+ * theta_a, theta may exceed 2 pi.  Arcs of one curve must each overlap exactly their cyclic
+ * neighbours; an arc alone on its curve is an open-arc obstacle (chi = 1). */
+typedef struct {
+  int curve;
+  double theta_a, theta_b;
+} fthms_arc;
+
+/* Incident field u^i(x, t) (Section 5's incident-field families, restricted to real signals):
+ * kind 0 = point source at z0: u = (1/(2 pi)) int_0^inf f(t - |x - z0| cosh v) dv,
+ * kind 1 = plane wave along unit vector dir: u = f(t - x.dir),
+ * f(t) = amp sin(carrier t) exp(-((t - centre)/width)^2).  Boundary data g_{j,1} = sign chi_j u^i
+ * (eq. criterion_int1 has sign = -1). */
+typedef struct {
+  int kind;
+  double z0[2];
+  double dir[2];
+  double sign;
+  double amp, carrier, centre, width;
+} fthms_signal;
+
+/* Discretisation and output options.
+ *  W, L      : frequencies omega_l = l*(W/(L-1)), l = 0..L-1; l = 1..L-1 are solved.
+ *  N rule    : nodes per arc N_j(omega) = N_fixed if > 0, else max(N_min, ceil(N_ppw*omega*len_j)
+ *              + N_off), len_j the arc length.  The transfer mesh of arc j is its first-kind
+ *              Chebyshev grid of size N_j(omega_{L-1}).
+ *  M         : multiple-scattering steps (Algorithm 1's outer loop).
+ *  Q, H      : time windows sqcap_q(t) = sqcap(t - s_q), s_q = 1.5 (q-1) H (Section 5).
+ *  n_period  : internal time samples per period 2 pi/h of the frequency grid (power of two,
+ *              16..16384); dt = 2 pi/(h n_period), t_n = -H + n dt covering [-H, s_Q + H].
+ *  obs_xy    : n_obs observation points (x, y), host array of 2*n_obs doubles.
+ *  n_tout, tout0, dtout : output times tout0 + k dtout of the traces u_M(z, t) (eq. mult-scatt-int).
+ *  precision : 0 = FP64 throughout (the only value implemented here; others -> FTHMS_ENOTIMPL).
+ *  keep_densities : 1 keeps phi_{j,m,q}(omega_l) of every step for fthms_densities; 0 keeps only
+ *              the sum over m. */
+typedef struct {
+  double W;
+  int L;
+  int N_fixed, N_min, N_off;
+  double N_ppw;
+  int M, Q;
+  double H;
+  int n_period;
+  int interior;
+  int n_obs;
+  const double* obs_xy;
+  int n_tout;
+  double tout0, dtout;
+  int precision;
+  int keep_densities;
+} fthms_options;
+
+typedef struct {
+  double gpu_ms;          /* device time of the last run of the job (CUDA events on the ctx stream) */
+  double setup_ms;        /* host planning time of fthms_prepare */
+  long long systems;      /* P (L-1): (arc, omega) systems assembled and factored */
+  long long solves;       /* P (L-1) M Q: executions of Algorithm 1's BIE solve */
+  long long kernel_launches; /* kernels launched by one run */
+  size_t device_bytes;    /* device memory held by the job */
+  double cross_entries;   /* stored cross-evaluation matrix entries */
+  double hankel_evals;    /* kernel evaluations in assembly (self + cross) */
+} fthms_stats_t;
+
+/* Create a context on CUDA device `device` that enqueues all work on `cuda_stream` (a
+ * cudaStream_t; NULL = the legacy default stream).  hbm_budget_bytes caps the device memory of
+ * all live jobs (0 = no cap).  Returns FTHMS_ECUDA if the device cannot be used. */
+fthms_status fthms_create(fthms_ctx** out, int device, size_t hbm_budget_bytes, void* cuda_stream);
+fthms_status fthms_destroy(fthms_ctx* ctx);
+
+/* Plan a job (Section 3.1 geometry, Section 5 grids) on the host, allocate its device memory and
+ * upload its tables; enqueues no compute.  Validation failures return FTHMS_EINVAL (overlapping
+ * rules of Section 3.1 violated, window wider than one period 2 pi/h, n_period not a power of
+ * two, ...); a job above the budget returns FTHMS_ENOMEM.  *out receives the job handle. */
+fthms_status fthms_prepare(fthms_ctx* ctx, const fthms_curve* curves, int ncurves,
+                           const fthms_arc* arcs, int narcs, const fthms_signal* signal,
+                           const fthms_options* options, fthms_req** out);
+
+/* Enqueue the whole hot path of a prepared job on the context stream (asynchronous): assembly,
+ * factorisation, m = 1 data, M multiple-scattering steps, output traces.  May be called again
+ * (recomputes everything from the uploaded tables). */
+fthms_status fthms_run(fthms_req* req);
+
+/* fthms_prepare followed by fthms_run. */
+fthms_status fthms_submit(fthms_ctx* ctx, const fthms_curve* curves, int ncurves,
+                          const fthms_arc* arcs, int narcs, const fthms_signal* signal,
+                          const fthms_options* options, fthms_req** out);
+
+/* *done = 1 when the last run finished (0 otherwise); never blocks. */
+fthms_status fthms_poll(fthms_req* req, int* done);
+/* Block until the last run finished or timeout_ms elapsed (negative = no limit):
+ * FTHMS_ETIMEOUT on timeout, FTHMS_ECUDA if the device reported an error. */
+fthms_status fthms_wait(fthms_req* req, int timeout_ms);
+
+/* Output traces u_M(z_k, t_i) (eq. mult-scatt-int, evaluated directly at the output times),
+ * row-major [n_obs][n_tout] doubles into out (cap >= n_obs*n_tout).  Waits for the job. */
+fthms_status fthms_traces(fthms_req* req, double* out, size_t cap);
+
+/* Densities phi_{j,m,q}(omega_l)[i] of arc j: m in 1..M (requires keep_densities) or m = 0 for
+ * the sum over m; q in 0..Q-1.  Layout: for l = 1..L-1, N_j(omega_l) complex values at the
+ * first-kind nodes t_i = cos((2i+1) pi/(2N)), i = 0..N-1, where phi(t) = Psi(x(t)) |x'(t)|
+ * sqrt(1 - t^2) is the smooth factor of eq. singularity.  Needs 2 sum_l N_j(omega_l) doubles;
+ * the size is written to *needed (may be NULL).  Waits for the job. */
+fthms_status fthms_densities(fthms_req* req, int arc, int m, int q, double* out, size_t cap,
+                             size_t* needed);
+
+/* Same layout, written to a device buffer on the context stream (no host copy). */
+fthms_status fthms_densities_dev(fthms_req* req, int arc, int m, int q, double* out_dev,
+                                 size_t cap);
+
+/* Node counts N_j(omega_l) for l = 1..L-1, row-major [narcs][L-1] ints (cap >= narcs*(L-1)). */
+fthms_status fthms_node_counts(fthms_req* req, int* out, size_t cap);
+
+fthms_status fthms_stats(fthms_req* req, fthms_stats_t* out);
+fthms_status fthms_release(fthms_req* req);
+
+/* Message of the last failed call on this thread (never NULL). */
+const char* fthms_last_error(void);
+
+/* ---- kernel-level entry points (device buffers, enqueued on `cuda_stream`) -------------------- */
+
+/* Bessel functions of order 0 for z_dev[i] > 0 (the kernel of Section 2.1): J0, Y0 and the
+ * regular part Yhat0 = Y0 - (2/pi)(ln(z/2) + gamma) J0.  Any output pointer may be NULL.
+ * Returns FTHMS_EINVAL for n < 0. */
+fthms_status fthms_bessel0(const double* z_dev, double* j0_dev, double* y0_dev,
+                           double* yhat0_dev, int n, void* cuda_stream);
+
+/* Nystrom matrix of V_Gamma on one arc (eq. FDBIEk-interior with the log-split Chebyshev rule):
+ * A[i + l*N] (column-major, interleaved complex, 2*N*N doubles in A_dev) for N first-kind nodes
+ * at wavenumber kappa > 0.  Allocates and frees its own temporary tables. */
+fthms_status fthms_assemble_self(const fthms_curve* curve, const fthms_arc* arc, int N,
+                                 double kappa, double* A_dev, void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FTHMS_H */

@@ -13,8 +13,8 @@ Discrete form (our reading; the paper's FC/FCC transforms are replaced by a unif
   forward   G_q(omega_l) = dt sum_n g(t_n) sqcap_q(t_n) e^{i omega_l (t_n - s_q)}
   inverse   v(t) = sum_q [valid_q(t)] (1/pi) Re sum_l w_l V_q(omega_l) e^{-i omega_l (t - s_q)}
             with w_l = h (l < L-1), h/2 (l = L-1), valid_q(t): -H <= t - s_q < 2 pi/h - H.
-  Phases: omega_l (t_n - s_q) = l*c_q + 2 pi (l n mod n_period)/n_period with c_q = h*(t_0 - s_q),
-  the same real number with the integer part of the reduction done exactly.
+  Phases: e^{i omega_l (t_n - s_q)} = e^{i l*c_q} e^{2 pi i (l n mod n_period)/n_period} with
+  c_q = h*(t_0 - s_q): the same number, with the integer part of the phase reduced exactly.
 """
 from __future__ import annotations
 
@@ -107,6 +107,8 @@ class TimeGrid:
         self.h = self.W / (self.L - 1)
         self.omega = np.array([l * self.h for l in range(self.L)])
         self.dt = 2.0 * math.pi / (self.h * self.K)
+        if 2.0 * math.pi / self.h < 2.0 * self.H:
+            raise ValueError("window support 2H exceeds the period 2 pi/h of the frequency grid")
         self.t0 = -self.H
         self.s = np.array([1.5 * q * self.H for q in range(self.Q)])      # s_q, q = 1..Q (0-based)
         self.NT = int((self.s[-1] + 2.0 * self.H) / self.dt) + 1
@@ -120,12 +122,13 @@ class TimeGrid:
         self.win = np.stack([window(self.t - sq, self.H) for sq in self.s])   # sqcap_q(t_n)
 
     def _phase_grid(self, q, sign):
-        """e^{sign * i omega_l (t_n - s_q)} for l = 0..L-1, n = 0..N_T-1 (exact integer reduction)."""
+        """e^{sign * i omega_l (t_n - s_q)} = e^{sign i l c_q} e^{sign 2 pi i (l n mod K)/K} for
+        l = 0..L-1, n = 0..N_T-1 (the integer part of the phase reduced exactly)."""
         l = np.arange(self.L, dtype=np.int64)
         n = np.arange(self.NT, dtype=np.int64)
         m = np.mod(np.outer(l, n), self.K).astype(np.float64)
-        ph = np.outer(l.astype(np.float64) * self.c[q], np.ones(self.NT)) + 2.0 * math.pi * m / self.K
-        return np.exp(sign * 1j * ph)
+        a = np.exp(sign * 1j * (l.astype(np.float64) * self.c[q]))
+        return a[:, None] * np.exp(sign * 2j * math.pi * m / self.K)
 
     def forward(self, g):
         """Slow forward transform (eq. Fourierk) of real samples g[..., N_T] -> [..., Q, L]."""

@@ -1,0 +1,523 @@
+// C ABI of the FTH-MS library (declared in include/fthms.h): contexts, jobs, device memory and the
+// order in which the pipeline stages of kernels.cu are enqueued.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "fthms.h"
+#include "kernels.h"
+#include "plan.h"
+
+using namespace fthms;
+
+namespace {
+
+thread_local std::string g_last_error = "no error";
+
+fthms_status fail(fthms_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+fthms_status cuda_fail(cudaError_t e, const char* what) {
+  char buf[256];
+  snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString(e));
+  g_last_error = buf;
+  return FTHMS_ECUDA;
+}
+
+#define CK(call)                                              \
+  do {                                                        \
+    cudaError_t e__ = (call);                                 \
+    if (e__ != cudaSuccess) return cuda_fail(e__, #call);     \
+  } while (0)
+
+std::mutex g_init_mu;
+bool g_init_done[64] = {};
+
+fthms_status ensure_device(int dev) {
+  CK(cudaSetDevice(dev));
+  std::lock_guard<std::mutex> lk(g_init_mu);
+  if (dev >= 0 && dev < 64 && !g_init_done[dev]) {
+    CK(init_constants());
+    g_init_done[dev] = true;
+  }
+  return FTHMS_OK;
+}
+
+}  // namespace
+
+struct fthms_ctx {
+  int device = 0;
+  size_t budget = 0;
+  size_t in_use = 0;
+  cudaStream_t stream = nullptr;
+  std::mutex mu;
+};
+
+struct fthms_req {
+  fthms_ctx* ctx = nullptr;
+  Plan plan;
+  DevJob J{};
+  std::vector<void*> allocs;
+  size_t bytes = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  bool ran = false;
+  int launches = 0;
+  double setup_ms = 0.0;
+};
+
+namespace {
+
+template <class T>
+fthms_status dev_upload(fthms_req* r, const std::vector<T>& v, const T** out) {
+  *out = nullptr;
+  if (v.empty()) return FTHMS_OK;
+  void* p = nullptr;
+  size_t b = v.size() * sizeof(T);
+  CK(cudaMalloc(&p, b));
+  r->allocs.push_back(p);
+  r->bytes += b;
+  CK(cudaMemcpy(p, v.data(), b, cudaMemcpyHostToDevice));
+  *out = static_cast<const T*>(p);
+  return FTHMS_OK;
+}
+
+template <class T>
+fthms_status dev_alloc(fthms_req* r, size_t count, T** out) {
+  *out = nullptr;
+  if (count == 0) return FTHMS_OK;
+  void* p = nullptr;
+  size_t b = count * sizeof(T);
+  CK(cudaMalloc(&p, b));
+  r->allocs.push_back(p);
+  r->bytes += b;
+  *out = static_cast<T*>(p);
+  return FTHMS_OK;
+}
+
+void free_req(fthms_req* r) {
+  for (void* p : r->allocs) cudaFree(p);
+  r->allocs.clear();
+  if (r->ev0) cudaEventDestroy(r->ev0);
+  if (r->ev1) cudaEventDestroy(r->ev1);
+}
+
+#define TRY(x)                         \
+  do {                                 \
+    fthms_status s__ = (x);            \
+    if (s__ != FTHMS_OK) return s__;   \
+  } while (0)
+
+fthms_status upload_job(fthms_req* r) {
+  Plan& p = r->plan;
+  DevJob& J = r->J;
+  J.P = p.P; J.L = p.L; J.Q = p.Q; J.K = p.K; J.NT = p.NT; J.M = p.M;
+  J.n_obs = p.n_obs; J.n_tout = p.n_tout;
+  J.nsys = (int)p.sys.size();
+  J.n_act = (int)p.act_idx.size();
+  J.n_grp = (int)p.grps.size();
+  J.n_asm = (int)p.asms.size();
+  J.n_tiles = (int)p.self_tiles.size();
+  J.n_rlogN = (int)p.rlogN.size();
+  J.n_restr = (int)p.restr_pairs.size();
+  J.logK = 0;
+  while ((1 << J.logK) < p.K) ++J.logK;
+  J.max_n = p.maxN;
+  J.max_nmax = 0;
+  for (int k = 0; k < p.P; ++k) J.max_nmax = std::max(J.max_nmax, p.Nmax[k]);
+  J.acc_cap = std::max(J.max_nmax, p.n_obs);
+  J.h = p.h; J.dt = p.dt; J.sign = p.sig.sign;
+  J.sig_kind = p.sig.kind;
+  J.z0x = p.sig.z0[0]; J.z0y = p.sig.z0[1];
+  J.dirx = p.sig.dir[0]; J.diry = p.sig.dir[1];
+  J.amp = p.sig.amp; J.carrier = p.sig.carrier; J.centre = p.sig.centre; J.width = p.sig.width;
+  J.H = p.H; J.period = p.period;
+  J.vec_total = p.vec_total;
+
+  TRY(dev_upload(r, p.sys, &J.sys));
+  TRY(dev_upload(r, p.panels, &J.panels));
+  TRY(dev_upload(r, p.node_t, &J.node_t));
+  TRY(dev_upload(r, p.node_x, &J.node_x));
+  TRY(dev_upload(r, p.node_y, &J.node_y));
+  TRY(dev_upload(r, p.node_sp, &J.node_sp));
+  TRY(dev_upload(r, p.rlogN, &J.rlogN));
+  TRY(dev_upload(r, p.rlog_off_N, &J.rlog_off_N));
+  TRY(dev_alloc(r, (size_t)p.rlog_total, &J.rlog));
+  std::vector<int> rn;
+  for (auto& pr : p.restr_pairs) { rn.push_back(pr.first); rn.push_back(pr.second); }
+  TRY(dev_upload(r, rn, &J.restr_N));
+  TRY(dev_upload(r, p.restr_off, &J.restr_off));
+  TRY(dev_alloc(r, (size_t)p.restr_total, &J.restr));
+  TRY(dev_upload(r, p.restr_of_sys, &J.restr_of_sys));
+  TRY(dev_upload(r, p.self_tiles, &J.tiles));
+  TRY(dev_upload(r, p.tgts, &J.tgts));
+  TRY(dev_upload(r, p.pairs, &J.pairs));
+  TRY(dev_upload(r, p.e_off, &J.e_off));
+  TRY(dev_upload(r, p.asms, &J.asms));
+  TRY(dev_upload(r, p.grps, &J.grps));
+  TRY(dev_upload(r, p.blks, &J.blks));
+  TRY(dev_upload(r, p.tpanel, &J.tpanel));
+  TRY(dev_upload(r, p.tr_off, &J.tr_off));
+  TRY(dev_upload(r, p.chi, &J.chi));
+  TRY(dev_upload(r, p.act_off, &J.act_off));
+  TRY(dev_upload(r, p.act_idx, &J.act_idx));
+  TRY(dev_upload(r, p.act_arc, &J.act_arc));
+  TRY(dev_upload(r, p.win, &J.win));
+  TRY(dev_upload(r, p.wl, &J.wl));
+  TRY(dev_upload(r, p.c_q, &J.c_q));
+  TRY(dev_upload(r, p.nlo, &J.nlo));
+  TRY(dev_upload(r, p.tout, &J.tout));
+  TRY(dev_upload(r, p.s_q, &J.s_q));
+  TRY(dev_alloc(r, (size_t)p.mat_total, &J.A));
+  TRY(dev_alloc(r, (size_t)p.piv_total, &J.piv));
+  TRY(dev_alloc(r, (size_t)p.piv_total, &J.dinv));
+  TRY(dev_alloc(r, (size_t)p.vec_total, &J.G));
+  TRY(dev_alloc(r, (size_t)p.vec_total, &J.phi));
+  TRY(dev_alloc(r, (size_t)p.vec_total, &J.phi_sum));
+  J.phi_all = nullptr;
+  if (p.opt.keep_densities) TRY(dev_alloc(r, (size_t)p.vec_total * p.M, &J.phi_all));
+  TRY(dev_alloc(r, (size_t)p.spec_total, &J.W));
+  TRY(dev_alloc(r, (size_t)p.spec_total, &J.Gt));
+  TRY(dev_alloc(r, (size_t)p.e_total, &J.E));
+  TRY(dev_alloc(r, (size_t)std::max(1, p.n_obs * p.Q * p.L), &J.Vobs));
+  TRY(dev_alloc(r, (size_t)std::max(1, p.n_obs * p.n_tout), &J.traces));
+  TRY(dev_alloc(r, (size_t)p.K / 2, &J.fft_tw));
+  TRY(dev_alloc(r, (size_t)p.Q * p.L, &J.syn_tw));
+  TRY(dev_alloc(r, (size_t)p.Q * p.L, &J.fwd_tw));
+  return FTHMS_OK;
+}
+
+fthms_status enqueue(fthms_req* r) {
+  const DevJob& J = r->J;
+  cudaStream_t st = r->ctx->stream;
+  int nl = 0;
+  CK(cudaEventRecord(r->ev0, st));
+  CK(launch_tables(J, st, &nl));
+  CK(launch_assemble_self(J, st, &nl));
+  CK(launch_lu(J, st, &nl));
+  CK(launch_cross_assemble(J, st, &nl));
+  CK(cudaMemsetAsync(J.Gt, 0, (size_t)r->plan.spec_total * sizeof(double2), st));
+  CK(cudaMemsetAsync(J.W, 0, (size_t)r->plan.spec_total * sizeof(double2), st));
+  CK(cudaMemsetAsync(J.Vobs, 0, (size_t)std::max(1, J.n_obs * J.Q * J.L) * sizeof(double2), st));
+  CK(launch_incident(J, st, &nl));
+  CK(launch_restrict(J, st, &nl));
+  for (int m = 1; m <= J.M; ++m) {
+    CK(launch_solve(J, m, st, &nl));
+    CK(launch_cross_apply(J, st, &nl));
+    if (m < J.M) {
+      CK(launch_synth_fwd(J, st, &nl));
+      CK(launch_restrict(J, st, &nl));
+    }
+  }
+  CK(launch_traces(J, st, &nl));
+  CK(cudaEventRecord(r->ev1, st));
+  r->launches = nl;
+  r->ran = true;
+  return FTHMS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fthms_status fthms_create(fthms_ctx** out, int device, size_t hbm_budget_bytes, void* cuda_stream) {
+  if (!out) return fail(FTHMS_EINVAL, "fthms_create: out is NULL");
+  *out = nullptr;
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+  if (device < 0 || device >= n) return fail(FTHMS_EINVAL, "fthms_create: no such device");
+  TRY(ensure_device(device));
+  fthms_ctx* c = new fthms_ctx;
+  c->device = device;
+  c->budget = hbm_budget_bytes;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  *out = c;
+  return FTHMS_OK;
+}
+
+fthms_status fthms_destroy(fthms_ctx* ctx) {
+  if (!ctx) return fail(FTHMS_EINVAL, "fthms_destroy: NULL context");
+  delete ctx;
+  return FTHMS_OK;
+}
+
+fthms_status fthms_prepare(fthms_ctx* ctx, const fthms_curve* curves, int ncurves, const fthms_arc* arcs,
+                           int narcs, const fthms_signal* signal, const fthms_options* options,
+                           fthms_req** out) {
+  if (!ctx || !out) return fail(FTHMS_EINVAL, "fthms_prepare: NULL context or output");
+  *out = nullptr;
+  auto t0 = std::chrono::steady_clock::now();
+  fthms_req* r = new fthms_req;
+  r->ctx = ctx;
+  std::string err;
+  int st = build_plan(curves, ncurves, arcs, narcs, signal, options, r->plan, err);
+  if (st != FTHMS_OK) {
+    delete r;
+    return fail((fthms_status)st, "fthms_prepare: " + err);
+  }
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (ctx->budget && ctx->in_use + r->plan.device_bytes > ctx->budget) {
+      char buf[160];
+      snprintf(buf, sizeof buf, "fthms_prepare: job needs %.3f GB, budget leaves %.3f GB",
+               r->plan.device_bytes / 1e9, (ctx->budget - ctx->in_use) / 1e9);
+      delete r;
+      return fail(FTHMS_ENOMEM, buf);
+    }
+    ctx->in_use += r->plan.device_bytes;
+  }
+  fthms_status s = ensure_device(ctx->device);
+  if (s == FTHMS_OK) {
+    cudaError_t e1 = cudaEventCreate(&r->ev0), e2 = cudaEventCreate(&r->ev1);
+    if (e1 != cudaSuccess || e2 != cudaSuccess) s = cuda_fail(e1 != cudaSuccess ? e1 : e2, "cudaEventCreate");
+  }
+  if (s == FTHMS_OK) s = upload_job(r);
+  if (s != FTHMS_OK) {
+    bool oom = g_last_error.find("out of memory") != std::string::npos;
+    std::string msg = g_last_error;
+    free_req(r);
+    {
+      std::lock_guard<std::mutex> lk(ctx->mu);
+      ctx->in_use -= r->plan.device_bytes;
+    }
+    delete r;
+    cudaGetLastError();
+    return fail(oom ? FTHMS_ENOMEM : s, msg);
+  }
+  r->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  *out = r;
+  return FTHMS_OK;
+}
+
+fthms_status fthms_run(fthms_req* req) {
+  if (!req) return fail(FTHMS_EINVAL, "fthms_run: NULL job");
+  TRY(ensure_device(req->ctx->device));
+  return enqueue(req);
+}
+
+fthms_status fthms_submit(fthms_ctx* ctx, const fthms_curve* curves, int ncurves, const fthms_arc* arcs,
+                          int narcs, const fthms_signal* signal, const fthms_options* options,
+                          fthms_req** out) {
+  TRY(fthms_prepare(ctx, curves, ncurves, arcs, narcs, signal, options, out));
+  fthms_status s = fthms_run(*out);
+  if (s != FTHMS_OK) {
+    std::string msg = g_last_error;
+    fthms_release(*out);
+    *out = nullptr;
+    return fail(s, msg);
+  }
+  return FTHMS_OK;
+}
+
+fthms_status fthms_poll(fthms_req* req, int* done) {
+  if (!req || !done) return fail(FTHMS_EINVAL, "fthms_poll: NULL argument");
+  if (!req->ran) { *done = 0; return FTHMS_OK; }
+  cudaError_t e = cudaEventQuery(req->ev1);
+  if (e == cudaSuccess) { *done = 1; return FTHMS_OK; }
+  if (e == cudaErrorNotReady) { *done = 0; return FTHMS_OK; }
+  return cuda_fail(e, "fthms_poll");
+}
+
+fthms_status fthms_wait(fthms_req* req, int timeout_ms) {
+  if (!req) return fail(FTHMS_EINVAL, "fthms_wait: NULL job");
+  if (!req->ran) return fail(FTHMS_EINVAL, "fthms_wait: job was never run");
+  TRY(ensure_device(req->ctx->device));
+  auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    cudaError_t e = cudaEventQuery(req->ev1);
+    if (e == cudaSuccess) return FTHMS_OK;
+    if (e != cudaErrorNotReady) return cuda_fail(e, "fthms_wait");
+    if (timeout_ms >= 0) {
+      double el = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+      if (el > timeout_ms) return fail(FTHMS_ETIMEOUT, "fthms_wait: timed out");
+    }
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+}
+
+fthms_status fthms_traces(fthms_req* req, double* out, size_t cap) {
+  if (!req || (!out && cap)) return fail(FTHMS_EINVAL, "fthms_traces: NULL argument");
+  size_t n = (size_t)req->plan.n_obs * req->plan.n_tout;
+  if (cap < n) return fail(FTHMS_EINVAL, "fthms_traces: output buffer too small");
+  TRY(fthms_wait(req, -1));
+  if (n) CK(cudaMemcpy(out, req->J.traces, n * sizeof(double), cudaMemcpyDeviceToHost));
+  return FTHMS_OK;
+}
+
+static fthms_status density_range(fthms_req* req, int arc, int m, int q, const double2** base,
+                                  long long* first, long long* last, size_t* needed) {
+  const Plan& p = req->plan;
+  if (arc < 0 || arc >= p.P || q < 0 || q >= p.Q || m < 0 || m > p.M)
+    return fail(FTHMS_EINVAL, "fthms_densities: arc, m or q out of range");
+  if (m > 0 && !p.opt.keep_densities)
+    return fail(FTHMS_EINVAL, "fthms_densities: per-step densities need keep_densities = 1");
+  size_t n = 0;
+  for (int l = 1; l < p.L; ++l) n += 2 * (size_t)p.Ntab[(size_t)arc * p.L + l];
+  if (needed) *needed = n;
+  const SysDesc& s0 = p.sys[(size_t)arc * (p.L - 1)];
+  const SysDesc& s1 = p.sys[(size_t)arc * (p.L - 1) + p.L - 2];
+  *first = s0.vec_off;
+  *last = s1.vec_off + (long long)p.Q * s1.N;
+  *base = m == 0 ? req->J.phi_sum : req->J.phi_all + (long long)(m - 1) * p.vec_total;
+  return FTHMS_OK;
+}
+
+fthms_status fthms_densities(fthms_req* req, int arc, int m, int q, double* out, size_t cap, size_t* needed) {
+  if (!req) return fail(FTHMS_EINVAL, "fthms_densities: NULL job");
+  const double2* base;
+  long long first, last;
+  size_t n;
+  TRY(density_range(req, arc, m, q, &base, &first, &last, &n));
+  if (needed) *needed = n;
+  if (!out || cap < n) return fail(FTHMS_EINVAL, "fthms_densities: output buffer too small");
+  TRY(fthms_wait(req, -1));
+  const Plan& p = req->plan;
+  std::vector<double2> h((size_t)(last - first));
+  CK(cudaMemcpy(h.data(), base + first, h.size() * sizeof(double2), cudaMemcpyDeviceToHost));
+  size_t o = 0;
+  for (int l = 1; l < p.L; ++l) {
+    const SysDesc& s = p.sys[(size_t)arc * (p.L - 1) + l - 1];
+    const double2* src = h.data() + (s.vec_off - first) + (long long)q * s.N;
+    for (int i = 0; i < s.N; ++i) {
+      out[o++] = src[i].x;
+      out[o++] = src[i].y;
+    }
+  }
+  return FTHMS_OK;
+}
+
+fthms_status fthms_densities_dev(fthms_req* req, int arc, int m, int q, double* out_dev, size_t cap) {
+  if (!req || !out_dev) return fail(FTHMS_EINVAL, "fthms_densities_dev: NULL argument");
+  const double2* base;
+  long long first, last;
+  size_t n;
+  TRY(density_range(req, arc, m, q, &base, &first, &last, &n));
+  if (cap < n) return fail(FTHMS_EINVAL, "fthms_densities_dev: output buffer too small");
+  TRY(ensure_device(req->ctx->device));
+  const Plan& p = req->plan;
+  size_t o = 0;
+  for (int l = 1; l < p.L; ++l) {
+    const SysDesc& s = p.sys[(size_t)arc * (p.L - 1) + l - 1];
+    CK(cudaMemcpyAsync(out_dev + o, base + s.vec_off + (long long)q * s.N, (size_t)s.N * sizeof(double2),
+                       cudaMemcpyDeviceToDevice, req->ctx->stream));
+    o += 2 * (size_t)s.N;
+  }
+  return FTHMS_OK;
+}
+
+fthms_status fthms_node_counts(fthms_req* req, int* out, size_t cap) {
+  if (!req || !out) return fail(FTHMS_EINVAL, "fthms_node_counts: NULL argument");
+  const Plan& p = req->plan;
+  if (cap < (size_t)p.P * (p.L - 1)) return fail(FTHMS_EINVAL, "fthms_node_counts: buffer too small");
+  for (int j = 0; j < p.P; ++j)
+    for (int l = 1; l < p.L; ++l) out[(size_t)j * (p.L - 1) + l - 1] = p.Ntab[(size_t)j * p.L + l];
+  return FTHMS_OK;
+}
+
+fthms_status fthms_stats(fthms_req* req, fthms_stats_t* out) {
+  if (!req || !out) return fail(FTHMS_EINVAL, "fthms_stats: NULL argument");
+  const Plan& p = req->plan;
+  std::memset(out, 0, sizeof *out);
+  out->setup_ms = req->setup_ms;
+  out->systems = (long long)p.P * (p.L - 1);
+  out->solves = (long long)p.P * (p.L - 1) * p.M * p.Q;
+  out->kernel_launches = req->launches;
+  out->device_bytes = req->bytes;
+  out->cross_entries = (double)p.e_total;
+  out->hankel_evals = p.hankel_self + p.hankel_cross;
+  if (req->ran) {
+    TRY(fthms_wait(req, -1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, req->ev0, req->ev1));
+    out->gpu_ms = ms;
+  }
+  return FTHMS_OK;
+}
+
+fthms_status fthms_release(fthms_req* req) {
+  if (!req) return fail(FTHMS_EINVAL, "fthms_release: NULL job");
+  if (req->ran) cudaEventSynchronize(req->ev1);
+  free_req(req);
+  {
+    std::lock_guard<std::mutex> lk(req->ctx->mu);
+    req->ctx->in_use -= req->plan.device_bytes;
+  }
+  delete req;
+  return FTHMS_OK;
+}
+
+const char* fthms_last_error(void) { return g_last_error.c_str(); }
+
+fthms_status fthms_bessel0(const double* z_dev, double* j0_dev, double* y0_dev, double* yhat0_dev, int n,
+                           void* cuda_stream) {
+  if (n < 0 || (n > 0 && !z_dev)) return fail(FTHMS_EINVAL, "fthms_bessel0: bad arguments");
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  TRY(ensure_device(dev));
+  CK(launch_bessel0(z_dev, j0_dev, y0_dev, yhat0_dev, n, static_cast<cudaStream_t>(cuda_stream)));
+  return FTHMS_OK;
+}
+
+fthms_status fthms_assemble_self(const fthms_curve* curve, const fthms_arc* arc, int N, double kappa,
+                                 double* A_dev, void* cuda_stream) {
+  if (!curve || !arc || !A_dev || N < 2 || N > 1024 || !(kappa > 0) || !(arc->theta_b > arc->theta_a))
+    return fail(FTHMS_EINVAL, "fthms_assemble_self: bad arguments");
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  TRY(ensure_device(dev));
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  Curve c;
+  c.ax.assign(curve->ax, curve->ax + curve->degree + 1);
+  c.bx.assign(curve->bx, curve->bx + curve->degree + 1);
+  c.ay.assign(curve->ay, curve->ay + curve->degree + 1);
+  c.by.assign(curve->by, curve->by + curve->degree + 1);
+  std::vector<double> t, x, y, sp;
+  arc_nodes(c, arc->theta_a, arc->theta_b, N, t, x, y, sp);
+  fthms_req tmp;
+  DevJob& J = tmp.J;
+  std::vector<SysDesc> sys(1);
+  sys[0].arc = 0; sys[0].l = 1; sys[0].N = N; sys[0].panel = 0; sys[0].mat_off = 0; sys[0].vec_off = 0;
+  sys[0].piv_off = 0; sys[0].rlog_off = 0; sys[0].kappa = kappa;
+  std::vector<Panel> panels(1, Panel{0, N, 0});
+  std::vector<int> rlogN(1, N);
+  std::vector<long long> rlog_off(1, 0);
+  std::vector<SelfTile> tiles;
+  int nt = (N + kSelfTile - 1) / kSelfTile;
+  for (int a = 0; a < nt; ++a)
+    for (int b = a; b < nt; ++b) tiles.push_back(SelfTile{0, a, b});
+  fthms_status s = FTHMS_OK;
+  if (s == FTHMS_OK) s = dev_upload(&tmp, sys, &J.sys);
+  if (s == FTHMS_OK) s = dev_upload(&tmp, panels, &J.panels);
+  if (s == FTHMS_OK) s = dev_upload(&tmp, t, &J.node_t);
+  if (s == FTHMS_OK) s = dev_upload(&tmp, x, &J.node_x);
+  if (s == FTHMS_OK) s = dev_upload(&tmp, y, &J.node_y);
+  if (s == FTHMS_OK) s = dev_upload(&tmp, sp, &J.node_sp);
+  if (s == FTHMS_OK) s = dev_upload(&tmp, rlogN, &J.rlogN);
+  if (s == FTHMS_OK) s = dev_upload(&tmp, rlog_off, &J.rlog_off_N);
+  if (s == FTHMS_OK) s = dev_upload(&tmp, tiles, &J.tiles);
+  if (s == FTHMS_OK) s = dev_alloc(&tmp, (size_t)N * N, &J.rlog);
+  if (s == FTHMS_OK) {
+    J.A = reinterpret_cast<double2*>(A_dev);
+    J.n_rlogN = 1;
+    J.n_tiles = (int)tiles.size();
+    J.max_n = N;
+    J.K = 16;  // unused FFT tables are not launched below
+    int nl = 0;
+    cudaError_t e = launch_tables_rlog_only(J, st, &nl);
+    if (e == cudaSuccess) e = launch_assemble_self(J, st, &nl);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) s = cuda_fail(e, "fthms_assemble_self");
+  }
+  free_req(&tmp);
+  return s;
+}
+
+}  // extern "C"

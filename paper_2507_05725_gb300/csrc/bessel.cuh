@@ -1,0 +1,134 @@
+// FP64 Bessel functions of order 0 for the Helmholtz kernel (i/4) H0^(1)(z) = (i/4)(J0 + i Y0)
+// of Section 2.1, written from the classical expansions:
+//   z <= 4       : power series J0 = sum_k (-z^2/4)^k/(k!)^2 and the regular part
+//                  Yhat0 = Y0 - (2/pi)(ln(z/2) + gamma) J0 = (2/pi) sum_{k>=1} (-1)^{k+1} H_k (z^2/4)^k/(k!)^2
+//                  (H_k the harmonic numbers; Abramowitz-Stegun 9.1.12-9.1.13).
+//   4 < z < 20   : Miller's backward recurrence J_{n-1} = (2n/z) J_n - J_{n+1} from order ~z+32,
+//                  normalised by J0 + 2 sum_k J_{2k} = 1, with Neumann's series
+//                  Yhat0 = -(4/pi) sum_{k>=1} (-1)^k J_{2k}/k (A-S 9.1.87-9.1.88).
+//   z >= 20      : Hankel's asymptotic expansion with 10 + 10 terms,
+//                  H0^(1)(z) ~ sqrt(2/(pi z)) e^{i(z - pi/4)} sum_k (-i)^k a_k/z^k,
+//                  a_k = 1^2 3^2 ... (2k-1)^2/(k! 8^k)  (A-S 9.2.7-9.2.10, DLMF 10.17.5).
+// Accuracy (checked against arbitrary-precision values): <= 4e-16 absolute for J0, Yhat0 below 20,
+// <= 4e-16 relative to the amplitude sqrt(2/(pi z)) above.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace fthms {
+
+constexpr double kEulerGamma = 0.57721566490153286060651209008240243;
+constexpr double kPiD = 3.14159265358979323846;
+constexpr double kInvPi = 0.31830988618379067153776752674502872;
+constexpr double kTwoOverPi = 0.63661977236758134307553505349005745;
+constexpr double kSqrtHalf = 0.70710678118654752440084436210484904;
+constexpr double kBesselSmall = 4.0;
+constexpr double kBesselLarge = 20.0;
+
+// 1/k^2, harmonic numbers H_k and 1/k for k = 1..32 (index k-1), and the Hankel coefficients a_k
+// (filled by init_constants(); this header is included by one translation unit only).
+__constant__ double c_inv_k2[32];
+__constant__ double c_harm[32];
+__constant__ double c_inv_k[32];
+__constant__ double c_hank_a[20];
+
+// Power series on 0 < z <= 4 (fixed trip count: converged lanes read the constant tables in
+// lock-step, so every table load is a broadcast).
+__device__ __forceinline__ void bessel0_series(double z, double& J0, double& Yh) {
+  const double x = 0.25 * z * z;
+  double term = 1.0, j = 1.0, y = 0.0;
+#pragma unroll 1
+  for (int k = 1; k <= 17; ++k) {
+    term *= -x * c_inv_k2[k - 1];
+    j += term;
+    y = fma(-c_harm[k - 1], term, y);
+  }
+  J0 = j;
+  Yh = kTwoOverPi * y;
+}
+
+// Miller backward recurrence on 4 < z < 20 from the fixed order 52 >= z + 32.
+__device__ __forceinline__ void bessel0_miller(double z, double& J0, double& Yh) {
+  const double tz = 2.0 / z;
+  double fp1 = 0.0, f = 1e-30, S = 0.0, T = 0.0;
+#pragma unroll 2
+  for (int n = 52; n >= 2; n -= 2) {
+    const int k = n >> 1;
+    S += f;
+    T = fma((k & 1) ? -c_inv_k[k - 1] : c_inv_k[k - 1], f, T);
+    const double fm1 = fma((double)n * tz, f, -fp1);
+    const double fm2 = fma((double)(n - 1) * tz, fm1, -f);
+    fp1 = fm1;
+    f = fm2;
+  }
+  const double inv = 1.0 / fma(2.0, S, f);
+  J0 = f * inv;
+  Yh = -4.0 * kInvPi * T * inv;
+}
+
+// Hankel asymptotics on z >= 20: J0 and Y0.
+__device__ __forceinline__ void bessel0_asym(double z, double& J0, double& Y0) {
+  const double w = 1.0 / z;
+  const double w2 = -w * w;
+  double P = c_hank_a[18], Qa = c_hank_a[19];
+#pragma unroll
+  for (int k = 8; k >= 0; --k) {
+    P = fma(P, w2, c_hank_a[2 * k]);
+    Qa = fma(Qa, w2, c_hank_a[2 * k + 1]);
+  }
+  Qa *= w;
+  const double amp = sqrt(kTwoOverPi * w);
+  double s, c;
+  sincos(z, &s, &c);
+  const double cx = (c + s) * kSqrtHalf;   // cos(z - pi/4)
+  const double sx = (s - c) * kSqrtHalf;   // sin(z - pi/4)
+  J0 = amp * fma(P, cx, Qa * sx);
+  Y0 = amp * fma(P, sx, -Qa * cx);
+}
+
+// Kernel pieces used by the Nystrom rules:
+//  J0(z) and either Yhat0(z) (z < 20, has_yhat = true) or Y0(z) (z >= 20, has_yhat = false).
+struct Bessel0 {
+  double j0;
+  double y;      // Yhat0 if has_yhat else Y0
+  bool has_yhat;
+};
+
+__device__ __forceinline__ Bessel0 bessel0(double z) {
+  Bessel0 b;
+  if (z <= kBesselSmall) {
+    bessel0_series(z, b.j0, b.y);
+    b.has_yhat = true;
+  } else if (z < kBesselLarge) {
+    bessel0_miller(z, b.j0, b.y);
+    b.has_yhat = true;
+  } else {
+    bessel0_asym(z, b.j0, b.y);
+    b.has_yhat = false;
+  }
+  return b;
+}
+
+// Full kernel Phi = (i/4) H0^(1)(z) = (-Y0/4, J0/4) for z > 0.
+__device__ __forceinline__ double2 phi_kernel(double z) {
+  Bessel0 b = bessel0(z);
+  double y0 = b.has_yhat ? fma(kTwoOverPi * (log(0.5 * z) + kEulerGamma), b.j0, b.y) : b.y;
+  return make_double2(-0.25 * y0, 0.25 * b.j0);
+}
+
+// Log-split pieces at a pair with parameter distance dts = |t - s| > 0 and z = kappa R:
+//   K1 = -J0/(2 pi),  K2 = K - K1 ln|t - s|
+//      = (i/4) J0 - (J0/(2 pi)) [ln(z/(2|t-s|)) + gamma] - Yhat0/4   (z < 20)
+//      = (i/4) J0 - Y0/4 + (J0/(2 pi)) ln|t-s|                       (z >= 20)
+__device__ __forceinline__ void log_split(double z, double dts, double& K1, double2& K2) {
+  Bessel0 b = bessel0(z);
+  K1 = -0.5 * kInvPi * b.j0;
+  double re;
+  if (b.has_yhat) {
+    re = fma(K1, log(z / (2.0 * dts)) + kEulerGamma, -0.25 * b.y);
+  } else {
+    re = fma(-K1, log(dts), -0.25 * b.y);
+  }
+  K2 = make_double2(re, 0.25 * b.j0);
+}
+
+}  // namespace fthms

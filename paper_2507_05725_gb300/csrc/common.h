@@ -1,0 +1,79 @@
+// Shared host/device descriptors of the FTH-MS library (plain structs, no CUDA types).
+#pragma once
+#include <cstdint>
+
+namespace fthms {
+
+// One (arc j, frequency l) open-arc system: N first-kind nodes, matrix A_j(omega_l).
+struct SysDesc {
+  int arc;
+  int l;            // frequency index, 1..L-1
+  int N;
+  int panel;        // node panel (arc, N)
+  long long mat_off;  // complex offset of the N x N matrix / LU factor (column-major)
+  long long vec_off;  // complex offset of the Q x N data / density block ([q][i])
+  long long piv_off;  // int offset of the N pivots
+  long long rlog_off; // double offset of the N x N self log-weight table
+  double kappa;
+};
+
+// Nodes of arc `arc` at first-kind Chebyshev size N: t_i, x(t_i), |x'(t_i)|.
+struct Panel {
+  int arc;
+  int N;
+  long long off;    // offset into the node arrays
+};
+
+// Target of a cross-evaluation block (receiving arc k or the observation set).
+struct CrossTgt {
+  double x, y;
+  double tstar;     // parameter of the target on the source arc's curve (near rule), else 0
+  int near;         // 1: near rule (same curve, 1 < |t*| <= 3)
+  int out;          // transfer-node index on arc k (or observation index)
+};
+
+// A (source arc j -> receiver k) block at one frequency: rows = targets, cols = N_j(omega_l).
+struct CrossBlk {
+  int j;            // source arc
+  int sys;          // system index of (j, l)
+  int N;
+  int nrows;
+  int tgt_off;      // first CrossTgt of the (k, j) pair
+  int pad;
+  long long e_off;  // complex offset of the row-major nrows x N block
+};
+
+// Group of blocks sharing (l, k): one launch unit of the cross matvec.
+struct CrossGrp {
+  int l;
+  int k;            // receiving arc, or P for the observation points
+  int blk_begin, blk_end;
+};
+
+// Receiver/source pair (k, j), k = P for the observation points.
+struct PairDesc {
+  int k, j;
+  int tgt_off;      // first CrossTgt
+  int nrows;
+};
+
+// Assembly task: rows [row0, row0+nrows) of pair `pair` for the band of frequencies l0..l1
+// (inclusive) that share the same N_j(omega_l); E offsets come from e_off[pair*L + l].
+struct CrossAsm {
+  int pair;
+  int l0, l1;
+  int N;
+  int row0, nrows;
+  int panel;        // node panel of source arc j at N
+  int pad;
+};
+
+// Upper-triangular tile of one self matrix.
+struct SelfTile {
+  int sys;
+  int ti, tl;       // tile row / column (tile edge = kSelfTile)
+};
+
+constexpr int kSelfTile = 16;
+
+}  // namespace fthms

@@ -1,0 +1,805 @@
+// CUDA kernels (sm_103a, FP64) of the FTH-MS open-arc hot path.
+//
+// Stages (one job):
+//   tables         FFT twiddles, recentring phases, self log-weight tables, restriction tables
+//   assemble_self  log-split Chebyshev Nystrom matrices A_j(omega_l)        (Section 4.2-4.3)
+//   lu             A = P L U per (arc, omega), reused for every step and window (Algorithm 1)
+//   cross_assemble stored S_Gamma_j rows at the other arcs' transfer nodes   (eq. FDsolk-interior)
+//   incident       g_{k,1} = sign chi_k u^i on the transfer meshes, slow transform (eqs.
+//                  criterion_int1, Fourierk)
+//   restrict       transfer-mesh spectra -> data on the N_k(omega_l) solve nodes
+//   per step m:
+//     solve        phi = A^{-1} G                                             (eq. FDBIEk-interior)
+//     cross_apply  W_k = sum_{j != k, masked} S_j[phi_j] (eq. vtilde) and the observation sum
+//     synth_fwd    recentred inverse transform (eq. TDsol), g = -chi_k w (eq. criterion_int2),
+//                  windowed slow transform (eq. Fourierk) -- one CTA per transfer node, in shared
+//                  memory, with a radix-2 FFT
+//   traces         u_M(z, t) at the output times (eq. mult-scatt-int)
+#include <cstdio>
+
+#include "bessel.cuh"
+#include "kernels.h"
+
+namespace fthms {
+
+cudaError_t init_constants() {
+  double ik2[32], harm[32], ik[32], ha[20];
+  double H = 0.0;
+  for (int k = 1; k <= 32; ++k) {
+    ik2[k - 1] = 1.0 / ((double)k * k);
+    H += 1.0 / k;
+    harm[k - 1] = H;
+    ik[k - 1] = 1.0 / k;
+  }
+  ha[0] = 1.0;
+  for (int k = 1; k < 20; ++k) ha[k] = ha[k - 1] * (double)((2 * k - 1) * (2 * k - 1)) / (8.0 * k);
+  cudaError_t e;
+  if ((e = cudaMemcpyToSymbol(c_inv_k2, ik2, sizeof ik2)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyToSymbol(c_harm, harm, sizeof harm)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyToSymbol(c_inv_k, ik, sizeof ik)) != cudaSuccess) return e;
+  return cudaMemcpyToSymbol(c_hank_a, ha, sizeof ha);
+}
+
+namespace {
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+// c + a * b
+__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c) {
+  return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
+}
+// c - a * b
+__device__ __forceinline__ double2 cfms(double2 a, double2 b, double2 c) {
+  return make_double2(fma(-a.x, b.x, fma(a.y, b.y, c.x)), fma(-a.x, b.y, fma(-a.y, b.x, c.y)));
+}
+__device__ __forceinline__ double2 crecip(double2 a) {
+  double d = 1.0 / fma(a.x, a.x, a.y * a.y);
+  return make_double2(a.x * d, -a.y * d);
+}
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+
+// ---------------------------------------------------------------------------------------------
+// Bessel test kernel
+__global__ void k_bessel0(const double* __restrict__ z, double* j0, double* y0, double* yh, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double zz = z[i];
+  Bessel0 b = bessel0(zz);
+  double lg = kTwoOverPi * (log(0.5 * zz) + kEulerGamma);
+  double Y0 = b.has_yhat ? fma(lg, b.j0, b.y) : b.y;
+  double Yh = b.has_yhat ? b.y : fma(-lg, b.j0, b.y);
+  if (j0) j0[i] = b.j0;
+  if (y0) y0[i] = Y0;
+  if (yh) yh[i] = Yh;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Tables
+
+__global__ void k_fft_tw(double2* tw, int K) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= K / 2) return;
+  double s, c;
+  sincospi(2.0 * r / K, &s, &c);
+  tw[r] = make_double2(c, -s);   // e^{-2 pi i r/K}
+}
+
+// syn_tw[q][l] = (w_l/pi) e^{-i l c_q} e^{-2 pi i (l nlo_q mod K)/K},  fwd_tw[q][l] = dt e^{i l c_q}
+__global__ void k_freq_tw(DevJob J) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= J.Q * J.L) return;
+  int q = idx / J.L, l = idx % J.L;
+  double s, c;
+  sincos((double)l * J.c_q[q], &s, &c);
+  long long m = ((long long)l * J.nlo[q]) % J.K;
+  double s2, c2;
+  sincospi(2.0 * (double)m / J.K, &s2, &c2);
+  double wl = J.wl[l] * kInvPi;
+  double2 e1 = make_double2(c, -s), e2 = make_double2(c2, -s2);
+  double2 sy = cmul(e1, e2);
+  J.syn_tw[idx] = make_double2(wl * sy.x, wl * sy.y);
+  J.fwd_tw[idx] = make_double2(J.dt * c, J.dt * s);
+}
+
+// Self log weights Rlog_il = -(pi/N) [ln 2 + F(|i-l|) + F(i+l+1)], F(m) = sum_{n=1}^{N-1} cos(n m pi/N)/n
+// (the product-to-sum form of -(pi/N)[ln 2 + 2 sum_n T_n(t_i) T_n(t_l)/n]).
+__global__ void k_rlog(DevJob J) {
+  extern __shared__ double sh[];
+  const int N = J.rlogN[blockIdx.x];
+  double* cosr = sh;           // 2N
+  double* F = sh + 2 * N;      // 2N
+  double* invn = sh + 4 * N;   // N
+  for (int r = threadIdx.x; r < 2 * N; r += blockDim.x) cosr[r] = cospi((double)r / N);
+  for (int n = threadIdx.x; n < N; n += blockDim.x) invn[n] = n ? 1.0 / n : 0.0;
+  __syncthreads();
+  for (int m = threadIdx.x; m < 2 * N; m += blockDim.x) {
+    double acc = 0.0;
+    for (int n = 1; n < N; ++n) acc = fma(cosr[(n * m) % (2 * N)], invn[n], acc);
+    F[m] = acc;
+  }
+  __syncthreads();
+  double* out = J.rlog + J.rlog_off_N[blockIdx.x];
+  const double ln2 = 0.69314718055994530941723212145817657;
+  const double sc = -kPiD / N;
+  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+    int i = e / N, l = e % N;
+    int d = i > l ? i - l : l - i;
+    out[e] = sc * (ln2 + F[d] + F[i + l + 1]);
+  }
+}
+
+// Transposed restriction tables RT[x][i] = l_x(t_i): the Lagrange basis of the first-kind grid of
+// size M evaluated at the first-kind nodes of size N, in the closed form
+//   l_x(t_i) = T_M(t_i) sin(beta_x) (-1)^x / (M (t_i - tau_x))
+// with the phases reduced exactly through D = (2i+1)M - (2x+1)N and S = (2i+1)M + (2x+1)N:
+//   l_x(t_i) = sin(beta_x) sinpi(D/(2N)) / (2M sinpi(S/(4NM)) sinpi(D/(4NM))),  = 1 when D = 0.
+__global__ void k_restr(DevJob J) {
+  const int t = blockIdx.y;
+  const int N = J.restr_N[2 * t], M = J.restr_N[2 * t + 1];
+  double* RT = J.restr + J.restr_off[t];
+  const long long total = (long long)N * M;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    int x = (int)(e / N), i = (int)(e % N);
+    long long D = (long long)(2 * i + 1) * M - (long long)(2 * x + 1) * N;
+    double v;
+    if (D == 0) {
+      v = 1.0;
+    } else {
+      long long S = (long long)(2 * i + 1) * M + (long long)(2 * x + 1) * N;
+      double nm4 = 4.0 * (double)N * (double)M;
+      double sb = sinpi((double)(2 * x + 1) / (2.0 * M));
+      double num = sinpi((double)D / (2.0 * N));
+      double den = 2.0 * M * sinpi((double)S / nm4) * sinpi((double)D / nm4);
+      v = sb * num / den;
+    }
+    RT[e] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Self assembly: A_il = K1(t_i,t_l) Rlog_il + K2(t_i,t_l) pi/N, symmetric in (i, l).
+__global__ void __launch_bounds__(256) k_assemble_self(DevJob J) {
+  const SelfTile tile = J.tiles[blockIdx.x];
+  const SysDesc s = J.sys[tile.sys];
+  const int N = s.N;
+  const int i = tile.ti * kSelfTile + (threadIdx.x % kSelfTile);
+  const int l = tile.tl * kSelfTile + (threadIdx.x / kSelfTile);
+  if (i >= N || l >= N) return;
+  if (tile.ti == tile.tl && i > l) return;
+  const Panel pn = J.panels[s.panel];
+  const double rl = J.rlog[s.rlog_off + (long long)i * N + l];
+  const double w = kPiD / N;
+  double K1;
+  double2 K2;
+  if (i == l) {
+    K1 = -0.5 * kInvPi;
+    K2 = make_double2(-0.5 * kInvPi * (kEulerGamma + log(0.5 * s.kappa * J.node_sp[pn.off + i])), 0.25);
+  } else {
+    double dx = J.node_x[pn.off + i] - J.node_x[pn.off + l];
+    double dy = J.node_y[pn.off + i] - J.node_y[pn.off + l];
+    double R = sqrt(fma(dx, dx, dy * dy));
+    double dts = fabs(J.node_t[pn.off + i] - J.node_t[pn.off + l]);
+    log_split(s.kappa * R, dts, K1, K2);
+  }
+  double2 v = make_double2(fma(K1, rl, K2.x * w), K2.y * w);
+  double2* A = J.A + s.mat_off;
+  A[(long long)l * N + i] = v;
+  if (i != l) A[(long long)i * N + l] = v;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Blocked right-looking LU with partial pivoting (pivot: max |re| + |im|, first index on ties),
+// one CTA of 256 threads per system, panel width 8 in shared memory, column-major factor in HBM.
+constexpr int kNB = 8;
+constexpr int kPS = kNB + 1;   // padded panel row stride (bank-conflict-free column access)
+constexpr int kLuThreads = 256;
+
+__global__ void __launch_bounds__(kLuThreads) k_lu(DevJob J) {
+  extern __shared__ double2 shl[];
+  const SysDesc s = J.sys[blockIdx.x];
+  const int N = s.N;
+  double2* A = J.A + s.mat_off;
+  int* piv = J.piv + s.piv_off;
+  double2* Pn = shl;                       // [N][kPS] panel rows
+  double2* U = shl + (size_t)N * kPS;      // [kNB][N] U12 rows
+  __shared__ double red_v[kLuThreads / 32];
+  __shared__ int red_i[kLuThreads / 32];
+  __shared__ int spiv[kNB];
+  __shared__ int s_p;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  for (int k0 = 0; k0 < N; k0 += kNB) {
+    const int w = min(kNB, N - k0);
+    const int nr = N - k0;
+    for (int idx = tid; idx < nr * w; idx += kLuThreads) {
+      int c = idx / nr, r = idx % nr;
+      Pn[r * kPS + c] = A[(long long)(k0 + c) * N + k0 + r];
+    }
+    __syncthreads();
+    for (int c = 0; c < w; ++c) {
+      double best = -1.0;
+      int bi = 0x7fffffff;
+      for (int r = c + tid; r < nr; r += kLuThreads) {
+        double2 v = Pn[r * kPS + c];
+        double m = fabs(v.x) + fabs(v.y);
+        if (m > best) { best = m; bi = r; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        double ov = __shfl_down_sync(0xffffffffu, best, o);
+        int oi = __shfl_down_sync(0xffffffffu, bi, o);
+        if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+      }
+      if (lane == 0) { red_v[wid] = best; red_i[wid] = bi; }
+      __syncthreads();
+      if (tid == 0) {
+        double b = red_v[0];
+        int ii = red_i[0];
+        for (int q = 1; q < kLuThreads / 32; ++q)
+          if (red_v[q] > b || (red_v[q] == b && red_i[q] < ii)) { b = red_v[q]; ii = red_i[q]; }
+        if (ii == 0x7fffffff) ii = c;
+        s_p = ii;
+        spiv[c] = ii;
+        piv[k0 + c] = k0 + ii;
+      }
+      __syncthreads();
+      const int p = s_p;
+      if (p != c && tid < w) {
+        double2 t = Pn[c * kPS + tid];
+        Pn[c * kPS + tid] = Pn[p * kPS + tid];
+        Pn[p * kPS + tid] = t;
+      }
+      __syncthreads();
+      const double2 inv = crecip(Pn[c * kPS + c]);
+      for (int r = c + 1 + tid; r < nr; r += kLuThreads) {
+        double2 lr = cmul(Pn[r * kPS + c], inv);
+        Pn[r * kPS + c] = lr;
+        for (int cc = c + 1; cc < w; ++cc) Pn[r * kPS + cc] = cfms(lr, Pn[c * kPS + cc], Pn[r * kPS + cc]);
+      }
+      __syncthreads();
+    }
+    for (int idx = tid; idx < nr * w; idx += kLuThreads) {
+      int c = idx / nr, r = idx % nr;
+      A[(long long)(k0 + c) * N + k0 + r] = Pn[r * kPS + c];
+    }
+    // Row interchanges on the columns outside the panel.
+    for (int col = tid; col < N; col += kLuThreads) {
+      if (col >= k0 && col < k0 + w) continue;
+      double2* Ac = A + (long long)col * N + k0;
+      for (int c = 0; c < w; ++c) {
+        int p = spiv[c];
+        if (p != c) { double2 t = Ac[c]; Ac[c] = Ac[p]; Ac[p] = t; }
+      }
+    }
+    __syncthreads();
+    const int nc = N - k0 - w;
+    if (nc > 0) {
+      // U12 = L11^{-1} A12 (unit lower triangular solve), one column per thread.
+      for (int j = tid; j < nc; j += kLuThreads) {
+        double2* Ac = A + (long long)(k0 + w + j) * N + k0;
+        double2 xv[kNB];
+#pragma unroll
+        for (int r = 0; r < kNB; ++r) {
+          if (r < w) {
+            double2 v = Ac[r];
+            for (int c = 0; c < r; ++c) v = cfms(Pn[r * kPS + c], xv[c], v);
+            xv[r] = v;
+            Ac[r] = v;
+            U[r * N + j] = v;
+          }
+        }
+      }
+      __syncthreads();
+      // A22 -= L21 U12.
+      const int mr = nr - w;
+      for (long long idx = tid; idx < (long long)mr * nc; idx += kLuThreads) {
+        int j = (int)(idx / mr), r = (int)(idx % mr);
+        double2* a = A + (long long)(k0 + w + j) * N + k0 + w + r;
+        double2 v = *a;
+#pragma unroll
+        for (int c = 0; c < kNB; ++c)
+          if (c < w) v = cfms(Pn[(w + r) * kPS + c], U[c * N + j], v);
+        *a = v;
+      }
+    }
+    __syncthreads();
+  }
+  for (int k = tid; k < N; k += kLuThreads) J.dinv[s.piv_off + k] = crecip(A[(long long)k * N + k]);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Triangular solves, one warp per system, all Q right-hand sides together.
+constexpr int kSolveWarps = 4;
+
+__global__ void __launch_bounds__(32 * kSolveWarps) k_solve(DevJob J, int m) {
+  extern __shared__ double2 shs[];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int sidx = blockIdx.x * kSolveWarps + wid;
+  if (sidx >= J.nsys) return;
+  const SysDesc s = J.sys[sidx];
+  const int N = s.N, Q = J.Q;
+  double2* b = shs + (size_t)wid * Q * J.max_n;
+  const double2* A = J.A + s.mat_off;
+  const int* piv = J.piv + s.piv_off;
+  const double2* dinv = J.dinv + s.piv_off;
+  const double2* G = J.G + s.vec_off;
+  for (int e = lane; e < Q * N; e += 32) b[e] = G[e];
+  __syncwarp();
+  if (lane < Q) {
+    double2* bq = b + lane * N;
+    for (int k = 0; k < N; ++k) {
+      int p = piv[k];
+      if (p != k) { double2 t = bq[k]; bq[k] = bq[p]; bq[p] = t; }
+    }
+  }
+  __syncwarp();
+  for (int k = 0; k < N - 1; ++k) {
+    const double2* Lc = A + (long long)k * N;
+    for (int q = 0; q < Q; ++q) {
+      const double2 xk = b[q * N + k];
+      for (int i = k + 1 + lane; i < N; i += 32) b[q * N + i] = cfms(Lc[i], xk, b[q * N + i]);
+    }
+    __syncwarp();
+  }
+  for (int k = N - 1; k >= 0; --k) {
+    const double2* Uc = A + (long long)k * N;
+    const double2 dk = dinv[k];
+    for (int q = 0; q < Q; ++q) {
+      const double2 xk = cmul(b[q * N + k], dk);
+      for (int i = lane; i < k; i += 32) b[q * N + i] = cfms(Uc[i], xk, b[q * N + i]);
+      __syncwarp();
+      if (lane == 0) b[q * N + k] = xk;
+    }
+    __syncwarp();
+  }
+  double2* out = J.phi + s.vec_off;
+  double2* sum = J.phi_sum + s.vec_off;
+  double2* all = J.phi_all ? J.phi_all + (long long)(m - 1) * J.vec_total + s.vec_off : nullptr;
+  for (int e = lane; e < Q * N; e += 32) {
+    double2 v = b[e];
+    out[e] = v;
+    sum[e] = m == 1 ? v : cadd(sum[e], v);
+    if (all) all[e] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Cross assembly: stored rows of S_Gamma_j for one (pair, frequency band, 8-row chunk).
+constexpr int kAsmThreads = 256;
+constexpr int kAsmRows = 8;
+
+__global__ void __launch_bounds__(kAsmThreads) k_cross_assemble(DevJob J) {
+  extern __shared__ double sha[];
+  const CrossAsm task = J.asms[blockIdx.x];
+  const PairDesc pr = J.pairs[task.pair];
+  const int N = task.N;
+  const Panel pn = J.panels[task.panel];
+  const CrossTgt* tg = J.tgts + pr.tgt_off + task.row0;
+  double* ctab = sha;                       // 4N: cospi(r/(2N))
+  double* lam = sha + 4 * N;                // kAsmRows x N
+  double* Wn = lam + kAsmRows * N;          // kAsmRows x N near weights
+  __shared__ int any_near;
+  if (threadIdx.x == 0) {
+    int a = 0;
+    for (int r = 0; r < task.nrows; ++r) a |= tg[r].near;
+    any_near = a;
+  }
+  __syncthreads();
+  if (any_near) {
+    for (int r = threadIdx.x; r < 4 * N; r += kAsmThreads) ctab[r] = cospi((double)r / (2.0 * N));
+    // lambda_n(t*) = int log|t* - s| T_n(s)/sqrt(1-s^2) ds for |t*| > 1
+    if (threadIdx.x < task.nrows && tg[threadIdx.x].near) {
+      const double ts = tg[threadIdx.x].tstar;
+      const double rt = sqrt(fma(ts, ts, -1.0));
+      const double zeta = ts > 0 ? ts - rt : ts + rt;
+      double* lr = lam + threadIdx.x * N;
+      lr[0] = kPiD * log(0.5 * (fabs(ts) + rt));
+      double pw = 1.0;
+      for (int n = 1; n < N; ++n) {
+        pw *= zeta;
+        lr[n] = -kPiD * pw / n;
+      }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < task.nrows * N; e += kAsmThreads) {
+      int r = e / N, i = e % N;
+      if (!tg[r].near) continue;
+      const double* lr = lam + r * N;
+      const int step = 2 * i + 1, mod = 4 * N;
+      double acc = 0.0;
+      int ph = 0;
+      for (int n = 1; n < N; ++n) {
+        ph += step;
+        if (ph >= mod) ph -= mod;
+        acc = fma(lr[n], ctab[ph], acc);
+      }
+      Wn[r * N + i] = (lr[0] + 2.0 * acc) / N;
+    }
+    __syncthreads();
+  }
+  const double w = kPiD / N;
+  for (int e = threadIdx.x; e < task.nrows * N; e += kAsmThreads) {
+    const int r = e / N, i = e % N;
+    const CrossTgt t = tg[r];
+    const double dx = t.x - J.node_x[pn.off + i], dy = t.y - J.node_y[pn.off + i];
+    const double R = sqrt(fma(dx, dx, dy * dy));
+    const double wn = t.near ? Wn[r * N + i] : 0.0;
+    const double dts = fabs(t.tstar - J.node_t[pn.off + i]);
+    const long long row = (long long)(task.row0 + r) * N + i;
+    for (int l = task.l0; l <= task.l1; ++l) {
+      const double z = (l * J.h) * R;
+      double2 v;
+      if (t.near) {
+        double K1;
+        double2 K2;
+        log_split(z, dts, K1, K2);
+        v = make_double2(fma(K1, wn, K2.x * w), K2.y * w);
+      } else {
+        double2 K = phi_kernel(z);
+        v = make_double2(K.x * w, K.y * w);
+      }
+      J.E[J.e_off[(long long)task.pair * J.L + l] + row] = v;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Cross apply: W_k(x, q, l) = sum_j sum_i E_{l,k,j}[r, i] phi_j[q, i]; observation sums accumulate.
+constexpr int kApplyThreads = 256;
+
+__global__ void __launch_bounds__(kApplyThreads) k_cross_apply(DevJob J) {
+  extern __shared__ double2 shc[];
+  const CrossGrp g = J.grps[blockIdx.x];
+  const int Q = J.Q, l = g.l;
+  const bool obs = g.k == J.P;
+  const int nout = obs ? J.n_obs : J.panels[J.tpanel[g.k]].N;
+  double2* acc = shc;                              // [Q][nout]
+  double2* ph = shc + (size_t)Q * J.acc_cap;        // [Q][N]
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = kApplyThreads / 32;
+  for (int e = threadIdx.x; e < Q * nout; e += kApplyThreads) acc[e] = make_double2(0.0, 0.0);
+  for (int b = g.blk_begin; b < g.blk_end; ++b) {
+    const CrossBlk B = J.blks[b];
+    const int N = B.N;
+    const double2* p = J.phi + J.sys[B.sys].vec_off;
+    __syncthreads();
+    for (int e = threadIdx.x; e < Q * N; e += kApplyThreads) ph[e] = p[e];
+    __syncthreads();
+    const double2* E = J.E + B.e_off;
+    for (int r = wid; r < B.nrows; r += nw) {
+      const double2* Er = E + (long long)r * N;
+      const int out = J.tgts[B.tgt_off + r].out;
+      for (int q = 0; q < Q; ++q) {
+        double2 s = make_double2(0.0, 0.0);
+        for (int i = lane; i < N; i += 32) s = cfma(Er[i], ph[q * N + i], s);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+          s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+        }
+        if (lane == 0) acc[q * nout + out] = cadd(acc[q * nout + out], s);
+      }
+    }
+  }
+  __syncthreads();
+  if (obs) {
+    for (int e = threadIdx.x; e < Q * nout; e += kApplyThreads) {
+      int q = e / nout, z = e % nout;
+      double2* v = J.Vobs + ((long long)z * Q + q) * J.L + l;
+      *v = cadd(*v, acc[e]);
+    }
+  } else {
+    const long long base = J.tr_off[g.k];
+    for (int e = threadIdx.x; e < Q * nout; e += kApplyThreads) {
+      int q = e / nout, x = e % nout;
+      J.W[((base + x) * Q + q) * J.L + l] = acc[e];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Time-domain kernels: one CTA per active transfer node.
+constexpr int kTimeThreads = 256;
+
+// In-place radix-2 decimation-in-time FFT, y_r = sum_b X_b e^{-2 pi i b r/K}; input in
+// bit-reversed order.
+__device__ void block_fft(double2* buf, int K, int logK, const double2* __restrict__ tw) {
+  for (int s = 1; s <= logK; ++s) {
+    const int half = 1 << (s - 1);
+    const int tws = K >> s;   // twiddle stride
+    for (int j = threadIdx.x; j < K / 2; j += blockDim.x) {
+      const int pos = j & (half - 1);
+      const int i0 = ((j >> (s - 1)) << s) + pos;
+      const int i1 = i0 + half;
+      const double2 wv = tw[pos * tws];
+      const double2 a = buf[i0];
+      const double2 bb = cmul(buf[i1], wv);
+      buf[i0] = cadd(a, bb);
+      buf[i1] = csub(a, bb);
+    }
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ int bitrev(int b, int logK) { return (int)(__brev((unsigned)b) >> (32 - logK)); }
+
+// Windowed slow transforms of g[0..NT) into out[q*L + l] (eq. Fourierk with the exact phase split).
+__device__ void forward_all(const DevJob& J, const double* g, double2* buf, double2* out) {
+  const int K = J.K, NT = J.NT, L = J.L;
+  for (int q = 0; q < J.Q; ++q) {
+    const double* wq = J.win + (long long)q * NT;
+    for (int b = threadIdx.x; b < K; b += blockDim.x) {
+      double acc = 0.0;
+      for (int n = b; n < NT; n += K) acc = fma(g[n], wq[n], acc);
+      buf[bitrev(b, J.logK)] = make_double2(acc, 0.0);
+    }
+    __syncthreads();
+    block_fft(buf, K, J.logK, J.fft_tw);
+    for (int l = threadIdx.x; l < L; l += blockDim.x) {
+      double2 v = make_double2(0.0, 0.0);
+      if (l > 0) {
+        double2 y = buf[l & (K - 1)];
+        v = cmul(J.fwd_tw[q * L + l], make_double2(y.x, -y.y));
+      }
+      out[q * L + l] = v;
+    }
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ double signal_f(const DevJob& J, double t) {
+  const double a = (t - J.centre) / J.width;
+  return J.amp * sin(J.carrier * t) * exp(-a * a);
+}
+
+// u^i at (X, Y) and time t (plane wave, or point source by the trapezoid rule in v).
+__device__ double incident_u(const DevJob& J, double X, double Y, double t) {
+  if (J.sig_kind == 1) return signal_f(J, t - fma(Y, J.diry, X * J.dirx));
+  const double dx = X - J.z0x, dy = Y - J.z0y;
+  const double r = sqrt(fma(dx, dx, dy * dy));
+  const double tau_hi = t - J.centre + 8.0 * J.width;
+  if (tau_hi <= r) return 0.0;
+  const double tau_lo = fmax(r, t - J.centre - 8.0 * J.width);
+  const double v_lo = acosh(tau_lo / r), v_hi = acosh(tau_hi / r);
+  const double rate = (fabs(J.carrier) + 8.0 / J.width) * r * sinh(v_hi) + 1.0;
+  const int n = (int)ceil((v_hi - v_lo) * (1.25 * rate + 24.0) / (2.0 * kPiD) * 2.0) + 16;
+  const double dv = (v_hi - v_lo) / n;
+  double acc = 0.5 * (signal_f(J, t - r * cosh(v_lo)) + signal_f(J, t - r * cosh(v_hi)));
+  for (int k = 1; k < n; ++k) acc += signal_f(J, t - r * cosh(v_lo + k * dv));
+  return acc * dv * (0.5 * kInvPi);
+}
+
+__global__ void __launch_bounds__(kTimeThreads) k_incident(DevJob J) {
+  extern __shared__ double2 sht[];
+  const int a = blockIdx.x;
+  const int k = J.act_arc[a], x = J.act_idx[a];
+  const Panel pn = J.panels[J.tpanel[k]];
+  double2* buf = sht;                               // K
+  double* g = reinterpret_cast<double*>(sht + J.K); // NT
+  const double X = J.node_x[pn.off + x], Y = J.node_y[pn.off + x];
+  const double pref = J.sign * J.chi[J.tr_off[k] + x];
+  for (int n = threadIdx.x; n < J.NT; n += blockDim.x) g[n] = pref * incident_u(J, X, Y, -J.H + n * J.dt);
+  __syncthreads();
+  forward_all(J, g, buf, J.Gt + (J.tr_off[k] + x) * J.Q * J.L);
+}
+
+__global__ void __launch_bounds__(kTimeThreads) k_synth_fwd(DevJob J) {
+  extern __shared__ double2 sht[];
+  const int a = blockIdx.x;
+  const int k = J.act_arc[a], x = J.act_idx[a];
+  const int K = J.K, L = J.L, NT = J.NT;
+  double2* buf = sht;
+  double* g = reinterpret_cast<double*>(sht + K);
+  const long long base = (J.tr_off[k] + x) * J.Q * L;
+  for (int n = threadIdx.x; n < NT; n += blockDim.x) g[n] = 0.0;
+  for (int q = 0; q < J.Q; ++q) {
+    const double2* Wq = J.W + base + (long long)q * L;
+    const double2* st = J.syn_tw + (long long)q * L;
+    for (int b = threadIdx.x; b < K; b += blockDim.x) {
+      double2 acc = make_double2(0.0, 0.0);
+      for (int l = (b == 0 ? K : b); l < L; l += K) acc = cfma(st[l], Wq[l], acc);
+      buf[bitrev(b, J.logK)] = acc;
+    }
+    __syncthreads();
+    block_fft(buf, K, J.logK, J.fft_tw);
+    const int n0 = J.nlo[q];
+    for (int r = threadIdx.x; r < K; r += blockDim.x) {
+      const int n = n0 + r;
+      if (n < NT) g[n] += buf[r].x;
+    }
+    __syncthreads();
+  }
+  const double mchi = -J.chi[J.tr_off[k] + x];
+  for (int n = threadIdx.x; n < NT; n += blockDim.x) g[n] *= mchi;
+  __syncthreads();
+  forward_all(J, g, buf, J.Gt + base);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Restriction of transfer-mesh spectra to the solve nodes of every system.
+constexpr int kRestrThreads = 128;
+
+__global__ void __launch_bounds__(kRestrThreads) k_restrict(DevJob J) {
+  extern __shared__ double2 shr[];
+  const int sidx = blockIdx.x;
+  const SysDesc s = J.sys[sidx];
+  const int k = s.arc, l = s.l, N = s.N, Q = J.Q, L = J.L;
+  const long long base = J.tr_off[k];
+  double2* G = J.G + s.vec_off;
+  const long long off = J.restr_of_sys[sidx];
+  if (off < 0) {
+    for (int e = threadIdx.x; e < Q * N; e += blockDim.x) {
+      int q = e / N, i = e % N;
+      G[e] = J.Gt[((base + i) * Q + q) * L + l];
+    }
+    return;
+  }
+  const int a0 = J.act_off[k], na = J.act_off[k + 1] - a0;
+  for (int e = threadIdx.x; e < Q * na; e += blockDim.x) {
+    int q = e / na, a = e % na;
+    shr[e] = J.Gt[((base + J.act_idx[a0 + a]) * Q + q) * L + l];
+  }
+  __syncthreads();
+  const double* RT = J.restr + off;
+  for (int e = threadIdx.x; e < Q * N; e += blockDim.x) {
+    int q = e / N, i = e % N;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int a = 0; a < na; ++a) {
+      const double rv = RT[(long long)J.act_idx[a0 + a] * N + i];
+      const double2 gv = shr[q * na + a];
+      acc.x = fma(rv, gv.x, acc.x);
+      acc.y = fma(rv, gv.y, acc.y);
+    }
+    G[e] = acc;
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Output traces u_M(z, t) = sum_q [valid] (1/pi) Re sum_l w_l Vobs(z, q, l) e^{-i l h (t - s_q)}.
+__global__ void k_traces(DevJob J) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= J.n_obs * J.n_tout) return;
+  const int z = idx / J.n_tout, it = idx % J.n_tout;
+  const double t = J.tout[it];
+  double acc = 0.0;
+  for (int q = 0; q < J.Q; ++q) {
+    const double rel = t - J.s_q[q];
+    if (!(rel >= -J.H && rel < J.period - J.H)) continue;
+    const double c = J.h * (t - J.s_q[q]);
+    const double2* V = J.Vobs + ((long long)z * J.Q + q) * J.L;
+    for (int l = 1; l < J.L; ++l) {
+      double sn, cs;
+      sincos((double)l * c, &sn, &cs);
+      acc = fma(J.wl[l], fma(V[l].x, cs, V[l].y * sn), acc);
+    }
+  }
+  J.traces[idx] = acc * kInvPi;
+}
+
+inline int cdiv(long long a, int b) { return (int)((a + b - 1) / b); }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------------
+// Launch wrappers
+
+cudaError_t launch_bessel0(const double* z, double* j0, double* y0, double* yh, int n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_bessel0<<<cdiv(n, 256), 256, 0, st>>>(z, j0, y0, yh, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tables(const DevJob& J, cudaStream_t st, int* launches) {
+  k_fft_tw<<<cdiv(J.K / 2, 256), 256, 0, st>>>(J.fft_tw, J.K);
+  k_freq_tw<<<cdiv((long long)J.Q * J.L, 256), 256, 0, st>>>(J);
+  *launches += 2;
+  if (J.n_rlogN > 0) {
+    size_t sh = (size_t)5 * J.max_n * sizeof(double);
+    cudaFuncSetAttribute(k_rlog, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+    k_rlog<<<J.n_rlogN, 256, sh, st>>>(J);
+    *launches += 1;
+  }
+  if (J.n_restr > 0) {
+    dim3 grid(64, J.n_restr);
+    k_restr<<<grid, 256, 0, st>>>(J);
+    *launches += 1;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tables_rlog_only(const DevJob& J, cudaStream_t st, int* launches) {
+  size_t sh = (size_t)5 * J.max_n * sizeof(double);
+  cudaError_t e = cudaFuncSetAttribute(k_rlog, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+  if (e != cudaSuccess) return e;
+  k_rlog<<<J.n_rlogN, 256, sh, st>>>(J);
+  *launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_assemble_self(const DevJob& J, cudaStream_t st, int* launches) {
+  if (J.n_tiles > 0) {
+    k_assemble_self<<<J.n_tiles, 256, 0, st>>>(J);
+    *launches += 1;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lu(const DevJob& J, cudaStream_t st, int* launches) {
+  size_t sh = (size_t)J.max_n * (kNB + kPS) * sizeof(double2);
+  cudaError_t e = cudaFuncSetAttribute(k_lu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+  if (e != cudaSuccess) return e;
+  k_lu<<<J.nsys, kLuThreads, sh, st>>>(J);
+  *launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cross_assemble(const DevJob& J, cudaStream_t st, int* launches) {
+  if (J.n_asm == 0) return cudaSuccess;
+  size_t sh = (size_t)(4 + 2 * kAsmRows) * J.max_n * sizeof(double);
+  cudaError_t e = cudaFuncSetAttribute(k_cross_assemble, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+  if (e != cudaSuccess) return e;
+  k_cross_assemble<<<J.n_asm, kAsmThreads, sh, st>>>(J);
+  *launches += 1;
+  return cudaGetLastError();
+}
+
+static size_t time_smem(const DevJob& J) { return (size_t)J.K * sizeof(double2) + (size_t)J.NT * sizeof(double); }
+
+cudaError_t launch_incident(const DevJob& J, cudaStream_t st, int* launches) {
+  if (J.n_act == 0) return cudaSuccess;
+  size_t sh = time_smem(J);
+  cudaError_t e = cudaFuncSetAttribute(k_incident, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+  if (e != cudaSuccess) return e;
+  k_incident<<<J.n_act, kTimeThreads, sh, st>>>(J);
+  *launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_synth_fwd(const DevJob& J, cudaStream_t st, int* launches) {
+  if (J.n_act == 0) return cudaSuccess;
+  size_t sh = time_smem(J);
+  cudaError_t e = cudaFuncSetAttribute(k_synth_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+  if (e != cudaSuccess) return e;
+  k_synth_fwd<<<J.n_act, kTimeThreads, sh, st>>>(J);
+  *launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_restrict(const DevJob& J, cudaStream_t st, int* launches) {
+  size_t sh = (size_t)J.Q * J.max_nmax * sizeof(double2);
+  cudaError_t e = cudaFuncSetAttribute(k_restrict, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+  if (e != cudaSuccess) return e;
+  k_restrict<<<J.nsys, kRestrThreads, sh, st>>>(J);
+  *launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_solve(const DevJob& J, int m, cudaStream_t st, int* launches) {
+  size_t sh = (size_t)kSolveWarps * J.Q * J.max_n * sizeof(double2);
+  cudaError_t e = cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+  if (e != cudaSuccess) return e;
+  k_solve<<<cdiv(J.nsys, kSolveWarps), 32 * kSolveWarps, sh, st>>>(J, m);
+  *launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cross_apply(const DevJob& J, cudaStream_t st, int* launches) {
+  if (J.n_grp == 0) return cudaSuccess;
+  int nmx = J.max_nmax > J.n_obs ? J.max_nmax : J.n_obs;
+  int nph = J.max_n;
+  size_t sh = (size_t)J.Q * (nmx + nph) * sizeof(double2);
+  cudaError_t e = cudaFuncSetAttribute(k_cross_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+  if (e != cudaSuccess) return e;
+  k_cross_apply<<<J.n_grp, kApplyThreads, sh, st>>>(J);
+  *launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_traces(const DevJob& J, cudaStream_t st, int* launches) {
+  int n = J.n_obs * J.n_tout;
+  if (n == 0) return cudaSuccess;
+  k_traces<<<cdiv(n, 128), 128, 0, st>>>(J);
+  *launches += 1;
+  return cudaGetLastError();
+}
+
+}  // namespace fthms

@@ -1,0 +1,82 @@
+// Launch wrappers of the FTH-MS CUDA kernels (host-callable, C++ linkage, device pointers).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "common.h"
+
+namespace fthms {
+
+// Device-side view of one job: every pointer is device memory owned by the job.
+struct DevJob {
+  int P, L, Q, K, NT, M, n_obs, n_tout, nsys, n_act, n_grp, n_asm, n_tiles, n_rlogN, n_restr;
+  int logK, max_nmax, max_n, acc_cap;
+  double h, dt, sign;
+  // signal
+  int sig_kind;
+  double z0x, z0y, dirx, diry, amp, carrier, centre, width;
+  // tables
+  const SysDesc* sys;
+  const Panel* panels;
+  const double *node_t, *node_x, *node_y, *node_sp;
+  const int* rlogN;
+  const long long* rlog_off_N;
+  double* rlog;
+  const int* restr_N;        // [n_restr][2] (N, Nmax)
+  const long long* restr_off;
+  double* restr;             // transposed tables RT[x][i]
+  const long long* restr_of_sys;
+  const SelfTile* tiles;
+  const CrossTgt* tgts;
+  const PairDesc* pairs;
+  const long long* e_off;
+  const CrossAsm* asms;
+  const CrossGrp* grps;
+  const CrossBlk* blks;
+  const int* tpanel;
+  const long long* tr_off;
+  const double* chi;
+  const int *act_off, *act_idx, *act_arc;
+  const double* win;         // [Q][NT]
+  const double* wl;          // [L]
+  const double* c_q;         // [Q]
+  const int* nlo;            // [Q]
+  const double* tout;        // [n_tout]
+  const double* s_q;         // [Q]
+  double H, period;
+  // work arrays
+  double2* A;                // LU factors
+  int* piv;
+  double2* dinv;             // 1 / U_kk
+  double2* G;                // data on solve nodes [s][q][i]
+  double2* phi;              // current densities
+  double2* phi_sum;
+  double2* phi_all;          // [m][...] or null
+  double2* W;                // cross fields at transfer nodes [(tr_off+x)*Q+q]*L+l
+  double2* Gt;               // transfer-node spectra (same layout)
+  double2* E;                // cross matrices
+  double2* Vobs;             // [z][q][l]
+  double* traces;            // [z][tout]
+  double2* fft_tw;           // K/2 twiddles e^{-2 pi i r/K}
+  double2* syn_tw;           // [Q][L]
+  double2* fwd_tw;           // [Q][L]
+  long long vec_total;
+};
+
+cudaError_t init_constants();
+
+cudaError_t launch_bessel0(const double* z, double* j0, double* y0, double* yh, int n, cudaStream_t st);
+
+// Individual pipeline stages (all asynchronous on `st`).
+cudaError_t launch_tables(const DevJob& J, cudaStream_t st, int* launches);
+cudaError_t launch_tables_rlog_only(const DevJob& J, cudaStream_t st, int* launches);
+cudaError_t launch_assemble_self(const DevJob& J, cudaStream_t st, int* launches);
+cudaError_t launch_lu(const DevJob& J, cudaStream_t st, int* launches);
+cudaError_t launch_cross_assemble(const DevJob& J, cudaStream_t st, int* launches);
+cudaError_t launch_incident(const DevJob& J, cudaStream_t st, int* launches);
+cudaError_t launch_restrict(const DevJob& J, cudaStream_t st, int* launches);
+cudaError_t launch_solve(const DevJob& J, int m, cudaStream_t st, int* launches);
+cudaError_t launch_cross_apply(const DevJob& J, cudaStream_t st, int* launches);
+cudaError_t launch_synth_fwd(const DevJob& J, cudaStream_t st, int* launches);
+cudaError_t launch_traces(const DevJob& J, cudaStream_t st, int* launches);
+
+}  // namespace fthms

@@ -1,0 +1,482 @@
+// Host planning of an FTH-MS job (see plan.h).
+#include "plan.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <map>
+
+namespace fthms {
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kTwoPi = 6.28318530717958647692;
+
+double wrap_pi(double a) {
+  double r = std::fmod(a + kPi, kTwoPi);
+  if (r < 0) r += kTwoPi;
+  r -= kPi;
+  if (r <= -kPi) r += kTwoPi;
+  return r;
+}
+
+// Smooth cut-off of eq. eta (Section 3.1).
+double eta(double t, double t0, double t1) {
+  t = std::fabs(t);
+  if (t <= t0) return 1.0;
+  if (t >= t1) return 0.0;
+  double s = (t - t0) / (t1 - t0);
+  return std::exp(2.0 * std::exp(-1.0 / s) / (s - 1.0));
+}
+
+// Time window sqcap of Section 5 (support [-H, H], equal to 1 on [-H/2, H/2]).
+double window(double s, double H) {
+  if (std::fabs(s) >= H) return 0.0;
+  if (s >= -H / 2.0) return eta(s / H, 0.5, 1.0);
+  return 1.0 - eta(s / H + 1.5, 0.5, 1.0);
+}
+
+// Clenshaw-Curtis rule on [-1, 1] with n+1 points (n even).
+void clenshaw_curtis(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.resize(n + 1);
+  w.resize(n + 1);
+  for (int k = 0; k <= n; ++k) {
+    double th = kPi * k / n;
+    x[k] = std::cos(th);
+    double s = 0.0;
+    for (int j = 1; j <= n / 2; ++j) {
+      double b = (2 * j == n) ? 1.0 : 2.0;
+      s += b / (4.0 * j * j - 1.0) * std::cos(2.0 * j * th);
+    }
+    double c = (k == 0 || k == n) ? 1.0 : 2.0;
+    w[k] = c / n * (1.0 - s);
+  }
+}
+
+}  // namespace
+
+void Curve::eval(double th, double& x, double& y, double& dx, double& dy) const {
+  x = y = dx = dy = 0.0;
+  for (size_t k = 0; k < ax.size(); ++k) {
+    double c = std::cos(k * th), s = std::sin(k * th);
+    x += ax[k] * c + bx[k] * s;
+    y += ay[k] * c + by[k] * s;
+    dx += k * (-ax[k] * s + bx[k] * c);
+    dy += k * (-ay[k] * s + by[k] * c);
+  }
+}
+
+namespace {
+
+void arc_point(const Plan& p, int j, double t, double& x, double& y, double& sp) {
+  const ArcGeo& a = p.arcs[j];
+  double dx, dy;
+  p.curves[a.curve].eval(a.tc + a.half * t, x, y, dx, dy);
+  sp = std::hypot(dx, dy) * a.half;
+}
+
+double chi_at(const Plan& p, int j, double t) {
+  const ArcGeo& a = p.arcs[j];
+  if (a.next < 0) return 1.0;
+  const Curve& c = p.curves[a.curve];
+  double x, y, sp;
+  arc_point(p, j, t, x, y, sp);
+  double th = a.tc + a.half * t;
+  double dum1, dum2;
+  const ArcGeo& nx = p.arcs[a.next];
+  const ArcGeo& pv = p.arcs[a.prev];
+  // Right overlap Gamma_j cap Gamma_next: theta in [next.theta_a, theta_b].
+  double dr = wrap_pi(th - nx.ta), span_r = wrap_pi(a.tb - nx.ta);
+  if (t > 0 && dr >= 0.0 && dr <= span_r) {
+    double ex, ey, fx, fy;
+    c.eval(a.tb, ex, ey, dum1, dum2);
+    c.eval(nx.ta, fx, fy, dum1, dum2);
+    double A = std::hypot(fx - ex, fy - ey);
+    double d = std::hypot(x - ex, y - ey);
+    return eta(A - d, A / 3.0, 2.0 * A / 3.0);
+  }
+  // Left overlap Gamma_prev cap Gamma_j: theta in [theta_a, prev.theta_b].
+  double dl = wrap_pi(pv.tb - th), span_l = wrap_pi(pv.tb - a.ta);
+  if (t < 0 && dl >= 0.0 && dl <= span_l) {
+    double ex, ey, fx, fy;
+    c.eval(pv.tb, ex, ey, dum1, dum2);
+    c.eval(a.ta, fx, fy, dum1, dum2);
+    double A = std::hypot(fx - ex, fy - ey);
+    double d = std::hypot(x - ex, y - ey);
+    return 1.0 - eta(A - d, A / 3.0, 2.0 * A / 3.0);
+  }
+  return 1.0;
+}
+
+bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+}  // namespace
+
+int build_plan(const fthms_curve* curves, int ncurves, const fthms_arc* arcs, int narcs,
+               const fthms_signal* sig, const fthms_options* opt, Plan& p, std::string& err) {
+  char buf[256];
+  if (!curves || ncurves <= 0 || !arcs || narcs <= 0 || !sig || !opt) {
+    err = "null or empty geometry/signal/options";
+    return FTHMS_EINVAL;
+  }
+  p.opt = *opt;
+  p.sig = *sig;
+  if (opt->precision != 0) {
+    err = "only precision = 0 (FP64) is implemented";
+    return FTHMS_ENOTIMPL;
+  }
+  if (opt->L < 3 || !(opt->W > 0) || opt->M < 1 || opt->Q < 1 || !(opt->H > 0) ||
+      !is_pow2(opt->n_period) || opt->n_period < 16 || opt->n_period > 16384 || opt->n_obs < 0 ||
+      opt->n_tout < 0 || (opt->n_obs > 0 && !opt->obs_xy)) {
+    err = "invalid options (need L >= 3, W > 0, M >= 1, Q >= 1, H > 0, n_period a power of two in [16, 16384])";
+    return FTHMS_EINVAL;
+  }
+  if (opt->N_fixed <= 0 && (opt->N_min < 4 || !(opt->N_ppw >= 0))) {
+    err = "node rule needs N_fixed > 0 or N_min >= 4";
+    return FTHMS_EINVAL;
+  }
+  if (sig->kind != 0 && sig->kind != 1) {
+    err = "signal kind must be 0 (point source) or 1 (plane wave)";
+    return FTHMS_EINVAL;
+  }
+  if (!(sig->width > 0)) {
+    err = "signal width must be positive";
+    return FTHMS_EINVAL;
+  }
+  p.curves.resize(ncurves);
+  for (int c = 0; c < ncurves; ++c) {
+    const fthms_curve& cv = curves[c];
+    if (cv.degree < 1 || !cv.ax || !cv.bx || !cv.ay || !cv.by) {
+      err = "curve with degree < 1 or null coefficients";
+      return FTHMS_EINVAL;
+    }
+    p.curves[c].ax.assign(cv.ax, cv.ax + cv.degree + 1);
+    p.curves[c].bx.assign(cv.bx, cv.bx + cv.degree + 1);
+    p.curves[c].ay.assign(cv.ay, cv.ay + cv.degree + 1);
+    p.curves[c].by.assign(cv.by, cv.by + cv.degree + 1);
+  }
+  p.P = narcs;
+  p.arcs.resize(narcs);
+  for (int j = 0; j < narcs; ++j) {
+    const fthms_arc& a = arcs[j];
+    if (a.curve < 0 || a.curve >= ncurves || !(a.theta_b > a.theta_a) || a.theta_b - a.theta_a >= kTwoPi) {
+      snprintf(buf, sizeof buf, "arc %d: bad curve index or parameter interval", j);
+      err = buf;
+      return FTHMS_EINVAL;
+    }
+    ArcGeo& g = p.arcs[j];
+    g.curve = a.curve;
+    g.ta = a.theta_a;
+    g.tb = a.theta_b;
+    g.tc = 0.5 * (a.theta_a + a.theta_b);
+    g.half = 0.5 * (a.theta_b - a.theta_a);
+  }
+  // Cyclic neighbours per curve, ordered by centre angle (Section 3.1).
+  for (int c = 0; c < ncurves; ++c) {
+    std::vector<int> mine;
+    for (int j = 0; j < narcs; ++j)
+      if (p.arcs[j].curve == c) mine.push_back(j);
+    if (mine.size() < 2) continue;
+    std::sort(mine.begin(), mine.end(), [&](int a, int b) {
+      double ca = std::fmod(p.arcs[a].tc, kTwoPi), cb = std::fmod(p.arcs[b].tc, kTwoPi);
+      if (ca < 0) ca += kTwoPi;
+      if (cb < 0) cb += kTwoPi;
+      return ca < cb;
+    });
+    int n = (int)mine.size();
+    for (int k = 0; k < n; ++k) {
+      p.arcs[mine[k]].next = mine[(k + 1) % n];
+      p.arcs[mine[k]].prev = mine[(k - 1 + n) % n];
+    }
+    // Each arc must overlap its neighbours, and the two overlaps must leave a truncated part.
+    for (int k = 0; k < n; ++k) {
+      const ArcGeo& a = p.arcs[mine[k]];
+      const ArcGeo& nx = p.arcs[a.next];
+      const ArcGeo& pv = p.arcs[a.prev];
+      double span_r = wrap_pi(a.tb - nx.ta), span_l = wrap_pi(pv.tb - a.ta);
+      double inner = 2.0 * a.half - span_r - span_l;
+      if (!(span_r > 0) || !(span_l > 0) || !(inner > 0)) {
+        snprintf(buf, sizeof buf, "arc %d: overlaps with its neighbours are empty or cover the whole arc", mine[k]);
+        err = buf;
+        return FTHMS_EINVAL;
+      }
+    }
+  }
+  {
+    std::vector<double> xs, ws;
+    clenshaw_curtis(256, xs, ws);
+    for (int j = 0; j < narcs; ++j) {
+      double s = 0.0, x, y, sp;
+      for (size_t k = 0; k < xs.size(); ++k) {
+        arc_point(p, j, xs[k], x, y, sp);
+        s += ws[k] * sp;
+      }
+      p.arcs[j].length = s;
+    }
+  }
+
+  // Frequency and time grids (Section 5 with the uniform-grid reading).
+  p.L = opt->L;
+  p.M = opt->M;
+  p.Q = opt->Q;
+  p.K = opt->n_period;
+  p.H = opt->H;
+  p.h = opt->W / (opt->L - 1);
+  p.dt = kTwoPi / (p.h * p.K);
+  p.t0 = -p.H;
+  p.period = kTwoPi / p.h;
+  if (p.period < 2.0 * p.H) {
+    err = "window support 2H exceeds the period 2 pi/h of the frequency grid (increase L or reduce H)";
+    return FTHMS_EINVAL;
+  }
+  p.s_q.resize(p.Q);
+  p.c_q.resize(p.Q);
+  p.nlo.resize(p.Q);
+  for (int q = 0; q < p.Q; ++q) {
+    p.s_q[q] = 1.5 * q * p.H;
+    p.c_q[q] = p.h * (p.t0 - p.s_q[q]);
+    p.nlo[q] = (int)std::ceil(p.s_q[q] / p.dt - 1e-9);
+  }
+  p.NT = (int)((p.s_q[p.Q - 1] + 2.0 * p.H) / p.dt) + 1;
+  if (p.NT > 65536) {
+    err = "internal time grid longer than 65536 samples";
+    return FTHMS_EINVAL;
+  }
+  p.win.assign((size_t)p.Q * p.NT, 0.0);
+  for (int q = 0; q < p.Q; ++q)
+    for (int n = 0; n < p.NT; ++n) {
+      double t = p.t0 + n * p.dt;
+      p.win[(size_t)q * p.NT + n] = window(t - p.s_q[q], p.H);
+    }
+  p.wl.assign(p.L, p.h);
+  p.wl[0] = 0.0;
+  p.wl[p.L - 1] = 0.5 * p.h;
+  p.n_obs = opt->n_obs;
+  p.obs.assign(opt->obs_xy, opt->obs_xy + 2 * (size_t)opt->n_obs);
+  p.n_tout = opt->n_tout;
+  p.tout.resize(p.n_tout);
+  for (int i = 0; i < p.n_tout; ++i) p.tout[i] = opt->tout0 + opt->dtout * i;
+
+  // Node counts N_j(omega_l).
+  p.Ntab.assign((size_t)p.P * p.L, 0);
+  p.Nmax.assign(p.P, 0);
+  for (int j = 0; j < p.P; ++j) {
+    for (int l = 1; l < p.L; ++l) {
+      double omega = l * p.h;
+      int N = opt->N_fixed > 0 ? opt->N_fixed
+                               : std::max(opt->N_min, (int)std::ceil(opt->N_ppw * omega * p.arcs[j].length) + opt->N_off);
+      if (N < 2 || N > 1024) {
+        snprintf(buf, sizeof buf, "arc %d omega index %d: node count %d outside [2, 1024]", j, l, N);
+        err = buf;
+        return FTHMS_EINVAL;
+      }
+      p.Ntab[(size_t)j * p.L + l] = N;
+      p.maxN = std::max(p.maxN, N);
+    }
+    p.Nmax[j] = p.Ntab[(size_t)j * p.L + p.L - 1];
+    for (int l = 1; l < p.L; ++l)
+      if (p.Ntab[(size_t)j * p.L + l] > p.Nmax[j]) {
+        err = "node count must not decrease with frequency";
+        return FTHMS_EINVAL;
+      }
+  }
+
+  // Node panels (arc, N): t_i, x(t_i), |x'(t_i)|.
+  p.panel_index.assign((size_t)p.P * (p.maxN + 1), -1);
+  long long noff = 0;
+  auto get_panel = [&](int j, int N) {
+    int& idx = p.panel_index[(size_t)j * (p.maxN + 1) + N];
+    if (idx >= 0) return idx;
+    idx = (int)p.panels.size();
+    p.panels.push_back(Panel{j, N, noff});
+    for (int i = 0; i < N; ++i) {
+      double t = std::cos((2.0 * i + 1.0) * kPi / (2.0 * N));
+      double x, y, sp;
+      arc_point(p, j, t, x, y, sp);
+      p.node_t.push_back(t);
+      p.node_x.push_back(x);
+      p.node_y.push_back(y);
+      p.node_sp.push_back(sp);
+    }
+    noff += N;
+    return idx;
+  };
+
+  // Systems, self tiles, distinct N for the log tables.
+  std::map<int, long long> rlog_map;
+  p.sys.resize((size_t)p.P * (p.L - 1));
+  for (int j = 0; j < p.P; ++j)
+    for (int l = 1; l < p.L; ++l) {
+      int N = p.Ntab[(size_t)j * p.L + l];
+      SysDesc& s = p.sys[(size_t)j * (p.L - 1) + (l - 1)];
+      s.arc = j;
+      s.l = l;
+      s.N = N;
+      s.panel = get_panel(j, N);
+      s.mat_off = p.mat_total;
+      s.vec_off = p.vec_total;
+      s.piv_off = p.piv_total;
+      s.kappa = l * p.h;
+      p.mat_total += (long long)N * N;
+      p.vec_total += (long long)p.Q * N;
+      p.piv_total += N;
+      rlog_map[N] = 0;
+      p.hankel_self += 0.5 * N * (N + 1.0);
+      int nt = (N + kSelfTile - 1) / kSelfTile;
+      int sidx = j * (p.L - 1) + (l - 1);
+      for (int a = 0; a < nt; ++a)
+        for (int b = a; b < nt; ++b) p.self_tiles.push_back(SelfTile{sidx, a, b});
+    }
+  for (auto& kv : rlog_map) {
+    kv.second = p.rlog_total;
+    p.rlogN.push_back(kv.first);
+    p.rlog_off_N.push_back(p.rlog_total);
+    p.rlog_total += (long long)kv.first * kv.first;
+  }
+  for (auto& s : p.sys) s.rlog_off = rlog_map[s.N];
+
+  // Transfer meshes, chi and the active (chi > 0) nodes.
+  p.tpanel.resize(p.P);
+  p.tr_off.resize(p.P);
+  p.act_off.assign(p.P + 1, 0);
+  for (int k = 0; k < p.P; ++k) {
+    p.tpanel[k] = get_panel(k, p.Nmax[k]);
+    p.tr_off[k] = p.tr_total;
+    const Panel& pn = p.panels[p.tpanel[k]];
+    p.act_off[k] = (int)p.act_idx.size();
+    for (int x = 0; x < pn.N; ++x) {
+      double c = chi_at(p, k, p.node_t[pn.off + x]);
+      p.chi.push_back(c);
+      if (c > 0.0) {
+        p.act_idx.push_back(x);
+        p.act_arc.push_back(k);
+      }
+    }
+    p.tr_total += pn.N;
+  }
+  p.act_off[p.P] = (int)p.act_idx.size();
+  p.spec_total = p.tr_total * (long long)p.Q * p.L;
+
+  // Cross-evaluation pairs and targets (eq. vtilde masking; near rule for 1 < |t*| <= 3).
+  for (int k = 0; k <= p.P; ++k) {
+    for (int j = 0; j < p.P; ++j) {
+      if (j == k) continue;
+      PairDesc pd{k, j, (int)p.tgts.size(), 0};
+      if (k == p.P) {
+        for (int z = 0; z < p.n_obs; ++z) p.tgts.push_back(CrossTgt{p.obs[2 * z], p.obs[2 * z + 1], 0.0, 0, z});
+      } else {
+        const Panel& pn = p.panels[p.tpanel[k]];
+        const ArcGeo& aj = p.arcs[j];
+        const ArcGeo& ak = p.arcs[k];
+        for (int a = p.act_off[k]; a < p.act_off[k + 1]; ++a) {
+          int x = p.act_idx[a];
+          double tx = p.node_t[pn.off + x];
+          double X = p.node_x[pn.off + x], Y = p.node_y[pn.off + x];
+          if (aj.curve == ak.curve) {
+            double th = ak.tc + ak.half * tx;
+            double ts = wrap_pi(th - aj.tc) / aj.half;
+            if (std::fabs(ts) <= 1.0) continue;  // point of Gamma_j: dropped (eq. vtilde)
+            int near = std::fabs(ts) <= 3.0 ? 1 : 0;
+            p.tgts.push_back(CrossTgt{X, Y, near ? ts : 0.0, near, x});
+          } else {
+            p.tgts.push_back(CrossTgt{X, Y, 0.0, 0, x});
+          }
+        }
+      }
+      pd.nrows = (int)p.tgts.size() - pd.tgt_off;
+      p.pairs.push_back(pd);
+    }
+  }
+  int npairs = (int)p.pairs.size();
+  p.e_off.assign((size_t)npairs * p.L, -1);
+  for (int pi = 0; pi < npairs; ++pi) {
+    const PairDesc& pd = p.pairs[pi];
+    if (pd.nrows == 0) continue;
+    for (int l = 1; l < p.L; ++l) {
+      int N = p.Ntab[(size_t)pd.j * p.L + l];
+      p.e_off[(size_t)pi * p.L + l] = p.e_total;
+      p.e_total += (long long)pd.nrows * N;
+    }
+  }
+  p.hankel_cross = (double)p.e_total;
+  for (int l = 1; l < p.L; ++l)
+    for (int k = 0; k <= p.P; ++k) {
+      CrossGrp g{l, k, (int)p.blks.size(), 0};
+      for (int pi = 0; pi < npairs; ++pi) {
+        const PairDesc& pd = p.pairs[pi];
+        if (pd.k != k || pd.nrows == 0) continue;
+        int N = p.Ntab[(size_t)pd.j * p.L + l];
+        CrossBlk b{pd.j, pd.j * (p.L - 1) + (l - 1), N, pd.nrows, pd.tgt_off, 0, p.e_off[(size_t)pi * p.L + l]};
+        p.blks.push_back(b);
+      }
+      g.blk_end = (int)p.blks.size();
+      if (g.blk_end > g.blk_begin) p.grps.push_back(g);
+    }
+  const int kRowChunk = 8;
+  for (int pi = 0; pi < npairs; ++pi) {
+    const PairDesc& pd = p.pairs[pi];
+    if (pd.nrows == 0) continue;
+    int l = 1;
+    while (l < p.L) {
+      int N = p.Ntab[(size_t)pd.j * p.L + l];
+      int l1 = l;
+      while (l1 + 1 < p.L && p.Ntab[(size_t)pd.j * p.L + l1 + 1] == N && l1 + 1 - l < 64) ++l1;
+      int panel = get_panel(pd.j, N);
+      for (int r0 = 0; r0 < pd.nrows; r0 += kRowChunk)
+        p.asms.push_back(CrossAsm{pi, l, l1, N, r0, std::min(kRowChunk, pd.nrows - r0), panel, 0});
+      l = l1 + 1;
+    }
+  }
+
+  // Restriction tables (N, Nmax) for systems below their arc's transfer-mesh size.
+  std::map<std::pair<int, int>, long long> rmap;
+  p.restr_of_sys.assign(p.sys.size(), -1);
+  for (size_t s = 0; s < p.sys.size(); ++s) {
+    int N = p.sys[s].N, Nm = p.Nmax[p.sys[s].arc];
+    if (N == Nm) continue;
+    auto key = std::make_pair(N, Nm);
+    auto it = rmap.find(key);
+    if (it == rmap.end()) {
+      rmap[key] = p.restr_total;
+      p.restr_pairs.push_back(key);
+      p.restr_off.push_back(p.restr_total);
+      p.restr_total += (long long)N * Nm;
+      it = rmap.find(key);
+    }
+    p.restr_of_sys[s] = it->second;
+  }
+  p.device_bytes = plan_device_bytes(p);
+  return FTHMS_OK;
+}
+
+void arc_nodes(const Curve& c, double theta_a, double theta_b, int N, std::vector<double>& t,
+               std::vector<double>& x, std::vector<double>& y, std::vector<double>& sp) {
+  const double tc = 0.5 * (theta_a + theta_b), half = 0.5 * (theta_b - theta_a);
+  t.resize(N); x.resize(N); y.resize(N); sp.resize(N);
+  for (int i = 0; i < N; ++i) {
+    t[i] = std::cos((2.0 * i + 1.0) * kPi / (2.0 * N));
+    double dx, dy;
+    c.eval(tc + half * t[i], x[i], y[i], dx, dy);
+    sp[i] = std::hypot(dx, dy) * half;
+  }
+}
+
+size_t plan_device_bytes(const Plan& p) {
+  size_t b = 0;
+  b += (size_t)p.mat_total * 16;                 // A / LU
+  b += (size_t)p.piv_total * 4;                  // pivots
+  b += (size_t)p.rlog_total * 8;                 // self log tables
+  b += (size_t)p.vec_total * 16 * 3;             // G, phi (current), phi sum
+  if (p.opt.keep_densities) b += (size_t)p.vec_total * 16 * p.M;
+  b += (size_t)p.spec_total * 16 * 2;            // W and Gt on transfer meshes
+  b += (size_t)p.e_total * 16;                   // cross matrices
+  b += (size_t)p.restr_total * 8;
+  b += (size_t)p.n_obs * p.Q * p.L * 16 + (size_t)p.n_obs * p.n_tout * 8;
+  b += p.node_t.size() * 32 + p.tgts.size() * sizeof(CrossTgt) + p.blks.size() * sizeof(CrossBlk) +
+       p.asms.size() * sizeof(CrossAsm) + p.self_tiles.size() * sizeof(SelfTile) + p.sys.size() * sizeof(SysDesc);
+  b += p.win.size() * 8 + (size_t)p.Q * p.L * 32 + (size_t)p.K * 8 + p.chi.size() * 8;
+  return b;
+}
+
+}  // namespace fthms

@@ -1,0 +1,269 @@
+"""Thin Python binding of the FTH-MS C ABI (include/fthms.h).
+
+Argument marshalling only: every step of the hot path runs in the CUDA library libfthms.so.  The
+functions carry the C names; ``Job`` is a small convenience wrapper over the same calls.  Importing
+this module loads the library and raises if it has not been built (there is no fallback).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libfthms.so")
+
+FTHMS_OK, FTHMS_EINVAL, FTHMS_ENOMEM, FTHMS_ENOCONV, FTHMS_ETIMEOUT, FTHMS_ECUDA, FTHMS_EBUSY, FTHMS_ENOTIMPL = range(8)
+STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ENOCONV", "ETIMEOUT", "ECUDA", "EBUSY", "ENOTIMPL"]
+
+
+class FthmsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
+        self.status = status
+
+
+class fthms_curve(C.Structure):
+    _fields_ = [("degree", C.c_int), ("ax", C.POINTER(C.c_double)), ("bx", C.POINTER(C.c_double)),
+                ("ay", C.POINTER(C.c_double)), ("by", C.POINTER(C.c_double))]
+
+
+class fthms_arc(C.Structure):
+    _fields_ = [("curve", C.c_int), ("theta_a", C.c_double), ("theta_b", C.c_double)]
+
+
+class fthms_signal(C.Structure):
+    _fields_ = [("kind", C.c_int), ("z0", C.c_double * 2), ("dir", C.c_double * 2), ("sign", C.c_double),
+                ("amp", C.c_double), ("carrier", C.c_double), ("centre", C.c_double), ("width", C.c_double)]
+
+
+class fthms_options(C.Structure):
+    _fields_ = [("W", C.c_double), ("L", C.c_int), ("N_fixed", C.c_int), ("N_min", C.c_int), ("N_off", C.c_int),
+                ("N_ppw", C.c_double), ("M", C.c_int), ("Q", C.c_int), ("H", C.c_double), ("n_period", C.c_int),
+                ("interior", C.c_int), ("n_obs", C.c_int), ("obs_xy", C.POINTER(C.c_double)),
+                ("n_tout", C.c_int), ("tout0", C.c_double), ("dtout", C.c_double), ("precision", C.c_int),
+                ("keep_densities", C.c_int)]
+
+
+class fthms_stats_t(C.Structure):
+    _fields_ = [("gpu_ms", C.c_double), ("setup_ms", C.c_double), ("systems", C.c_longlong),
+                ("solves", C.c_longlong), ("kernel_launches", C.c_longlong), ("device_bytes", C.c_size_t),
+                ("cross_entries", C.c_double), ("hankel_evals", C.c_double)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libfthms.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+    lib = C.CDLL(LIB_PATH)
+    vp, st = C.c_void_p, C.c_int
+    pp = C.POINTER(C.c_void_p)
+    sigs = {
+        "fthms_create": (st, [pp, C.c_int, C.c_size_t, vp]),
+        "fthms_destroy": (st, [vp]),
+        "fthms_prepare": (st, [vp, C.POINTER(fthms_curve), C.c_int, C.POINTER(fthms_arc), C.c_int,
+                               C.POINTER(fthms_signal), C.POINTER(fthms_options), pp]),
+        "fthms_run": (st, [vp]),
+        "fthms_submit": (st, [vp, C.POINTER(fthms_curve), C.c_int, C.POINTER(fthms_arc), C.c_int,
+                              C.POINTER(fthms_signal), C.POINTER(fthms_options), pp]),
+        "fthms_poll": (st, [vp, C.POINTER(C.c_int)]),
+        "fthms_wait": (st, [vp, C.c_int]),
+        "fthms_traces": (st, [vp, C.POINTER(C.c_double), C.c_size_t]),
+        "fthms_densities": (st, [vp, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double), C.c_size_t,
+                                 C.POINTER(C.c_size_t)]),
+        "fthms_densities_dev": (st, [vp, C.c_int, C.c_int, C.c_int, vp, C.c_size_t]),
+        "fthms_node_counts": (st, [vp, C.POINTER(C.c_int), C.c_size_t]),
+        "fthms_stats": (st, [vp, C.POINTER(fthms_stats_t)]),
+        "fthms_release": (st, [vp]),
+        "fthms_last_error": (C.c_char_p, []),
+        "fthms_bessel0": (st, [vp, vp, vp, vp, C.c_int, vp]),
+        "fthms_assemble_self": (st, [C.POINTER(fthms_curve), C.POINTER(fthms_arc), C.c_int, C.c_double, vp, vp]),
+    }
+    for name, (res, args) in sigs.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+LIB = _load()
+
+EXPORTED = ["fthms_create", "fthms_destroy", "fthms_prepare", "fthms_run", "fthms_submit", "fthms_poll",
+            "fthms_wait", "fthms_traces", "fthms_densities", "fthms_densities_dev", "fthms_node_counts",
+            "fthms_stats", "fthms_release", "fthms_last_error", "fthms_bessel0", "fthms_assemble_self"]
+
+
+def _check(status):
+    if status != FTHMS_OK:
+        raise FthmsError(status, LIB.fthms_last_error().decode())
+
+
+def _dptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+class Marshalled:
+    """ctypes views of a problem dict (see workloads); keeps the numpy buffers alive."""
+
+    def __init__(self, problem, keep_densities=True, precision=0):
+        self._keep = []
+        curves = problem["curves"]
+        self.curves = (fthms_curve * len(curves))()
+        for i, c in enumerate(curves):
+            arrs = [np.ascontiguousarray(np.asarray(c[k], dtype=np.float64)) for k in ("ax", "bx", "ay", "by")]
+            self._keep += arrs
+            self.curves[i] = fthms_curve(len(arrs[0]) - 1, *[_dptr(a) for a in arrs])
+        arcs = problem["arcs"]
+        self.arcs = (fthms_arc * len(arcs))(*[fthms_arc(int(c), float(a), float(b)) for c, a, b in arcs])
+        s = problem["signal"]
+        self.signal = fthms_signal(int(s["kind"]), (C.c_double * 2)(*s["z0"]), (C.c_double * 2)(*s["dir"]),
+                                   s["sign"], s["amp"], s["carrier"], s["centre"], s["width"])
+        o = problem["options"]
+        obs = np.ascontiguousarray(np.asarray(o["obs"], dtype=np.float64).reshape(-1))
+        self._keep.append(obs)
+        self.options = fthms_options(o["W"], o["L"], o["N_fixed"], o["N_min"], o["N_off"], o["N_ppw"], o["M"],
+                                     o["Q"], o["H"], o["n_period"], o["interior"], obs.size // 2,
+                                     _dptr(obs) if obs.size else None, o["n_tout"], o["tout0"], o["dtout"],
+                                     int(precision), int(keep_densities))
+        self.ncurves, self.narcs = len(curves), len(arcs)
+
+
+def fthms_create(device=0, hbm_budget_bytes=0, cuda_stream=None):
+    ctx = C.c_void_p()
+    _check(LIB.fthms_create(C.byref(ctx), int(device), int(hbm_budget_bytes), cuda_stream))
+    return ctx
+
+
+def fthms_destroy(ctx):
+    _check(LIB.fthms_destroy(ctx))
+
+
+def fthms_prepare(ctx, m: Marshalled):
+    req = C.c_void_p()
+    _check(LIB.fthms_prepare(ctx, m.curves, m.ncurves, m.arcs, m.narcs, C.byref(m.signal), C.byref(m.options),
+                             C.byref(req)))
+    return req
+
+
+def fthms_run(req):
+    _check(LIB.fthms_run(req))
+
+
+def fthms_submit(ctx, m: Marshalled):
+    req = C.c_void_p()
+    _check(LIB.fthms_submit(ctx, m.curves, m.ncurves, m.arcs, m.narcs, C.byref(m.signal), C.byref(m.options),
+                            C.byref(req)))
+    return req
+
+
+def fthms_poll(req):
+    d = C.c_int()
+    _check(LIB.fthms_poll(req, C.byref(d)))
+    return bool(d.value)
+
+
+def fthms_wait(req, timeout_ms=-1):
+    _check(LIB.fthms_wait(req, int(timeout_ms)))
+
+
+def fthms_traces(req, n_obs, n_tout, out=None):
+    if out is None:
+        out = np.empty((n_obs, n_tout), dtype=np.float64)
+    _check(LIB.fthms_traces(req, _dptr(out), out.size))
+    return out
+
+
+def fthms_densities(req, arc, m, q, out=None):
+    need = C.c_size_t()
+    LIB.fthms_densities(req, int(arc), int(m), int(q), None, 0, C.byref(need))
+    if out is None:
+        out = np.empty(need.value, dtype=np.float64)
+    _check(LIB.fthms_densities(req, int(arc), int(m), int(q), _dptr(out), out.size, C.byref(need)))
+    return out
+
+
+def fthms_densities_dev(req, arc, m, q, out_ptr, cap):
+    _check(LIB.fthms_densities_dev(req, int(arc), int(m), int(q), C.c_void_p(out_ptr), int(cap)))
+
+
+def fthms_node_counts(req, narcs, L):
+    out = np.empty((narcs, L - 1), dtype=np.int32)
+    _check(LIB.fthms_node_counts(req, out.ctypes.data_as(C.POINTER(C.c_int)), out.size))
+    return out
+
+
+def fthms_stats(req):
+    s = fthms_stats_t()
+    _check(LIB.fthms_stats(req, C.byref(s)))
+    return {k: getattr(s, k) for k, _ in fthms_stats_t._fields_}
+
+
+def fthms_release(req):
+    _check(LIB.fthms_release(req))
+
+
+def fthms_last_error():
+    return LIB.fthms_last_error().decode()
+
+
+def fthms_bessel0(z_ptr, j0_ptr, y0_ptr, yh_ptr, n, stream=None):
+    _check(LIB.fthms_bessel0(z_ptr, j0_ptr, y0_ptr, yh_ptr, int(n), stream))
+
+
+def fthms_assemble_self(curve: dict, arc, N, kappa, A_ptr, stream=None):
+    arrs = [np.ascontiguousarray(np.asarray(curve[k], dtype=np.float64)) for k in ("ax", "bx", "ay", "by")]
+    c = fthms_curve(len(arrs[0]) - 1, *[_dptr(a) for a in arrs])
+    a = fthms_arc(0, float(arc[0]), float(arc[1]))
+    _check(LIB.fthms_assemble_self(C.byref(c), C.byref(a), int(N), float(kappa), C.c_void_p(A_ptr), stream))
+
+
+class Job:
+    """One FTH-MS job through the C ABI: ``Job(ctx, problem).run().wait()``."""
+
+    def __init__(self, ctx, problem, keep_densities=True):
+        self.problem = problem
+        self.m = Marshalled(problem, keep_densities=keep_densities)
+        self.req = fthms_prepare(ctx, self.m)
+        o = problem["options"]
+        self.P, self.L, self.M, self.Q = len(problem["arcs"]), o["L"], o["M"], o["Q"]
+        self.n_obs, self.n_tout = self.m.options.n_obs, o["n_tout"]
+
+    def run(self):
+        fthms_run(self.req)
+        return self
+
+    def wait(self, timeout_ms=-1):
+        fthms_wait(self.req, timeout_ms)
+        return self
+
+    def node_counts(self):
+        return fthms_node_counts(self.req, self.P, self.L)
+
+    def traces(self):
+        return fthms_traces(self.req, self.n_obs, self.n_tout)
+
+    def densities(self, arc, m, q=0):
+        """{l: complex array (N_arc(omega_l),)} for l = 1..L-1."""
+        flat = fthms_densities(self.req, arc, m, q)
+        z = flat[0::2] + 1j * flat[1::2]
+        Ns = self.node_counts()[arc]
+        out, o = {}, 0
+        for l in range(1, self.L):
+            n = int(Ns[l - 1])
+            out[l] = z[o:o + n]
+            o += n
+        return out
+
+    def stats(self):
+        return fthms_stats(self.req)
+
+    def release(self):
+        if self.req is not None:
+            fthms_release(self.req)
+            self.req = None
+
+    def __del__(self):
+        try:
+            self.release()
+        except Exception:
+            pass

@@ -1,0 +1,155 @@
+"""GPU (C ABI) vs CPU oracle parity of the FTH-MS hot path.
+
+Bar: densities phi_{j,m,q}(omega_l) within 1e-11 relative L2 of the FP64 oracle (all j, m, q, l
+together and per step m); traces within 1e-10 of the trace scale; node counts identical.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+from scipy import special
+
+import workloads as wl
+from oracle import kernels as oker
+from oracle import run_oracle
+from oracle.fthms import Setup
+from oracle.transforms import incident_field
+
+pytestmark = pytest.mark.gpu
+
+DENSITY_TOL = 1e-11
+TRACE_TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def F():
+    from paper_2507_05725_gb300 import fthms
+    return fthms
+
+
+@pytest.fixture(scope="module")
+def ctx(F):
+    torch.cuda.set_device(0)
+    c = F.fthms_create(0, 0, None)
+    yield c
+    F.fthms_destroy(c)
+
+
+def test_bessel0_against_scipy(F):
+    z = np.concatenate([np.geomspace(1e-6, 4.0, 600), [4.0, np.nextafter(4.0, 5.0), 19.999999, 20.0],
+                        np.linspace(4.0, 20.0, 3001), np.linspace(20.0, 3000.0, 4001)])
+    zt = torch.tensor(z, dtype=torch.float64, device="cuda")
+    j0, y0, yh = (torch.empty_like(zt) for _ in range(3))
+    F.fthms_bessel0(zt.data_ptr(), j0.data_ptr(), y0.data_ptr(), yh.data_ptr(), z.size)
+    torch.cuda.synchronize()
+    j0, y0, yh = j0.cpu().numpy(), y0.cpu().numpy(), yh.cpu().numpy()
+    rj, ry = special.j0(z), special.y0(z)
+    amp = np.where(z > 1.0, np.sqrt(2.0 / (np.pi * z)), 1.0)
+    assert np.max(np.abs(j0 - rj) / amp) < 2e-15
+    assert np.max(np.abs(y0 - ry) / np.maximum(amp, np.abs(ry))) < 2e-15
+    ryh = ry - (2.0 / np.pi) * (np.log(z / 2.0) + np.euler_gamma) * rj
+    small = z < 20.0
+    assert np.max(np.abs(yh - ryh)[small] / (1.0 + np.abs(np.log(z[small])))) < 2e-15
+
+
+@pytest.mark.parametrize("case", [("kite", 64, 7.3), ("ellipse", 33, 0.05), ("circle", 96, 24.0),
+                                  ("kite", 259, 60.0), ("star", 5, 3.0)])
+def test_self_matrix_against_oracle(F, case):
+    name, N, kappa = case
+    curve = {"kite": wl.kite(0.3, -0.2), "ellipse": wl.ellipse(1.0, 0.6), "circle": wl.circle(1.0),
+             "star": wl.star(0.3, 5, 0.4)}[name]
+    ta, tb = -1.9, 1.7
+    A = torch.empty(2 * N * N, dtype=torch.float64, device="cuda")
+    F.fthms_assemble_self(curve, (ta, tb), N, kappa, A.data_ptr())
+    torch.cuda.synchronize()
+    a = A.cpu().numpy()
+    Ag = (a[0::2] + 1j * a[1::2]).reshape(N, N).T
+    from oracle.geometry import Arc
+    Ao = oker.self_matrix(Arc(0, 0, curve, ta, tb), N, kappa)
+    assert np.max(np.abs(Ag - Ao)) < 1e-13 * np.max(np.abs(Ao))
+
+
+def _parity(F, ctx, problem):
+    job = F.Job(ctx, problem).run().wait()
+    ref = run_oracle(problem)
+    o = problem["options"]
+    P, L, M, Q = len(problem["arcs"]), o["L"], o["M"], o["Q"]
+    assert np.array_equal(job.node_counts(), ref.Ntab[:, 1:])
+    num = den = 0.0
+    for m in range(1, M + 1):
+        nm = dm = 0.0
+        for j in range(P):
+            for q in range(Q):
+                d = job.densities(j, m, q)
+                for l in range(1, L):
+                    r = ref.phi[(m, j, l)][q]
+                    nm += float(np.sum(np.abs(d[l] - r) ** 2))
+                    dm += float(np.sum(np.abs(r) ** 2))
+        assert math.sqrt(nm / dm) < DENSITY_TOL, (m, math.sqrt(nm / dm))
+        num += nm
+        den += dm
+    # the sum over m (m = 0 in the C ABI)
+    for j in range(P):
+        d = job.densities(j, 0, 0)
+        for l in range(1, L):
+            r = sum(ref.phi[(m, j, l)][0] for m in range(1, M + 1))
+            assert np.max(np.abs(d[l] - r)) <= DENSITY_TOL * 10 * max(1e-300, np.max(np.abs(r)))
+    tr = job.traces()
+    scale = max(1e-300, np.max(np.abs(ref.traces)))
+    assert np.max(np.abs(tr - ref.traces)) < TRACE_TOL * scale
+    st = job.stats()
+    job.release()
+    return math.sqrt(num / den), st
+
+
+SMALL = {
+    "small-plane": lambda: wl.random_small(0, n_arcs_per_curve=3, kind=1),
+    "small-point": lambda: wl.random_small(2, n_arcs_per_curve=3, kind=0, M=3),
+    "two-curves-Q2": lambda: wl.random_small(5, n_curves=2, n_arcs_per_curve=2, Q=2, L=65, M=2),
+    "four-arcs": lambda: wl.random_small(7, n_arcs_per_curve=4, M=3),
+    "fixed-N": lambda: wl.random_small(9, n_arcs_per_curve=3, N_fixed=20, M=2),
+    "tiny-L": lambda: wl.random_small(11, n_arcs_per_curve=3, L=17, H=4.0, M=2),
+}
+
+
+@pytest.mark.parametrize("name", sorted(SMALL))
+def test_small_problem_parity(F, ctx, name):
+    rel, st = _parity(F, ctx, SMALL[name]())
+    assert rel < DENSITY_TOL
+
+
+def test_config1_parity(F, ctx):
+    """Disk, 3 arcs, N = 96, 256 solved frequencies, M = 8 (the full first configuration)."""
+    rel, st = _parity(F, ctx, wl.config1())
+    assert rel < DENSITY_TOL
+
+
+def test_config2_reduced_parity(F, ctx):
+    """Config 2's geometry, signal and node rule on a narrower band (N from 48 to ~140)."""
+    rel, st = _parity(F, ctx, wl.config2_reduced(M=2))
+    assert rel < DENSITY_TOL
+
+
+def test_config2_full_size_sampled(F, ctx):
+    """Full-size config 2 in the bench's launch configuration: m = 1 densities at sampled (arc,
+    omega) systems against the oracle computed system by system, and the trace scale finite."""
+    problem = wl.config2(M=2)
+    job = F.Job(ctx, problem).run().wait()
+    S = Setup(problem)
+    tg = S.grid
+    sig = problem["signal"]
+    rng = np.random.default_rng(0)
+    for j in (0, 3, 4, 7):
+        g = sig["sign"] * S.chi[j][:, None] * incident_field(sig, S.X[j], tg.t)
+        Gt = tg.forward(g)                              # [Nmax, Q, L]
+        d = job.densities(j, 1, 0)
+        for l in sorted(set(rng.integers(1, tg.L, size=4).tolist()) | {1, tg.L - 1}):
+            n = int(S.Ntab[j, l])
+            G = oker.restriction(n, int(S.Nmax[j])) @ Gt[:, 0, l]
+            phi = np.linalg.solve(oker.self_matrix(S.arcs[j], n, tg.omega[l]), G)
+            err = np.linalg.norm(d[l] - phi) / np.linalg.norm(phi)
+            assert err < DENSITY_TOL, (j, l, err)
+    tr = job.traces()
+    assert np.all(np.isfinite(tr)) and np.max(np.abs(tr)) > 0
+    job.release()

@@ -1,0 +1,39 @@
+"""The C ABI library loads on the host and exports every entry point that include/fthms.h declares
+(no compute calls: those need a GPU)."""
+import os
+import re
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "fthms.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:fthms_status|const char\*)\s+(fthms_\w+)\s*\(", src, re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for n in ["fthms_create", "fthms_destroy", "fthms_submit", "fthms_poll", "fthms_wait", "fthms_traces",
+              "fthms_densities", "fthms_stats", "fthms_release", "fthms_last_error"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2507_05725_gb300 import fthms as F
+    for n in declared_symbols():
+        assert hasattr(F.LIB, n), n
+        assert n in F.EXPORTED, n
+
+
+def test_host_validation_without_gpu():
+    """Argument checks run before any device call."""
+    import ctypes as C
+
+    from paper_2507_05725_gb300 import fthms as F
+    assert F.LIB.fthms_create(None, 0, 0, None) == F.FTHMS_EINVAL
+    assert "NULL" in F.fthms_last_error()
+    assert F.LIB.fthms_bessel0(None, None, None, None, -1, None) == F.FTHMS_EINVAL
+    assert F.LIB.fthms_release(None) == F.FTHMS_EINVAL
+    assert F.LIB.fthms_wait(None, 0) == F.FTHMS_EINVAL
+    d = C.c_int()
+    assert F.LIB.fthms_poll(None, C.byref(d)) == F.FTHMS_EINVAL

@@ -111,7 +111,7 @@ def _min_gap(c1, c2, n=720):
     return float(np.min(np.linalg.norm(a[:, None, :] - b[None, :, :], axis=2)))
 
 
-def config2(seed=2, L=1025, M=12, W=60.0, Q=1, H=40.0, n_period=4096, n_tout=201):
+def config2(seed=2, L=1025, M=12, W=60.0, Q=1, H=40.0, n_period=4096, n_tout=201, T=20.0):
     """Exterior problem, 4 obstacles (ellipses (1,0.6) and (0.8,0.5), kite, circle r=0.7) at seeded
     positions with pairwise gap >= 0.5, each split into 2 overlapping arcs (8 arcs), plane-wave pulse
     f(t) = sin(10t) exp(-((t-6)/2)^2) at a seeded angle, N = max(48, ceil(2 omega len/pi) + 16),
@@ -136,15 +136,15 @@ def config2(seed=2, L=1025, M=12, W=60.0, Q=1, H=40.0, n_period=4096, n_tout=201
     signal = _signal(1, -1.0, 1.0, 10.0, 6.0, 2.0, direction=(math.cos(ang), math.sin(ang)))
     ph = float(rng.uniform(0.0, 2.0 * math.pi))
     obs = [(6.0 * math.cos(ph + 2 * math.pi * k / 5), 6.0 * math.sin(ph + 2 * math.pi * k / 5)) for k in range(5)]
-    options = _options(W, L, M, Q, H, n_period, obs, 0.0, 20.0 / (n_tout - 1), n_tout,
+    options = _options(W, L, M, Q, H, n_period, obs, 0.0, T / (n_tout - 1), n_tout,
                        N_min=48, N_off=16, N_ppw=2.0 / math.pi, interior=0)
     return {"name": "4obstacles-planewave", "curves": curves, "arcs": arcs, "signal": signal, "options": options}
 
 
-def config2_reduced(seed=2, L=129, M=3, n_period=512):
-    """Config 2's geometry and node-count rule (N from 48 up to the full maximum at omega = 60) on a
-    coarser frequency grid and fewer steps, sized for the oracle to finish in seconds."""
-    return config2(seed=seed, L=L, M=M, n_period=n_period)
+def config2_reduced(seed=2, L=129, M=3, W=30.0, H=12.0, n_period=1024):
+    """Config 2's geometry, signal and node-count rule on a band omega <= 30 (N from 48 to ~140)
+    with 129 frequencies, H = 12 and fewer steps, sized for the oracle to finish in seconds."""
+    return config2(seed=seed, L=L, M=M, W=W, H=H, n_period=n_period, T=14.0)
 
 
 def random_small(seed, n_arcs_per_curve=3, n_curves=1, L=33, M=2, Q=1, N_fixed=0, W=10.0, kind=None,
