@@ -1,0 +1,286 @@
+"""Benchmark of the FTH-MS hot path on GB300: arc-omega BIE solves per second.
+
+Workload (one step = one whole job, every hot-path stage): the 4-obstacle exterior problem (two
+ellipses, a kite, a circle; 8 overlapping arcs; plane-wave pulse; N = max(48, ceil(2 omega len/pi)
++ 16) from 48 to 259; 1025 frequencies on [0, 60]; 12 multiple-scattering steps; FP64).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+`value` is device-timed with the job's tables resident in HBM (CUDA events on the library's
+stream around K back-to-back runs); `e2e` times the public C ABI call with host buffers
+(prepare + run + wait + traces + densities to host + release) per step.  With --gpus N (torchrun)
+every rank runs its own replica of the job (the solves of different jobs are independent; no
+collective on the data path) and rank 0 prints the job-wide line.  `--impl reference` times the CPU
+oracle on a bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "arc-ω BIE solves/s at ≤1e-10 rel err, served+batched vs plain FP64; p50/p99 ms"
+FP64_PEAK_GFLOPS = 152 * 4 * 2.07  # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz max SM clock
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    lrank = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, lrank
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def bench_workload():
+    import workloads
+    return workloads.config2()
+
+
+def cpu_sample_problem():
+    """Bounded sample of the same workload for the CPU oracle: the same geometry, signal, node rule
+    and 12 steps on 64 frequencies of [0, 30] (H = 6 so that the window fits one period)."""
+    import workloads
+    return workloads.config2(L=65, W=30.0, H=6.0, M=12, n_period=512, T=6.0)
+
+
+def run_oracle_sample():
+    from oracle import run_oracle
+    p = cpu_sample_problem()
+    o = p["options"]
+    solves = len(p["arcs"]) * (o["L"] - 1) * o["M"] * o["Q"]
+    t0 = time.perf_counter()
+    run_oracle(p, arcs_phi=[])
+    dt = time.perf_counter() - t0
+    return solves, dt
+
+
+def cpu_cores_used():
+    try:
+        from threadpoolctl import threadpool_info
+        n = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
+        return int(n)
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def reference_arm(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    for _ in range(args.warmup):
+        run_oracle_sample()
+    times, solves = [], 0
+    for _ in range(args.steps):
+        s, dt = run_oracle_sample()
+        solves, times = s, times + [dt]
+    ms = 1000.0 * statistics.mean(times)
+    value = solves / (ms / 1000.0)
+    p = cpu_sample_problem()
+    o = p["options"]
+    sample = (f"oracle (numpy/scipy FP64) on 8 arcs x {o['L'] - 1} frequencies of [0, {o['W']:g}] x {o['M']} steps "
+              f"({solves} solves) per step, same geometry/signal/node rule as the bench workload")
+    cores = cpu_cores_used()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "4obstacles-planewave sample on host cores", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def ours(args):
+    import torch
+
+    from paper_2507_05725_gb300 import fthms as F
+
+    ws, rank, lrank = _dist()
+    torch.cuda.set_device(lrank)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    stream = torch.cuda.Stream()
+    problem = bench_workload()
+    o = problem["options"]
+    P, L, M, Q = len(problem["arcs"]), o["L"], o["M"], o["Q"]
+    solves = P * (L - 1) * M * Q
+    ctx = F.fthms_create(lrank, 0, stream.cuda_stream)
+    job = F.Job(ctx, problem, keep_densities=False)
+    st = job.stats()
+    # warm-up, then K timed runs on the library stream
+    for _ in range(args.warmup):
+        job.run()
+    job.wait()
+    F.fthms_profile(job.req, True)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(lrank) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            job.run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    stages = F.fthms_stage_times(job.req)
+    F.fthms_profile(job.req, False)
+    if ws > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * solves / (ms / 1000.0)
+    launches_per_run = st["kernel_launches"] if st["kernel_launches"] else sum(v[1] for v in stages.values()) // args.steps
+    traces_ok = np.all(np.isfinite(job.traces()))
+    job.release()
+
+    # end to end through the C ABI with host buffers
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    d2h = 0
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        m = F.Marshalled(problem, keep_densities=False)
+        req = F.fthms_submit(ctx, m)
+        F.fthms_wait(req)
+        tr = F.fthms_traces(req, m.options.n_obs, o["n_tout"])
+        d2h = tr.nbytes
+        for j in range(P):
+            d2h += F.fthms_densities(req, j, 0, 0).nbytes
+        h2d = F.fthms_stats(req)["h2d_bytes"]
+        F.fthms_release(req)
+    torch.cuda.synchronize()
+    e2e_ms = 1000.0 * (time.perf_counter() - t0) / e2e_steps
+    if ws > 1:
+        t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    F.fthms_destroy(ctx)
+
+    # roofline of the dominant stage (FP64 pipe-bound kernels)
+    dom = max(stages, key=lambda k: stages[k][0])
+    dom_ms, dom_launch = stages[dom]
+    per_launch_ms = dom_ms / max(1, dom_launch)
+    flops_per_launch = {"cross_apply": st["apply_flops"] / M, "lu": st["lu_flops"], "solve": st["solve_flops"] / M}
+    roofline = None
+    if dom in flops_per_launch:
+        ach = flops_per_launch[dom] / (per_launch_ms * 1e-3) / 1e9
+        roofline = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                    "frac": ach / FP64_PEAK_GFLOPS, "traffic": None, "kernel": dom,
+                    "note": "FP64 pipe: 152 SMs x 4 flop/clk x 2.07 GHz; algorithmic flops per launch / event time"}
+    else:
+        roofline = {"bound": "alu", "achieved": None, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": None,
+                    "traffic": None, "kernel": dom}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        s, dt = run_oracle_sample()
+        cpu = {"value": s / dt, "unit": "solves/s", "cores": cpu_cores_used(), "kind": "oracle",
+               "sample": f"{s} solves of the same 8-arc geometry on 64 frequencies of [0, 30], M = 12, "
+                         f"{dt:.1f} s of CPU time"}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": "4obstacles-planewave: 8 arcs, N 48..259, L=1025 on [0,60], M=12, Q=1, "
+                                       "plain FP64 (one job per step)",
+                           "solves_per_step": solves, "systems_per_step": P * (L - 1),
+                           "form": "plain FP64", "l2": "working set > L2 (cross matrices "
+                           f"{st['cross_entries'] * 16 / 1e9:.1f} GB, factors {st['lu_flops'] > 0})",
+                           "parallelism": f"replicas x{ws}"},
+                "e2e": {"value": ws * solves / (e2e_ms / 1000.0), "unit": "solves/s", "ms_per_step": e2e_ms,
+                        "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+                "gpu_launches": int(launches_per_run * args.steps),
+                "roofline": roofline,
+                "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
+                "clocks": clk.summary(),
+                "cpu_baseline": cpu,
+                "traces_finite": bool(traces_ok)}
+        print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+    return ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -116,6 +116,10 @@ typedef struct {
   size_t device_bytes;    /* device memory held by the job */
   double cross_entries;   /* stored cross-evaluation matrix entries */
   double hankel_evals;    /* kernel evaluations in assembly (self + cross) */
+  size_t h2d_bytes;       /* host -> device bytes uploaded by fthms_prepare */
+  double lu_flops;        /* (8/3) sum N^3: complex LU of every system */
+  double solve_flops;     /* 8 sum N^2 Q M: triangular solves of one run */
+  double apply_flops;     /* 8 Q M (cross + observation entries): cross matvecs of one run */
 } fthms_stats_t;
 
 /* Create a context on CUDA device `device` that enqueues all work on `cuda_stream` (a
@@ -168,6 +172,29 @@ fthms_status fthms_densities_dev(fthms_req* req, int arc, int m, int q, double* 
 fthms_status fthms_node_counts(fthms_req* req, int* out, size_t cap);
 
 fthms_status fthms_stats(fthms_req* req, fthms_stats_t* out);
+
+/* Pipeline stages, in enqueue order, for the per-stage timers below. */
+enum {
+  FTHMS_STAGE_TABLES = 0,      /* FFT twiddles, recentring phases, log and restriction tables */
+  FTHMS_STAGE_ASSEMBLE = 1,    /* self matrices (eq. FDBIEk-interior, log-split rule) */
+  FTHMS_STAGE_LU = 2,          /* LU factorisation of every (arc, omega) matrix */
+  FTHMS_STAGE_CROSS_ASM = 3,   /* stored cross-arc single-layer rows (eq. FDsolk-interior) */
+  FTHMS_STAGE_INCIDENT = 4,    /* g_{k,1} and its slow transform (eqs. criterion_int1, Fourierk) */
+  FTHMS_STAGE_RESTRICT = 5,    /* transfer mesh -> solve nodes */
+  FTHMS_STAGE_SOLVE = 6,       /* triangular solves (Algorithm 1, BIE solve) */
+  FTHMS_STAGE_CROSS_APPLY = 7, /* cross-arc and observation potentials */
+  FTHMS_STAGE_SYNTH_FWD = 8,   /* eq. TDsol, eq. criterion_int2, eq. Fourierk */
+  FTHMS_STAGE_TRACES = 9,      /* eq. mult-scatt-int at the output times */
+  FTHMS_NSTAGES = 10
+};
+
+/* enable != 0: later runs record CUDA events around every stage launch on the context stream
+ * (small overhead); 0 stops recording.  Accumulated totals are kept until reset by enabling again. */
+fthms_status fthms_profile(fthms_req* req, int enable);
+
+/* Accumulated device milliseconds and kernel launches per stage over the profiled runs; both
+ * arrays need FTHMS_NSTAGES entries.  Waits for the last run. */
+fthms_status fthms_stage_times(fthms_req* req, double* ms, long long* launches);
 fthms_status fthms_release(fthms_req* req);
 
 /* Message of the last failed call on this thread (never NULL). */

@@ -61,12 +61,25 @@ struct fthms_ctx {
   std::mutex mu;
 };
 
+struct ProfMark {
+  int stage;
+  int launches;
+  cudaEvent_t a, b;
+};
+
 struct fthms_req {
   fthms_ctx* ctx = nullptr;
   Plan plan;
   DevJob J{};
   std::vector<void*> allocs;
   size_t bytes = 0;
+  size_t h2d = 0;
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<ProfMark> marks;
+  double stage_ms[FTHMS_NSTAGES] = {};
+  long long stage_launches[FTHMS_NSTAGES] = {};
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   bool ran = false;
   int launches = 0;
@@ -85,6 +98,7 @@ fthms_status dev_upload(fthms_req* r, const std::vector<T>& v, const T** out) {
   r->allocs.push_back(p);
   r->bytes += b;
   CK(cudaMemcpy(p, v.data(), b, cudaMemcpyHostToDevice));
+  r->h2d += b;
   *out = static_cast<const T*>(p);
   return FTHMS_OK;
 }
@@ -105,6 +119,8 @@ fthms_status dev_alloc(fthms_req* r, size_t count, T** out) {
 void free_req(fthms_req* r) {
   for (void* p : r->allocs) cudaFree(p);
   r->allocs.clear();
+  for (cudaEvent_t e : r->ev_pool) cudaEventDestroy(e);
+  r->ev_pool.clear();
   if (r->ev0) cudaEventDestroy(r->ev0);
   if (r->ev1) cudaEventDestroy(r->ev1);
 }
@@ -194,29 +210,75 @@ fthms_status upload_job(fthms_req* r) {
   return FTHMS_OK;
 }
 
+fthms_status next_event(fthms_req* r, cudaEvent_t* e) {
+  if (r->ev_used == r->ev_pool.size()) {
+    cudaEvent_t ev;
+    CK(cudaEventCreate(&ev));
+    r->ev_pool.push_back(ev);
+  }
+  *e = r->ev_pool[r->ev_used++];
+  return FTHMS_OK;
+}
+
+// Fold the stage timers of a finished run into the totals.
+fthms_status flush_marks(fthms_req* r) {
+  if (r->marks.empty()) return FTHMS_OK;
+  CK(cudaEventSynchronize(r->marks.back().b));
+  for (const ProfMark& m : r->marks) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, m.a, m.b));
+    r->stage_ms[m.stage] += ms;
+    r->stage_launches[m.stage] += m.launches;
+  }
+  r->marks.clear();
+  r->ev_used = 0;
+  return FTHMS_OK;
+}
+
+// One pipeline stage, bracketed by profiling events when enabled.
+template <class F>
+fthms_status stage(fthms_req* r, int st_id, cudaStream_t st, int* nl, F&& launch) {
+  ProfMark m{st_id, 0, nullptr, nullptr};
+  if (r->profiling) {
+    TRY(next_event(r, &m.a));
+    CK(cudaEventRecord(m.a, st));
+  }
+  int before = *nl;
+  cudaError_t e = launch();
+  if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+  if (r->profiling) {
+    TRY(next_event(r, &m.b));
+    CK(cudaEventRecord(m.b, st));
+    m.launches = *nl - before;
+    r->marks.push_back(m);
+  }
+  return FTHMS_OK;
+}
+
 fthms_status enqueue(fthms_req* r) {
   const DevJob& J = r->J;
   cudaStream_t st = r->ctx->stream;
   int nl = 0;
+  TRY(flush_marks(r));
   CK(cudaEventRecord(r->ev0, st));
-  CK(launch_tables(J, st, &nl));
-  CK(launch_assemble_self(J, st, &nl));
-  CK(launch_lu(J, st, &nl));
-  CK(launch_cross_assemble(J, st, &nl));
+  TRY(stage(r, FTHMS_STAGE_TABLES, st, &nl, [&] { return launch_tables(J, st, &nl); }));
+  TRY(stage(r, FTHMS_STAGE_ASSEMBLE, st, &nl, [&] { return launch_assemble_self(J, st, &nl); }));
+  TRY(stage(r, FTHMS_STAGE_LU, st, &nl, [&] { return launch_lu(J, st, &nl); }));
+  TRY(stage(r, FTHMS_STAGE_CROSS_ASM, st, &nl, [&] { return launch_cross_assemble(J, st, &nl); }));
   CK(cudaMemsetAsync(J.Gt, 0, (size_t)r->plan.spec_total * sizeof(double2), st));
   CK(cudaMemsetAsync(J.W, 0, (size_t)r->plan.spec_total * sizeof(double2), st));
   CK(cudaMemsetAsync(J.Vobs, 0, (size_t)std::max(1, J.n_obs * J.Q * J.L) * sizeof(double2), st));
-  CK(launch_incident(J, st, &nl));
-  CK(launch_restrict(J, st, &nl));
+  TRY(stage(r, FTHMS_STAGE_INCIDENT, st, &nl, [&] { return launch_incident(J, st, &nl); }));
+  TRY(stage(r, FTHMS_STAGE_RESTRICT, st, &nl, [&] { return launch_restrict(J, st, &nl); }));
   for (int m = 1; m <= J.M; ++m) {
-    CK(launch_solve(J, m, st, &nl));
-    CK(launch_cross_apply(J, st, &nl));
+    TRY(stage(r, FTHMS_STAGE_SOLVE, st, &nl, [&] { return launch_solve(J, m, st, &nl); }));
+    TRY(stage(r, FTHMS_STAGE_CROSS_APPLY, st, &nl, [&] { return launch_cross_apply(J, st, &nl); }));
     if (m < J.M) {
-      CK(launch_synth_fwd(J, st, &nl));
-      CK(launch_restrict(J, st, &nl));
+      TRY(stage(r, FTHMS_STAGE_SYNTH_FWD, st, &nl, [&] { return launch_synth_fwd(J, st, &nl); }));
+      TRY(stage(r, FTHMS_STAGE_RESTRICT, st, &nl, [&] { return launch_restrict(J, st, &nl); }));
     }
   }
-  CK(launch_traces(J, st, &nl));
+  TRY(stage(r, FTHMS_STAGE_TRACES, st, &nl, [&] { return launch_traces(J, st, &nl); }));
   CK(cudaEventRecord(r->ev1, st));
   r->launches = nl;
   r->ran = true;
@@ -433,6 +495,15 @@ fthms_status fthms_stats(fthms_req* req, fthms_stats_t* out) {
   out->device_bytes = req->bytes;
   out->cross_entries = (double)p.e_total;
   out->hankel_evals = p.hankel_self + p.hankel_cross;
+  out->h2d_bytes = req->h2d;
+  double lu = 0.0, sv = 0.0;
+  for (const SysDesc& s : p.sys) {
+    lu += (8.0 / 3.0) * (double)s.N * s.N * s.N;
+    sv += 8.0 * (double)s.N * s.N * p.Q * p.M;
+  }
+  out->lu_flops = lu;
+  out->solve_flops = sv;
+  out->apply_flops = 8.0 * p.Q * p.M * (double)p.e_total;
   if (req->ran) {
     TRY(fthms_wait(req, -1));
     float ms = 0.f;
@@ -455,6 +526,29 @@ fthms_status fthms_release(fthms_req* req) {
 }
 
 const char* fthms_last_error(void) { return g_last_error.c_str(); }
+
+fthms_status fthms_profile(fthms_req* req, int enable) {
+  if (!req) return fail(FTHMS_EINVAL, "fthms_profile: NULL job");
+  TRY(flush_marks(req));
+  if (enable) {
+    for (int k = 0; k < FTHMS_NSTAGES; ++k) {
+      req->stage_ms[k] = 0.0;
+      req->stage_launches[k] = 0;
+    }
+  }
+  req->profiling = enable != 0;
+  return FTHMS_OK;
+}
+
+fthms_status fthms_stage_times(fthms_req* req, double* ms, long long* launches) {
+  if (!req || !ms || !launches) return fail(FTHMS_EINVAL, "fthms_stage_times: NULL argument");
+  TRY(flush_marks(req));
+  for (int k = 0; k < FTHMS_NSTAGES; ++k) {
+    ms[k] = req->stage_ms[k];
+    launches[k] = req->stage_launches[k];
+  }
+  return FTHMS_OK;
+}
 
 fthms_status fthms_bessel0(const double* z_dev, double* j0_dev, double* y0_dev, double* yhat0_dev, int n,
                            void* cuda_stream) {

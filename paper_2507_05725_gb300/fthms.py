@@ -49,7 +49,12 @@ class fthms_options(C.Structure):
 class fthms_stats_t(C.Structure):
     _fields_ = [("gpu_ms", C.c_double), ("setup_ms", C.c_double), ("systems", C.c_longlong),
                 ("solves", C.c_longlong), ("kernel_launches", C.c_longlong), ("device_bytes", C.c_size_t),
-                ("cross_entries", C.c_double), ("hankel_evals", C.c_double)]
+                ("cross_entries", C.c_double), ("hankel_evals", C.c_double), ("h2d_bytes", C.c_size_t),
+                ("lu_flops", C.c_double), ("solve_flops", C.c_double), ("apply_flops", C.c_double)]
+
+
+STAGES = ["tables", "assemble_self", "lu", "cross_assemble", "incident", "restrict", "solve", "cross_apply",
+          "synth_fwd", "traces"]
 
 
 def _load():
@@ -78,6 +83,8 @@ def _load():
         "fthms_last_error": (C.c_char_p, []),
         "fthms_bessel0": (st, [vp, vp, vp, vp, C.c_int, vp]),
         "fthms_assemble_self": (st, [C.POINTER(fthms_curve), C.POINTER(fthms_arc), C.c_int, C.c_double, vp, vp]),
+        "fthms_profile": (st, [vp, C.c_int]),
+        "fthms_stage_times": (st, [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -90,7 +97,8 @@ LIB = _load()
 
 EXPORTED = ["fthms_create", "fthms_destroy", "fthms_prepare", "fthms_run", "fthms_submit", "fthms_poll",
             "fthms_wait", "fthms_traces", "fthms_densities", "fthms_densities_dev", "fthms_node_counts",
-            "fthms_stats", "fthms_release", "fthms_last_error", "fthms_bessel0", "fthms_assemble_self"]
+            "fthms_stats", "fthms_release", "fthms_last_error", "fthms_bessel0", "fthms_assemble_self",
+            "fthms_profile", "fthms_stage_times"]
 
 
 def _check(status):
@@ -196,6 +204,17 @@ def fthms_stats(req):
     s = fthms_stats_t()
     _check(LIB.fthms_stats(req, C.byref(s)))
     return {k: getattr(s, k) for k, _ in fthms_stats_t._fields_}
+
+
+def fthms_profile(req, enable=True):
+    _check(LIB.fthms_profile(req, int(bool(enable))))
+
+
+def fthms_stage_times(req):
+    ms = (C.c_double * len(STAGES))()
+    n = (C.c_longlong * len(STAGES))()
+    _check(LIB.fthms_stage_times(req, ms, n))
+    return {s: (ms[i], n[i]) for i, s in enumerate(STAGES)}
 
 
 def fthms_release(req):
