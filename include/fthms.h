@@ -82,7 +82,7 @@ typedef struct {
  *              + N_off), len_j the arc length.  The transfer mesh of arc j is its first-kind
  *              Chebyshev grid of size N_j(omega_{L-1}).
  *  M         : multiple-scattering steps (Algorithm 1's outer loop).
- *  Q, H      : time windows sqcap_q(t) = sqcap(t - s_q), s_q = 1.5 (q-1) H (Section 5).
+ *  Q, H      : 1 <= Q <= 4 time windows sqcap_q(t) = sqcap(t - s_q), s_q = 1.5 (q-1) H (Section 5).
  *  n_period  : internal time samples per period 2 pi/h of the frequency grid (power of two,
  *              16..16384); dt = 2 pi/(h n_period), t_n = -H + n dt covering [-H, s_Q + H].
  *  obs_xy    : n_obs observation points (x, y), host array of 2*n_obs doubles.

@@ -65,9 +65,9 @@ __device__ __forceinline__ void bessel0_miller(double z, double& J0, double& Yh)
   Yh = -4.0 * kInvPi * T * inv;
 }
 
-// Hankel asymptotics on z >= 20: J0 and Y0.
-__device__ __forceinline__ void bessel0_asym(double z, double& J0, double& Y0) {
-  const double w = 1.0 / z;
+// Hankel asymptotics given w = 1/z, amp = sqrt(2/(pi z)) and (s, c) = (sin z, cos z).
+__device__ __forceinline__ void hankel_asym_phase(double w, double amp, double s, double c, double& J0,
+                                                  double& Y0) {
   const double w2 = -w * w;
   double P = c_hank_a[18], Qa = c_hank_a[19];
 #pragma unroll
@@ -76,13 +76,18 @@ __device__ __forceinline__ void bessel0_asym(double z, double& J0, double& Y0) {
     Qa = fma(Qa, w2, c_hank_a[2 * k + 1]);
   }
   Qa *= w;
-  const double amp = sqrt(kTwoOverPi * w);
-  double s, c;
-  sincos(z, &s, &c);
   const double cx = (c + s) * kSqrtHalf;   // cos(z - pi/4)
   const double sx = (s - c) * kSqrtHalf;   // sin(z - pi/4)
   J0 = amp * fma(P, cx, Qa * sx);
   Y0 = amp * fma(P, sx, -Qa * cx);
+}
+
+// Hankel asymptotics on z >= 20: J0 and Y0.
+__device__ __forceinline__ void bessel0_asym(double z, double& J0, double& Y0) {
+  const double w = 1.0 / z;
+  double s, c;
+  sincos(z, &s, &c);
+  hankel_asym_phase(w, sqrt(kTwoOverPi * w), s, c, J0, Y0);
 }
 
 // Kernel pieces used by the Nystrom rules:

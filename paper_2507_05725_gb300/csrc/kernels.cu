@@ -367,6 +367,7 @@ __global__ void __launch_bounds__(32 * kSolveWarps) k_solve(DevJob J, int m) {
 // Cross assembly: stored rows of S_Gamma_j for one (pair, frequency band, 8-row chunk).
 constexpr int kAsmThreads = 256;
 constexpr int kAsmRows = 8;
+constexpr int kAsmBand = 64;   // frequencies per assembly task (matches the planner's band cap)
 
 __global__ void __launch_bounds__(kAsmThreads) k_cross_assemble(DevJob J) {
   extern __shared__ double sha[];
@@ -418,34 +419,73 @@ __global__ void __launch_bounds__(kAsmThreads) k_cross_assemble(DevJob J) {
     __syncthreads();
   }
   const double w = kPiD / N;
+  const int ld = pr.nrows;   // blocks are stored source-major: E[i * nrows + row]
+  // 1/l and 1/sqrt(l) over the band, for the far-field recurrence below
+  double* invl = Wn + kAsmRows * N;          // <= kAsmBand
+  double* rsql = invl + kAsmBand;
+  for (int l = task.l0 + threadIdx.x; l <= task.l1; l += kAsmThreads) {
+    invl[l - task.l0] = 1.0 / l;
+    rsql[l - task.l0] = rsqrt((double)l);
+  }
+  __syncthreads();
   for (int e = threadIdx.x; e < task.nrows * N; e += kAsmThreads) {
-    const int r = e / N, i = e % N;
+    const int r = e % task.nrows, i = e / task.nrows;
     const CrossTgt t = tg[r];
     const double dx = t.x - J.node_x[pn.off + i], dy = t.y - J.node_y[pn.off + i];
     const double R = sqrt(fma(dx, dx, dy * dy));
-    const double wn = t.near ? Wn[r * N + i] : 0.0;
-    const double dts = fabs(t.tstar - J.node_t[pn.off + i]);
-    const long long row = (long long)(task.row0 + r) * N + i;
-    for (int l = task.l0; l <= task.l1; ++l) {
-      const double z = (l * J.h) * R;
-      double2 v;
-      if (t.near) {
+    const long long pos = (long long)i * ld + task.row0 + r;
+    if (t.near) {
+      const double wn = Wn[r * N + i];
+      const double dts = fabs(t.tstar - J.node_t[pn.off + i]);
+      for (int l = task.l0; l <= task.l1; ++l) {
         double K1;
         double2 K2;
-        log_split(z, dts, K1, K2);
-        v = make_double2(fma(K1, wn, K2.x * w), K2.y * w);
-      } else {
-        double2 K = phi_kernel(z);
-        v = make_double2(K.x * w, K.y * w);
+        log_split((l * J.h) * R, dts, K1, K2);
+        J.E[J.e_off[(long long)task.pair * J.L + l] + pos] = make_double2(fma(K1, wn, K2.x * w), K2.y * w);
       }
-      J.E[J.e_off[(long long)task.pair * J.L + l] + row] = v;
+      continue;
+    }
+    // Far rule.  Above z = 20 the Hankel expansion's phase e^{iz} advances by the fixed rotation
+    // e^{i h R} from one frequency to the next (re-seeded by sincos every 16 steps) and
+    // 1/z = (1/(hR))(1/l), sqrt(2/(pi z)) = sqrt(2/(pi hR))/sqrt(l).
+    const double hR = J.h * R;
+    const double inv_u = 1.0 / hR;
+    const double amp_u = sqrt(kTwoOverPi * inv_u);
+    double su, cu;
+    sincos(hR, &su, &cu);
+    double s0 = 0.0, c0 = 1.0;
+    int since = 16;
+    for (int l = task.l0; l <= task.l1; ++l) {
+      const double z = (l * J.h) * R;
+      double2 K;
+      if (z >= kBesselLarge) {
+        if (since >= 16) {
+          sincos(z, &s0, &c0);
+          since = 0;
+        }
+        const double wz = inv_u * invl[l - task.l0];
+        const double amp = amp_u * rsql[l - task.l0];
+        double J0, Y0;
+        hankel_asym_phase(wz, amp, s0, c0, J0, Y0);
+        K = make_double2(-0.25 * Y0, 0.25 * J0);
+        const double cn = fma(c0, cu, -s0 * su);
+        s0 = fma(s0, cu, c0 * su);
+        c0 = cn;
+        ++since;
+      } else {
+        K = phi_kernel(z);
+      }
+      J.E[J.e_off[(long long)task.pair * J.L + l] + pos] = make_double2(K.x * w, K.y * w);
     }
   }
 }
 
 // ---------------------------------------------------------------------------------------------
-// Cross apply: W_k(x, q, l) = sum_j sum_i E_{l,k,j}[r, i] phi_j[q, i]; observation sums accumulate.
+// Cross apply: W_k(x, q, l) = sum_j sum_i E_{l,k,j}[i, r] phi_j[q, i]; observation sums accumulate.
+// One thread per target row: the source-major blocks make every load coalesced across the warp,
+// the densities are shared-memory broadcasts and no cross-lane reduction is needed.
 constexpr int kApplyThreads = 256;
+constexpr int kApplyMaxQ = 4;
 
 __global__ void __launch_bounds__(kApplyThreads) k_cross_apply(DevJob J) {
   extern __shared__ double2 shc[];
@@ -454,30 +494,32 @@ __global__ void __launch_bounds__(kApplyThreads) k_cross_apply(DevJob J) {
   const bool obs = g.k == J.P;
   const int nout = obs ? J.n_obs : J.panels[J.tpanel[g.k]].N;
   double2* acc = shc;                              // [Q][nout]
-  double2* ph = shc + (size_t)Q * J.acc_cap;        // [Q][N]
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = kApplyThreads / 32;
+  double2* ph = shc + (size_t)Q * J.acc_cap;       // [Q][N]
   for (int e = threadIdx.x; e < Q * nout; e += kApplyThreads) acc[e] = make_double2(0.0, 0.0);
   for (int b = g.blk_begin; b < g.blk_end; ++b) {
     const CrossBlk B = J.blks[b];
-    const int N = B.N;
+    const int N = B.N, nr = B.nrows;
     const double2* p = J.phi + J.sys[B.sys].vec_off;
     __syncthreads();
     for (int e = threadIdx.x; e < Q * N; e += kApplyThreads) ph[e] = p[e];
     __syncthreads();
     const double2* E = J.E + B.e_off;
-    for (int r = wid; r < B.nrows; r += nw) {
-      const double2* Er = E + (long long)r * N;
-      const int out = J.tgts[B.tgt_off + r].out;
-      for (int q = 0; q < Q; ++q) {
-        double2 s = make_double2(0.0, 0.0);
-        for (int i = lane; i < N; i += 32) s = cfma(Er[i], ph[q * N + i], s);
+    for (int r = threadIdx.x; r < nr; r += kApplyThreads) {
+      double2 s[kApplyMaxQ];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
-          s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
-        }
-        if (lane == 0) acc[q * nout + out] = cadd(acc[q * nout + out], s);
+      for (int q = 0; q < kApplyMaxQ; ++q) s[q] = make_double2(0.0, 0.0);
+      const double2* Er = E + r;
+#pragma unroll 4
+      for (int i = 0; i < N; ++i) {
+        const double2 ev = Er[(long long)i * nr];
+#pragma unroll
+        for (int q = 0; q < kApplyMaxQ; ++q)
+          if (q < Q) s[q] = cfma(ev, ph[q * N + i], s[q]);
       }
+      const int out = J.tgts[B.tgt_off + r].out;
+#pragma unroll
+      for (int q = 0; q < kApplyMaxQ; ++q)
+        if (q < Q) acc[q * nout + out] = cadd(acc[q * nout + out], s[q]);
     }
   }
   __syncthreads();
@@ -734,7 +776,7 @@ cudaError_t launch_lu(const DevJob& J, cudaStream_t st, int* launches) {
 
 cudaError_t launch_cross_assemble(const DevJob& J, cudaStream_t st, int* launches) {
   if (J.n_asm == 0) return cudaSuccess;
-  size_t sh = (size_t)(4 + 2 * kAsmRows) * J.max_n * sizeof(double);
+  size_t sh = ((size_t)(4 + 2 * kAsmRows) * J.max_n + 2 * kAsmBand) * sizeof(double);
   cudaError_t e = cudaFuncSetAttribute(k_cross_assemble, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
   if (e != cudaSuccess) return e;
   k_cross_assemble<<<J.n_asm, kAsmThreads, sh, st>>>(J);

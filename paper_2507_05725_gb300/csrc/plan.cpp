@@ -132,6 +132,10 @@ int build_plan(const fthms_curve* curves, int ncurves, const fthms_arc* arcs, in
     err = "invalid options (need L >= 3, W > 0, M >= 1, Q >= 1, H > 0, n_period a power of two in [16, 16384])";
     return FTHMS_EINVAL;
   }
+  if (opt->Q > 4) {
+    err = "at most 4 time windows per job";
+    return FTHMS_EINVAL;
+  }
   if (opt->N_fixed <= 0 && (opt->N_min < 4 || !(opt->N_ppw >= 0))) {
     err = "node rule needs N_fixed > 0 or N_min >= 4";
     return FTHMS_EINVAL;
