@@ -586,7 +586,7 @@ fthms_status fthms_assemble_self(const fthms_curve* curve, const fthms_arc* arc,
   std::vector<SelfTile> tiles;
   int nt = (N + kSelfTile - 1) / kSelfTile;
   for (int a = 0; a < nt; ++a)
-    for (int b = a; b < nt; ++b) tiles.push_back(SelfTile{0, a, b});
+    for (int b = a; b < nt; ++b) tiles.push_back(SelfTile{0, 1, a, b});
   fthms_status s = FTHMS_OK;
   if (s == FTHMS_OK) s = dev_upload(&tmp, sys, &J.sys);
   if (s == FTHMS_OK) s = dev_upload(&tmp, panels, &J.panels);

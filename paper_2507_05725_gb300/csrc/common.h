@@ -68,12 +68,15 @@ struct CrossAsm {
   int pad;
 };
 
-// Upper-triangular tile of one self matrix.
+// Upper-triangular tile of the self matrices of a band of consecutive systems (same arc, same N,
+// consecutive frequencies sys .. sys+nsys-1).
 struct SelfTile {
   int sys;
+  int nsys;
   int ti, tl;       // tile row / column (tile edge = kSelfTile)
 };
 
 constexpr int kSelfTile = 16;
+constexpr int kSelfBand = 32;
 
 }  // namespace fthms

@@ -159,34 +159,78 @@ __global__ void k_restr(DevJob J) {
 }
 
 // ---------------------------------------------------------------------------------------------
-// Self assembly: A_il = K1(t_i,t_l) Rlog_il + K2(t_i,t_l) pi/N, symmetric in (i, l).
+// Self assembly: A_ic = K1(t_i,t_c) Rlog_ic + K2(t_i,t_c) pi/N, symmetric in (i, c), for a band of
+// consecutive frequencies sharing N (nodes, log table, |t - s| and its logarithm are shared).
 __global__ void __launch_bounds__(256) k_assemble_self(DevJob J) {
   const SelfTile tile = J.tiles[blockIdx.x];
-  const SysDesc s = J.sys[tile.sys];
-  const int N = s.N;
-  const int i = tile.ti * kSelfTile + (threadIdx.x % kSelfTile);
-  const int l = tile.tl * kSelfTile + (threadIdx.x / kSelfTile);
-  if (i >= N || l >= N) return;
-  if (tile.ti == tile.tl && i > l) return;
-  const Panel pn = J.panels[s.panel];
-  const double rl = J.rlog[s.rlog_off + (long long)i * N + l];
-  const double w = kPiD / N;
-  double K1;
-  double2 K2;
-  if (i == l) {
-    K1 = -0.5 * kInvPi;
-    K2 = make_double2(-0.5 * kInvPi * (kEulerGamma + log(0.5 * s.kappa * J.node_sp[pn.off + i])), 0.25);
-  } else {
-    double dx = J.node_x[pn.off + i] - J.node_x[pn.off + l];
-    double dy = J.node_y[pn.off + i] - J.node_y[pn.off + l];
-    double R = sqrt(fma(dx, dx, dy * dy));
-    double dts = fabs(J.node_t[pn.off + i] - J.node_t[pn.off + l]);
-    log_split(s.kappa * R, dts, K1, K2);
+  const SysDesc s0 = J.sys[tile.sys];
+  const int N = s0.N, nb = tile.nsys;
+  __shared__ double lnl[kSelfBand], invl[kSelfBand], rsql[kSelfBand];
+  if (threadIdx.x < nb) {
+    const double l = (double)(s0.l + threadIdx.x);
+    lnl[threadIdx.x] = log(l);
+    invl[threadIdx.x] = 1.0 / l;
+    rsql[threadIdx.x] = rsqrt(l);
   }
-  double2 v = make_double2(fma(K1, rl, K2.x * w), K2.y * w);
-  double2* A = J.A + s.mat_off;
-  A[(long long)l * N + i] = v;
-  if (i != l) A[(long long)i * N + l] = v;
+  __syncthreads();
+  const int i = tile.ti * kSelfTile + (threadIdx.x % kSelfTile);
+  const int c = tile.tl * kSelfTile + (threadIdx.x / kSelfTile);
+  if (i >= N || c >= N) return;
+  if (tile.ti == tile.tl && i > c) return;
+  const Panel pn = J.panels[s0.panel];
+  const double rl = J.rlog[s0.rlog_off + (long long)i * N + c];
+  const double w = kPiD / N;
+  const long long e1 = (long long)c * N + i, e2 = (long long)i * N + c;
+  if (i == c) {
+    const double K1 = -0.5 * kInvPi;
+    const double lsp = log(0.5 * J.h * J.node_sp[pn.off + i]);
+    for (int b = 0; b < nb; ++b) {
+      const double re = -0.5 * kInvPi * (kEulerGamma + lnl[b] + lsp);
+      J.A[J.sys[tile.sys + b].mat_off + e1] = make_double2(fma(K1, rl, re * w), 0.25 * w);
+    }
+    return;
+  }
+  const double dx = J.node_x[pn.off + i] - J.node_x[pn.off + c];
+  const double dy = J.node_y[pn.off + i] - J.node_y[pn.off + c];
+  const double R = sqrt(fma(dx, dx, dy * dy));
+  const double dts = fabs(J.node_t[pn.off + i] - J.node_t[pn.off + c]);
+  const double ldts = log(dts);
+  const double hR = J.h * R;
+  const double lratio = log(hR / (2.0 * dts)) + kEulerGamma;   // ln(z/(2|t-s|)) + gamma - ln l
+  const double inv_u = 1.0 / hR, amp_u = sqrt(kTwoOverPi * inv_u);
+  double su, cu;
+  sincos(hR, &su, &cu);
+  double s = 0.0, co = 1.0;
+  int since = 16;
+  for (int b = 0; b < nb; ++b) {
+    const int l = s0.l + b;
+    const double z = (l * J.h) * R;
+    double K1, re, J0;
+    if (z >= kBesselLarge) {
+      if (since >= 16) {
+        sincos(z, &s, &co);
+        since = 0;
+      }
+      double Y0;
+      hankel_asym_phase(inv_u * invl[b], amp_u * rsql[b], s, co, J0, Y0);
+      K1 = -0.5 * kInvPi * J0;
+      re = fma(-K1, ldts, -0.25 * Y0);
+      const double cn = fma(co, cu, -s * su);
+      s = fma(s, cu, co * su);
+      co = cn;
+      ++since;
+    } else {
+      double Yh;
+      if (z <= kBesselSmall) bessel0_series(z, J0, Yh);
+      else bessel0_miller(z, J0, Yh);
+      K1 = -0.5 * kInvPi * J0;
+      re = fma(K1, lnl[b] + lratio, -0.25 * Yh);
+    }
+    const double2 v = make_double2(fma(K1, rl, re * w), 0.25 * J0 * w);
+    double2* A = J.A + J.sys[tile.sys + b].mat_off;
+    A[e1] = v;
+    A[e2] = v;
+  }
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -304,58 +348,77 @@ __global__ void __launch_bounds__(kLuThreads) k_lu(DevJob J) {
     }
     __syncthreads();
   }
+  // U = D U' with unit-diagonal U': keep 1/U_kk and scale row k of U (right of the diagonal).
   for (int k = tid; k < N; k += kLuThreads) J.dinv[s.piv_off + k] = crecip(A[(long long)k * N + k]);
+  __syncthreads();
+  for (long long e = tid; e < (long long)N * N; e += kLuThreads) {
+    const int col = (int)(e / N), row = (int)(e % N);
+    if (col > row) A[e] = cmul(A[e], J.dinv[s.piv_off + row]);
+  }
 }
 
 // ---------------------------------------------------------------------------------------------
-// Triangular solves, one warp per system, all Q right-hand sides together.
+// Triangular solves: a warp carries 4 consecutive systems (8 lanes each; the systems of a band share
+// N so their sweeps run in lock-step), all Q right-hand sides together.  Both factors have a unit
+// diagonal (U was scaled by the LU kernel), so each step is a pure column update; D^{-1} is applied
+// once, lane-parallel, between the sweeps.
 constexpr int kSolveWarps = 4;
+constexpr int kSolveGroup = 8;                  // lanes per system
+constexpr int kSolvePerWarp = 32 / kSolveGroup;
 
 __global__ void __launch_bounds__(32 * kSolveWarps) k_solve(DevJob J, int m) {
   extern __shared__ double2 shs[];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int sidx = blockIdx.x * kSolveWarps + wid;
-  if (sidx >= J.nsys) return;
-  const SysDesc s = J.sys[sidx];
-  const int N = s.N, Q = J.Q;
-  double2* b = shs + (size_t)wid * Q * J.max_n;
+  const int sub = lane / kSolveGroup, gl = lane % kSolveGroup;
+  const int sidx = (blockIdx.x * kSolveWarps + wid) * kSolvePerWarp + sub;
+  const bool live = sidx < J.nsys;
+  const int Q = J.Q;
+  const SysDesc s = J.sys[live ? sidx : J.nsys - 1];
+  const int N = live ? s.N : 0;
+  int Nw = N;                                   // longest system of the warp
+  for (int o = kSolveGroup; o < 32; o <<= 1) Nw = max(Nw, __shfl_xor_sync(0xffffffffu, Nw, o));
+  double2* b = shs + ((size_t)wid * kSolvePerWarp + sub) * Q * J.max_n;
   const double2* A = J.A + s.mat_off;
   const int* piv = J.piv + s.piv_off;
   const double2* dinv = J.dinv + s.piv_off;
   const double2* G = J.G + s.vec_off;
-  for (int e = lane; e < Q * N; e += 32) b[e] = G[e];
+  for (int e = gl; e < Q * N; e += kSolveGroup) b[e] = G[e];
   __syncwarp();
-  if (lane < Q) {
-    double2* bq = b + lane * N;
+  if (gl < Q) {
+    double2* bq = b + gl * N;
     for (int k = 0; k < N; ++k) {
       int p = piv[k];
       if (p != k) { double2 t = bq[k]; bq[k] = bq[p]; bq[p] = t; }
     }
   }
   __syncwarp();
-  for (int k = 0; k < N - 1; ++k) {
-    const double2* Lc = A + (long long)k * N;
-    for (int q = 0; q < Q; ++q) {
-      const double2 xk = b[q * N + k];
-      for (int i = k + 1 + lane; i < N; i += 32) b[q * N + i] = cfms(Lc[i], xk, b[q * N + i]);
+  for (int k = 0; k < Nw - 1; ++k) {
+    if (k < N - 1) {
+      const double2* Lc = A + (long long)k * N;
+      for (int q = 0; q < Q; ++q) {
+        const double2 xk = b[q * N + k];
+        for (int i = k + 1 + gl; i < N; i += kSolveGroup) b[q * N + i] = cfms(Lc[i], xk, b[q * N + i]);
+      }
     }
     __syncwarp();
   }
-  for (int k = N - 1; k >= 0; --k) {
-    const double2* Uc = A + (long long)k * N;
-    const double2 dk = dinv[k];
-    for (int q = 0; q < Q; ++q) {
-      const double2 xk = cmul(b[q * N + k], dk);
-      for (int i = lane; i < k; i += 32) b[q * N + i] = cfms(Uc[i], xk, b[q * N + i]);
-      __syncwarp();
-      if (lane == 0) b[q * N + k] = xk;
+  for (int e = gl; e < Q * N; e += kSolveGroup) b[e] = cmul(b[e], dinv[e % N]);
+  __syncwarp();
+  for (int k = Nw - 1; k >= 1; --k) {
+    if (k < N) {
+      const double2* Uc = A + (long long)k * N;
+      for (int q = 0; q < Q; ++q) {
+        const double2 xk = b[q * N + k];
+        for (int i = gl; i < k; i += kSolveGroup) b[q * N + i] = cfms(Uc[i], xk, b[q * N + i]);
+      }
     }
     __syncwarp();
   }
+  if (!live) return;
   double2* out = J.phi + s.vec_off;
   double2* sum = J.phi_sum + s.vec_off;
   double2* all = J.phi_all ? J.phi_all + (long long)(m - 1) * J.vec_total + s.vec_off : nullptr;
-  for (int e = lane; e < Q * N; e += 32) {
+  for (int e = gl; e < Q * N; e += kSolveGroup) {
     double2 v = b[e];
     out[e] = v;
     sum[e] = m == 1 ? v : cadd(sum[e], v);
@@ -485,12 +548,14 @@ __global__ void __launch_bounds__(kAsmThreads) k_cross_assemble(DevJob J) {
 // One thread per target row: the source-major blocks make every load coalesced across the warp,
 // the densities are shared-memory broadcasts and no cross-lane reduction is needed.
 constexpr int kApplyThreads = 256;
-constexpr int kApplyMaxQ = 4;
 
+// The window count is a template parameter: on this GPU an FP64 instruction costs a full warp slot
+// of the FP64 pipe whether or not its lanes are predicated on, so no FMA is issued for absent windows.
+template <int Q>
 __global__ void __launch_bounds__(kApplyThreads) k_cross_apply(DevJob J) {
   extern __shared__ double2 shc[];
   const CrossGrp g = J.grps[blockIdx.x];
-  const int Q = J.Q, l = g.l;
+  const int l = g.l;
   const bool obs = g.k == J.P;
   const int nout = obs ? J.n_obs : J.panels[J.tpanel[g.k]].N;
   double2* acc = shc;                              // [Q][nout]
@@ -505,21 +570,19 @@ __global__ void __launch_bounds__(kApplyThreads) k_cross_apply(DevJob J) {
     __syncthreads();
     const double2* E = J.E + B.e_off;
     for (int r = threadIdx.x; r < nr; r += kApplyThreads) {
-      double2 s[kApplyMaxQ];
+      double2 s[Q];
 #pragma unroll
-      for (int q = 0; q < kApplyMaxQ; ++q) s[q] = make_double2(0.0, 0.0);
+      for (int q = 0; q < Q; ++q) s[q] = make_double2(0.0, 0.0);
       const double2* Er = E + r;
 #pragma unroll 4
       for (int i = 0; i < N; ++i) {
         const double2 ev = Er[(long long)i * nr];
 #pragma unroll
-        for (int q = 0; q < kApplyMaxQ; ++q)
-          if (q < Q) s[q] = cfma(ev, ph[q * N + i], s[q]);
+        for (int q = 0; q < Q; ++q) s[q] = cfma(ev, ph[q * N + i], s[q]);
       }
       const int out = J.tgts[B.tgt_off + r].out;
 #pragma unroll
-      for (int q = 0; q < kApplyMaxQ; ++q)
-        if (q < Q) acc[q * nout + out] = cadd(acc[q * nout + out], s[q]);
+      for (int q = 0; q < Q; ++q) acc[q * nout + out] = cadd(acc[q * nout + out], s[q]);
     }
   }
   __syncthreads();
@@ -816,24 +879,32 @@ cudaError_t launch_restrict(const DevJob& J, cudaStream_t st, int* launches) {
 }
 
 cudaError_t launch_solve(const DevJob& J, int m, cudaStream_t st, int* launches) {
-  size_t sh = (size_t)kSolveWarps * J.Q * J.max_n * sizeof(double2);
+  size_t sh = (size_t)kSolveWarps * kSolvePerWarp * J.Q * J.max_n * sizeof(double2);
   cudaError_t e = cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
   if (e != cudaSuccess) return e;
-  k_solve<<<cdiv(J.nsys, kSolveWarps), 32 * kSolveWarps, sh, st>>>(J, m);
+  k_solve<<<cdiv(J.nsys, kSolveWarps * kSolvePerWarp), 32 * kSolveWarps, sh, st>>>(J, m);
   *launches += 1;
+  return cudaGetLastError();
+}
+
+template <int Q>
+static cudaError_t launch_cross_apply_q(const DevJob& J, size_t sh, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(k_cross_apply<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+  if (e != cudaSuccess) return e;
+  k_cross_apply<Q><<<J.n_grp, kApplyThreads, sh, st>>>(J);
   return cudaGetLastError();
 }
 
 cudaError_t launch_cross_apply(const DevJob& J, cudaStream_t st, int* launches) {
   if (J.n_grp == 0) return cudaSuccess;
-  int nmx = J.max_nmax > J.n_obs ? J.max_nmax : J.n_obs;
-  int nph = J.max_n;
-  size_t sh = (size_t)J.Q * (nmx + nph) * sizeof(double2);
-  cudaError_t e = cudaFuncSetAttribute(k_cross_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
-  if (e != cudaSuccess) return e;
-  k_cross_apply<<<J.n_grp, kApplyThreads, sh, st>>>(J);
+  size_t sh = (size_t)J.Q * (J.acc_cap + J.max_n) * sizeof(double2);
   *launches += 1;
-  return cudaGetLastError();
+  switch (J.Q) {
+    case 1: return launch_cross_apply_q<1>(J, sh, st);
+    case 2: return launch_cross_apply_q<2>(J, sh, st);
+    case 3: return launch_cross_apply_q<3>(J, sh, st);
+    default: return launch_cross_apply_q<4>(J, sh, st);
+  }
 }
 
 cudaError_t launch_traces(const DevJob& J, cudaStream_t st, int* launches) {

@@ -327,11 +327,21 @@ int build_plan(const fthms_curve* curves, int ncurves, const fthms_arc* arcs, in
       p.piv_total += N;
       rlog_map[N] = 0;
       p.hankel_self += 0.5 * N * (N + 1.0);
+    }
+  // Self-assembly tiles over bands of consecutive frequencies with the same N.
+  for (int j = 0; j < p.P; ++j) {
+    int l = 1;
+    while (l < p.L) {
+      int N = p.Ntab[(size_t)j * p.L + l];
+      int l1 = l;
+      while (l1 + 1 < p.L && p.Ntab[(size_t)j * p.L + l1 + 1] == N && l1 + 1 - l < kSelfBand) ++l1;
       int nt = (N + kSelfTile - 1) / kSelfTile;
       int sidx = j * (p.L - 1) + (l - 1);
       for (int a = 0; a < nt; ++a)
-        for (int b = a; b < nt; ++b) p.self_tiles.push_back(SelfTile{sidx, a, b});
+        for (int b = a; b < nt; ++b) p.self_tiles.push_back(SelfTile{sidx, l1 - l + 1, a, b});
+      l = l1 + 1;
     }
+  }
   for (auto& kv : rlog_map) {
     kv.second = p.rlog_total;
     p.rlogN.push_back(kv.first);
