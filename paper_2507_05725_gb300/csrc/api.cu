@@ -53,6 +53,8 @@ fthms_status ensure_device(int dev) {
 
 }  // namespace
 
+void fthms::set_last_error(const char* msg) { g_last_error = msg; }
+
 struct fthms_ctx {
   int device = 0;
   size_t budget = 0;
@@ -578,6 +580,8 @@ fthms_status fthms_assemble_self(const fthms_curve* curve, const fthms_arc* arc,
   fthms_req tmp;
   DevJob& J = tmp.J;
   std::vector<SysDesc> sys(1);
+  // One system in a band of length 1 at frequency index 1 with step h = kappa: the band kernel's
+  // kappa = l h, ln l = 0 and the recurrence step h R all refer to this kappa.
   sys[0].arc = 0; sys[0].l = 1; sys[0].N = N; sys[0].panel = 0; sys[0].mat_off = 0; sys[0].vec_off = 0;
   sys[0].piv_off = 0; sys[0].rlog_off = 0; sys[0].kappa = kappa;
   std::vector<Panel> panels(1, Panel{0, N, 0});
@@ -600,6 +604,7 @@ fthms_status fthms_assemble_self(const fthms_curve* curve, const fthms_arc* arc,
   if (s == FTHMS_OK) s = dev_alloc(&tmp, (size_t)N * N, &J.rlog);
   if (s == FTHMS_OK) {
     J.A = reinterpret_cast<double2*>(A_dev);
+    J.h = kappa;
     J.n_rlogN = 1;
     J.n_tiles = (int)tiles.size();
     J.max_n = N;

@@ -1,18 +1,18 @@
 // FP64 Bessel functions of order 0 for the Helmholtz kernel (i/4) H0^(1)(z) = (i/4)(J0 + i Y0)
-// of Section 2.1, written from the classical expansions:
-//   z <= 4       : power series J0 = sum_k (-z^2/4)^k/(k!)^2 and the regular part
-//                  Yhat0 = Y0 - (2/pi)(ln(z/2) + gamma) J0 = (2/pi) sum_{k>=1} (-1)^{k+1} H_k (z^2/4)^k/(k!)^2
-//                  (H_k the harmonic numbers; Abramowitz-Stegun 9.1.12-9.1.13).
-//   4 < z < 20   : Miller's backward recurrence J_{n-1} = (2n/z) J_n - J_{n+1} from order ~z+32,
-//                  normalised by J0 + 2 sum_k J_{2k} = 1, with Neumann's series
-//                  Yhat0 = -(4/pi) sum_{k>=1} (-1)^k J_{2k}/k (A-S 9.1.87-9.1.88).
+// of Section 2.1, in two regimes:
+//   0 <= z < 20  : J0 and the regular part Yhat0 = Y0 - (2/pi)(ln(z/2) + gamma) J0, both entire
+//                  (J0 = sum_k (-z^2/4)^k/(k!)^2, Yhat0 = (2/pi) sum_{k>=1} (-1)^{k+1} H_k (z^2/4)^k/(k!)^2,
+//                  Abramowitz-Stegun 9.1.12-9.1.13), by 13-term Taylor expansions about the centres
+//                  0.25 + 0.5 k of 40 intervals of width 1/2 (coefficients: bessel_taylor.cuh).
 //   z >= 20      : Hankel's asymptotic expansion with 10 + 10 terms,
 //                  H0^(1)(z) ~ sqrt(2/(pi z)) e^{i(z - pi/4)} sum_k (-i)^k a_k/z^k,
 //                  a_k = 1^2 3^2 ... (2k-1)^2/(k! 8^k)  (A-S 9.2.7-9.2.10, DLMF 10.17.5).
-// Accuracy (checked against arbitrary-precision values): <= 4e-16 absolute for J0, Yhat0 below 20,
+// Accuracy (checked against arbitrary-precision values): <= 1.2e-16 absolute for J0, Yhat0 below 20,
 // <= 4e-16 relative to the amplitude sqrt(2/(pi z)) above.
 #pragma once
 #include <cuda_runtime.h>
+
+#include "bessel_taylor.cuh"
 
 namespace fthms {
 
@@ -21,48 +21,28 @@ constexpr double kPiD = 3.14159265358979323846;
 constexpr double kInvPi = 0.31830988618379067153776752674502872;
 constexpr double kTwoOverPi = 0.63661977236758134307553505349005745;
 constexpr double kSqrtHalf = 0.70710678118654752440084436210484904;
-constexpr double kBesselSmall = 4.0;
 constexpr double kBesselLarge = 20.0;
 
-// 1/k^2, harmonic numbers H_k and 1/k for k = 1..32 (index k-1), and the Hankel coefficients a_k
-// (filled by init_constants(); this header is included by one translation unit only).
-__constant__ double c_inv_k2[32];
-__constant__ double c_harm[32];
-__constant__ double c_inv_k[32];
+// Hankel coefficients a_k (filled by init_constants(); this header is included by one translation
+// unit only).
 __constant__ double c_hank_a[20];
 
-// Power series on 0 < z <= 4 (fixed trip count: converged lanes read the constant tables in
-// lock-step, so every table load is a broadcast).
-__device__ __forceinline__ void bessel0_series(double z, double& J0, double& Yh) {
-  const double x = 0.25 * z * z;
-  double term = 1.0, j = 1.0, y = 0.0;
-#pragma unroll 1
-  for (int k = 1; k <= 17; ++k) {
-    term *= -x * c_inv_k2[k - 1];
-    j += term;
-    y = fma(-c_harm[k - 1], term, y);
+// 0 <= z < 20: piecewise Taylor expansions of J0 and Yhat0 about c_k = 0.25 + 0.5 k (both functions
+// are entire), 13 terms each, coefficients from gen_bessel_taylor.py (mpmath).  Every lane runs the
+// same instruction stream (two 12-step Horner chains), whatever its interval.
+__device__ __forceinline__ void bessel0_taylor(double z, double& J0, double& Yh) {
+  const int k = min((int)(2.0 * z), kTaylorIntervals - 1);
+  const double d = z - fma(0.5, (double)k, 0.25);
+  const double* cj = kTaylorJ0[k];
+  const double* cy = kTaylorYh[k];
+  double j = __ldg(&cj[kTaylorDegree]), y = __ldg(&cy[kTaylorDegree]);
+#pragma unroll
+  for (int n = kTaylorDegree - 1; n >= 0; --n) {
+    j = fma(j, d, __ldg(&cj[n]));
+    y = fma(y, d, __ldg(&cy[n]));
   }
   J0 = j;
-  Yh = kTwoOverPi * y;
-}
-
-// Miller backward recurrence on 4 < z < 20 from the fixed order 52 >= z + 32.
-__device__ __forceinline__ void bessel0_miller(double z, double& J0, double& Yh) {
-  const double tz = 2.0 / z;
-  double fp1 = 0.0, f = 1e-30, S = 0.0, T = 0.0;
-#pragma unroll 2
-  for (int n = 52; n >= 2; n -= 2) {
-    const int k = n >> 1;
-    S += f;
-    T = fma((k & 1) ? -c_inv_k[k - 1] : c_inv_k[k - 1], f, T);
-    const double fm1 = fma((double)n * tz, f, -fp1);
-    const double fm2 = fma((double)(n - 1) * tz, fm1, -f);
-    fp1 = fm1;
-    f = fm2;
-  }
-  const double inv = 1.0 / fma(2.0, S, f);
-  J0 = f * inv;
-  Yh = -4.0 * kInvPi * T * inv;
+  Yh = y;
 }
 
 // Hankel asymptotics given w = 1/z, amp = sqrt(2/(pi z)) and (s, c) = (sin z, cos z).
@@ -100,11 +80,8 @@ struct Bessel0 {
 
 __device__ __forceinline__ Bessel0 bessel0(double z) {
   Bessel0 b;
-  if (z <= kBesselSmall) {
-    bessel0_series(z, b.j0, b.y);
-    b.has_yhat = true;
-  } else if (z < kBesselLarge) {
-    bessel0_miller(z, b.j0, b.y);
+  if (z < kBesselLarge) {
+    bessel0_taylor(z, b.j0, b.y);
     b.has_yhat = true;
   } else {
     bessel0_asym(z, b.j0, b.y);

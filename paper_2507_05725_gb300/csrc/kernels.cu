@@ -23,20 +23,9 @@
 namespace fthms {
 
 cudaError_t init_constants() {
-  double ik2[32], harm[32], ik[32], ha[20];
-  double H = 0.0;
-  for (int k = 1; k <= 32; ++k) {
-    ik2[k - 1] = 1.0 / ((double)k * k);
-    H += 1.0 / k;
-    harm[k - 1] = H;
-    ik[k - 1] = 1.0 / k;
-  }
+  double ha[20];
   ha[0] = 1.0;
   for (int k = 1; k < 20; ++k) ha[k] = ha[k - 1] * (double)((2 * k - 1) * (2 * k - 1)) / (8.0 * k);
-  cudaError_t e;
-  if ((e = cudaMemcpyToSymbol(c_inv_k2, ik2, sizeof ik2)) != cudaSuccess) return e;
-  if ((e = cudaMemcpyToSymbol(c_harm, harm, sizeof harm)) != cudaSuccess) return e;
-  if ((e = cudaMemcpyToSymbol(c_inv_k, ik, sizeof ik)) != cudaSuccess) return e;
   return cudaMemcpyToSymbol(c_hank_a, ha, sizeof ha);
 }
 
@@ -221,8 +210,7 @@ __global__ void __launch_bounds__(256) k_assemble_self(DevJob J) {
       ++since;
     } else {
       double Yh;
-      if (z <= kBesselSmall) bessel0_series(z, J0, Yh);
-      else bessel0_miller(z, J0, Yh);
+      bessel0_taylor(z, J0, Yh);
       K1 = -0.5 * kInvPi * J0;
       re = fma(K1, lnl[b] + lratio, -0.25 * Yh);
     }
@@ -358,67 +346,58 @@ __global__ void __launch_bounds__(kLuThreads) k_lu(DevJob J) {
 }
 
 // ---------------------------------------------------------------------------------------------
-// Triangular solves: a warp carries 4 consecutive systems (8 lanes each; the systems of a band share
-// N so their sweeps run in lock-step), all Q right-hand sides together.  Both factors have a unit
-// diagonal (U was scaled by the LU kernel), so each step is a pure column update; D^{-1} is applied
-// once, lane-parallel, between the sweeps.
+// Triangular solves, one warp per system, all Q right-hand sides together.  Both factors have a unit
+// diagonal (the LU kernel scaled U), so every step is a pure column update; D^{-1} is applied once,
+// lane-parallel, between the sweeps.  Factor columns are read through the read-only path so that all
+// loads of a step are in flight together.
 constexpr int kSolveWarps = 4;
-constexpr int kSolveGroup = 8;                  // lanes per system
-constexpr int kSolvePerWarp = 32 / kSolveGroup;
 
 __global__ void __launch_bounds__(32 * kSolveWarps) k_solve(DevJob J, int m) {
   extern __shared__ double2 shs[];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int sub = lane / kSolveGroup, gl = lane % kSolveGroup;
-  const int sidx = (blockIdx.x * kSolveWarps + wid) * kSolvePerWarp + sub;
-  const bool live = sidx < J.nsys;
-  const int Q = J.Q;
-  const SysDesc s = J.sys[live ? sidx : J.nsys - 1];
-  const int N = live ? s.N : 0;
-  int Nw = N;                                   // longest system of the warp
-  for (int o = kSolveGroup; o < 32; o <<= 1) Nw = max(Nw, __shfl_xor_sync(0xffffffffu, Nw, o));
-  double2* b = shs + ((size_t)wid * kSolvePerWarp + sub) * Q * J.max_n;
-  const double2* A = J.A + s.mat_off;
-  const int* piv = J.piv + s.piv_off;
-  const double2* dinv = J.dinv + s.piv_off;
-  const double2* G = J.G + s.vec_off;
-  for (int e = gl; e < Q * N; e += kSolveGroup) b[e] = G[e];
+  const int sidx = blockIdx.x * kSolveWarps + wid;
+  if (sidx >= J.nsys) return;
+  const SysDesc s = J.sys[sidx];
+  const int N = s.N, Q = J.Q;
+  double2* b = shs + (size_t)wid * Q * J.max_n;
+  const double2* __restrict__ A = J.A + s.mat_off;
+  const int* __restrict__ piv = J.piv + s.piv_off;
+  const double2* __restrict__ dinv = J.dinv + s.piv_off;
+  const double2* __restrict__ G = J.G + s.vec_off;
+  for (int e = lane; e < Q * N; e += 32) b[e] = G[e];
   __syncwarp();
-  if (gl < Q) {
-    double2* bq = b + gl * N;
+  if (lane < Q) {
+    double2* bq = b + lane * N;
     for (int k = 0; k < N; ++k) {
-      int p = piv[k];
+      int p = __ldg(&piv[k]);
       if (p != k) { double2 t = bq[k]; bq[k] = bq[p]; bq[p] = t; }
     }
   }
   __syncwarp();
-  for (int k = 0; k < Nw - 1; ++k) {
-    if (k < N - 1) {
-      const double2* Lc = A + (long long)k * N;
-      for (int q = 0; q < Q; ++q) {
-        const double2 xk = b[q * N + k];
-        for (int i = k + 1 + gl; i < N; i += kSolveGroup) b[q * N + i] = cfms(Lc[i], xk, b[q * N + i]);
-      }
+  for (int k = 0; k < N - 1; ++k) {
+    const double2* __restrict__ Lc = A + (long long)k * N;
+    for (int q = 0; q < Q; ++q) {
+      const double2 xk = b[q * N + k];
+#pragma unroll 4
+      for (int i = k + 1 + lane; i < N; i += 32) b[q * N + i] = cfms(__ldg(&Lc[i]), xk, b[q * N + i]);
     }
     __syncwarp();
   }
-  for (int e = gl; e < Q * N; e += kSolveGroup) b[e] = cmul(b[e], dinv[e % N]);
+  for (int e = lane; e < Q * N; e += 32) b[e] = cmul(b[e], __ldg(&dinv[e % N]));
   __syncwarp();
-  for (int k = Nw - 1; k >= 1; --k) {
-    if (k < N) {
-      const double2* Uc = A + (long long)k * N;
-      for (int q = 0; q < Q; ++q) {
-        const double2 xk = b[q * N + k];
-        for (int i = gl; i < k; i += kSolveGroup) b[q * N + i] = cfms(Uc[i], xk, b[q * N + i]);
-      }
+  for (int k = N - 1; k >= 1; --k) {
+    const double2* __restrict__ Uc = A + (long long)k * N;
+    for (int q = 0; q < Q; ++q) {
+      const double2 xk = b[q * N + k];
+#pragma unroll 4
+      for (int i = lane; i < k; i += 32) b[q * N + i] = cfms(__ldg(&Uc[i]), xk, b[q * N + i]);
     }
     __syncwarp();
   }
-  if (!live) return;
   double2* out = J.phi + s.vec_off;
   double2* sum = J.phi_sum + s.vec_off;
   double2* all = J.phi_all ? J.phi_all + (long long)(m - 1) * J.vec_total + s.vec_off : nullptr;
-  for (int e = gl; e < Q * N; e += kSolveGroup) {
+  for (int e = lane; e < Q * N; e += 32) {
     double2 v = b[e];
     out[e] = v;
     sum[e] = m == 1 ? v : cadd(sum[e], v);
@@ -486,9 +465,11 @@ __global__ void __launch_bounds__(kAsmThreads) k_cross_assemble(DevJob J) {
   // 1/l and 1/sqrt(l) over the band, for the far-field recurrence below
   double* invl = Wn + kAsmRows * N;          // <= kAsmBand
   double* rsql = invl + kAsmBand;
+  double* lnl = rsql + kAsmBand;
   for (int l = task.l0 + threadIdx.x; l <= task.l1; l += kAsmThreads) {
     invl[l - task.l0] = 1.0 / l;
     rsql[l - task.l0] = rsqrt((double)l);
+    lnl[l - task.l0] = log((double)l);
   }
   __syncthreads();
   for (int e = threadIdx.x; e < task.nrows * N; e += kAsmThreads) {
@@ -514,6 +495,7 @@ __global__ void __launch_bounds__(kAsmThreads) k_cross_assemble(DevJob J) {
     const double hR = J.h * R;
     const double inv_u = 1.0 / hR;
     const double amp_u = sqrt(kTwoOverPi * inv_u);
+    const double lhr = log(0.5 * hR) + kEulerGamma;     // ln(z/2) + gamma - ln l
     double su, cu;
     sincos(hR, &su, &cu);
     double s0 = 0.0, c0 = 1.0;
@@ -536,7 +518,10 @@ __global__ void __launch_bounds__(kAsmThreads) k_cross_assemble(DevJob J) {
         c0 = cn;
         ++since;
       } else {
-        K = phi_kernel(z);
+        double J0, Yh;
+        bessel0_taylor(z, J0, Yh);
+        const double Y0 = fma(kTwoOverPi * (lnl[l - task.l0] + lhr), J0, Yh);
+        K = make_double2(-0.25 * Y0, 0.25 * J0);
       }
       J.E[J.e_off[(long long)task.pair * J.L + l] + pos] = make_double2(K.x * w, K.y * w);
     }
@@ -839,7 +824,7 @@ cudaError_t launch_lu(const DevJob& J, cudaStream_t st, int* launches) {
 
 cudaError_t launch_cross_assemble(const DevJob& J, cudaStream_t st, int* launches) {
   if (J.n_asm == 0) return cudaSuccess;
-  size_t sh = ((size_t)(4 + 2 * kAsmRows) * J.max_n + 2 * kAsmBand) * sizeof(double);
+  size_t sh = ((size_t)(4 + 2 * kAsmRows) * J.max_n + 3 * kAsmBand) * sizeof(double);
   cudaError_t e = cudaFuncSetAttribute(k_cross_assemble, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
   if (e != cudaSuccess) return e;
   k_cross_assemble<<<J.n_asm, kAsmThreads, sh, st>>>(J);
@@ -879,10 +864,10 @@ cudaError_t launch_restrict(const DevJob& J, cudaStream_t st, int* launches) {
 }
 
 cudaError_t launch_solve(const DevJob& J, int m, cudaStream_t st, int* launches) {
-  size_t sh = (size_t)kSolveWarps * kSolvePerWarp * J.Q * J.max_n * sizeof(double2);
+  size_t sh = (size_t)kSolveWarps * J.Q * J.max_n * sizeof(double2);
   cudaError_t e = cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
   if (e != cudaSuccess) return e;
-  k_solve<<<cdiv(J.nsys, kSolveWarps * kSolvePerWarp), 32 * kSolveWarps, sh, st>>>(J, m);
+  k_solve<<<cdiv(J.nsys, kSolveWarps), 32 * kSolveWarps, sh, st>>>(J, m);
   *launches += 1;
   return cudaGetLastError();
 }

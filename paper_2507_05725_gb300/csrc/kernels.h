@@ -64,6 +64,9 @@ struct DevJob {
 
 cudaError_t init_constants();
 
+// Sets the calling thread's message returned by fthms_last_error() (defined with the C ABI).
+void set_last_error(const char* msg);
+
 cudaError_t launch_bessel0(const double* z, double* j0, double* y0, double* yh, int n, cudaStream_t st);
 
 // Individual pipeline stages (all asynchronous on `st`).
