@@ -214,6 +214,25 @@ fthms_status fthms_bessel0(const double* z_dev, double* j0_dev, double* y0_dev,
 fthms_status fthms_assemble_self(const fthms_curve* curve, const fthms_arc* arc, int N,
                                  double kappa, double* A_dev, void* cuda_stream);
 
+/* Allocation-free variant of fthms_assemble_self (the paper has no counterpart; this is a library
+ * convenience).  It is for callers that may not allocate device memory: code running inside a
+ * stream capture or a memory-capped pool, or a host application whose own allocator owns all device
+ * memory and forbids cudaMalloc/cudaFree from third-party code.  It computes the same matrix (same
+ * kernels, same layout: A[i + l*N], interleaved complex, 2*N*N doubles in A_dev) but keeps its
+ * temporary device data in a fixed ~534 KB static device array of the library instead of
+ * allocating: every GPU that loads the library holds that array until the process exits.  The
+ * caller still provides A_dev.
+ *  - N must be in [2, 256] (the array's capacity); larger N returns FTHMS_EINVAL.
+ *  - The first call on each device (with that device current) looks up the array's device address
+ *    and uploads the Bessel coefficient tables; make that first call before any stream capture.
+ *  - All calls share the one array and leave their data in it.  Calls whose work overlaps on the
+ *    GPU (different streams or threads without ordering) race on it; calls on one stream are
+ *    ordered.  Every call rewrites all of the array that it reads, so nothing needs clearing.
+ *  - No cudaMalloc/cudaFree or other allocating routine is called; the upload is a cudaMemcpyAsync
+ *    from host stack memory on cuda_stream. */
+fthms_status fthms_assemble_self_noalloc(const fthms_curve* curve, const fthms_arc* arc, int N,
+                                         double kappa, double* A_dev, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

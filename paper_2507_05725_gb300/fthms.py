@@ -83,6 +83,8 @@ def _load():
         "fthms_last_error": (C.c_char_p, []),
         "fthms_bessel0": (st, [vp, vp, vp, vp, C.c_int, vp]),
         "fthms_assemble_self": (st, [C.POINTER(fthms_curve), C.POINTER(fthms_arc), C.c_int, C.c_double, vp, vp]),
+        "fthms_assemble_self_noalloc": (st, [C.POINTER(fthms_curve), C.POINTER(fthms_arc), C.c_int, C.c_double,
+                                             vp, vp]),
         "fthms_profile": (st, [vp, C.c_int]),
         "fthms_stage_times": (st, [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
     }
@@ -98,7 +100,7 @@ LIB = _load()
 EXPORTED = ["fthms_create", "fthms_destroy", "fthms_prepare", "fthms_run", "fthms_submit", "fthms_poll",
             "fthms_wait", "fthms_traces", "fthms_densities", "fthms_densities_dev", "fthms_node_counts",
             "fthms_stats", "fthms_release", "fthms_last_error", "fthms_bessel0", "fthms_assemble_self",
-            "fthms_profile", "fthms_stage_times"]
+            "fthms_profile", "fthms_stage_times", "fthms_assemble_self_noalloc"]
 
 
 def _check(status):
@@ -234,6 +236,15 @@ def fthms_assemble_self(curve: dict, arc, N, kappa, A_ptr, stream=None):
     c = fthms_curve(len(arrs[0]) - 1, *[_dptr(a) for a in arrs])
     a = fthms_arc(0, float(arc[0]), float(arc[1]))
     _check(LIB.fthms_assemble_self(C.byref(c), C.byref(a), int(N), float(kappa), C.c_void_p(A_ptr), stream))
+
+
+def fthms_assemble_self_noalloc(curve: dict, arc, N, kappa, A_ptr, stream=None):
+    """Same matrix as fthms_assemble_self, without device allocation (static scratch, N <= 256)."""
+    arrs = [np.ascontiguousarray(np.asarray(curve[k], dtype=np.float64)) for k in ("ax", "bx", "ay", "by")]
+    c = fthms_curve(len(arrs[0]) - 1, *[_dptr(a) for a in arrs])
+    a = fthms_arc(0, float(arc[0]), float(arc[1]))
+    _check(LIB.fthms_assemble_self_noalloc(C.byref(c), C.byref(a), int(N), float(kappa), C.c_void_p(A_ptr),
+                                           stream))
 
 
 class Job:
