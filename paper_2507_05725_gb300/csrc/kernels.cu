@@ -183,41 +183,62 @@ __global__ void __launch_bounds__(256) k_assemble_self(DevJob J) {
   const double dy = J.node_y[pn.off + i] - J.node_y[pn.off + c];
   const double R = sqrt(fma(dx, dx, dy * dy));
   const double dts = fabs(J.node_t[pn.off + i] - J.node_t[pn.off + c]);
-  const double ldts = log(dts);
   const double hR = J.h * R;
-  const double lratio = log(hR / (2.0 * dts)) + kEulerGamma;   // ln(z/(2|t-s|)) + gamma - ln l
+  // A = K1 Rlog + K2 w with K1 = -J0/(2 pi):
+  //   z < 20:  K2 = (i/4) J0 - (J0/(2 pi)) [ln l + ln(hR/(2|t-s|)) + gamma] - Yhat0/4
+  //   z >= 20: K2 = (i/4) J0 - Y0/4 + (J0/(2 pi)) ln|t-s|
+  // so Re A = J0 * alpha - (w/4) Y, with alpha depending on the entry (and on ln l below 20).
+  const double lratio = log(hR / (2.0 * dts)) + kEulerGamma;
+  const double alpha_a = -0.5 * kInvPi * (rl - w * log(dts));          // z >= 20
+  const double qw = 0.25 * w;
   const double inv_u = 1.0 / hR, amp_u = sqrt(kTwoOverPi * inv_u);
   double su, cu;
   sincos(hR, &su, &cu);
-  double s = 0.0, co = 1.0;
-  int since = 16;
-  for (int b = 0; b < nb; ++b) {
-    const int l = s0.l + b;
+  const int lsw = max(s0.l, (int)ceil(kBesselLarge * inv_u));         // first l with z >= 20
+  const int lend = s0.l + nb;
+  const double zmin = (lsw * J.h) * R;
+  const int kmax = zmin >= 100.0 ? 4 : (zmin >= 50.0 ? 5 : (zmin >= 30.0 ? 7 : 9));
+  for (int l = s0.l; l < min(lsw, lend); ++l) {
+    const int b = l - s0.l;
     const double z = (l * J.h) * R;
-    double K1, re, J0;
-    if (z >= kBesselLarge) {
-      if (since >= 16) {
-        sincos(z, &s, &co);
-        since = 0;
-      }
-      double Y0;
-      hankel_asym_phase(inv_u * invl[b], amp_u * rsql[b], s, co, J0, Y0);
-      K1 = -0.5 * kInvPi * J0;
-      re = fma(-K1, ldts, -0.25 * Y0);
-      const double cn = fma(co, cu, -s * su);
-      s = fma(s, cu, co * su);
-      co = cn;
-      ++since;
-    } else {
-      double Yh;
-      bessel0_taylor(z, J0, Yh);
-      K1 = -0.5 * kInvPi * J0;
-      re = fma(K1, lnl[b] + lratio, -0.25 * Yh);
-    }
-    const double2 v = make_double2(fma(K1, rl, re * w), 0.25 * J0 * w);
+    double J0, Yh;
+    bessel0_taylor(z, J0, Yh);
+    const double alpha = -0.5 * kInvPi * fma(w, lnl[b] + lratio, rl);
+    const double2 v = make_double2(fma(alpha, J0, -qw * Yh), qw * J0);
     double2* A = J.A + J.sys[tile.sys + b].mat_off;
     A[e1] = v;
     A[e2] = v;
+  }
+  double cx = 0.0, sx = 0.0;
+  int since = 16;
+  for (int l = lsw; l < lend; ++l) {
+    const int b = l - s0.l;
+    if (since >= 16) {
+      double sn, cs;
+      sincos((l * J.h) * R, &sn, &cs);
+      cx = (cs + sn) * kSqrtHalf;
+      sx = (sn - cs) * kSqrtHalf;
+      since = 0;
+    }
+    const double wz = inv_u * invl[b];
+    const double w2 = -wz * wz;
+    double P = c_hank_a[2 * kmax], Qa = c_hank_a[2 * kmax + 1];
+    for (int k = kmax - 1; k >= 0; --k) {
+      P = fma(P, w2, c_hank_a[2 * k]);
+      Qa = fma(Qa, w2, c_hank_a[2 * k + 1]);
+    }
+    Qa *= wz;
+    const double amp = amp_u * rsql[b];
+    const double J0 = amp * fma(P, cx, Qa * sx);
+    const double Y0 = amp * fma(P, sx, -Qa * cx);
+    const double2 v = make_double2(fma(alpha_a, J0, -qw * Y0), qw * J0);
+    double2* A = J.A + J.sys[tile.sys + b].mat_off;
+    A[e1] = v;
+    A[e2] = v;
+    const double cn = fma(cx, cu, -sx * su);
+    sx = fma(sx, cu, cx * su);
+    cx = cn;
+    ++since;
   }
 }
 
@@ -489,41 +510,52 @@ __global__ void __launch_bounds__(kAsmThreads) k_cross_assemble(DevJob J) {
       }
       continue;
     }
-    // Far rule.  Above z = 20 the Hankel expansion's phase e^{iz} advances by the fixed rotation
-    // e^{i h R} from one frequency to the next (re-seeded by sincos every 16 steps) and
-    // 1/z = (1/(hR))(1/l), sqrt(2/(pi z)) = sqrt(2/(pi hR))/sqrt(l).
+    // Far rule.  Above z = 20 the Hankel expansion's phase advances by the fixed rotation e^{i h R}
+    // from one frequency to the next (re-seeded by sincos every 16 steps); 1/z = (1/(hR))(1/l) and
+    // sqrt(2/(pi z)) = sqrt(2/(pi hR))/sqrt(l) come from per-band tables; the number of asymptotic
+    // terms follows the smallest z of the band.  The regime switch is an integer frequency index.
     const double hR = J.h * R;
     const double inv_u = 1.0 / hR;
-    const double amp_u = sqrt(kTwoOverPi * inv_u);
+    const double ampw = sqrt(kTwoOverPi * inv_u) * (0.25 * w);
     const double lhr = log(0.5 * hR) + kEulerGamma;     // ln(z/2) + gamma - ln l
     double su, cu;
     sincos(hR, &su, &cu);
-    double s0 = 0.0, c0 = 1.0;
+    const int lsw = max(task.l0, (int)ceil(kBesselLarge * inv_u));   // first l with z >= 20
+    const double zmin = (lsw * J.h) * R;
+    const int kmax = zmin >= 100.0 ? 4 : (zmin >= 50.0 ? 5 : (zmin >= 30.0 ? 7 : 9));
+    double cx = 0.0, sx = 0.0;
     int since = 16;
-    for (int l = task.l0; l <= task.l1; ++l) {
+    double2* Ep = J.E + pos;
+    const long long* eo = J.e_off + (long long)task.pair * J.L;
+    for (int l = task.l0; l < min(lsw, task.l1 + 1); ++l) {
       const double z = (l * J.h) * R;
-      double2 K;
-      if (z >= kBesselLarge) {
-        if (since >= 16) {
-          sincos(z, &s0, &c0);
-          since = 0;
-        }
-        const double wz = inv_u * invl[l - task.l0];
-        const double amp = amp_u * rsql[l - task.l0];
-        double J0, Y0;
-        hankel_asym_phase(wz, amp, s0, c0, J0, Y0);
-        K = make_double2(-0.25 * Y0, 0.25 * J0);
-        const double cn = fma(c0, cu, -s0 * su);
-        s0 = fma(s0, cu, c0 * su);
-        c0 = cn;
-        ++since;
-      } else {
-        double J0, Yh;
-        bessel0_taylor(z, J0, Yh);
-        const double Y0 = fma(kTwoOverPi * (lnl[l - task.l0] + lhr), J0, Yh);
-        K = make_double2(-0.25 * Y0, 0.25 * J0);
+      double J0, Yh;
+      bessel0_taylor(z, J0, Yh);
+      const double Y0 = fma(kTwoOverPi * (lnl[l - task.l0] + lhr), J0, Yh);
+      Ep[eo[l]] = make_double2(-0.25 * w * Y0, 0.25 * w * J0);
+    }
+    for (int l = lsw; l <= task.l1; ++l) {
+      if (since >= 16) {
+        double s, c;
+        sincos((l * J.h) * R, &s, &c);
+        cx = (c + s) * kSqrtHalf;                        // cos(z - pi/4)
+        sx = (s - c) * kSqrtHalf;                        // sin(z - pi/4)
+        since = 0;
       }
-      J.E[J.e_off[(long long)task.pair * J.L + l] + pos] = make_double2(K.x * w, K.y * w);
+      const double wz = inv_u * invl[l - task.l0];
+      const double w2 = -wz * wz;
+      double P = c_hank_a[2 * kmax], Qa = c_hank_a[2 * kmax + 1];
+      for (int k = kmax - 1; k >= 0; --k) {
+        P = fma(P, w2, c_hank_a[2 * k]);
+        Qa = fma(Qa, w2, c_hank_a[2 * k + 1]);
+      }
+      Qa *= wz;
+      const double a = ampw * rsql[l - task.l0];
+      Ep[eo[l]] = make_double2(-a * fma(P, sx, -Qa * cx), a * fma(P, cx, Qa * sx));
+      const double cn = fma(cx, cu, -sx * su);
+      sx = fma(sx, cu, cx * su);
+      cx = cn;
+      ++since;
     }
   }
 }
