@@ -367,58 +367,114 @@ __global__ void __launch_bounds__(kLuThreads) k_lu(DevJob J) {
 }
 
 // ---------------------------------------------------------------------------------------------
-// Triangular solves, one warp per system, all Q right-hand sides together.  Both factors have a unit
-// diagonal (the LU kernel scaled U), so every step is a pure column update; D^{-1} is applied once,
-// lane-parallel, between the sweeps.  Factor columns are read through the read-only path so that all
-// loads of a step are in flight together.
+// Triangular solves.  A warp carries kSolvePerWarp = 4 systems (8 lanes each; consecutive systems of a
+// frequency band share N, so the groups run converged).  Both factors have a unit diagonal (the LU
+// kernel scaled U and kept D^{-1}), and both sweeps go in blocks of 8 columns: an 8 x 8 triangle by
+// group shuffles, then a rectangular update whose 8 column loads per row are independent, so a block
+// costs about one memory latency instead of eight.
 constexpr int kSolveWarps = 4;
+constexpr int kSolveGroup = 8;
+constexpr int kSolvePerWarp = 32 / kSolveGroup;
+constexpr int kSB = 8;   // sweep block
 
 __global__ void __launch_bounds__(32 * kSolveWarps) k_solve(DevJob J, int m) {
   extern __shared__ double2 shs[];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int sidx = blockIdx.x * kSolveWarps + wid;
-  if (sidx >= J.nsys) return;
+  const int sub = lane / kSolveGroup, gl = lane % kSolveGroup;
+  const unsigned gmask = 0xffu << (sub * kSolveGroup);
+  const int sidx = (blockIdx.x * kSolveWarps + wid) * kSolvePerWarp + sub;
+  if (sidx >= J.nsys) return;   // whole groups leave together
   const SysDesc s = J.sys[sidx];
   const int N = s.N, Q = J.Q;
-  double2* b = shs + (size_t)wid * Q * J.max_n;
+  double2* b = shs + ((size_t)wid * kSolvePerWarp + sub) * Q * J.max_n;
   const double2* __restrict__ A = J.A + s.mat_off;
   const int* __restrict__ piv = J.piv + s.piv_off;
   const double2* __restrict__ dinv = J.dinv + s.piv_off;
   const double2* __restrict__ G = J.G + s.vec_off;
-  for (int e = lane; e < Q * N; e += 32) b[e] = G[e];
-  __syncwarp();
-  if (lane < Q) {
-    double2* bq = b + lane * N;
+  for (int e = gl; e < Q * N; e += kSolveGroup) b[e] = G[e];
+  __syncwarp(gmask);
+  if (gl < Q) {
+    double2* bq = b + gl * N;
     for (int k = 0; k < N; ++k) {
-      int p = __ldg(&piv[k]);
+      const int p = __ldg(&piv[k]);
       if (p != k) { double2 t = bq[k]; bq[k] = bq[p]; bq[p] = t; }
     }
   }
-  __syncwarp();
-  for (int k = 0; k < N - 1; ++k) {
-    const double2* __restrict__ Lc = A + (long long)k * N;
+  __syncwarp(gmask);
+  // forward sweep with unit lower L
+  for (int k0 = 0; k0 < N; k0 += kSB) {
+    const int w = min(kSB, N - k0);
+    double2 Lr[kSB];
+#pragma unroll
+    for (int c = 0; c < kSB; ++c)
+      Lr[c] = (c < gl && gl < w) ? __ldg(&A[(long long)(k0 + c) * N + k0 + gl]) : make_double2(0.0, 0.0);
     for (int q = 0; q < Q; ++q) {
-      const double2 xk = b[q * N + k];
-#pragma unroll 4
-      for (int i = k + 1 + lane; i < N; i += 32) b[q * N + i] = cfms(__ldg(&Lc[i]), xk, b[q * N + i]);
+      double2* bq = b + q * N;
+      double2 x = gl < w ? bq[k0 + gl] : make_double2(0.0, 0.0);
+      double2 xs[kSB];
+#pragma unroll
+      for (int c = 0; c < kSB; ++c) {
+        const double2 xc = make_double2(__shfl_sync(gmask, x.x, c, kSolveGroup), __shfl_sync(gmask, x.y, c, kSolveGroup));
+        xs[c] = xc;
+        if (c + 1 < w && gl > c) x = cfms(Lr[c], xc, x);
+      }
+      if (gl < w) bq[k0 + gl] = x;
+#pragma unroll
+      for (int c = 0; c < kSB; ++c)
+        xs[c] = make_double2(__shfl_sync(gmask, x.x, c, kSolveGroup), __shfl_sync(gmask, x.y, c, kSolveGroup));
+      if (w == kSB) {
+#pragma unroll 2
+        for (int i = k0 + kSB + gl; i < N; i += kSolveGroup) {
+          double2 acc = bq[i];
+#pragma unroll
+          for (int c = 0; c < kSB; ++c) acc = cfms(__ldg(&A[(long long)(k0 + c) * N + i]), xs[c], acc);
+          bq[i] = acc;
+        }
+      }
     }
-    __syncwarp();
+    __syncwarp(gmask);
   }
-  for (int e = lane; e < Q * N; e += 32) b[e] = cmul(b[e], __ldg(&dinv[e % N]));
-  __syncwarp();
-  for (int k = N - 1; k >= 1; --k) {
-    const double2* __restrict__ Uc = A + (long long)k * N;
+  for (int e = gl; e < Q * N; e += kSolveGroup) b[e] = cmul(b[e], __ldg(&dinv[e % N]));
+  __syncwarp(gmask);
+  // backward sweep with unit upper U'
+  for (int k1 = N; k1 > 0; k1 -= kSB) {
+    const int k0 = max(0, k1 - kSB), w = k1 - k0;
+    double2 Ur[kSB];
+#pragma unroll
+    for (int c = 0; c < kSB; ++c)
+      Ur[c] = (c > gl && c < w) ? __ldg(&A[(long long)(k0 + c) * N + k0 + gl]) : make_double2(0.0, 0.0);
     for (int q = 0; q < Q; ++q) {
-      const double2 xk = b[q * N + k];
-#pragma unroll 4
-      for (int i = lane; i < k; i += 32) b[q * N + i] = cfms(__ldg(&Uc[i]), xk, b[q * N + i]);
+      double2* bq = b + q * N;
+      double2 x = gl < w ? bq[k0 + gl] : make_double2(0.0, 0.0);
+#pragma unroll
+      for (int c = kSB - 1; c >= 1; --c) {
+        if (c < w) {
+          const double2 xc = make_double2(__shfl_sync(gmask, x.x, c, kSolveGroup), __shfl_sync(gmask, x.y, c, kSolveGroup));
+          if (gl < c) x = cfms(Ur[c], xc, x);
+        }
+      }
+      if (gl < w) bq[k0 + gl] = x;
+      double2 xs[kSB];
+#pragma unroll
+      for (int c = 0; c < kSB; ++c)
+        xs[c] = make_double2(__shfl_sync(gmask, x.x, c, kSolveGroup), __shfl_sync(gmask, x.y, c, kSolveGroup));
+      // a partial block (w < 8) is always the top one (k0 = 0): no rows above it
+      if (w == kSB) {
+#pragma unroll 2
+        for (int i = gl; i < k0; i += kSolveGroup) {
+          double2 acc = bq[i];
+#pragma unroll
+          for (int c = 0; c < kSB; ++c) acc = cfms(__ldg(&A[(long long)(k0 + c) * N + i]), xs[c], acc);
+          bq[i] = acc;
+        }
+      }
     }
-    __syncwarp();
+    __syncwarp(gmask);
   }
   double2* out = J.phi + s.vec_off;
   double2* sum = J.phi_sum + s.vec_off;
   double2* all = J.phi_all ? J.phi_all + (long long)(m - 1) * J.vec_total + s.vec_off : nullptr;
-  for (int e = lane; e < Q * N; e += 32) {
+  for (int e = gl; e < Q * N; e += kSolveGroup) {
     double2 v = b[e];
     out[e] = v;
     sum[e] = m == 1 ? v : cadd(sum[e], v);
@@ -896,10 +952,10 @@ cudaError_t launch_restrict(const DevJob& J, cudaStream_t st, int* launches) {
 }
 
 cudaError_t launch_solve(const DevJob& J, int m, cudaStream_t st, int* launches) {
-  size_t sh = (size_t)kSolveWarps * J.Q * J.max_n * sizeof(double2);
+  size_t sh = (size_t)kSolveWarps * kSolvePerWarp * J.Q * J.max_n * sizeof(double2);
   cudaError_t e = cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
   if (e != cudaSuccess) return e;
-  k_solve<<<cdiv(J.nsys, kSolveWarps), 32 * kSolveWarps, sh, st>>>(J, m);
+  k_solve<<<cdiv(J.nsys, kSolveWarps * kSolvePerWarp), 32 * kSolveWarps, sh, st>>>(J, m);
   *launches += 1;
   return cudaGetLastError();
 }
