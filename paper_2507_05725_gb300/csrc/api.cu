@@ -151,6 +151,17 @@ fthms_status upload_job(fthms_req* r) {
   J.max_nmax = 0;
   for (int k = 0; k < p.P; ++k) J.max_nmax = std::max(J.max_nmax, p.Nmax[k]);
   J.acc_cap = std::max(J.max_nmax, p.n_obs);
+  J.row_cap = 0;
+  J.ph_cap = 0;
+  for (const CrossGrp& g : p.grps) {
+    int rows = 0, nsum = 0;
+    for (int b = g.blk_begin; b < g.blk_end; ++b) {
+      rows += p.blks[b].nrows;
+      nsum += p.blks[b].N;
+    }
+    J.row_cap = std::max(J.row_cap, rows);
+    J.ph_cap = std::max(J.ph_cap, nsum);
+  }
   J.h = p.h; J.dt = p.dt; J.sign = p.sig.sign;
   J.sig_kind = p.sig.kind;
   J.z0x = p.sig.z0[0]; J.z0y = p.sig.z0[1];

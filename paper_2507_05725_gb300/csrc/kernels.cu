@@ -618,12 +618,14 @@ __global__ void __launch_bounds__(kAsmThreads) k_cross_assemble(DevJob J) {
 
 // ---------------------------------------------------------------------------------------------
 // Cross apply: W_k(x, q, l) = sum_j sum_i E_{l,k,j}[i, r] phi_j[q, i]; observation sums accumulate.
-// One thread per target row: the source-major blocks make every load coalesced across the warp,
-// the densities are shared-memory broadcasts and no cross-lane reduction is needed.
+// One thread per target row, the rows of all source blocks of the group concatenated so that warps
+// stay full (on this GPU an FP64 instruction costs a full warp slot of the FP64 pipe whatever its
+// active lanes); the source-major blocks make every load coalesced, the densities are shared-memory
+// broadcasts, and the per-row sums are added per target in a fixed block order (deterministic).
+// The window count is a template parameter so that no FMA is issued for absent windows.
 constexpr int kApplyThreads = 256;
+constexpr int kApplyMaxBlk = 64;   // receiving groups have at most P <= 64 source blocks
 
-// The window count is a template parameter: on this GPU an FP64 instruction costs a full warp slot
-// of the FP64 pipe whether or not its lanes are predicated on, so no FMA is issued for absent windows.
 template <int Q>
 __global__ void __launch_bounds__(kApplyThreads) k_cross_apply(DevJob J) {
   extern __shared__ double2 shc[];
@@ -631,34 +633,60 @@ __global__ void __launch_bounds__(kApplyThreads) k_cross_apply(DevJob J) {
   const int l = g.l;
   const bool obs = g.k == J.P;
   const int nout = obs ? J.n_obs : J.panels[J.tpanel[g.k]].N;
-  double2* acc = shc;                              // [Q][nout]
-  double2* ph = shc + (size_t)Q * J.acc_cap;       // [Q][N]
-  for (int e = threadIdx.x; e < Q * nout; e += kApplyThreads) acc[e] = make_double2(0.0, 0.0);
-  for (int b = g.blk_begin; b < g.blk_end; ++b) {
-    const CrossBlk B = J.blks[b];
-    const int N = B.N, nr = B.nrows;
-    const double2* p = J.phi + J.sys[B.sys].vec_off;
-    __syncthreads();
-    for (int e = threadIdx.x; e < Q * N; e += kApplyThreads) ph[e] = p[e];
-    __syncthreads();
-    const double2* E = J.E + B.e_off;
-    for (int r = threadIdx.x; r < nr; r += kApplyThreads) {
-      double2 s[Q];
-#pragma unroll
-      for (int q = 0; q < Q; ++q) s[q] = make_double2(0.0, 0.0);
-      const double2* Er = E + r;
-#pragma unroll 4
-      for (int i = 0; i < N; ++i) {
-        const double2 ev = Er[(long long)i * nr];
-#pragma unroll
-        for (int q = 0; q < Q; ++q) s[q] = cfma(ev, ph[q * N + i], s[q]);
-      }
-      const int out = J.tgts[B.tgt_off + r].out;
-#pragma unroll
-      for (int q = 0; q < Q; ++q) acc[q * nout + out] = cadd(acc[q * nout + out], s[q]);
+  const int nb = g.blk_end - g.blk_begin;
+  __shared__ int s_row0[kApplyMaxBlk + 1], s_ph0[kApplyMaxBlk + 1];
+  if (threadIdx.x == 0) {
+    int r = 0, p = 0;
+    for (int b = 0; b < nb; ++b) {
+      s_row0[b] = r;
+      s_ph0[b] = p;
+      r += J.blks[g.blk_begin + b].nrows;
+      p += Q * J.blks[g.blk_begin + b].N;
     }
+    s_row0[nb] = r;
+    s_ph0[nb] = p;
   }
   __syncthreads();
+  const int nrow = s_row0[nb];
+  double2* acc = shc;                              // [Q][nout]
+  double2* res = acc + (size_t)Q * J.acc_cap;      // [Q][nrow]
+  double2* ph = res + (size_t)Q * J.row_cap;       // concatenated [Q][N_b] densities
+  for (int e = threadIdx.x; e < Q * nout; e += kApplyThreads) acc[e] = make_double2(0.0, 0.0);
+  for (int b = 0; b < nb; ++b) {
+    const CrossBlk B = J.blks[g.blk_begin + b];
+    const double2* p = J.phi + J.sys[B.sys].vec_off;
+    for (int e = threadIdx.x; e < Q * B.N; e += kApplyThreads) ph[s_ph0[b] + e] = p[e];
+  }
+  __syncthreads();
+  int b = 0;
+  for (int row = threadIdx.x; row < nrow; row += kApplyThreads) {
+    while (row >= s_row0[b + 1]) ++b;
+    const CrossBlk B = J.blks[g.blk_begin + b];
+    const int N = B.N, nr = B.nrows, r = row - s_row0[b];
+    const double2* phb = ph + s_ph0[b];
+    double2 s[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) s[q] = make_double2(0.0, 0.0);
+    const double2* __restrict__ Er = J.E + B.e_off + r;
+#pragma unroll 4
+    for (int i = 0; i < N; ++i) {
+      const double2 ev = __ldg(&Er[(long long)i * nr]);
+#pragma unroll
+      for (int q = 0; q < Q; ++q) s[q] = cfma(ev, phb[q * N + i], s[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < Q; ++q) res[q * nrow + row] = s[q];
+  }
+  __syncthreads();
+  for (int bb = 0; bb < nb; ++bb) {
+    const CrossBlk B = J.blks[g.blk_begin + bb];
+    for (int r = threadIdx.x; r < B.nrows; r += kApplyThreads) {
+      const int out = J.tgts[B.tgt_off + r].out;
+#pragma unroll
+      for (int q = 0; q < Q; ++q) acc[q * nout + out] = cadd(acc[q * nout + out], res[q * nrow + s_row0[bb] + r]);
+    }
+    __syncthreads();
+  }
   if (obs) {
     for (int e = threadIdx.x; e < Q * nout; e += kApplyThreads) {
       int q = e / nout, z = e % nout;
@@ -970,7 +998,7 @@ static cudaError_t launch_cross_apply_q(const DevJob& J, size_t sh, cudaStream_t
 
 cudaError_t launch_cross_apply(const DevJob& J, cudaStream_t st, int* launches) {
   if (J.n_grp == 0) return cudaSuccess;
-  size_t sh = (size_t)J.Q * (J.acc_cap + J.max_n) * sizeof(double2);
+  size_t sh = (size_t)J.Q * (J.acc_cap + J.row_cap + J.ph_cap) * sizeof(double2);
   *launches += 1;
   switch (J.Q) {
     case 1: return launch_cross_apply_q<1>(J, sh, st);

@@ -10,6 +10,7 @@ namespace fthms {
 struct DevJob {
   int P, L, Q, K, NT, M, n_obs, n_tout, nsys, n_act, n_grp, n_asm, n_tiles, n_rlogN, n_restr;
   int logK, max_nmax, max_n, acc_cap;
+  int row_cap, ph_cap;           // max rows and max sum of source N over the cross groups
   double h, dt, sign;
   // signal
   int sig_kind;

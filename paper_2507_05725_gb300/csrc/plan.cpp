@@ -160,6 +160,10 @@ int build_plan(const fthms_curve* curves, int ncurves, const fthms_arc* arcs, in
     p.curves[c].ay.assign(cv.ay, cv.ay + cv.degree + 1);
     p.curves[c].by.assign(cv.by, cv.by + cv.degree + 1);
   }
+  if (narcs > 64) {
+    err = "at most 64 arcs per job";
+    return FTHMS_EINVAL;
+  }
   p.P = narcs;
   p.arcs.resize(narcs);
   for (int j = 0; j < narcs; ++j) {
