@@ -32,6 +32,37 @@ import numpy as np  # noqa: E402
 
 METRIC = "arc-ω BIE solves/s at ≤1e-10 rel err, served+batched vs plain FP64; p50/p99 ms"
 FP64_PEAK_GFLOPS = 152 * 4 * 2.07  # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz max SM clock
+# Algorithmic FP64 flops of one stored kernel entry: one far-field Hankel step at the fewest asymptotic
+# terms (5 + 5 Horner FMAs, 1/z and 1/z^2, the amplitude, the two components, the phase rotation).
+FLOPS_PER_KERNEL_ENTRY = 34
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_config2_small.md")
+
+
+def kernels_hash():
+    import hashlib
+    with open(os.path.join(ROOT, "paper_2507_05725_gb300", "csrc", "kernels.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def measured_traffic_per_unit():
+    """DRAM bytes per unit of work and kernel, from the committed ncu summary, if it was taken on the
+    current kernels.cu (else {})."""
+    try:
+        txt = open(TRAFFIC_FILE).read()
+    except OSError:
+        return {}
+    h = None
+    out = {}
+    for line in txt.splitlines():
+        if line.startswith("kernels.cu sha256:"):
+            h = line.split(":", 1)[1].strip().strip("`")
+        cells = [c.strip().strip("`") for c in line.strip().strip("|").split("|")]
+        if len(cells) >= 6 and cells[0].startswith("k_"):
+            try:
+                out[cells[0]] = float(cells[5])
+            except ValueError:
+                pass
+    return out if h == kernels_hash() else {}
 
 
 def _dist():
@@ -224,20 +255,28 @@ def ours(args):
         e2e_ms = float(t.item())
     F.fthms_destroy(ctx)
 
-    # roofline of the dominant stage (FP64 pipe-bound kernels)
+    # roofline of the dominant stage (every stage is FP64-pipe bound)
     dom = max(stages, key=lambda k: stages[k][0])
     dom_ms, dom_launch = stages[dom]
     per_launch_ms = dom_ms / max(1, dom_launch)
-    flops_per_launch = {"cross_apply": st["apply_flops"] / M, "lu": st["lu_flops"], "solve": st["solve_flops"] / M}
-    roofline = None
+    self_entries = st["hankel_evals"] - st["cross_entries"]
+    units = {"cross_apply": st["cross_entries"] * Q, "cross_assemble": st["cross_entries"],
+             "assemble_self": self_entries, "lu": st["systems"], "solve": st["systems"] * Q}
+    flops_per_launch = {"cross_apply": st["apply_flops"] / M, "lu": st["lu_flops"], "solve": st["solve_flops"] / M,
+                        "cross_assemble": FLOPS_PER_KERNEL_ENTRY * st["cross_entries"],
+                        "assemble_self": FLOPS_PER_KERNEL_ENTRY * self_entries}
+    kname = {"cross_apply": "k_cross_apply", "cross_assemble": "k_cross_assemble", "lu": "k_lu",
+             "solve": "k_solve", "assemble_self": "k_assemble_self"}.get(dom)
+    tpu = measured_traffic_per_unit()
+    traffic = tpu[kname] * units[dom] if kname in tpu and dom in units else None
+    roofline = {"bound": "alu", "achieved": None, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": None,
+                "traffic": traffic, "kernel": dom,
+                "note": "FP64 pipe peak derived from the unit counts and clock: 152 SMs x 4 flop/clk x 2.07 GHz; "
+                        "algorithmic flops per launch / CUDA-event time on the library stream"}
     if dom in flops_per_launch:
         ach = flops_per_launch[dom] / (per_launch_ms * 1e-3) / 1e9
-        roofline = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                    "frac": ach / FP64_PEAK_GFLOPS, "traffic": None, "kernel": dom,
-                    "note": "FP64 pipe: 152 SMs x 4 flop/clk x 2.07 GHz; algorithmic flops per launch / event time"}
-    else:
-        roofline = {"bound": "alu", "achieved": None, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": None,
-                    "traffic": None, "kernel": dom}
+        roofline.update({"achieved": ach, "frac": ach / FP64_PEAK_GFLOPS,
+                         "algorithmic_flops_per_launch": flops_per_launch[dom], "ms_per_launch": per_launch_ms})
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

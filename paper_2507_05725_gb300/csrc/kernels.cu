@@ -367,21 +367,20 @@ __global__ void __launch_bounds__(kLuThreads) k_lu(DevJob J) {
 }
 
 // ---------------------------------------------------------------------------------------------
-// Triangular solves.  A warp carries kSolvePerWarp = 4 systems (8 lanes each; consecutive systems of a
-// frequency band share N, so the groups run converged).  Both factors have a unit diagonal (the LU
-// kernel scaled U and kept D^{-1}), and both sweeps go in blocks of 8 columns: an 8 x 8 triangle by
-// group shuffles, then a rectangular update whose 8 column loads per row are independent, so a block
-// costs about one memory latency instead of eight.
+// Triangular solves.  A warp carries kSolvePerWarp = 2 systems (16 lanes each; consecutive systems of
+// a frequency band share N, so the halves run converged): enough warps per SM to hide the latency of
+// the column loads, and at most 15 idle lanes per column step.  Both factors have a unit diagonal
+// (the LU kernel scaled U and kept D^{-1}), so every step is a pure column update whose loads are all
+// issued together through the read-only path.
 constexpr int kSolveWarps = 4;
-constexpr int kSolveGroup = 8;
+constexpr int kSolveGroup = 16;
 constexpr int kSolvePerWarp = 32 / kSolveGroup;
-constexpr int kSB = 8;   // sweep block
 
 __global__ void __launch_bounds__(32 * kSolveWarps) k_solve(DevJob J, int m) {
   extern __shared__ double2 shs[];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int sub = lane / kSolveGroup, gl = lane % kSolveGroup;
-  const unsigned gmask = 0xffu << (sub * kSolveGroup);
+  const unsigned gmask = 0xffffu << (sub * kSolveGroup);
   const int sidx = (blockIdx.x * kSolveWarps + wid) * kSolvePerWarp + sub;
   if (sidx >= J.nsys) return;   // whole groups leave together
   const SysDesc s = J.sys[sidx];
@@ -401,73 +400,25 @@ __global__ void __launch_bounds__(32 * kSolveWarps) k_solve(DevJob J, int m) {
     }
   }
   __syncwarp(gmask);
-  // forward sweep with unit lower L
-  for (int k0 = 0; k0 < N; k0 += kSB) {
-    const int w = min(kSB, N - k0);
-    double2 Lr[kSB];
-#pragma unroll
-    for (int c = 0; c < kSB; ++c)
-      Lr[c] = (c < gl && gl < w) ? __ldg(&A[(long long)(k0 + c) * N + k0 + gl]) : make_double2(0.0, 0.0);
+  for (int k = 0; k < N - 1; ++k) {
+    const double2* __restrict__ Lc = A + (long long)k * N;
     for (int q = 0; q < Q; ++q) {
       double2* bq = b + q * N;
-      double2 x = gl < w ? bq[k0 + gl] : make_double2(0.0, 0.0);
-      double2 xs[kSB];
-#pragma unroll
-      for (int c = 0; c < kSB; ++c) {
-        const double2 xc = make_double2(__shfl_sync(gmask, x.x, c, kSolveGroup), __shfl_sync(gmask, x.y, c, kSolveGroup));
-        xs[c] = xc;
-        if (c + 1 < w && gl > c) x = cfms(Lr[c], xc, x);
-      }
-      if (gl < w) bq[k0 + gl] = x;
-#pragma unroll
-      for (int c = 0; c < kSB; ++c)
-        xs[c] = make_double2(__shfl_sync(gmask, x.x, c, kSolveGroup), __shfl_sync(gmask, x.y, c, kSolveGroup));
-      if (w == kSB) {
-#pragma unroll 2
-        for (int i = k0 + kSB + gl; i < N; i += kSolveGroup) {
-          double2 acc = bq[i];
-#pragma unroll
-          for (int c = 0; c < kSB; ++c) acc = cfms(__ldg(&A[(long long)(k0 + c) * N + i]), xs[c], acc);
-          bq[i] = acc;
-        }
-      }
+      const double2 xk = bq[k];
+#pragma unroll 4
+      for (int i = k + 1 + gl; i < N; i += kSolveGroup) bq[i] = cfms(__ldg(&Lc[i]), xk, bq[i]);
     }
     __syncwarp(gmask);
   }
   for (int e = gl; e < Q * N; e += kSolveGroup) b[e] = cmul(b[e], __ldg(&dinv[e % N]));
   __syncwarp(gmask);
-  // backward sweep with unit upper U'
-  for (int k1 = N; k1 > 0; k1 -= kSB) {
-    const int k0 = max(0, k1 - kSB), w = k1 - k0;
-    double2 Ur[kSB];
-#pragma unroll
-    for (int c = 0; c < kSB; ++c)
-      Ur[c] = (c > gl && c < w) ? __ldg(&A[(long long)(k0 + c) * N + k0 + gl]) : make_double2(0.0, 0.0);
+  for (int k = N - 1; k >= 1; --k) {
+    const double2* __restrict__ Uc = A + (long long)k * N;
     for (int q = 0; q < Q; ++q) {
       double2* bq = b + q * N;
-      double2 x = gl < w ? bq[k0 + gl] : make_double2(0.0, 0.0);
-#pragma unroll
-      for (int c = kSB - 1; c >= 1; --c) {
-        if (c < w) {
-          const double2 xc = make_double2(__shfl_sync(gmask, x.x, c, kSolveGroup), __shfl_sync(gmask, x.y, c, kSolveGroup));
-          if (gl < c) x = cfms(Ur[c], xc, x);
-        }
-      }
-      if (gl < w) bq[k0 + gl] = x;
-      double2 xs[kSB];
-#pragma unroll
-      for (int c = 0; c < kSB; ++c)
-        xs[c] = make_double2(__shfl_sync(gmask, x.x, c, kSolveGroup), __shfl_sync(gmask, x.y, c, kSolveGroup));
-      // a partial block (w < 8) is always the top one (k0 = 0): no rows above it
-      if (w == kSB) {
-#pragma unroll 2
-        for (int i = gl; i < k0; i += kSolveGroup) {
-          double2 acc = bq[i];
-#pragma unroll
-          for (int c = 0; c < kSB; ++c) acc = cfms(__ldg(&A[(long long)(k0 + c) * N + i]), xs[c], acc);
-          bq[i] = acc;
-        }
-      }
+      const double2 xk = bq[k];
+#pragma unroll 4
+      for (int i = gl; i < k; i += kSolveGroup) bq[i] = cfms(__ldg(&Uc[i]), xk, bq[i]);
     }
     __syncwarp(gmask);
   }
@@ -573,10 +524,10 @@ __global__ void __launch_bounds__(kAsmThreads) k_cross_assemble(DevJob J) {
     const double hR = J.h * R;
     const double inv_u = 1.0 / hR;
     const double ampw = sqrt(kTwoOverPi * inv_u) * (0.25 * w);
-    const double lhr = log(0.5 * hR) + kEulerGamma;     // ln(z/2) + gamma - ln l
+    const int lsw = max(task.l0, (int)ceil(kBesselLarge * inv_u));   // first l with z >= 20
+    const double lhr = lsw > task.l0 ? log(0.5 * hR) + kEulerGamma : 0.0;   // ln(z/2) + gamma - ln l
     double su, cu;
     sincos(hR, &su, &cu);
-    const int lsw = max(task.l0, (int)ceil(kBesselLarge * inv_u));   // first l with z >= 20
     const double zmin = (lsw * J.h) * R;
     const int kmax = zmin >= 100.0 ? 4 : (zmin >= 50.0 ? 5 : (zmin >= 30.0 ? 7 : 9));
     double cx = 0.0, sx = 0.0;
