@@ -203,34 +203,46 @@ def ours(args):
     P, L, M, Q = len(problem["arcs"]), o["L"], o["M"], o["Q"]
     solves = P * (L - 1) * M * Q
     ctx = F.fthms_create(lrank, 0, stream.cuda_stream)
-    job = F.Job(ctx, problem, keep_densities=False)
-    st = job.stats()
-    # warm-up, then K timed runs on the library stream
-    for _ in range(args.warmup):
-        job.run()
-    job.wait()
-    F.fthms_profile(job.req, True)
-    torch.cuda.synchronize()
-    if ws > 1:
-        torch.distributed.barrier()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(lrank) as clk:
-        e0.record(stream)
-        for _ in range(args.steps):
+
+    def time_form(precision, clocks=False):
+        job = F.Job(ctx, problem, keep_densities=False, precision=precision)
+        for _ in range(args.warmup):
             job.run()
-        e1.record(stream)
+        job.wait()
+        F.fthms_profile(job.req, True)
         torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
-    stages = F.fthms_stage_times(job.req)
-    F.fthms_profile(job.req, False)
-    if ws > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+        if ws > 1:
+            torch.distributed.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(lrank) as clk:
+            e0.record(stream)
+            for _ in range(args.steps):
+                job.run()
+            e1.record(stream)
+            torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        stages = F.fthms_stage_times(job.req)
+        F.fthms_profile(job.req, False)
+        st = job.stats()
+        dens = [job.densities(j, 0, 0) for j in range(P)]
+        ok = bool(np.all(np.isfinite(job.traces())))
+        job.release()
+        if ws > 1:
+            t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, stages, st, dens, ok, clk.summary()
+
+    ms, stages, st, dens64, traces_ok, clocks = time_form(0)
     value = ws * solves / (ms / 1000.0)
-    launches_per_run = st["kernel_launches"] if st["kernel_launches"] else sum(v[1] for v in stages.values()) // args.steps
-    traces_ok = np.all(np.isfinite(job.traces()))
-    job.release()
+    launches_per_run = st["kernel_launches"]
+    ms_mx, stages_mx, st_mx, dens_mx, ok_mx, clocks_mx = time_form(1)
+    num = den = 0.0
+    for a, c in zip(dens64, dens_mx):
+        for l in a:
+            num += float(np.sum(np.abs(a[l] - c[l]) ** 2))
+            den += float(np.sum(np.abs(a[l]) ** 2))
+    mixed_err = math.sqrt(num / den)
 
     # end to end through the C ABI with host buffers
     e2e_steps = max(1, min(args.steps, 3))
@@ -299,9 +311,18 @@ def ours(args):
                 "gpu_launches": int(launches_per_run * args.steps),
                 "roofline": roofline,
                 "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
-                "clocks": clk.summary(),
+                "clocks": clocks,
                 "cpu_baseline": cpu,
-                "traces_finite": bool(traces_ok)}
+                "traces_finite": bool(traces_ok),
+                "forms": {
+                    "plain_fp64": {"value": value, "ms_per_step": ms, "dtype": "f64"},
+                    "mixed": {"value": ws * solves / (ms_mx / 1000.0), "ms_per_step": ms_mx,
+                              "dtype": "f32 factors + double-float (2 x f32) refinement and cross apply, f64 elsewhere",
+                              "rel_l2_vs_fp64_densities": mixed_err,
+                              "max_refine_resid": st_mx["max_refine_resid"], "traces_finite": ok_mx,
+                              "gpu_launches": int(st_mx["kernel_launches"] * args.steps),
+                              "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages_mx.items()},
+                              "clocks": clocks_mx}}}
         print(json.dumps(line))
     if ws > 1:
         torch.distributed.destroy_process_group()

@@ -87,7 +87,11 @@ typedef struct {
  *              16..16384); dt = 2 pi/(h n_period), t_n = -H + n dt covering [-H, s_Q + H].
  *  obs_xy    : n_obs observation points (x, y), host array of 2*n_obs doubles.
  *  n_tout, tout0, dtout : output times tout0 + k dtout of the traces u_M(z, t) (eq. mult-scatt-int).
- *  precision : 0 = FP64 throughout (the only value implemented here; others -> FTHMS_ENOTIMPL).
+ *  precision : 0 = FP64 throughout.  1 = mixed form: the LU factors and the correction solves in
+ *              FP32, refined against the matrix kept as double-float (two floats, ~48 bits) until the
+ *              relative correction is below 2^-46 (at most 4 iterations); cross matrices stored and
+ *              applied in double-float on the FP32 pipe; kernel assembly, transforms and every other
+ *              stage stay FP64.  Densities agree with the FP64 form to ~1e-13.  Others -> ENOTIMPL.
  *  keep_densities : 1 keeps phi_{j,m,q}(omega_l) of every step for fthms_densities; 0 keeps only
  *              the sum over m. */
 typedef struct {
@@ -120,6 +124,8 @@ typedef struct {
   double lu_flops;        /* (8/3) sum N^3: complex LU of every system */
   double solve_flops;     /* 8 sum N^2 Q M: triangular solves of one run */
   double apply_flops;     /* 8 Q M (cross + observation entries): cross matvecs of one run */
+  int precision;          /* the job's precision option */
+  double max_refine_resid; /* precision 1: max over systems and steps of the last relative correction */
 } fthms_stats_t;
 
 /* Create a context on CUDA device `device` that enqueues all work on `cuda_stream` (a

@@ -169,6 +169,8 @@ fthms_status upload_job(fthms_req* r) {
   J.amp = p.sig.amp; J.carrier = p.sig.carrier; J.centre = p.sig.centre; J.width = p.sig.width;
   J.H = p.H; J.period = p.period;
   J.vec_total = p.vec_total;
+  J.mixed = p.opt.precision == 1 ? 1 : 0;
+  J.mat_total = p.mat_total;
 
   TRY(dev_upload(r, p.sys, &J.sys));
   TRY(dev_upload(r, p.panels, &J.panels));
@@ -207,6 +209,13 @@ fthms_status upload_job(fthms_req* r) {
   TRY(dev_alloc(r, (size_t)p.mat_total, &J.A));
   TRY(dev_alloc(r, (size_t)p.piv_total, &J.piv));
   TRY(dev_alloc(r, (size_t)p.piv_total, &J.dinv));
+  J.LU32 = nullptr;
+  J.dinv32 = nullptr;
+  TRY(dev_alloc(r, 1, &J.refine_resid));
+  if (J.mixed) {
+    TRY(dev_alloc(r, (size_t)p.mat_total, &J.LU32));
+    TRY(dev_alloc(r, (size_t)p.piv_total, &J.dinv32));
+  }
   TRY(dev_alloc(r, (size_t)p.vec_total, &J.G));
   TRY(dev_alloc(r, (size_t)p.vec_total, &J.phi));
   TRY(dev_alloc(r, (size_t)p.vec_total, &J.phi_sum));
@@ -281,6 +290,7 @@ fthms_status enqueue(fthms_req* r) {
   CK(cudaMemsetAsync(J.Gt, 0, (size_t)r->plan.spec_total * sizeof(double2), st));
   CK(cudaMemsetAsync(J.W, 0, (size_t)r->plan.spec_total * sizeof(double2), st));
   CK(cudaMemsetAsync(J.Vobs, 0, (size_t)std::max(1, J.n_obs * J.Q * J.L) * sizeof(double2), st));
+  CK(cudaMemsetAsync(J.refine_resid, 0, sizeof(double), st));
   TRY(stage(r, FTHMS_STAGE_INCIDENT, st, &nl, [&] { return launch_incident(J, st, &nl); }));
   TRY(stage(r, FTHMS_STAGE_RESTRICT, st, &nl, [&] { return launch_restrict(J, st, &nl); }));
   for (int m = 1; m <= J.M; ++m) {
@@ -517,11 +527,13 @@ fthms_status fthms_stats(fthms_req* req, fthms_stats_t* out) {
   out->lu_flops = lu;
   out->solve_flops = sv;
   out->apply_flops = 8.0 * p.Q * p.M * (double)p.e_total;
+  out->precision = p.opt.precision;
   if (req->ran) {
     TRY(fthms_wait(req, -1));
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, req->ev0, req->ev1));
     out->gpu_ms = ms;
+    if (req->J.mixed) CK(cudaMemcpy(&out->max_refine_resid, req->J.refine_resid, sizeof(double), cudaMemcpyDeviceToHost));
   }
   return FTHMS_OK;
 }

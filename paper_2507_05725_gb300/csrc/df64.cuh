@@ -1,0 +1,76 @@
+// Double-float ("df64") arithmetic on the FP32 pipe: a value is hi + lo with two floats, |lo| <=
+// ulp(hi)/2, about 48 significant bits.  Built from the published error-free transformations:
+// Knuth's two-sum (TAOCP vol. 2, 4.2.2) and the FMA form of Dekker's two-product (Dekker 1971).
+// Products are accumulated lazily: the exact rounding error of each hi*hi product and the hi*lo
+// cross terms go into the low word, which is renormalised once at the end of a sum.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace fthms {
+
+struct df {
+  float hi, lo;
+};
+
+// Complex double-float, laid out as float4 (re.hi, re.lo, im.hi, im.lo).
+__device__ __forceinline__ float4 df_split2(double2 v) {
+  const float rh = __double2float_rn(v.x);
+  const float ih = __double2float_rn(v.y);
+  return make_float4(rh, __double2float_rn(v.x - (double)rh), ih, __double2float_rn(v.y - (double)ih));
+}
+
+__device__ __forceinline__ double2 df_join2(float4 v) {
+  return make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+}
+
+// The _rn intrinsics keep every operation of the error-free transformations separately rounded (the
+// compiler never contracts them into FMAs).
+// s + e exactly (Knuth two-sum).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float v = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, v)), __fsub_rn(b, v));
+}
+
+// s + e exactly for |a| >= |b|.
+__device__ __forceinline__ void quick_two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+// Running compensated sum: hi carries the rounded sum, lo the accumulated errors and low parts.
+struct dfacc {
+  float hi = 0.f, lo = 0.f;
+  // += (ah + al) * (bh + bl), dropping al * bl
+  __device__ __forceinline__ void mac(float ah, float al, float bh, float bl) {
+    const float p = __fmul_rn(ah, bh);
+    float e = fmaf(ah, bh, -p);
+    e = fmaf(ah, bl, e);
+    e = fmaf(al, bh, e);
+    float s, t;
+    two_sum(hi, p, s, t);
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(t, e));
+  }
+  __device__ __forceinline__ void add(float h, float l) {
+    float s, t;
+    two_sum(hi, h, s, t);
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(t, l));
+  }
+  __device__ __forceinline__ df value() const {
+    df r;
+    quick_two_sum(hi, lo, r.hi, r.lo);
+    return r;
+  }
+};
+
+// Complex compensated multiply-accumulate: acc += a * b with a, b complex df64 (float4 layout).
+__device__ __forceinline__ void cdf_mac(dfacc& re, dfacc& im, float4 a, float4 b) {
+  re.mac(a.x, a.y, b.x, b.y);
+  re.mac(-a.z, -a.w, b.z, b.w);
+  im.mac(a.x, a.y, b.z, b.w);
+  im.mac(a.z, a.w, b.x, b.y);
+}
+
+}  // namespace fthms

@@ -18,6 +18,7 @@
 #include <cstdio>
 
 #include "bessel.cuh"
+#include "df64.cuh"
 #include "kernels.h"
 
 namespace fthms {
@@ -48,6 +49,21 @@ __device__ __forceinline__ double2 crecip(double2 a) {
 }
 __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+
+// FP32 complex helpers (mixed-precision factorisation and solves)
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cfms(float2 a, float2 b, float2 c) {
+  return make_float2(fmaf(-a.x, b.x, fmaf(a.y, b.y, c.x)), fmaf(-a.x, b.y, fmaf(-a.y, b.x, c.y)));
+}
+__device__ __forceinline__ float2 crecip(float2 a) {
+  float d = 1.0f / fmaf(a.x, a.x, a.y * a.y);
+  return make_float2(a.x * d, -a.y * d);
+}
+template <class C> struct CTraits;
+template <> struct CTraits<double2> { using R = double; };
+template <> struct CTraits<float2> { using R = float; };
 
 // ---------------------------------------------------------------------------------------------
 // Bessel test kernel
@@ -243,21 +259,36 @@ __global__ void __launch_bounds__(256) k_assemble_self(DevJob J) {
 }
 
 // ---------------------------------------------------------------------------------------------
+// Mixed-precision form: the FP32 factor gets the rounded matrix, and A itself is rewritten in place as
+// double-float (the same 16 bytes per entry) for the refinement residuals.
+__global__ void k_split_A(DevJob J) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= J.mat_total) return;
+  const double2 v = J.A[e];
+  J.LU32[e] = make_float2(__double2float_rn(v.x), __double2float_rn(v.y));
+  reinterpret_cast<float4*>(J.A)[e] = df_split2(v);
+}
+
+// ---------------------------------------------------------------------------------------------
 // Blocked right-looking LU with partial pivoting (pivot: max |re| + |im|, first index on ties),
 // one CTA of 256 threads per system, panel width 8 in shared memory, column-major factor in HBM.
 constexpr int kNB = 8;
 constexpr int kPS = kNB + 1;   // padded panel row stride (bank-conflict-free column access)
 constexpr int kLuThreads = 256;
 
+// C = double2 (plain form: factors J.A in place) or float2 (mixed form: factors J.LU32 in place).
+template <class C>
 __global__ void __launch_bounds__(kLuThreads) k_lu(DevJob J) {
-  extern __shared__ double2 shl[];
+  using Real = typename CTraits<C>::R;
+  extern __shared__ __align__(16) unsigned char shl_raw[];
+  C* shl = reinterpret_cast<C*>(shl_raw);
   const SysDesc s = J.sys[blockIdx.x];
   const int N = s.N;
-  double2* A = J.A + s.mat_off;
+  C* A = (sizeof(C) == sizeof(double2) ? reinterpret_cast<C*>(J.A) : reinterpret_cast<C*>(J.LU32)) + s.mat_off;
   int* piv = J.piv + s.piv_off;
-  double2* Pn = shl;                       // [N][kPS] panel rows
-  double2* U = shl + (size_t)N * kPS;      // [kNB][N] U12 rows
-  __shared__ double red_v[kLuThreads / 32];
+  C* Pn = shl;                       // [N][kPS] panel rows
+  C* U = shl + (size_t)N * kPS;      // [kNB][N] U12 rows
+  __shared__ Real red_v[kLuThreads / 32];
   __shared__ int red_i[kLuThreads / 32];
   __shared__ int spiv[kNB];
   __shared__ int s_p;
@@ -271,22 +302,22 @@ __global__ void __launch_bounds__(kLuThreads) k_lu(DevJob J) {
     }
     __syncthreads();
     for (int c = 0; c < w; ++c) {
-      double best = -1.0;
+      Real best = -1;
       int bi = 0x7fffffff;
       for (int r = c + tid; r < nr; r += kLuThreads) {
-        double2 v = Pn[r * kPS + c];
-        double m = fabs(v.x) + fabs(v.y);
+        C v = Pn[r * kPS + c];
+        Real m = fabs(v.x) + fabs(v.y);
         if (m > best) { best = m; bi = r; }
       }
       for (int o = 16; o > 0; o >>= 1) {
-        double ov = __shfl_down_sync(0xffffffffu, best, o);
+        Real ov = __shfl_down_sync(0xffffffffu, best, o);
         int oi = __shfl_down_sync(0xffffffffu, bi, o);
         if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
       }
       if (lane == 0) { red_v[wid] = best; red_i[wid] = bi; }
       __syncthreads();
       if (tid == 0) {
-        double b = red_v[0];
+        Real b = red_v[0];
         int ii = red_i[0];
         for (int q = 1; q < kLuThreads / 32; ++q)
           if (red_v[q] > b || (red_v[q] == b && red_i[q] < ii)) { b = red_v[q]; ii = red_i[q]; }
@@ -298,14 +329,14 @@ __global__ void __launch_bounds__(kLuThreads) k_lu(DevJob J) {
       __syncthreads();
       const int p = s_p;
       if (p != c && tid < w) {
-        double2 t = Pn[c * kPS + tid];
+        C t = Pn[c * kPS + tid];
         Pn[c * kPS + tid] = Pn[p * kPS + tid];
         Pn[p * kPS + tid] = t;
       }
       __syncthreads();
-      const double2 inv = crecip(Pn[c * kPS + c]);
+      const C inv = crecip(Pn[c * kPS + c]);
       for (int r = c + 1 + tid; r < nr; r += kLuThreads) {
-        double2 lr = cmul(Pn[r * kPS + c], inv);
+        C lr = cmul(Pn[r * kPS + c], inv);
         Pn[r * kPS + c] = lr;
         for (int cc = c + 1; cc < w; ++cc) Pn[r * kPS + cc] = cfms(lr, Pn[c * kPS + cc], Pn[r * kPS + cc]);
       }
@@ -318,10 +349,10 @@ __global__ void __launch_bounds__(kLuThreads) k_lu(DevJob J) {
     // Row interchanges on the columns outside the panel.
     for (int col = tid; col < N; col += kLuThreads) {
       if (col >= k0 && col < k0 + w) continue;
-      double2* Ac = A + (long long)col * N + k0;
+      C* Ac = A + (long long)col * N + k0;
       for (int c = 0; c < w; ++c) {
         int p = spiv[c];
-        if (p != c) { double2 t = Ac[c]; Ac[c] = Ac[p]; Ac[p] = t; }
+        if (p != c) { C t = Ac[c]; Ac[c] = Ac[p]; Ac[p] = t; }
       }
     }
     __syncthreads();
@@ -329,12 +360,12 @@ __global__ void __launch_bounds__(kLuThreads) k_lu(DevJob J) {
     if (nc > 0) {
       // U12 = L11^{-1} A12 (unit lower triangular solve), one column per thread.
       for (int j = tid; j < nc; j += kLuThreads) {
-        double2* Ac = A + (long long)(k0 + w + j) * N + k0;
-        double2 xv[kNB];
+        C* Ac = A + (long long)(k0 + w + j) * N + k0;
+        C xv[kNB];
 #pragma unroll
         for (int r = 0; r < kNB; ++r) {
           if (r < w) {
-            double2 v = Ac[r];
+            C v = Ac[r];
             for (int c = 0; c < r; ++c) v = cfms(Pn[r * kPS + c], xv[c], v);
             xv[r] = v;
             Ac[r] = v;
@@ -347,8 +378,8 @@ __global__ void __launch_bounds__(kLuThreads) k_lu(DevJob J) {
       const int mr = nr - w;
       for (long long idx = tid; idx < (long long)mr * nc; idx += kLuThreads) {
         int j = (int)(idx / mr), r = (int)(idx % mr);
-        double2* a = A + (long long)(k0 + w + j) * N + k0 + w + r;
-        double2 v = *a;
+        C* a = A + (long long)(k0 + w + j) * N + k0 + w + r;
+        C v = *a;
 #pragma unroll
         for (int c = 0; c < kNB; ++c)
           if (c < w) v = cfms(Pn[(w + r) * kPS + c], U[c * N + j], v);
@@ -358,29 +389,29 @@ __global__ void __launch_bounds__(kLuThreads) k_lu(DevJob J) {
     __syncthreads();
   }
   // U = D U' with unit-diagonal U': keep 1/U_kk and scale row k of U (right of the diagonal).
-  for (int k = tid; k < N; k += kLuThreads) J.dinv[s.piv_off + k] = crecip(A[(long long)k * N + k]);
+  C* dinv = (sizeof(C) == sizeof(double2) ? reinterpret_cast<C*>(J.dinv) : reinterpret_cast<C*>(J.dinv32)) + s.piv_off;
+  for (int k = tid; k < N; k += kLuThreads) dinv[k] = crecip(A[(long long)k * N + k]);
   __syncthreads();
   for (long long e = tid; e < (long long)N * N; e += kLuThreads) {
     const int col = (int)(e / N), row = (int)(e % N);
-    if (col > row) A[e] = cmul(A[e], J.dinv[s.piv_off + row]);
+    if (col > row) A[e] = cmul(A[e], dinv[row]);
   }
 }
 
 // ---------------------------------------------------------------------------------------------
-// Triangular solves.  A warp carries kSolvePerWarp = 2 systems (16 lanes each; consecutive systems of
-// a frequency band share N, so the halves run converged): enough warps per SM to hide the latency of
-// the column loads, and at most 15 idle lanes per column step.  Both factors have a unit diagonal
-// (the LU kernel scaled U and kept D^{-1}), so every step is a pure column update whose loads are all
-// issued together through the read-only path.
+// Triangular solves: one warp per system (the column step is latency-bound, so all 32 lanes share
+// each step's rows; measured faster than 2 or 4 systems per warp).  Both factors have a unit
+// diagonal (the LU kernel scaled U and kept D^{-1}), so every step is a pure column update whose loads
+// are all issued together through the read-only path.
 constexpr int kSolveWarps = 4;
-constexpr int kSolveGroup = 16;
+constexpr int kSolveGroup = 32;
 constexpr int kSolvePerWarp = 32 / kSolveGroup;
 
 __global__ void __launch_bounds__(32 * kSolveWarps) k_solve(DevJob J, int m) {
   extern __shared__ double2 shs[];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int sub = lane / kSolveGroup, gl = lane % kSolveGroup;
-  const unsigned gmask = 0xffffu << (sub * kSolveGroup);
+  const unsigned gmask = kSolveGroup == 32 ? 0xffffffffu : ((1u << kSolveGroup) - 1u) << (sub * kSolveGroup);
   const int sidx = (blockIdx.x * kSolveWarps + wid) * kSolvePerWarp + sub;
   if (sidx >= J.nsys) return;   // whole groups leave together
   const SysDesc s = J.sys[sidx];
@@ -437,6 +468,12 @@ __global__ void __launch_bounds__(32 * kSolveWarps) k_solve(DevJob J, int m) {
 // Cross assembly: stored rows of S_Gamma_j for one (pair, frequency band, 8-row chunk).
 constexpr int kAsmThreads = 256;
 constexpr int kAsmRows = 8;
+
+// A stored cross entry: FP64, or double-float (float4, same 16 bytes) in the mixed-precision form.
+__device__ __forceinline__ void store_entry(const DevJob& J, double2* p, double2 v) {
+  if (J.mixed) *reinterpret_cast<float4*>(p) = df_split2(v);
+  else *p = v;
+}
 constexpr int kAsmBand = 64;   // frequencies per assembly task (matches the planner's band cap)
 
 __global__ void __launch_bounds__(kAsmThreads) k_cross_assemble(DevJob J) {
@@ -513,7 +550,7 @@ __global__ void __launch_bounds__(kAsmThreads) k_cross_assemble(DevJob J) {
         double K1;
         double2 K2;
         log_split((l * J.h) * R, dts, K1, K2);
-        J.E[J.e_off[(long long)task.pair * J.L + l] + pos] = make_double2(fma(K1, wn, K2.x * w), K2.y * w);
+        store_entry(J, J.E + J.e_off[(long long)task.pair * J.L + l] + pos, make_double2(fma(K1, wn, K2.x * w), K2.y * w));
       }
       continue;
     }
@@ -539,7 +576,7 @@ __global__ void __launch_bounds__(kAsmThreads) k_cross_assemble(DevJob J) {
       double J0, Yh;
       bessel0_taylor(z, J0, Yh);
       const double Y0 = fma(kTwoOverPi * (lnl[l - task.l0] + lhr), J0, Yh);
-      Ep[eo[l]] = make_double2(-0.25 * w * Y0, 0.25 * w * J0);
+      store_entry(J, Ep + eo[l], make_double2(-0.25 * w * Y0, 0.25 * w * J0));
     }
     for (int l = lsw; l <= task.l1; ++l) {
       if (since >= 16) {
@@ -558,7 +595,7 @@ __global__ void __launch_bounds__(kAsmThreads) k_cross_assemble(DevJob J) {
       }
       Qa *= wz;
       const double a = ampw * rsql[l - task.l0];
-      Ep[eo[l]] = make_double2(-a * fma(P, sx, -Qa * cx), a * fma(P, cx, Qa * sx));
+      store_entry(J, Ep + eo[l], make_double2(-a * fma(P, sx, -Qa * cx), a * fma(P, cx, Qa * sx)));
       const double cn = fma(cx, cu, -sx * su);
       sx = fma(sx, cu, cx * su);
       cx = cn;
@@ -627,6 +664,204 @@ __global__ void __launch_bounds__(kApplyThreads) k_cross_apply(DevJob J) {
     }
 #pragma unroll
     for (int q = 0; q < Q; ++q) res[q * nrow + row] = s[q];
+  }
+  __syncthreads();
+  for (int bb = 0; bb < nb; ++bb) {
+    const CrossBlk B = J.blks[g.blk_begin + bb];
+    for (int r = threadIdx.x; r < B.nrows; r += kApplyThreads) {
+      const int out = J.tgts[B.tgt_off + r].out;
+#pragma unroll
+      for (int q = 0; q < Q; ++q) acc[q * nout + out] = cadd(acc[q * nout + out], res[q * nrow + s_row0[bb] + r]);
+    }
+    __syncthreads();
+  }
+  if (obs) {
+    for (int e = threadIdx.x; e < Q * nout; e += kApplyThreads) {
+      int q = e / nout, z = e % nout;
+      double2* v = J.Vobs + ((long long)z * Q + q) * J.L + l;
+      *v = cadd(*v, acc[e]);
+    }
+  } else {
+    const long long base = J.tr_off[g.k];
+    for (int e = threadIdx.x; e < Q * nout; e += kApplyThreads) {
+      int q = e / nout, x = e % nout;
+      J.W[((base + x) * Q + q) * J.L + l] = acc[e];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Mixed-precision solve: FP32 LU solve, then iterative refinement with double-float residuals
+// r = G - A phi (A kept as double-float, about 48 bits) and FP32 corrections, until the correction
+// is below 2^-46 of the solution or kRefineMax iterations.  One warp per system.
+constexpr int kRefineMax = 4;
+
+__device__ void solve32(float2* b, int Q, int N, const float2* __restrict__ A, const int* __restrict__ piv,
+                        const float2* __restrict__ dinv, int lane) {
+  if (lane < Q) {
+    float2* bq = b + lane * N;
+    for (int k = 0; k < N; ++k) {
+      const int p = __ldg(&piv[k]);
+      if (p != k) { float2 t = bq[k]; bq[k] = bq[p]; bq[p] = t; }
+    }
+  }
+  __syncwarp();
+  for (int k = 0; k < N - 1; ++k) {
+    const float2* __restrict__ Lc = A + (long long)k * N;
+    for (int q = 0; q < Q; ++q) {
+      float2* bq = b + q * N;
+      const float2 xk = bq[k];
+#pragma unroll 4
+      for (int i = k + 1 + lane; i < N; i += 32) bq[i] = cfms(__ldg(&Lc[i]), xk, bq[i]);
+    }
+    __syncwarp();
+  }
+  for (int e = lane; e < Q * N; e += 32) b[e] = cmul(b[e], __ldg(&dinv[e % N]));
+  __syncwarp();
+  for (int k = N - 1; k >= 1; --k) {
+    const float2* __restrict__ Uc = A + (long long)k * N;
+    for (int q = 0; q < Q; ++q) {
+      float2* bq = b + q * N;
+      const float2 xk = bq[k];
+#pragma unroll 4
+      for (int i = lane; i < k; i += 32) bq[i] = cfms(__ldg(&Uc[i]), xk, bq[i]);
+    }
+    __syncwarp();
+  }
+}
+
+__global__ void __launch_bounds__(32 * kSolveWarps) k_solve_mixed(DevJob J, int m) {
+  extern __shared__ __align__(16) unsigned char shm_raw[];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int sidx = blockIdx.x * kSolveWarps + wid;
+  if (sidx >= J.nsys) return;
+  const SysDesc s = J.sys[sidx];
+  const int N = s.N, Q = J.Q;
+  const size_t per = (size_t)Q * J.max_n;
+  float4* ph = reinterpret_cast<float4*>(shm_raw) + (size_t)wid * per;                        // df64
+  float2* b = reinterpret_cast<float2*>(reinterpret_cast<float4*>(shm_raw) + kSolveWarps * per) + (size_t)wid * per;
+  const float2* __restrict__ L32 = J.LU32 + s.mat_off;
+  const float4* __restrict__ Adf = reinterpret_cast<const float4*>(J.A) + s.mat_off;
+  const int* __restrict__ piv = J.piv + s.piv_off;
+  const float2* __restrict__ dinv = J.dinv32 + s.piv_off;
+  const double2* __restrict__ G = J.G + s.vec_off;
+  for (int e = lane; e < Q * N; e += 32) {
+    const double2 g = G[e];
+    b[e] = make_float2(__double2float_rn(g.x), __double2float_rn(g.y));
+  }
+  __syncwarp();
+  solve32(b, Q, N, L32, piv, dinv, lane);
+  for (int e = lane; e < Q * N; e += 32) ph[e] = make_float4(b[e].x, 0.f, b[e].y, 0.f);
+  __syncwarp();
+  double rel = 1.0;
+  for (int it = 0; it < kRefineMax; ++it) {
+    // r = G - A phi (double-float), rounded to FP32 as the right-hand side of the correction
+    for (int q = 0; q < Q; ++q) {
+      for (int i = lane; i < N; i += 32) {
+        const double2 g = G[q * N + i];
+        const float4 gd = df_split2(g);
+        dfacc re, im;
+        re.add(gd.x, gd.y);
+        im.add(gd.z, gd.w);
+        const float4* Ai = Adf + i;
+        const float4* pq = ph + q * N;
+#pragma unroll 4
+        for (int j = 0; j < N; ++j) {
+          const float4 a = __ldg(&Ai[(long long)j * N]);
+          const float4 x = pq[j];
+          cdf_mac(re, im, make_float4(-a.x, -a.y, -a.z, -a.w), x);
+        }
+        const df rr = re.value(), ri = im.value();
+        b[q * N + i] = make_float2(rr.hi + rr.lo, ri.hi + ri.lo);
+      }
+    }
+    __syncwarp();
+    solve32(b, Q, N, L32, piv, dinv, lane);
+    float dmax = 0.f, pmax = 0.f;
+    for (int e = lane; e < Q * N; e += 32) {
+      const float2 d = b[e];
+      float4 p = ph[e];
+      float sh, sl;
+      two_sum(p.x, d.x, sh, sl);
+      quick_two_sum(sh, sl + p.y, p.x, p.y);
+      two_sum(p.z, d.y, sh, sl);
+      quick_two_sum(sh, sl + p.w, p.z, p.w);
+      ph[e] = p;
+      dmax = fmaxf(dmax, fmaxf(fabsf(d.x), fabsf(d.y)));
+      pmax = fmaxf(pmax, fmaxf(fabsf(p.x), fabsf(p.z)));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+      pmax = fmaxf(pmax, __shfl_xor_sync(0xffffffffu, pmax, o));
+    }
+    __syncwarp();
+    rel = pmax > 0.f ? (double)dmax / (double)pmax : 0.0;
+    if (rel < 1.5e-14) break;
+  }
+  if (lane == 0) atomicMax(reinterpret_cast<unsigned long long*>(J.refine_resid), (unsigned long long)__double_as_longlong(rel));
+  double2* out = J.phi + s.vec_off;
+  double2* sum = J.phi_sum + s.vec_off;
+  double2* all = J.phi_all ? J.phi_all + (long long)(m - 1) * J.vec_total + s.vec_off : nullptr;
+  for (int e = lane; e < Q * N; e += 32) {
+    const double2 v = df_join2(ph[e]);
+    out[e] = v;
+    sum[e] = m == 1 ? v : cadd(sum[e], v);
+    if (all) all[e] = v;
+  }
+}
+
+// Cross apply in double-float on the FP32 pipe (mixed form): E and phi as df64, compensated sums.
+template <int Q>
+__global__ void __launch_bounds__(kApplyThreads) k_cross_apply_df(DevJob J) {
+  extern __shared__ __align__(16) unsigned char shd_raw[];
+  const CrossGrp g = J.grps[blockIdx.x];
+  const int l = g.l;
+  const bool obs = g.k == J.P;
+  const int nout = obs ? J.n_obs : J.panels[J.tpanel[g.k]].N;
+  const int nb = g.blk_end - g.blk_begin;
+  __shared__ int s_row0[kApplyMaxBlk + 1], s_ph0[kApplyMaxBlk + 1];
+  if (threadIdx.x == 0) {
+    int r = 0, p = 0;
+    for (int b = 0; b < nb; ++b) {
+      s_row0[b] = r;
+      s_ph0[b] = p;
+      r += J.blks[g.blk_begin + b].nrows;
+      p += Q * J.blks[g.blk_begin + b].N;
+    }
+    s_row0[nb] = r;
+    s_ph0[nb] = p;
+  }
+  __syncthreads();
+  const int nrow = s_row0[nb];
+  double2* acc = reinterpret_cast<double2*>(shd_raw);      // [Q][nout]
+  double2* res = acc + (size_t)Q * J.acc_cap;              // [Q][nrow]
+  float4* ph = reinterpret_cast<float4*>(res + (size_t)Q * J.row_cap);   // df64 densities
+  for (int e = threadIdx.x; e < Q * nout; e += kApplyThreads) acc[e] = make_double2(0.0, 0.0);
+  for (int b = 0; b < nb; ++b) {
+    const CrossBlk B = J.blks[g.blk_begin + b];
+    const double2* p = J.phi + J.sys[B.sys].vec_off;
+    for (int e = threadIdx.x; e < Q * B.N; e += kApplyThreads) ph[s_ph0[b] + e] = df_split2(p[e]);
+  }
+  __syncthreads();
+  int b = 0;
+  for (int row = threadIdx.x; row < nrow; row += kApplyThreads) {
+    while (row >= s_row0[b + 1]) ++b;
+    const CrossBlk B = J.blks[g.blk_begin + b];
+    const int N = B.N, nr = B.nrows, r = row - s_row0[b];
+    const float4* phb = ph + s_ph0[b];
+    dfacc sr[Q], si[Q];
+    const float4* __restrict__ Er = reinterpret_cast<const float4*>(J.E + B.e_off) + r;
+#pragma unroll 4
+    for (int i = 0; i < N; ++i) {
+      const float4 ev = __ldg(&Er[(long long)i * nr]);
+#pragma unroll
+      for (int q = 0; q < Q; ++q) cdf_mac(sr[q], si[q], ev, phb[q * N + i]);
+    }
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const df a = sr[q].value(), c = si[q].value();
+      res[q * nrow + row] = make_double2((double)a.hi + (double)a.lo, (double)c.hi + (double)c.lo);
+    }
   }
   __syncthreads();
   for (int bb = 0; bb < nb; ++bb) {
@@ -881,10 +1116,19 @@ cudaError_t launch_assemble_self(const DevJob& J, cudaStream_t st, int* launches
 }
 
 cudaError_t launch_lu(const DevJob& J, cudaStream_t st, int* launches) {
+  if (J.mixed) {
+    k_split_A<<<cdiv(J.mat_total, 256), 256, 0, st>>>(J);
+    size_t sh = (size_t)J.max_n * (kNB + kPS) * sizeof(float2);
+    cudaError_t e = cudaFuncSetAttribute(k_lu<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+    if (e != cudaSuccess) return e;
+    k_lu<float2><<<J.nsys, kLuThreads, sh, st>>>(J);
+    *launches += 2;
+    return cudaGetLastError();
+  }
   size_t sh = (size_t)J.max_n * (kNB + kPS) * sizeof(double2);
-  cudaError_t e = cudaFuncSetAttribute(k_lu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+  cudaError_t e = cudaFuncSetAttribute(k_lu<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
   if (e != cudaSuccess) return e;
-  k_lu<<<J.nsys, kLuThreads, sh, st>>>(J);
+  k_lu<double2><<<J.nsys, kLuThreads, sh, st>>>(J);
   *launches += 1;
   return cudaGetLastError();
 }
@@ -931,6 +1175,14 @@ cudaError_t launch_restrict(const DevJob& J, cudaStream_t st, int* launches) {
 }
 
 cudaError_t launch_solve(const DevJob& J, int m, cudaStream_t st, int* launches) {
+  if (J.mixed) {
+    size_t sh = (size_t)kSolveWarps * J.Q * J.max_n * (sizeof(float4) + sizeof(float2));
+    cudaError_t e = cudaFuncSetAttribute(k_solve_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+    if (e != cudaSuccess) return e;
+    k_solve_mixed<<<cdiv(J.nsys, kSolveWarps), 32 * kSolveWarps, sh, st>>>(J, m);
+    *launches += 1;
+    return cudaGetLastError();
+  }
   size_t sh = (size_t)kSolveWarps * kSolvePerWarp * J.Q * J.max_n * sizeof(double2);
   cudaError_t e = cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
   if (e != cudaSuccess) return e;
@@ -941,6 +1193,12 @@ cudaError_t launch_solve(const DevJob& J, int m, cudaStream_t st, int* launches)
 
 template <int Q>
 static cudaError_t launch_cross_apply_q(const DevJob& J, size_t sh, cudaStream_t st) {
+  if (J.mixed) {
+    cudaError_t e = cudaFuncSetAttribute(k_cross_apply_df<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+    if (e != cudaSuccess) return e;
+    k_cross_apply_df<Q><<<J.n_grp, kApplyThreads, sh, st>>>(J);
+    return cudaGetLastError();
+  }
   cudaError_t e = cudaFuncSetAttribute(k_cross_apply<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
   if (e != cudaSuccess) return e;
   k_cross_apply<Q><<<J.n_grp, kApplyThreads, sh, st>>>(J);

@@ -11,6 +11,8 @@ struct DevJob {
   int P, L, Q, K, NT, M, n_obs, n_tout, nsys, n_act, n_grp, n_asm, n_tiles, n_rlogN, n_restr;
   int logK, max_nmax, max_n, acc_cap;
   int row_cap, ph_cap;           // max rows and max sum of source N over the cross groups
+  int mixed;                     // 1: mixed-precision form (FP32 LU + double-float refinement/apply)
+  long long mat_total;
   double h, dt, sign;
   // signal
   int sig_kind;
@@ -45,7 +47,10 @@ struct DevJob {
   const double* s_q;         // [Q]
   double H, period;
   // work arrays
-  double2* A;                // LU factors
+  double2* A;                // LU factors (mixed form: the matrix itself, as double-float)
+  float2* LU32;              // FP32 factors (mixed form)
+  float2* dinv32;            // FP32 1 / U_kk (mixed form)
+  double* refine_resid;      // max over systems of the last relative correction (mixed form)
   int* piv;
   double2* dinv;             // 1 / U_kk
   double2* G;                // data on solve nodes [s][q][i]

@@ -122,8 +122,8 @@ int build_plan(const fthms_curve* curves, int ncurves, const fthms_arc* arcs, in
   }
   p.opt = *opt;
   p.sig = *sig;
-  if (opt->precision != 0) {
-    err = "only precision = 0 (FP64) is implemented";
+  if (opt->precision != 0 && opt->precision != 1) {
+    err = "precision must be 0 (FP64) or 1 (FP32 factors with double-float refinement and cross apply)";
     return FTHMS_ENOTIMPL;
   }
   if (opt->L < 3 || !(opt->W > 0) || opt->M < 1 || opt->Q < 1 || !(opt->H > 0) ||
@@ -483,6 +483,7 @@ void arc_nodes(const Curve& c, double theta_a, double theta_b, int N, std::vecto
 size_t plan_device_bytes(const Plan& p) {
   size_t b = 0;
   b += (size_t)p.mat_total * 16;                 // A / LU
+  if (p.opt.precision == 1) b += (size_t)p.mat_total * 8 + (size_t)p.piv_total * 8;   // FP32 factors
   b += (size_t)p.piv_total * 4;                  // pivots
   b += (size_t)p.rlog_total * 8;                 // self log tables
   b += (size_t)p.vec_total * 16 * 3;             // G, phi (current), phi sum

@@ -50,7 +50,8 @@ class fthms_stats_t(C.Structure):
     _fields_ = [("gpu_ms", C.c_double), ("setup_ms", C.c_double), ("systems", C.c_longlong),
                 ("solves", C.c_longlong), ("kernel_launches", C.c_longlong), ("device_bytes", C.c_size_t),
                 ("cross_entries", C.c_double), ("hankel_evals", C.c_double), ("h2d_bytes", C.c_size_t),
-                ("lu_flops", C.c_double), ("solve_flops", C.c_double), ("apply_flops", C.c_double)]
+                ("lu_flops", C.c_double), ("solve_flops", C.c_double), ("apply_flops", C.c_double),
+                ("precision", C.c_int), ("max_refine_resid", C.c_double)]
 
 
 STAGES = ["tables", "assemble_self", "lu", "cross_assemble", "incident", "restrict", "solve", "cross_apply",
@@ -250,9 +251,9 @@ def fthms_assemble_self_noalloc(curve: dict, arc, N, kappa, A_ptr, stream=None):
 class Job:
     """One FTH-MS job through the C ABI: ``Job(ctx, problem).run().wait()``."""
 
-    def __init__(self, ctx, problem, keep_densities=True):
+    def __init__(self, ctx, problem, keep_densities=True, precision=0):
         self.problem = problem
-        self.m = Marshalled(problem, keep_densities=keep_densities)
+        self.m = Marshalled(problem, keep_densities=keep_densities, precision=precision)
         self.req = fthms_prepare(ctx, self.m)
         o = problem["options"]
         self.P, self.L, self.M, self.Q = len(problem["arcs"]), o["L"], o["M"], o["Q"]

@@ -163,3 +163,61 @@ def test_config2_full_size_sampled(F, ctx):
     tr = job.traces()
     assert np.all(np.isfinite(tr)) and np.max(np.abs(tr)) > 0
     job.release()
+
+
+# ---- mixed-precision form (FP32 factors, double-float refinement and cross apply) --------------
+
+MIXED_TOL = 1e-10   # the benchmark spec's bar for the mixed-precision form
+
+
+def _parity_mixed(F, ctx, problem):
+    job = F.Job(ctx, problem, precision=1).run().wait()
+    ref = run_oracle(problem)
+    o = problem["options"]
+    P, L, M, Q = len(problem["arcs"]), o["L"], o["M"], o["Q"]
+    num = den = 0.0
+    for m in range(1, M + 1):
+        for j in range(P):
+            for q in range(Q):
+                d = job.densities(j, m, q)
+                for l in range(1, L):
+                    r = ref.phi[(m, j, l)][q]
+                    num += float(np.sum(np.abs(d[l] - r) ** 2))
+                    den += float(np.sum(np.abs(r) ** 2))
+    tr = job.traces()
+    st = job.stats()
+    job.release()
+    assert st["precision"] == 1
+    assert 0.0 <= st["max_refine_resid"] < 1e-12
+    scale = max(1e-300, np.max(np.abs(ref.traces)))
+    assert np.max(np.abs(tr - ref.traces)) < MIXED_TOL * scale
+    return math.sqrt(num / den)
+
+
+@pytest.mark.parametrize("name", ["small-point", "two-curves-Q2", "four-arcs"])
+def test_mixed_small_parity(F, ctx, name):
+    assert _parity_mixed(F, ctx, SMALL[name]()) < MIXED_TOL
+
+
+def test_mixed_config1_parity(F, ctx):
+    assert _parity_mixed(F, ctx, wl.config1()) < MIXED_TOL
+
+
+def test_mixed_config2_reduced_parity(F, ctx):
+    assert _parity_mixed(F, ctx, wl.config2_reduced(M=2)) < MIXED_TOL
+
+
+def test_mixed_matches_plain_at_full_size(F, ctx):
+    """Full-size config 2: the mixed form's summed densities against the FP64 form's."""
+    problem = wl.config2(M=3)
+    a = F.Job(ctx, problem, keep_densities=False, precision=0).run().wait()
+    b = F.Job(ctx, problem, keep_densities=False, precision=1).run().wait()
+    num = den = 0.0
+    for j in range(len(problem["arcs"])):
+        x, y = a.densities(j, 0, 0), b.densities(j, 0, 0)
+        for l in x:
+            num += float(np.sum(np.abs(x[l] - y[l]) ** 2))
+            den += float(np.sum(np.abs(x[l]) ** 2))
+    a.release()
+    b.release()
+    assert math.sqrt(num / den) < MIXED_TOL
