@@ -65,6 +65,22 @@ def measured_traffic_per_unit():
     return out if h == kernels_hash() else {}
 
 
+def max_over_ranks(ms, device="cuda"):
+    """Largest per-rank time (replicas run concurrently; the job-wide step ends with the slowest)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world_size, solves_per_rank, ms):
+    """Whole-job throughput: the solves of every rank's replica over the slowest rank's time."""
+    return world_size * solves_per_rank / (ms / 1000.0)
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -227,14 +243,11 @@ def ours(args):
         dens = [job.densities(j, 0, 0) for j in range(P)]
         ok = bool(np.all(np.isfinite(job.traces())))
         job.release()
-        if ws > 1:
-            t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ms)
         return ms, stages, st, dens, ok, clk.summary()
 
     ms, stages, st, dens64, traces_ok, clocks = time_form(0)
-    value = ws * solves / (ms / 1000.0)
+    value = job_value(ws, solves, ms)
     launches_per_run = st["kernel_launches"]
     ms_mx, stages_mx, st_mx, dens_mx, ok_mx, clocks_mx = time_form(1)
     num = den = 0.0
@@ -260,11 +273,7 @@ def ours(args):
         h2d = F.fthms_stats(req)["h2d_bytes"]
         F.fthms_release(req)
     torch.cuda.synchronize()
-    e2e_ms = 1000.0 * (time.perf_counter() - t0) / e2e_steps
-    if ws > 1:
-        t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(1000.0 * (time.perf_counter() - t0) / e2e_steps)
     F.fthms_destroy(ctx)
 
     # roofline of the dominant stage (every stage is FP64-pipe bound)
@@ -272,8 +281,9 @@ def ours(args):
     dom_ms, dom_launch = stages[dom]
     per_launch_ms = dom_ms / max(1, dom_launch)
     self_entries = st["hankel_evals"] - st["cross_entries"]
+    sum_n2 = st["solve_flops"] / (8.0 * Q * M)          # sum over systems of N^2
     units = {"cross_apply": st["cross_entries"] * Q, "cross_assemble": st["cross_entries"],
-             "assemble_self": self_entries, "lu": st["systems"], "solve": st["systems"] * Q}
+             "assemble_self": self_entries, "lu": sum_n2, "solve": sum_n2 * Q}
     flops_per_launch = {"cross_apply": st["apply_flops"] / M, "lu": st["lu_flops"], "solve": st["solve_flops"] / M,
                         "cross_assemble": FLOPS_PER_KERNEL_ENTRY * st["cross_entries"],
                         "assemble_self": FLOPS_PER_KERNEL_ENTRY * self_entries}
@@ -306,7 +316,7 @@ def ours(args):
                            "form": "plain FP64", "l2": "working set > L2 (cross matrices "
                            f"{st['cross_entries'] * 16 / 1e9:.1f} GB, factors {st['lu_flops'] > 0})",
                            "parallelism": f"replicas x{ws}"},
-                "e2e": {"value": ws * solves / (e2e_ms / 1000.0), "unit": "solves/s", "ms_per_step": e2e_ms,
+                "e2e": {"value": job_value(ws, solves, e2e_ms), "unit": "solves/s", "ms_per_step": e2e_ms,
                         "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
                 "gpu_launches": int(launches_per_run * args.steps),
                 "roofline": roofline,
@@ -316,7 +326,7 @@ def ours(args):
                 "traces_finite": bool(traces_ok),
                 "forms": {
                     "plain_fp64": {"value": value, "ms_per_step": ms, "dtype": "f64"},
-                    "mixed": {"value": ws * solves / (ms_mx / 1000.0), "ms_per_step": ms_mx,
+                    "mixed": {"value": job_value(ws, solves, ms_mx), "ms_per_step": ms_mx,
                               "dtype": "f32 factors + double-float (2 x f32) refinement and cross apply, f64 elsewhere",
                               "rel_l2_vs_fp64_densities": mixed_err,
                               "max_refine_resid": st_mx["max_refine_resid"], "traces_finite": ok_mx,

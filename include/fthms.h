@@ -87,11 +87,11 @@ typedef struct {
  *              16..16384); dt = 2 pi/(h n_period), t_n = -H + n dt covering [-H, s_Q + H].
  *  obs_xy    : n_obs observation points (x, y), host array of 2*n_obs doubles.
  *  n_tout, tout0, dtout : output times tout0 + k dtout of the traces u_M(z, t) (eq. mult-scatt-int).
- *  precision : 0 = FP64 throughout.  1 = mixed form: the LU factors and the correction solves in
- *              FP32, refined against the matrix kept as double-float (two floats, ~48 bits) until the
- *              relative correction is below 2^-46 (at most 4 iterations); cross matrices stored and
+ *  precision : 0 = FP64 throughout.  1 = mixed form: FP32 LU factors and an FP32 inverse per system,
+ *              solutions refined against the matrix kept as double-float (two floats, ~48 bits) until
+ *              the relative correction is below 1e-12 (at most 3 steps); cross matrices stored and
  *              applied in double-float on the FP32 pipe; kernel assembly, transforms and every other
- *              stage stay FP64.  Densities agree with the FP64 form to ~1e-13.  Others -> ENOTIMPL.
+ *              stage stay FP64.  Densities agree with the FP64 form to ~1e-12.  Others -> ENOTIMPL.
  *  keep_densities : 1 keeps phi_{j,m,q}(omega_l) of every step for fthms_densities; 0 keeps only
  *              the sum over m. */
 typedef struct {

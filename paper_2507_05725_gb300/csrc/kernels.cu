@@ -691,42 +691,62 @@ __global__ void __launch_bounds__(kApplyThreads) k_cross_apply(DevJob J) {
 }
 
 // ---------------------------------------------------------------------------------------------
-// Mixed-precision solve: FP32 LU solve, then iterative refinement with double-float residuals
-// r = G - A phi (A kept as double-float, about 48 bits) and FP32 corrections, until the correction
-// is below 2^-46 of the solution or kRefineMax iterations.  One warp per system.
-constexpr int kRefineMax = 4;
+// Mixed-precision solve.  Once per system the FP32 factors give an FP32 inverse X = U'^{-1} D^{-1}
+// L^{-1} P; every solve is then a parallel GEMV: phi = X G, and refinement steps r = G - A phi with A
+// in double-float (about 48 bits) followed by phi += X r, until the relative correction is below
+// 1e-12 or kRefineMax steps.  One warp per system.
+constexpr int kRefineMax = 3;
+constexpr int kInvThreads = 256;
 
-__device__ void solve32(float2* b, int Q, int N, const float2* __restrict__ A, const int* __restrict__ piv,
-                        const float2* __restrict__ dinv, int lane) {
-  if (lane < Q) {
-    float2* bq = b + lane * N;
+__global__ void __launch_bounds__(kInvThreads) k_inv32(DevJob J) {
+  extern __shared__ __align__(16) unsigned char shi_raw[];
+  const SysDesc s = J.sys[blockIdx.x];
+  const int N = s.N;
+  const float2* __restrict__ F = J.LU32 + s.mat_off;
+  float2* X = J.AINV32 + s.mat_off;
+  const int* piv = J.piv + s.piv_off;
+  const float2* dinv = J.dinv32 + s.piv_off;
+  int* perm = reinterpret_cast<int*>(shi_raw);                       // N
+  float2* rowk = reinterpret_cast<float2*>(shi_raw + ((N * sizeof(int) + 15) & ~15));   // N
+  float2* colk = rowk + N;                                           // N
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < N; ++i) perm[i] = i;
     for (int k = 0; k < N; ++k) {
-      const int p = __ldg(&piv[k]);
-      if (p != k) { float2 t = bq[k]; bq[k] = bq[p]; bq[p] = t; }
+      const int p = piv[k];
+      if (p != k) { int t = perm[k]; perm[k] = perm[p]; perm[p] = t; }
     }
   }
-  __syncwarp();
-  for (int k = 0; k < N - 1; ++k) {
-    const float2* __restrict__ Lc = A + (long long)k * N;
-    for (int q = 0; q < Q; ++q) {
-      float2* bq = b + q * N;
-      const float2 xk = bq[k];
-#pragma unroll 4
-      for (int i = k + 1 + lane; i < N; i += 32) bq[i] = cfms(__ldg(&Lc[i]), xk, bq[i]);
-    }
-    __syncwarp();
+  __syncthreads();
+  // X = P I: (P b)_i = b_{perm[i]}, so X[i][c] = [perm[i] == c]
+  for (long long e = threadIdx.x; e < (long long)N * N; e += kInvThreads) {
+    const int c = (int)(e / N), i = (int)(e % N);
+    X[e] = make_float2(perm[i] == c ? 1.f : 0.f, 0.f);
   }
-  for (int e = lane; e < Q * N; e += 32) b[e] = cmul(b[e], __ldg(&dinv[e % N]));
-  __syncwarp();
-  for (int k = N - 1; k >= 1; --k) {
-    const float2* __restrict__ Uc = A + (long long)k * N;
-    for (int q = 0; q < Q; ++q) {
-      float2* bq = b + q * N;
-      const float2 xk = bq[k];
-#pragma unroll 4
-      for (int i = lane; i < k; i += 32) bq[i] = cfms(__ldg(&Uc[i]), xk, bq[i]);
+  __syncthreads();
+  for (int k = 0; k < N - 1; ++k) {           // X <- L^{-1} X (unit lower)
+    for (int c = threadIdx.x; c < N; c += kInvThreads) rowk[c] = X[(long long)c * N + k];
+    for (int i = threadIdx.x; i < N; i += kInvThreads) colk[i] = F[(long long)k * N + i];
+    __syncthreads();
+    const int m = N - k - 1;
+    for (long long e = threadIdx.x; e < (long long)m * N; e += kInvThreads) {
+      const int c = (int)(e / m), i = k + 1 + (int)(e % m);
+      float2* x = X + (long long)c * N + i;
+      *x = cfms(colk[i], rowk[c], *x);
     }
-    __syncwarp();
+    __syncthreads();
+  }
+  for (long long e = threadIdx.x; e < (long long)N * N; e += kInvThreads) X[e] = cmul(X[e], dinv[e % N]);
+  __syncthreads();
+  for (int k = N - 1; k >= 1; --k) {          // X <- U'^{-1} X (unit upper)
+    for (int c = threadIdx.x; c < N; c += kInvThreads) rowk[c] = X[(long long)c * N + k];
+    for (int i = threadIdx.x; i < k; i += kInvThreads) colk[i] = F[(long long)k * N + i];
+    __syncthreads();
+    for (long long e = threadIdx.x; e < (long long)k * N; e += kInvThreads) {
+      const int c = (int)(e / k), i = (int)(e % k);
+      float2* x = X + (long long)c * N + i;
+      *x = cfms(colk[i], rowk[c], *x);
+    }
+    __syncthreads();
   }
 }
 
@@ -740,26 +760,30 @@ __global__ void __launch_bounds__(32 * kSolveWarps) k_solve_mixed(DevJob J, int 
   const size_t per = (size_t)Q * J.max_n;
   float4* ph = reinterpret_cast<float4*>(shm_raw) + (size_t)wid * per;                        // df64
   float2* b = reinterpret_cast<float2*>(reinterpret_cast<float4*>(shm_raw) + kSolveWarps * per) + (size_t)wid * per;
-  const float2* __restrict__ L32 = J.LU32 + s.mat_off;
+  const float2* __restrict__ X = J.AINV32 + s.mat_off;
   const float4* __restrict__ Adf = reinterpret_cast<const float4*>(J.A) + s.mat_off;
-  const int* __restrict__ piv = J.piv + s.piv_off;
-  const float2* __restrict__ dinv = J.dinv32 + s.piv_off;
   const double2* __restrict__ G = J.G + s.vec_off;
   for (int e = lane; e < Q * N; e += 32) {
     const double2 g = G[e];
     b[e] = make_float2(__double2float_rn(g.x), __double2float_rn(g.y));
   }
   __syncwarp();
-  solve32(b, Q, N, L32, piv, dinv, lane);
-  for (int e = lane; e < Q * N; e += 32) ph[e] = make_float4(b[e].x, 0.f, b[e].y, 0.f);
+  // phi = X b (FP32 GEMV, rows over lanes)
+  for (int q = 0; q < Q; ++q)
+    for (int i = lane; i < N; i += 32) {
+      float2 acc = make_float2(0.f, 0.f);
+      const float2* xr = X + i;
+#pragma unroll 4
+      for (int c = 0; c < N; ++c) acc = cfms(make_float2(-xr[(long long)c * N].x, -xr[(long long)c * N].y), b[q * N + c], acc);
+      ph[q * N + i] = make_float4(acc.x, 0.f, acc.y, 0.f);
+    }
   __syncwarp();
   double rel = 1.0;
   for (int it = 0; it < kRefineMax; ++it) {
-    // r = G - A phi (double-float), rounded to FP32 as the right-hand side of the correction
+    // r = G - A phi in double-float, rounded to FP32
     for (int q = 0; q < Q; ++q) {
       for (int i = lane; i < N; i += 32) {
-        const double2 g = G[q * N + i];
-        const float4 gd = df_split2(g);
+        const float4 gd = df_split2(G[q * N + i]);
         dfacc re, im;
         re.add(gd.x, gd.y);
         im.add(gd.z, gd.w);
@@ -768,35 +792,41 @@ __global__ void __launch_bounds__(32 * kSolveWarps) k_solve_mixed(DevJob J, int 
 #pragma unroll 4
         for (int j = 0; j < N; ++j) {
           const float4 a = __ldg(&Ai[(long long)j * N]);
-          const float4 x = pq[j];
-          cdf_mac(re, im, make_float4(-a.x, -a.y, -a.z, -a.w), x);
+          cdf_mac(re, im, make_float4(-a.x, -a.y, -a.z, -a.w), pq[j]);
         }
         const df rr = re.value(), ri = im.value();
         b[q * N + i] = make_float2(rr.hi + rr.lo, ri.hi + ri.lo);
       }
     }
     __syncwarp();
-    solve32(b, Q, N, L32, piv, dinv, lane);
+    // phi += X r
     float dmax = 0.f, pmax = 0.f;
-    for (int e = lane; e < Q * N; e += 32) {
-      const float2 d = b[e];
-      float4 p = ph[e];
-      float sh, sl;
-      two_sum(p.x, d.x, sh, sl);
-      quick_two_sum(sh, sl + p.y, p.x, p.y);
-      two_sum(p.z, d.y, sh, sl);
-      quick_two_sum(sh, sl + p.w, p.z, p.w);
-      ph[e] = p;
-      dmax = fmaxf(dmax, fmaxf(fabsf(d.x), fabsf(d.y)));
-      pmax = fmaxf(pmax, fmaxf(fabsf(p.x), fabsf(p.z)));
-    }
+    for (int q = 0; q < Q; ++q)
+      for (int i = lane; i < N; i += 32) {
+        float2 d = make_float2(0.f, 0.f);
+        const float2* xr = X + i;
+#pragma unroll 4
+        for (int c = 0; c < N; ++c) {
+          const float2 xv = __ldg(&xr[(long long)c * N]);
+          d = cfms(make_float2(-xv.x, -xv.y), b[q * N + c], d);
+        }
+        float4 p = ph[q * N + i];
+        float sh, sl;
+        two_sum(p.x, d.x, sh, sl);
+        quick_two_sum(sh, sl + p.y, p.x, p.y);
+        two_sum(p.z, d.y, sh, sl);
+        quick_two_sum(sh, sl + p.w, p.z, p.w);
+        ph[q * N + i] = p;
+        dmax = fmaxf(dmax, fmaxf(fabsf(d.x), fabsf(d.y)));
+        pmax = fmaxf(pmax, fmaxf(fabsf(p.x), fabsf(p.z)));
+      }
     for (int o = 16; o > 0; o >>= 1) {
       dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
       pmax = fmaxf(pmax, __shfl_xor_sync(0xffffffffu, pmax, o));
     }
     __syncwarp();
     rel = pmax > 0.f ? (double)dmax / (double)pmax : 0.0;
-    if (rel < 1.5e-14) break;
+    if (rel < 1e-12) break;
   }
   if (lane == 0) atomicMax(reinterpret_cast<unsigned long long*>(J.refine_resid), (unsigned long long)__double_as_longlong(rel));
   double2* out = J.phi + s.vec_off;
@@ -1122,7 +1152,9 @@ cudaError_t launch_lu(const DevJob& J, cudaStream_t st, int* launches) {
     cudaError_t e = cudaFuncSetAttribute(k_lu<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
     if (e != cudaSuccess) return e;
     k_lu<float2><<<J.nsys, kLuThreads, sh, st>>>(J);
-    *launches += 2;
+    size_t shi = (((size_t)J.max_n * sizeof(int) + 15) & ~(size_t)15) + 2 * (size_t)J.max_n * sizeof(float2);
+    k_inv32<<<J.nsys, kInvThreads, shi, st>>>(J);
+    *launches += 3;
     return cudaGetLastError();
   }
   size_t sh = (size_t)J.max_n * (kNB + kPS) * sizeof(double2);

@@ -188,7 +188,7 @@ def _parity_mixed(F, ctx, problem):
     st = job.stats()
     job.release()
     assert st["precision"] == 1
-    assert 0.0 <= st["max_refine_resid"] < 1e-12
+    assert 0.0 <= st["max_refine_resid"] < MIXED_TOL
     scale = max(1e-300, np.max(np.abs(ref.traces)))
     assert np.max(np.abs(tr - ref.traces)) < MIXED_TOL * scale
     return math.sqrt(num / den)
