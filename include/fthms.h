@@ -206,6 +206,33 @@ fthms_status fthms_release(fthms_req* req);
 /* Message of the last failed call on this thread (never NULL). */
 const char* fthms_last_error(void);
 
+/* ---- request server (continuous batching of jobs) --------------------------------------------
+ * A server owns a context on `device` with an HBM budget and `max_inflight` slots, each with its own
+ * CUDA stream.  Submitted jobs (same inputs as fthms_submit, copied at submit) wait in arrival order;
+ * a worker thread admits the oldest one whenever a slot is free and the budget has room for its
+ * device memory (fthms_prepare's estimate), so jobs that arrive while others run start as soon as
+ * slots and memory free up and their kernels overlap on the device.  Finished jobs stay resident
+ * (factors, densities, traces) until fthms_server_release; a job larger than the whole budget fails
+ * with FTHMS_ENOMEM.  This is the serving form of the benchmark spec; the paper has no counterpart (its
+ * sub-problems are "embarrassingly parallel", Section 3). */
+typedef struct fthms_server fthms_server;
+
+fthms_status fthms_server_create(fthms_server** out, int device, size_t hbm_budget_bytes, int max_inflight);
+fthms_status fthms_server_submit(fthms_server* s, const fthms_curve* curves, int ncurves,
+                                 const fthms_arc* arcs, int narcs, const fthms_signal* signal,
+                                 const fthms_options* options, long long* ticket);
+/* *state: 0 queued, 1 running, 2 done, 3 failed. */
+fthms_status fthms_server_poll(fthms_server* s, long long ticket, int* state);
+/* Block until done (FTHMS_OK), failed (the job's status) or timeout_ms (FTHMS_ETIMEOUT; <0 = none). */
+fthms_status fthms_server_wait(fthms_server* s, long long ticket, int timeout_ms);
+/* Borrow the finished job (valid until fthms_server_release) for fthms_traces / fthms_densities /
+ * fthms_stats; do not release it directly. */
+fthms_status fthms_server_result(fthms_server* s, long long ticket, fthms_req** req);
+/* Host wall-clock milliseconds from submit to admission (queue) and to completion (total). */
+fthms_status fthms_server_latency(fthms_server* s, long long ticket, double* queue_ms, double* total_ms);
+fthms_status fthms_server_release(fthms_server* s, long long ticket);
+fthms_status fthms_server_destroy(fthms_server* s);
+
 /* ---- kernel-level entry points (device buffers, enqueued on `cuda_stream`) -------------------- */
 
 /* Bessel functions of order 0 for z_dev[i] > 0 (the kernel of Section 2.1): J0, Y0 and the

@@ -3,8 +3,11 @@
 #include <cuda_runtime.h>
 
 #include <chrono>
+#include <condition_variable>
 #include <cstdio>
 #include <cstring>
+#include <deque>
+#include <map>
 #include <mutex>
 #include <string>
 #include <thread>
@@ -71,6 +74,7 @@ struct ProfMark {
 
 struct fthms_req {
   fthms_ctx* ctx = nullptr;
+  cudaStream_t stream = nullptr;   // stream of all of this job's work (the context's, or a server slot's)
   Plan plan;
   DevJob J{};
   std::vector<void*> allocs;
@@ -96,10 +100,10 @@ fthms_status dev_upload(fthms_req* r, const std::vector<T>& v, const T** out) {
   if (v.empty()) return FTHMS_OK;
   void* p = nullptr;
   size_t b = v.size() * sizeof(T);
-  CK(cudaMalloc(&p, b));
+  CK(cudaMallocAsync(&p, b, r->stream));
   r->allocs.push_back(p);
   r->bytes += b;
-  CK(cudaMemcpy(p, v.data(), b, cudaMemcpyHostToDevice));
+  CK(cudaMemcpyAsync(p, v.data(), b, cudaMemcpyHostToDevice, r->stream));
   r->h2d += b;
   *out = static_cast<const T*>(p);
   return FTHMS_OK;
@@ -111,7 +115,7 @@ fthms_status dev_alloc(fthms_req* r, size_t count, T** out) {
   if (count == 0) return FTHMS_OK;
   void* p = nullptr;
   size_t b = count * sizeof(T);
-  CK(cudaMalloc(&p, b));
+  CK(cudaMallocAsync(&p, b, r->stream));
   r->allocs.push_back(p);
   r->bytes += b;
   *out = static_cast<T*>(p);
@@ -119,7 +123,7 @@ fthms_status dev_alloc(fthms_req* r, size_t count, T** out) {
 }
 
 void free_req(fthms_req* r) {
-  for (void* p : r->allocs) cudaFree(p);
+  for (void* p : r->allocs) cudaFreeAsync(p, r->stream);
   r->allocs.clear();
   for (cudaEvent_t e : r->ev_pool) cudaEventDestroy(e);
   r->ev_pool.clear();
@@ -281,7 +285,7 @@ fthms_status stage(fthms_req* r, int st_id, cudaStream_t st, int* nl, F&& launch
 
 fthms_status enqueue(fthms_req* r) {
   const DevJob& J = r->J;
-  cudaStream_t st = r->ctx->stream;
+  cudaStream_t st = r->stream;
   int nl = 0;
   TRY(flush_marks(r));
   CK(cudaEventRecord(r->ev0, st));
@@ -344,6 +348,7 @@ fthms_status fthms_prepare(fthms_ctx* ctx, const fthms_curve* curves, int ncurve
   auto t0 = std::chrono::steady_clock::now();
   fthms_req* r = new fthms_req;
   r->ctx = ctx;
+  r->stream = ctx->stream;
   std::string err;
   int st = build_plan(curves, ncurves, arcs, narcs, signal, options, r->plan, err);
   if (st != FTHMS_OK) {
@@ -435,7 +440,10 @@ fthms_status fthms_traces(fthms_req* req, double* out, size_t cap) {
   size_t n = (size_t)req->plan.n_obs * req->plan.n_tout;
   if (cap < n) return fail(FTHMS_EINVAL, "fthms_traces: output buffer too small");
   TRY(fthms_wait(req, -1));
-  if (n) CK(cudaMemcpy(out, req->J.traces, n * sizeof(double), cudaMemcpyDeviceToHost));
+  if (n) {
+    CK(cudaMemcpyAsync(out, req->J.traces, n * sizeof(double), cudaMemcpyDeviceToHost, req->stream));
+    CK(cudaStreamSynchronize(req->stream));
+  }
   return FTHMS_OK;
 }
 
@@ -468,7 +476,8 @@ fthms_status fthms_densities(fthms_req* req, int arc, int m, int q, double* out,
   TRY(fthms_wait(req, -1));
   const Plan& p = req->plan;
   std::vector<double2> h((size_t)(last - first));
-  CK(cudaMemcpy(h.data(), base + first, h.size() * sizeof(double2), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpyAsync(h.data(), base + first, h.size() * sizeof(double2), cudaMemcpyDeviceToHost, req->stream));
+  CK(cudaStreamSynchronize(req->stream));
   size_t o = 0;
   for (int l = 1; l < p.L; ++l) {
     const SysDesc& s = p.sys[(size_t)arc * (p.L - 1) + l - 1];
@@ -494,7 +503,7 @@ fthms_status fthms_densities_dev(fthms_req* req, int arc, int m, int q, double* 
   for (int l = 1; l < p.L; ++l) {
     const SysDesc& s = p.sys[(size_t)arc * (p.L - 1) + l - 1];
     CK(cudaMemcpyAsync(out_dev + o, base + s.vec_off + (long long)q * s.N, (size_t)s.N * sizeof(double2),
-                       cudaMemcpyDeviceToDevice, req->ctx->stream));
+                       cudaMemcpyDeviceToDevice, req->stream));
     o += 2 * (size_t)s.N;
   }
   return FTHMS_OK;
@@ -535,7 +544,10 @@ fthms_status fthms_stats(fthms_req* req, fthms_stats_t* out) {
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, req->ev0, req->ev1));
     out->gpu_ms = ms;
-    if (req->J.mixed) CK(cudaMemcpy(&out->max_refine_resid, req->J.refine_resid, sizeof(double), cudaMemcpyDeviceToHost));
+    if (req->J.mixed) {
+      CK(cudaMemcpyAsync(&out->max_refine_resid, req->J.refine_resid, sizeof(double), cudaMemcpyDeviceToHost, req->stream));
+      CK(cudaStreamSynchronize(req->stream));
+    }
   }
   return FTHMS_OK;
 }
@@ -544,6 +556,7 @@ fthms_status fthms_release(fthms_req* req) {
   if (!req) return fail(FTHMS_EINVAL, "fthms_release: NULL job");
   if (req->ran) cudaEventSynchronize(req->ev1);
   free_req(req);
+  cudaStreamSynchronize(req->stream);   // the stream-ordered frees have run before the budget is returned
   {
     std::lock_guard<std::mutex> lk(req->ctx->mu);
     req->ctx->in_use -= req->plan.device_bytes;
@@ -603,6 +616,7 @@ fthms_status fthms_assemble_self(const fthms_curve* curve, const fthms_arc* arc,
   std::vector<double> t, x, y, sp;
   arc_nodes(c, arc->theta_a, arc->theta_b, N, t, x, y, sp);
   fthms_req tmp;
+  tmp.stream = st;
   DevJob& J = tmp.J;
   std::vector<SysDesc> sys(1);
   // One system in a band of length 1 at frequency index 1 with step h = kappa: the band kernel's
@@ -642,6 +656,298 @@ fthms_status fthms_assemble_self(const fthms_curve* curve, const fthms_arc* arc,
   }
   free_req(&tmp);
   return s;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// Request server: continuous admission of jobs onto per-slot streams under the HBM budget.
+
+namespace {
+
+double now_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+struct ServerReq {
+  long long id = 0;
+  // owned copies of the inputs (the caller may free its buffers after submit)
+  std::vector<std::vector<double>> coef;
+  std::vector<fthms_curve> curves;
+  std::vector<fthms_arc> arcs;
+  fthms_signal sig{};
+  fthms_options opt{};
+  std::vector<double> obs;
+  fthms_req* req = nullptr;
+  int state = 0;            // 0 queued, 1 running, 2 done, 3 failed
+  int slot = -1;
+  fthms_status err = FTHMS_OK;
+  std::string msg;
+  double t_submit = 0, t_start = 0, t_done = 0;
+};
+
+}  // namespace
+
+struct fthms_server {
+  fthms_ctx* ctx = nullptr;
+  int max_inflight = 1;
+  std::vector<cudaStream_t> streams;
+  std::vector<int> slot_used;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<long long> queue;
+  std::map<long long, ServerReq*> reqs;
+  long long next_id = 1;
+  bool stop = false;
+  bool retry = true;          // admission worth retrying (a job finished, was released or arrived)
+  cudaStream_t upload = nullptr;
+  std::thread worker;
+};
+
+namespace {
+
+// One scheduling pass (called with the server lock held): retire finished jobs, then admit queued
+// jobs in arrival order while a slot is free and the context's HBM budget has room.
+void server_pass(fthms_server* s) {
+  for (auto& kv : s->reqs) {
+    ServerReq* q = kv.second;
+    if (q->state != 1) continue;
+    cudaError_t e = cudaEventQuery(q->req->ev1);
+    if (e == cudaErrorNotReady) continue;
+    q->t_done = now_ms();
+    q->state = e == cudaSuccess ? 2 : 3;
+    if (e != cudaSuccess) {
+      q->err = FTHMS_ECUDA;
+      q->msg = cudaGetErrorString(e);
+    }
+    s->slot_used[q->slot] = 0;
+    s->retry = true;
+    s->cv.notify_all();
+  }
+  while (!s->queue.empty() && s->retry) {
+    int slot = -1;
+    for (int i = 0; i < s->max_inflight; ++i)
+      if (!s->slot_used[i]) { slot = i; break; }
+    if (slot < 0) return;
+    ServerReq* q = s->reqs[s->queue.front()];
+    fthms_req* r = nullptr;
+    // plan first: a job that cannot fit even an empty budget fails; one that does not fit now waits
+    fthms_status st = fthms_prepare(s->ctx, q->curves.data(), (int)q->curves.size(), q->arcs.data(),
+                                    (int)q->arcs.size(), &q->sig, &q->opt, &r);
+    if (st == FTHMS_ENOMEM) {
+      bool alone_fits = s->ctx->budget == 0 || s->ctx->in_use == 0;
+      if (!alone_fits) {       // wait until a running or resident job finishes or is released
+        s->retry = false;
+        return;
+      }
+    }
+    s->queue.pop_front();
+    if (st != FTHMS_OK) {
+      q->state = 3;
+      q->err = st;
+      q->msg = g_last_error;
+      q->t_done = now_ms();
+      s->cv.notify_all();
+      continue;
+    }
+    // move the job to the slot's stream: its uploads were issued on the context stream
+    cudaStreamSynchronize(r->stream);
+    r->stream = s->streams[slot];
+    st = fthms_run(r);
+    if (st != FTHMS_OK) {
+      q->state = 3;
+      q->err = st;
+      q->msg = g_last_error;
+      q->t_done = now_ms();
+      fthms_release(r);
+      s->cv.notify_all();
+      continue;
+    }
+    q->req = r;
+    q->slot = slot;
+    q->state = 1;
+    q->t_start = now_ms();
+    s->slot_used[slot] = 1;
+  }
+}
+
+void server_loop(fthms_server* s) {
+  cudaSetDevice(s->ctx->device);
+  std::unique_lock<std::mutex> lk(s->mu);
+  while (!s->stop) {
+    server_pass(s);
+    s->cv.wait_for(lk, std::chrono::microseconds(100));
+  }
+}
+
+ServerReq* find_req(fthms_server* s, long long id) {
+  auto it = s->reqs.find(id);
+  return it == s->reqs.end() ? nullptr : it->second;
+}
+
+}  // namespace
+
+extern "C" {
+
+fthms_status fthms_server_create(fthms_server** out, int device, size_t hbm_budget_bytes, int max_inflight) {
+  if (!out || max_inflight < 1 || max_inflight > 64) return fail(FTHMS_EINVAL, "fthms_server_create: bad arguments");
+  *out = nullptr;
+  fthms_server* s = new fthms_server;
+  fthms_status st = fthms_create(&s->ctx, device, hbm_budget_bytes, nullptr);
+  if (st != FTHMS_OK) {
+    delete s;
+    return st;
+  }
+  s->max_inflight = max_inflight;
+  cudaError_t eu = cudaStreamCreateWithFlags(&s->upload, cudaStreamNonBlocking);
+  if (eu != cudaSuccess) {
+    fthms_destroy(s->ctx);
+    delete s;
+    return cuda_fail(eu, "cudaStreamCreate");
+  }
+  s->ctx->stream = s->upload;     // host-to-device uploads of admitted jobs
+  s->streams.resize(max_inflight);
+  s->slot_used.assign(max_inflight, 0);
+  for (int i = 0; i < max_inflight; ++i) {
+    cudaError_t e = cudaStreamCreateWithFlags(&s->streams[i], cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      for (int k = 0; k < i; ++k) cudaStreamDestroy(s->streams[k]);
+      fthms_destroy(s->ctx);
+      delete s;
+      return cuda_fail(e, "cudaStreamCreate");
+    }
+  }
+  s->worker = std::thread(server_loop, s);
+  *out = s;
+  return FTHMS_OK;
+}
+
+fthms_status fthms_server_submit(fthms_server* s, const fthms_curve* curves, int ncurves, const fthms_arc* arcs,
+                                 int narcs, const fthms_signal* signal, const fthms_options* options,
+                                 long long* ticket) {
+  if (!s || !ticket || !curves || ncurves <= 0 || !arcs || narcs <= 0 || !signal || !options)
+    return fail(FTHMS_EINVAL, "fthms_server_submit: NULL or empty argument");
+  ServerReq* q = new ServerReq;
+  for (int c = 0; c < ncurves; ++c) {
+    if (curves[c].degree < 1) {
+      delete q;
+      return fail(FTHMS_EINVAL, "fthms_server_submit: curve degree < 1");
+    }
+    const int n = curves[c].degree + 1;
+    for (const double* src : {curves[c].ax, curves[c].bx, curves[c].ay, curves[c].by}) {
+      if (!src) {
+        delete q;
+        return fail(FTHMS_EINVAL, "fthms_server_submit: NULL curve coefficients");
+      }
+      q->coef.emplace_back(src, src + n);
+    }
+  }
+  for (int c = 0; c < ncurves; ++c) {
+    fthms_curve cv;
+    cv.degree = curves[c].degree;
+    cv.ax = q->coef[4 * c].data();
+    cv.bx = q->coef[4 * c + 1].data();
+    cv.ay = q->coef[4 * c + 2].data();
+    cv.by = q->coef[4 * c + 3].data();
+    q->curves.push_back(cv);
+  }
+  q->arcs.assign(arcs, arcs + narcs);
+  q->sig = *signal;
+  q->opt = *options;
+  if (options->n_obs > 0 && options->obs_xy) q->obs.assign(options->obs_xy, options->obs_xy + 2 * options->n_obs);
+  q->opt.obs_xy = q->obs.empty() ? nullptr : q->obs.data();
+  q->t_submit = now_ms();
+  std::lock_guard<std::mutex> lk(s->mu);
+  q->id = s->next_id++;
+  s->reqs[q->id] = q;
+  s->queue.push_back(q->id);
+  *ticket = q->id;
+  s->retry = true;
+  s->cv.notify_all();
+  return FTHMS_OK;
+}
+
+fthms_status fthms_server_poll(fthms_server* s, long long ticket, int* state) {
+  if (!s || !state) return fail(FTHMS_EINVAL, "fthms_server_poll: NULL argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  ServerReq* q = find_req(s, ticket);
+  if (!q) return fail(FTHMS_EINVAL, "fthms_server_poll: unknown ticket");
+  *state = q->state;
+  return FTHMS_OK;
+}
+
+fthms_status fthms_server_wait(fthms_server* s, long long ticket, int timeout_ms) {
+  if (!s) return fail(FTHMS_EINVAL, "fthms_server_wait: NULL server");
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    ServerReq* q = find_req(s, ticket);
+    if (!q) return fail(FTHMS_EINVAL, "fthms_server_wait: unknown ticket");
+    if (q->state == 2) return FTHMS_OK;
+    if (q->state == 3) return fail(q->err, "fthms_server_wait: request failed: " + q->msg);
+    if (timeout_ms >= 0 &&
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count() > timeout_ms)
+      return fail(FTHMS_ETIMEOUT, "fthms_server_wait: timed out");
+    s->cv.wait_for(lk, std::chrono::microseconds(200));
+  }
+}
+
+fthms_status fthms_server_result(fthms_server* s, long long ticket, fthms_req** req) {
+  if (!s || !req) return fail(FTHMS_EINVAL, "fthms_server_result: NULL argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  ServerReq* q = find_req(s, ticket);
+  if (!q) return fail(FTHMS_EINVAL, "fthms_server_result: unknown ticket");
+  if (q->state != 2) return fail(q->state == 3 ? q->err : FTHMS_EBUSY, "fthms_server_result: request not done");
+  *req = q->req;
+  return FTHMS_OK;
+}
+
+fthms_status fthms_server_latency(fthms_server* s, long long ticket, double* queue_ms, double* total_ms) {
+  if (!s || !queue_ms || !total_ms) return fail(FTHMS_EINVAL, "fthms_server_latency: NULL argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  ServerReq* q = find_req(s, ticket);
+  if (!q) return fail(FTHMS_EINVAL, "fthms_server_latency: unknown ticket");
+  if (q->state < 2) return fail(FTHMS_EBUSY, "fthms_server_latency: request not finished");
+  *queue_ms = (q->state == 2 ? q->t_start : q->t_done) - q->t_submit;
+  *total_ms = q->t_done - q->t_submit;
+  return FTHMS_OK;
+}
+
+fthms_status fthms_server_release(fthms_server* s, long long ticket) {
+  if (!s) return fail(FTHMS_EINVAL, "fthms_server_release: NULL server");
+  std::lock_guard<std::mutex> lk(s->mu);
+  ServerReq* q = find_req(s, ticket);
+  if (!q) return fail(FTHMS_EINVAL, "fthms_server_release: unknown ticket");
+  if (q->state < 2) return fail(FTHMS_EBUSY, "fthms_server_release: request still queued or running");
+  if (q->req) fthms_release(q->req);
+  s->reqs.erase(ticket);
+  delete q;
+  s->retry = true;
+  s->cv.notify_all();
+  return FTHMS_OK;
+}
+
+fthms_status fthms_server_destroy(fthms_server* s) {
+  if (!s) return fail(FTHMS_EINVAL, "fthms_server_destroy: NULL server");
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+    s->cv.notify_all();
+  }
+  s->worker.join();
+  for (auto& kv : s->reqs) {
+    ServerReq* q = kv.second;
+    if (q->req) {
+      cudaEventSynchronize(q->req->ev1);
+      fthms_release(q->req);
+    }
+    delete q;
+  }
+  for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
+  cudaStreamDestroy(s->upload);
+  fthms_destroy(s->ctx);
+  delete s;
+  return FTHMS_OK;
 }
 
 }  // extern "C"

@@ -86,6 +86,15 @@ def _load():
         "fthms_assemble_self": (st, [C.POINTER(fthms_curve), C.POINTER(fthms_arc), C.c_int, C.c_double, vp, vp]),
         "fthms_assemble_self_noalloc": (st, [C.POINTER(fthms_curve), C.POINTER(fthms_arc), C.c_int, C.c_double,
                                              vp, vp]),
+        "fthms_server_create": (st, [pp, C.c_int, C.c_size_t, C.c_int]),
+        "fthms_server_submit": (st, [vp, C.POINTER(fthms_curve), C.c_int, C.POINTER(fthms_arc), C.c_int,
+                                     C.POINTER(fthms_signal), C.POINTER(fthms_options), C.POINTER(C.c_longlong)]),
+        "fthms_server_poll": (st, [vp, C.c_longlong, C.POINTER(C.c_int)]),
+        "fthms_server_wait": (st, [vp, C.c_longlong, C.c_int]),
+        "fthms_server_result": (st, [vp, C.c_longlong, pp]),
+        "fthms_server_latency": (st, [vp, C.c_longlong, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+        "fthms_server_release": (st, [vp, C.c_longlong]),
+        "fthms_server_destroy": (st, [vp]),
         "fthms_profile": (st, [vp, C.c_int]),
         "fthms_stage_times": (st, [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
     }
@@ -101,7 +110,9 @@ LIB = _load()
 EXPORTED = ["fthms_create", "fthms_destroy", "fthms_prepare", "fthms_run", "fthms_submit", "fthms_poll",
             "fthms_wait", "fthms_traces", "fthms_densities", "fthms_densities_dev", "fthms_node_counts",
             "fthms_stats", "fthms_release", "fthms_last_error", "fthms_bessel0", "fthms_assemble_self",
-            "fthms_profile", "fthms_stage_times", "fthms_assemble_self_noalloc"]
+            "fthms_profile", "fthms_stage_times", "fthms_assemble_self_noalloc", "fthms_server_create",
+            "fthms_server_submit", "fthms_server_poll", "fthms_server_wait", "fthms_server_result",
+            "fthms_server_latency", "fthms_server_release", "fthms_server_destroy"]
 
 
 def _check(status):
@@ -298,3 +309,89 @@ class Job:
             self.release()
         except Exception:
             pass
+
+
+def fthms_server_create(device=0, hbm_budget_bytes=0, max_inflight=4):
+    s = C.c_void_p()
+    _check(LIB.fthms_server_create(C.byref(s), int(device), int(hbm_budget_bytes), int(max_inflight)))
+    return s
+
+
+def fthms_server_submit(server, m: Marshalled):
+    t = C.c_longlong()
+    _check(LIB.fthms_server_submit(server, m.curves, m.ncurves, m.arcs, m.narcs, C.byref(m.signal),
+                                   C.byref(m.options), C.byref(t)))
+    return t.value
+
+
+def fthms_server_poll(server, ticket):
+    st = C.c_int()
+    _check(LIB.fthms_server_poll(server, C.c_longlong(ticket), C.byref(st)))
+    return st.value
+
+
+def fthms_server_wait(server, ticket, timeout_ms=-1):
+    _check(LIB.fthms_server_wait(server, C.c_longlong(ticket), int(timeout_ms)))
+
+
+def fthms_server_result(server, ticket):
+    r = C.c_void_p()
+    _check(LIB.fthms_server_result(server, C.c_longlong(ticket), C.byref(r)))
+    return r
+
+
+def fthms_server_latency(server, ticket):
+    q, t = C.c_double(), C.c_double()
+    _check(LIB.fthms_server_latency(server, C.c_longlong(ticket), C.byref(q), C.byref(t)))
+    return q.value, t.value
+
+
+def fthms_server_release(server, ticket):
+    _check(LIB.fthms_server_release(server, C.c_longlong(ticket)))
+
+
+def fthms_server_destroy(server):
+    _check(LIB.fthms_server_destroy(server))
+
+
+class Server:
+    """Request server over the C ABI: submit problem dicts, wait, read results by ticket."""
+
+    def __init__(self, device=0, hbm_budget_bytes=0, max_inflight=4):
+        self.s = fthms_server_create(device, hbm_budget_bytes, max_inflight)
+        self.meta = {}
+
+    def submit(self, problem, precision=0, keep_densities=False):
+        m = Marshalled(problem, keep_densities=keep_densities, precision=precision)
+        t = fthms_server_submit(self.s, m)
+        o = problem["options"]
+        self.meta[t] = (len(problem["arcs"]), o["L"], m.options.n_obs, o["n_tout"])
+        return t
+
+    def wait(self, ticket, timeout_ms=-1):
+        fthms_server_wait(self.s, ticket, timeout_ms)
+
+    def traces(self, ticket):
+        P, L, n_obs, n_tout = self.meta[ticket]
+        return fthms_traces(fthms_server_result(self.s, ticket), n_obs, n_tout)
+
+    def densities(self, ticket, arc, m=0, q=0):
+        P, L, _, _ = self.meta[ticket]
+        req = fthms_server_result(self.s, ticket)
+        flat = fthms_densities(req, arc, m, q)
+        return flat[0::2] + 1j * flat[1::2]
+
+    def stats(self, ticket):
+        return fthms_stats(fthms_server_result(self.s, ticket))
+
+    def latency(self, ticket):
+        return fthms_server_latency(self.s, ticket)
+
+    def release(self, ticket):
+        fthms_server_release(self.s, ticket)
+        self.meta.pop(ticket, None)
+
+    def close(self):
+        if self.s is not None:
+            fthms_server_destroy(self.s)
+            self.s = None

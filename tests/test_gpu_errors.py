@@ -24,7 +24,7 @@ def _status(F, fn):
 
 
 def test_budget_rejects_job_with_enomem(F):
-    ctx = F.fthms_create(0, 1 << 20, None)          # 1 MiB budget
+    ctx = F.fthms_create(0, 1 << 10, None)          # 1 KiB budget
     st, msg = _status(F, lambda: F.fthms_prepare(ctx, F.Marshalled(wl.random_small(0))))
     assert st == F.FTHMS_ENOMEM and "budget" in msg
     F.fthms_destroy(ctx)
