@@ -156,6 +156,54 @@ def cpu_sample_problem():
     return workloads.config2(L=65, W=30.0, H=6.0, M=12, n_period=512, T=6.0)
 
 
+def served_form(F, n=32, seed=11, max_inflight=4, precision=1):
+    """Served stream on a bounded seeded sample of the fifth configuration's request mix: a saturated
+    pass (every request submitted at t = 0) measures capacity, then Poisson arrivals at 0.7 x that
+    rate give per-request latency (submit -> result on the device, host clock) and throughput."""
+    import workloads
+    problems = workloads.served_requests(seed, n)
+    solves = [len(p["arcs"]) * (p["options"]["L"] - 1) * p["options"]["M"] * p["options"]["Q"] for p in problems]
+    srv = F.Server(0, 0, max_inflight=max_inflight)
+    for p in problems[:2]:                      # warm-up
+        t = srv.submit(p, precision=precision)
+        srv.wait(t)
+        srv.release(t)
+    t0 = time.perf_counter()
+    tickets = [srv.submit(p, precision=precision) for p in problems]
+    for t in tickets:
+        srv.wait(t)
+    makespan = time.perf_counter() - t0
+    for t in tickets:
+        srv.release(t)
+    rate = 0.7 * n / makespan
+    rng = np.random.default_rng(seed)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n))
+    t0 = time.perf_counter()
+    tickets = []
+    for p, a in zip(problems, arrivals):
+        dt = t0 + a - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        tickets.append(srv.submit(p, precision=precision))
+    lat, qlat = [], []
+    for t in tickets:
+        srv.wait(t)
+    t_end = time.perf_counter()
+    for t in tickets:
+        q, tot = srv.latency(t)
+        lat.append(tot)
+        qlat.append(q)
+        srv.release(t)
+    srv.close()
+    lat = np.array(lat)
+    return {"value": float(sum(solves) / (t_end - t0)), "unit": "solves/s",
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "queue_p50_ms": float(np.percentile(qlat, 50)), "saturated_solves_per_s": float(sum(solves) / makespan),
+            "arrival_rate_per_s": rate, "requests": n, "max_inflight": max_inflight, "precision": precision,
+            "sample": f"{n} seeded requests (disk / star cavity / 1-3 ellipses, 2-6 arcs, omega_max in [20, 60], "
+                      f"129 or 257 frequencies, M 3-6), Poisson arrivals at 0.7 x saturated capacity"}
+
+
 def run_oracle_sample():
     from oracle import run_oracle
     p = cpu_sample_problem()
@@ -257,6 +305,8 @@ def ours(args):
             den += float(np.sum(np.abs(a[l]) ** 2))
     mixed_err = math.sqrt(num / den)
 
+    served = served_form(F) if (rank == 0 and not args.no_served) else None
+
     # end to end through the C ABI with host buffers
     e2e_steps = max(1, min(args.steps, 3))
     torch.cuda.synchronize()
@@ -332,7 +382,8 @@ def ours(args):
                               "max_refine_resid": st_mx["max_refine_resid"], "traces_finite": ok_mx,
                               "gpu_launches": int(st_mx["kernel_launches"] * args.steps),
                               "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages_mx.items()},
-                              "clocks": clocks_mx}}}
+                              "clocks": clocks_mx},
+                    "served": served}}
         print(json.dumps(line))
     if ws > 1:
         torch.distributed.destroy_process_group()
@@ -346,6 +397,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-served", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)

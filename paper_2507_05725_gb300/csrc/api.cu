@@ -216,11 +216,9 @@ fthms_status upload_job(fthms_req* r) {
   J.LU32 = nullptr;
   J.dinv32 = nullptr;
   TRY(dev_alloc(r, 1, &J.refine_resid));
-  J.AINV32 = nullptr;
   if (J.mixed) {
     TRY(dev_alloc(r, (size_t)p.mat_total, &J.LU32));
     TRY(dev_alloc(r, (size_t)p.piv_total, &J.dinv32));
-    TRY(dev_alloc(r, (size_t)p.mat_total, &J.AINV32));
   }
   TRY(dev_alloc(r, (size_t)p.vec_total, &J.G));
   TRY(dev_alloc(r, (size_t)p.vec_total, &J.phi));

@@ -61,6 +61,9 @@ __device__ __forceinline__ float2 crecip(float2 a) {
   float d = 1.0f / fmaf(a.x, a.x, a.y * a.y);
   return make_float2(a.x * d, -a.y * d);
 }
+__device__ __forceinline__ double2 make_neg(double2 a) { return make_double2(-a.x, -a.y); }
+__device__ __forceinline__ float2 make_neg(float2 a) { return make_float2(-a.x, -a.y); }
+constexpr int kSB = 32;   // diagonal block of the blocked triangular solves
 template <class C> struct CTraits;
 template <> struct CTraits<double2> { using R = double; };
 template <> struct CTraits<float2> { using R = float; };
@@ -396,67 +399,131 @@ __global__ void __launch_bounds__(kLuThreads) k_lu(DevJob J) {
     const int col = (int)(e / N), row = (int)(e % N);
     if (col > row) A[e] = cmul(A[e], dinv[row]);
   }
+  __syncthreads();
+  // Invert the kSB x kSB diagonal blocks of the unit-lower L and of the unit-upper U' in place (the
+  // strictly lower part of a block holds L^{-1}'s, the strictly upper part U'^{-1}'s), so that the
+  // triangular solves take ceil(N/kSB) dependent block steps.  Column c of the inverse of a unit
+  // triangular T: X[c][c] = 1, X[i][c] = -sum_k T[i][k] X[k][c] over k between c and i.
+  C* T = shl;                      // kSB x kSB block, column-major (reuses the panel space)
+  C* Xi = shl + kSB * kSB;
+  for (int r0 = 0; r0 < N; r0 += kSB) {
+    const int w = min(kSB, N - r0);
+    for (int e = tid; e < kSB * kSB; e += kLuThreads) {
+      const int c = e / kSB, i = e % kSB;
+      T[e] = (c < w && i < w) ? A[(long long)(r0 + c) * N + r0 + i] : C{};
+    }
+    __syncthreads();
+    if (tid < w) {                   // L^{-1}, column c = tid
+      const int c = tid;
+      for (int i = c + 1; i < w; ++i) {
+        C s = T[c * kSB + i];          // k = c term (X[c][c] = 1)
+        for (int kk = c + 1; kk < i; ++kk) s = cfms(make_neg(T[kk * kSB + i]), Xi[c * kSB + kk], s);
+        Xi[c * kSB + i] = make_neg(s);
+      }
+    } else if (tid >= 32 && tid < 32 + w) {   // U'^{-1}, column c = tid - 32
+      const int c = tid - 32;
+      for (int i = c - 1; i >= 0; --i) {
+        C s = T[c * kSB + i];
+        for (int kk = i + 1; kk < c; ++kk) s = cfms(make_neg(T[kk * kSB + i]), Xi[c * kSB + kk], s);
+        Xi[c * kSB + i] = make_neg(s);
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < w * w; e += kLuThreads) {
+      const int c = e / w, i = e % w;
+      if (i != c) A[(long long)(r0 + c) * N + r0 + i] = Xi[c * kSB + i];
+    }
+    __syncthreads();
+  }
 }
 
 // ---------------------------------------------------------------------------------------------
-// Triangular solves: one warp per system (the column step is latency-bound, so all 32 lanes share
-// each step's rows; measured faster than 2 or 4 systems per warp).  Both factors have a unit
-// diagonal (the LU kernel scaled U and kept D^{-1}), so every step is a pure column update whose loads
-// are all issued together through the read-only path.
+// Triangular solves, one warp per system, all Q right-hand sides together, in blocks of kSB = 32
+// rows: x_b = T_b^{-1} b_b with the inverted diagonal block (a 32 x 32 GEMV, lane = row), then the
+// rows beyond the block are updated with the block's columns (independent loads, lane = row).
+// ceil(N/32) dependent steps per sweep instead of N.  Both factors have a unit diagonal (U was scaled
+// and D^{-1} is applied between the sweeps).  C = double2 (FP64 factors) or float2 (FP32 factors).
 constexpr int kSolveWarps = 4;
-constexpr int kSolveGroup = 32;
-constexpr int kSolvePerWarp = 32 / kSolveGroup;
+
+template <class C>
+__device__ void tri_solve(C* b, int Q, int N, const C* __restrict__ A, const int* __restrict__ piv,
+                          const C* __restrict__ dinv, int lane) {
+  if (lane < Q) {
+    C* bq = b + lane * N;
+    for (int k = 0; k < N; ++k) {
+      const int p = __ldg(&piv[k]);
+      if (p != k) { C t = bq[k]; bq[k] = bq[p]; bq[p] = t; }
+    }
+  }
+  __syncwarp();
+  for (int r0 = 0; r0 < N; r0 += kSB) {           // forward, unit lower
+    const int w = min(kSB, N - r0), r1 = r0 + w;
+    for (int q = 0; q < Q; ++q) {
+      C* bq = b + q * N;
+      C x = C{};
+      if (lane < w) {
+        x = bq[r0 + lane];
+#pragma unroll 8
+        for (int c = 0; c < kSB; ++c)
+          if (c < lane && c < w) x = cfms(make_neg(__ldg(&A[(long long)(r0 + c) * N + r0 + lane])), bq[r0 + c], x);
+      }
+      __syncwarp();
+      if (lane < w) bq[r0 + lane] = x;
+      __syncwarp();
+      for (int i = r1 + lane; i < N; i += 32) {
+        C acc = bq[i];
+#pragma unroll 8
+        for (int c = 0; c < kSB; ++c)
+          if (c < w) acc = cfms(__ldg(&A[(long long)(r0 + c) * N + i]), bq[r0 + c], acc);
+        bq[i] = acc;
+      }
+      __syncwarp();
+    }
+  }
+  for (int e = lane; e < Q * N; e += 32) b[e] = cmul(b[e], __ldg(&dinv[e % N]));
+  __syncwarp();
+  for (int r0 = ((N - 1) / kSB) * kSB; r0 >= 0; r0 -= kSB) {   // backward, unit upper
+    const int w = min(kSB, N - r0);
+    for (int q = 0; q < Q; ++q) {
+      C* bq = b + q * N;
+      C x = C{};
+      if (lane < w) {
+        x = bq[r0 + lane];
+#pragma unroll 8
+        for (int c = 0; c < kSB; ++c)
+          if (c > lane && c < w) x = cfms(make_neg(__ldg(&A[(long long)(r0 + c) * N + r0 + lane])), bq[r0 + c], x);
+      }
+      __syncwarp();
+      if (lane < w) bq[r0 + lane] = x;
+      __syncwarp();
+      for (int i = lane; i < r0; i += 32) {
+        C acc = bq[i];
+#pragma unroll 8
+        for (int c = 0; c < kSB; ++c)
+          if (c < w) acc = cfms(__ldg(&A[(long long)(r0 + c) * N + i]), bq[r0 + c], acc);
+        bq[i] = acc;
+      }
+      __syncwarp();
+    }
+  }
+}
 
 __global__ void __launch_bounds__(32 * kSolveWarps) k_solve(DevJob J, int m) {
   extern __shared__ double2 shs[];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int sub = lane / kSolveGroup, gl = lane % kSolveGroup;
-  const unsigned gmask = kSolveGroup == 32 ? 0xffffffffu : ((1u << kSolveGroup) - 1u) << (sub * kSolveGroup);
-  const int sidx = (blockIdx.x * kSolveWarps + wid) * kSolvePerWarp + sub;
-  if (sidx >= J.nsys) return;   // whole groups leave together
+  const int sidx = blockIdx.x * kSolveWarps + wid;
+  if (sidx >= J.nsys) return;
   const SysDesc s = J.sys[sidx];
   const int N = s.N, Q = J.Q;
-  double2* b = shs + ((size_t)wid * kSolvePerWarp + sub) * Q * J.max_n;
-  const double2* __restrict__ A = J.A + s.mat_off;
-  const int* __restrict__ piv = J.piv + s.piv_off;
-  const double2* __restrict__ dinv = J.dinv + s.piv_off;
-  const double2* __restrict__ G = J.G + s.vec_off;
-  for (int e = gl; e < Q * N; e += kSolveGroup) b[e] = G[e];
-  __syncwarp(gmask);
-  if (gl < Q) {
-    double2* bq = b + gl * N;
-    for (int k = 0; k < N; ++k) {
-      const int p = __ldg(&piv[k]);
-      if (p != k) { double2 t = bq[k]; bq[k] = bq[p]; bq[p] = t; }
-    }
-  }
-  __syncwarp(gmask);
-  for (int k = 0; k < N - 1; ++k) {
-    const double2* __restrict__ Lc = A + (long long)k * N;
-    for (int q = 0; q < Q; ++q) {
-      double2* bq = b + q * N;
-      const double2 xk = bq[k];
-#pragma unroll 4
-      for (int i = k + 1 + gl; i < N; i += kSolveGroup) bq[i] = cfms(__ldg(&Lc[i]), xk, bq[i]);
-    }
-    __syncwarp(gmask);
-  }
-  for (int e = gl; e < Q * N; e += kSolveGroup) b[e] = cmul(b[e], __ldg(&dinv[e % N]));
-  __syncwarp(gmask);
-  for (int k = N - 1; k >= 1; --k) {
-    const double2* __restrict__ Uc = A + (long long)k * N;
-    for (int q = 0; q < Q; ++q) {
-      double2* bq = b + q * N;
-      const double2 xk = bq[k];
-#pragma unroll 4
-      for (int i = gl; i < k; i += kSolveGroup) bq[i] = cfms(__ldg(&Uc[i]), xk, bq[i]);
-    }
-    __syncwarp(gmask);
-  }
+  double2* b = shs + (size_t)wid * Q * J.max_n;
+  const double2* G = J.G + s.vec_off;
+  for (int e = lane; e < Q * N; e += 32) b[e] = G[e];
+  __syncwarp();
+  tri_solve<double2>(b, Q, N, J.A + s.mat_off, J.piv + s.piv_off, J.dinv + s.piv_off, lane);
   double2* out = J.phi + s.vec_off;
   double2* sum = J.phi_sum + s.vec_off;
   double2* all = J.phi_all ? J.phi_all + (long long)(m - 1) * J.vec_total + s.vec_off : nullptr;
-  for (int e = gl; e < Q * N; e += kSolveGroup) {
+  for (int e = lane; e < Q * N; e += 32) {
     double2 v = b[e];
     out[e] = v;
     sum[e] = m == 1 ? v : cadd(sum[e], v);
@@ -691,64 +758,10 @@ __global__ void __launch_bounds__(kApplyThreads) k_cross_apply(DevJob J) {
 }
 
 // ---------------------------------------------------------------------------------------------
-// Mixed-precision solve.  Once per system the FP32 factors give an FP32 inverse X = U'^{-1} D^{-1}
-// L^{-1} P; every solve is then a parallel GEMV: phi = X G, and refinement steps r = G - A phi with A
-// in double-float (about 48 bits) followed by phi += X r, until the relative correction is below
-// 1e-12 or kRefineMax steps.  One warp per system.
+// Mixed-precision solve: FP32 blocked solves with the FP32 factors, then refinement steps with
+// double-float residuals r = G - A phi (A kept as double-float, about 48 bits) and FP32 corrections,
+// until the relative correction is below 1e-11 or kRefineMax steps.  One warp per system.
 constexpr int kRefineMax = 3;
-constexpr int kInvThreads = 256;
-
-__global__ void __launch_bounds__(kInvThreads) k_inv32(DevJob J) {
-  extern __shared__ __align__(16) unsigned char shi_raw[];
-  const SysDesc s = J.sys[blockIdx.x];
-  const int N = s.N;
-  const float2* __restrict__ F = J.LU32 + s.mat_off;
-  float2* X = J.AINV32 + s.mat_off;
-  const int* piv = J.piv + s.piv_off;
-  const float2* dinv = J.dinv32 + s.piv_off;
-  int* perm = reinterpret_cast<int*>(shi_raw);                       // N
-  float2* rowk = reinterpret_cast<float2*>(shi_raw + ((N * sizeof(int) + 15) & ~15));   // N
-  float2* colk = rowk + N;                                           // N
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < N; ++i) perm[i] = i;
-    for (int k = 0; k < N; ++k) {
-      const int p = piv[k];
-      if (p != k) { int t = perm[k]; perm[k] = perm[p]; perm[p] = t; }
-    }
-  }
-  __syncthreads();
-  // X = P I: (P b)_i = b_{perm[i]}, so X[i][c] = [perm[i] == c]
-  for (long long e = threadIdx.x; e < (long long)N * N; e += kInvThreads) {
-    const int c = (int)(e / N), i = (int)(e % N);
-    X[e] = make_float2(perm[i] == c ? 1.f : 0.f, 0.f);
-  }
-  __syncthreads();
-  for (int k = 0; k < N - 1; ++k) {           // X <- L^{-1} X (unit lower)
-    for (int c = threadIdx.x; c < N; c += kInvThreads) rowk[c] = X[(long long)c * N + k];
-    for (int i = threadIdx.x; i < N; i += kInvThreads) colk[i] = F[(long long)k * N + i];
-    __syncthreads();
-    const int m = N - k - 1;
-    for (long long e = threadIdx.x; e < (long long)m * N; e += kInvThreads) {
-      const int c = (int)(e / m), i = k + 1 + (int)(e % m);
-      float2* x = X + (long long)c * N + i;
-      *x = cfms(colk[i], rowk[c], *x);
-    }
-    __syncthreads();
-  }
-  for (long long e = threadIdx.x; e < (long long)N * N; e += kInvThreads) X[e] = cmul(X[e], dinv[e % N]);
-  __syncthreads();
-  for (int k = N - 1; k >= 1; --k) {          // X <- U'^{-1} X (unit upper)
-    for (int c = threadIdx.x; c < N; c += kInvThreads) rowk[c] = X[(long long)c * N + k];
-    for (int i = threadIdx.x; i < k; i += kInvThreads) colk[i] = F[(long long)k * N + i];
-    __syncthreads();
-    for (long long e = threadIdx.x; e < (long long)k * N; e += kInvThreads) {
-      const int c = (int)(e / k), i = (int)(e % k);
-      float2* x = X + (long long)c * N + i;
-      *x = cfms(colk[i], rowk[c], *x);
-    }
-    __syncthreads();
-  }
-}
 
 __global__ void __launch_bounds__(32 * kSolveWarps) k_solve_mixed(DevJob J, int m) {
   extern __shared__ __align__(16) unsigned char shm_raw[];
@@ -760,27 +773,21 @@ __global__ void __launch_bounds__(32 * kSolveWarps) k_solve_mixed(DevJob J, int 
   const size_t per = (size_t)Q * J.max_n;
   float4* ph = reinterpret_cast<float4*>(shm_raw) + (size_t)wid * per;                        // df64
   float2* b = reinterpret_cast<float2*>(reinterpret_cast<float4*>(shm_raw) + kSolveWarps * per) + (size_t)wid * per;
-  const float2* __restrict__ X = J.AINV32 + s.mat_off;
+  const float2* __restrict__ L32 = J.LU32 + s.mat_off;
   const float4* __restrict__ Adf = reinterpret_cast<const float4*>(J.A) + s.mat_off;
+  const int* __restrict__ piv = J.piv + s.piv_off;
+  const float2* __restrict__ dinv = J.dinv32 + s.piv_off;
   const double2* __restrict__ G = J.G + s.vec_off;
   for (int e = lane; e < Q * N; e += 32) {
     const double2 g = G[e];
     b[e] = make_float2(__double2float_rn(g.x), __double2float_rn(g.y));
   }
   __syncwarp();
-  // phi = X b (FP32 GEMV, rows over lanes)
-  for (int q = 0; q < Q; ++q)
-    for (int i = lane; i < N; i += 32) {
-      float2 acc = make_float2(0.f, 0.f);
-      const float2* xr = X + i;
-#pragma unroll 4
-      for (int c = 0; c < N; ++c) acc = cfms(make_float2(-xr[(long long)c * N].x, -xr[(long long)c * N].y), b[q * N + c], acc);
-      ph[q * N + i] = make_float4(acc.x, 0.f, acc.y, 0.f);
-    }
+  tri_solve<float2>(b, Q, N, L32, piv, dinv, lane);
+  for (int e = lane; e < Q * N; e += 32) ph[e] = make_float4(b[e].x, 0.f, b[e].y, 0.f);
   __syncwarp();
   double rel = 1.0;
   for (int it = 0; it < kRefineMax; ++it) {
-    // r = G - A phi in double-float, rounded to FP32
     for (int q = 0; q < Q; ++q) {
       for (int i = lane; i < N; i += 32) {
         const float4 gd = df_split2(G[q * N + i]);
@@ -799,34 +806,27 @@ __global__ void __launch_bounds__(32 * kSolveWarps) k_solve_mixed(DevJob J, int 
       }
     }
     __syncwarp();
-    // phi += X r
+    tri_solve<float2>(b, Q, N, L32, piv, dinv, lane);
     float dmax = 0.f, pmax = 0.f;
-    for (int q = 0; q < Q; ++q)
-      for (int i = lane; i < N; i += 32) {
-        float2 d = make_float2(0.f, 0.f);
-        const float2* xr = X + i;
-#pragma unroll 4
-        for (int c = 0; c < N; ++c) {
-          const float2 xv = __ldg(&xr[(long long)c * N]);
-          d = cfms(make_float2(-xv.x, -xv.y), b[q * N + c], d);
-        }
-        float4 p = ph[q * N + i];
-        float sh, sl;
-        two_sum(p.x, d.x, sh, sl);
-        quick_two_sum(sh, sl + p.y, p.x, p.y);
-        two_sum(p.z, d.y, sh, sl);
-        quick_two_sum(sh, sl + p.w, p.z, p.w);
-        ph[q * N + i] = p;
-        dmax = fmaxf(dmax, fmaxf(fabsf(d.x), fabsf(d.y)));
-        pmax = fmaxf(pmax, fmaxf(fabsf(p.x), fabsf(p.z)));
-      }
+    for (int e = lane; e < Q * N; e += 32) {
+      const float2 d = b[e];
+      float4 p = ph[e];
+      float sh, sl;
+      two_sum(p.x, d.x, sh, sl);
+      quick_two_sum(sh, sl + p.y, p.x, p.y);
+      two_sum(p.z, d.y, sh, sl);
+      quick_two_sum(sh, sl + p.w, p.z, p.w);
+      ph[e] = p;
+      dmax = fmaxf(dmax, fmaxf(fabsf(d.x), fabsf(d.y)));
+      pmax = fmaxf(pmax, fmaxf(fabsf(p.x), fabsf(p.z)));
+    }
     for (int o = 16; o > 0; o >>= 1) {
       dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
       pmax = fmaxf(pmax, __shfl_xor_sync(0xffffffffu, pmax, o));
     }
     __syncwarp();
     rel = pmax > 0.f ? (double)dmax / (double)pmax : 0.0;
-    if (rel < 1e-12) break;
+    if (rel < 1e-11) break;
   }
   if (lane == 0) atomicMax(reinterpret_cast<unsigned long long*>(J.refine_resid), (unsigned long long)__double_as_longlong(rel));
   double2* out = J.phi + s.vec_off;
@@ -1148,16 +1148,14 @@ cudaError_t launch_assemble_self(const DevJob& J, cudaStream_t st, int* launches
 cudaError_t launch_lu(const DevJob& J, cudaStream_t st, int* launches) {
   if (J.mixed) {
     k_split_A<<<cdiv(J.mat_total, 256), 256, 0, st>>>(J);
-    size_t sh = (size_t)J.max_n * (kNB + kPS) * sizeof(float2);
+    size_t sh = std::max((size_t)J.max_n * (kNB + kPS), (size_t)2 * kSB * kSB) * sizeof(float2);
     cudaError_t e = cudaFuncSetAttribute(k_lu<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
     if (e != cudaSuccess) return e;
     k_lu<float2><<<J.nsys, kLuThreads, sh, st>>>(J);
-    size_t shi = (((size_t)J.max_n * sizeof(int) + 15) & ~(size_t)15) + 2 * (size_t)J.max_n * sizeof(float2);
-    k_inv32<<<J.nsys, kInvThreads, shi, st>>>(J);
-    *launches += 3;
+    *launches += 2;
     return cudaGetLastError();
   }
-  size_t sh = (size_t)J.max_n * (kNB + kPS) * sizeof(double2);
+  size_t sh = std::max((size_t)J.max_n * (kNB + kPS), (size_t)2 * kSB * kSB) * sizeof(double2);
   cudaError_t e = cudaFuncSetAttribute(k_lu<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
   if (e != cudaSuccess) return e;
   k_lu<double2><<<J.nsys, kLuThreads, sh, st>>>(J);
@@ -1215,10 +1213,10 @@ cudaError_t launch_solve(const DevJob& J, int m, cudaStream_t st, int* launches)
     *launches += 1;
     return cudaGetLastError();
   }
-  size_t sh = (size_t)kSolveWarps * kSolvePerWarp * J.Q * J.max_n * sizeof(double2);
+  size_t sh = (size_t)kSolveWarps * J.Q * J.max_n * sizeof(double2);
   cudaError_t e = cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
   if (e != cudaSuccess) return e;
-  k_solve<<<cdiv(J.nsys, kSolveWarps * kSolvePerWarp), 32 * kSolveWarps, sh, st>>>(J, m);
+  k_solve<<<cdiv(J.nsys, kSolveWarps), 32 * kSolveWarps, sh, st>>>(J, m);
   *launches += 1;
   return cudaGetLastError();
 }

@@ -50,7 +50,6 @@ struct DevJob {
   double2* A;                // LU factors (mixed form: the matrix itself, as double-float)
   float2* LU32;              // FP32 factors (mixed form)
   float2* dinv32;            // FP32 1 / U_kk (mixed form)
-  float2* AINV32;            // FP32 inverse per system (mixed form), column-major
   double* refine_resid;      // max over systems of the last relative correction (mixed form)
   int* piv;
   double2* dinv;             // 1 / U_kk

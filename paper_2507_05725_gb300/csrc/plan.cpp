@@ -483,7 +483,7 @@ void arc_nodes(const Curve& c, double theta_a, double theta_b, int N, std::vecto
 size_t plan_device_bytes(const Plan& p) {
   size_t b = 0;
   b += (size_t)p.mat_total * 16;                 // A / LU
-  if (p.opt.precision == 1) b += (size_t)p.mat_total * 16 + (size_t)p.piv_total * 8;   // FP32 factors, inverse
+  if (p.opt.precision == 1) b += (size_t)p.mat_total * 8 + (size_t)p.piv_total * 8;   // FP32 factors
   b += (size_t)p.piv_total * 4;                  // pivots
   b += (size_t)p.rlog_total * 8;                 // self log tables
   b += (size_t)p.vec_total * 16 * 3;             // G, phi (current), phi sum
