@@ -194,6 +194,11 @@ enum {
   FTHMS_NSTAGES = 10
 };
 
+/* enable != 0: fthms_run captures the job's whole pipeline (all stages and steps) into a CUDA graph on
+ * its first run and replays it afterwards as one launch; the graph is rebuilt never (the job's inputs
+ * are fixed at prepare).  Runs with per-stage profiling enabled launch stage by stage. */
+fthms_status fthms_use_graph(fthms_req* req, int enable);
+
 /* enable != 0: later runs record CUDA events around every stage launch on the context stream
  * (small overhead); 0 stops recording.  Accumulated totals are kept until reset by enabling again. */
 fthms_status fthms_profile(fthms_req* req, int enable);

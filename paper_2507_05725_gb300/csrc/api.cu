@@ -90,6 +90,8 @@ struct fthms_req {
   bool ran = false;
   int launches = 0;
   double setup_ms = 0.0;
+  bool use_graph = false;          // replay the captured pipeline instead of launching stage by stage
+  cudaGraphExec_t graph = nullptr;
 };
 
 namespace {
@@ -123,6 +125,10 @@ fthms_status dev_alloc(fthms_req* r, size_t count, T** out) {
 }
 
 void free_req(fthms_req* r) {
+  if (r->graph) {
+    cudaGraphExecDestroy(r->graph);
+    r->graph = nullptr;
+  }
   for (void* p : r->allocs) cudaFreeAsync(p, r->stream);
   r->allocs.clear();
   for (cudaEvent_t e : r->ev_pool) cudaEventDestroy(e);
@@ -281,7 +287,34 @@ fthms_status stage(fthms_req* r, int st_id, cudaStream_t st, int* nl, F&& launch
   return FTHMS_OK;
 }
 
+fthms_status enqueue_stages(fthms_req* r);
+
+// Run the pipeline: directly, or (use_graph, profiling off) through a CUDA graph captured on the first
+// run and replayed afterwards (one launch for the whole job).
 fthms_status enqueue(fthms_req* r) {
+  if (!r->use_graph || r->profiling) return enqueue_stages(r);
+  TRY(flush_marks(r));
+  cudaStream_t st = r->stream;
+  if (!r->graph) {
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    fthms_status s = enqueue_stages(r);
+    cudaError_t e = cudaStreamEndCapture(st, &g);
+    if (s != FTHMS_OK) {
+      if (g) cudaGraphDestroy(g);
+      return s;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&r->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+  }
+  CK(cudaGraphLaunch(r->graph, st));
+  r->ran = true;
+  return FTHMS_OK;
+}
+
+fthms_status enqueue_stages(fthms_req* r) {
   const DevJob& J = r->J;
   cudaStream_t st = r->stream;
   int nl = 0;
@@ -564,6 +597,12 @@ fthms_status fthms_release(fthms_req* req) {
 }
 
 const char* fthms_last_error(void) { return g_last_error.c_str(); }
+
+fthms_status fthms_use_graph(fthms_req* req, int enable) {
+  if (!req) return fail(FTHMS_EINVAL, "fthms_use_graph: NULL job");
+  req->use_graph = enable != 0;
+  return FTHMS_OK;
+}
 
 fthms_status fthms_profile(fthms_req* req, int enable) {
   if (!req) return fail(FTHMS_EINVAL, "fthms_profile: NULL job");

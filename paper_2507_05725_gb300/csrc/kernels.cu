@@ -413,22 +413,23 @@ __global__ void __launch_bounds__(kLuThreads) k_lu(DevJob J) {
       T[e] = (c < w && i < w) ? A[(long long)(r0 + c) * N + r0 + i] : C{};
     }
     __syncthreads();
-    if (tid < w) {                   // L^{-1}, column c = tid
-      const int c = tid;
-      for (int i = c + 1; i < w; ++i) {
-        C s = T[c * kSB + i];          // k = c term (X[c][c] = 1)
-        for (int kk = c + 1; kk < i; ++kk) s = cfms(make_neg(T[kk * kSB + i]), Xi[c * kSB + kk], s);
-        Xi[c * kSB + i] = make_neg(s);
-      }
-    } else if (tid >= 32 && tid < 32 + w) {   // U'^{-1}, column c = tid - 32
-      const int c = tid - 32;
-      for (int i = c - 1; i >= 0; --i) {
-        C s = T[c * kSB + i];
-        for (int kk = i + 1; kk < c; ++kk) s = cfms(make_neg(T[kk * kSB + i]), Xi[c * kSB + kk], s);
-        Xi[c * kSB + i] = make_neg(s);
-      }
-    }
+    // Xi <- identity; then step k: X[i][c] -= T[i][k] X[k][c] for i > k, c <= k (lower part) and,
+    // from the bottom, X[i][c] -= T[i][k'] X[k'][c] for i < k', c >= k' (upper part), k' = w-1-k:
+    // all (i, c) pairs of a step in parallel.
+    for (int e = tid; e < kSB * kSB; e += kLuThreads) Xi[e] = (e / kSB == e % kSB) ? C{1} : C{};
     __syncthreads();
+    for (int kk = 0; kk < w - 1; ++kk) {
+      const int ku = w - 1 - kk;
+      for (int e = tid; e < 2 * kSB * kSB; e += kLuThreads) {
+        const int half = e / (kSB * kSB), f = e % (kSB * kSB), c = f / kSB, i = f % kSB;
+        if (half == 0) {
+          if (i > kk && i < w && c <= kk) Xi[c * kSB + i] = cfms(T[kk * kSB + i], Xi[c * kSB + kk], Xi[c * kSB + i]);
+        } else {
+          if (i < ku && c >= ku && c < w) Xi[c * kSB + i] = cfms(T[ku * kSB + i], Xi[c * kSB + ku], Xi[c * kSB + i]);
+        }
+      }
+      __syncthreads();
+    }
     for (int e = tid; e < w * w; e += kLuThreads) {
       const int c = e / w, i = e % w;
       if (i != c) A[(long long)(r0 + c) * N + r0 + i] = Xi[c * kSB + i];
@@ -788,21 +789,52 @@ __global__ void __launch_bounds__(32 * kSolveWarps) k_solve_mixed(DevJob J, int 
   __syncwarp();
   double rel = 1.0;
   for (int it = 0; it < kRefineMax; ++it) {
+    // r = G - A phi, four rows per lane in flight (independent compensated sums)
     for (int q = 0; q < Q; ++q) {
-      for (int i = lane; i < N; i += 32) {
-        const float4 gd = df_split2(G[q * N + i]);
-        dfacc re, im;
-        re.add(gd.x, gd.y);
-        im.add(gd.z, gd.w);
-        const float4* Ai = Adf + i;
-        const float4* pq = ph + q * N;
-#pragma unroll 4
-        for (int j = 0; j < N; ++j) {
-          const float4 a = __ldg(&Ai[(long long)j * N]);
-          cdf_mac(re, im, make_float4(-a.x, -a.y, -a.z, -a.w), pq[j]);
+      const float4* pq = ph + q * N;
+      for (int i0 = lane; i0 < N; i0 += 4 * 32) {
+        dfacc re[4], im[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = i0 + 32 * u;
+          if (i < N) {
+            const float4 gd = df_split2(G[q * N + i]);
+            re[u].add(gd.x, gd.y);
+            im[u].add(gd.z, gd.w);
+          }
         }
-        const df rr = re.value(), ri = im.value();
-        b[q * N + i] = make_float2(rr.hi + rr.lo, ri.hi + ri.lo);
+        const int nu = min(4, (N - i0 + 31) / 32);
+        if (nu == 4) {
+#pragma unroll 2
+          for (int j = 0; j < N; ++j) {
+            const float4 x = pq[j];
+            const float4* Aj = Adf + (long long)j * N + i0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const float4 a = __ldg(&Aj[32 * u]);
+              cdf_mac(re[u], im[u], make_float4(-a.x, -a.y, -a.z, -a.w), x);
+            }
+          }
+        } else {
+          for (int j = 0; j < N; ++j) {
+            const float4 x = pq[j];
+            const float4* Aj = Adf + (long long)j * N + i0;
+            for (int u = 0; u < nu; ++u) {
+              if (i0 + 32 * u < N) {
+                const float4 a = __ldg(&Aj[32 * u]);
+                cdf_mac(re[u], im[u], make_float4(-a.x, -a.y, -a.z, -a.w), x);
+              }
+            }
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = i0 + 32 * u;
+          if (i < N) {
+            const df rr = re[u].value(), ri = im[u].value();
+            b[q * N + i] = make_float2(rr.hi + rr.lo, ri.hi + ri.lo);
+          }
+        }
       }
     }
     __syncwarp();

@@ -221,3 +221,20 @@ def test_mixed_matches_plain_at_full_size(F, ctx):
     a.release()
     b.release()
     assert math.sqrt(num / den) < MIXED_TOL
+
+
+def test_graph_replay_matches_direct_launches(F, ctx):
+    """A job captured into a CUDA graph and replayed gives the same densities and traces."""
+    problem = wl.random_small(5, n_curves=2, n_arcs_per_curve=2, Q=2, L=65, M=2)
+    a = F.Job(ctx, problem).run().wait()
+    b = F.Job(ctx, problem)
+    F.fthms_use_graph(b.req, True)
+    b.run().wait()
+    b.run().wait()                       # replay
+    assert np.array_equal(a.traces(), b.traces())
+    for j in range(len(problem["arcs"])):
+        da, db = a.densities(j, 2, 1), b.densities(j, 2, 1)
+        for l in da:
+            assert np.array_equal(da[l], db[l])
+    a.release()
+    b.release()
