@@ -3,7 +3,18 @@
 import os
 import re
 
+import pytest
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built_library():
+    """Build libfthms.so (nvcc cross-compiles for sm_103a without a GPU) if this checkout has none."""
+    lib = os.path.join(ROOT, "paper_2507_05725_gb300", "lib", "libfthms.so")
+    if not os.path.exists(lib):
+        from paper_2507_05725_gb300.build import build
+        build()
 
 
 def declared_symbols():

@@ -194,7 +194,7 @@ def test_time_window_pou():
 
 def test_forward_transform_matches_closed_form():
     sig = {"amp": 1.0, "carrier": 10.0, "centre": 6.0, "width": 2.0}
-    opts = {"W": 60.0, "L": 257, "Q": 1, "H": 40.0, "n_period": 2048}
+    opts = {"W": 60.0, "L": 1025, "Q": 1, "H": 40.0, "n_period": 4096}
     g = tr.TimeGrid(opts)
     G = g.forward(tr.signal_f(sig, g.t)[None, :])[0, 0]
     ref = tr.signal_F(sig, g.omega) * np.exp(-1j * g.omega * g.s[0])
@@ -270,7 +270,7 @@ def test_ms_horizon_theorem():
     field early and departs from it later; more steps extend the matching interval."""
     errs = {}
     for M in (1, 3):
-        p = wl.config1(L=129, M=M, N=64)
+        p = wl.config1(L=257, M=M, N=64)
         r = run_oracle(p)
         o = p["options"]
         tout = o["tout0"] + o["dtout"] * np.arange(o["n_tout"])
