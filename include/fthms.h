@@ -79,7 +79,7 @@ typedef struct {
 /* Discretisation and output options.
  *  W, L      : frequencies omega_l = l*(W/(L-1)), l = 0..L-1; l = 1..L-1 are solved.
  *  N rule    : nodes per arc N_j(omega) = N_fixed if > 0, else max(N_min, ceil(N_ppw*omega*len_j)
- *              + N_off), len_j the arc length.  The transfer mesh of arc j is its first-kind
+ *              + N_off), len_j the arc length; every N_j(omega) must lie in [2, 800].  The transfer mesh of arc j is its first-kind
  *              Chebyshev grid of size N_j(omega_{L-1}).
  *  M         : multiple-scattering steps (Algorithm 1's outer loop).
  *  Q, H      : 1 <= Q <= 4 time windows sqcap_q(t) = sqcap(t - s_q), s_q = 1.5 (q-1) H (Section 5).
@@ -218,8 +218,8 @@ const char* fthms_last_error(void);
  * device memory (fthms_prepare's estimate), so jobs that arrive while others run start as soon as
  * slots and memory free up and their kernels overlap on the device.  Finished jobs stay resident
  * (factors, densities, traces) until fthms_server_release; a job larger than the whole budget fails
- * with FTHMS_ENOMEM.  This is the serving form of the benchmark spec; the paper has no counterpart (its
- * sub-problems are "embarrassingly parallel", Section 3). */
+ * with FTHMS_ENOMEM.  This is a serving form of the solver; the paper has no counterpart (it notes only that the
+ * sub-problems are independent of one another, Section 3). */
 typedef struct fthms_server fthms_server;
 
 fthms_status fthms_server_create(fthms_server** out, int device, size_t hbm_budget_bytes, int max_inflight);

@@ -16,7 +16,7 @@ The oracle is a plain, slow, readable numpy/scipy restatement of the discrete me
 * ``fthms``      -- the multiple-scattering driver of Algorithm 1 and eqs. criterion_int1/2.
 
 Every function cites the passage it follows.  Readings of passages that the paper leaves open are
-listed in the design doc and repeated in the docstrings.  Library primitives used as steps: scipy.special
+stated in the docstrings of the functions that take them.  Library primitives used as steps: scipy.special
 Bessel functions, LAPACK LU (scipy.linalg.lu_factor), numpy matrix products.
 """
 from .fthms import run_oracle, OracleResult  # noqa: F401

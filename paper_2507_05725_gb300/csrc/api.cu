@@ -287,7 +287,7 @@ fthms_status stage(fthms_req* r, int st_id, cudaStream_t st, int* nl, F&& launch
   return FTHMS_OK;
 }
 
-fthms_status enqueue_stages(fthms_req* r);
+fthms_status enqueue_stages(fthms_req* r, bool bracket = true);
 
 // Run the pipeline: directly, or (use_graph, profiling off) through a CUDA graph captured on the first
 // run and replayed afterwards (one launch for the whole job).
@@ -298,7 +298,9 @@ fthms_status enqueue(fthms_req* r) {
   if (!r->graph) {
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    fthms_status s = enqueue_stages(r);
+    // An event recorded on a capturing stream only marks a dependency inside the graph, so the
+    // job's start and end events are recorded around each replay instead.
+    fthms_status s = enqueue_stages(r, false);
     cudaError_t e = cudaStreamEndCapture(st, &g);
     if (s != FTHMS_OK) {
       if (g) cudaGraphDestroy(g);
@@ -309,17 +311,19 @@ fthms_status enqueue(fthms_req* r) {
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
   }
+  CK(cudaEventRecord(r->ev0, st));
   CK(cudaGraphLaunch(r->graph, st));
+  CK(cudaEventRecord(r->ev1, st));
   r->ran = true;
   return FTHMS_OK;
 }
 
-fthms_status enqueue_stages(fthms_req* r) {
+fthms_status enqueue_stages(fthms_req* r, bool bracket) {
   const DevJob& J = r->J;
   cudaStream_t st = r->stream;
   int nl = 0;
   TRY(flush_marks(r));
-  CK(cudaEventRecord(r->ev0, st));
+  if (bracket) CK(cudaEventRecord(r->ev0, st));
   TRY(stage(r, FTHMS_STAGE_TABLES, st, &nl, [&] { return launch_tables(J, st, &nl); }));
   TRY(stage(r, FTHMS_STAGE_ASSEMBLE, st, &nl, [&] { return launch_assemble_self(J, st, &nl); }));
   TRY(stage(r, FTHMS_STAGE_LU, st, &nl, [&] { return launch_lu(J, st, &nl); }));
@@ -339,9 +343,11 @@ fthms_status enqueue_stages(fthms_req* r) {
     }
   }
   TRY(stage(r, FTHMS_STAGE_TRACES, st, &nl, [&] { return launch_traces(J, st, &nl); }));
-  CK(cudaEventRecord(r->ev1, st));
+  if (bracket) {
+    CK(cudaEventRecord(r->ev1, st));
+    r->ran = true;
+  }
   r->launches = nl;
-  r->ran = true;
   return FTHMS_OK;
 }
 

@@ -911,16 +911,29 @@ __global__ void __launch_bounds__(kApplyThreads) k_cross_apply_df(DevJob J) {
     const CrossBlk B = J.blks[g.blk_begin + b];
     const int N = B.N, nr = B.nrows, r = row - s_row0[b];
     const float4* phb = ph + s_ph0[b];
-    dfacc sr[Q], si[Q];
+    // two independent compensated sums (even and odd sources) halve the serial chain
+    dfacc sr[Q], si[Q], tr[Q], ti[Q];
     const float4* __restrict__ Er = reinterpret_cast<const float4*>(J.E + B.e_off) + r;
-#pragma unroll 4
-    for (int i = 0; i < N; ++i) {
-      const float4 ev = __ldg(&Er[(long long)i * nr]);
+    int i = 0;
+#pragma unroll 2
+    for (; i + 1 < N; i += 2) {
+      const float4 e0 = __ldg(&Er[(long long)i * nr]);
+      const float4 e1 = __ldg(&Er[(long long)(i + 1) * nr]);
 #pragma unroll
-      for (int q = 0; q < Q; ++q) cdf_mac(sr[q], si[q], ev, phb[q * N + i]);
+      for (int q = 0; q < Q; ++q) {
+        cdf_mac(sr[q], si[q], e0, phb[q * N + i]);
+        cdf_mac(tr[q], ti[q], e1, phb[q * N + i + 1]);
+      }
+    }
+    if (i < N) {
+      const float4 e0 = __ldg(&Er[(long long)i * nr]);
+#pragma unroll
+      for (int q = 0; q < Q; ++q) cdf_mac(sr[q], si[q], e0, phb[q * N + i]);
     }
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
+      sr[q].add(tr[q].hi, tr[q].lo);
+      si[q].add(ti[q].hi, ti[q].lo);
       const df a = sr[q].value(), c = si[q].value();
       res[q * nrow + row] = make_double2((double)a.hi + (double)a.lo, (double)c.hi + (double)c.lo);
     }

@@ -274,8 +274,8 @@ int build_plan(const fthms_curve* curves, int ncurves, const fthms_arc* arcs, in
       double omega = l * p.h;
       int N = opt->N_fixed > 0 ? opt->N_fixed
                                : std::max(opt->N_min, (int)std::ceil(opt->N_ppw * omega * p.arcs[j].length) + opt->N_off);
-      if (N < 2 || N > 1024) {
-        snprintf(buf, sizeof buf, "arc %d omega index %d: node count %d outside [2, 1024]", j, l, N);
+      if (N < 2 || N > 800) {
+        snprintf(buf, sizeof buf, "arc %d omega index %d: node count %d outside [2, 800] (shared-memory panel of the LU)", j, l, N);
         err = buf;
         return FTHMS_EINVAL;
       }
