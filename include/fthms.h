@@ -129,9 +129,13 @@ typedef struct {
 } fthms_stats_t;
 
 /* Create a context on CUDA device `device` that enqueues all work on `cuda_stream` (a
- * cudaStream_t; NULL = the legacy default stream).  hbm_budget_bytes caps the device memory of
- * all live jobs (0 = no cap).  Returns FTHMS_ECUDA if the device cannot be used. */
+ * cudaStream_t; NULL = a non-blocking stream that the context creates, owns and destroys).
+ * hbm_budget_bytes caps the device memory of all live jobs (0 = no cap).  Returns FTHMS_ECUDA if
+ * the device cannot be used. */
 fthms_status fthms_create(fthms_ctx** out, int device, size_t hbm_budget_bytes, void* cuda_stream);
+/* Destroy a context.  Jobs of the context that were not released are waited for and their device
+ * memory is freed; their handles then accept fthms_release only (every other call returns
+ * FTHMS_EINVAL). */
 fthms_status fthms_destroy(fthms_ctx* ctx);
 
 /* Plan a job (Section 3.1 geometry, Section 5 grids) on the host, allocate its device memory and

@@ -9,6 +9,7 @@
 #include <deque>
 #include <map>
 #include <mutex>
+#include <set>
 #include <string>
 #include <thread>
 #include <vector>
@@ -63,7 +64,9 @@ struct fthms_ctx {
   size_t budget = 0;
   size_t in_use = 0;
   cudaStream_t stream = nullptr;
+  bool own_stream = false;         // created by fthms_create (no stream was given)
   std::mutex mu;
+  std::set<fthms_req*> live;       // prepared and not yet released jobs
 };
 
 struct ProfMark {
@@ -363,16 +366,39 @@ fthms_status fthms_create(fthms_ctx** out, int device, size_t hbm_budget_bytes, 
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
   if (device < 0 || device >= n) return fail(FTHMS_EINVAL, "fthms_create: no such device");
   TRY(ensure_device(device));
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  bool own = false;
+  if (!st) {
+    // A stream of its own (the legacy default stream cannot be captured into a CUDA graph).
+    e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreateWithFlags");
+    own = true;
+  }
   fthms_ctx* c = new fthms_ctx;
   c->device = device;
   c->budget = hbm_budget_bytes;
-  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  c->stream = st;
+  c->own_stream = own;
   *out = c;
   return FTHMS_OK;
 }
 
 fthms_status fthms_destroy(fthms_ctx* ctx) {
   if (!ctx) return fail(FTHMS_EINVAL, "fthms_destroy: NULL context");
+  ensure_device(ctx->device);
+  {
+    // Jobs still alive: wait for their work, free their device memory and detach them, so that
+    // their handles stay valid for fthms_release alone.
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    for (fthms_req* r : ctx->live) {
+      if (r->ran) cudaEventSynchronize(r->ev1);
+      free_req(r);
+      cudaStreamSynchronize(r->stream);
+      r->ctx = nullptr;
+    }
+    ctx->live.clear();
+  }
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
   return FTHMS_OK;
 }
@@ -422,12 +448,17 @@ fthms_status fthms_prepare(fthms_ctx* ctx, const fthms_curve* curves, int ncurve
     return fail(oom ? FTHMS_ENOMEM : s, msg);
   }
   r->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->live.insert(r);
+  }
   *out = r;
   return FTHMS_OK;
 }
 
 fthms_status fthms_run(fthms_req* req) {
   if (!req) return fail(FTHMS_EINVAL, "fthms_run: NULL job");
+  if (!req->ctx) return fail(FTHMS_EINVAL, "fthms_run: the job's context was destroyed");
   TRY(ensure_device(req->ctx->device));
   return enqueue(req);
 }
@@ -448,6 +479,7 @@ fthms_status fthms_submit(fthms_ctx* ctx, const fthms_curve* curves, int ncurves
 
 fthms_status fthms_poll(fthms_req* req, int* done) {
   if (!req || !done) return fail(FTHMS_EINVAL, "fthms_poll: NULL argument");
+  if (!req->ctx) return fail(FTHMS_EINVAL, "fthms_poll: the job's context was destroyed");
   if (!req->ran) { *done = 0; return FTHMS_OK; }
   cudaError_t e = cudaEventQuery(req->ev1);
   if (e == cudaSuccess) { *done = 1; return FTHMS_OK; }
@@ -457,6 +489,7 @@ fthms_status fthms_poll(fthms_req* req, int* done) {
 
 fthms_status fthms_wait(fthms_req* req, int timeout_ms) {
   if (!req) return fail(FTHMS_EINVAL, "fthms_wait: NULL job");
+  if (!req->ctx) return fail(FTHMS_EINVAL, "fthms_wait: the job's context was destroyed");
   if (!req->ran) return fail(FTHMS_EINVAL, "fthms_wait: job was never run");
   TRY(ensure_device(req->ctx->device));
   auto t0 = std::chrono::steady_clock::now();
@@ -474,6 +507,7 @@ fthms_status fthms_wait(fthms_req* req, int timeout_ms) {
 
 fthms_status fthms_traces(fthms_req* req, double* out, size_t cap) {
   if (!req || (!out && cap)) return fail(FTHMS_EINVAL, "fthms_traces: NULL argument");
+  if (!req->ctx) return fail(FTHMS_EINVAL, "fthms_traces: the job's context was destroyed");
   size_t n = (size_t)req->plan.n_obs * req->plan.n_tout;
   if (cap < n) return fail(FTHMS_EINVAL, "fthms_traces: output buffer too small");
   TRY(fthms_wait(req, -1));
@@ -504,6 +538,7 @@ static fthms_status density_range(fthms_req* req, int arc, int m, int q, const d
 
 fthms_status fthms_densities(fthms_req* req, int arc, int m, int q, double* out, size_t cap, size_t* needed) {
   if (!req) return fail(FTHMS_EINVAL, "fthms_densities: NULL job");
+  if (!req->ctx) return fail(FTHMS_EINVAL, "fthms_densities: the job's context was destroyed");
   const double2* base;
   long long first, last;
   size_t n;
@@ -529,6 +564,7 @@ fthms_status fthms_densities(fthms_req* req, int arc, int m, int q, double* out,
 
 fthms_status fthms_densities_dev(fthms_req* req, int arc, int m, int q, double* out_dev, size_t cap) {
   if (!req || !out_dev) return fail(FTHMS_EINVAL, "fthms_densities_dev: NULL argument");
+  if (!req->ctx) return fail(FTHMS_EINVAL, "fthms_densities_dev: the job's context was destroyed");
   const double2* base;
   long long first, last;
   size_t n;
@@ -548,6 +584,7 @@ fthms_status fthms_densities_dev(fthms_req* req, int arc, int m, int q, double* 
 
 fthms_status fthms_node_counts(fthms_req* req, int* out, size_t cap) {
   if (!req || !out) return fail(FTHMS_EINVAL, "fthms_node_counts: NULL argument");
+  if (!req->ctx) return fail(FTHMS_EINVAL, "fthms_node_counts: the job's context was destroyed");
   const Plan& p = req->plan;
   if (cap < (size_t)p.P * (p.L - 1)) return fail(FTHMS_EINVAL, "fthms_node_counts: buffer too small");
   for (int j = 0; j < p.P; ++j)
@@ -557,6 +594,7 @@ fthms_status fthms_node_counts(fthms_req* req, int* out, size_t cap) {
 
 fthms_status fthms_stats(fthms_req* req, fthms_stats_t* out) {
   if (!req || !out) return fail(FTHMS_EINVAL, "fthms_stats: NULL argument");
+  if (!req->ctx) return fail(FTHMS_EINVAL, "fthms_stats: the job's context was destroyed");
   const Plan& p = req->plan;
   std::memset(out, 0, sizeof *out);
   out->setup_ms = req->setup_ms;
@@ -591,12 +629,17 @@ fthms_status fthms_stats(fthms_req* req, fthms_stats_t* out) {
 
 fthms_status fthms_release(fthms_req* req) {
   if (!req) return fail(FTHMS_EINVAL, "fthms_release: NULL job");
+  if (!req->ctx) {            // detached by fthms_destroy: device memory already freed
+    delete req;
+    return FTHMS_OK;
+  }
   if (req->ran) cudaEventSynchronize(req->ev1);
   free_req(req);
   cudaStreamSynchronize(req->stream);   // the stream-ordered frees have run before the budget is returned
   {
     std::lock_guard<std::mutex> lk(req->ctx->mu);
     req->ctx->in_use -= req->plan.device_bytes;
+    req->ctx->live.erase(req);
   }
   delete req;
   return FTHMS_OK;
@@ -606,12 +649,14 @@ const char* fthms_last_error(void) { return g_last_error.c_str(); }
 
 fthms_status fthms_use_graph(fthms_req* req, int enable) {
   if (!req) return fail(FTHMS_EINVAL, "fthms_use_graph: NULL job");
+  if (!req->ctx) return fail(FTHMS_EINVAL, "fthms_use_graph: the job's context was destroyed");
   req->use_graph = enable != 0;
   return FTHMS_OK;
 }
 
 fthms_status fthms_profile(fthms_req* req, int enable) {
   if (!req) return fail(FTHMS_EINVAL, "fthms_profile: NULL job");
+  if (!req->ctx) return fail(FTHMS_EINVAL, "fthms_profile: the job's context was destroyed");
   TRY(flush_marks(req));
   if (enable) {
     for (int k = 0; k < FTHMS_NSTAGES; ++k) {
@@ -625,6 +670,7 @@ fthms_status fthms_profile(fthms_req* req, int enable) {
 
 fthms_status fthms_stage_times(fthms_req* req, double* ms, long long* launches) {
   if (!req || !ms || !launches) return fail(FTHMS_EINVAL, "fthms_stage_times: NULL argument");
+  if (!req->ctx) return fail(FTHMS_EINVAL, "fthms_stage_times: the job's context was destroyed");
   TRY(flush_marks(req));
   for (int k = 0; k < FTHMS_NSTAGES; ++k) {
     ms[k] = req->stage_ms[k];
@@ -842,13 +888,7 @@ fthms_status fthms_server_create(fthms_server** out, int device, size_t hbm_budg
     return st;
   }
   s->max_inflight = max_inflight;
-  cudaError_t eu = cudaStreamCreateWithFlags(&s->upload, cudaStreamNonBlocking);
-  if (eu != cudaSuccess) {
-    fthms_destroy(s->ctx);
-    delete s;
-    return cuda_fail(eu, "cudaStreamCreate");
-  }
-  s->ctx->stream = s->upload;     // host-to-device uploads of admitted jobs
+  s->upload = s->ctx->stream;     // the context's own stream carries the uploads of admitted jobs
   s->streams.resize(max_inflight);
   s->slot_used.assign(max_inflight, 0);
   for (int i = 0; i < max_inflight; ++i) {
@@ -987,7 +1027,6 @@ fthms_status fthms_server_destroy(fthms_server* s) {
     delete q;
   }
   for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
-  cudaStreamDestroy(s->upload);
   fthms_destroy(s->ctx);
   delete s;
   return FTHMS_OK;

@@ -22,6 +22,15 @@ constexpr double kInvPi = 0.31830988618379067153776752674502872;
 constexpr double kTwoOverPi = 0.63661977236758134307553505349005745;
 constexpr double kSqrtHalf = 0.70710678118654752440084436210484904;
 constexpr double kBesselLarge = 20.0;
+constexpr double kSqrtTwoOverPi = 0.79788456080286535587989211986876373;
+
+// Terms (k = 0..kmax of P, k = 0..kmax of Q/w) of Hankel's expansion needed at z >= 20: the first
+// omitted terms a_{2kmax+2}/z^{2kmax+2} and a_{2kmax+3}/z^{2kmax+3} stay below 2^-54 from these
+// bounds on (below 24.2 the 9-term sum is the one checked against arbitrary-precision values).
+__device__ __forceinline__ int hankel_terms(float z) {
+  return z >= 467.f ? 2 : z >= 135.f ? 3 : z >= 67.7f ? 4 : z >= 44.2f ? 5 : z >= 33.5f ? 6 : z >= 27.7f ? 7
+       : z >= 24.2f ? 8 : 9;
+}
 
 // Hankel coefficients a_k (filled by init_constants(); this header is included by one translation
 // unit only).

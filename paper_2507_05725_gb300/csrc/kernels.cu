@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(256) k_assemble_self(DevJob J) {
   const int lsw = max(s0.l, (int)ceil(kBesselLarge * inv_u));         // first l with z >= 20
   const int lend = s0.l + nb;
   const double zmin = (lsw * J.h) * R;
-  const int kmax = zmin >= 100.0 ? 4 : (zmin >= 50.0 ? 5 : (zmin >= 30.0 ? 7 : 9));
+  const int kmax = hankel_terms((float)zmin);
   for (int l = s0.l; l < min(lsw, lend); ++l) {
     const int b = l - s0.l;
     const double z = (l * J.h) * R;
@@ -593,68 +593,80 @@ __global__ void __launch_bounds__(kAsmThreads) k_cross_assemble(DevJob J) {
     }
     __syncthreads();
   }
-  const double w = kPiD / N;
+  const double w = kPiD / N, qw = 0.25 * w, invw = N * kInvPi;
+  const double A1 = -0.5 * kInvPi * w;          // coefficient of ln l below z = 20
+  const double camp = kSqrtTwoOverPi * qw;      // sqrt(2/pi) w/4
+  const double inv_h = 1.0 / J.h;
   const int ld = pr.nrows;   // blocks are stored source-major: E[i * nrows + row]
-  // 1/l and 1/sqrt(l) over the band, for the far-field recurrence below
-  double* invl = Wn + kAsmRows * N;          // <= kAsmBand
+  const int nl = task.l1 - task.l0 + 1;
+  // per-band tables: 1/l, 1/sqrt(l), ln l and omega_l = l h
+  double* invl = Wn + kAsmRows * N;          // <= kAsmBand each
   double* rsql = invl + kAsmBand;
   double* lnl = rsql + kAsmBand;
-  for (int l = task.l0 + threadIdx.x; l <= task.l1; l += kAsmThreads) {
-    invl[l - task.l0] = 1.0 / l;
-    rsql[l - task.l0] = rsqrt((double)l);
-    lnl[l - task.l0] = log((double)l);
+  double* lh = lnl + kAsmBand;
+  for (int b = threadIdx.x; b < nl; b += kAsmThreads) {
+    const int l = task.l0 + b;
+    invl[b] = 1.0 / l;
+    rsql[b] = rsqrt((double)l);
+    lnl[b] = log((double)l);
+    lh[b] = l * J.h;
   }
   __syncthreads();
+  const long long* eo = J.e_off + (long long)task.pair * J.L;
   for (int e = threadIdx.x; e < task.nrows * N; e += kAsmThreads) {
     const int r = e % task.nrows, i = e / task.nrows;
     const CrossTgt t = tg[r];
     const double dx = t.x - J.node_x[pn.off + i], dy = t.y - J.node_y[pn.off + i];
-    const double R = sqrt(fma(dx, dx, dy * dy));
-    const long long pos = (long long)i * ld + task.row0 + r;
-    if (t.near) {
-      const double wn = Wn[r * N + i];
-      const double dts = fabs(t.tstar - J.node_t[pn.off + i]);
-      for (int l = task.l0; l <= task.l1; ++l) {
-        double K1;
-        double2 K2;
-        log_split((l * J.h) * R, dts, K1, K2);
-        store_entry(J, J.E + J.e_off[(long long)task.pair * J.L + l] + pos, make_double2(fma(K1, wn, K2.x * w), K2.y * w));
-      }
-      continue;
-    }
-    // Far rule.  Above z = 20 the Hankel expansion's phase advances by the fixed rotation e^{i h R}
-    // from one frequency to the next (re-seeded by sincos every 16 steps); 1/z = (1/(hR))(1/l) and
-    // sqrt(2/(pi z)) = sqrt(2/(pi hR))/sqrt(l) come from per-band tables; the number of asymptotic
-    // terms follows the smallest z of the band.  The regime switch is an integer frequency index.
+    const double R2 = fma(dx, dx, dy * dy);
+    const double rinv = rsqrt(R2);
+    const double R0 = R2 * rinv;
+    const double R = fma(fma(-R0, R0, R2), 0.5 * rinv, R0);   // one Newton step on sqrt(R2)
     const double hR = J.h * R;
-    const double inv_u = 1.0 / hR;
-    const double ampw = sqrt(kTwoOverPi * inv_u) * (0.25 * w);
-    const int lsw = max(task.l0, (int)ceil(kBesselLarge * inv_u));   // first l with z >= 20
-    const double lhr = lsw > task.l0 ? log(0.5 * hR) + kEulerGamma : 0.0;   // ln(z/2) + gamma - ln l
+    const double inv_u = rinv * inv_h;                        // 1 / (h R)
+    const int lsw = max(task.l0, (int)ceil(fmin(kBesselLarge * inv_u, 1.0e9)));   // first l with z >= 20
+    // Every entry, near or far, is E = (alpha J0 - (w/4) Y, (w/4) J0) with Y = Yhat0 below z = 20
+    // and Y0 above; alpha = A0 + A1 ln l below 20 and beta w/4 above.
+    //   far rule:  A0 = -(w/(2 pi)) (ln(hR/2) + gamma),  beta = 0;
+    //   near rule: the log-singular part K1 ln|t* - s| is integrated with the weights wn instead of
+    //              w, so A0 = -(wn + w (ln(hR/2) + gamma - ln|t* - t_i|))/(2 pi) and
+    //              beta = -(2/pi)(wn/w - ln|t* - t_i|).
+    double A0 = 0.0, beta = 0.0, wn = 0.0, lt = 0.0;
+    if (t.near) {
+      wn = Wn[r * N + i];
+      lt = log(fabs(t.tstar - J.node_t[pn.off + i]));
+      beta = -kTwoOverPi * fma(wn, invw, -lt);
+    }
+    if (lsw > task.l0) A0 = -0.5 * kInvPi * fma(w, log(0.5 * hR) + kEulerGamma - lt, wn);
+    double2* Ep = J.E + (long long)i * ld + task.row0 + r;
+    const int lend = min(lsw, task.l1 + 1);
+    for (int l = task.l0; l < lend; ++l) {
+      const int b = l - task.l0;
+      double J0, Yh;
+      bessel0_taylor(lh[b] * R, J0, Yh);
+      const double alpha = fma(A1, lnl[b], A0);
+      store_entry(J, Ep + eo[l], make_double2(fma(alpha, J0, -qw * Yh), qw * J0));
+    }
+    if (lsw > task.l1) continue;
+    // Above z = 20 the Hankel expansion's phase advances by the fixed rotation e^{i h R} from one
+    // frequency to the next (re-seeded by sincos every 16 steps); 1/z = (1/(hR))(1/l) and
+    // sqrt(2/(pi z)) = sqrt(2/(pi hR))/sqrt(l) come from the band tables; the number of terms
+    // follows the smallest z of the band.
+    const double ampw = rsqrt(hR) * camp;
     double su, cu;
     sincos(hR, &su, &cu);
-    const double zmin = (lsw * J.h) * R;
-    const int kmax = zmin >= 100.0 ? 4 : (zmin >= 50.0 ? 5 : (zmin >= 30.0 ? 7 : 9));
+    const int kmax = hankel_terms((float)(lh[lsw - task.l0] * R));
     double cx = 0.0, sx = 0.0;
     int since = 16;
-    double2* Ep = J.E + pos;
-    const long long* eo = J.e_off + (long long)task.pair * J.L;
-    for (int l = task.l0; l < min(lsw, task.l1 + 1); ++l) {
-      const double z = (l * J.h) * R;
-      double J0, Yh;
-      bessel0_taylor(z, J0, Yh);
-      const double Y0 = fma(kTwoOverPi * (lnl[l - task.l0] + lhr), J0, Yh);
-      store_entry(J, Ep + eo[l], make_double2(-0.25 * w * Y0, 0.25 * w * J0));
-    }
     for (int l = lsw; l <= task.l1; ++l) {
+      const int b = l - task.l0;
       if (since >= 16) {
         double s, c;
-        sincos((l * J.h) * R, &s, &c);
+        sincos(lh[b] * R, &s, &c);
         cx = (c + s) * kSqrtHalf;                        // cos(z - pi/4)
         sx = (s - c) * kSqrtHalf;                        // sin(z - pi/4)
         since = 0;
       }
-      const double wz = inv_u * invl[l - task.l0];
+      const double wz = inv_u * invl[b];
       const double w2 = -wz * wz;
       double P = c_hank_a[2 * kmax], Qa = c_hank_a[2 * kmax + 1];
       for (int k = kmax - 1; k >= 0; --k) {
@@ -662,8 +674,10 @@ __global__ void __launch_bounds__(kAsmThreads) k_cross_assemble(DevJob J) {
         Qa = fma(Qa, w2, c_hank_a[2 * k + 1]);
       }
       Qa *= wz;
-      const double a = ampw * rsql[l - task.l0];
-      store_entry(J, Ep + eo[l], make_double2(-a * fma(P, sx, -Qa * cx), a * fma(P, cx, Qa * sx)));
+      const double a = ampw * rsql[b];
+      const double t1 = fma(P, cx, Qa * sx);             // J0 / a
+      const double t2 = fma(P, sx, -Qa * cx);            // Y0 / a
+      store_entry(J, Ep + eo[l], make_double2(a * fma(beta, t1, -t2), a * t1));
       const double cn = fma(cx, cu, -sx * su);
       sx = fma(sx, cu, cx * su);
       cx = cn;
@@ -1210,7 +1224,7 @@ cudaError_t launch_lu(const DevJob& J, cudaStream_t st, int* launches) {
 
 cudaError_t launch_cross_assemble(const DevJob& J, cudaStream_t st, int* launches) {
   if (J.n_asm == 0) return cudaSuccess;
-  size_t sh = ((size_t)(4 + 2 * kAsmRows) * J.max_n + 3 * kAsmBand) * sizeof(double);
+  size_t sh = ((size_t)(4 + 2 * kAsmRows) * J.max_n + 4 * kAsmBand) * sizeof(double);
   cudaError_t e = cudaFuncSetAttribute(k_cross_assemble, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
   if (e != cudaSuccess) return e;
   k_cross_assemble<<<J.n_asm, kAsmThreads, sh, st>>>(J);

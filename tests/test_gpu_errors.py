@@ -64,3 +64,18 @@ def test_wait_poll_and_results_after_completion(F):
     assert e.value.status == F.FTHMS_EINVAL
     job.release()
     F.fthms_destroy(ctx)
+
+
+def test_destroying_a_context_detaches_its_live_jobs(F):
+    """A job that outlives its context: destroy waits for it and frees its device memory; the
+    handle then accepts release only."""
+    ctx = F.fthms_create(0, 0, None)
+    m = F.Marshalled(wl.random_small(3))
+    req = F.fthms_prepare(ctx, m)
+    F.fthms_run(req)
+    F.fthms_destroy(ctx)
+    st, msg = _status(F, lambda: F.fthms_run(req))
+    assert st == F.FTHMS_EINVAL and "context was destroyed" in msg
+    st, _ = _status(F, lambda: F.fthms_wait(req, 0))
+    assert st == F.FTHMS_EINVAL
+    F.fthms_release(req)

@@ -90,6 +90,9 @@ def _parity(F, ctx, problem):
                     r = ref.phi[(m, j, l)][q]
                     nm += float(np.sum(np.abs(d[l] - r) ** 2))
                     dm += float(np.sum(np.abs(r) ** 2))
+        if dm == 0.0:            # no cross fields (a lone arc): every later step is exactly zero
+            assert nm == 0.0, (m, nm)
+            continue
         assert math.sqrt(nm / dm) < DENSITY_TOL, (m, math.sqrt(nm / dm))
         num += nm
         den += dm
