@@ -31,9 +31,22 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 METRIC = "arc-ω BIE solves/s at ≤1e-10 rel err, served+batched vs plain FP64; p50/p99 ms"
+
+
+def _hbm_peak_gbs():
+    """Measured copy bandwidth of this GPU type (MEASURED_PEAKS.json), else the 6.8 TB/s fallback."""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0
+
+
+HBM_PEAK_GBS = _hbm_peak_gbs()
 FP64_PEAK_GFLOPS = 152 * 4 * 2.07  # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz max SM clock
-# Algorithmic FP64 flops of one stored kernel entry: one far-field Hankel step at the fewest asymptotic
-# terms (5 + 5 Horner FMAs, 1/z and 1/z^2, the amplitude, the two components, the phase rotation).
+# Algorithmic FP64 flops of one stored kernel entry: one far-field Hankel step at four asymptotic terms, the
+# most common count at this workload (4 + 4 Horner FMAs, 1/z and 1/z^2, the amplitude, the two components,
+# the phase rotation).
 FLOPS_PER_KERNEL_ENTRY = 34
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_config2_small.md")
 
@@ -366,19 +379,30 @@ def ours(args):
                             "solve": st_["solve_flops"] / M,
                             "cross_assemble": FLOPS_PER_KERNEL_ENTRY * st_["cross_entries"],
                             "assemble_self": FLOPS_PER_KERNEL_ENTRY * self_entries}
-        kname = {"cross_apply": "k_cross_apply", "cross_assemble": "k_cross_assemble", "lu": "k_lu",
-                 "solve": "k_solve", "assemble_self": "k_assemble_self"}.get(dom)
+        kname = {"cross_apply": "k_cross_apply_df" if mixed else "k_cross_apply",
+                 "cross_assemble": "k_cross_assemble", "lu": "k_lu",
+                 "solve": "k_solve_mixed" if mixed else "k_solve", "assemble_self": "k_assemble_self"}.get(dom)
         tpu = measured_traffic_per_unit()
-        traffic = tpu[kname] * units[dom] if (kname in tpu and dom in units and dom in fp64_stages) else None
-        r = {"bound": "alu", "achieved": None, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": None,
-             "traffic": traffic, "kernel": dom,
-             "note": "FP64 pipe peak derived from the unit counts and clock: 152 SMs x 4 flop/clk x 2.07 GHz; "
-                     "algorithmic flops per launch / CUDA-event time on the library stream"}
+        traffic = tpu[kname] * units[dom] if (kname in tpu and dom in units) else None
         if dom in flops_per_launch and dom in fp64_stages:
             ach = flops_per_launch[dom] / (per_launch_ms * 1e-3) / 1e9
-            r.update({"achieved": ach, "frac": ach / FP64_PEAK_GFLOPS,
-                      "algorithmic_flops_per_launch": flops_per_launch[dom], "ms_per_launch": per_launch_ms})
-        return r
+            return {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                    "frac": ach / FP64_PEAK_GFLOPS, "traffic": traffic, "kernel": kname,
+                    "algorithmic_flops_per_launch": flops_per_launch[dom], "ms_per_launch": per_launch_ms,
+                    "note": "FP64 pipe peak derived from the unit counts and clock: 152 SMs x 4 flop/clk x "
+                            "2.07 GHz; algorithmic flops per launch / CUDA-event time on the library stream"}
+        # Mixed form: the solve and the cross apply stream stored matrices (FP32 factor + double-float
+        # matrix, double-float cross entries); algorithmic bytes = every stored matrix read once.
+        bytes_per_launch = {"solve": 24.0 * sum_n2, "cross_apply": 16.0 * st_["cross_entries"]}
+        if dom in bytes_per_launch:
+            ach = bytes_per_launch[dom] / (per_launch_ms * 1e-3) / 1e9
+            return {"bound": "hbm", "achieved": ach, "peak": HBM_PEAK_GBS, "unit": "GB/s",
+                    "frac": ach / HBM_PEAK_GBS, "traffic": traffic, "kernel": kname,
+                    "algorithmic_bytes_per_launch": bytes_per_launch[dom], "ms_per_launch": per_launch_ms,
+                    "note": "peak: measured copy bandwidth (of measured); algorithmic bytes = each stored "
+                            "matrix read once per launch (refinement re-reads count as excess)"}
+        return {"bound": "alu", "achieved": None, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": None,
+                "traffic": traffic, "kernel": kname, "note": "no roofline model for this stage"}
 
     roofline_plain = roofline_of(stages, st, False)
     roofline_mixed = roofline_of(stages_mx, st_mx, True)

@@ -141,8 +141,11 @@ def chi(arc, t, c0=1.0 / 3.0, c1=2.0 / 3.0):
 
 
 def node_count(problem, arc_len, omega):
-    """Per-arc node count: N_fixed, else max(N_min, ceil(N_ppw * omega * length) + N_off)."""
+    """Per-arc node count: N_fixed, else max(N_min, ceil(N_ppw * omega * length - 1e-9) + N_off).
+    The ceiling is taken 1e-9 below the product so that a product that is an integer in exact
+    arithmetic (equal arcs of a circle at a grid frequency) gives that integer whatever the last bit
+    of the quadrature length."""
     o = problem["options"]
     if o["N_fixed"] > 0:
         return int(o["N_fixed"])
-    return max(int(o["N_min"]), int(math.ceil(o["N_ppw"] * omega * arc_len)) + int(o["N_off"]))
+    return max(int(o["N_min"]), int(math.ceil(o["N_ppw"] * omega * arc_len - 1e-9)) + int(o["N_off"]))

@@ -778,6 +778,42 @@ __global__ void __launch_bounds__(kApplyThreads) k_cross_apply(DevJob J) {
 // until the relative correction is below 1e-11 or kRefineMax steps.  One warp per system.
 constexpr int kRefineMax = 3;
 
+// Rows i0, i0 + 32, ..., i0 + 32 (U - 1) of r = G - A phi in double-float, A column-major (float4
+// per entry), phi a shared-memory broadcast.  A row past N (the last slot of some lanes) is computed
+// on a valid row and not stored, so every lane runs the same instruction stream.
+template <int U>
+__device__ __forceinline__ void residual_rows(const float4* __restrict__ Adf, const double2* __restrict__ G,
+                                              const float4* pq, float2* b, int N, int i0) {
+  dfacc re[U], im[U];
+  int row[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int i = i0 + 32 * u;
+    row[u] = i < N ? i : (i0 < N ? i0 : N - 1);
+    const float4 gd = df_split2(G[row[u]]);
+    re[u].add(gd.x, gd.y);
+    im[u].add(gd.z, gd.w);
+  }
+#pragma unroll 2
+  for (int j = 0; j < N; ++j) {
+    const float4 x = pq[j];
+    const float4* Aj = Adf + (long long)j * N;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const float4 a = __ldg(&Aj[row[u]]);
+      cdf_mac(re[u], im[u], make_float4(-a.x, -a.y, -a.z, -a.w), x);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int i = i0 + 32 * u;
+    if (i < N) {
+      const df rr = re[u].value(), ri = im[u].value();
+      b[i] = make_float2(rr.hi + rr.lo, ri.hi + ri.lo);
+    }
+  }
+}
+
 __global__ void __launch_bounds__(32 * kSolveWarps) k_solve_mixed(DevJob J, int m) {
   extern __shared__ __align__(16) unsigned char shm_raw[];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -803,51 +839,16 @@ __global__ void __launch_bounds__(32 * kSolveWarps) k_solve_mixed(DevJob J, int 
   __syncwarp();
   double rel = 1.0;
   for (int it = 0; it < kRefineMax; ++it) {
-    // r = G - A phi, four rows per lane in flight (independent compensated sums)
+    // r = G - A phi, up to four rows per lane in flight (independent compensated sums)
     for (int q = 0; q < Q; ++q) {
-      const float4* pq = ph + q * N;
-      for (int i0 = lane; i0 < N; i0 += 4 * 32) {
-        dfacc re[4], im[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int i = i0 + 32 * u;
-          if (i < N) {
-            const float4 gd = df_split2(G[q * N + i]);
-            re[u].add(gd.x, gd.y);
-            im[u].add(gd.z, gd.w);
-          }
-        }
-        const int nu = min(4, (N - i0 + 31) / 32);
-        if (nu == 4) {
-#pragma unroll 2
-          for (int j = 0; j < N; ++j) {
-            const float4 x = pq[j];
-            const float4* Aj = Adf + (long long)j * N + i0;
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              const float4 a = __ldg(&Aj[32 * u]);
-              cdf_mac(re[u], im[u], make_float4(-a.x, -a.y, -a.z, -a.w), x);
-            }
-          }
-        } else {
-          for (int j = 0; j < N; ++j) {
-            const float4 x = pq[j];
-            const float4* Aj = Adf + (long long)j * N + i0;
-            for (int u = 0; u < nu; ++u) {
-              if (i0 + 32 * u < N) {
-                const float4 a = __ldg(&Aj[32 * u]);
-                cdf_mac(re[u], im[u], make_float4(-a.x, -a.y, -a.z, -a.w), x);
-              }
-            }
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int i = i0 + 32 * u;
-          if (i < N) {
-            const df rr = re[u].value(), ri = im[u].value();
-            b[q * N + i] = make_float2(rr.hi + rr.lo, ri.hi + ri.lo);
-          }
+      const int slots = (N + 31) / 32;                  // rows per lane, the same for the whole warp
+      for (int s0 = 0; s0 < slots; s0 += 4) {
+        const int i0 = lane + 32 * s0;
+        switch (min(4, slots - s0)) {
+          case 4: residual_rows<4>(Adf, G + q * N, ph + q * N, b + q * N, N, i0); break;
+          case 3: residual_rows<3>(Adf, G + q * N, ph + q * N, b + q * N, N, i0); break;
+          case 2: residual_rows<2>(Adf, G + q * N, ph + q * N, b + q * N, N, i0); break;
+          default: residual_rows<1>(Adf, G + q * N, ph + q * N, b + q * N, N, i0); break;
         }
       }
     }

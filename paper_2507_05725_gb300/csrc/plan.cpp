@@ -273,7 +273,7 @@ int build_plan(const fthms_curve* curves, int ncurves, const fthms_arc* arcs, in
     for (int l = 1; l < p.L; ++l) {
       double omega = l * p.h;
       int N = opt->N_fixed > 0 ? opt->N_fixed
-                               : std::max(opt->N_min, (int)std::ceil(opt->N_ppw * omega * p.arcs[j].length) + opt->N_off);
+                               : std::max(opt->N_min, (int)std::ceil(opt->N_ppw * omega * p.arcs[j].length - 1e-9) + opt->N_off);
       if (N < 2 || N > 800) {
         snprintf(buf, sizeof buf, "arc %d omega index %d: node count %d outside [2, 800] (shared-memory panel of the LU)", j, l, N);
         err = buf;

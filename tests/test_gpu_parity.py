@@ -149,6 +149,7 @@ def test_config2_full_size_sampled(F, ctx):
     problem = wl.config2(M=2)
     job = F.Job(ctx, problem).run().wait()
     S = Setup(problem)
+    assert np.array_equal(job.node_counts(), S.Ntab[:, 1:])   # every (arc, omega), so every transfer mesh
     tg = S.grid
     sig = problem["signal"]
     rng = np.random.default_rng(0)
