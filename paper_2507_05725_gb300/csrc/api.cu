@@ -186,6 +186,7 @@ fthms_status upload_job(fthms_req* r) {
   J.mat_total = p.mat_total;
 
   TRY(dev_upload(r, p.sys, &J.sys));
+  TRY(dev_upload(r, p.sys_order, &J.sys_order));
   TRY(dev_upload(r, p.panels, &J.panels));
   TRY(dev_upload(r, p.node_t, &J.node_t));
   TRY(dev_upload(r, p.node_x, &J.node_x));

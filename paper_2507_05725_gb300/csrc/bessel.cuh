@@ -32,6 +32,39 @@ __device__ __forceinline__ int hankel_terms(float z) {
        : z >= 24.2f ? 8 : 9;
 }
 
+// sin x and cos x for |x| <= 1 from their Taylor series (x^21/21! and x^22/22! < 2e-20 bound the
+// truncation), by Horner's rule in u = x^2 with the coefficients (-1)^k/(2k+1)! and (-1)^k/(2k)!.
+// Used for the per-pair phase step e^{i h R}, whose argument is small.
+__device__ __forceinline__ void sincos_taylor(double x, double& s, double& c) {
+  constexpr double f3 = 6.0, f5 = f3 * 20.0, f7 = f5 * 42.0, f9 = f7 * 72.0, f11 = f9 * 110.0,
+                   f13 = f11 * 156.0, f15 = f13 * 210.0, f17 = f15 * 272.0, f19 = f17 * 342.0;
+  constexpr double f2 = 2.0, f4 = f2 * 12.0, f6 = f4 * 30.0, f8 = f6 * 56.0, f10 = f8 * 90.0,
+                   f12 = f10 * 132.0, f14 = f12 * 182.0, f16 = f14 * 240.0, f18 = f16 * 306.0,
+                   f20 = f18 * 380.0;
+  const double u = x * x;
+  double ps = -1.0 / f19;
+  ps = fma(ps, u, 1.0 / f17);
+  ps = fma(ps, u, -1.0 / f15);
+  ps = fma(ps, u, 1.0 / f13);
+  ps = fma(ps, u, -1.0 / f11);
+  ps = fma(ps, u, 1.0 / f9);
+  ps = fma(ps, u, -1.0 / f7);
+  ps = fma(ps, u, 1.0 / f5);
+  ps = fma(ps, u, -1.0 / f3);
+  s = fma(x * u, ps, x);
+  double pc = 1.0 / f20;
+  pc = fma(pc, u, -1.0 / f18);
+  pc = fma(pc, u, 1.0 / f16);
+  pc = fma(pc, u, -1.0 / f14);
+  pc = fma(pc, u, 1.0 / f12);
+  pc = fma(pc, u, -1.0 / f10);
+  pc = fma(pc, u, 1.0 / f8);
+  pc = fma(pc, u, -1.0 / f6);
+  pc = fma(pc, u, 1.0 / f4);
+  pc = fma(pc, u, -1.0 / f2);
+  c = fma(u, pc, 1.0);
+}
+
 // Hankel coefficients a_k (filled by init_constants(); this header is included by one translation
 // unit only).
 __constant__ double c_hank_a[20];

@@ -212,7 +212,8 @@ __global__ void __launch_bounds__(256) k_assemble_self(DevJob J) {
   const double qw = 0.25 * w;
   const double inv_u = 1.0 / hR, amp_u = sqrt(kTwoOverPi * inv_u);
   double su, cu;
-  sincos(hR, &su, &cu);
+  if (hR <= 1.0) sincos_taylor(hR, su, cu);
+  else sincos(hR, &su, &cu);
   const int lsw = max(s0.l, (int)ceil(kBesselLarge * inv_u));         // first l with z >= 20
   const int lend = s0.l + nb;
   const double zmin = (lsw * J.h) * R;
@@ -285,7 +286,7 @@ __global__ void __launch_bounds__(kLuThreads) k_lu(DevJob J) {
   using Real = typename CTraits<C>::R;
   extern __shared__ __align__(16) unsigned char shl_raw[];
   C* shl = reinterpret_cast<C*>(shl_raw);
-  const SysDesc s = J.sys[blockIdx.x];
+  const SysDesc s = J.sys[J.sys_order[blockIdx.x]];
   const int N = s.N;
   C* A = (sizeof(C) == sizeof(double2) ? reinterpret_cast<C*>(J.A) : reinterpret_cast<C*>(J.LU32)) + s.mat_off;
   int* piv = J.piv + s.piv_off;
@@ -445,6 +446,39 @@ __global__ void __launch_bounds__(kLuThreads) k_lu(DevJob J) {
 // ceil(N/32) dependent steps per sweep instead of N.  Both factors have a unit diagonal (U was scaled
 // and D^{-1} is applied between the sweeps).  C = double2 (FP64 factors) or float2 (FP32 factors).
 constexpr int kSolveWarps = 4;
+constexpr int kSolveMinBlocks = 6;   // resident blocks per SM the register budget must allow
+
+// Rows i0 and i0 + 32 of b -= T[:, r0..r0+w) x with x = b[r0..r0+w), column-major T of leading
+// dimension N.  Each batch of 8 columns issues the loads of both rows before their FMAs, so a lane has
+// 16 independent loads in flight instead of walking its rows one after another.  A second row past
+// `end` is computed on the first and not stored.
+template <class C>
+__device__ __forceinline__ void tri_update2(C* bq, const C* __restrict__ A, int N, int r0, int w, int i0, int end) {
+  const int i1 = i0 + 32 < end ? i0 + 32 : i0;
+  C a0 = bq[i0], a1 = bq[i1];
+#pragma unroll 1
+  for (int c0 = 0; c0 < kSB; c0 += 8) {
+    C v0[8], v1[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      if (c0 + k < w) {
+        const C* col = A + (long long)(r0 + c0 + k) * N;
+        v0[k] = __ldg(&col[i0]);
+        v1[k] = __ldg(&col[i1]);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      if (c0 + k < w) {
+        const C x = bq[r0 + c0 + k];
+        a0 = cfms(v0[k], x, a0);
+        a1 = cfms(v1[k], x, a1);
+      }
+    }
+  }
+  bq[i0] = a0;
+  if (i0 + 32 < end) bq[i0 + 32] = a1;
+}
 
 template <class C>
 __device__ void tri_solve(C* b, int Q, int N, const C* __restrict__ A, const int* __restrict__ piv,
@@ -464,20 +498,22 @@ __device__ void tri_solve(C* b, int Q, int N, const C* __restrict__ A, const int
       C x = C{};
       if (lane < w) {
         x = bq[r0 + lane];
-#pragma unroll 8
-        for (int c = 0; c < kSB; ++c)
-          if (c < lane && c < w) x = cfms(make_neg(__ldg(&A[(long long)(r0 + c) * N + r0 + lane])), bq[r0 + c], x);
+#pragma unroll 1
+        for (int h = 0; h < kSB; h += 16) {        // 16 loads in flight, then their FMAs
+          C v[16];
+#pragma unroll
+          for (int k = 0; k < 16; ++k)
+            if (h + k < lane) v[k] = __ldg(&A[(long long)(r0 + h + k) * N + r0 + lane]);
+#pragma unroll
+          for (int k = 0; k < 16; ++k)
+            if (h + k < lane) x = cfms(make_neg(v[k]), bq[r0 + h + k], x);
+        }
       }
       __syncwarp();
       if (lane < w) bq[r0 + lane] = x;
       __syncwarp();
-      for (int i = r1 + lane; i < N; i += 32) {
-        C acc = bq[i];
-#pragma unroll 8
-        for (int c = 0; c < kSB; ++c)
-          if (c < w) acc = cfms(__ldg(&A[(long long)(r0 + c) * N + i]), bq[r0 + c], acc);
-        bq[i] = acc;
-      }
+#pragma unroll 1
+      for (int i0 = r1 + lane; i0 < N; i0 += 64) tri_update2(bq, A, N, r0, w, i0, N);
       __syncwarp();
     }
   }
@@ -490,20 +526,22 @@ __device__ void tri_solve(C* b, int Q, int N, const C* __restrict__ A, const int
       C x = C{};
       if (lane < w) {
         x = bq[r0 + lane];
-#pragma unroll 8
-        for (int c = 0; c < kSB; ++c)
-          if (c > lane && c < w) x = cfms(make_neg(__ldg(&A[(long long)(r0 + c) * N + r0 + lane])), bq[r0 + c], x);
+#pragma unroll 1
+        for (int h = 0; h < kSB; h += 16) {
+          C v[16];
+#pragma unroll
+          for (int k = 0; k < 16; ++k)
+            if (h + k > lane && h + k < w) v[k] = __ldg(&A[(long long)(r0 + h + k) * N + r0 + lane]);
+#pragma unroll
+          for (int k = 0; k < 16; ++k)
+            if (h + k > lane && h + k < w) x = cfms(make_neg(v[k]), bq[r0 + h + k], x);
+        }
       }
       __syncwarp();
       if (lane < w) bq[r0 + lane] = x;
       __syncwarp();
-      for (int i = lane; i < r0; i += 32) {
-        C acc = bq[i];
-#pragma unroll 8
-        for (int c = 0; c < kSB; ++c)
-          if (c < w) acc = cfms(__ldg(&A[(long long)(r0 + c) * N + i]), bq[r0 + c], acc);
-        bq[i] = acc;
-      }
+#pragma unroll 1
+      for (int i0 = lane; i0 < r0; i0 += 64) tri_update2(bq, A, N, r0, w, i0, r0);
       __syncwarp();
     }
   }
@@ -512,8 +550,9 @@ __device__ void tri_solve(C* b, int Q, int N, const C* __restrict__ A, const int
 __global__ void __launch_bounds__(32 * kSolveWarps) k_solve(DevJob J, int m) {
   extern __shared__ double2 shs[];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int sidx = blockIdx.x * kSolveWarps + wid;
-  if (sidx >= J.nsys) return;
+  const int slot = blockIdx.x * kSolveWarps + wid;
+  if (slot >= J.nsys) return;
+  const int sidx = J.sys_order[slot];
   const SysDesc s = J.sys[sidx];
   const int N = s.N, Q = J.Q;
   double2* b = shs + (size_t)wid * Q * J.max_n;
@@ -534,7 +573,7 @@ __global__ void __launch_bounds__(32 * kSolveWarps) k_solve(DevJob J, int m) {
 
 // ---------------------------------------------------------------------------------------------
 // Cross assembly: stored rows of S_Gamma_j for one (pair, frequency band, 8-row chunk).
-constexpr int kAsmThreads = 256;
+constexpr int kAsmThreads = 128;   // small blocks: an 8-row task leaves a short last pass
 constexpr int kAsmRows = 8;
 
 // A stored cross entry: FP64, or double-float (float4, same 16 bytes) in the mixed-precision form.
@@ -653,7 +692,8 @@ __global__ void __launch_bounds__(kAsmThreads) k_cross_assemble(DevJob J) {
     // follows the smallest z of the band.
     const double ampw = rsqrt(hR) * camp;
     double su, cu;
-    sincos(hR, &su, &cu);
+    if (hR <= 1.0) sincos_taylor(hR, su, cu);
+    else sincos(hR, &su, &cu);
     const int kmax = hankel_terms((float)(lh[lsw - task.l0] * R));
     double cx = 0.0, sx = 0.0;
     int since = 16;
@@ -817,8 +857,9 @@ __device__ __forceinline__ void residual_rows(const float4* __restrict__ Adf, co
 __global__ void __launch_bounds__(32 * kSolveWarps) k_solve_mixed(DevJob J, int m) {
   extern __shared__ __align__(16) unsigned char shm_raw[];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int sidx = blockIdx.x * kSolveWarps + wid;
-  if (sidx >= J.nsys) return;
+  const int slot = blockIdx.x * kSolveWarps + wid;
+  if (slot >= J.nsys) return;
+  const int sidx = J.sys_order[slot];
   const SysDesc s = J.sys[sidx];
   const int N = s.N, Q = J.Q;
   const size_t per = (size_t)Q * J.max_n;

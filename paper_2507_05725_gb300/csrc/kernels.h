@@ -19,6 +19,7 @@ struct DevJob {
   double z0x, z0y, dirx, diry, amp, carrier, centre, width;
   // tables
   const SysDesc* sys;
+  const int* sys_order;       // systems by decreasing N (launch order of k_lu and the solves)
   const Panel* panels;
   const double *node_t, *node_x, *node_y, *node_sp;
   const int* rlogN;

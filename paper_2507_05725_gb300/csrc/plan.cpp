@@ -353,6 +353,10 @@ int build_plan(const fthms_curve* curves, int ncurves, const fthms_arc* arcs, in
     p.rlog_total += (long long)kv.first * kv.first;
   }
   for (auto& s : p.sys) s.rlog_off = rlog_map[s.N];
+  // Largest systems first, so that the last wave of the per-system kernels holds the small ones.
+  p.sys_order.resize(p.sys.size());
+  for (size_t s = 0; s < p.sys.size(); ++s) p.sys_order[s] = (int)s;
+  std::stable_sort(p.sys_order.begin(), p.sys_order.end(), [&](int a, int b) { return p.sys[a].N > p.sys[b].N; });
 
   // Transfer meshes, chi and the active (chi > 0) nodes.
   p.tpanel.resize(p.P);
@@ -493,7 +497,7 @@ size_t plan_device_bytes(const Plan& p) {
   b += (size_t)p.restr_total * 8;
   b += (size_t)p.n_obs * p.Q * p.L * 16 + (size_t)p.n_obs * p.n_tout * 8;
   b += p.node_t.size() * 32 + p.tgts.size() * sizeof(CrossTgt) + p.blks.size() * sizeof(CrossBlk) +
-       p.asms.size() * sizeof(CrossAsm) + p.self_tiles.size() * sizeof(SelfTile) + p.sys.size() * sizeof(SysDesc);
+       p.asms.size() * sizeof(CrossAsm) + p.self_tiles.size() * sizeof(SelfTile) + p.sys.size() * (sizeof(SysDesc) + sizeof(int));
   b += p.win.size() * 8 + (size_t)p.Q * p.L * 32 + (size_t)p.K * 8 + p.chi.size() * 8;
   return b;
 }

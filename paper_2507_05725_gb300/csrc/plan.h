@@ -43,6 +43,7 @@ struct Plan {
   int maxN = 0;
 
   std::vector<SysDesc> sys;  // s = j*(L-1) + (l-1)
+  std::vector<int> sys_order;  // systems by decreasing N: launch order of the per-system kernels
   long long mat_total = 0, vec_total = 0, piv_total = 0;
 
   std::vector<int> rlogN;               // distinct N values
