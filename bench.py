@@ -379,7 +379,7 @@ def ours(args):
                             "solve": st_["solve_flops"] / M,
                             "cross_assemble": FLOPS_PER_KERNEL_ENTRY * st_["cross_entries"],
                             "assemble_self": FLOPS_PER_KERNEL_ENTRY * self_entries}
-        kname = {"cross_apply": "k_cross_apply_df" if mixed else "k_cross_apply",
+        kname = {"cross_apply": "k_cross_rows_df" if mixed else "k_cross_apply",
                  "cross_assemble": "k_cross_assemble", "lu": "k_lu",
                  "solve": "k_solve_mixed" if mixed else "k_solve", "assemble_self": "k_assemble_self"}.get(dom)
         tpu = measured_traffic_per_unit()
@@ -450,7 +450,8 @@ def ours(args):
                     "mixed": {"value": job_value(ws, solves, ms_mx), "ms_per_step": ms_mx,
                               "dtype": "f32 factors + double-float (2 x f32) refinement and cross apply, f64 elsewhere",
                               "rel_l2_vs_fp64_densities": mixed_err,
-                              "max_refine_resid": st_mx["max_refine_resid"], "traces_finite": ok_mx,
+                              "max_refine_resid": st_mx["max_refine_resid"],
+                              "refine_passes_per_solve": st_mx.get("refine_passes"), "traces_finite": ok_mx,
                               "roofline": roofline_mixed,
                               "gpu_launches": int(st_mx["kernel_launches"] * args.steps),
                               "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages_mx.items()},

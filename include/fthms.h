@@ -126,6 +126,7 @@ typedef struct {
   double apply_flops;     /* 8 Q M (cross + observation entries): cross matvecs of one run */
   int precision;          /* the job's precision option */
   double max_refine_resid; /* precision 1: max over systems and steps of the last relative correction */
+  double refine_passes;   /* precision 1: mean refinement passes (residual + correction) per system and step */
 } fthms_stats_t;
 
 /* Create a context on CUDA device `device` that enqueues all work on `cuda_stream` (a

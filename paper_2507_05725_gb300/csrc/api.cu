@@ -208,6 +208,17 @@ fthms_status upload_job(fthms_req* r) {
   TRY(dev_upload(r, p.asms, &J.asms));
   TRY(dev_upload(r, p.grps, &J.grps));
   TRY(dev_upload(r, p.blks, &J.blks));
+  J.n_slices = 0;
+  J.slice_ph_cap = p.slice_ph_cap;
+  J.slices = nullptr;
+  J.grp_res_off = nullptr;
+  J.apply_res = nullptr;
+  if (J.mixed) {
+    TRY(dev_upload(r, p.slices, &J.slices));
+    TRY(dev_upload(r, p.grp_res_off, &J.grp_res_off));
+    TRY(dev_alloc(r, (size_t)std::max(1LL, p.res_total) * p.Q, &J.apply_res));
+    J.n_slices = (int)p.slices.size();
+  }
   TRY(dev_upload(r, p.tpanel, &J.tpanel));
   TRY(dev_upload(r, p.tr_off, &J.tr_off));
   TRY(dev_upload(r, p.chi, &J.chi));
@@ -225,7 +236,7 @@ fthms_status upload_job(fthms_req* r) {
   TRY(dev_alloc(r, (size_t)p.piv_total, &J.dinv));
   J.LU32 = nullptr;
   J.dinv32 = nullptr;
-  TRY(dev_alloc(r, 1, &J.refine_resid));
+  TRY(dev_alloc(r, 2, &J.refine_resid));          // [0] max last correction, [1] refinement passes (u64)
   if (J.mixed) {
     TRY(dev_alloc(r, (size_t)p.mat_total, &J.LU32));
     TRY(dev_alloc(r, (size_t)p.piv_total, &J.dinv32));
@@ -335,7 +346,7 @@ fthms_status enqueue_stages(fthms_req* r, bool bracket) {
   CK(cudaMemsetAsync(J.Gt, 0, (size_t)r->plan.spec_total * sizeof(double2), st));
   CK(cudaMemsetAsync(J.W, 0, (size_t)r->plan.spec_total * sizeof(double2), st));
   CK(cudaMemsetAsync(J.Vobs, 0, (size_t)std::max(1, J.n_obs * J.Q * J.L) * sizeof(double2), st));
-  CK(cudaMemsetAsync(J.refine_resid, 0, sizeof(double), st));
+  CK(cudaMemsetAsync(J.refine_resid, 0, 2 * sizeof(double), st));
   TRY(stage(r, FTHMS_STAGE_INCIDENT, st, &nl, [&] { return launch_incident(J, st, &nl); }));
   TRY(stage(r, FTHMS_STAGE_RESTRICT, st, &nl, [&] { return launch_restrict(J, st, &nl); }));
   for (int m = 1; m <= J.M; ++m) {
@@ -621,8 +632,13 @@ fthms_status fthms_stats(fthms_req* req, fthms_stats_t* out) {
     CK(cudaEventElapsedTime(&ms, req->ev0, req->ev1));
     out->gpu_ms = ms;
     if (req->J.mixed) {
-      CK(cudaMemcpyAsync(&out->max_refine_resid, req->J.refine_resid, sizeof(double), cudaMemcpyDeviceToHost, req->stream));
+      double buf[2] = {0.0, 0.0};
+      CK(cudaMemcpyAsync(buf, req->J.refine_resid, 2 * sizeof(double), cudaMemcpyDeviceToHost, req->stream));
       CK(cudaStreamSynchronize(req->stream));
+      unsigned long long passes = 0;
+      std::memcpy(&passes, &buf[1], sizeof passes);
+      out->max_refine_resid = buf[0];
+      out->refine_passes = (double)passes / ((double)req->J.nsys * p.M);
     }
   }
   return FTHMS_OK;

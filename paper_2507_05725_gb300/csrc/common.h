@@ -50,6 +50,17 @@ struct CrossGrp {
   int blk_begin, blk_end;
 };
 
+// Row slice of a group for the double-float cross apply: rows [row0, row0 + nrows) of the group's
+// concatenated block rows, overlapping blocks b0..b1 (indices into the block list, inclusive), the
+// first of which starts at group row rowb0.
+constexpr int kApplySlice = 256;
+struct ApplySlice {
+  int grp;
+  int row0, nrows;
+  int b0, b1;
+  int rowb0;
+};
+
 // Receiver/source pair (k, j), k = P for the observation points.
 struct PairDesc {
   int k, j;

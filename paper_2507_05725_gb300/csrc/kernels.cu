@@ -602,7 +602,9 @@ __global__ void __launch_bounds__(kAsmThreads) k_cross_assemble(DevJob J) {
   __syncthreads();
   if (any_near) {
     for (int r = threadIdx.x; r < 4 * N; r += kAsmThreads) ctab[r] = cospi((double)r / (2.0 * N));
-    // lambda_n(t*) = int log|t* - s| T_n(s)/sqrt(1-s^2) ds for |t*| > 1
+    // lambda_n(t*) = int log|t* - s| T_n(s)/sqrt(1-s^2) ds for |t*| > 1, = -pi zeta^n / n (n >= 1):
+    // the sum below stops where |zeta|^n < 1e-18 (the omitted terms are below 1e-17 of the weights).
+    __shared__ int s_nlam[kAsmRows];
     if (threadIdx.x < task.nrows && tg[threadIdx.x].near) {
       const double ts = tg[threadIdx.x].tstar;
       const double rt = sqrt(fma(ts, ts, -1.0));
@@ -610,20 +612,23 @@ __global__ void __launch_bounds__(kAsmThreads) k_cross_assemble(DevJob J) {
       double* lr = lam + threadIdx.x * N;
       lr[0] = kPiD * log(0.5 * (fabs(ts) + rt));
       double pw = 1.0;
-      for (int n = 1; n < N; ++n) {
+      int n = 1;
+      for (; n < N; ++n) {
         pw *= zeta;
+        if (fabs(pw) < 1e-18) break;
         lr[n] = -kPiD * pw / n;
       }
+      s_nlam[threadIdx.x] = n;
     }
     __syncthreads();
     for (int e = threadIdx.x; e < task.nrows * N; e += kAsmThreads) {
       int r = e / N, i = e % N;
       if (!tg[r].near) continue;
       const double* lr = lam + r * N;
-      const int step = 2 * i + 1, mod = 4 * N;
+      const int step = 2 * i + 1, mod = 4 * N, nlam = s_nlam[r];
       double acc = 0.0;
       int ph = 0;
-      for (int n = 1; n < N; ++n) {
+      for (int n = 1; n < nlam; ++n) {
         ph += step;
         if (ph >= mod) ph -= mod;
         acc = fma(lr[n], ctab[ph], acc);
@@ -879,7 +884,9 @@ __global__ void __launch_bounds__(32 * kSolveWarps) k_solve_mixed(DevJob J, int 
   for (int e = lane; e < Q * N; e += 32) ph[e] = make_float4(b[e].x, 0.f, b[e].y, 0.f);
   __syncwarp();
   double rel = 1.0;
+  int passes = 0;
   for (int it = 0; it < kRefineMax; ++it) {
+    ++passes;
     // r = G - A phi, up to four rows per lane in flight (independent compensated sums)
     for (int q = 0; q < Q; ++q) {
       const int slots = (N + 31) / 32;                  // rows per lane, the same for the whole warp
@@ -916,7 +923,10 @@ __global__ void __launch_bounds__(32 * kSolveWarps) k_solve_mixed(DevJob J, int 
     rel = pmax > 0.f ? (double)dmax / (double)pmax : 0.0;
     if (rel < 1e-11) break;
   }
-  if (lane == 0) atomicMax(reinterpret_cast<unsigned long long*>(J.refine_resid), (unsigned long long)__double_as_longlong(rel));
+  if (lane == 0) {
+    atomicMax(reinterpret_cast<unsigned long long*>(J.refine_resid), (unsigned long long)__double_as_longlong(rel));
+    atomicAdd(reinterpret_cast<unsigned long long*>(J.refine_resid) + 1, (unsigned long long)passes);
+  }
   double2* out = J.phi + s.vec_off;
   double2* sum = J.phi_sum + s.vec_off;
   double2* all = J.phi_all ? J.phi_all + (long long)(m - 1) * J.vec_total + s.vec_off : nullptr;
@@ -929,79 +939,91 @@ __global__ void __launch_bounds__(32 * kSolveWarps) k_solve_mixed(DevJob J, int 
 }
 
 // Cross apply in double-float on the FP32 pipe (mixed form): E and phi as df64, compensated sums.
+// Mixed form, first half: one CTA per slice of kApplySlice rows of a group, one thread per row, the
+// row's double-float sum over its block's sources (E and phi as df64, two compensated sums).  No
+// barrier after the density staging, and many small CTAs per SM keep enough loads in flight.
 template <int Q>
-__global__ void __launch_bounds__(kApplyThreads) k_cross_apply_df(DevJob J) {
+__global__ void __launch_bounds__(kApplySlice) k_cross_rows_df(DevJob J) {
   extern __shared__ __align__(16) unsigned char shd_raw[];
-  const CrossGrp g = J.grps[blockIdx.x];
-  const int l = g.l;
-  const bool obs = g.k == J.P;
-  const int nout = obs ? J.n_obs : J.panels[J.tpanel[g.k]].N;
-  const int nb = g.blk_end - g.blk_begin;
+  float4* ph = reinterpret_cast<float4*>(shd_raw);        // df64 densities of the overlapped blocks
+  const ApplySlice sl = J.slices[blockIdx.x];
+  const int nb = sl.b1 - sl.b0 + 1;
   __shared__ int s_row0[kApplyMaxBlk + 1], s_ph0[kApplyMaxBlk + 1];
   if (threadIdx.x == 0) {
-    int r = 0, p = 0;
+    int r = sl.rowb0, p = 0;
     for (int b = 0; b < nb; ++b) {
       s_row0[b] = r;
       s_ph0[b] = p;
-      r += J.blks[g.blk_begin + b].nrows;
-      p += Q * J.blks[g.blk_begin + b].N;
+      r += J.blks[sl.b0 + b].nrows;
+      p += Q * J.blks[sl.b0 + b].N;
     }
     s_row0[nb] = r;
     s_ph0[nb] = p;
   }
   __syncthreads();
-  const int nrow = s_row0[nb];
-  double2* acc = reinterpret_cast<double2*>(shd_raw);      // [Q][nout]
-  double2* res = acc + (size_t)Q * J.acc_cap;              // [Q][nrow]
-  float4* ph = reinterpret_cast<float4*>(res + (size_t)Q * J.row_cap);   // df64 densities
-  for (int e = threadIdx.x; e < Q * nout; e += kApplyThreads) acc[e] = make_double2(0.0, 0.0);
   for (int b = 0; b < nb; ++b) {
-    const CrossBlk B = J.blks[g.blk_begin + b];
+    const CrossBlk B = J.blks[sl.b0 + b];
     const double2* p = J.phi + J.sys[B.sys].vec_off;
-    for (int e = threadIdx.x; e < Q * B.N; e += kApplyThreads) ph[s_ph0[b] + e] = df_split2(p[e]);
+    for (int e = threadIdx.x; e < Q * B.N; e += kApplySlice) ph[s_ph0[b] + e] = df_split2(p[e]);
   }
   __syncthreads();
+  if ((int)threadIdx.x >= sl.nrows) return;
+  const int row = sl.row0 + threadIdx.x;
   int b = 0;
-  for (int row = threadIdx.x; row < nrow; row += kApplyThreads) {
-    while (row >= s_row0[b + 1]) ++b;
-    const CrossBlk B = J.blks[g.blk_begin + b];
-    const int N = B.N, nr = B.nrows, r = row - s_row0[b];
-    const float4* phb = ph + s_ph0[b];
-    // two independent compensated sums (even and odd sources) halve the serial chain
-    dfacc sr[Q], si[Q], tr[Q], ti[Q];
-    const float4* __restrict__ Er = reinterpret_cast<const float4*>(J.E + B.e_off) + r;
-    int i = 0;
+  while (row >= s_row0[b + 1]) ++b;
+  const CrossBlk B = J.blks[sl.b0 + b];
+  const int N = B.N, nr = B.nrows, r = row - s_row0[b];
+  const float4* phb = ph + s_ph0[b];
+  dfacc sr[Q], si[Q], tr[Q], ti[Q];
+  const float4* __restrict__ Er = reinterpret_cast<const float4*>(J.E + B.e_off) + r;
+  int i = 0;
 #pragma unroll 2
-    for (; i + 1 < N; i += 2) {
-      const float4 e0 = __ldg(&Er[(long long)i * nr]);
-      const float4 e1 = __ldg(&Er[(long long)(i + 1) * nr]);
-#pragma unroll
-      for (int q = 0; q < Q; ++q) {
-        cdf_mac(sr[q], si[q], e0, phb[q * N + i]);
-        cdf_mac(tr[q], ti[q], e1, phb[q * N + i + 1]);
-      }
-    }
-    if (i < N) {
-      const float4 e0 = __ldg(&Er[(long long)i * nr]);
-#pragma unroll
-      for (int q = 0; q < Q; ++q) cdf_mac(sr[q], si[q], e0, phb[q * N + i]);
-    }
+  for (; i + 1 < N; i += 2) {
+    const float4 e0 = __ldg(&Er[(long long)i * nr]);
+    const float4 e1 = __ldg(&Er[(long long)(i + 1) * nr]);
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-      sr[q].add(tr[q].hi, tr[q].lo);
-      si[q].add(ti[q].hi, ti[q].lo);
-      const df a = sr[q].value(), c = si[q].value();
-      res[q * nrow + row] = make_double2((double)a.hi + (double)a.lo, (double)c.hi + (double)c.lo);
+      cdf_mac(sr[q], si[q], e0, phb[q * N + i]);
+      cdf_mac(tr[q], ti[q], e1, phb[q * N + i + 1]);
     }
   }
-  __syncthreads();
-  for (int bb = 0; bb < nb; ++bb) {
-    const CrossBlk B = J.blks[g.blk_begin + bb];
-    for (int r = threadIdx.x; r < B.nrows; r += kApplyThreads) {
-      const int out = J.tgts[B.tgt_off + r].out;
+  if (i < N) {
+    const float4 e0 = __ldg(&Er[(long long)i * nr]);
 #pragma unroll
-      for (int q = 0; q < Q; ++q) acc[q * nout + out] = cadd(acc[q * nout + out], res[q * nrow + s_row0[bb] + r]);
+    for (int q = 0; q < Q; ++q) cdf_mac(sr[q], si[q], e0, phb[q * N + i]);
+  }
+  double2* out = J.apply_res + (J.grp_res_off[sl.grp] + row) * Q;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    sr[q].add(tr[q].hi, tr[q].lo);
+    si[q].add(ti[q].hi, ti[q].lo);
+    const df a = sr[q].value(), c = si[q].value();
+    out[q] = make_double2((double)a.hi + (double)a.lo, (double)c.hi + (double)c.lo);
+  }
+}
+
+// Mixed form, second half: per group, the row sums of every source block added to their targets in
+// the fixed block order (deterministic), then W (transfer nodes) or the observation spectra.
+template <int Q>
+__global__ void __launch_bounds__(kApplyThreads) k_cross_reduce(DevJob J) {
+  extern __shared__ __align__(16) unsigned char shd_raw[];
+  const CrossGrp g = J.grps[blockIdx.x];
+  const int l = g.l;
+  const bool obs = g.k == J.P;
+  const int nout = obs ? J.n_obs : J.panels[J.tpanel[g.k]].N;
+  double2* acc = reinterpret_cast<double2*>(shd_raw);      // [Q][nout]
+  for (int e = threadIdx.x; e < Q * nout; e += kApplyThreads) acc[e] = make_double2(0.0, 0.0);
+  __syncthreads();
+  const double2* res = J.apply_res + J.grp_res_off[blockIdx.x] * Q;
+  int row0 = 0;
+  for (int bb = g.blk_begin; bb < g.blk_end; ++bb) {
+    const CrossBlk B = J.blks[bb];
+    for (int r = threadIdx.x; r < B.nrows; r += kApplyThreads) {
+      const int o = J.tgts[B.tgt_off + r].out;
+#pragma unroll
+      for (int q = 0; q < Q; ++q) acc[q * nout + o] = cadd(acc[q * nout + o], res[(row0 + r) * Q + q]);
     }
+    row0 += B.nrows;
     __syncthreads();
   }
   if (obs) {
@@ -1325,9 +1347,14 @@ cudaError_t launch_solve(const DevJob& J, int m, cudaStream_t st, int* launches)
 template <int Q>
 static cudaError_t launch_cross_apply_q(const DevJob& J, size_t sh, cudaStream_t st) {
   if (J.mixed) {
-    cudaError_t e = cudaFuncSetAttribute(k_cross_apply_df<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+    const size_t sh_rows = (size_t)Q * J.slice_ph_cap * sizeof(float4);
+    const size_t sh_red = (size_t)Q * J.acc_cap * sizeof(double2);
+    cudaError_t e = cudaFuncSetAttribute(k_cross_rows_df<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh_rows);
     if (e != cudaSuccess) return e;
-    k_cross_apply_df<Q><<<J.n_grp, kApplyThreads, sh, st>>>(J);
+    e = cudaFuncSetAttribute(k_cross_reduce<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh_red);
+    if (e != cudaSuccess) return e;
+    if (J.n_slices > 0) k_cross_rows_df<Q><<<J.n_slices, kApplySlice, sh_rows, st>>>(J);
+    k_cross_reduce<Q><<<J.n_grp, kApplyThreads, sh_red, st>>>(J);
     return cudaGetLastError();
   }
   cudaError_t e = cudaFuncSetAttribute(k_cross_apply<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
@@ -1339,7 +1366,7 @@ static cudaError_t launch_cross_apply_q(const DevJob& J, size_t sh, cudaStream_t
 cudaError_t launch_cross_apply(const DevJob& J, cudaStream_t st, int* launches) {
   if (J.n_grp == 0) return cudaSuccess;
   size_t sh = (size_t)J.Q * (J.acc_cap + J.row_cap + J.ph_cap) * sizeof(double2);
-  *launches += 1;
+  *launches += J.mixed ? 2 : 1;
   switch (J.Q) {
     case 1: return launch_cross_apply_q<1>(J, sh, st);
     case 2: return launch_cross_apply_q<2>(J, sh, st);

@@ -36,6 +36,10 @@ struct DevJob {
   const CrossAsm* asms;
   const CrossGrp* grps;
   const CrossBlk* blks;
+  const ApplySlice* slices;  // mixed-form apply: row slices of the groups
+  const long long* grp_res_off;
+  double2* apply_res;        // [group rows][Q] per-row cross sums (mixed form)
+  int n_slices, slice_ph_cap;
   const int* tpanel;
   const long long* tr_off;
   const double* chi;

@@ -435,6 +435,38 @@ int build_plan(const fthms_curve* curves, int ncurves, const fthms_arc* arcs, in
       g.blk_end = (int)p.blks.size();
       if (g.blk_end > g.blk_begin) p.grps.push_back(g);
     }
+  // Row slices for the mixed-form apply: kApplySlice consecutive rows of a group per CTA.
+  p.grp_res_off.resize(p.grps.size());
+  for (size_t gi = 0; gi < p.grps.size(); ++gi) {
+    const CrossGrp& g = p.grps[gi];
+    p.grp_res_off[gi] = p.res_total;
+    int rows = 0;
+    for (int b = g.blk_begin; b < g.blk_end; ++b) rows += p.blks[b].nrows;
+    p.res_total += rows;
+    // A slice ends early at a block boundary when the densities it stages (Q x summed N) would
+    // exceed kSliceDensities complex values (196 KB of shared memory).
+    const int kSliceDensities = 12288;
+    int b = g.blk_begin, rb = 0;              // block containing row0 and its first row
+    for (int row0 = 0; row0 < rows;) {
+      while (row0 >= rb + p.blks[b].nrows) rb += p.blks[b++].nrows;
+      int end = std::min(row0 + kApplySlice, rows);
+      ApplySlice sl{(int)gi, row0, 0, b, b, rb};
+      int nsum = p.blks[b].N, re = rb + p.blks[b].nrows;
+      while (re < end) {
+        if ((nsum + p.blks[sl.b1 + 1].N) * p.Q > kSliceDensities) {
+          end = re;
+          break;
+        }
+        ++sl.b1;
+        nsum += p.blks[sl.b1].N;
+        re += p.blks[sl.b1].nrows;
+      }
+      sl.nrows = end - row0;
+      p.slice_ph_cap = std::max(p.slice_ph_cap, nsum);
+      p.slices.push_back(sl);
+      row0 = end;
+    }
+  }
   const int kRowChunk = 8;
   for (int pi = 0; pi < npairs; ++pi) {
     const PairDesc& pd = p.pairs[pi];
@@ -497,7 +529,8 @@ size_t plan_device_bytes(const Plan& p) {
   b += (size_t)p.restr_total * 8;
   b += (size_t)p.n_obs * p.Q * p.L * 16 + (size_t)p.n_obs * p.n_tout * 8;
   b += p.node_t.size() * 32 + p.tgts.size() * sizeof(CrossTgt) + p.blks.size() * sizeof(CrossBlk) +
-       p.asms.size() * sizeof(CrossAsm) + p.self_tiles.size() * sizeof(SelfTile) + p.sys.size() * (sizeof(SysDesc) + sizeof(int));
+       p.asms.size() * sizeof(CrossAsm) + p.self_tiles.size() * sizeof(SelfTile) + p.sys.size() * (sizeof(SysDesc) + sizeof(int)) + p.slices.size() * sizeof(ApplySlice) + p.grp_res_off.size() * 8;
+  if (p.opt.precision == 1) b += (size_t)p.res_total * p.Q * 16;   // per-row results of the mixed-form apply
   b += p.win.size() * 8 + (size_t)p.Q * p.L * 32 + (size_t)p.K * 8 + p.chi.size() * 8;
   return b;
 }

@@ -51,7 +51,8 @@ class fthms_stats_t(C.Structure):
                 ("solves", C.c_longlong), ("kernel_launches", C.c_longlong), ("device_bytes", C.c_size_t),
                 ("cross_entries", C.c_double), ("hankel_evals", C.c_double), ("h2d_bytes", C.c_size_t),
                 ("lu_flops", C.c_double), ("solve_flops", C.c_double), ("apply_flops", C.c_double),
-                ("precision", C.c_int), ("max_refine_resid", C.c_double)]
+                ("precision", C.c_int), ("max_refine_resid", C.c_double),
+                ("refine_passes", C.c_double)]
 
 
 STAGES = ["tables", "assemble_self", "lu", "cross_assemble", "incident", "restrict", "solve", "cross_apply",
