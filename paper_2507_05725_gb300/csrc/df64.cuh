@@ -65,6 +65,35 @@ struct dfacc {
   }
 };
 
+// Double-float scalar arithmetic (a value is hi + lo): products from the FMA two-product with the
+// cross terms, sums from two Knuth two-sums (the accurate form, safe under cancellation).
+__device__ __forceinline__ df df_from(double v) {
+  const float h = __double2float_rn(v);
+  return df{h, __double2float_rn(v - (double)h)};
+}
+__device__ __forceinline__ df df_mul(df a, df b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  df r;
+  quick_two_sum(p, e, r.hi, r.lo);
+  return r;
+}
+__device__ __forceinline__ df df_add(df a, df b) {
+  float s, e, t, f;
+  two_sum(a.hi, b.hi, s, e);
+  two_sum(a.lo, b.lo, t, f);
+  e = __fadd_rn(e, t);
+  quick_two_sum(s, e, s, e);
+  e = __fadd_rn(e, f);
+  df r;
+  quick_two_sum(s, e, r.hi, r.lo);
+  return r;
+}
+__device__ __forceinline__ df df_neg(df a) { return df{-a.hi, -a.lo}; }
+__device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
+
 // Complex compensated multiply-accumulate: acc += a * b with a, b complex df64 (float4 layout).
 __device__ __forceinline__ void cdf_mac(dfacc& re, dfacc& im, float4 a, float4 b) {
   re.mac(a.x, a.y, b.x, b.y);

@@ -27,7 +27,14 @@ cudaError_t init_constants() {
   double ha[20];
   ha[0] = 1.0;
   for (int k = 1; k < 20; ++k) ha[k] = ha[k - 1] * (double)((2 * k - 1) * (2 * k - 1)) / (8.0 * k);
-  return cudaMemcpyToSymbol(c_hank_a, ha, sizeof ha);
+  float2 hd[20];
+  for (int k = 0; k < 20; ++k) {
+    const float h = (float)ha[k];
+    hd[k] = make_float2(h, (float)(ha[k] - (double)h));
+  }
+  cudaError_t e = cudaMemcpyToSymbol(c_hank_a, ha, sizeof ha);
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyToSymbol(c_hank_df, hd, sizeof hd);
 }
 
 namespace {
@@ -648,12 +655,18 @@ __global__ void __launch_bounds__(kAsmThreads) k_cross_assemble(DevJob J) {
   double* rsql = invl + kAsmBand;
   double* lnl = rsql + kAsmBand;
   double* lh = lnl + kAsmBand;
+  df* invl_d = reinterpret_cast<df*>(lh + kAsmBand);      // the same as double-float (mixed form)
+  df* rsql_d = invl_d + kAsmBand;
   for (int b = threadIdx.x; b < nl; b += kAsmThreads) {
     const int l = task.l0 + b;
     invl[b] = 1.0 / l;
     rsql[b] = rsqrt((double)l);
     lnl[b] = log((double)l);
     lh[b] = l * J.h;
+    if (J.mixed) {
+      invl_d[b] = df_from(invl[b]);
+      rsql_d[b] = df_from(rsql[b]);
+    }
   }
   __syncthreads();
   const long long* eo = J.e_off + (long long)task.pair * J.L;
@@ -700,6 +713,48 @@ __global__ void __launch_bounds__(kAsmThreads) k_cross_assemble(DevJob J) {
     if (hR <= 1.0) sincos_taylor(hR, su, cu);
     else sincos(hR, &su, &cu);
     const int kmax = hankel_terms((float)(lh[lsw - task.l0] * R));
+    if (J.mixed) {
+      // Mixed form: the same recurrence in double-float on the FP32 pipe (about 48 bits), stored as
+      // the double-float pairs the mixed-form apply reads; FP64 only for the seeds.
+      const df ampw_d = df_from(ampw), invu_d = df_from(inv_u), beta_d = df_from(beta);
+      const df cu_d = df_from(cu), su_d = df_from(su);
+      df cx_d{0.f, 0.f}, sx_d{0.f, 0.f};
+      int since_d = 16;
+      for (int l = lsw; l <= task.l1; ++l) {
+        const int b = l - task.l0;
+        if (since_d >= 16) {
+          double sn, cs;
+          sincos(lh[b] * R, &sn, &cs);
+          cx_d = df_from((cs + sn) * kSqrtHalf);
+          sx_d = df_from((sn - cs) * kSqrtHalf);
+          since_d = 0;
+        }
+        const df wz = df_mul(invu_d, invl_d[b]);
+        const df w2 = df_neg(df_mul(wz, wz));
+        float2 c = c_hank_df[2 * kmax];
+        df P{c.x, c.y};
+        c = c_hank_df[2 * kmax + 1];
+        df Qa{c.x, c.y};
+        for (int k = kmax - 1; k >= 0; --k) {
+          c = c_hank_df[2 * k];
+          P = df_add(df_mul(P, w2), df{c.x, c.y});
+          c = c_hank_df[2 * k + 1];
+          Qa = df_add(df_mul(Qa, w2), df{c.x, c.y});
+        }
+        Qa = df_mul(Qa, wz);
+        const df a = df_mul(ampw_d, rsql_d[b]);
+        const df t1 = df_add(df_mul(P, cx_d), df_mul(Qa, sx_d));
+        const df t2 = df_sub(df_mul(P, sx_d), df_mul(Qa, cx_d));
+        const df re = df_mul(a, df_sub(df_mul(beta_d, t1), t2));
+        const df im = df_mul(a, t1);
+        *reinterpret_cast<float4*>(Ep + eo[l]) = make_float4(re.hi, re.lo, im.hi, im.lo);
+        const df cn = df_sub(df_mul(cx_d, cu_d), df_mul(sx_d, su_d));
+        sx_d = df_add(df_mul(sx_d, cu_d), df_mul(cx_d, su_d));
+        cx_d = cn;
+        ++since_d;
+      }
+      continue;
+    }
     double cx = 0.0, sx = 0.0;
     int since = 16;
     for (int l = lsw; l <= task.l1; ++l) {
@@ -1288,7 +1343,7 @@ cudaError_t launch_lu(const DevJob& J, cudaStream_t st, int* launches) {
 
 cudaError_t launch_cross_assemble(const DevJob& J, cudaStream_t st, int* launches) {
   if (J.n_asm == 0) return cudaSuccess;
-  size_t sh = ((size_t)(4 + 2 * kAsmRows) * J.max_n + 4 * kAsmBand) * sizeof(double);
+  size_t sh = ((size_t)(4 + 2 * kAsmRows) * J.max_n + 5 * kAsmBand) * sizeof(double);   // + 2 df tables
   cudaError_t e = cudaFuncSetAttribute(k_cross_assemble, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
   if (e != cudaSuccess) return e;
   k_cross_assemble<<<J.n_asm, kAsmThreads, sh, st>>>(J);
