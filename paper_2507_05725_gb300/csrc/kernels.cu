@@ -1343,7 +1343,9 @@ cudaError_t launch_lu(const DevJob& J, cudaStream_t st, int* launches) {
 
 cudaError_t launch_cross_assemble(const DevJob& J, cudaStream_t st, int* launches) {
   if (J.n_asm == 0) return cudaSuccess;
-  size_t sh = ((size_t)(4 + 2 * kAsmRows) * J.max_n + 5 * kAsmBand) * sizeof(double);   // + 2 df tables
+  // Shared layout of k_cross_assemble, in 8-byte words: ctab 4N, lam kAsmRows N, Wn kAsmRows N, then
+  // band tables invl, rsql, lnl, lh (doubles) and invl_d, rsql_d (double-float pairs), kAsmBand each.
+  size_t sh = ((size_t)(4 + 2 * kAsmRows) * J.max_n + 6 * kAsmBand) * sizeof(double);
   cudaError_t e = cudaFuncSetAttribute(k_cross_assemble, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
   if (e != cudaSuccess) return e;
   k_cross_assemble<<<J.n_asm, kAsmThreads, sh, st>>>(J);
