@@ -380,7 +380,8 @@ def ours(args):
                             "cross_assemble": FLOPS_PER_KERNEL_ENTRY * st_["cross_entries"],
                             "assemble_self": FLOPS_PER_KERNEL_ENTRY * self_entries}
         kname = {"cross_apply": "k_cross_rows_df" if mixed else "k_cross_apply",
-                 "cross_assemble": "k_cross_assemble", "lu": "k_lu",
+                 "cross_assemble": "k_cross_assemble[mixed]" if mixed else "k_cross_assemble",
+                 "lu": "k_lu[mixed]" if mixed else "k_lu",
                  "solve": "k_solve_mixed" if mixed else "k_solve", "assemble_self": "k_assemble_self"}.get(dom)
         tpu = measured_traffic_per_unit()
         traffic = tpu[kname] * units[dom] if (kname in tpu and dom in units) else None
