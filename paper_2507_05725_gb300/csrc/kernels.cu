@@ -453,7 +453,6 @@ __global__ void __launch_bounds__(kLuThreads) k_lu(DevJob J) {
 // ceil(N/32) dependent steps per sweep instead of N.  Both factors have a unit diagonal (U was scaled
 // and D^{-1} is applied between the sweeps).  C = double2 (FP64 factors) or float2 (FP32 factors).
 constexpr int kSolveWarps = 4;
-constexpr int kSolveMinBlocks = 6;   // resident blocks per SM the register budget must allow
 
 // Rows i0 and i0 + 32 of b -= T[:, r0..r0+w) x with x = b[r0..r0+w), column-major T of leading
 // dimension N.  Each batch of 8 columns issues the loads of both rows before their FMAs, so a lane has
