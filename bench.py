@@ -426,8 +426,8 @@ def ours(args):
                 "dtype": ("f64 assembly/transforms + f32 factors + double-float (2 x f32) refinement and cross apply"
                           if use_mixed else "f64"),
                 "data": "synthetic",
-                "config": {"workload": "4obstacles-planewave: 8 arcs, N 48..259, L=1025 on [0,60], M=12, Q=1, "
-                                       "plain FP64 (one job per step)",
+                "config": {"workload": "4obstacles-planewave: 8 arcs, N 48..259, L=1025 on [0,60], M=12, Q=1 "
+                                       "(one whole job per step)",
                            "solves_per_step": solves, "systems_per_step": P * (L - 1),
                            "form": "mixed (verified <= 1e-10 vs FP64 in-run)" if use_mixed else "plain FP64",
                            "l2": "working set > L2 (cross matrices "
