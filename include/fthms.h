@@ -87,13 +87,19 @@ typedef struct {
  *              16..16384); dt = 2 pi/(h n_period), t_n = -H + n dt covering [-H, s_Q + H].
  *  obs_xy    : n_obs observation points (x, y), host array of 2*n_obs doubles.
  *  n_tout, tout0, dtout : output times tout0 + k dtout of the traces u_M(z, t) (eq. mult-scatt-int).
- *  precision : 0 = FP64 throughout.  1 = mixed form: FP32 LU factors and an FP32 inverse per system,
- *              solutions refined against the matrix kept as double-float (two floats, ~48 bits) until
- *              the relative correction is below 1e-12 (at most 3 steps); cross matrices stored and
- *              applied in double-float on the FP32 pipe; kernel assembly, transforms and every other
- *              stage stay FP64.  Densities agree with the FP64 form to ~1e-12.  Others -> ENOTIMPL.
+ *  precision : 0 = FP64 throughout.  1 = mixed form: FP32 LU factors; solutions refined against the
+ *              matrix kept as double-float (two floats, ~48 bits) until the relative correction is
+ *              below 1e-11 (at most 3 steps); the far-field cross entries evaluated, stored and applied
+ *              in double-float on the FP32 pipe; self matrices, phase seeds, log-singular corrections,
+ *              transforms and restriction stay FP64.  Densities agree with the FP64 form to ~1e-12.
+ *              Others -> ENOTIMPL.
  *  keep_densities : 1 keeps phi_{j,m,q}(omega_l) of every step for fthms_densities; 0 keeps only
- *              the sum over m. */
+ *              the sum over m.
+ *  cross_mode: 0 = the cross-arc and observation rows of eq. FDsolk-interior are assembled once per job,
+ *              stored in device memory and applied every step (fast while they fit: 16 bytes per
+ *              entry).  1 = they are evaluated again in every step and summed at once, nothing stored
+ *              (for jobs whose cross rows do not fit, e.g. many arcs on one curve at high frequency).
+ *              Both modes give the same densities to rounding.  Others -> EINVAL. */
 typedef struct {
   double W;
   int L;
@@ -109,6 +115,7 @@ typedef struct {
   double tout0, dtout;
   int precision;
   int keep_densities;
+  int cross_mode;
 } fthms_options;
 
 typedef struct {

@@ -213,11 +213,26 @@ fthms_status upload_job(fthms_req* r) {
   J.slices = nullptr;
   J.grp_res_off = nullptr;
   J.apply_res = nullptr;
-  if (J.mixed) {
-    TRY(dev_upload(r, p.slices, &J.slices));
+  J.otf = p.opt.cross_mode == 1 ? 1 : 0;
+  J.n_otf = 0;
+  J.otf_tasks = nullptr;
+  J.wn_off = nullptr;
+  J.wn = nullptr;
+  J.otf_res_off = nullptr;
+  if (J.mixed || J.otf) {
     TRY(dev_upload(r, p.grp_res_off, &J.grp_res_off));
     TRY(dev_alloc(r, (size_t)std::max(1LL, p.res_total) * p.Q, &J.apply_res));
+  }
+  if (J.mixed && !J.otf) {
+    TRY(dev_upload(r, p.slices, &J.slices));
     J.n_slices = (int)p.slices.size();
+  }
+  if (J.otf) {
+    TRY(dev_upload(r, p.otf, &J.otf_tasks));
+    TRY(dev_upload(r, p.wn_off, &J.wn_off));
+    TRY(dev_upload(r, p.otf_res_off, &J.otf_res_off));
+    TRY(dev_alloc(r, (size_t)p.wn_total, &J.wn));
+    J.n_otf = (int)p.otf.size();
   }
   TRY(dev_upload(r, p.tpanel, &J.tpanel));
   TRY(dev_upload(r, p.tr_off, &J.tr_off));
@@ -248,7 +263,8 @@ fthms_status upload_job(fthms_req* r) {
   if (p.opt.keep_densities) TRY(dev_alloc(r, (size_t)p.vec_total * p.M, &J.phi_all));
   TRY(dev_alloc(r, (size_t)p.spec_total, &J.W));
   TRY(dev_alloc(r, (size_t)p.spec_total, &J.Gt));
-  TRY(dev_alloc(r, (size_t)p.e_total, &J.E));
+  J.E = nullptr;
+  if (!J.otf) TRY(dev_alloc(r, (size_t)p.e_total, &J.E));
   TRY(dev_alloc(r, (size_t)std::max(1, p.n_obs * p.Q * p.L), &J.Vobs));
   TRY(dev_alloc(r, (size_t)std::max(1, p.n_obs * p.n_tout), &J.traces));
   TRY(dev_alloc(r, (size_t)p.K / 2, &J.fft_tw));
@@ -342,7 +358,9 @@ fthms_status enqueue_stages(fthms_req* r, bool bracket) {
   TRY(stage(r, FTHMS_STAGE_TABLES, st, &nl, [&] { return launch_tables(J, st, &nl); }));
   TRY(stage(r, FTHMS_STAGE_ASSEMBLE, st, &nl, [&] { return launch_assemble_self(J, st, &nl); }));
   TRY(stage(r, FTHMS_STAGE_LU, st, &nl, [&] { return launch_lu(J, st, &nl); }));
-  TRY(stage(r, FTHMS_STAGE_CROSS_ASM, st, &nl, [&] { return launch_cross_assemble(J, st, &nl); }));
+  TRY(stage(r, FTHMS_STAGE_CROSS_ASM, st, &nl, [&] {
+    return J.otf ? launch_near_weights(J, st, &nl) : launch_cross_assemble(J, st, &nl);
+  }));
   CK(cudaMemsetAsync(J.Gt, 0, (size_t)r->plan.spec_total * sizeof(double2), st));
   CK(cudaMemsetAsync(J.W, 0, (size_t)r->plan.spec_total * sizeof(double2), st));
   CK(cudaMemsetAsync(J.Vobs, 0, (size_t)std::max(1, J.n_obs * J.Q * J.L) * sizeof(double2), st));
@@ -351,7 +369,9 @@ fthms_status enqueue_stages(fthms_req* r, bool bracket) {
   TRY(stage(r, FTHMS_STAGE_RESTRICT, st, &nl, [&] { return launch_restrict(J, st, &nl); }));
   for (int m = 1; m <= J.M; ++m) {
     TRY(stage(r, FTHMS_STAGE_SOLVE, st, &nl, [&] { return launch_solve(J, m, st, &nl); }));
-    TRY(stage(r, FTHMS_STAGE_CROSS_APPLY, st, &nl, [&] { return launch_cross_apply(J, st, &nl); }));
+    TRY(stage(r, FTHMS_STAGE_CROSS_APPLY, st, &nl, [&] {
+      return J.otf ? launch_cross_otf(J, st, &nl) : launch_cross_apply(J, st, &nl);
+    }));
     if (m < J.M) {
       TRY(stage(r, FTHMS_STAGE_SYNTH_FWD, st, &nl, [&] { return launch_synth_fwd(J, st, &nl); }));
       TRY(stage(r, FTHMS_STAGE_RESTRICT, st, &nl, [&] { return launch_restrict(J, st, &nl); }));

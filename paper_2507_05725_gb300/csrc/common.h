@@ -79,6 +79,15 @@ struct CrossAsm {
   int pad;
 };
 
+// On-the-fly cross task (cross_mode 1): assembly task `task`, restricted to the frequencies l0..l1
+// (at most kOtfBand / Q of them, so that the per-frequency sums stay in registers).
+constexpr int kOtfBand = 8;
+struct CrossOtf {
+  int task;
+  int l0, l1;
+  int pad;
+};
+
 // Upper-triangular tile of the self matrices of a band of consecutive systems (same arc, same N,
 // consecutive frequencies sys .. sys+nsys-1).
 struct SelfTile {

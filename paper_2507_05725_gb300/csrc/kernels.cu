@@ -589,6 +589,138 @@ __device__ __forceinline__ void store_entry(const DevJob& J, double2* p, double2
 }
 constexpr int kAsmBand = 64;   // frequencies per assembly task (matches the planner's band cap)
 
+// Near-rule product-integration weights of the rows of one task at N source nodes (block-wide, all
+// threads call): Wn[r * N + i] = (lambda_0 + 2 sum_n lambda_n T_n(t_i)) / N for the near rows r, with
+// lambda_n(t*) = int log|t* - s| T_n(s)/sqrt(1-s^2) ds for |t*| > 1, = -pi zeta^n / n (n >= 1); the sum
+// stops where |zeta|^n < 1e-18 (the omitted terms are below 1e-17 of the weights).  ctab: 4N doubles,
+// lam: kAsmRows x N doubles of shared memory; Wn may be shared or global memory.
+__device__ void near_weights_block(const CrossTgt* tg, int nrows, int N, double* ctab, double* lam, double* Wn) {
+  __shared__ int s_nlam[kAsmRows];
+  for (int r = threadIdx.x; r < 4 * N; r += blockDim.x) ctab[r] = cospi((double)r / (2.0 * N));
+  if (threadIdx.x < nrows && tg[threadIdx.x].near) {
+    const double ts = tg[threadIdx.x].tstar;
+    const double rt = sqrt(fma(ts, ts, -1.0));
+    const double zeta = ts > 0 ? ts - rt : ts + rt;
+    double* lr = lam + threadIdx.x * N;
+    lr[0] = kPiD * log(0.5 * (fabs(ts) + rt));
+    double pw = 1.0;
+    int n = 1;
+    for (; n < N; ++n) {
+      pw *= zeta;
+      if (fabs(pw) < 1e-18) break;
+      lr[n] = -kPiD * pw / n;
+    }
+    s_nlam[threadIdx.x] = n;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < nrows * N; e += blockDim.x) {
+    int r = e / N, i = e % N;
+    if (!tg[r].near) continue;
+    const double* lr = lam + r * N;
+    const int step = 2 * i + 1, mod = 4 * N, nlam = s_nlam[r];
+    double acc = 0.0;
+    int ph = 0;
+    for (int n = 1; n < nlam; ++n) {
+      ph += step;
+      if (ph >= mod) ph -= mod;
+      acc = fma(lr[n], ctab[ph], acc);
+    }
+    Wn[r * N + i] = (lr[0] + 2.0 * acc) / N;
+  }
+  __syncthreads();
+}
+
+// Quantities of one (target row, source node) pair shared by every frequency of a band.  Every entry,
+// near or far, is E = (alpha J0 - (w/4) Y, (w/4) J0) with Y = Yhat0 below z = 20 and Y0 above;
+// alpha = A0 + A1 ln l below 20 and beta w/4 above.
+//   far rule:  A0 = -(w/(2 pi)) (ln(hR/2) + gamma),  beta = 0;
+//   near rule: the log-singular part K1 ln|t* - s| is integrated with the weights wn instead of w,
+//              so A0 = -(wn + w (ln(hR/2) + gamma - ln|t* - t_i|))/(2 pi) and
+//              beta = -(2/pi)(wn/w - ln|t* - t_i|).
+struct PairSetup {
+  double R, hR, inv_u, A0, beta;
+  int lsw;     // first frequency index with z = l h R >= 20
+};
+
+__device__ __forceinline__ PairSetup pair_setup(const DevJob& J, const CrossTgt& t, double xi, double yi, double ti,
+                                                double wn, int l0, double w, double invw, double inv_h) {
+  PairSetup s;
+  const double dx = t.x - xi, dy = t.y - yi;
+  const double R2 = fma(dx, dx, dy * dy);
+  const double rinv = rsqrt(R2);
+  const double R0 = R2 * rinv;
+  s.R = fma(fma(-R0, R0, R2), 0.5 * rinv, R0);   // one Newton step on sqrt(R2)
+  s.hR = J.h * s.R;
+  s.inv_u = rinv * inv_h;                        // 1 / (h R)
+  s.lsw = max(l0, (int)ceil(fmin(kBesselLarge * s.inv_u, 1.0e9)));
+  s.A0 = 0.0;
+  s.beta = 0.0;
+  double lt = 0.0;
+  if (t.near) {
+    lt = log(fabs(t.tstar - ti));
+    s.beta = -kTwoOverPi * fma(wn, invw, -lt);
+  } else {
+    wn = 0.0;
+  }
+  if (s.lsw > l0) s.A0 = -0.5 * kInvPi * fma(w, log(0.5 * s.hR) + kEulerGamma - lt, wn);
+  return s;
+}
+
+// Entry at z = (l h) R < 20 from the Taylor tables (lh = l h, lnl = ln l).
+__device__ __forceinline__ double2 taylor_entry(const PairSetup& s, double lh, double lnl, double A1, double qw) {
+  double J0, Yh;
+  bessel0_taylor(lh * s.R, J0, Yh);
+  const double alpha = fma(A1, lnl, s.A0);
+  return make_double2(fma(alpha, J0, -qw * Yh), qw * J0);
+}
+
+// Above z = 20 the Hankel expansion's phase advances by the fixed rotation e^{i h R} from one frequency
+// to the next (re-seeded by sincos every 16 steps); 1/z = (1/(hR))(1/l) and sqrt(2/(pi z)) =
+// sqrt(2/(pi hR))/sqrt(l); the number of terms follows the first (smallest) z of the run.
+struct AsymState {
+  double cx, sx;   // cos(z - pi/4), sin(z - pi/4) at the current frequency
+  double cu, su;   // the step rotation e^{i h R}
+  double ampw;     // sqrt(2/(pi h R)) w/4
+  int since, kmax;
+};
+
+__device__ __forceinline__ AsymState asym_start(const PairSetup& s, double lh_first, double camp) {
+  AsymState a;
+  a.ampw = rsqrt(s.hR) * camp;
+  if (s.hR <= 1.0) sincos_taylor(s.hR, a.su, a.cu);
+  else sincos(s.hR, &a.su, &a.cu);
+  a.kmax = hankel_terms((float)(lh_first * s.R));
+  a.cx = a.sx = 0.0;
+  a.since = 16;
+  return a;
+}
+
+__device__ __forceinline__ double2 asym_entry(AsymState& a, const PairSetup& s, double lh, double invl, double rsql) {
+  if (a.since >= 16) {
+    double sn, cs;
+    sincos(lh * s.R, &sn, &cs);
+    a.cx = (cs + sn) * kSqrtHalf;
+    a.sx = (sn - cs) * kSqrtHalf;
+    a.since = 0;
+  }
+  const double wz = s.inv_u * invl;
+  const double w2 = -wz * wz;
+  double P = c_hank_a[2 * a.kmax], Qa = c_hank_a[2 * a.kmax + 1];
+  for (int k = a.kmax - 1; k >= 0; --k) {
+    P = fma(P, w2, c_hank_a[2 * k]);
+    Qa = fma(Qa, w2, c_hank_a[2 * k + 1]);
+  }
+  Qa *= wz;
+  const double amp = a.ampw * rsql;
+  const double t1 = fma(P, a.cx, Qa * a.sx);             // J0 / amp
+  const double t2 = fma(P, a.sx, -Qa * a.cx);            // Y0 / amp
+  const double cn = fma(a.cx, a.cu, -a.sx * a.su);
+  a.sx = fma(a.sx, a.cu, a.cx * a.su);
+  a.cx = cn;
+  ++a.since;
+  return make_double2(amp * fma(s.beta, t1, -t2), amp * t1);
+}
+
 __global__ void __launch_bounds__(kAsmThreads) k_cross_assemble(DevJob J) {
   extern __shared__ double sha[];
   const CrossAsm task = J.asms[blockIdx.x];
@@ -606,43 +738,7 @@ __global__ void __launch_bounds__(kAsmThreads) k_cross_assemble(DevJob J) {
     any_near = a;
   }
   __syncthreads();
-  if (any_near) {
-    for (int r = threadIdx.x; r < 4 * N; r += kAsmThreads) ctab[r] = cospi((double)r / (2.0 * N));
-    // lambda_n(t*) = int log|t* - s| T_n(s)/sqrt(1-s^2) ds for |t*| > 1, = -pi zeta^n / n (n >= 1):
-    // the sum below stops where |zeta|^n < 1e-18 (the omitted terms are below 1e-17 of the weights).
-    __shared__ int s_nlam[kAsmRows];
-    if (threadIdx.x < task.nrows && tg[threadIdx.x].near) {
-      const double ts = tg[threadIdx.x].tstar;
-      const double rt = sqrt(fma(ts, ts, -1.0));
-      const double zeta = ts > 0 ? ts - rt : ts + rt;
-      double* lr = lam + threadIdx.x * N;
-      lr[0] = kPiD * log(0.5 * (fabs(ts) + rt));
-      double pw = 1.0;
-      int n = 1;
-      for (; n < N; ++n) {
-        pw *= zeta;
-        if (fabs(pw) < 1e-18) break;
-        lr[n] = -kPiD * pw / n;
-      }
-      s_nlam[threadIdx.x] = n;
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < task.nrows * N; e += kAsmThreads) {
-      int r = e / N, i = e % N;
-      if (!tg[r].near) continue;
-      const double* lr = lam + r * N;
-      const int step = 2 * i + 1, mod = 4 * N, nlam = s_nlam[r];
-      double acc = 0.0;
-      int ph = 0;
-      for (int n = 1; n < nlam; ++n) {
-        ph += step;
-        if (ph >= mod) ph -= mod;
-        acc = fma(lr[n], ctab[ph], acc);
-      }
-      Wn[r * N + i] = (lr[0] + 2.0 * acc) / N;
-    }
-    __syncthreads();
-  }
+  if (any_near) near_weights_block(tg, task.nrows, N, ctab, lam, Wn);
   const double w = kPiD / N, qw = 0.25 * w, invw = N * kInvPi;
   const double A1 = -0.5 * kInvPi * w;          // coefficient of ln l below z = 20
   const double camp = kSqrtTwoOverPi * qw;      // sqrt(2/pi) w/4
@@ -672,64 +768,36 @@ __global__ void __launch_bounds__(kAsmThreads) k_cross_assemble(DevJob J) {
   for (int e = threadIdx.x; e < task.nrows * N; e += kAsmThreads) {
     const int r = e % task.nrows, i = e / task.nrows;
     const CrossTgt t = tg[r];
-    const double dx = t.x - J.node_x[pn.off + i], dy = t.y - J.node_y[pn.off + i];
-    const double R2 = fma(dx, dx, dy * dy);
-    const double rinv = rsqrt(R2);
-    const double R0 = R2 * rinv;
-    const double R = fma(fma(-R0, R0, R2), 0.5 * rinv, R0);   // one Newton step on sqrt(R2)
-    const double hR = J.h * R;
-    const double inv_u = rinv * inv_h;                        // 1 / (h R)
-    const int lsw = max(task.l0, (int)ceil(fmin(kBesselLarge * inv_u, 1.0e9)));   // first l with z >= 20
-    // Every entry, near or far, is E = (alpha J0 - (w/4) Y, (w/4) J0) with Y = Yhat0 below z = 20
-    // and Y0 above; alpha = A0 + A1 ln l below 20 and beta w/4 above.
-    //   far rule:  A0 = -(w/(2 pi)) (ln(hR/2) + gamma),  beta = 0;
-    //   near rule: the log-singular part K1 ln|t* - s| is integrated with the weights wn instead of
-    //              w, so A0 = -(wn + w (ln(hR/2) + gamma - ln|t* - t_i|))/(2 pi) and
-    //              beta = -(2/pi)(wn/w - ln|t* - t_i|).
-    double A0 = 0.0, beta = 0.0, wn = 0.0, lt = 0.0;
-    if (t.near) {
-      wn = Wn[r * N + i];
-      lt = log(fabs(t.tstar - J.node_t[pn.off + i]));
-      beta = -kTwoOverPi * fma(wn, invw, -lt);
-    }
-    if (lsw > task.l0) A0 = -0.5 * kInvPi * fma(w, log(0.5 * hR) + kEulerGamma - lt, wn);
+    const PairSetup ps = pair_setup(J, t, J.node_x[pn.off + i], J.node_y[pn.off + i], J.node_t[pn.off + i],
+                                    t.near ? Wn[r * N + i] : 0.0, task.l0, w, invw, inv_h);
     double2* Ep = J.E + (long long)i * ld + task.row0 + r;
-    const int lend = min(lsw, task.l1 + 1);
+    const int lend = min(ps.lsw, task.l1 + 1);
     for (int l = task.l0; l < lend; ++l) {
       const int b = l - task.l0;
-      double J0, Yh;
-      bessel0_taylor(lh[b] * R, J0, Yh);
-      const double alpha = fma(A1, lnl[b], A0);
-      store_entry(J, Ep + eo[l], make_double2(fma(alpha, J0, -qw * Yh), qw * J0));
+      store_entry(J, Ep + eo[l], taylor_entry(ps, lh[b], lnl[b], A1, qw));
     }
-    if (lsw > task.l1) continue;
-    // Above z = 20 the Hankel expansion's phase advances by the fixed rotation e^{i h R} from one
-    // frequency to the next (re-seeded by sincos every 16 steps); 1/z = (1/(hR))(1/l) and
-    // sqrt(2/(pi z)) = sqrt(2/(pi hR))/sqrt(l) come from the band tables; the number of terms
-    // follows the smallest z of the band.
-    const double ampw = rsqrt(hR) * camp;
-    double su, cu;
-    if (hR <= 1.0) sincos_taylor(hR, su, cu);
-    else sincos(hR, &su, &cu);
-    const int kmax = hankel_terms((float)(lh[lsw - task.l0] * R));
+    if (ps.lsw > task.l1) continue;
+    const int lsw = ps.lsw;
+    AsymState as = asym_start(ps, lh[lsw - task.l0], camp);
     if (J.mixed) {
       // Mixed form: the same recurrence in double-float on the FP32 pipe (about 48 bits), stored as
       // the double-float pairs the mixed-form apply reads; FP64 only for the seeds.
-      const df ampw_d = df_from(ampw), invu_d = df_from(inv_u), beta_d = df_from(beta);
-      const df cu_d = df_from(cu), su_d = df_from(su);
+      const df ampw_d = df_from(as.ampw), invu_d = df_from(ps.inv_u), beta_d = df_from(ps.beta);
+      const df cu_d = df_from(as.cu), su_d = df_from(as.su);
       df cx_d{0.f, 0.f}, sx_d{0.f, 0.f};
       int since_d = 16;
       for (int l = lsw; l <= task.l1; ++l) {
         const int b = l - task.l0;
         if (since_d >= 16) {
           double sn, cs;
-          sincos(lh[b] * R, &sn, &cs);
+          sincos(lh[b] * ps.R, &sn, &cs);
           cx_d = df_from((cs + sn) * kSqrtHalf);
           sx_d = df_from((sn - cs) * kSqrtHalf);
           since_d = 0;
         }
         const df wz = df_mul(invu_d, invl_d[b]);
         const df w2 = df_neg(df_mul(wz, wz));
+        const int kmax = as.kmax;
         float2 c = c_hank_df[2 * kmax];
         df P{c.x, c.y};
         c = c_hank_df[2 * kmax + 1];
@@ -754,34 +822,103 @@ __global__ void __launch_bounds__(kAsmThreads) k_cross_assemble(DevJob J) {
       }
       continue;
     }
-    double cx = 0.0, sx = 0.0;
-    int since = 16;
     for (int l = lsw; l <= task.l1; ++l) {
       const int b = l - task.l0;
-      if (since >= 16) {
-        double s, c;
-        sincos(lh[b] * R, &s, &c);
-        cx = (c + s) * kSqrtHalf;                        // cos(z - pi/4)
-        sx = (s - c) * kSqrtHalf;                        // sin(z - pi/4)
-        since = 0;
-      }
-      const double wz = inv_u * invl[b];
-      const double w2 = -wz * wz;
-      double P = c_hank_a[2 * kmax], Qa = c_hank_a[2 * kmax + 1];
-      for (int k = kmax - 1; k >= 0; --k) {
-        P = fma(P, w2, c_hank_a[2 * k]);
-        Qa = fma(Qa, w2, c_hank_a[2 * k + 1]);
-      }
-      Qa *= wz;
-      const double a = ampw * rsql[b];
-      const double t1 = fma(P, cx, Qa * sx);             // J0 / a
-      const double t2 = fma(P, sx, -Qa * cx);            // Y0 / a
-      store_entry(J, Ep + eo[l], make_double2(a * fma(beta, t1, -t2), a * t1));
-      const double cn = fma(cx, cu, -sx * su);
-      sx = fma(sx, cu, cx * su);
-      cx = cn;
-      ++since;
+      store_entry(J, Ep + eo[l], asym_entry(as, ps, lh[b], invl[b], rsql[b]));
     }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Cross rows evaluated every step (cross_mode 1), nothing stored.  Near weights first, once per job,
+// into a table (one slab of nrows x N per assembly task with near rows).
+__global__ void __launch_bounds__(kAsmThreads) k_near_weights(DevJob J) {
+  const long long off = J.wn_off[blockIdx.x];
+  if (off < 0) return;
+  extern __shared__ double shn[];
+  const CrossAsm task = J.asms[blockIdx.x];
+  const CrossTgt* tg = J.tgts + J.pairs[task.pair].tgt_off + task.row0;
+  near_weights_block(tg, task.nrows, task.N, shn, shn + 4 * task.N, J.wn + off);
+}
+
+// One CTA per (assembly task, band of at most kOtfBand / Q frequencies): thread (row r, source group
+// g) evaluates the entries of its sources i = g, g + 16, ... for every frequency of the band exactly as
+// k_cross_assemble does, multiplies them by the densities of the current step and sums; the 16 partial
+// sums of a row are then added in group order (deterministic) into the per-row results, which
+// k_cross_reduce adds per target in block order.
+template <int Q>
+__global__ void __launch_bounds__(kAsmThreads) k_cross_otf(DevJob J) {
+  constexpr int B = kOtfBand / Q > 0 ? kOtfBand / Q : 1;
+  constexpr int G = kAsmThreads / kAsmRows;          // source groups
+  extern __shared__ double2 sho[];                    // [G][kAsmRows][Q * B] partial sums
+  __shared__ double tb[4][kOtfBand];                  // 1/l, 1/sqrt(l), ln l, l h
+  const CrossOtf ot = J.otf_tasks[blockIdx.x];
+  const CrossAsm task = J.asms[ot.task];
+  const PairDesc pr = J.pairs[task.pair];
+  const int N = task.N, nl = ot.l1 - ot.l0 + 1;
+  const Panel pn = J.panels[task.panel];
+  const CrossTgt* tg = J.tgts + pr.tgt_off + task.row0;
+  const long long woff = J.wn_off[ot.task];
+  const double* Wn = woff >= 0 ? J.wn + woff : nullptr;
+  if (threadIdx.x < nl) {
+    const int l = ot.l0 + threadIdx.x;
+    tb[0][threadIdx.x] = 1.0 / l;
+    tb[1][threadIdx.x] = rsqrt((double)l);
+    tb[2][threadIdx.x] = log((double)l);
+    tb[3][threadIdx.x] = l * J.h;
+  }
+  __syncthreads();
+  const double w = kPiD / N, qw = 0.25 * w, invw = N * kInvPi;
+  const double A1 = -0.5 * kInvPi * w;
+  const double camp = kSqrtTwoOverPi * qw;
+  const double inv_h = 1.0 / J.h;
+  const int r = threadIdx.x % kAsmRows, g = threadIdx.x / kAsmRows;
+  double2 acc[Q][B];
+#pragma unroll
+  for (int q = 0; q < Q; ++q)
+#pragma unroll
+    for (int b = 0; b < B; ++b) acc[q][b] = make_double2(0.0, 0.0);
+  if (r < task.nrows) {
+    const CrossTgt t = tg[r];
+    const SysDesc* sj = J.sys + (long long)pr.j * (J.L - 1) + (ot.l0 - 1);   // systems (j, l0..l1)
+    for (int i = g; i < N; i += G) {
+      const PairSetup ps = pair_setup(J, t, J.node_x[pn.off + i], J.node_y[pn.off + i], J.node_t[pn.off + i],
+                                      t.near ? Wn[r * N + i] : 0.0, ot.l0, w, invw, inv_h);
+      AsymState as{};
+      bool started = false;
+#pragma unroll
+      for (int b = 0; b < B; ++b) {
+        if (b < nl) {
+          const int l = ot.l0 + b;
+          double2 E;
+          if (l < ps.lsw) {
+            E = taylor_entry(ps, tb[3][b], tb[2][b], A1, qw);
+          } else {
+            if (!started) {
+              as = asym_start(ps, tb[3][b], camp);
+              started = true;
+            }
+            E = asym_entry(as, ps, tb[3][b], tb[0][b], tb[1][b]);
+          }
+          const double2* ph = J.phi + sj[b].vec_off + i;
+#pragma unroll
+          for (int q = 0; q < Q; ++q) acc[q][b] = cfma(E, ph[q * N], acc[q][b]);
+        }
+      }
+    }
+  }
+  double2* red = sho + (g * kAsmRows + r) * (Q * B);
+#pragma unroll
+  for (int q = 0; q < Q; ++q)
+#pragma unroll
+    for (int b = 0; b < B; ++b) red[q * B + b] = acc[q][b];
+  __syncthreads();
+  for (int e = threadIdx.x; e < task.nrows * Q * nl; e += kAsmThreads) {
+    const int rr = e / (Q * nl), q = (e / nl) % Q, b = e % nl;
+    double2 sum = make_double2(0.0, 0.0);
+    for (int gg = 0; gg < G; ++gg) sum = cadd(sum, sho[(gg * kAsmRows + rr) * (Q * B) + q * B + b]);
+    const long long row = J.otf_res_off[(long long)task.pair * J.L + ot.l0 + b] + task.row0 + rr;
+    J.apply_res[row * Q + q] = sum;
   }
 }
 
@@ -1428,6 +1565,39 @@ cudaError_t launch_cross_apply(const DevJob& J, cudaStream_t st, int* launches) 
     case 2: return launch_cross_apply_q<2>(J, sh, st);
     case 3: return launch_cross_apply_q<3>(J, sh, st);
     default: return launch_cross_apply_q<4>(J, sh, st);
+  }
+}
+
+cudaError_t launch_near_weights(const DevJob& J, cudaStream_t st, int* launches) {
+  if (J.n_asm == 0) return cudaSuccess;
+  const size_t sh = (size_t)(4 + kAsmRows) * J.max_n * sizeof(double);   // ctab 4N, lam kAsmRows N
+  cudaError_t e = cudaFuncSetAttribute(k_near_weights, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+  if (e != cudaSuccess) return e;
+  k_near_weights<<<J.n_asm, kAsmThreads, sh, st>>>(J);
+  *launches += 1;
+  return cudaGetLastError();
+}
+
+template <int Q>
+static cudaError_t launch_cross_otf_q(const DevJob& J, cudaStream_t st) {
+  constexpr int B = kOtfBand / Q > 0 ? kOtfBand / Q : 1;
+  const size_t sh = (size_t)kAsmThreads * Q * B * sizeof(double2);
+  const size_t sh_red = (size_t)Q * J.acc_cap * sizeof(double2);
+  cudaError_t e = cudaFuncSetAttribute(k_cross_reduce<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh_red);
+  if (e != cudaSuccess) return e;
+  if (J.n_otf > 0) k_cross_otf<Q><<<J.n_otf, kAsmThreads, sh, st>>>(J);
+  k_cross_reduce<Q><<<J.n_grp, kApplyThreads, sh_red, st>>>(J);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cross_otf(const DevJob& J, cudaStream_t st, int* launches) {
+  if (J.n_grp == 0) return cudaSuccess;
+  *launches += 2;
+  switch (J.Q) {
+    case 1: return launch_cross_otf_q<1>(J, st);
+    case 2: return launch_cross_otf_q<2>(J, st);
+    case 3: return launch_cross_otf_q<3>(J, st);
+    default: return launch_cross_otf_q<4>(J, st);
   }
 }
 

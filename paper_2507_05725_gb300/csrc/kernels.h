@@ -40,6 +40,12 @@ struct DevJob {
   const long long* grp_res_off;
   double2* apply_res;        // [group rows][Q] per-row cross sums (mixed form)
   int n_slices, slice_ph_cap;
+  // cross_mode 1: cross rows evaluated every step (nothing stored)
+  int otf, n_otf;
+  const CrossOtf* otf_tasks;
+  const long long* wn_off;   // per assembly task: near weights offset or -1
+  double* wn;                // near weights, nrows x N per assembly task with near rows
+  const long long* otf_res_off;
   const int* tpanel;
   const long long* tr_off;
   const double* chi;
@@ -90,6 +96,8 @@ cudaError_t launch_incident(const DevJob& J, cudaStream_t st, int* launches);
 cudaError_t launch_restrict(const DevJob& J, cudaStream_t st, int* launches);
 cudaError_t launch_solve(const DevJob& J, int m, cudaStream_t st, int* launches);
 cudaError_t launch_cross_apply(const DevJob& J, cudaStream_t st, int* launches);
+cudaError_t launch_near_weights(const DevJob& J, cudaStream_t st, int* launches);
+cudaError_t launch_cross_otf(const DevJob& J, cudaStream_t st, int* launches);
 cudaError_t launch_synth_fwd(const DevJob& J, cudaStream_t st, int* launches);
 cudaError_t launch_traces(const DevJob& J, cudaStream_t st, int* launches);
 

@@ -122,6 +122,10 @@ int build_plan(const fthms_curve* curves, int ncurves, const fthms_arc* arcs, in
   }
   p.opt = *opt;
   p.sig = *sig;
+  if (opt->cross_mode != 0 && opt->cross_mode != 1) {
+    err = "cross_mode must be 0 (stored cross rows) or 1 (evaluated every step)";
+    return FTHMS_EINVAL;
+  }
   if (opt->precision != 0 && opt->precision != 1) {
     err = "precision must be 0 (FP64) or 1 (FP32 factors with double-float refinement and cross apply)";
     return FTHMS_ENOTIMPL;
@@ -482,6 +486,35 @@ int build_plan(const fthms_curve* curves, int ncurves, const fthms_arc* arcs, in
       l = l1 + 1;
     }
   }
+  if (p.opt.cross_mode == 1) {
+    // Rows of pair (k, j) inside the per-row results of group (k, l), in the groups' block order.
+    p.otf_res_off.assign((size_t)npairs * p.L, -1);
+    for (size_t gi = 0; gi < p.grps.size(); ++gi) {
+      const CrossGrp& g = p.grps[gi];
+      long long r = p.grp_res_off[gi];
+      for (int pi = 0; pi < npairs; ++pi) {
+        const PairDesc& pd = p.pairs[pi];
+        if (pd.k != g.k || pd.nrows == 0) continue;
+        p.otf_res_off[(size_t)pi * p.L + g.l] = r;
+        r += pd.nrows;
+      }
+    }
+    // Near weights once per job (they depend on the target and N only); tasks of at most
+    // kOtfBand / Q frequencies each.
+    const int band = std::max(1, kOtfBand / p.Q);
+    p.wn_off.assign(p.asms.size(), -1);
+    for (size_t a = 0; a < p.asms.size(); ++a) {
+      const CrossAsm& t = p.asms[a];
+      const PairDesc& pd = p.pairs[t.pair];
+      bool near = false;
+      for (int r = 0; r < t.nrows; ++r) near = near || p.tgts[pd.tgt_off + t.row0 + r].near;
+      if (near) {
+        p.wn_off[a] = p.wn_total;
+        p.wn_total += (long long)t.nrows * t.N;
+      }
+      for (int l = t.l0; l <= t.l1; l += band) p.otf.push_back(CrossOtf{(int)a, l, std::min(l + band - 1, t.l1), 0});
+    }
+  }
 
   // Restriction tables (N, Nmax) for systems below their arc's transfer-mesh size.
   std::map<std::pair<int, int>, long long> rmap;
@@ -525,12 +558,14 @@ size_t plan_device_bytes(const Plan& p) {
   b += (size_t)p.vec_total * 16 * 3;             // G, phi (current), phi sum
   if (p.opt.keep_densities) b += (size_t)p.vec_total * 16 * p.M;
   b += (size_t)p.spec_total * 16 * 2;            // W and Gt on transfer meshes
-  b += (size_t)p.e_total * 16;                   // cross matrices
+  if (p.opt.cross_mode == 0) b += (size_t)p.e_total * 16;   // stored cross matrices
   b += (size_t)p.restr_total * 8;
   b += (size_t)p.n_obs * p.Q * p.L * 16 + (size_t)p.n_obs * p.n_tout * 8;
   b += p.node_t.size() * 32 + p.tgts.size() * sizeof(CrossTgt) + p.blks.size() * sizeof(CrossBlk) +
        p.asms.size() * sizeof(CrossAsm) + p.self_tiles.size() * sizeof(SelfTile) + p.sys.size() * (sizeof(SysDesc) + sizeof(int)) + p.slices.size() * sizeof(ApplySlice) + p.grp_res_off.size() * 8;
-  if (p.opt.precision == 1) b += (size_t)p.res_total * p.Q * 16;   // per-row results of the mixed-form apply
+  if (p.opt.precision == 1 || p.opt.cross_mode == 1) b += (size_t)p.res_total * p.Q * 16;   // per-row cross sums
+  if (p.opt.cross_mode == 1)
+    b += (size_t)p.wn_total * 8 + p.otf.size() * sizeof(CrossOtf) + p.otf_res_off.size() * 8 + p.wn_off.size() * 8;
   b += p.win.size() * 8 + (size_t)p.Q * p.L * 32 + (size_t)p.K * 8 + p.chi.size() * 8;
   return b;
 }

@@ -67,6 +67,10 @@ struct Plan {
   std::vector<long long> grp_res_off;    // first row of each group in the per-row result buffer
   long long res_total = 0;               // rows over all groups
   int slice_ph_cap = 0;                  // max over slices of the summed N of the blocks it overlaps
+  std::vector<CrossOtf> otf;            // cross_mode 1: on-the-fly tasks
+  std::vector<long long> wn_off;         // per assembly task: offset of its near weights (nrows x N), or -1
+  long long wn_total = 0;
+  std::vector<long long> otf_res_off;    // [pairs][L]: first row of pair (k, j) in group (k, l)'s result rows
   std::vector<CrossAsm> asms;
   std::vector<SelfTile> self_tiles;
 

@@ -43,7 +43,7 @@ class fthms_options(C.Structure):
                 ("N_ppw", C.c_double), ("M", C.c_int), ("Q", C.c_int), ("H", C.c_double), ("n_period", C.c_int),
                 ("interior", C.c_int), ("n_obs", C.c_int), ("obs_xy", C.POINTER(C.c_double)),
                 ("n_tout", C.c_int), ("tout0", C.c_double), ("dtout", C.c_double), ("precision", C.c_int),
-                ("keep_densities", C.c_int)]
+                ("keep_densities", C.c_int), ("cross_mode", C.c_int)]
 
 
 class fthms_stats_t(C.Structure):
@@ -148,7 +148,7 @@ class Marshalled:
         self.options = fthms_options(o["W"], o["L"], o["N_fixed"], o["N_min"], o["N_off"], o["N_ppw"], o["M"],
                                      o["Q"], o["H"], o["n_period"], o["interior"], obs.size // 2,
                                      _dptr(obs) if obs.size else None, o["n_tout"], o["tout0"], o["dtout"],
-                                     int(precision), int(keep_densities))
+                                     int(precision), int(keep_densities), int(o.get("cross_mode", 0)))
         self.ncurves, self.narcs = len(curves), len(arcs)
 
 

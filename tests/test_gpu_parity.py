@@ -323,3 +323,48 @@ def test_largest_supported_system(F, ctx):
     with pytest.raises(F.FthmsError) as e:
         F.Job(ctx, big)
     assert e.value.status == F.FTHMS_EINVAL and "800" in str(e.value)
+
+
+# ---- cross rows evaluated every step (cross_mode 1) ------------------------------------------------
+
+def _cross_mode(problem, mode):
+    problem["options"]["cross_mode"] = mode
+    return problem
+
+
+@pytest.mark.parametrize("name", ["small-plane", "two-curves-Q2", "four-arcs"])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_on_the_fly_cross_matches_stored(F, ctx, name, precision):
+    """Evaluating the cross rows in every step gives the densities and traces of the stored rows (the same
+    entries, summed in another order; the mixed form's stored rows are double-float)."""
+    tol = 1e-12 if precision == 0 else 1e-11
+    a = F.Job(ctx, _cross_mode(SMALL[name](), 0), precision=precision).run().wait()
+    b = F.Job(ctx, _cross_mode(SMALL[name](), 1), precision=precision).run().wait()
+    P = len(SMALL[name]()["arcs"])
+    num = den = 0.0
+    for j in range(P):
+        da, db = a.densities(j, 0, 0), b.densities(j, 0, 0)
+        for l in da:
+            num += float(np.sum(np.abs(da[l] - db[l]) ** 2))
+            den += float(np.sum(np.abs(da[l]) ** 2))
+    ta, tb = a.traces(), b.traces()
+    a.release()
+    b.release()
+    assert math.sqrt(num / den) < tol
+    assert np.max(np.abs(ta - tb)) < tol * max(1e-300, np.max(np.abs(ta)))
+
+
+def test_on_the_fly_cross_parity(F, ctx):
+    rel, st = _parity(F, ctx, _cross_mode(wl.random_small(7, n_arcs_per_curve=4, M=3), 1))
+    assert rel < DENSITY_TOL
+
+
+def test_config3_reduced_parity(F, ctx):
+    """Config 3's 12-arc star cavity (one curve: every arc sees every other, near rows on both sides) on
+    omega <= 16 with two windows, cross rows evaluated every step."""
+    rel, st = _parity(F, ctx, wl.config3_reduced())
+    assert rel < DENSITY_TOL
+
+
+def test_config3_reduced_mixed_parity(F, ctx):
+    assert _parity_mixed(F, ctx, wl.config3_reduced()) < MIXED_TOL

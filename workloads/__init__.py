@@ -28,7 +28,7 @@ import numpy as np
 
 __all__ = [
     "circle", "ellipse", "kite", "star", "split_closed_curve", "config1", "config2",
-    "config2_reduced", "random_small", "served_requests", "problem_summary",
+    "config2_reduced", "config3", "config3_reduced", "random_small", "served_requests", "problem_summary",
 ]
 
 
@@ -145,6 +145,32 @@ def config2_reduced(seed=2, L=129, M=3, W=30.0, H=12.0, n_period=1024):
     """Config 2's geometry, signal and node-count rule on a band omega <= 30 (N from 48 to ~140)
     with 129 frequencies, H = 12 and fewer steps, sized for the oracle to finish in seconds."""
     return config2(seed=seed, L=L, M=M, W=W, H=H, n_period=n_period, T=14.0)
+
+
+def config3(seed=3, L=2049, M=8, W=200.0, Q=4, H=12.0, n_period=8192, carrier=30.0, centre=20.0, width=8.0,
+            N_min=32, N_off=16, N_ppw=3.6, n_tout=601, T=60.0):
+    """Interior problem in a seeded star-shaped cavity r(theta) = 1 + 0.3 cos(5 theta + phi), split into 12
+    overlapping arcs; boundary data = +field of a point source at (2.5, 0.7) outside the cavity (so the
+    exact interior solution is u^i); f(t) = sin(30t) exp(-((t-20)/8)^2) on t in [0, 60] with 4 windows
+    (H = 12); N = max(32, ceil(3.6 omega len) + 16) from 32 to ~760 over omega in [0, 200] with 2049 points
+    (dt = pi/400 internally); M = 8; 5 interior observation points.  Its cross rows (~10^11 entries) do not
+    fit in device memory, so the job evaluates them every step (cross_mode = 1)."""
+    rng = np.random.default_rng(seed)
+    curves = [star(0.3, 5, float(rng.uniform(0.0, 2.0 * math.pi)))]
+    arcs = split_closed_curve(0, 12, 1.25, 0.0)
+    signal = _signal(0, +1.0, 1.0, carrier, centre, width, z0=(2.5, 0.7))
+    obs = [(0.0, 0.0), (0.3, 0.2), (-0.4, 0.1), (0.1, -0.5), (-0.2, -0.3)]
+    options = _options(W, L, M, Q, H, n_period, obs, 0.0, T / (n_tout - 1), n_tout, N_min=N_min, N_off=N_off,
+                       N_ppw=N_ppw, interior=1)
+    options["cross_mode"] = 1
+    return {"name": "star12-cavity", "curves": curves, "arcs": arcs, "signal": signal, "options": options}
+
+
+def config3_reduced(seed=3, L=129, M=2, W=16.0, Q=2, n_period=1024):
+    """Config 3's cavity, arcs and node rule on omega in [0, 16] (N from 32 to ~76), the carrier moved
+    into that band (sin(6t) exp(-((t-8)/3)^2)), Q = 2 windows."""
+    return config3(seed=seed, L=L, M=M, W=W, Q=Q, H=12.0, n_period=n_period, carrier=6.0, centre=8.0,
+                   width=3.0, n_tout=121, T=30.0)
 
 
 def random_small(seed, n_arcs_per_curve=3, n_curves=1, L=33, M=2, Q=1, N_fixed=0, W=10.0, kind=None,
