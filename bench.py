@@ -464,6 +464,62 @@ def ours(args):
     return 0
 
 
+def star12(args):
+    """Auxiliary measurement (not the headline): one config-3 job per form -- the 12-arc star cavity, N 32..760,
+    2048 solved frequencies, Q = 4 windows, M = 8, cross rows evaluated every step -- device-timed like the
+    main line; prints one JSON line."""
+    import torch
+
+    import workloads
+    from paper_2507_05725_gb300 import fthms as F
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    problem = workloads.config3()
+    o = problem["options"]
+    P, L, M, Q = len(problem["arcs"]), o["L"], o["M"], o["Q"]
+    solves = P * (L - 1) * M * Q
+    ctx = F.fthms_create(0, 0, stream.cuda_stream)
+    forms, dens = {}, {}
+    for precision in (1, 0):
+        job = F.Job(ctx, problem, keep_densities=False, precision=precision)
+        for _ in range(args.warmup):
+            job.run()
+        job.wait()
+        F.fthms_profile(job.req, True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(0) as clk:
+            e0.record(stream)
+            for _ in range(args.steps):
+                job.run()
+            e1.record(stream)
+            torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        stages = F.fthms_stage_times(job.req)
+        st = job.stats()
+        dens[precision] = [job.densities(j, 0, 0) for j in (0, P // 2)]
+        job.release()
+        forms["mixed" if precision else "plain_fp64"] = {
+            "value": solves / (ms * 1e-3), "ms_per_step": ms, "device_gb": st["device_bytes"] / 1e9,
+            "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()}, "clocks": clk.summary()}
+    num = den = 0.0
+    for a, c in zip(dens[0], dens[1]):
+        for l in a:
+            num += float(np.sum(np.abs(a[l] - c[l]) ** 2))
+            den += float(np.sum(np.abs(a[l]) ** 2))
+    forms["mixed"]["rel_l2_vs_fp64_densities_arcs_0_6"] = math.sqrt(num / den)
+    F.fthms_destroy(ctx)
+    print(json.dumps({"metric": METRIC, "value": forms["mixed"]["value"], "unit": "solves/s",
+                      "ms_per_step": forms["mixed"]["ms_per_step"], "steps": args.steps, "warmup": args.warmup,
+                      "higher_is_better": True, "data": "synthetic",
+                      "config": {"workload": "star12-cavity: 12 arcs, N 32..760, L=2049 on [0,200], M=8, Q=4, "
+                                             "cross rows evaluated every step (one job per step)",
+                                 "solves_per_step": solves},
+                      "forms": forms}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -473,9 +529,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--plain-only", action="store_true", help="time the plain FP64 form only (profiling runs)")
+    ap.add_argument("--workload", default="4obstacles", choices=["4obstacles", "star12"],
+                    help="star12: auxiliary single-GPU measurement of the 12-arc cavity (config 3)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.workload == "star12":
+        return star12(args)
     return ours(args)
 
 
