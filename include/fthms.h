@@ -84,7 +84,9 @@ typedef struct {
  *  M         : multiple-scattering steps (Algorithm 1's outer loop).
  *  Q, H      : 1 <= Q <= 4 time windows sqcap_q(t) = sqcap(t - s_q), s_q = 1.5 (q-1) H (Section 5).
  *  n_period  : internal time samples per period 2 pi/h of the frequency grid (power of two,
- *              16..16384); dt = 2 pi/(h n_period), t_n = -H + n dt covering [-H, s_Q + H].
+ *              16..16384); dt = 2 pi/(h n_period), t_n = -H + n dt covering [-H, s_Q + H].  The time
+ *              kernels keep one period and these N_T samples of a node in shared memory:
+ *              16 n_period + 8 N_T <= 232448 bytes, else EINVAL.
  *  obs_xy    : n_obs observation points (x, y), host array of 2*n_obs doubles.
  *  n_tout, tout0, dtout : output times tout0 + k dtout of the traces u_M(z, t) (eq. mult-scatt-int).
  *  precision : 0 = FP64 throughout.  1 = mixed form: FP32 LU factors; solutions refined against the

@@ -175,6 +175,10 @@ fthms_status upload_job(fthms_req* r) {
     J.row_cap = std::max(J.row_cap, rows);
     J.ph_cap = std::max(J.ph_cap, nsum);
   }
+  if (!J.mixed && p.opt.cross_mode == 0 &&
+      (size_t)J.Q * (J.acc_cap + J.row_cap + J.ph_cap) * 16 > (size_t)227 * 1024)
+    return fail(FTHMS_EINVAL, "fthms_prepare: the stored cross rows of one (arc, frequency) group do not fit the "
+                              "apply's shared memory; use cross_mode 1");
   J.h = p.h; J.dt = p.dt; J.sign = p.sig.sign;
   J.sig_kind = p.sig.kind;
   J.z0x = p.sig.z0[0]; J.z0y = p.sig.z0[1];

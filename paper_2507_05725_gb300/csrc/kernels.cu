@@ -556,7 +556,7 @@ __device__ void tri_solve(C* b, int Q, int N, const C* __restrict__ A, const int
 __global__ void __launch_bounds__(32 * kSolveWarps) k_solve(DevJob J, int m) {
   extern __shared__ double2 shs[];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int slot = blockIdx.x * kSolveWarps + wid;
+  const int slot = blockIdx.x * (blockDim.x >> 5) + wid;
   if (slot >= J.nsys) return;
   const int sidx = J.sys_order[slot];
   const SysDesc s = J.sys[sidx];
@@ -1053,14 +1053,15 @@ __device__ __forceinline__ void residual_rows(const float4* __restrict__ Adf, co
 __global__ void __launch_bounds__(32 * kSolveWarps) k_solve_mixed(DevJob J, int m) {
   extern __shared__ __align__(16) unsigned char shm_raw[];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int slot = blockIdx.x * kSolveWarps + wid;
+  const int nw = blockDim.x >> 5;
+  const int slot = blockIdx.x * nw + wid;
   if (slot >= J.nsys) return;
   const int sidx = J.sys_order[slot];
   const SysDesc s = J.sys[sidx];
   const int N = s.N, Q = J.Q;
   const size_t per = (size_t)Q * J.max_n;
   float4* ph = reinterpret_cast<float4*>(shm_raw) + (size_t)wid * per;                        // df64
-  float2* b = reinterpret_cast<float2*>(reinterpret_cast<float4*>(shm_raw) + kSolveWarps * per) + (size_t)wid * per;
+  float2* b = reinterpret_cast<float2*>(reinterpret_cast<float4*>(shm_raw) + nw * per) + (size_t)wid * per;
   const float2* __restrict__ L32 = J.LU32 + s.mat_off;
   const float4* __restrict__ Adf = reinterpret_cast<const float4*>(J.A) + s.mat_off;
   const int* __restrict__ piv = J.piv + s.piv_off;
@@ -1520,19 +1521,32 @@ cudaError_t launch_restrict(const DevJob& J, cudaStream_t st, int* launches) {
   return cudaGetLastError();
 }
 
+// Warps (systems) per solve block: kSolveWarps, fewer when their right-hand sides would not fit in the
+// 227 KB of shared memory a block may use (large Q x N).
+static int solve_warps(size_t bytes_per_warp) {
+  const size_t cap = 227 * 1024;
+  int nw = kSolveWarps;
+  while (nw > 1 && (size_t)nw * bytes_per_warp > cap) --nw;
+  return nw;
+}
+
 cudaError_t launch_solve(const DevJob& J, int m, cudaStream_t st, int* launches) {
   if (J.mixed) {
-    size_t sh = (size_t)kSolveWarps * J.Q * J.max_n * (sizeof(float4) + sizeof(float2));
+    const size_t per = (size_t)J.Q * J.max_n * (sizeof(float4) + sizeof(float2));
+    const int nw = solve_warps(per);
+    size_t sh = (size_t)nw * per;
     cudaError_t e = cudaFuncSetAttribute(k_solve_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
     if (e != cudaSuccess) return e;
-    k_solve_mixed<<<cdiv(J.nsys, kSolveWarps), 32 * kSolveWarps, sh, st>>>(J, m);
+    k_solve_mixed<<<cdiv(J.nsys, nw), 32 * nw, sh, st>>>(J, m);
     *launches += 1;
     return cudaGetLastError();
   }
-  size_t sh = (size_t)kSolveWarps * J.Q * J.max_n * sizeof(double2);
+  const size_t per = (size_t)J.Q * J.max_n * sizeof(double2);
+  const int nw = solve_warps(per);
+  size_t sh = (size_t)nw * per;
   cudaError_t e = cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
   if (e != cudaSuccess) return e;
-  k_solve<<<cdiv(J.nsys, kSolveWarps), 32 * kSolveWarps, sh, st>>>(J, m);
+  k_solve<<<cdiv(J.nsys, nw), 32 * nw, sh, st>>>(J, m);
   *launches += 1;
   return cudaGetLastError();
 }

@@ -255,6 +255,14 @@ int build_plan(const fthms_curve* curves, int ncurves, const fthms_arc* arcs, in
     err = "internal time grid longer than 65536 samples";
     return FTHMS_EINVAL;
   }
+  // The time kernels hold one period (n_period complex values) and the internal samples (NT doubles) of a
+  // transfer node in shared memory.
+  if ((size_t)p.K * 16 + (size_t)p.NT * 8 > (size_t)227 * 1024) {
+    snprintf(buf, sizeof buf, "n_period (%d) and the internal time samples (%d) need %zu bytes of shared memory; "
+             "at most 232448 (lower n_period, H or Q)", p.K, p.NT, (size_t)p.K * 16 + (size_t)p.NT * 8);
+    err = buf;
+    return FTHMS_EINVAL;
+  }
   p.win.assign((size_t)p.Q * p.NT, 0.0);
   for (int q = 0; q < p.Q; ++q)
     for (int n = 0; n < p.NT; ++n) {

@@ -43,6 +43,14 @@ def test_invalid_geometry_and_options(F):
     bad = copy.deepcopy(p)
     bad["options"]["n_period"] = 1000               # not a power of two
     assert _status(F, lambda: F.fthms_prepare(ctx, F.Marshalled(bad)))[0] == F.FTHMS_EINVAL
+    bad = copy.deepcopy(p)                          # a period and time grid too long for the time kernels
+    bad["options"]["n_period"] = 16384
+    bad["options"]["Q"] = 4
+    st, msg = _status(F, lambda: F.fthms_prepare(ctx, F.Marshalled(bad)))
+    assert st == F.FTHMS_EINVAL and "shared memory" in msg
+    bad = copy.deepcopy(p)                          # unknown cross mode
+    bad["options"]["cross_mode"] = 2
+    assert _status(F, lambda: F.fthms_prepare(ctx, F.Marshalled(bad)))[0] == F.FTHMS_EINVAL
     st, _ = _status(F, lambda: F.fthms_prepare(ctx, F.Marshalled(p, precision=2)))
     assert st == F.FTHMS_ENOTIMPL
     F.fthms_destroy(ctx)
