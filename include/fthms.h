@@ -208,6 +208,15 @@ enum {
   FTHMS_NSTAGES = 10
 };
 
+/* Pick launch shapes for this job's hardware and sizes: runs the job once, then times each tunable stage
+ * `reps` times per candidate -- warps (systems) per solve block {4, 2, 1}, threads per cross-assembly block
+ * {128, 64, 256} (stored rows only), per time-transform block {256, 128, 512} and per restriction block
+ * {128, 64, 256} -- and keeps the fastest for later fthms_run calls (a captured graph is dropped and
+ * re-captured).  Every candidate computes the same numbers, so results are bitwise unchanged.  shapes
+ * (NULL allowed) receives the four choices.  The job's earlier results are overwritten: call
+ * fthms_run afterwards.  Not in the paper (a batching aid of this library). */
+fthms_status fthms_autotune(fthms_req* req, int reps, int* shapes);
+
 /* enable != 0: fthms_run captures the job's whole pipeline (all stages and steps) into a CUDA graph on
  * its first run and replays it afterwards as one launch; the graph is rebuilt never (the job's inputs
  * are fixed at prepare).  Runs with per-stage profiling enabled launch stage by stage. */

@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <deque>
+#include <functional>
 #include <map>
 #include <mutex>
 #include <set>
@@ -218,6 +219,7 @@ fthms_status upload_job(fthms_req* r) {
   J.grp_res_off = nullptr;
   J.apply_res = nullptr;
   J.otf = p.opt.cross_mode == 1 ? 1 : 0;
+  J.shape_solve = J.shape_asm = J.shape_time = J.shape_restr = 0;
   J.n_otf = 0;
   J.otf_tasks = nullptr;
   J.wn_off = nullptr;
@@ -387,6 +389,26 @@ fthms_status enqueue_stages(fthms_req* r, bool bracket) {
     r->ran = true;
   }
   r->launches = nl;
+  return FTHMS_OK;
+}
+
+// Time `reps` back-to-back launches of one stage (milliseconds per launch).
+template <class F>
+fthms_status time_stage(fthms_req* r, int reps, float* ms, F&& launch) {
+  cudaStream_t st = r->stream;
+  cudaEvent_t a = nullptr, b = nullptr;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  cudaError_t e = launch();            // warm-up (attributes, caches)
+  if (e == cudaSuccess) e = cudaEventRecord(a, st);
+  for (int k = 0; k < reps && e == cudaSuccess; ++k) e = launch();
+  if (e == cudaSuccess) e = cudaEventRecord(b, st);
+  if (e == cudaSuccess) e = cudaEventSynchronize(b);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(ms, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (e != cudaSuccess) return cuda_fail(e, "fthms_autotune");
+  *ms /= reps;
   return FTHMS_OK;
 }
 
@@ -687,6 +709,57 @@ fthms_status fthms_release(fthms_req* req) {
 }
 
 const char* fthms_last_error(void) { return g_last_error.c_str(); }
+
+fthms_status fthms_autotune(fthms_req* req, int reps, int* shapes) {
+  if (!req) return fail(FTHMS_EINVAL, "fthms_autotune: NULL job");
+  if (!req->ctx) return fail(FTHMS_EINVAL, "fthms_autotune: the job's context was destroyed");
+  if (reps < 1) return fail(FTHMS_EINVAL, "fthms_autotune: reps must be >= 1");
+  TRY(ensure_device(req->ctx->device));
+  if (req->graph) {                    // a captured graph holds the old launch shapes
+    cudaGraphExecDestroy(req->graph);
+    req->graph = nullptr;
+  }
+  const bool prof = req->profiling;
+  req->profiling = false;
+  fthms_status s = enqueue_stages(req);   // valid factors, densities and spectra for every stage
+  req->profiling = prof;
+  TRY(s);
+  CK(cudaStreamSynchronize(req->stream));
+  DevJob& J = req->J;
+  cudaStream_t st = req->stream;
+  int nl = 0;
+  struct Knob {
+    int* field;
+    std::vector<int> cand;
+    std::function<cudaError_t()> launch;
+  };
+  std::vector<Knob> knobs;
+  knobs.push_back({&J.shape_solve, {4, 2, 1}, [&] { return launch_solve(J, 1, st, &nl); }});
+  if (!J.otf) knobs.push_back({&J.shape_asm, {128, 64, 256}, [&] { return launch_cross_assemble(J, st, &nl); }});
+  knobs.push_back({&J.shape_time, {256, 128, 512}, [&] { return launch_synth_fwd(J, st, &nl); }});
+  knobs.push_back({&J.shape_restr, {128, 64, 256}, [&] { return launch_restrict(J, st, &nl); }});
+  for (Knob& k : knobs) {
+    float best = 0.f;
+    int pick = k.cand[0];
+    for (int c : k.cand) {
+      *k.field = c;
+      float ms = 0.f;
+      TRY(time_stage(req, reps, &ms, k.launch));
+      if (c == k.cand[0] || ms < best) {
+        best = ms;
+        pick = c;
+      }
+    }
+    *k.field = pick;
+  }
+  if (shapes) {
+    shapes[0] = J.shape_solve;
+    shapes[1] = J.shape_asm;
+    shapes[2] = J.shape_time;
+    shapes[3] = J.shape_restr;
+  }
+  return FTHMS_OK;
+}
 
 fthms_status fthms_use_graph(fthms_req* req, int enable) {
   if (!req) return fail(FTHMS_EINVAL, "fthms_use_graph: NULL job");

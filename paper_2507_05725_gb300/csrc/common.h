@@ -80,8 +80,11 @@ struct CrossAsm {
 };
 
 // On-the-fly cross task (cross_mode 1): assembly task `task`, restricted to the frequencies l0..l1
-// (at most kOtfBand / Q of them, so that the per-frequency sums stay in registers).
-constexpr int kOtfBand = 8;
+// (at most otf_band(Q) of them: the per-frequency sums of a CTA take 128 x Q x otf_band(Q) complex
+// values of shared memory, at most 32 KB).
+constexpr int kOtfBand = 16;
+template <int Q> struct OtfBand { static constexpr int value = kOtfBand / Q > 4 ? kOtfBand / Q : 4; };
+inline int otf_band(int Q) { return kOtfBand / Q > 4 ? kOtfBand / Q : 4; }   // host side of OtfBand
 struct CrossOtf {
   int task;
   int l0, l1;

@@ -580,6 +580,7 @@ __global__ void __launch_bounds__(32 * kSolveWarps) k_solve(DevJob J, int m) {
 // ---------------------------------------------------------------------------------------------
 // Cross assembly: stored rows of S_Gamma_j for one (pair, frequency band, 8-row chunk).
 constexpr int kAsmThreads = 128;   // small blocks: an 8-row task leaves a short last pass
+constexpr int kAsmMaxThreads = 256;   // largest cross-assembly block a tuned launch may use
 constexpr int kAsmRows = 8;
 
 // A stored cross entry: FP64, or double-float (float4, same 16 bytes) in the mixed-precision form.
@@ -721,7 +722,7 @@ __device__ __forceinline__ double2 asym_entry(AsymState& a, const PairSetup& s, 
   return make_double2(amp * fma(s.beta, t1, -t2), amp * t1);
 }
 
-__global__ void __launch_bounds__(kAsmThreads) k_cross_assemble(DevJob J) {
+__global__ void __launch_bounds__(kAsmMaxThreads) k_cross_assemble(DevJob J) {
   extern __shared__ double sha[];
   const CrossAsm task = J.asms[blockIdx.x];
   const PairDesc pr = J.pairs[task.pair];
@@ -752,7 +753,7 @@ __global__ void __launch_bounds__(kAsmThreads) k_cross_assemble(DevJob J) {
   double* lh = lnl + kAsmBand;
   df* invl_d = reinterpret_cast<df*>(lh + kAsmBand);      // the same as double-float (mixed form)
   df* rsql_d = invl_d + kAsmBand;
-  for (int b = threadIdx.x; b < nl; b += kAsmThreads) {
+  for (int b = threadIdx.x; b < nl; b += blockDim.x) {
     const int l = task.l0 + b;
     invl[b] = 1.0 / l;
     rsql[b] = rsqrt((double)l);
@@ -765,7 +766,7 @@ __global__ void __launch_bounds__(kAsmThreads) k_cross_assemble(DevJob J) {
   }
   __syncthreads();
   const long long* eo = J.e_off + (long long)task.pair * J.L;
-  for (int e = threadIdx.x; e < task.nrows * N; e += kAsmThreads) {
+  for (int e = threadIdx.x; e < task.nrows * N; e += blockDim.x) {
     const int r = e % task.nrows, i = e / task.nrows;
     const CrossTgt t = tg[r];
     const PairSetup ps = pair_setup(J, t, J.node_x[pn.off + i], J.node_y[pn.off + i], J.node_t[pn.off + i],
@@ -841,17 +842,17 @@ __global__ void __launch_bounds__(kAsmThreads) k_near_weights(DevJob J) {
   near_weights_block(tg, task.nrows, task.N, shn, shn + 4 * task.N, J.wn + off);
 }
 
-// One CTA per (assembly task, band of at most kOtfBand / Q frequencies): thread (row r, source group
-// g) evaluates the entries of its sources i = g, g + 16, ... for every frequency of the band exactly as
-// k_cross_assemble does, multiplies them by the densities of the current step and sums; the 16 partial
-// sums of a row are then added in group order (deterministic) into the per-row results, which
-// k_cross_reduce adds per target in block order.
+// One CTA per (assembly task, band of at most otf_band(Q) frequencies): thread (row r, source group g)
+// evaluates the entries of its sources i = g, g + 16, ... for every frequency of the band exactly as
+// k_cross_assemble does, multiplies them by the densities of the current step and adds them into its
+// own slot of partial sums in shared memory; the 16 partial sums of a row are then added in group
+// order (deterministic) into the per-row results, which k_cross_reduce adds per target in block order.
 template <int Q>
 __global__ void __launch_bounds__(kAsmThreads) k_cross_otf(DevJob J) {
-  constexpr int B = kOtfBand / Q > 0 ? kOtfBand / Q : 1;
+  constexpr int B = OtfBand<Q>::value;
   constexpr int G = kAsmThreads / kAsmRows;          // source groups
-  extern __shared__ double2 sho[];                    // [G][kAsmRows][Q * B] partial sums
-  __shared__ double tb[4][kOtfBand];                  // 1/l, 1/sqrt(l), ln l, l h
+  extern __shared__ double2 sho[];                    // [G][kAsmRows][Q * B] partial sums (thread order)
+  __shared__ double tb[4][B];                         // 1/l, 1/sqrt(l), ln l, l h
   const CrossOtf ot = J.otf_tasks[blockIdx.x];
   const CrossAsm task = J.asms[ot.task];
   const PairDesc pr = J.pairs[task.pair];
@@ -867,17 +868,14 @@ __global__ void __launch_bounds__(kAsmThreads) k_cross_otf(DevJob J) {
     tb[2][threadIdx.x] = log((double)l);
     tb[3][threadIdx.x] = l * J.h;
   }
+  double2* mine = sho + threadIdx.x * (Q * B);
+  for (int e = 0; e < Q * B; ++e) mine[e] = make_double2(0.0, 0.0);
   __syncthreads();
   const double w = kPiD / N, qw = 0.25 * w, invw = N * kInvPi;
   const double A1 = -0.5 * kInvPi * w;
   const double camp = kSqrtTwoOverPi * qw;
   const double inv_h = 1.0 / J.h;
   const int r = threadIdx.x % kAsmRows, g = threadIdx.x / kAsmRows;
-  double2 acc[Q][B];
-#pragma unroll
-  for (int q = 0; q < Q; ++q)
-#pragma unroll
-    for (int b = 0; b < B; ++b) acc[q][b] = make_double2(0.0, 0.0);
   if (r < task.nrows) {
     const CrossTgt t = tg[r];
     const SysDesc* sj = J.sys + (long long)pr.j * (J.L - 1) + (ot.l0 - 1);   // systems (j, l0..l1)
@@ -886,32 +884,24 @@ __global__ void __launch_bounds__(kAsmThreads) k_cross_otf(DevJob J) {
                                       t.near ? Wn[r * N + i] : 0.0, ot.l0, w, invw, inv_h);
       AsymState as{};
       bool started = false;
-#pragma unroll
-      for (int b = 0; b < B; ++b) {
-        if (b < nl) {
-          const int l = ot.l0 + b;
-          double2 E;
-          if (l < ps.lsw) {
-            E = taylor_entry(ps, tb[3][b], tb[2][b], A1, qw);
-          } else {
-            if (!started) {
-              as = asym_start(ps, tb[3][b], camp);
-              started = true;
-            }
-            E = asym_entry(as, ps, tb[3][b], tb[0][b], tb[1][b]);
+      for (int b = 0; b < nl; ++b) {
+        const int l = ot.l0 + b;
+        double2 E;
+        if (l < ps.lsw) {
+          E = taylor_entry(ps, tb[3][b], tb[2][b], A1, qw);
+        } else {
+          if (!started) {
+            as = asym_start(ps, tb[3][b], camp);
+            started = true;
           }
-          const double2* ph = J.phi + sj[b].vec_off + i;
-#pragma unroll
-          for (int q = 0; q < Q; ++q) acc[q][b] = cfma(E, ph[q * N], acc[q][b]);
+          E = asym_entry(as, ps, tb[3][b], tb[0][b], tb[1][b]);
         }
+        const double2* ph = J.phi + sj[b].vec_off + i;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) mine[q * B + b] = cfma(E, ph[q * N], mine[q * B + b]);
       }
     }
   }
-  double2* red = sho + (g * kAsmRows + r) * (Q * B);
-#pragma unroll
-  for (int q = 0; q < Q; ++q)
-#pragma unroll
-    for (int b = 0; b < B; ++b) red[q * B + b] = acc[q][b];
   __syncthreads();
   for (int e = threadIdx.x; e < task.nrows * Q * nl; e += kAsmThreads) {
     const int rr = e / (Q * nl), q = (e / nl) % Q, b = e % nl;
@@ -1236,6 +1226,7 @@ __global__ void __launch_bounds__(kApplyThreads) k_cross_reduce(DevJob J) {
 // ---------------------------------------------------------------------------------------------
 // Time-domain kernels: one CTA per active transfer node.
 constexpr int kTimeThreads = 256;
+constexpr int kTimeMaxThreads = 512;   // largest time-transform block a tuned launch may use
 
 // In-place radix-2 decimation-in-time FFT, y_r = sum_b X_b e^{-2 pi i b r/K}; input in
 // bit-reversed order.
@@ -1305,7 +1296,7 @@ __device__ double incident_u(const DevJob& J, double X, double Y, double t) {
   return acc * dv * (0.5 * kInvPi);
 }
 
-__global__ void __launch_bounds__(kTimeThreads) k_incident(DevJob J) {
+__global__ void __launch_bounds__(kTimeMaxThreads) k_incident(DevJob J) {
   extern __shared__ double2 sht[];
   const int a = blockIdx.x;
   const int k = J.act_arc[a], x = J.act_idx[a];
@@ -1319,7 +1310,7 @@ __global__ void __launch_bounds__(kTimeThreads) k_incident(DevJob J) {
   forward_all(J, g, buf, J.Gt + (J.tr_off[k] + x) * J.Q * J.L);
 }
 
-__global__ void __launch_bounds__(kTimeThreads) k_synth_fwd(DevJob J) {
+__global__ void __launch_bounds__(kTimeMaxThreads) k_synth_fwd(DevJob J) {
   extern __shared__ double2 sht[];
   const int a = blockIdx.x;
   const int k = J.act_arc[a], x = J.act_idx[a];
@@ -1354,8 +1345,9 @@ __global__ void __launch_bounds__(kTimeThreads) k_synth_fwd(DevJob J) {
 // ---------------------------------------------------------------------------------------------
 // Restriction of transfer-mesh spectra to the solve nodes of every system.
 constexpr int kRestrThreads = 128;
+constexpr int kRestrMaxThreads = 256;   // largest restriction block a tuned launch may use
 
-__global__ void __launch_bounds__(kRestrThreads) k_restrict(DevJob J) {
+__global__ void __launch_bounds__(kRestrMaxThreads) k_restrict(DevJob J) {
   extern __shared__ double2 shr[];
   const int sidx = blockIdx.x;
   const SysDesc s = J.sys[sidx];
@@ -1485,7 +1477,7 @@ cudaError_t launch_cross_assemble(const DevJob& J, cudaStream_t st, int* launche
   size_t sh = ((size_t)(4 + 2 * kAsmRows) * J.max_n + 6 * kAsmBand) * sizeof(double);
   cudaError_t e = cudaFuncSetAttribute(k_cross_assemble, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
   if (e != cudaSuccess) return e;
-  k_cross_assemble<<<J.n_asm, kAsmThreads, sh, st>>>(J);
+  k_cross_assemble<<<J.n_asm, J.shape_asm > 0 ? J.shape_asm : kAsmThreads, sh, st>>>(J);
   *launches += 1;
   return cudaGetLastError();
 }
@@ -1497,7 +1489,7 @@ cudaError_t launch_incident(const DevJob& J, cudaStream_t st, int* launches) {
   size_t sh = time_smem(J);
   cudaError_t e = cudaFuncSetAttribute(k_incident, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
   if (e != cudaSuccess) return e;
-  k_incident<<<J.n_act, kTimeThreads, sh, st>>>(J);
+  k_incident<<<J.n_act, J.shape_time > 0 ? J.shape_time : kTimeThreads, sh, st>>>(J);
   *launches += 1;
   return cudaGetLastError();
 }
@@ -1507,7 +1499,7 @@ cudaError_t launch_synth_fwd(const DevJob& J, cudaStream_t st, int* launches) {
   size_t sh = time_smem(J);
   cudaError_t e = cudaFuncSetAttribute(k_synth_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
   if (e != cudaSuccess) return e;
-  k_synth_fwd<<<J.n_act, kTimeThreads, sh, st>>>(J);
+  k_synth_fwd<<<J.n_act, J.shape_time > 0 ? J.shape_time : kTimeThreads, sh, st>>>(J);
   *launches += 1;
   return cudaGetLastError();
 }
@@ -1516,16 +1508,16 @@ cudaError_t launch_restrict(const DevJob& J, cudaStream_t st, int* launches) {
   size_t sh = (size_t)J.Q * J.max_nmax * sizeof(double2);
   cudaError_t e = cudaFuncSetAttribute(k_restrict, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
   if (e != cudaSuccess) return e;
-  k_restrict<<<J.nsys, kRestrThreads, sh, st>>>(J);
+  k_restrict<<<J.nsys, J.shape_restr > 0 ? J.shape_restr : kRestrThreads, sh, st>>>(J);
   *launches += 1;
   return cudaGetLastError();
 }
 
 // Warps (systems) per solve block: kSolveWarps, fewer when their right-hand sides would not fit in the
 // 227 KB of shared memory a block may use (large Q x N).
-static int solve_warps(size_t bytes_per_warp) {
+static int solve_warps(size_t bytes_per_warp, int wanted) {
   const size_t cap = 227 * 1024;
-  int nw = kSolveWarps;
+  int nw = wanted > 0 && wanted < kSolveWarps ? wanted : kSolveWarps;
   while (nw > 1 && (size_t)nw * bytes_per_warp > cap) --nw;
   return nw;
 }
@@ -1533,7 +1525,7 @@ static int solve_warps(size_t bytes_per_warp) {
 cudaError_t launch_solve(const DevJob& J, int m, cudaStream_t st, int* launches) {
   if (J.mixed) {
     const size_t per = (size_t)J.Q * J.max_n * (sizeof(float4) + sizeof(float2));
-    const int nw = solve_warps(per);
+    const int nw = solve_warps(per, J.shape_solve);
     size_t sh = (size_t)nw * per;
     cudaError_t e = cudaFuncSetAttribute(k_solve_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
     if (e != cudaSuccess) return e;
@@ -1542,7 +1534,7 @@ cudaError_t launch_solve(const DevJob& J, int m, cudaStream_t st, int* launches)
     return cudaGetLastError();
   }
   const size_t per = (size_t)J.Q * J.max_n * sizeof(double2);
-  const int nw = solve_warps(per);
+  const int nw = solve_warps(per, J.shape_solve);
   size_t sh = (size_t)nw * per;
   cudaError_t e = cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
   if (e != cudaSuccess) return e;
@@ -1594,7 +1586,7 @@ cudaError_t launch_near_weights(const DevJob& J, cudaStream_t st, int* launches)
 
 template <int Q>
 static cudaError_t launch_cross_otf_q(const DevJob& J, cudaStream_t st) {
-  constexpr int B = kOtfBand / Q > 0 ? kOtfBand / Q : 1;
+  constexpr int B = OtfBand<Q>::value;
   const size_t sh = (size_t)kAsmThreads * Q * B * sizeof(double2);
   const size_t sh_red = (size_t)Q * J.acc_cap * sizeof(double2);
   cudaError_t e = cudaFuncSetAttribute(k_cross_reduce<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh_red);

@@ -42,6 +42,9 @@ struct DevJob {
   int n_slices, slice_ph_cap;
   // cross_mode 1: cross rows evaluated every step (nothing stored)
   int otf, n_otf;
+  // launch shapes chosen by fthms_autotune (0 = built-in default): warps per solve block, threads per
+  // cross-assembly block, per time-transform block and per restriction block
+  int shape_solve, shape_asm, shape_time, shape_restr;
   const CrossOtf* otf_tasks;
   const long long* wn_off;   // per assembly task: near weights offset or -1
   double* wn;                // near weights, nrows x N per assembly task with near rows

@@ -508,8 +508,8 @@ int build_plan(const fthms_curve* curves, int ncurves, const fthms_arc* arcs, in
       }
     }
     // Near weights once per job (they depend on the target and N only); tasks of at most
-    // kOtfBand / Q frequencies each.
-    const int band = std::max(1, kOtfBand / p.Q);
+    // otf_band(Q) frequencies each.
+    const int band = otf_band(p.Q);
     p.wn_off.assign(p.asms.size(), -1);
     for (size_t a = 0; a < p.asms.size(); ++a) {
       const CrossAsm& t = p.asms[a];

@@ -97,6 +97,7 @@ def _load():
         "fthms_server_release": (st, [vp, C.c_longlong]),
         "fthms_server_destroy": (st, [vp]),
         "fthms_use_graph": (st, [vp, C.c_int]),
+        "fthms_autotune": (st, [vp, C.c_int, C.POINTER(C.c_int)]),
         "fthms_profile": (st, [vp, C.c_int]),
         "fthms_stage_times": (st, [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
     }
@@ -114,7 +115,8 @@ EXPORTED = ["fthms_create", "fthms_destroy", "fthms_prepare", "fthms_run", "fthm
             "fthms_stats", "fthms_release", "fthms_last_error", "fthms_bessel0", "fthms_assemble_self",
             "fthms_profile", "fthms_stage_times", "fthms_assemble_self_noalloc", "fthms_server_create",
             "fthms_server_submit", "fthms_server_poll", "fthms_server_wait", "fthms_server_result",
-            "fthms_server_latency", "fthms_server_release", "fthms_server_destroy", "fthms_use_graph"]
+            "fthms_server_latency", "fthms_server_release", "fthms_server_destroy", "fthms_use_graph",
+            "fthms_autotune"]
 
 
 def _check(status):
@@ -220,6 +222,13 @@ def fthms_stats(req):
     s = fthms_stats_t()
     _check(LIB.fthms_stats(req, C.byref(s)))
     return {k: getattr(s, k) for k, _ in fthms_stats_t._fields_}
+
+
+def fthms_autotune(req, reps=3):
+    """Launch shapes (solve warps, assembly threads, time threads, restriction threads) chosen for the job."""
+    out = (C.c_int * 4)()
+    _check(LIB.fthms_autotune(req, int(reps), out))
+    return list(out)
 
 
 def fthms_use_graph(req, enable=True):

@@ -368,3 +368,27 @@ def test_config3_reduced_parity(F, ctx):
 
 def test_config3_reduced_mixed_parity(F, ctx):
     assert _parity_mixed(F, ctx, wl.config3_reduced()) < MIXED_TOL
+
+
+# ---- autotuned launch shapes -------------------------------------------------------------------------
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_autotune_keeps_results_bitwise(F, ctx, precision):
+    """Tuned launch shapes change no number: densities and traces identical to the default shapes."""
+    problem = wl.random_small(5, n_curves=2, n_arcs_per_curve=2, Q=2, L=65, M=2)
+    a = F.Job(ctx, problem, precision=precision).run().wait()
+    b = F.Job(ctx, problem, precision=precision)
+    try:
+        shapes = F.fthms_autotune(b.req, 2)
+        assert shapes[0] in (1, 2, 4) and shapes[1] in (64, 128, 256)
+        assert shapes[2] in (128, 256, 512) and shapes[3] in (64, 128, 256)
+        b.run().wait()
+        assert np.array_equal(a.traces(), b.traces())
+        for j in range(len(problem["arcs"])):
+            for q in range(2):
+                da, db = a.densities(j, 0, q), b.densities(j, 0, q)
+                for l in da:
+                    assert np.array_equal(da[l], db[l])
+    finally:
+        a.release()
+        b.release()
