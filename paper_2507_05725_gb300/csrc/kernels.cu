@@ -149,25 +149,41 @@ __global__ void k_rlog(DevJob J) {
 // size M evaluated at the first-kind nodes of size N, in the closed form
 //   l_x(t_i) = T_M(t_i) sin(beta_x) (-1)^x / (M (t_i - tau_x))
 // with the phases reduced exactly through D = (2i+1)M - (2x+1)N and S = (2i+1)M + (2x+1)N:
-//   l_x(t_i) = sin(beta_x) sinpi(D/(2N)) / (2M sinpi(S/(4NM)) sinpi(D/(4NM))),  = 1 when D = 0.
+//   l_x(t_i) = sin(beta_x) sinpi(D/(2N)) / (2M sinpi(S/(4NM)) sinpi(D/(4NM))),  = 1 when D = 0,
+// where sinpi(D/(2N)) = (-1)^(x+1) cospi((2i+1)M/(2N)) (the argument reduced mod 4N in integers) and
+// sinpi(S/(4NM)) = sin(a_i + g_x), a_i = pi(2i+1)/(4N), g_x = pi(2x+1)/(4M), both in (0, pi/2), so
+// only sinpi(D/(4NM)) is evaluated per entry.  One CTA per (N, M) pair; node tables in shared memory.
 __global__ void k_restr(DevJob J) {
-  const int t = blockIdx.y;
+  extern __shared__ double shq[];
+  const int t = blockIdx.x;
   const int N = J.restr_N[2 * t], M = J.restr_N[2 * t + 1];
   double* RT = J.restr + J.restr_off[t];
+  double* cA = shq;          // N: cospi((2i+1)M / (2N))
+  double* sa = cA + N;       // N: sin(a_i)
+  double* ca = sa + N;       // N: cos(a_i)
+  double* sb = ca + N;       // M: (-1)^(x+1) sin(beta_x)
+  double* sg = sb + M;       // M: sin(g_x)
+  double* cg = sg + M;       // M: cos(g_x)
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    const long long A = ((long long)(2 * i + 1) * M) % (4LL * N);
+    cA[i] = cospi((double)A / (2.0 * N));
+    sincospi((double)(2 * i + 1) / (4.0 * N), &sa[i], &ca[i]);
+  }
+  for (int x = threadIdx.x; x < M; x += blockDim.x) {
+    const double sbeta = sinpi((double)(2 * x + 1) / (2.0 * M));
+    sb[x] = (x & 1) ? sbeta : -sbeta;
+    sincospi((double)(2 * x + 1) / (4.0 * M), &sg[x], &cg[x]);
+  }
+  __syncthreads();
   const long long total = (long long)N * M;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
-    int x = (int)(e / N), i = (int)(e % N);
-    long long D = (long long)(2 * i + 1) * M - (long long)(2 * x + 1) * N;
-    double v;
-    if (D == 0) {
-      v = 1.0;
-    } else {
-      long long S = (long long)(2 * i + 1) * M + (long long)(2 * x + 1) * N;
-      double nm4 = 4.0 * (double)N * (double)M;
-      double sb = sinpi((double)(2 * x + 1) / (2.0 * M));
-      double num = sinpi((double)D / (2.0 * N));
-      double den = 2.0 * M * sinpi((double)S / nm4) * sinpi((double)D / nm4);
-      v = sb * num / den;
+  const double nm4 = 4.0 * (double)N * (double)M, m2 = 2.0 * M;
+  for (long long e = threadIdx.x; e < total; e += blockDim.x) {
+    const int x = (int)(e / N), i = (int)(e % N);
+    const long long D = (long long)(2 * i + 1) * M - (long long)(2 * x + 1) * N;
+    double v = 1.0;
+    if (D != 0) {
+      const double ssum = fma(sa[i], cg[x], ca[i] * sg[x]);
+      v = sb[x] * cA[i] / (m2 * ssum * sinpi((double)D / nm4));
     }
     RT[e] = v;
   }
@@ -1428,8 +1444,8 @@ cudaError_t launch_tables(const DevJob& J, cudaStream_t st, int* launches) {
     *launches += 1;
   }
   if (J.n_restr > 0) {
-    dim3 grid(64, J.n_restr);
-    k_restr<<<grid, 256, 0, st>>>(J);
+    const size_t sh = (size_t)3 * (J.max_n + J.max_nmax) * sizeof(double);   // <= 38 KB
+    k_restr<<<J.n_restr, 256, sh, st>>>(J);
     *launches += 1;
   }
   return cudaGetLastError();
