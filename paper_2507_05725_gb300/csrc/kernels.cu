@@ -192,16 +192,33 @@ __global__ void k_restr(DevJob J) {
 // ---------------------------------------------------------------------------------------------
 // Self assembly: A_ic = K1(t_i,t_c) Rlog_ic + K2(t_i,t_c) pi/N, symmetric in (i, c), for a band of
 // consecutive frequencies sharing N (nodes, log table, |t - s| and its logarithm are shared).
+// A self-matrix entry: FP64, or (mixed form) the double-float pair the refinement reads plus its FP32
+// rounding for the FP32 factorisation -- what a separate split of the FP64 matrix would give.
+__device__ __forceinline__ void store_self(const DevJob& J, long long off, double2 v) {
+  if (J.mixed) {
+    const float4 d = df_split2(v);
+    reinterpret_cast<float4*>(J.A)[off] = d;
+    J.LU32[off] = make_float2(d.x, d.z);
+  } else {
+    J.A[off] = v;
+  }
+}
+
 __global__ void __launch_bounds__(256) k_assemble_self(DevJob J) {
   const SelfTile tile = J.tiles[blockIdx.x];
   const SysDesc s0 = J.sys[tile.sys];
   const int N = s0.N, nb = tile.nsys;
   __shared__ double lnl[kSelfBand], invl[kSelfBand], rsql[kSelfBand];
+  __shared__ df invl_d[kSelfBand], rsql_d[kSelfBand];      // mixed form
   if (threadIdx.x < nb) {
     const double l = (double)(s0.l + threadIdx.x);
     lnl[threadIdx.x] = log(l);
     invl[threadIdx.x] = 1.0 / l;
     rsql[threadIdx.x] = rsqrt(l);
+    if (J.mixed) {
+      invl_d[threadIdx.x] = df_from(invl[threadIdx.x]);
+      rsql_d[threadIdx.x] = df_from(rsql[threadIdx.x]);
+    }
   }
   __syncthreads();
   const int i = tile.ti * kSelfTile + (threadIdx.x % kSelfTile);
@@ -217,7 +234,7 @@ __global__ void __launch_bounds__(256) k_assemble_self(DevJob J) {
     const double lsp = log(0.5 * J.h * J.node_sp[pn.off + i]);
     for (int b = 0; b < nb; ++b) {
       const double re = -0.5 * kInvPi * (kEulerGamma + lnl[b] + lsp);
-      J.A[J.sys[tile.sys + b].mat_off + e1] = make_double2(fma(K1, rl, re * w), 0.25 * w);
+      store_self(J, J.sys[tile.sys + b].mat_off + e1, make_double2(fma(K1, rl, re * w), 0.25 * w));
     }
     return;
   }
@@ -248,9 +265,57 @@ __global__ void __launch_bounds__(256) k_assemble_self(DevJob J) {
     bessel0_taylor(z, J0, Yh);
     const double alpha = -0.5 * kInvPi * fma(w, lnl[b] + lratio, rl);
     const double2 v = make_double2(fma(alpha, J0, -qw * Yh), qw * J0);
-    double2* A = J.A + J.sys[tile.sys + b].mat_off;
-    A[e1] = v;
-    A[e2] = v;
+    const long long mo = J.sys[tile.sys + b].mat_off;
+    store_self(J, mo + e1, v);
+    store_self(J, mo + e2, v);
+  }
+  if (J.mixed && lsw < lend) {
+    // Mixed form: the recurrence above z = 20 in double-float on the FP32 pipe (about 48 bits), stored
+    // as the pair and its FP32 rounding; FP64 only for the seeds.
+    const df ampu_d = df_from(amp_u), invu_d = df_from(inv_u), alpha_d = df_from(alpha_a), qw_d = df_from(qw);
+    const df cu_d = df_from(cu), su_d = df_from(su);
+    df cx_d{0.f, 0.f}, sx_d{0.f, 0.f};
+    int since_d = 16;
+    for (int l = lsw; l < lend; ++l) {
+      const int b = l - s0.l;
+      if (since_d >= 16) {
+        double sn, cs;
+        sincos((l * J.h) * R, &sn, &cs);
+        cx_d = df_from((cs + sn) * kSqrtHalf);
+        sx_d = df_from((sn - cs) * kSqrtHalf);
+        since_d = 0;
+      }
+      const df wz = df_mul(invu_d, invl_d[b]);
+      const df w2 = df_neg(df_mul(wz, wz));
+      float2 cf = c_hank_df[2 * kmax];
+      df P{cf.x, cf.y};
+      cf = c_hank_df[2 * kmax + 1];
+      df Qa{cf.x, cf.y};
+      for (int k = kmax - 1; k >= 0; --k) {
+        cf = c_hank_df[2 * k];
+        P = df_add(df_mul(P, w2), df{cf.x, cf.y});
+        cf = c_hank_df[2 * k + 1];
+        Qa = df_add(df_mul(Qa, w2), df{cf.x, cf.y});
+      }
+      Qa = df_mul(Qa, wz);
+      const df amp = df_mul(ampu_d, rsql_d[b]);
+      const df J0 = df_mul(amp, df_add(df_mul(P, cx_d), df_mul(Qa, sx_d)));
+      const df Y0 = df_mul(amp, df_sub(df_mul(P, sx_d), df_mul(Qa, cx_d)));
+      const df re = df_sub(df_mul(alpha_d, J0), df_mul(qw_d, Y0));
+      const df im = df_mul(qw_d, J0);
+      const long long mo = J.sys[tile.sys + b].mat_off;
+      const float4 d = make_float4(re.hi, re.lo, im.hi, im.lo);
+      const float2 f = make_float2(re.hi, im.hi);
+      reinterpret_cast<float4*>(J.A)[mo + e1] = d;
+      reinterpret_cast<float4*>(J.A)[mo + e2] = d;
+      J.LU32[mo + e1] = f;
+      J.LU32[mo + e2] = f;
+      const df cn = df_sub(df_mul(cx_d, cu_d), df_mul(sx_d, su_d));
+      sx_d = df_add(df_mul(sx_d, cu_d), df_mul(cx_d, su_d));
+      cx_d = cn;
+      ++since_d;
+    }
+    return;
   }
   double cx = 0.0, sx = 0.0;
   int since = 16;
@@ -275,25 +340,14 @@ __global__ void __launch_bounds__(256) k_assemble_self(DevJob J) {
     const double J0 = amp * fma(P, cx, Qa * sx);
     const double Y0 = amp * fma(P, sx, -Qa * cx);
     const double2 v = make_double2(fma(alpha_a, J0, -qw * Y0), qw * J0);
-    double2* A = J.A + J.sys[tile.sys + b].mat_off;
-    A[e1] = v;
-    A[e2] = v;
+    const long long mo = J.sys[tile.sys + b].mat_off;
+    store_self(J, mo + e1, v);
+    store_self(J, mo + e2, v);
     const double cn = fma(cx, cu, -sx * su);
     sx = fma(sx, cu, cx * su);
     cx = cn;
     ++since;
   }
-}
-
-// ---------------------------------------------------------------------------------------------
-// Mixed-precision form: the FP32 factor gets the rounded matrix, and A itself is rewritten in place as
-// double-float (the same 16 bytes per entry) for the refinement residuals.
-__global__ void k_split_A(DevJob J) {
-  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= J.mat_total) return;
-  const double2 v = J.A[e];
-  J.LU32[e] = make_float2(__double2float_rn(v.x), __double2float_rn(v.y));
-  reinterpret_cast<float4*>(J.A)[e] = df_split2(v);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -1470,12 +1524,12 @@ cudaError_t launch_assemble_self(const DevJob& J, cudaStream_t st, int* launches
 
 cudaError_t launch_lu(const DevJob& J, cudaStream_t st, int* launches) {
   if (J.mixed) {
-    k_split_A<<<cdiv(J.mat_total, 256), 256, 0, st>>>(J);
+    // k_assemble_self already wrote the FP32 matrix and the double-float pairs
     size_t sh = std::max((size_t)J.max_n * (kNB + kPS), (size_t)2 * kSB * kSB) * sizeof(float2);
     cudaError_t e = cudaFuncSetAttribute(k_lu<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
     if (e != cudaSuccess) return e;
     k_lu<float2><<<J.nsys, kLuThreads, sh, st>>>(J);
-    *launches += 2;
+    *launches += 1;
     return cudaGetLastError();
   }
   size_t sh = std::max((size_t)J.max_n * (kNB + kPS), (size_t)2 * kSB * kSB) * sizeof(double2);
