@@ -94,6 +94,34 @@ __device__ __forceinline__ df df_add(df a, df b) {
 __device__ __forceinline__ df df_neg(df a) { return df{-a.hi, -a.lo}; }
 __device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
 
+// A double constant as a double-float pair, folded at compile time when used in a constant expression.
+__host__ __device__ constexpr df df_const(double v) { return df{(float)v, (float)(v - (double)(float)v)}; }
+
+// sin x and cos x for |x| <= 1 in double-float: the Taylor series (truncation below 2e-20, as for the
+// FP64 version) by Horner's rule in u = x^2 with the coefficients (-1)^k/(2k+1)! and (-1)^k/(2k)!.
+__device__ __forceinline__ void df_sincos_taylor(df x, df& s, df& c) {
+  constexpr double f3 = 6.0, f5 = f3 * 20.0, f7 = f5 * 42.0, f9 = f7 * 72.0, f11 = f9 * 110.0,
+                   f13 = f11 * 156.0, f15 = f13 * 210.0, f17 = f15 * 272.0, f19 = f17 * 342.0;
+  constexpr double f2 = 2.0, f4 = f2 * 12.0, f6 = f4 * 30.0, f8 = f6 * 56.0, f10 = f8 * 90.0,
+                   f12 = f10 * 132.0, f14 = f12 * 182.0, f16 = f14 * 240.0, f18 = f16 * 306.0,
+                   f20 = f18 * 380.0;
+  constexpr df ks[9] = {df_const(-1.0 / f19), df_const(1.0 / f17), df_const(-1.0 / f15), df_const(1.0 / f13),
+                        df_const(-1.0 / f11), df_const(1.0 / f9),  df_const(-1.0 / f7),  df_const(1.0 / f5),
+                        df_const(-1.0 / f3)};
+  constexpr df kc[10] = {df_const(1.0 / f20),  df_const(-1.0 / f18), df_const(1.0 / f16), df_const(-1.0 / f14),
+                         df_const(1.0 / f12),  df_const(-1.0 / f10), df_const(1.0 / f8),  df_const(-1.0 / f6),
+                         df_const(1.0 / f4),   df_const(-1.0 / f2)};
+  const df u = df_mul(x, x);
+  df ps = ks[0];
+#pragma unroll
+  for (int k = 1; k < 9; ++k) ps = df_add(df_mul(ps, u), ks[k]);
+  s = df_add(x, df_mul(df_mul(x, u), ps));
+  df pc = kc[0];
+#pragma unroll
+  for (int k = 1; k < 10; ++k) pc = df_add(df_mul(pc, u), kc[k]);
+  c = df_add(df{1.f, 0.f}, df_mul(u, pc));
+}
+
 // Complex compensated multiply-accumulate: acc += a * b with a, b complex df64 (float4 layout).
 __device__ __forceinline__ void cdf_mac(dfacc& re, dfacc& im, float4 a, float4 b) {
   re.mac(a.x, a.y, b.x, b.y);

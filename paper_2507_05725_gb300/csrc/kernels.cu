@@ -755,11 +755,15 @@ struct AsymState {
   int since, kmax;
 };
 
-__device__ __forceinline__ AsymState asym_start(const PairSetup& s, double lh_first, double camp) {
+__device__ __forceinline__ AsymState asym_start(const PairSetup& s, double lh_first, double camp, bool step = true) {
   AsymState a;
   a.ampw = rsqrt(s.hR) * camp;
-  if (s.hR <= 1.0) sincos_taylor(s.hR, a.su, a.cu);
-  else sincos(s.hR, &a.su, &a.cu);
+  a.su = 0.0;
+  a.cu = 1.0;
+  if (step) {
+    if (s.hR <= 1.0) sincos_taylor(s.hR, a.su, a.cu);
+    else sincos(s.hR, &a.su, &a.cu);
+  }
   a.kmax = hankel_terms((float)(lh_first * s.R));
   a.cx = a.sx = 0.0;
   a.since = 16;
@@ -849,12 +853,21 @@ __global__ void __launch_bounds__(kAsmMaxThreads) k_cross_assemble(DevJob J) {
     }
     if (ps.lsw > task.l1) continue;
     const int lsw = ps.lsw;
-    AsymState as = asym_start(ps, lh[lsw - task.l0], camp);
     if (J.mixed) {
       // Mixed form: the same recurrence in double-float on the FP32 pipe (about 48 bits), stored as
-      // the double-float pairs the mixed-form apply reads; FP64 only for the seeds.
+      // the double-float pairs the mixed-form apply reads; FP64 only for the seeds (the step
+      // rotation e^{i h R} itself is evaluated in double-float).
+      const AsymState as = asym_start(ps, lh[lsw - task.l0], camp, false);
       const df ampw_d = df_from(as.ampw), invu_d = df_from(ps.inv_u), beta_d = df_from(ps.beta);
-      const df cu_d = df_from(as.cu), su_d = df_from(as.su);
+      df cu_d, su_d;
+      if (ps.hR <= 1.0) {
+        df_sincos_taylor(df_from(ps.hR), su_d, cu_d);
+      } else {
+        double su, cu;
+        sincos(ps.hR, &su, &cu);
+        su_d = df_from(su);
+        cu_d = df_from(cu);
+      }
       df cx_d{0.f, 0.f}, sx_d{0.f, 0.f};
       int since_d = 16;
       for (int l = lsw; l <= task.l1; ++l) {
@@ -893,6 +906,7 @@ __global__ void __launch_bounds__(kAsmMaxThreads) k_cross_assemble(DevJob J) {
       }
       continue;
     }
+    AsymState as = asym_start(ps, lh[lsw - task.l0], camp);
     for (int l = lsw; l <= task.l1; ++l) {
       const int b = l - task.l0;
       store_entry(J, Ep + eo[l], asym_entry(as, ps, lh[b], invl[b], rsql[b]));
