@@ -192,6 +192,28 @@ __global__ void k_restr(DevJob J) {
 // ---------------------------------------------------------------------------------------------
 // Self assembly: A_ic = K1(t_i,t_c) Rlog_ic + K2(t_i,t_c) pi/N, symmetric in (i, c), for a band of
 // consecutive frequencies sharing N (nodes, log table, |t - s| and its logarithm are shared).
+// cos(theta - pi/4) and sin(theta - pi/4) as double-float pairs for a phase theta >= 0 given in FP64 (up
+// to ~2e4): theta is reduced by n pi/2 in FP64 (pi/2 as the sum of two doubles, each product inside an
+// FMA), the remainder |r| <= pi/4 is rounded to double-float (~3e-15 absolute) and its sine and cosine
+// come from the double-float Taylor series; the quadrant n mod 4 permutes them.
+__device__ __forceinline__ void df_phase_seed(double theta, df& cx, df& sx) {
+  constexpr double kPio2Hi = 1.57079632679489661923, kPio2Lo = 6.123233995736766e-17;   // pi/2 = Hi + Lo
+  const double n = rint(theta * kTwoOverPi);
+  const double r = fma(-n, kPio2Lo, fma(-n, kPio2Hi, theta));
+  df sr, cr;
+  df_sincos_taylor(df_from(r), sr, cr);
+  df s, c;
+  switch (((long long)n) & 3) {
+    case 0: s = sr; c = cr; break;
+    case 1: s = cr; c = df_neg(sr); break;
+    case 2: s = df_neg(sr); c = df_neg(cr); break;
+    default: s = df_neg(cr); c = sr; break;
+  }
+  constexpr df kSqrtHalfD = df_const(0.70710678118654752440084436210484904);
+  cx = df_mul(df_add(c, s), kSqrtHalfD);      // cos(theta - pi/4)
+  sx = df_mul(df_sub(s, c), kSqrtHalfD);      // sin(theta - pi/4)
+}
+
 // A self-matrix entry: FP64, or (mixed form) the double-float pair the refinement reads plus its FP32
 // rounding for the FP32 factorisation -- what a separate split of the FP64 matrix would give.
 __device__ __forceinline__ void store_self(const DevJob& J, long long off, double2 v) {
@@ -251,9 +273,6 @@ __global__ void __launch_bounds__(256) k_assemble_self(DevJob J) {
   const double alpha_a = -0.5 * kInvPi * (rl - w * log(dts));          // z >= 20
   const double qw = 0.25 * w;
   const double inv_u = 1.0 / hR, amp_u = sqrt(kTwoOverPi * inv_u);
-  double su, cu;
-  if (hR <= 1.0) sincos_taylor(hR, su, cu);
-  else sincos(hR, &su, &cu);
   const int lsw = max(s0.l, (int)ceil(kBesselLarge * inv_u));         // first l with z >= 20
   const int lend = s0.l + nb;
   const double zmin = (lsw * J.h) * R;
@@ -273,16 +292,21 @@ __global__ void __launch_bounds__(256) k_assemble_self(DevJob J) {
     // Mixed form: the recurrence above z = 20 in double-float on the FP32 pipe (about 48 bits), stored
     // as the pair and its FP32 rounding; FP64 only for the seeds.
     const df ampu_d = df_from(amp_u), invu_d = df_from(inv_u), alpha_d = df_from(alpha_a), qw_d = df_from(qw);
-    const df cu_d = df_from(cu), su_d = df_from(su);
+    df cu_d, su_d;
+    if (hR <= 1.0) {
+      df_sincos_taylor(df_from(hR), su_d, cu_d);
+    } else {
+      double su, cu;
+      sincos(hR, &su, &cu);
+      su_d = df_from(su);
+      cu_d = df_from(cu);
+    }
     df cx_d{0.f, 0.f}, sx_d{0.f, 0.f};
     int since_d = 16;
     for (int l = lsw; l < lend; ++l) {
       const int b = l - s0.l;
       if (since_d >= 16) {
-        double sn, cs;
-        sincos((l * J.h) * R, &sn, &cs);
-        cx_d = df_from((cs + sn) * kSqrtHalf);
-        sx_d = df_from((sn - cs) * kSqrtHalf);
+        df_phase_seed((l * J.h) * R, cx_d, sx_d);
         since_d = 0;
       }
       const df wz = df_mul(invu_d, invl_d[b]);
@@ -317,6 +341,9 @@ __global__ void __launch_bounds__(256) k_assemble_self(DevJob J) {
     }
     return;
   }
+  double su, cu;
+  if (hR <= 1.0) sincos_taylor(hR, su, cu);
+  else sincos(hR, &su, &cu);
   double cx = 0.0, sx = 0.0;
   int since = 16;
   for (int l = lsw; l < lend; ++l) {
@@ -873,10 +900,7 @@ __global__ void __launch_bounds__(kAsmMaxThreads) k_cross_assemble(DevJob J) {
       for (int l = lsw; l <= task.l1; ++l) {
         const int b = l - task.l0;
         if (since_d >= 16) {
-          double sn, cs;
-          sincos(lh[b] * ps.R, &sn, &cs);
-          cx_d = df_from((cs + sn) * kSqrtHalf);
-          sx_d = df_from((sn - cs) * kSqrtHalf);
+          df_phase_seed(lh[b] * ps.R, cx_d, sx_d);
           since_d = 0;
         }
         const df wz = df_mul(invu_d, invl_d[b]);
