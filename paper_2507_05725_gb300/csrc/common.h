@@ -61,6 +61,11 @@ struct ApplySlice {
   int rowb0;
 };
 
+// Mixed-form refinement residuals: 32 consecutive rows of one system (one warp, a row per lane).
+struct ResidChunk {
+  int sys, row0;
+};
+
 // Receiver/source pair (k, j), k = P for the observation points.
 struct PairDesc {
   int k, j;

@@ -552,18 +552,20 @@ __global__ void __launch_bounds__(kLuThreads) k_lu(DevJob J) {
 constexpr int kSolveWarps = 4;
 
 // Rows i0 and i0 + 32 of b -= T[:, r0..r0+w) x with x = b[r0..r0+w), column-major T of leading
-// dimension N.  Each batch of 8 columns issues the loads of both rows before their FMAs, so a lane has
-// 16 independent loads in flight instead of walking its rows one after another.  A second row past
+// dimension N.  Each batch of columns (8 for FP64 factors, 16 for FP32) issues the loads of both rows
+// before their FMAs, so a lane has 16 or 32 independent loads in flight instead of walking its rows one
+// after another.  A second row past
 // `end` is computed on the first and not stored.
 template <class C>
 __device__ __forceinline__ void tri_update2(C* bq, const C* __restrict__ A, int N, int r0, int w, int i0, int end) {
   const int i1 = i0 + 32 < end ? i0 + 32 : i0;
+  constexpr int kCols = sizeof(C) == 8 ? 16 : 8;   // columns per load batch (FP32 factors: 16)
   C a0 = bq[i0], a1 = bq[i1];
 #pragma unroll 1
-  for (int c0 = 0; c0 < kSB; c0 += 8) {
-    C v0[8], v1[8];
+  for (int c0 = 0; c0 < kSB; c0 += kCols) {
+    C v0[kCols], v1[kCols];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
+    for (int k = 0; k < kCols; ++k) {
       if (c0 + k < w) {
         const C* col = A + (long long)(r0 + c0 + k) * N;
         v0[k] = __ldg(&col[i0]);
@@ -571,7 +573,7 @@ __device__ __forceinline__ void tri_update2(C* bq, const C* __restrict__ A, int 
       }
     }
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
+    for (int k = 0; k < kCols; ++k) {
       if (c0 + k < w) {
         const C x = bq[r0 + c0 + k];
         a0 = cfms(v0[k], x, a0);
@@ -1107,116 +1109,114 @@ __global__ void __launch_bounds__(kApplyThreads) k_cross_apply(DevJob J) {
 }
 
 // ---------------------------------------------------------------------------------------------
-// Mixed-precision solve: FP32 blocked solves with the FP32 factors, then refinement steps with
-// double-float residuals r = G - A phi (A kept as double-float, about 48 bits) and FP32 corrections,
-// until the relative correction is below 1e-11 or kRefineMax steps.  One warp per system.
+// Mixed-precision solve: an FP32 blocked solve with the FP32 factors, then refinement steps, each a
+// double-float residual r = G - A phi (A kept as double-float, about 48 bits) and an FP32 correction,
+// until the relative correction is below 1e-11 or kRefineMax steps.  A step is two launches over the
+// systems still refining: k_mresid streams the double-float matrix with one thread per row (many
+// warps in flight per SM), k_msolve runs the triangular solves with one warp per system and little
+// register state.  Until a system finishes, its densities sit in its phi slots as double-float pairs
+// (16 bytes, the size of the FP64 value written there at the end).
 constexpr int kRefineMax = 3;
+constexpr int kResidThreads = 128;
 
-// Rows i0, i0 + 32, ..., i0 + 32 (U - 1) of r = G - A phi in double-float, A column-major (float4
-// per entry), phi a shared-memory broadcast.  A row past N (the last slot of some lanes) is computed
-// on a valid row and not stored, so every lane runs the same instruction stream.
-template <int U>
-__device__ __forceinline__ void residual_rows(const float4* __restrict__ Adf, const double2* __restrict__ G,
-                                              const float4* pq, float2* b, int N, int i0) {
-  dfacc re[U], im[U];
-  int row[U];
+// One thread per row (rows past N recompute the last row and store nothing), all Q windows of the row:
+// r_q = G_q - A phi_q with compensated double-float sums over the columns in order.
+template <int Q>
+__global__ void __launch_bounds__(kResidThreads) k_mresid(DevJob J) {
+  const int chunk = blockIdx.x * (kResidThreads / 32) + (threadIdx.x >> 5);
+  if (chunk >= J.n_rchunks) return;
+  const ResidChunk c = J.rchunks[chunk];
+  if (J.mdone[c.sys]) return;
+  const SysDesc s = J.sys[c.sys];
+  const int N = s.N;
+  const int i = c.row0 + (threadIdx.x & 31);
+  const int row = i < N ? i : N - 1;
+  const float4* __restrict__ Adf = reinterpret_cast<const float4*>(J.A) + s.mat_off;
+  const float4* __restrict__ ph = reinterpret_cast<const float4*>(J.phi + s.vec_off);
+  const double2* __restrict__ G = J.G + s.vec_off;
+  dfacc re[Q], im[Q];
 #pragma unroll
-  for (int u = 0; u < U; ++u) {
-    const int i = i0 + 32 * u;
-    row[u] = i < N ? i : (i0 < N ? i0 : N - 1);
-    const float4 gd = df_split2(G[row[u]]);
-    re[u].add(gd.x, gd.y);
-    im[u].add(gd.z, gd.w);
+  for (int q = 0; q < Q; ++q) {
+    const float4 gd = df_split2(G[q * N + row]);
+    re[q].add(gd.x, gd.y);
+    im[q].add(gd.z, gd.w);
   }
-#pragma unroll 2
+#pragma unroll 4
   for (int j = 0; j < N; ++j) {
-    const float4 x = pq[j];
-    const float4* Aj = Adf + (long long)j * N;
+    const float4 a = __ldg(&Adf[(long long)j * N + row]);
+    const float4 na = make_float4(-a.x, -a.y, -a.z, -a.w);
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const float4 a = __ldg(&Aj[row[u]]);
-      cdf_mac(re[u], im[u], make_float4(-a.x, -a.y, -a.z, -a.w), x);
-    }
+    for (int q = 0; q < Q; ++q) cdf_mac(re[q], im[q], na, ph[q * N + j]);
   }
+  if (i < N) {
 #pragma unroll
-  for (int u = 0; u < U; ++u) {
-    const int i = i0 + 32 * u;
-    if (i < N) {
-      const df rr = re[u].value(), ri = im[u].value();
-      b[i] = make_float2(rr.hi + rr.lo, ri.hi + ri.lo);
+    for (int q = 0; q < Q; ++q) {
+      const df rr = re[q].value(), ri = im[q].value();
+      J.rres[s.vec_off + q * N + i] = make_float2(rr.hi + rr.lo, ri.hi + ri.lo);
     }
   }
 }
 
-__global__ void __launch_bounds__(32 * kSolveWarps) k_solve_mixed(DevJob J, int m) {
+// pass 0: solve with FP32 G, store phi as double-float, mark the system as refining.  pass p >= 1:
+// solve for the correction from the residual, add it in double-float, and finish the system (FP64
+// densities, their running sum, the statistics) once the correction is small enough or p = kRefineMax.
+__global__ void __launch_bounds__(32 * kSolveWarps, 4) k_msolve(DevJob J, int m, int pass) {
   extern __shared__ __align__(16) unsigned char shm_raw[];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nw = blockDim.x >> 5;
   const int slot = blockIdx.x * nw + wid;
   if (slot >= J.nsys) return;
   const int sidx = J.sys_order[slot];
+  if (pass > 0 && J.mdone[sidx]) return;
   const SysDesc s = J.sys[sidx];
   const int N = s.N, Q = J.Q;
-  const size_t per = (size_t)Q * J.max_n;
-  float4* ph = reinterpret_cast<float4*>(shm_raw) + (size_t)wid * per;                        // df64
-  float2* b = reinterpret_cast<float2*>(reinterpret_cast<float4*>(shm_raw) + nw * per) + (size_t)wid * per;
+  float2* b = reinterpret_cast<float2*>(shm_raw) + (size_t)wid * Q * J.max_n;
   const float2* __restrict__ L32 = J.LU32 + s.mat_off;
-  const float4* __restrict__ Adf = reinterpret_cast<const float4*>(J.A) + s.mat_off;
   const int* __restrict__ piv = J.piv + s.piv_off;
   const float2* __restrict__ dinv = J.dinv32 + s.piv_off;
-  const double2* __restrict__ G = J.G + s.vec_off;
-  for (int e = lane; e < Q * N; e += 32) {
-    const double2 g = G[e];
-    b[e] = make_float2(__double2float_rn(g.x), __double2float_rn(g.y));
+  float4* ph = reinterpret_cast<float4*>(J.phi + s.vec_off);
+  if (pass == 0) {
+    const double2* __restrict__ G = J.G + s.vec_off;
+    for (int e = lane; e < Q * N; e += 32) {
+      const double2 g = G[e];
+      b[e] = make_float2(__double2float_rn(g.x), __double2float_rn(g.y));
+    }
+  } else {
+    const float2* __restrict__ r = J.rres + s.vec_off;
+    for (int e = lane; e < Q * N; e += 32) b[e] = r[e];
   }
   __syncwarp();
   tri_solve<float2>(b, Q, N, L32, piv, dinv, lane);
-  for (int e = lane; e < Q * N; e += 32) ph[e] = make_float4(b[e].x, 0.f, b[e].y, 0.f);
-  __syncwarp();
-  double rel = 1.0;
-  int passes = 0;
-  for (int it = 0; it < kRefineMax; ++it) {
-    ++passes;
-    // r = G - A phi, up to four rows per lane in flight (independent compensated sums)
-    for (int q = 0; q < Q; ++q) {
-      const int slots = (N + 31) / 32;                  // rows per lane, the same for the whole warp
-      for (int s0 = 0; s0 < slots; s0 += 4) {
-        const int i0 = lane + 32 * s0;
-        switch (min(4, slots - s0)) {
-          case 4: residual_rows<4>(Adf, G + q * N, ph + q * N, b + q * N, N, i0); break;
-          case 3: residual_rows<3>(Adf, G + q * N, ph + q * N, b + q * N, N, i0); break;
-          case 2: residual_rows<2>(Adf, G + q * N, ph + q * N, b + q * N, N, i0); break;
-          default: residual_rows<1>(Adf, G + q * N, ph + q * N, b + q * N, N, i0); break;
-        }
-      }
-    }
-    __syncwarp();
-    tri_solve<float2>(b, Q, N, L32, piv, dinv, lane);
-    float dmax = 0.f, pmax = 0.f;
-    for (int e = lane; e < Q * N; e += 32) {
-      const float2 d = b[e];
-      float4 p = ph[e];
-      float sh, sl;
-      two_sum(p.x, d.x, sh, sl);
-      quick_two_sum(sh, sl + p.y, p.x, p.y);
-      two_sum(p.z, d.y, sh, sl);
-      quick_two_sum(sh, sl + p.w, p.z, p.w);
-      ph[e] = p;
-      dmax = fmaxf(dmax, fmaxf(fabsf(d.x), fabsf(d.y)));
-      pmax = fmaxf(pmax, fmaxf(fabsf(p.x), fabsf(p.z)));
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
-      pmax = fmaxf(pmax, __shfl_xor_sync(0xffffffffu, pmax, o));
-    }
-    __syncwarp();
-    rel = pmax > 0.f ? (double)dmax / (double)pmax : 0.0;
-    if (rel < 1e-11) break;
+  if (pass == 0) {
+    for (int e = lane; e < Q * N; e += 32) ph[e] = make_float4(b[e].x, 0.f, b[e].y, 0.f);
+    if (lane == 0) J.mdone[sidx] = 0;
+    return;
   }
+  float dmax = 0.f, pmax = 0.f;
+  for (int e = lane; e < Q * N; e += 32) {
+    const float2 d = b[e];
+    float4 p = ph[e];
+    float sh, sl;
+    two_sum(p.x, d.x, sh, sl);
+    quick_two_sum(sh, sl + p.y, p.x, p.y);
+    two_sum(p.z, d.y, sh, sl);
+    quick_two_sum(sh, sl + p.w, p.z, p.w);
+    ph[e] = p;
+    dmax = fmaxf(dmax, fmaxf(fabsf(d.x), fabsf(d.y)));
+    pmax = fmaxf(pmax, fmaxf(fabsf(p.x), fabsf(p.z)));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    pmax = fmaxf(pmax, __shfl_xor_sync(0xffffffffu, pmax, o));
+  }
+  const double rel = pmax > 0.f ? (double)dmax / (double)pmax : 0.0;
+  if (rel >= 1e-11 && pass < kRefineMax) return;
   if (lane == 0) {
+    J.mdone[sidx] = 1;
     atomicMax(reinterpret_cast<unsigned long long*>(J.refine_resid), (unsigned long long)__double_as_longlong(rel));
-    atomicAdd(reinterpret_cast<unsigned long long*>(J.refine_resid) + 1, (unsigned long long)passes);
+    atomicAdd(reinterpret_cast<unsigned long long*>(J.refine_resid) + 1, (unsigned long long)pass);
   }
+  // Each lane reads back the double-float values it wrote itself, then replaces them by FP64.
   double2* out = J.phi + s.vec_off;
   double2* sum = J.phi_sum + s.vec_off;
   double2* all = J.phi_all ? J.phi_all + (long long)(m - 1) * J.vec_total + s.vec_off : nullptr;
@@ -1632,13 +1632,23 @@ static int solve_warps(size_t bytes_per_warp, int wanted) {
 
 cudaError_t launch_solve(const DevJob& J, int m, cudaStream_t st, int* launches) {
   if (J.mixed) {
-    const size_t per = (size_t)J.Q * J.max_n * (sizeof(float4) + sizeof(float2));
+    const size_t per = (size_t)J.Q * J.max_n * sizeof(float2);
     const int nw = solve_warps(per, J.shape_solve);
-    size_t sh = (size_t)nw * per;
-    cudaError_t e = cudaFuncSetAttribute(k_solve_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+    const size_t sh = (size_t)nw * per;
+    cudaError_t e = cudaFuncSetAttribute(k_msolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
     if (e != cudaSuccess) return e;
-    k_solve_mixed<<<cdiv(J.nsys, nw), 32 * nw, sh, st>>>(J, m);
-    *launches += 1;
+    const int grid = cdiv(J.nsys, nw), rgrid = cdiv(J.n_rchunks, kResidThreads / 32);
+    k_msolve<<<grid, 32 * nw, sh, st>>>(J, m, 0);
+    for (int pass = 1; pass <= kRefineMax && rgrid > 0; ++pass) {
+      switch (J.Q) {
+        case 1: k_mresid<1><<<rgrid, kResidThreads, 0, st>>>(J); break;
+        case 2: k_mresid<2><<<rgrid, kResidThreads, 0, st>>>(J); break;
+        case 3: k_mresid<3><<<rgrid, kResidThreads, 0, st>>>(J); break;
+        default: k_mresid<4><<<rgrid, kResidThreads, 0, st>>>(J); break;
+      }
+      k_msolve<<<grid, 32 * nw, sh, st>>>(J, m, pass);
+    }
+    *launches += 1 + 2 * kRefineMax;
     return cudaGetLastError();
   }
   const size_t per = (size_t)J.Q * J.max_n * sizeof(double2);

@@ -65,6 +65,10 @@ struct DevJob {
   float2* LU32;              // FP32 factors (mixed form)
   float2* dinv32;            // FP32 1 / U_kk (mixed form)
   double* refine_resid;      // max over systems of the last relative correction (mixed form)
+  float2* rres;              // FP32-rounded refinement residuals, laid out like G (mixed form)
+  int* mdone;                // per system: 1 once its refinement has finished this step (mixed form)
+  const ResidChunk* rchunks; // 32-row chunks of the systems, largest first (mixed form)
+  int n_rchunks;
   int* piv;
   double2* dinv;             // 1 / U_kk
   double2* G;                // data on solve nodes [s][q][i]

@@ -369,6 +369,9 @@ int build_plan(const fthms_curve* curves, int ncurves, const fthms_arc* arcs, in
   p.sys_order.resize(p.sys.size());
   for (size_t s = 0; s < p.sys.size(); ++s) p.sys_order[s] = (int)s;
   std::stable_sort(p.sys_order.begin(), p.sys_order.end(), [&](int a, int b) { return p.sys[a].N > p.sys[b].N; });
+  if (p.opt.precision == 1)
+    for (int s : p.sys_order)
+      for (int r0 = 0; r0 < p.sys[s].N; r0 += 32) p.rchunks.push_back(ResidChunk{s, r0});
 
   // Transfer meshes, chi and the active (chi > 0) nodes.
   p.tpanel.resize(p.P);
@@ -560,7 +563,9 @@ void arc_nodes(const Curve& c, double theta_a, double theta_b, int N, std::vecto
 size_t plan_device_bytes(const Plan& p) {
   size_t b = 0;
   b += (size_t)p.mat_total * 16;                 // A / LU
-  if (p.opt.precision == 1) b += (size_t)p.mat_total * 8 + (size_t)p.piv_total * 8;   // FP32 factors
+  if (p.opt.precision == 1)                      // FP32 factors, FP32 residuals, refinement state
+    b += (size_t)p.mat_total * 8 + (size_t)p.piv_total * 8 + (size_t)p.vec_total * 8 + p.sys.size() * 4 +
+         p.rchunks.size() * sizeof(ResidChunk);
   b += (size_t)p.piv_total * 4;                  // pivots
   b += (size_t)p.rlog_total * 8;                 // self log tables
   b += (size_t)p.vec_total * 16 * 3;             // G, phi (current), phi sum

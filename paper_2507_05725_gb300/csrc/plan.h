@@ -64,6 +64,7 @@ struct Plan {
   std::vector<CrossGrp> grps;
   std::vector<CrossBlk> blks;
   std::vector<ApplySlice> slices;       // row slices of the groups (mixed-form cross apply)
+  std::vector<ResidChunk> rchunks;      // 32-row chunks of the systems, largest first (mixed-form residuals)
   std::vector<long long> grp_res_off;    // first row of each group in the per-row result buffer
   long long res_total = 0;               // rows over all groups
   int slice_ph_cap = 0;                  // max over slices of the summed N of the blocks it overlaps
