@@ -90,8 +90,9 @@ typedef struct {
  *  obs_xy    : n_obs observation points (x, y), host array of 2*n_obs doubles.
  *  n_tout, tout0, dtout : output times tout0 + k dtout of the traces u_M(z, t) (eq. mult-scatt-int).
  *  precision : 0 = FP64 throughout.  1 = mixed form: FP32 LU factors; solutions refined against the
- *              matrix kept as double-float (two floats, ~48 bits) until the relative correction is
- *              below 1e-11 (at most 3 steps); the far-field cross entries evaluated, stored and applied
+ *              matrix kept as double-float (two floats, ~48 bits) until the relative error estimated
+ *              to remain (last correction x estimated contraction factor) is below 1e-12, at most 3
+ *              steps; the far-field cross entries evaluated, stored and applied
  *              in double-float on the FP32 pipe; self matrices, phase seeds, log-singular corrections,
  *              transforms and restriction stay FP64.  Densities agree with the FP64 form to ~1e-12.
  *              Others -> ENOTIMPL.
@@ -134,7 +135,8 @@ typedef struct {
   double solve_flops;     /* 8 sum N^2 Q M: triangular solves of one run */
   double apply_flops;     /* 8 Q M (cross + observation entries): cross matvecs of one run */
   int precision;          /* the job's precision option */
-  double max_refine_resid; /* precision 1: max over systems and steps of the last relative correction */
+  double max_refine_resid; /* precision 1: max over systems and steps of the relative error estimated to
+                              remain after the last correction (its size x the estimated contraction) */
   double refine_passes;   /* precision 1: mean refinement passes (residual + correction) per system and step */
 } fthms_stats_t;
 

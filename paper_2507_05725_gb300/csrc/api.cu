@@ -259,6 +259,7 @@ fthms_status upload_job(fthms_req* r) {
   J.dinv32 = nullptr;
   J.rres = nullptr;
   J.mdone = nullptr;
+  J.mrel = nullptr;
   J.rchunks = nullptr;
   J.n_rchunks = 0;
   TRY(dev_alloc(r, 2, &J.refine_resid));          // [0] max last correction, [1] refinement passes (u64)
@@ -267,6 +268,7 @@ fthms_status upload_job(fthms_req* r) {
     TRY(dev_alloc(r, (size_t)p.piv_total, &J.dinv32));
     TRY(dev_alloc(r, (size_t)p.vec_total, &J.rres));
     TRY(dev_alloc(r, p.sys.size(), &J.mdone));
+    TRY(dev_alloc(r, p.sys.size(), &J.mrel));
     TRY(dev_upload(r, p.rchunks, &J.rchunks));
     J.n_rchunks = (int)p.rchunks.size();
   }

@@ -1111,12 +1111,17 @@ __global__ void __launch_bounds__(kApplyThreads) k_cross_apply(DevJob J) {
 // ---------------------------------------------------------------------------------------------
 // Mixed-precision solve: an FP32 blocked solve with the FP32 factors, then refinement steps, each a
 // double-float residual r = G - A phi (A kept as double-float, about 48 bits) and an FP32 correction,
-// until the relative correction is below 1e-11 or kRefineMax steps.  A step is two launches over the
+// until the error estimated to remain is below kRefineTol, or kRefineMax steps.  Each step shrinks the
+// error by a factor rho (the FP32 solve's relative accuracy), so what remains after a correction of
+// relative size rel is about rho * rel; rho is estimated by the ratio of the last two corrections, or
+// after the first step by rel itself (that correction is the FP32 solution's own error, rho times the
+// solution for a generic right-hand side).  A step is two launches over the
 // systems still refining: k_mresid streams the double-float matrix with one thread per row (many
 // warps in flight per SM), k_msolve runs the triangular solves with one warp per system and little
 // register state.  Until a system finishes, its densities sit in its phi slots as double-float pairs
 // (16 bytes, the size of the FP64 value written there at the end).
 constexpr int kRefineMax = 3;
+constexpr double kRefineTol = 1e-12;
 constexpr int kResidThreads = 128;
 
 // One thread per row (rows past N recompute the last row and store nothing), all Q windows of the row:
@@ -1210,10 +1215,15 @@ __global__ void __launch_bounds__(32 * kSolveWarps, 4) k_msolve(DevJob J, int m,
     pmax = fmaxf(pmax, __shfl_xor_sync(0xffffffffu, pmax, o));
   }
   const double rel = pmax > 0.f ? (double)dmax / (double)pmax : 0.0;
-  if (rel >= 1e-11 && pass < kRefineMax) return;
+  const double rho = pass == 1 ? rel : rel / (double)J.mrel[sidx];
+  const double left = rel * rho;
+  if (left >= kRefineTol && pass < kRefineMax) {
+    if (lane == 0) J.mrel[sidx] = (float)rel;
+    return;
+  }
   if (lane == 0) {
     J.mdone[sidx] = 1;
-    atomicMax(reinterpret_cast<unsigned long long*>(J.refine_resid), (unsigned long long)__double_as_longlong(rel));
+    atomicMax(reinterpret_cast<unsigned long long*>(J.refine_resid), (unsigned long long)__double_as_longlong(left));
     atomicAdd(reinterpret_cast<unsigned long long*>(J.refine_resid) + 1, (unsigned long long)pass);
   }
   // Each lane reads back the double-float values it wrote itself, then replaces them by FP64.

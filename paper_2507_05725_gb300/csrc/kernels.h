@@ -67,6 +67,7 @@ struct DevJob {
   double* refine_resid;      // max over systems of the last relative correction (mixed form)
   float2* rres;              // FP32-rounded refinement residuals, laid out like G (mixed form)
   int* mdone;                // per system: 1 once its refinement has finished this step (mixed form)
+  float* mrel;               // per system: relative size of its last correction (mixed form)
   const ResidChunk* rchunks; // 32-row chunks of the systems, largest first (mixed form)
   int n_rchunks;
   int* piv;
