@@ -284,6 +284,8 @@ fthms_status upload_job(fthms_req* r) {
   TRY(dev_alloc(r, (size_t)std::max(1, p.n_obs * p.Q * p.L), &J.Vobs));
   TRY(dev_alloc(r, (size_t)std::max(1, p.n_obs * p.n_tout), &J.traces));
   TRY(dev_alloc(r, (size_t)p.K / 2, &J.fft_tw));
+  J.fft_tw_df = nullptr;
+  if (J.mixed) TRY(dev_alloc(r, (size_t)p.K / 2, &J.fft_tw_df));
   TRY(dev_alloc(r, (size_t)p.Q * p.L, &J.syn_tw));
   TRY(dev_alloc(r, (size_t)p.Q * p.L, &J.fwd_tw));
   return FTHMS_OK;

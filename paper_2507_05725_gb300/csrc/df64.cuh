@@ -94,6 +94,49 @@ __device__ __forceinline__ df df_add(df a, df b) {
 __device__ __forceinline__ df df_neg(df a) { return df{-a.hi, -a.lo}; }
 __device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
 
+// a * b + c * d with one two-sum on the rounded products (their exact errors and the hi * lo cross
+// terms added to the low word): error about 2^-46 (|ab| + |cd|).  Enough where accuracy is judged
+// against the norm of a whole vector, as in the butterflies of an FFT.
+__device__ __forceinline__ df df_dot2(df a, df b, df c, df d) {
+  const float p = __fmul_rn(a.hi, b.hi), q = __fmul_rn(c.hi, d.hi);
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  float f = fmaf(c.hi, d.hi, -q);
+  f = fmaf(c.hi, d.lo, f);
+  f = fmaf(c.lo, d.hi, f);
+  float s, t;
+  two_sum(p, q, s, t);
+  t = __fadd_rn(t, __fadd_rn(e, f));
+  df r;
+  quick_two_sum(s, t, r.hi, r.lo);
+  return r;
+}
+// a + b with one two-sum on the high words; error about 2^-46 (|a| + |b|), as df_dot2.
+__device__ __forceinline__ df df_add_fast(df a, df b) {
+  float s, t;
+  two_sum(a.hi, b.hi, s, t);
+  t = __fadd_rn(t, __fadd_rn(a.lo, b.lo));
+  df r;
+  quick_two_sum(s, t, r.hi, r.lo);
+  return r;
+}
+
+// Complex double-float (float4 layout) for the mixed-form FFT butterflies.
+__device__ __forceinline__ float4 dfc_mul(float4 a, float4 b) {
+  const df re = df_dot2(df{a.x, a.y}, df{b.x, b.y}, df{-a.z, -a.w}, df{b.z, b.w});
+  const df im = df_dot2(df{a.x, a.y}, df{b.z, b.w}, df{a.z, a.w}, df{b.x, b.y});
+  return make_float4(re.hi, re.lo, im.hi, im.lo);
+}
+__device__ __forceinline__ float4 dfc_add(float4 a, float4 b) {
+  const df re = df_add_fast(df{a.x, a.y}, df{b.x, b.y}), im = df_add_fast(df{a.z, a.w}, df{b.z, b.w});
+  return make_float4(re.hi, re.lo, im.hi, im.lo);
+}
+__device__ __forceinline__ float4 dfc_sub(float4 a, float4 b) {
+  const df re = df_add_fast(df{a.x, a.y}, df{-b.x, -b.y}), im = df_add_fast(df{a.z, a.w}, df{-b.z, -b.w});
+  return make_float4(re.hi, re.lo, im.hi, im.lo);
+}
+
 // A double constant as a double-float pair, folded at compile time when used in a constant expression.
 __host__ __device__ constexpr df df_const(double v) { return df{(float)v, (float)(v - (double)(float)v)}; }
 

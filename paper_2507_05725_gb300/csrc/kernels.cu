@@ -93,12 +93,13 @@ __global__ void k_bessel0(const double* __restrict__ z, double* j0, double* y0, 
 // ---------------------------------------------------------------------------------------------
 // Tables
 
-__global__ void k_fft_tw(double2* tw, int K) {
+__global__ void k_fft_tw(double2* tw, float4* tw_df, int K) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= K / 2) return;
   double s, c;
   sincospi(2.0 * r / K, &s, &c);
   tw[r] = make_double2(c, -s);   // e^{-2 pi i r/K}
+  if (tw_df) tw_df[r] = df_split2(make_double2(c, -s));
 }
 
 // syn_tw[q][l] = (w_l/pi) e^{-i l c_q} e^{-2 pi i (l nlo_q mod K)/K},  fwd_tw[q][l] = dt e^{i l c_q}
@@ -1366,9 +1367,47 @@ __device__ void block_fft(double2* buf, int K, int logK, const double2* __restri
   }
 }
 
+// The same FFT in double-float on the FP32 pipe (mixed form): complex values as float4 (re.hi,
+// re.lo, im.hi, im.lo), twiddles from a double-float table.
+__device__ void block_fft_df(float4* buf, int K, int logK, const float4* __restrict__ tw) {
+  for (int s = 1; s <= logK; ++s) {
+    const int half = 1 << (s - 1);
+    const int tws = K >> s;
+    for (int j = threadIdx.x; j < K / 2; j += blockDim.x) {
+      const int pos = j & (half - 1);
+      const int i0 = ((j >> (s - 1)) << s) + pos;
+      const int i1 = i0 + half;
+      const float4 a = buf[i0];
+      const float4 bb = dfc_mul(buf[i1], tw[pos * tws]);
+      buf[i0] = dfc_add(a, bb);
+      buf[i1] = dfc_sub(a, bb);
+    }
+    __syncthreads();
+  }
+}
+
 __device__ __forceinline__ int bitrev(int b, int logK) { return (int)(__brev((unsigned)b) >> (32 - logK)); }
 
+// Transform of the bit-reversed spectrum in buf (FP64, or double-float for DF) and read-back of bin
+// r as FP64.
+template <bool DF>
+__device__ __forceinline__ void fft_in_place(const DevJob& J, double2* buf) {
+  if (DF) block_fft_df(reinterpret_cast<float4*>(buf), J.K, J.logK, J.fft_tw_df);
+  else block_fft(buf, J.K, J.logK, J.fft_tw);
+}
+template <bool DF>
+__device__ __forceinline__ void fft_put(double2* buf, int i, double2 v) {
+  if (DF) reinterpret_cast<float4*>(buf)[i] = df_split2(v);
+  else buf[i] = v;
+}
+template <bool DF>
+__device__ __forceinline__ double2 fft_get(const double2* buf, int i) {
+  if (DF) return df_join2(reinterpret_cast<const float4*>(buf)[i]);
+  return buf[i];
+}
+
 // Windowed slow transforms of g[0..NT) into out[q*L + l] (eq. Fourierk with the exact phase split).
+template <bool DF>
 __device__ void forward_all(const DevJob& J, const double* g, double2* buf, double2* out) {
   const int K = J.K, NT = J.NT, L = J.L;
   for (int q = 0; q < J.Q; ++q) {
@@ -1376,14 +1415,14 @@ __device__ void forward_all(const DevJob& J, const double* g, double2* buf, doub
     for (int b = threadIdx.x; b < K; b += blockDim.x) {
       double acc = 0.0;
       for (int n = b; n < NT; n += K) acc = fma(g[n], wq[n], acc);
-      buf[bitrev(b, J.logK)] = make_double2(acc, 0.0);
+      fft_put<DF>(buf, bitrev(b, J.logK), make_double2(acc, 0.0));
     }
     __syncthreads();
-    block_fft(buf, K, J.logK, J.fft_tw);
+    fft_in_place<DF>(J, buf);
     for (int l = threadIdx.x; l < L; l += blockDim.x) {
       double2 v = make_double2(0.0, 0.0);
       if (l > 0) {
-        double2 y = buf[l & (K - 1)];
+        double2 y = fft_get<DF>(buf, l & (K - 1));
         v = cmul(J.fwd_tw[q * L + l], make_double2(y.x, -y.y));
       }
       out[q * L + l] = v;
@@ -1414,6 +1453,7 @@ __device__ double incident_u(const DevJob& J, double X, double Y, double t) {
   return acc * dv * (0.5 * kInvPi);
 }
 
+template <bool DF>
 __global__ void __launch_bounds__(kTimeMaxThreads) k_incident(DevJob J) {
   extern __shared__ double2 sht[];
   const int a = blockIdx.x;
@@ -1425,9 +1465,10 @@ __global__ void __launch_bounds__(kTimeMaxThreads) k_incident(DevJob J) {
   const double pref = J.sign * J.chi[J.tr_off[k] + x];
   for (int n = threadIdx.x; n < J.NT; n += blockDim.x) g[n] = pref * incident_u(J, X, Y, -J.H + n * J.dt);
   __syncthreads();
-  forward_all(J, g, buf, J.Gt + (J.tr_off[k] + x) * J.Q * J.L);
+  forward_all<DF>(J, g, buf, J.Gt + (J.tr_off[k] + x) * J.Q * J.L);
 }
 
+template <bool DF>
 __global__ void __launch_bounds__(kTimeMaxThreads) k_synth_fwd(DevJob J) {
   extern __shared__ double2 sht[];
   const int a = blockIdx.x;
@@ -1443,21 +1484,21 @@ __global__ void __launch_bounds__(kTimeMaxThreads) k_synth_fwd(DevJob J) {
     for (int b = threadIdx.x; b < K; b += blockDim.x) {
       double2 acc = make_double2(0.0, 0.0);
       for (int l = (b == 0 ? K : b); l < L; l += K) acc = cfma(st[l], Wq[l], acc);
-      buf[bitrev(b, J.logK)] = acc;
+      fft_put<DF>(buf, bitrev(b, J.logK), acc);
     }
     __syncthreads();
-    block_fft(buf, K, J.logK, J.fft_tw);
+    fft_in_place<DF>(J, buf);
     const int n0 = J.nlo[q];
     for (int r = threadIdx.x; r < K; r += blockDim.x) {
       const int n = n0 + r;
-      if (n < NT) g[n] += buf[r].x;
+      if (n < NT) g[n] += fft_get<DF>(buf, r).x;
     }
     __syncthreads();
   }
   const double mchi = -J.chi[J.tr_off[k] + x];
   for (int n = threadIdx.x; n < NT; n += blockDim.x) g[n] *= mchi;
   __syncthreads();
-  forward_all(J, g, buf, J.Gt + base);
+  forward_all<DF>(J, g, buf, J.Gt + base);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -1536,7 +1577,7 @@ cudaError_t launch_bessel0(const double* z, double* j0, double* y0, double* yh, 
 }
 
 cudaError_t launch_tables(const DevJob& J, cudaStream_t st, int* launches) {
-  k_fft_tw<<<cdiv(J.K / 2, 256), 256, 0, st>>>(J.fft_tw, J.K);
+  k_fft_tw<<<cdiv(J.K / 2, 256), 256, 0, st>>>(J.fft_tw, J.fft_tw_df, J.K);
   k_freq_tw<<<cdiv((long long)J.Q * J.L, 256), 256, 0, st>>>(J);
   *launches += 2;
   if (J.n_rlogN > 0) {
@@ -1605,9 +1646,12 @@ static size_t time_smem(const DevJob& J) { return (size_t)J.K * sizeof(double2) 
 cudaError_t launch_incident(const DevJob& J, cudaStream_t st, int* launches) {
   if (J.n_act == 0) return cudaSuccess;
   size_t sh = time_smem(J);
-  cudaError_t e = cudaFuncSetAttribute(k_incident, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+  const int nt = J.shape_time > 0 ? J.shape_time : kTimeThreads;
+  cudaError_t e = cudaFuncSetAttribute(J.mixed ? k_incident<true> : k_incident<false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
   if (e != cudaSuccess) return e;
-  k_incident<<<J.n_act, J.shape_time > 0 ? J.shape_time : kTimeThreads, sh, st>>>(J);
+  if (J.mixed) k_incident<true><<<J.n_act, nt, sh, st>>>(J);
+  else k_incident<false><<<J.n_act, nt, sh, st>>>(J);
   *launches += 1;
   return cudaGetLastError();
 }
@@ -1615,9 +1659,12 @@ cudaError_t launch_incident(const DevJob& J, cudaStream_t st, int* launches) {
 cudaError_t launch_synth_fwd(const DevJob& J, cudaStream_t st, int* launches) {
   if (J.n_act == 0) return cudaSuccess;
   size_t sh = time_smem(J);
-  cudaError_t e = cudaFuncSetAttribute(k_synth_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+  const int nt = J.shape_time > 0 ? J.shape_time : kTimeThreads;
+  cudaError_t e = cudaFuncSetAttribute(J.mixed ? k_synth_fwd<true> : k_synth_fwd<false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
   if (e != cudaSuccess) return e;
-  k_synth_fwd<<<J.n_act, J.shape_time > 0 ? J.shape_time : kTimeThreads, sh, st>>>(J);
+  if (J.mixed) k_synth_fwd<true><<<J.n_act, nt, sh, st>>>(J);
+  else k_synth_fwd<false><<<J.n_act, nt, sh, st>>>(J);
   *launches += 1;
   return cudaGetLastError();
 }

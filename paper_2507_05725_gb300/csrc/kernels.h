@@ -82,6 +82,7 @@ struct DevJob {
   double2* Vobs;             // [z][q][l]
   double* traces;            // [z][tout]
   double2* fft_tw;           // K/2 twiddles e^{-2 pi i r/K}
+  float4* fft_tw_df;         // the same as double-float pairs (mixed form)
   double2* syn_tw;           // [Q][L]
   double2* fwd_tw;           // [Q][L]
   long long vec_total;

@@ -579,7 +579,7 @@ size_t plan_device_bytes(const Plan& p) {
   if (p.opt.precision == 1 || p.opt.cross_mode == 1) b += (size_t)p.res_total * p.Q * 16;   // per-row cross sums
   if (p.opt.cross_mode == 1)
     b += (size_t)p.wn_total * 8 + p.otf.size() * sizeof(CrossOtf) + p.otf_res_off.size() * 8 + p.wn_off.size() * 8;
-  b += p.win.size() * 8 + (size_t)p.Q * p.L * 32 + (size_t)p.K * 8 + p.chi.size() * 8;
+  b += p.win.size() * 8 + (size_t)p.Q * p.L * 32 + (size_t)p.K * (p.opt.precision == 1 ? 16 : 8) + p.chi.size() * 8;
   return b;
 }
 
