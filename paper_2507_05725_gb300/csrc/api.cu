@@ -274,6 +274,8 @@ fthms_status upload_job(fthms_req* r) {
   }
   TRY(dev_alloc(r, (size_t)p.vec_total, &J.G));
   TRY(dev_alloc(r, (size_t)p.vec_total, &J.phi));
+  J.phi_df = nullptr;
+  if (J.mixed) TRY(dev_alloc(r, (size_t)p.vec_total, &J.phi_df));
   TRY(dev_alloc(r, (size_t)p.vec_total, &J.phi_sum));
   J.phi_all = nullptr;
   if (p.opt.keep_densities) TRY(dev_alloc(r, (size_t)p.vec_total * p.M, &J.phi_all));

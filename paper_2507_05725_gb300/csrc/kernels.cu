@@ -1231,8 +1231,11 @@ __global__ void __launch_bounds__(32 * kSolveWarps, 4) k_msolve(DevJob J, int m,
   double2* out = J.phi + s.vec_off;
   double2* sum = J.phi_sum + s.vec_off;
   double2* all = J.phi_all ? J.phi_all + (long long)(m - 1) * J.vec_total + s.vec_off : nullptr;
+  float4* pdf = J.phi_df + s.vec_off;
   for (int e = lane; e < Q * N; e += 32) {
-    const double2 v = df_join2(ph[e]);
+    const float4 p = ph[e];
+    const double2 v = df_join2(p);
+    pdf[e] = p;
     out[e] = v;
     sum[e] = m == 1 ? v : cadd(sum[e], v);
     if (all) all[e] = v;
@@ -1264,8 +1267,8 @@ __global__ void __launch_bounds__(kApplySlice) k_cross_rows_df(DevJob J) {
   __syncthreads();
   for (int b = 0; b < nb; ++b) {
     const CrossBlk B = J.blks[sl.b0 + b];
-    const double2* p = J.phi + J.sys[B.sys].vec_off;
-    for (int e = threadIdx.x; e < Q * B.N; e += kApplySlice) ph[s_ph0[b] + e] = df_split2(p[e]);
+    const float4* p = J.phi_df + J.sys[B.sys].vec_off;
+    for (int e = threadIdx.x; e < Q * B.N; e += kApplySlice) ph[s_ph0[b] + e] = p[e];
   }
   __syncthreads();
   if ((int)threadIdx.x >= sl.nrows) return;

@@ -74,6 +74,7 @@ struct DevJob {
   double2* dinv;             // 1 / U_kk
   double2* G;                // data on solve nodes [s][q][i]
   double2* phi;              // current densities
+  float4* phi_df;            // the same as double-float pairs, written by the mixed solve for the apply
   double2* phi_sum;
   double2* phi_all;          // [m][...] or null
   double2* W;                // cross fields at transfer nodes [(tr_off+x)*Q+q]*L+l
