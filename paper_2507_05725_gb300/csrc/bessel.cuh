@@ -69,6 +69,8 @@ __device__ __forceinline__ void sincos_taylor(double x, double& s, double& c) {
 // unit only).
 __constant__ double c_hank_a[20];
 __constant__ float2 c_hank_df[20];   // the same coefficients as double-float (hi, lo)
+// kTaylorJ0 and kTaylorYh as double-float pairs (mixed form), split on the host at start-up.
+__device__ float2 c_taylor_df[2][kTaylorIntervals][kTaylorDegree + 1];
 
 // 0 <= z < 20: piecewise Taylor expansions of J0 and Yhat0 about c_k = 0.25 + 0.5 k (both functions
 // are entire), 13 terms each, coefficients from gen_bessel_taylor.py (mpmath).  Every lane runs the

@@ -34,7 +34,21 @@ cudaError_t init_constants() {
   }
   cudaError_t e = cudaMemcpyToSymbol(c_hank_a, ha, sizeof ha);
   if (e != cudaSuccess) return e;
-  return cudaMemcpyToSymbol(c_hank_df, hd, sizeof hd);
+  e = cudaMemcpyToSymbol(c_hank_df, hd, sizeof hd);
+  if (e != cudaSuccess) return e;
+  static double tj[kTaylorIntervals][kTaylorDegree + 1], ty[kTaylorIntervals][kTaylorDegree + 1];
+  static float2 td[2][kTaylorIntervals][kTaylorDegree + 1];
+  e = cudaMemcpyFromSymbol(tj, kTaylorJ0, sizeof tj);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyFromSymbol(ty, kTaylorYh, sizeof ty);
+  if (e != cudaSuccess) return e;
+  for (int k = 0; k < kTaylorIntervals; ++k)
+    for (int n = 0; n <= kTaylorDegree; ++n) {
+      const float a = (float)tj[k][n], c = (float)ty[k][n];
+      td[0][k][n] = make_float2(a, (float)(tj[k][n] - (double)a));
+      td[1][k][n] = make_float2(c, (float)(ty[k][n] - (double)c));
+    }
+  return cudaMemcpyToSymbol(c_taylor_df, td, sizeof td);
 }
 
 namespace {
@@ -768,6 +782,28 @@ __device__ __forceinline__ PairSetup pair_setup(const DevJob& J, const CrossTgt&
 }
 
 // Entry at z = (l h) R < 20 from the Taylor tables (lh = l h, lnl = ln l).
+// J0 and Yhat0 for 0 <= z < 20 in double-float (mixed form): the piecewise Taylor expansions of
+// bessel0_taylor with double-float coefficients, products and sums.
+__device__ __forceinline__ void bessel0_taylor_df(df z, df& J0, df& Yh) {
+  const int k = min((int)(2.f * z.hi), kTaylorIntervals - 1);
+  const df d = df_add_fast(z, df{-(0.25f + 0.5f * (float)k), 0.f});
+  const float2* cj = c_taylor_df[0][k];
+  const float2* cy = c_taylor_df[1][k];
+  float2 c = __ldg(&cj[kTaylorDegree]);
+  df j{c.x, c.y};
+  c = __ldg(&cy[kTaylorDegree]);
+  df y{c.x, c.y};
+#pragma unroll
+  for (int n = kTaylorDegree - 1; n >= 0; --n) {
+    c = __ldg(&cj[n]);
+    j = df_add_fast(df_mul(j, d), df{c.x, c.y});
+    c = __ldg(&cy[n]);
+    y = df_add_fast(df_mul(y, d), df{c.x, c.y});
+  }
+  J0 = j;
+  Yh = y;
+}
+
 __device__ __forceinline__ double2 taylor_entry(const PairSetup& s, double lh, double lnl, double A1, double qw) {
   double J0, Yh;
   bessel0_taylor(lh * s.R, J0, Yh);
@@ -857,6 +893,8 @@ __global__ void __launch_bounds__(kAsmMaxThreads) k_cross_assemble(DevJob J) {
   double* lh = lnl + kAsmBand;
   df* invl_d = reinterpret_cast<df*>(lh + kAsmBand);      // the same as double-float (mixed form)
   df* rsql_d = invl_d + kAsmBand;
+  df* lnl_d = rsql_d + kAsmBand;
+  df* lh_d = lnl_d + kAsmBand;
   for (int b = threadIdx.x; b < nl; b += blockDim.x) {
     const int l = task.l0 + b;
     invl[b] = 1.0 / l;
@@ -866,6 +904,8 @@ __global__ void __launch_bounds__(kAsmMaxThreads) k_cross_assemble(DevJob J) {
     if (J.mixed) {
       invl_d[b] = df_from(invl[b]);
       rsql_d[b] = df_from(rsql[b]);
+      lnl_d[b] = df_from(lnl[b]);
+      lh_d[b] = df_from(lh[b]);
     }
   }
   __syncthreads();
@@ -877,9 +917,23 @@ __global__ void __launch_bounds__(kAsmMaxThreads) k_cross_assemble(DevJob J) {
                                     t.near ? Wn[r * N + i] : 0.0, task.l0, w, invw, inv_h);
     double2* Ep = J.E + (long long)i * ld + task.row0 + r;
     const int lend = min(ps.lsw, task.l1 + 1);
-    for (int l = task.l0; l < lend; ++l) {
-      const int b = l - task.l0;
-      store_entry(J, Ep + eo[l], taylor_entry(ps, lh[b], lnl[b], A1, qw));
+    if (J.mixed) {
+      // Mixed form, z < 20: the Taylor range in double-float, stored as double-float pairs.
+      const df R_d = df_from(ps.R), A0_d = df_from(ps.A0), A1_d = df_from(A1), qw_d = df_from(qw);
+      for (int l = task.l0; l < lend; ++l) {
+        const int b = l - task.l0;
+        df J0, Yh;
+        bessel0_taylor_df(df_mul(lh_d[b], R_d), J0, Yh);
+        const df alpha = df_add_fast(df_mul(A1_d, lnl_d[b]), A0_d);
+        const df re = df_dot2(alpha, J0, df_neg(qw_d), Yh);
+        const df im = df_mul(qw_d, J0);
+        *reinterpret_cast<float4*>(Ep + eo[l]) = make_float4(re.hi, re.lo, im.hi, im.lo);
+      }
+    } else {
+      for (int l = task.l0; l < lend; ++l) {
+        const int b = l - task.l0;
+        store_entry(J, Ep + eo[l], taylor_entry(ps, lh[b], lnl[b], A1, qw));
+      }
     }
     if (ps.lsw > task.l1) continue;
     const int lsw = ps.lsw;
@@ -908,22 +962,38 @@ __global__ void __launch_bounds__(kAsmMaxThreads) k_cross_assemble(DevJob J) {
         }
         const df wz = df_mul(invu_d, invl_d[b]);
         const df w2 = df_neg(df_mul(wz, wz));
+        // P and Q/w by Horner in w2 = -1/z^2, |w2| <= 1/400: the term of level k is below 2^(-8.6 k)
+        // of the sum, so levels k >= 3 need only FP32 (22 bits) and the outer three double-float;
+        // there the products stay far below the coefficients they are added to (no cancellation).
         const int kmax = as.kmax;
-        float2 c = c_hank_df[2 * kmax];
-        df P{c.x, c.y};
-        c = c_hank_df[2 * kmax + 1];
-        df Qa{c.x, c.y};
-        for (int k = kmax - 1; k >= 0; --k) {
-          c = c_hank_df[2 * k];
-          P = df_add(df_mul(P, w2), df{c.x, c.y});
-          c = c_hank_df[2 * k + 1];
-          Qa = df_add(df_mul(Qa, w2), df{c.x, c.y});
+        df P, Qa;
+        int k;
+        if (kmax >= 3) {
+          const float w2f = w2.hi;
+          float pf = c_hank_df[2 * kmax].x, qf = c_hank_df[2 * kmax + 1].x;
+          for (k = kmax - 1; k >= 3; --k) {
+            pf = fmaf(pf, w2f, c_hank_df[2 * k].x);
+            qf = fmaf(qf, w2f, c_hank_df[2 * k + 1].x);
+          }
+          P = df{pf, 0.f};
+          Qa = df{qf, 0.f};
+          k = 2;
+        } else {
+          const float2 cp = c_hank_df[2 * kmax], cq = c_hank_df[2 * kmax + 1];
+          P = df{cp.x, cp.y};
+          Qa = df{cq.x, cq.y};
+          k = kmax - 1;
+        }
+        for (; k >= 0; --k) {
+          const float2 cp = c_hank_df[2 * k], cq = c_hank_df[2 * k + 1];
+          P = df_add_fast(df_mul(P, w2), df{cp.x, cp.y});
+          Qa = df_add_fast(df_mul(Qa, w2), df{cq.x, cq.y});
         }
         Qa = df_mul(Qa, wz);
         const df a = df_mul(ampw_d, rsql_d[b]);
-        const df t1 = df_add(df_mul(P, cx_d), df_mul(Qa, sx_d));
-        const df t2 = df_sub(df_mul(P, sx_d), df_mul(Qa, cx_d));
-        const df re = df_mul(a, df_sub(df_mul(beta_d, t1), t2));
+        const df t1 = df_dot2(P, cx_d, Qa, sx_d);
+        const df t2 = df_dot2(P, sx_d, df_neg(Qa), cx_d);
+        const df re = df_mul(a, df_dot2(beta_d, t1, df{-1.f, 0.f}, t2));
         const df im = df_mul(a, t1);
         *reinterpret_cast<float4*>(Ep + eo[l]) = make_float4(re.hi, re.lo, im.hi, im.lo);
         const df cn = df_sub(df_mul(cx_d, cu_d), df_mul(sx_d, su_d));
@@ -1635,8 +1705,9 @@ cudaError_t launch_lu(const DevJob& J, cudaStream_t st, int* launches) {
 cudaError_t launch_cross_assemble(const DevJob& J, cudaStream_t st, int* launches) {
   if (J.n_asm == 0) return cudaSuccess;
   // Shared layout of k_cross_assemble, in 8-byte words: ctab 4N, lam kAsmRows N, Wn kAsmRows N, then
-  // band tables invl, rsql, lnl, lh (doubles) and invl_d, rsql_d (double-float pairs), kAsmBand each.
-  size_t sh = ((size_t)(4 + 2 * kAsmRows) * J.max_n + 6 * kAsmBand) * sizeof(double);
+  // band tables invl, rsql, lnl, lh (doubles) and invl_d, rsql_d, lnl_d, lh_d (double-float pairs),
+  // kAsmBand each.
+  size_t sh = ((size_t)(4 + 2 * kAsmRows) * J.max_n + 8 * kAsmBand) * sizeof(double);
   cudaError_t e = cudaFuncSetAttribute(k_cross_assemble, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
   if (e != cudaSuccess) return e;
   k_cross_assemble<<<J.n_asm, J.shape_asm > 0 ? J.shape_asm : kAsmThreads, sh, st>>>(J);
