@@ -241,12 +241,63 @@ __device__ __forceinline__ void store_self(const DevJob& J, long long off, doubl
   }
 }
 
+// P and Q/w of the Hankel asymptotics (kmax + 1 terms each) by Horner's rule in w2 = -1/z^2 in
+// double-float.  With |w2| <= 1/400 (z >= 20) the level-k term is below 2^(-8.6 k) of the sum, so the
+// levels k >= 3 need only FP32 (22 bits) and the outer three double-float, where each product stays
+// far below the coefficient it is added to (no cancellation).
+__device__ __forceinline__ void hankel_pq_df(int kmax, df w2, df& P, df& Qa) {
+  int k;
+  if (kmax >= 3) {
+    const float w2f = w2.hi;
+    float pf = c_hank_df[2 * kmax].x, qf = c_hank_df[2 * kmax + 1].x;
+    for (k = kmax - 1; k >= 3; --k) {
+      pf = fmaf(pf, w2f, c_hank_df[2 * k].x);
+      qf = fmaf(qf, w2f, c_hank_df[2 * k + 1].x);
+    }
+    P = df{pf, 0.f};
+    Qa = df{qf, 0.f};
+    k = 2;
+  } else {
+    const float2 cp = c_hank_df[2 * kmax], cq = c_hank_df[2 * kmax + 1];
+    P = df{cp.x, cp.y};
+    Qa = df{cq.x, cq.y};
+    k = kmax - 1;
+  }
+  for (; k >= 0; --k) {
+    const float2 cp = c_hank_df[2 * k], cq = c_hank_df[2 * k + 1];
+    P = df_add_fast(df_mul(P, w2), df{cp.x, cp.y});
+    Qa = df_add_fast(df_mul(Qa, w2), df{cq.x, cq.y});
+  }
+}
+
+// J0 and Yhat0 for 0 <= z < 20 in double-float (mixed form): the piecewise Taylor expansions of
+// bessel0_taylor with double-float coefficients, products and sums.
+__device__ __forceinline__ void bessel0_taylor_df(df z, df& J0, df& Yh) {
+  const int k = min((int)(2.f * z.hi), kTaylorIntervals - 1);
+  const df d = df_add_fast(z, df{-(0.25f + 0.5f * (float)k), 0.f});
+  const float2* cj = c_taylor_df[0][k];
+  const float2* cy = c_taylor_df[1][k];
+  float2 c = __ldg(&cj[kTaylorDegree]);
+  df j{c.x, c.y};
+  c = __ldg(&cy[kTaylorDegree]);
+  df y{c.x, c.y};
+#pragma unroll
+  for (int n = kTaylorDegree - 1; n >= 0; --n) {
+    c = __ldg(&cj[n]);
+    j = df_add_fast(df_mul(j, d), df{c.x, c.y});
+    c = __ldg(&cy[n]);
+    y = df_add_fast(df_mul(y, d), df{c.x, c.y});
+  }
+  J0 = j;
+  Yh = y;
+}
+
 __global__ void __launch_bounds__(256) k_assemble_self(DevJob J) {
   const SelfTile tile = J.tiles[blockIdx.x];
   const SysDesc s0 = J.sys[tile.sys];
   const int N = s0.N, nb = tile.nsys;
   __shared__ double lnl[kSelfBand], invl[kSelfBand], rsql[kSelfBand];
-  __shared__ df invl_d[kSelfBand], rsql_d[kSelfBand];      // mixed form
+  __shared__ df invl_d[kSelfBand], rsql_d[kSelfBand], lnl_d[kSelfBand], lh_d[kSelfBand];   // mixed form
   if (threadIdx.x < nb) {
     const double l = (double)(s0.l + threadIdx.x);
     lnl[threadIdx.x] = log(l);
@@ -255,6 +306,8 @@ __global__ void __launch_bounds__(256) k_assemble_self(DevJob J) {
     if (J.mixed) {
       invl_d[threadIdx.x] = df_from(invl[threadIdx.x]);
       rsql_d[threadIdx.x] = df_from(rsql[threadIdx.x]);
+      lnl_d[threadIdx.x] = df_from(lnl[threadIdx.x]);
+      lh_d[threadIdx.x] = df_from(l * J.h);
     }
   }
   __syncthreads();
@@ -292,16 +345,37 @@ __global__ void __launch_bounds__(256) k_assemble_self(DevJob J) {
   const int lend = s0.l + nb;
   const double zmin = (lsw * J.h) * R;
   const int kmax = hankel_terms((float)zmin);
-  for (int l = s0.l; l < min(lsw, lend); ++l) {
-    const int b = l - s0.l;
-    const double z = (l * J.h) * R;
-    double J0, Yh;
-    bessel0_taylor(z, J0, Yh);
-    const double alpha = -0.5 * kInvPi * fma(w, lnl[b] + lratio, rl);
-    const double2 v = make_double2(fma(alpha, J0, -qw * Yh), qw * J0);
-    const long long mo = J.sys[tile.sys + b].mat_off;
-    store_self(J, mo + e1, v);
-    store_self(J, mo + e2, v);
+  if (J.mixed) {
+    // Mixed form, z < 20: the Taylor range in double-float, alpha = aw ln l + a0.
+    const df R_d = df_from(R), qw_d = df_from(qw), aw_d = df_from(-0.5 * kInvPi * w),
+             a0_d = df_from(-0.5 * kInvPi * fma(w, lratio, rl));
+    for (int l = s0.l; l < min(lsw, lend); ++l) {
+      const int b = l - s0.l;
+      df J0, Yh;
+      bessel0_taylor_df(df_mul(lh_d[b], R_d), J0, Yh);
+      const df alpha = df_add_fast(df_mul(aw_d, lnl_d[b]), a0_d);
+      const df re = df_dot2(alpha, J0, df_neg(qw_d), Yh);
+      const df im = df_mul(qw_d, J0);
+      const long long mo = J.sys[tile.sys + b].mat_off;
+      const float4 d = make_float4(re.hi, re.lo, im.hi, im.lo);
+      const float2 f = make_float2(re.hi, im.hi);
+      reinterpret_cast<float4*>(J.A)[mo + e1] = d;
+      reinterpret_cast<float4*>(J.A)[mo + e2] = d;
+      J.LU32[mo + e1] = f;
+      J.LU32[mo + e2] = f;
+    }
+  } else {
+    for (int l = s0.l; l < min(lsw, lend); ++l) {
+      const int b = l - s0.l;
+      const double z = (l * J.h) * R;
+      double J0, Yh;
+      bessel0_taylor(z, J0, Yh);
+      const double alpha = -0.5 * kInvPi * fma(w, lnl[b] + lratio, rl);
+      const double2 v = make_double2(fma(alpha, J0, -qw * Yh), qw * J0);
+      const long long mo = J.sys[tile.sys + b].mat_off;
+      store_self(J, mo + e1, v);
+      store_self(J, mo + e2, v);
+    }
   }
   if (J.mixed && lsw < lend) {
     // Mixed form: the recurrence above z = 20 in double-float on the FP32 pipe (about 48 bits), stored
@@ -326,21 +400,13 @@ __global__ void __launch_bounds__(256) k_assemble_self(DevJob J) {
       }
       const df wz = df_mul(invu_d, invl_d[b]);
       const df w2 = df_neg(df_mul(wz, wz));
-      float2 cf = c_hank_df[2 * kmax];
-      df P{cf.x, cf.y};
-      cf = c_hank_df[2 * kmax + 1];
-      df Qa{cf.x, cf.y};
-      for (int k = kmax - 1; k >= 0; --k) {
-        cf = c_hank_df[2 * k];
-        P = df_add(df_mul(P, w2), df{cf.x, cf.y});
-        cf = c_hank_df[2 * k + 1];
-        Qa = df_add(df_mul(Qa, w2), df{cf.x, cf.y});
-      }
+      df P, Qa;
+      hankel_pq_df(kmax, w2, P, Qa);
       Qa = df_mul(Qa, wz);
       const df amp = df_mul(ampu_d, rsql_d[b]);
-      const df J0 = df_mul(amp, df_add(df_mul(P, cx_d), df_mul(Qa, sx_d)));
-      const df Y0 = df_mul(amp, df_sub(df_mul(P, sx_d), df_mul(Qa, cx_d)));
-      const df re = df_sub(df_mul(alpha_d, J0), df_mul(qw_d, Y0));
+      const df J0 = df_mul(amp, df_dot2(P, cx_d, Qa, sx_d));
+      const df Y0 = df_mul(amp, df_dot2(P, sx_d, df_neg(Qa), cx_d));
+      const df re = df_dot2(alpha_d, J0, df_neg(qw_d), Y0);
       const df im = df_mul(qw_d, J0);
       const long long mo = J.sys[tile.sys + b].mat_off;
       const float4 d = make_float4(re.hi, re.lo, im.hi, im.lo);
@@ -782,28 +848,6 @@ __device__ __forceinline__ PairSetup pair_setup(const DevJob& J, const CrossTgt&
 }
 
 // Entry at z = (l h) R < 20 from the Taylor tables (lh = l h, lnl = ln l).
-// J0 and Yhat0 for 0 <= z < 20 in double-float (mixed form): the piecewise Taylor expansions of
-// bessel0_taylor with double-float coefficients, products and sums.
-__device__ __forceinline__ void bessel0_taylor_df(df z, df& J0, df& Yh) {
-  const int k = min((int)(2.f * z.hi), kTaylorIntervals - 1);
-  const df d = df_add_fast(z, df{-(0.25f + 0.5f * (float)k), 0.f});
-  const float2* cj = c_taylor_df[0][k];
-  const float2* cy = c_taylor_df[1][k];
-  float2 c = __ldg(&cj[kTaylorDegree]);
-  df j{c.x, c.y};
-  c = __ldg(&cy[kTaylorDegree]);
-  df y{c.x, c.y};
-#pragma unroll
-  for (int n = kTaylorDegree - 1; n >= 0; --n) {
-    c = __ldg(&cj[n]);
-    j = df_add_fast(df_mul(j, d), df{c.x, c.y});
-    c = __ldg(&cy[n]);
-    y = df_add_fast(df_mul(y, d), df{c.x, c.y});
-  }
-  J0 = j;
-  Yh = y;
-}
-
 __device__ __forceinline__ double2 taylor_entry(const PairSetup& s, double lh, double lnl, double A1, double qw) {
   double J0, Yh;
   bessel0_taylor(lh * s.R, J0, Yh);
@@ -962,33 +1006,8 @@ __global__ void __launch_bounds__(kAsmMaxThreads) k_cross_assemble(DevJob J) {
         }
         const df wz = df_mul(invu_d, invl_d[b]);
         const df w2 = df_neg(df_mul(wz, wz));
-        // P and Q/w by Horner in w2 = -1/z^2, |w2| <= 1/400: the term of level k is below 2^(-8.6 k)
-        // of the sum, so levels k >= 3 need only FP32 (22 bits) and the outer three double-float;
-        // there the products stay far below the coefficients they are added to (no cancellation).
-        const int kmax = as.kmax;
         df P, Qa;
-        int k;
-        if (kmax >= 3) {
-          const float w2f = w2.hi;
-          float pf = c_hank_df[2 * kmax].x, qf = c_hank_df[2 * kmax + 1].x;
-          for (k = kmax - 1; k >= 3; --k) {
-            pf = fmaf(pf, w2f, c_hank_df[2 * k].x);
-            qf = fmaf(qf, w2f, c_hank_df[2 * k + 1].x);
-          }
-          P = df{pf, 0.f};
-          Qa = df{qf, 0.f};
-          k = 2;
-        } else {
-          const float2 cp = c_hank_df[2 * kmax], cq = c_hank_df[2 * kmax + 1];
-          P = df{cp.x, cp.y};
-          Qa = df{cq.x, cq.y};
-          k = kmax - 1;
-        }
-        for (; k >= 0; --k) {
-          const float2 cp = c_hank_df[2 * k], cq = c_hank_df[2 * k + 1];
-          P = df_add_fast(df_mul(P, w2), df{cp.x, cp.y});
-          Qa = df_add_fast(df_mul(Qa, w2), df{cq.x, cq.y});
-        }
+        hankel_pq_df(as.kmax, w2, P, Qa);
         Qa = df_mul(Qa, wz);
         const df a = df_mul(ampw_d, rsql_d[b]);
         const df t1 = df_dot2(P, cx_d, Qa, sx_d);
