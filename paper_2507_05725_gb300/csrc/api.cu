@@ -205,6 +205,8 @@ fthms_status upload_job(fthms_req* r) {
   TRY(dev_upload(r, rn, &J.restr_N));
   TRY(dev_upload(r, p.restr_off, &J.restr_off));
   TRY(dev_alloc(r, (size_t)p.restr_total, &J.restr));
+  J.restr_df = nullptr;
+  if (p.opt.precision == 1) TRY(dev_alloc(r, (size_t)p.restr_total, &J.restr_df));
   TRY(dev_upload(r, p.restr_of_sys, &J.restr_of_sys));
   TRY(dev_upload(r, p.self_tiles, &J.tiles));
   TRY(dev_upload(r, p.tgts, &J.tgts));

@@ -201,6 +201,10 @@ __global__ void k_restr(DevJob J) {
       v = sb[x] * cA[i] / (m2 * ssum * sinpi((double)D / nm4));
     }
     RT[e] = v;
+    if (J.restr_df) {   // mixed form: the same table as double-float pairs
+      const float h = __double2float_rn(v);
+      J.restr_df[J.restr_off[t] + e] = make_float2(h, __double2float_rn(v - (double)h));
+    }
   }
 }
 
@@ -1598,6 +1602,7 @@ __global__ void __launch_bounds__(kTimeMaxThreads) k_synth_fwd(DevJob J) {
 constexpr int kRestrThreads = 128;
 constexpr int kRestrMaxThreads = 256;   // largest restriction block a tuned launch may use
 
+template <bool DF>
 __global__ void __launch_bounds__(kRestrMaxThreads) k_restrict(DevJob J) {
   extern __shared__ double2 shr[];
   const int sidx = blockIdx.x;
@@ -1614,6 +1619,29 @@ __global__ void __launch_bounds__(kRestrMaxThreads) k_restrict(DevJob J) {
     return;
   }
   const int a0 = J.act_off[k], na = J.act_off[k + 1] - a0;
+  if (DF) {
+    // Mixed form: the same sums in double-float (spectra split once, compensated sums).
+    float4* sh4 = reinterpret_cast<float4*>(shr);
+    for (int e = threadIdx.x; e < Q * na; e += blockDim.x) {
+      int q = e / na, a = e % na;
+      sh4[e] = df_split2(J.Gt[((base + J.act_idx[a0 + a]) * Q + q) * L + l]);
+    }
+    __syncthreads();
+    const float2* RTd = J.restr_df + off;
+    for (int e = threadIdx.x; e < Q * N; e += blockDim.x) {
+      int q = e / N, i = e % N;
+      dfacc re, im;
+      for (int a = 0; a < na; ++a) {
+        const float2 rv = RTd[(long long)J.act_idx[a0 + a] * N + i];
+        const float4 gv = sh4[q * na + a];
+        re.mac(rv.x, rv.y, gv.x, gv.y);
+        im.mac(rv.x, rv.y, gv.z, gv.w);
+      }
+      const df vr = re.value(), vi = im.value();
+      G[e] = make_double2((double)vr.hi + (double)vr.lo, (double)vi.hi + (double)vi.lo);
+    }
+    return;
+  }
   for (int e = threadIdx.x; e < Q * na; e += blockDim.x) {
     int q = e / na, a = e % na;
     shr[e] = J.Gt[((base + J.act_idx[a0 + a]) * Q + q) * L + l];
@@ -1764,9 +1792,12 @@ cudaError_t launch_synth_fwd(const DevJob& J, cudaStream_t st, int* launches) {
 
 cudaError_t launch_restrict(const DevJob& J, cudaStream_t st, int* launches) {
   size_t sh = (size_t)J.Q * J.max_nmax * sizeof(double2);
-  cudaError_t e = cudaFuncSetAttribute(k_restrict, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+  const int nt = J.shape_restr > 0 ? J.shape_restr : kRestrThreads;
+  cudaError_t e = cudaFuncSetAttribute(J.mixed ? k_restrict<true> : k_restrict<false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
   if (e != cudaSuccess) return e;
-  k_restrict<<<J.nsys, J.shape_restr > 0 ? J.shape_restr : kRestrThreads, sh, st>>>(J);
+  if (J.mixed) k_restrict<true><<<J.nsys, nt, sh, st>>>(J);
+  else k_restrict<false><<<J.nsys, nt, sh, st>>>(J);
   *launches += 1;
   return cudaGetLastError();
 }

@@ -28,6 +28,7 @@ struct DevJob {
   const int* restr_N;        // [n_restr][2] (N, Nmax)
   const long long* restr_off;
   double* restr;             // transposed tables RT[x][i]
+  float2* restr_df;          // the same as double-float pairs (mixed form)
   const long long* restr_of_sys;
   const SelfTile* tiles;
   const CrossTgt* tgts;

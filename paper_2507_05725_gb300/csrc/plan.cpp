@@ -572,7 +572,7 @@ size_t plan_device_bytes(const Plan& p) {
   if (p.opt.keep_densities) b += (size_t)p.vec_total * 16 * p.M;
   b += (size_t)p.spec_total * 16 * 2;            // W and Gt on transfer meshes
   if (p.opt.cross_mode == 0) b += (size_t)p.e_total * 16;   // stored cross matrices
-  b += (size_t)p.restr_total * 8;
+  b += (size_t)p.restr_total * (p.opt.precision == 1 ? 16 : 8);
   b += (size_t)p.n_obs * p.Q * p.L * 16 + (size_t)p.n_obs * p.n_tout * 8;
   b += p.node_t.size() * 32 + p.tgts.size() * sizeof(CrossTgt) + p.blks.size() * sizeof(CrossBlk) +
        p.asms.size() * sizeof(CrossAsm) + p.self_tiles.size() * sizeof(SelfTile) + p.sys.size() * (sizeof(SysDesc) + sizeof(int)) + p.slices.size() * sizeof(ApplySlice) + p.grp_res_off.size() * 8;
