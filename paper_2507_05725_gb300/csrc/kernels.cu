@@ -1240,7 +1240,8 @@ __global__ void __launch_bounds__(kResidThreads) k_mresid(DevJob J) {
     re[q].add(gd.x, gd.y);
     im[q].add(gd.z, gd.w);
   }
-#pragma unroll 4
+  constexpr int kUnroll = Q == 1 ? 8 : Q == 2 ? 4 : 2;   // loads in flight without spilling
+#pragma unroll kUnroll
   for (int j = 0; j < N; ++j) {
     const float4 a = __ldg(&Adf[(long long)j * N + row]);
     const float4 na = make_float4(-a.x, -a.y, -a.z, -a.w);
@@ -1340,7 +1341,7 @@ __global__ void __launch_bounds__(32 * kSolveWarps, 4) k_msolve(DevJob J, int m,
 // row's double-float sum over its block's sources (E and phi as df64, two compensated sums).  No
 // barrier after the density staging, and many small CTAs per SM keep enough loads in flight.
 template <int Q>
-__global__ void __launch_bounds__(kApplySlice) k_cross_rows_df(DevJob J) {
+__global__ void __launch_bounds__(kApplySlice, 3) k_cross_rows_df(DevJob J) {
   extern __shared__ __align__(16) unsigned char shd_raw[];
   float4* ph = reinterpret_cast<float4*>(shd_raw);        // df64 densities of the overlapped blocks
   const ApplySlice sl = J.slices[blockIdx.x];
@@ -1374,7 +1375,8 @@ __global__ void __launch_bounds__(kApplySlice) k_cross_rows_df(DevJob J) {
   dfacc sr[Q], si[Q], tr[Q], ti[Q];
   const float4* __restrict__ Er = reinterpret_cast<const float4*>(J.E + B.e_off) + r;
   int i = 0;
-#pragma unroll 2
+  constexpr int kUnroll = Q <= 2 ? 4 : 2;   // independent loads in flight without spilling
+#pragma unroll kUnroll
   for (; i + 1 < N; i += 2) {
     const float4 e0 = __ldg(&Er[(long long)i * nr]);
     const float4 e1 = __ldg(&Er[(long long)(i + 1) * nr]);
@@ -1619,7 +1621,7 @@ __global__ void __launch_bounds__(kRestrMaxThreads) k_restrict(DevJob J) {
     return;
   }
   const int a0 = J.act_off[k], na = J.act_off[k + 1] - a0;
-  if (DF) {
+  if constexpr (DF) {
     // Mixed form: the same sums in double-float (spectra split once, compensated sums).
     float4* sh4 = reinterpret_cast<float4*>(shr);
     for (int e = threadIdx.x; e < Q * na; e += blockDim.x) {
@@ -1640,24 +1642,24 @@ __global__ void __launch_bounds__(kRestrMaxThreads) k_restrict(DevJob J) {
       const df vr = re.value(), vi = im.value();
       G[e] = make_double2((double)vr.hi + (double)vr.lo, (double)vi.hi + (double)vi.lo);
     }
-    return;
-  }
-  for (int e = threadIdx.x; e < Q * na; e += blockDim.x) {
-    int q = e / na, a = e % na;
-    shr[e] = J.Gt[((base + J.act_idx[a0 + a]) * Q + q) * L + l];
-  }
-  __syncthreads();
-  const double* RT = J.restr + off;
-  for (int e = threadIdx.x; e < Q * N; e += blockDim.x) {
-    int q = e / N, i = e % N;
-    double2 acc = make_double2(0.0, 0.0);
-    for (int a = 0; a < na; ++a) {
-      const double rv = RT[(long long)J.act_idx[a0 + a] * N + i];
-      const double2 gv = shr[q * na + a];
-      acc.x = fma(rv, gv.x, acc.x);
-      acc.y = fma(rv, gv.y, acc.y);
+  } else {
+    for (int e = threadIdx.x; e < Q * na; e += blockDim.x) {
+      int q = e / na, a = e % na;
+      shr[e] = J.Gt[((base + J.act_idx[a0 + a]) * Q + q) * L + l];
     }
-    G[e] = acc;
+    __syncthreads();
+    const double* RT = J.restr + off;
+    for (int e = threadIdx.x; e < Q * N; e += blockDim.x) {
+      int q = e / N, i = e % N;
+      double2 acc = make_double2(0.0, 0.0);
+      for (int a = 0; a < na; ++a) {
+        const double rv = RT[(long long)J.act_idx[a0 + a] * N + i];
+        const double2 gv = shr[q * na + a];
+        acc.x = fma(rv, gv.x, acc.x);
+        acc.y = fma(rv, gv.y, acc.y);
+      }
+      G[e] = acc;
+    }
   }
 }
 
