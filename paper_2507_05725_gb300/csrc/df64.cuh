@@ -122,6 +122,15 @@ __device__ __forceinline__ df df_add_fast(df a, df b) {
   return r;
 }
 
+// a / b: the FP32 quotient corrected once with the double-float remainder (error about 2^-46).
+__device__ __forceinline__ df df_div(df a, df b) {
+  const float q1 = __fdiv_rn(a.hi, b.hi);
+  const df r = df_sub(a, df_mul(b, df{q1, 0.f}));
+  df q;
+  quick_two_sum(q1, __fdiv_rn(r.hi, b.hi), q.hi, q.lo);
+  return q;
+}
+
 // Complex double-float (float4 layout) for the mixed-form FFT butterflies.
 __device__ __forceinline__ float4 dfc_mul(float4 a, float4 b) {
   const df re = df_dot2(df{a.x, a.y}, df{b.x, b.y}, df{-a.z, -a.w}, df{b.z, b.w});
@@ -163,6 +172,26 @@ __device__ __forceinline__ void df_sincos_taylor(df x, df& s, df& c) {
 #pragma unroll
   for (int k = 1; k < 10; ++k) pc = df_add(df_mul(pc, u), kc[k]);
   c = df_add(df{1.f, 0.f}, df_mul(u, pc));
+}
+
+// sin(pi D / den) for |D| < den < 2^24, den divisible by 4, in double-float: the fraction reduced in
+// integers to a = Da / den in [0, 1/4] (sin(pi (1 - t)) = sin(pi t), sin(pi t) = cos(pi (1/2 - t))),
+// the quotient formed exactly to double-float (FMA remainder), then the Taylor series at pi a.
+__device__ __forceinline__ df df_sinpi_frac(int D, int den) {
+  int a = D < 0 ? -D : D;
+  if (2 * a > den) a = den - a;
+  const bool use_cos = 4 * a > den;
+  if (use_cos) a = den / 2 - a;
+  const float fa = (float)a, fd = (float)den;
+  const float q0 = __fdiv_rn(fa, fd);
+  const float r = fmaf(-q0, fd, fa);
+  df q;
+  quick_two_sum(q0, __fdiv_rn(r, fd), q.hi, q.lo);
+  constexpr df kPi = df_const(3.14159265358979323846);
+  df s, c;
+  df_sincos_taylor(df_mul(kPi, q), s, c);
+  const df v = use_cos ? c : s;
+  return D < 0 ? df_neg(v) : v;
 }
 
 // Complex compensated multiply-accumulate: acc += a * b with a, b complex df64 (float4 layout).

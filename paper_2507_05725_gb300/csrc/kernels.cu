@@ -191,6 +191,28 @@ __global__ void k_restr(DevJob J) {
   }
   __syncthreads();
   const long long total = (long long)N * M;
+  if (J.mixed) {
+    // Mixed form: only the double-float table, computed on the FP32 pipe from the node tables
+    // (converted in place, 8 bytes either way) with the exact fraction D / (4NM) for the sine.
+    df* td = reinterpret_cast<df*>(shq);
+    for (int k = threadIdx.x; k < 3 * (N + M); k += blockDim.x) td[k] = df_from(shq[k]);
+    __syncthreads();
+    const df *cAd = td, *sad = cAd + N, *cad = sad + N, *sbd = cad + N, *sgd = sbd + M, *cgd = sgd + M;
+    const df m2d{(float)(2 * M), 0.f};
+    const int den = 4 * N * M;
+    float2* out = J.restr_df + J.restr_off[t];
+    for (long long e = threadIdx.x; e < total; e += blockDim.x) {
+      const int x = (int)(e / N), i = (int)(e % N);
+      const int D = (2 * i + 1) * M - (2 * x + 1) * N;
+      df v{1.f, 0.f};
+      if (D != 0) {
+        const df ssum = df_dot2(sad[i], cgd[x], cad[i], sgd[x]);
+        v = df_div(df_mul(sbd[x], cAd[i]), df_mul(df_mul(m2d, ssum), df_sinpi_frac(D, den)));
+      }
+      out[e] = make_float2(v.hi, v.lo);
+    }
+    return;
+  }
   const double nm4 = 4.0 * (double)N * (double)M, m2 = 2.0 * M;
   for (long long e = threadIdx.x; e < total; e += blockDim.x) {
     const int x = (int)(e / N), i = (int)(e % N);
@@ -201,10 +223,6 @@ __global__ void k_restr(DevJob J) {
       v = sb[x] * cA[i] / (m2 * ssum * sinpi((double)D / nm4));
     }
     RT[e] = v;
-    if (J.restr_df) {   // mixed form: the same table as double-float pairs
-      const float h = __double2float_rn(v);
-      J.restr_df[J.restr_off[t] + e] = make_float2(h, __double2float_rn(v - (double)h));
-    }
   }
 }
 
