@@ -1683,9 +1683,13 @@ __global__ void __launch_bounds__(kRestrMaxThreads) k_restrict(DevJob J) {
 
 // ---------------------------------------------------------------------------------------------
 // Output traces u_M(z, t) = sum_q [valid] (1/pi) Re sum_l w_l Vobs(z, q, l) e^{-i l h (t - s_q)}.
-__global__ void k_traces(DevJob J) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= J.n_obs * J.n_tout) return;
+constexpr int kTraceThreads = 128;
+
+// One block per (observation point, output time): the threads split the frequencies, then a
+// fixed-order tree sums their partial sums (deterministic).
+__global__ void __launch_bounds__(kTraceThreads) k_traces(DevJob J) {
+  __shared__ double part[kTraceThreads];
+  const int idx = blockIdx.x;
   const int z = idx / J.n_tout, it = idx % J.n_tout;
   const double t = J.tout[it];
   double acc = 0.0;
@@ -1694,13 +1698,19 @@ __global__ void k_traces(DevJob J) {
     if (!(rel >= -J.H && rel < J.period - J.H)) continue;
     const double c = J.h * (t - J.s_q[q]);
     const double2* V = J.Vobs + ((long long)z * J.Q + q) * J.L;
-    for (int l = 1; l < J.L; ++l) {
+    for (int l = 1 + threadIdx.x; l < J.L; l += kTraceThreads) {
       double sn, cs;
       sincos((double)l * c, &sn, &cs);
       acc = fma(J.wl[l], fma(V[l].x, cs, V[l].y * sn), acc);
     }
   }
-  J.traces[idx] = acc * kInvPi;
+  part[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = kTraceThreads / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) J.traces[idx] = part[0] * kInvPi;
 }
 
 inline int cdiv(long long a, int b) { return (int)((a + b - 1) / b); }
@@ -1929,7 +1939,7 @@ cudaError_t launch_cross_otf(const DevJob& J, cudaStream_t st, int* launches) {
 cudaError_t launch_traces(const DevJob& J, cudaStream_t st, int* launches) {
   int n = J.n_obs * J.n_tout;
   if (n == 0) return cudaSuccess;
-  k_traces<<<cdiv(n, 128), 128, 0, st>>>(J);
+  k_traces<<<n, kTraceThreads, 0, st>>>(J);
   *launches += 1;
   return cudaGetLastError();
 }
