@@ -312,8 +312,10 @@ def ours(args):
     ms, stages, st, dens64, traces_ok, clocks = time_form(0)
     value = job_value(ws, solves, ms)
 
-    def time_graph(precision):
+    def time_graph(precision, autotune=False):
         job = F.Job(ctx, problem, keep_densities=False, precision=precision)
+        if autotune:
+            F.fthms_autotune(job.req, 3)
         F.fthms_use_graph(job.req, True)
         for _ in range(args.warmup):
             job.run()
@@ -325,6 +327,7 @@ def ours(args):
             job.run()
         e1.record(stream)
         torch.cuda.synchronize()
+        time_graph.dens = [job.densities(j, 0, 0) for j in range(P)]
         job.release()
         return max_over_ranks(e0.elapsed_time(e1) / args.steps)
 
@@ -355,6 +358,18 @@ def ours(args):
                  "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages_t.items()}}
         if same and ok_t and ms_t < ms_mx:
             ms_mx, stages_mx, st_mx, clocks_mx = ms_t, stages_t, st_t, clocks_t
+    # The tuned mixed form replayed as one captured CUDA graph per job (no launch gaps): the headline when
+    # faster and bitwise equal; its stage times and roofline come from the same kernels launched directly.
+    graph_mx = None
+    graph_used = False
+    if not args.plain_only:
+        ms_g = time_graph(1, autotune=True)
+        same_g = all(np.array_equal(a[l], c[l]) for a, c in zip(dens_mx, time_graph.dens) for l in a)
+        graph_mx = {"value": job_value(ws, solves, ms_g), "ms_per_step": ms_g, "bitwise_equal_to_direct": bool(same_g),
+                    "note": "tuned mixed job replayed as one captured CUDA graph"}
+        if same_g and ms_g < ms_mx:
+            ms_mx = ms_g
+            graph_used = True
 
     # Headline: the mixed form when its densities agree with the FP64 form within 1e-10 (the metric's
     # bar), else the plain FP64 form.
@@ -448,7 +463,8 @@ def ours(args):
                 "config": {"workload": "4obstacles-planewave: 8 arcs, N 48..259, L=1025 on [0,60], M=12, Q=1 "
                                        "(one whole job per step)",
                            "solves_per_step": solves, "systems_per_step": P * (L - 1),
-                           "form": "mixed (verified <= 1e-10 vs FP64 in-run)" if use_mixed else "plain FP64",
+                           "form": ("mixed" + (", CUDA-graph replay" if graph_used else "") +
+                                    " (verified <= 1e-10 vs FP64 in-run)") if use_mixed else "plain FP64",
                            "l2": "working set > L2 (cross matrices "
                            f"{st['cross_entries'] * 16 / 1e9:.1f} GB, factors {st['lu_flops'] > 0})",
                            "parallelism": f"replicas x{ws}"},
@@ -468,6 +484,7 @@ def ours(args):
                         "value": job_value(ws, solves, ms_graph), "ms_per_step": ms_graph,
                         "note": "whole job replayed as one captured CUDA graph"},
                     "mixed_autotuned": tuned,
+                    "mixed_autotuned_graph": graph_mx,
                     "mixed": {"value": job_value(ws, solves, ms_mx), "ms_per_step": ms_mx,
                               "dtype": "f32 factors + double-float (2 x f32) refinement and cross apply, f64 elsewhere",
                               "rel_l2_vs_fp64_densities": mixed_err,

@@ -254,11 +254,12 @@ def test_mixed_matches_plain_at_full_size(F, ctx):
     assert math.sqrt(num / den) < MIXED_TOL
 
 
-def test_graph_replay_matches_direct_launches(F, ctx):
-    """A job captured into a CUDA graph and replayed gives the same densities and traces."""
+@pytest.mark.parametrize("precision", [0, 1])
+def test_graph_replay_matches_direct_launches(F, ctx, precision):
+    """A job captured into a CUDA graph and replayed gives the same densities and traces (both forms)."""
     problem = wl.random_small(5, n_curves=2, n_arcs_per_curve=2, Q=2, L=65, M=2)
-    a = F.Job(ctx, problem).run().wait()
-    b = F.Job(ctx, problem)
+    a = F.Job(ctx, problem, precision=precision).run().wait()
+    b = F.Job(ctx, problem, precision=precision)
     try:
         F.fthms_use_graph(b.req, True)
         b.run().wait()
