@@ -499,10 +499,7 @@ __global__ void __launch_bounds__(kLuThreads) k_lu(DevJob J) {
   int* piv = J.piv + s.piv_off;
   C* Pn = shl;                       // [N][kPS] panel rows
   C* U = shl + (size_t)N * kPS;      // [kNB][N] U12 rows
-  __shared__ Real red_v[kLuThreads / 32];
-  __shared__ int red_i[kLuThreads / 32];
   __shared__ int spiv[kNB];
-  __shared__ int s_p;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   for (int k0 = 0; k0 < N; k0 += kNB) {
     const int w = min(kNB, N - k0);
@@ -512,47 +509,43 @@ __global__ void __launch_bounds__(kLuThreads) k_lu(DevJob J) {
       Pn[r * kPS + c] = A[(long long)(k0 + c) * N + k0 + r];
     }
     __syncthreads();
-    for (int c = 0; c < w; ++c) {
-      Real best = -1;
-      int bi = 0x7fffffff;
-      for (int r = c + tid; r < nr; r += kLuThreads) {
-        C v = Pn[r * kPS + c];
-        Real m = fabs(v.x) + fabs(v.y);
-        if (m > best) { best = m; bi = r; }
+    // The panel's columns by one warp (warp barriers only): the pivot is the largest |re| + |im| with
+    // the lowest row among ties, then the row swap inside the panel and the rank-1 update.
+    if (wid == 0) {
+      for (int c = 0; c < w; ++c) {
+        Real best = -1;
+        int bi = 0x7fffffff;
+        for (int r = c + lane; r < nr; r += 32) {
+          C v = Pn[r * kPS + c];
+          Real m = fabs(v.x) + fabs(v.y);
+          if (m > best) { best = m; bi = r; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          Real ov = __shfl_xor_sync(0xffffffffu, best, o);
+          int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+          if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+        }
+        const int p = bi == 0x7fffffff ? c : bi;
+        if (lane == 0) {
+          spiv[c] = p;
+          piv[k0 + c] = k0 + p;
+        }
+        if (p != c && lane < w) {
+          C t = Pn[c * kPS + lane];
+          Pn[c * kPS + lane] = Pn[p * kPS + lane];
+          Pn[p * kPS + lane] = t;
+        }
+        __syncwarp();
+        const C inv = crecip(Pn[c * kPS + c]);
+        for (int r = c + 1 + lane; r < nr; r += 32) {
+          C lr = cmul(Pn[r * kPS + c], inv);
+          Pn[r * kPS + c] = lr;
+          for (int cc = c + 1; cc < w; ++cc) Pn[r * kPS + cc] = cfms(lr, Pn[c * kPS + cc], Pn[r * kPS + cc]);
+        }
+        __syncwarp();
       }
-      for (int o = 16; o > 0; o >>= 1) {
-        Real ov = __shfl_down_sync(0xffffffffu, best, o);
-        int oi = __shfl_down_sync(0xffffffffu, bi, o);
-        if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-      }
-      if (lane == 0) { red_v[wid] = best; red_i[wid] = bi; }
-      __syncthreads();
-      if (tid == 0) {
-        Real b = red_v[0];
-        int ii = red_i[0];
-        for (int q = 1; q < kLuThreads / 32; ++q)
-          if (red_v[q] > b || (red_v[q] == b && red_i[q] < ii)) { b = red_v[q]; ii = red_i[q]; }
-        if (ii == 0x7fffffff) ii = c;
-        s_p = ii;
-        spiv[c] = ii;
-        piv[k0 + c] = k0 + ii;
-      }
-      __syncthreads();
-      const int p = s_p;
-      if (p != c && tid < w) {
-        C t = Pn[c * kPS + tid];
-        Pn[c * kPS + tid] = Pn[p * kPS + tid];
-        Pn[p * kPS + tid] = t;
-      }
-      __syncthreads();
-      const C inv = crecip(Pn[c * kPS + c]);
-      for (int r = c + 1 + tid; r < nr; r += kLuThreads) {
-        C lr = cmul(Pn[r * kPS + c], inv);
-        Pn[r * kPS + c] = lr;
-        for (int cc = c + 1; cc < w; ++cc) Pn[r * kPS + cc] = cfms(lr, Pn[c * kPS + cc], Pn[r * kPS + cc]);
-      }
-      __syncthreads();
     }
+    __syncthreads();
     for (int idx = tid; idx < nr * w; idx += kLuThreads) {
       int c = idx / nr, r = idx % nr;
       A[(long long)(k0 + c) * N + k0 + r] = Pn[r * kPS + c];
