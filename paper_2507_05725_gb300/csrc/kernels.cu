@@ -437,8 +437,8 @@ __global__ void __launch_bounds__(256) k_assemble_self(DevJob J) {
       reinterpret_cast<float4*>(J.A)[mo + e2] = d;
       J.LU32[mo + e1] = f;
       J.LU32[mo + e2] = f;
-      const df cn = df_sub(df_mul(cx_d, cu_d), df_mul(sx_d, su_d));
-      sx_d = df_add(df_mul(sx_d, cu_d), df_mul(cx_d, su_d));
+      const df cn = df_dot2(cx_d, cu_d, df_neg(sx_d), su_d);   // rotation by e^{i h R}
+      sx_d = df_dot2(sx_d, cu_d, cx_d, su_d);
       cx_d = cn;
       ++since_d;
     }
@@ -1030,8 +1030,8 @@ __global__ void __launch_bounds__(kAsmMaxThreads) k_cross_assemble(DevJob J) {
         const df re = df_mul(a, df_dot2(beta_d, t1, df{-1.f, 0.f}, t2));
         const df im = df_mul(a, t1);
         *reinterpret_cast<float4*>(Ep + eo[l]) = make_float4(re.hi, re.lo, im.hi, im.lo);
-        const df cn = df_sub(df_mul(cx_d, cu_d), df_mul(sx_d, su_d));
-        sx_d = df_add(df_mul(sx_d, cu_d), df_mul(cx_d, su_d));
+        const df cn = df_dot2(cx_d, cu_d, df_neg(sx_d), su_d);   // rotation by e^{i h R}
+        sx_d = df_dot2(sx_d, cu_d, cx_d, su_d);
         cx_d = cn;
         ++since_d;
       }
