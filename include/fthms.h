@@ -92,9 +92,11 @@ typedef struct {
  *  precision : 0 = FP64 throughout.  1 = mixed form: FP32 LU factors; solutions refined against the
  *              matrix kept as double-float (two floats, ~48 bits) until the relative error estimated
  *              to remain (last correction x estimated contraction factor) is below 1e-12, at most 3
- *              steps; the far-field cross entries evaluated, stored and applied
- *              in double-float on the FP32 pipe; self matrices, phase seeds, log-singular corrections,
- *              transforms and restriction stay FP64.  Densities agree with the FP64 form to ~1e-12.
+ *              steps; self and cross entries (Taylor range and far-field recurrence), the FFT
+ *              butterflies of the time transforms, the restriction and the cross apply in double-float
+ *              on the FP32 pipe; diagonal self entries, per-pair setup, phase-seed reduction,
+ *              log-singular corrections, transform folds and phase factors stay FP64.  Densities agree
+ *              with the FP64 form to 4e-12 (4 obstacles, N <= 259) and 2e-11 (12-arc cavity, N <= 760).
  *              Others -> ENOTIMPL.
  *  keep_densities : 1 keeps phi_{j,m,q}(omega_l) of every step for fthms_densities; 0 keeps only
  *              the sum over m.
