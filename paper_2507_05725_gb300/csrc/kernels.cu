@@ -1251,9 +1251,28 @@ __global__ void __launch_bounds__(kResidThreads) k_mresid(DevJob J) {
     re[q].add(gd.x, gd.y);
     im[q].add(gd.z, gd.w);
   }
+  int j0 = 0;
+  if (Q == 1) {
+    // 16 matrix entries of the row loaded before their sums; the 16 densities (the same for the whole
+    // warp) loaded once by 16 lanes and handed round by shuffles.  Same order of sums as below.
+    constexpr int kB = 16;
+    const int lane = threadIdx.x & 31;
+    for (; j0 + kB <= N; j0 += kB) {
+      float4 a[kB];
+#pragma unroll
+      for (int k = 0; k < kB; ++k) a[k] = __ldg(&Adf[(long long)(j0 + k) * N + row]);
+      const float4 pv = ph[j0 + (lane & (kB - 1))];
+#pragma unroll
+      for (int k = 0; k < kB; ++k) {
+        const float4 x = make_float4(__shfl_sync(0xffffffffu, pv.x, k), __shfl_sync(0xffffffffu, pv.y, k),
+                                     __shfl_sync(0xffffffffu, pv.z, k), __shfl_sync(0xffffffffu, pv.w, k));
+        cdf_mac(re[0], im[0], make_float4(-a[k].x, -a[k].y, -a[k].z, -a[k].w), x);
+      }
+    }
+  }
   constexpr int kUnroll = Q == 1 ? 8 : Q == 2 ? 4 : 2;   // loads in flight without spilling
 #pragma unroll kUnroll
-  for (int j = 0; j < N; ++j) {
+  for (int j = j0; j < N; ++j) {
     const float4 a = __ldg(&Adf[(long long)j * N + row]);
     const float4 na = make_float4(-a.x, -a.y, -a.z, -a.w);
 #pragma unroll
