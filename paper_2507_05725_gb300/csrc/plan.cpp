@@ -2,9 +2,11 @@
 #include "plan.h"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <map>
+#include <thread>
 
 namespace fthms {
 
@@ -302,24 +304,35 @@ int build_plan(const fthms_curve* curves, int ncurves, const fthms_arc* arcs, in
       }
   }
 
-  // Node panels (arc, N): t_i, x(t_i), |x'(t_i)|.
+  // Node panels (arc, N): t_i, x(t_i), |x'(t_i)|.  Panels met by the systems loop are only registered
+  // there and filled afterwards on several threads (each panel independently, the same arithmetic).
   p.panel_index.assign((size_t)p.P * (p.maxN + 1), -1);
   long long noff = 0;
-  auto get_panel = [&](int j, int N) {
+  std::vector<int> deferred;
+  auto fill_panel = [&](int idx) {
+    const Panel pn = p.panels[idx];
+    for (int i = 0; i < pn.N; ++i) {
+      const double t = std::cos((2.0 * i + 1.0) * kPi / (2.0 * pn.N));
+      double x, y, sp;
+      arc_point(p, pn.arc, t, x, y, sp);
+      p.node_t[pn.off + i] = t;
+      p.node_x[pn.off + i] = x;
+      p.node_y[pn.off + i] = y;
+      p.node_sp[pn.off + i] = sp;
+    }
+  };
+  auto get_panel = [&](int j, int N, bool defer = false) {
     int& idx = p.panel_index[(size_t)j * (p.maxN + 1) + N];
     if (idx >= 0) return idx;
     idx = (int)p.panels.size();
     p.panels.push_back(Panel{j, N, noff});
-    for (int i = 0; i < N; ++i) {
-      double t = std::cos((2.0 * i + 1.0) * kPi / (2.0 * N));
-      double x, y, sp;
-      arc_point(p, j, t, x, y, sp);
-      p.node_t.push_back(t);
-      p.node_x.push_back(x);
-      p.node_y.push_back(y);
-      p.node_sp.push_back(sp);
-    }
     noff += N;
+    p.node_t.resize(noff);
+    p.node_x.resize(noff);
+    p.node_y.resize(noff);
+    p.node_sp.resize(noff);
+    if (defer) deferred.push_back(idx);
+    else fill_panel(idx);
     return idx;
   };
 
@@ -333,7 +346,7 @@ int build_plan(const fthms_curve* curves, int ncurves, const fthms_arc* arcs, in
       s.arc = j;
       s.l = l;
       s.N = N;
-      s.panel = get_panel(j, N);
+      s.panel = get_panel(j, N, true);
       s.mat_off = p.mat_total;
       s.vec_off = p.vec_total;
       s.piv_off = p.piv_total;
@@ -344,6 +357,22 @@ int build_plan(const fthms_curve* curves, int ncurves, const fthms_arc* arcs, in
       rlog_map[N] = 0;
       p.hankel_self += 0.5 * N * (N + 1.0);
     }
+  {
+    const int nthr = std::max(1, std::min(16, (int)std::thread::hardware_concurrency()));
+    std::atomic<int> next{0};
+    auto work = [&] {
+      for (int k = next.fetch_add(1); k < (int)deferred.size(); k = next.fetch_add(1)) fill_panel(deferred[k]);
+    };
+    std::vector<std::thread> pool;
+    if (nthr > 1 && deferred.size() >= 64) {
+      try {
+        for (int t = 1; t < nthr; ++t) pool.emplace_back(work);
+      } catch (...) {   // no threads available: the calling thread fills the rest
+      }
+    }
+    work();
+    for (auto& t : pool) t.join();
+  }
   // Self-assembly tiles over bands of consecutive frequencies with the same N.
   for (int j = 0; j < p.P; ++j) {
     int l = 1;
@@ -437,12 +466,16 @@ int build_plan(const fthms_curve* curves, int ncurves, const fthms_arc* arcs, in
     }
   }
   p.hankel_cross = (double)p.e_total;
+  // Pairs with rows, per receiver, in pair order (the block order of every group).
+  std::vector<std::vector<int>> pairs_of(p.P + 1);
+  for (int pi = 0; pi < npairs; ++pi)
+    if (p.pairs[pi].nrows > 0) pairs_of[p.pairs[pi].k].push_back(pi);
+  p.blks.reserve((size_t)npairs * (p.L - 1));
   for (int l = 1; l < p.L; ++l)
     for (int k = 0; k <= p.P; ++k) {
       CrossGrp g{l, k, (int)p.blks.size(), 0};
-      for (int pi = 0; pi < npairs; ++pi) {
+      for (int pi : pairs_of[k]) {
         const PairDesc& pd = p.pairs[pi];
-        if (pd.k != k || pd.nrows == 0) continue;
         int N = p.Ntab[(size_t)pd.j * p.L + l];
         CrossBlk b{pd.j, pd.j * (p.L - 1) + (l - 1), N, pd.nrows, pd.tgt_off, 0, p.e_off[(size_t)pi * p.L + l]};
         p.blks.push_back(b);
@@ -483,14 +516,28 @@ int build_plan(const fthms_curve* curves, int ncurves, const fthms_arc* arcs, in
     }
   }
   const int kRowChunk = 8;
+  // Assembly tasks: (pair, band of up to 64 equal-N frequencies, kRowChunk target rows); counted first so
+  // that the list is filled without reallocation.
+  auto band_end = [&](int j, int l) {
+    const int N = p.Ntab[(size_t)j * p.L + l];
+    int l1 = l;
+    while (l1 + 1 < p.L && p.Ntab[(size_t)j * p.L + l1 + 1] == N && l1 + 1 - l < 64) ++l1;
+    return l1;
+  };
+  size_t n_asm = 0;
+  for (int pi = 0; pi < npairs; ++pi) {
+    const PairDesc& pd = p.pairs[pi];
+    if (pd.nrows == 0) continue;
+    for (int l = 1; l < p.L; l = band_end(pd.j, l) + 1) n_asm += (pd.nrows + kRowChunk - 1) / kRowChunk;
+  }
+  p.asms.reserve(n_asm);
   for (int pi = 0; pi < npairs; ++pi) {
     const PairDesc& pd = p.pairs[pi];
     if (pd.nrows == 0) continue;
     int l = 1;
     while (l < p.L) {
       int N = p.Ntab[(size_t)pd.j * p.L + l];
-      int l1 = l;
-      while (l1 + 1 < p.L && p.Ntab[(size_t)pd.j * p.L + l1 + 1] == N && l1 + 1 - l < 64) ++l1;
+      int l1 = band_end(pd.j, l);
       int panel = get_panel(pd.j, N);
       for (int r0 = 0; r0 < pd.nrows; r0 += kRowChunk)
         p.asms.push_back(CrossAsm{pi, l, l1, N, r0, std::min(kRowChunk, pd.nrows - r0), panel, 0});
@@ -503,11 +550,9 @@ int build_plan(const fthms_curve* curves, int ncurves, const fthms_arc* arcs, in
     for (size_t gi = 0; gi < p.grps.size(); ++gi) {
       const CrossGrp& g = p.grps[gi];
       long long r = p.grp_res_off[gi];
-      for (int pi = 0; pi < npairs; ++pi) {
-        const PairDesc& pd = p.pairs[pi];
-        if (pd.k != g.k || pd.nrows == 0) continue;
+      for (int pi : pairs_of[g.k]) {
         p.otf_res_off[(size_t)pi * p.L + g.l] = r;
-        r += pd.nrows;
+        r += p.pairs[pi].nrows;
       }
     }
     // Near weights once per job (they depend on the target and N only); tasks of at most
