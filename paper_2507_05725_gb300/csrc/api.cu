@@ -51,6 +51,16 @@ fthms_status ensure_device(int dev) {
   std::lock_guard<std::mutex> lk(g_init_mu);
   if (dev >= 0 && dev < 64 && !g_init_done[dev]) {
     CK(init_constants());
+    // Job memory comes from the device's stream-ordered pool (cudaMallocAsync); keep what released
+    // jobs free there for the next job instead of returning it to the driver at every synchronisation
+    // (a per-process pool attribute; the HBM budget still admits jobs by its own accounting).
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      unsigned long long keep = ~0ULL;   // the attribute is a 64-bit unsigned byte count
+      if (cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess) cudaGetLastError();
+    } else {
+      cudaGetLastError();
+    }
     g_init_done[dev] = true;
   }
   return FTHMS_OK;
