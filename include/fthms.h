@@ -145,7 +145,10 @@ typedef struct {
 /* Create a context on CUDA device `device` that enqueues all work on `cuda_stream` (a
  * cudaStream_t; NULL = a non-blocking stream that the context creates, owns and destroys).
  * hbm_budget_bytes caps the device memory of all live jobs (0 = no cap).  Returns FTHMS_ECUDA if
- * the device cannot be used. */
+ * the device cannot be used.  Job memory comes from the device's default stream-ordered memory
+ * pool (cudaMallocAsync); the first use of a device in the process raises that pool's release
+ * threshold, so memory freed by released jobs stays in the pool for later jobs of the process
+ * (cudaMemPoolTrimTo on the default pool returns it to the driver). */
 fthms_status fthms_create(fthms_ctx** out, int device, size_t hbm_budget_bytes, void* cuda_stream);
 /* Destroy a context.  Jobs of the context that were not released are waited for and their device
  * memory is freed; their handles then accept fthms_release only (every other call returns
