@@ -274,7 +274,7 @@ fthms_status upload_job(fthms_req* r) {
   J.mrel = nullptr;
   J.rchunks = nullptr;
   J.n_rchunks = 0;
-  TRY(dev_alloc(r, 2, &J.refine_resid));          // [0] max last correction, [1] refinement passes (u64)
+  TRY(dev_alloc(r, 2, &J.refine_resid));          // [0] max estimated error left, [1] refinement passes (u64)
   if (J.mixed) {
     TRY(dev_alloc(r, (size_t)p.mat_total, &J.LU32));
     TRY(dev_alloc(r, (size_t)p.piv_total, &J.dinv32));

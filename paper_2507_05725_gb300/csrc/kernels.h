@@ -65,7 +65,7 @@ struct DevJob {
   double2* A;                // LU factors (mixed form: the matrix itself, as double-float)
   float2* LU32;              // FP32 factors (mixed form)
   float2* dinv32;            // FP32 1 / U_kk (mixed form)
-  double* refine_resid;      // max over systems of the last relative correction (mixed form)
+  double* refine_resid;      // max over systems of the estimated error left, and the passes (mixed form)
   float2* rres;              // FP32-rounded refinement residuals, laid out like G (mixed form)
   int* mdone;                // per system: 1 once its refinement has finished this step (mixed form)
   float* mrel;               // per system: relative size of its last correction (mixed form)
