@@ -457,7 +457,8 @@ def ours(args):
         line = {"metric": METRIC, "value": head_value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": head_ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None,
-                "dtype": ("f64 assembly/transforms + f32 factors + double-float (2 x f32) refinement and cross apply"
+                "dtype": ("f32 factors + double-float (2 x f32) assembly, refinement, FFT butterflies, restriction and cross "
+                          "apply; f64 per-pair setup, diagonal, transform folds and outputs"
                           if use_mixed else "f64"),
                 "data": "synthetic",
                 "config": {"workload": "4obstacles-planewave: 8 arcs, N 48..259, L=1025 on [0,60], M=12, Q=1 "
@@ -486,7 +487,7 @@ def ours(args):
                     "mixed_autotuned": tuned,
                     "mixed_autotuned_graph": graph_mx,
                     "mixed": {"value": job_value(ws, solves, ms_mx), "ms_per_step": ms_mx,
-                              "dtype": "f32 factors + double-float (2 x f32) refinement and cross apply, f64 elsewhere",
+                              "dtype": "f32 factors + double-float (2 x f32) assembly, refinement, FFT butterflies, restriction and cross apply; f64 setup, folds, outputs",
                               "rel_l2_vs_fp64_densities": mixed_err,
                               "max_refine_resid": st_mx["max_refine_resid"],
                               "refine_passes_per_solve": st_mx.get("refine_passes"), "traces_finite": ok_mx,
