@@ -163,6 +163,15 @@ fthms_status fthms_prepare(fthms_ctx* ctx, const fthms_curve* curves, int ncurve
                            const fthms_arc* arcs, int narcs, const fthms_signal* signal,
                            const fthms_options* options, fthms_req** out);
 
+/* Plan a job on the host only: the same validation as fthms_prepare (same status codes and
+ * messages), without a device, allocation or upload.  *device_bytes receives the device memory the job
+ * would hold (what fthms_prepare charges against a context budget) and *n_systems its number of
+ * (arc, omega) systems; either pointer may be NULL.  For capacity planning (no counterpart in the
+ * paper). */
+fthms_status fthms_plan_info(const fthms_curve* curves, int ncurves, const fthms_arc* arcs, int narcs,
+                             const fthms_signal* signal, const fthms_options* options,
+                             size_t* device_bytes, int* n_systems);
+
 /* Enqueue the whole hot path of a prepared job on the context stream (asynchronous): assembly,
  * factorisation, m = 1 data, M multiple-scattering steps, output traces.  May be called again
  * (recomputes everything from the uploaded tables). */

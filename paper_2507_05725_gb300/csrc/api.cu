@@ -487,6 +487,18 @@ fthms_status fthms_destroy(fthms_ctx* ctx) {
   return FTHMS_OK;
 }
 
+fthms_status fthms_plan_info(const fthms_curve* curves, int ncurves, const fthms_arc* arcs, int narcs,
+                             const fthms_signal* signal, const fthms_options* options, size_t* device_bytes,
+                             int* n_systems) {
+  fthms::Plan plan;
+  std::string err;
+  const int st = build_plan(curves, ncurves, arcs, narcs, signal, options, plan, err);
+  if (st != FTHMS_OK) return fail((fthms_status)st, "fthms_prepare: " + err);
+  if (device_bytes) *device_bytes = plan.device_bytes;
+  if (n_systems) *n_systems = (int)plan.sys.size();
+  return FTHMS_OK;
+}
+
 fthms_status fthms_prepare(fthms_ctx* ctx, const fthms_curve* curves, int ncurves, const fthms_arc* arcs,
                            int narcs, const fthms_signal* signal, const fthms_options* options,
                            fthms_req** out) {

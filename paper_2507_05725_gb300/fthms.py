@@ -116,7 +116,7 @@ EXPORTED = ["fthms_create", "fthms_destroy", "fthms_prepare", "fthms_run", "fthm
             "fthms_profile", "fthms_stage_times", "fthms_assemble_self_noalloc", "fthms_server_create",
             "fthms_server_submit", "fthms_server_poll", "fthms_server_wait", "fthms_server_result",
             "fthms_server_latency", "fthms_server_release", "fthms_server_destroy", "fthms_use_graph",
-            "fthms_autotune"]
+            "fthms_autotune", "fthms_plan_info"]
 
 
 def _check(status):
@@ -169,6 +169,14 @@ def fthms_prepare(ctx, m: Marshalled):
     _check(LIB.fthms_prepare(ctx, m.curves, m.ncurves, m.arcs, m.narcs, C.byref(m.signal), C.byref(m.options),
                              C.byref(req)))
     return req
+
+
+def fthms_plan_info(m: Marshalled):
+    """(device bytes, number of systems) of a job, planned on the host only (no GPU needed)."""
+    nbytes, nsys = C.c_size_t(), C.c_int()
+    _check(LIB.fthms_plan_info(m.curves, m.ncurves, m.arcs, m.narcs, C.byref(m.signal), C.byref(m.options),
+                               C.byref(nbytes), C.byref(nsys)))
+    return nbytes.value, nsys.value
 
 
 def fthms_run(req):

@@ -1,0 +1,66 @@
+"""Host-only planning through the C ABI (fthms_plan_info): the validation of fthms_prepare and the job's
+device-memory accounting, without a GPU."""
+import copy
+import math
+
+import pytest
+
+import workloads as wl
+
+
+@pytest.fixture(scope="module")
+def F():
+    from paper_2507_05725_gb300 import fthms
+    return fthms
+
+
+def _status(F, problem, **kw):
+    with pytest.raises(F.FthmsError) as e:
+        F.fthms_plan_info(F.Marshalled(problem, **kw))
+    return e.value.status, str(e.value)
+
+
+def test_config_sizes_and_determinism(F):
+    """Config 2 has 8 arcs x 1024 solved frequencies; the same input plans to the same footprint."""
+    m = F.Marshalled(wl.config2(), keep_densities=False, precision=1)
+    b1, n1 = F.fthms_plan_info(m)
+    b2, n2 = F.fthms_plan_info(m)
+    assert n1 == n2 == 8 * 1024
+    assert b1 == b2 and 5e9 < b1 < 2e10
+
+
+def test_memory_accounting_follows_the_options(F):
+    """Mixed precision adds the FP32 factors; every-step cross rows drop the stored cross matrices;
+    keeping every step's densities adds M copies of them."""
+    p = wl.config2_reduced()
+    base, nsys = F.fthms_plan_info(F.Marshalled(p, keep_densities=False, precision=0))
+    mixed, _ = F.fthms_plan_info(F.Marshalled(p, keep_densities=False, precision=1))
+    kept, _ = F.fthms_plan_info(F.Marshalled(p, keep_densities=True, precision=0))
+    q = copy.deepcopy(p)
+    q["options"]["cross_mode"] = 1
+    otf, _ = F.fthms_plan_info(F.Marshalled(q, keep_densities=False, precision=0))
+    assert nsys == len(p["arcs"]) * (p["options"]["L"] - 1)
+    assert mixed > base and kept > base and otf < base
+
+
+def test_validation_without_a_gpu(F):
+    p = wl.random_small(0)
+    bad = copy.deepcopy(p)                          # arcs that do not overlap their neighbours
+    bad["arcs"] = [(0, 2 * math.pi * k / 3, 2 * math.pi * k / 3 + 1.0) for k in range(3)]
+    assert _status(F, bad)[0] == F.FTHMS_EINVAL
+    bad = copy.deepcopy(p)                          # window wider than the frequency grid's period
+    bad["options"]["H"] = 1e3
+    st, msg = _status(F, bad)
+    assert st == F.FTHMS_EINVAL and "period" in msg
+    bad = copy.deepcopy(p)
+    bad["options"]["n_period"] = 1000               # not a power of two
+    assert _status(F, bad)[0] == F.FTHMS_EINVAL
+    bad = copy.deepcopy(p)                          # period and time grid too long for the time kernels
+    bad["options"]["n_period"] = 16384
+    bad["options"]["Q"] = 4
+    st, msg = _status(F, bad)
+    assert st == F.FTHMS_EINVAL and "shared memory" in msg
+    bad = copy.deepcopy(p)                          # unknown cross mode
+    bad["options"]["cross_mode"] = 2
+    assert _status(F, bad)[0] == F.FTHMS_EINVAL
+    assert _status(F, p, precision=2)[0] == F.FTHMS_ENOTIMPL
