@@ -48,3 +48,21 @@ def test_host_validation_without_gpu():
     assert F.LIB.fthms_wait(None, 0) == F.FTHMS_EINVAL
     d = C.c_int()
     assert F.LIB.fthms_poll(None, C.byref(d)) == F.FTHMS_EINVAL
+
+
+def test_header_is_plain_c(tmp_path):
+    """The boundary is a C ABI: include/fthms.h compiles as C11 on its own (no C++ or CUDA types), and a C
+    program that calls every declared entry point links against the library."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use_abi.c"
+    calls = "\n".join(f"  (void)&{n};" for n in declared_symbols())
+    src.write_text('#include "fthms.h"\nint main(void) {\n' + calls + "\n  return 0;\n}\n")
+    lib_dir = os.path.join(ROOT, "paper_2507_05725_gb300", "lib")
+    r = subprocess.run([cc, "-std=c11", "-Wall", "-Werror", "-pedantic", "-I", os.path.join(ROOT, "include"),
+                        str(src), "-L", lib_dir, "-lfthms", "-o", str(tmp_path / "use_abi")],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
