@@ -34,7 +34,8 @@ typedef enum {
   FTHMS_OK = 0,
   FTHMS_EINVAL = 1,   /* invalid argument, geometry or option (nothing was enqueued) */
   FTHMS_ENOMEM = 2,   /* the job does not fit the context's HBM budget or device memory */
-  FTHMS_ENOCONV = 3,  /* reserved: iterative refinement did not reach its tolerance */
+  FTHMS_ENOCONV = 3,  /* fthms_wait: the job finished, but the iterative refinement of some (arc, omega)
+                         systems (mixed forms) did not reach refine_tol within refine_max passes */
   FTHMS_ETIMEOUT = 4, /* fthms_wait: the job did not finish within the timeout */
   FTHMS_ECUDA = 5,    /* a CUDA runtime call failed; the message names it */
   FTHMS_EBUSY = 6,    /* results requested before the job finished */
@@ -63,24 +64,39 @@ typedef struct {
   double theta_a, theta_b;
 } fthms_arc;
 
-/* Incident field u^i(x, t) (Section 5's incident-field families, restricted to real signals):
- * kind 0 = point source at z0: u = (1/(2 pi)) int_0^inf f(t - |x - z0| cosh v) dv,
- * kind 1 = plane wave along unit vector dir: u = f(t - x.dir),
- * f(t) = amp sin(carrier t) exp(-((t - centre)/width)^2).  Boundary data g_{j,1} = sign chi_j u^i
- * (eq. criterion_int1 has sign = -1). */
+/* Incident field u^i(x, t) of a real time signal f (Section 2's boundary data; Section 5's incident-field
+ * families): kind 0 = point source at z0: u = (1/(2 pi)) int_0^inf f(t - |x - z0| cosh v) dv (the 2-D
+ * retarded field, evaluated by the trapezoid rule in v), kind 1 = plane wave along unit vector dir:
+ * u = f(t - x.dir).  Boundary data g_{j,1} = sign chi_j u^i (eq. criterion_int1 has sign = -1).
+ * The signal is either
+ *  - analytic (n_t = 0): f(t) = amp sin(carrier t) exp(-((t - centre)/width)^2), width > 0; or
+ *  - sampled (n_t >= 8): f[i] = f(t0 + i dt), i = 0..n_t-1 (host array, copied at prepare), dt > 0.
+ *    Between the samples f is the degree-7 Lagrange interpolant through the 8 samples whose indices
+ *    are floor(s) - 3 .. floor(s) + 4, s = (t - t0)/dt (indices outside 0..n_t-1 count as zero
+ *    samples), and f = 0 outside [t0, t0 + (n_t - 1) dt].  band > 0 is the highest angular frequency
+ *    that the signal carries (it sets the point-source rule's step, as carrier + 8/width does for the
+ *    analytic signal); amp, carrier, centre and width are ignored.
+ * The point-source rule integrates over the v-range where f(t - |x - z0| cosh v) can be nonzero (the
+ * analytic signal: |tau - (t - centre)| <= 8 width; the sampled one: its sample range) with
+ * n = ceil((v_hi - v_lo)(1.25 rate + 24)/pi) + 16 intervals, rate = B |x - z0| sinh(v_hi) + 1,
+ * B = |carrier| + 8/width or band. */
 typedef struct {
   int kind;
   double z0[2];
   double dir[2];
   double sign;
   double amp, carrier, centre, width;
+  int n_t;            /* 0: analytic signal; >= 8: sampled signal */
+  double t0, dt;
+  const double* f;
+  double band;
 } fthms_signal;
 
 /* Discretisation and output options.
  *  W, L      : frequencies omega_l = l*(W/(L-1)), l = 0..L-1; l = 1..L-1 are solved.
  *  N rule    : nodes per arc N_j(omega) = N_fixed if > 0, else max(N_min, ceil(N_ppw*omega*len_j)
- *              + N_off), len_j the arc length; every N_j(omega) must lie in [2, 800].  The transfer mesh of arc j is its first-kind
- *              Chebyshev grid of size N_j(omega_{L-1}).
+ *              + N_off), len_j the arc length; every N_j(omega) must lie in [2, 800].  The transfer
+ *              mesh of arc j is its first-kind Chebyshev grid of size N_j(omega_{L-1}).
  *  M         : multiple-scattering steps (Algorithm 1's outer loop).
  *  Q, H      : 1 <= Q <= 4 time windows sqcap_q(t) = sqcap(t - s_q), s_q = 1.5 (q-1) H (Section 5).
  *  n_period  : internal time samples per period 2 pi/h of the frequency grid (power of two,
@@ -91,20 +107,32 @@ typedef struct {
  *  n_tout, tout0, dtout : output times tout0 + k dtout of the traces u_M(z, t) (eq. mult-scatt-int).
  *  precision : 0 = FP64 throughout.  1 = mixed form: FP32 LU factors; solutions refined against the
  *              matrix kept as double-float (two floats, ~48 bits) until the relative error estimated
- *              to remain (last correction x estimated contraction factor) is below 1e-12, at most 3
- *              steps; self and cross entries (Taylor range and far-field recurrence), the FFT
- *              butterflies of the time transforms, the restriction and the cross apply in double-float
- *              on the FP32 pipe; diagonal self entries, per-pair setup, phase-seed reduction,
- *              log-singular corrections, transform folds and phase factors stay FP64.  Densities agree
- *              with the FP64 form to 4e-12 (4 obstacles, N <= 259) and 2e-11 (12-arc cavity, N <= 760).
- *              Others -> ENOTIMPL.
+ *              to remain (last correction x estimated contraction factor) is below refine_tol, at most
+ *              refine_max steps; self and cross entries (Taylor range and far-field recurrence), the
+ *              refinement residuals, the FFT butterflies of the time transforms, the restriction and the
+ *              cross apply in double-float on the FP32 pipe; diagonal self entries, per-pair setup,
+ *              phase-seed reduction, log-singular corrections, transform folds and phase factors stay
+ *              FP64.  The refinement solves the double-float matrix exactly; its rounding (~2^-44 of an
+ *              entry) still reaches the densities through the matrix's conditioning.  2 = the mixed form
+ *              with FP64 kept where accuracy is decided: the self matrices assembled and kept in FP64 (the
+ *              FP32 factor is their rounding) with FP64 refinement residuals, the small-argument (z < 20)
+ *              Hankel series of the stored cross entries, and the FFT butterflies of the time transforms
+ *              (everything else as in 1).  Others -> ENOTIMPL.
  *  keep_densities : 1 keeps phi_{j,m,q}(omega_l) of every step for fthms_densities; 0 keeps only
  *              the sum over m.
  *  cross_mode: 0 = the cross-arc and observation rows of eq. FDsolk-interior are assembled once per job,
  *              stored in device memory and applied every step (fast while they fit: 16 bytes per
  *              entry).  1 = they are evaluated again in every step and summed at once, nothing stored
  *              (for jobs whose cross rows do not fit, e.g. many arcs on one curve at high frequency).
- *              Both modes give the same densities to rounding.  Others -> EINVAL. */
+ *              Both modes give the same densities to rounding.  Others -> EINVAL.
+ *  refine_tol, refine_max : mixed forms: a system stops refining once the estimated relative error left
+ *              is below refine_tol (0 = 1e-12), after at most refine_max passes (0 = 3; at most 16).  The
+ *              estimate is the last correction's relative size times the contraction factor: the ratio
+ *              of the last two corrections, or after the first correction 10 x its own size.
+ *  refine_fallback : mixed forms: 0 = a job in which some system did not meet refine_tol within
+ *              refine_max passes finishes with those results and fthms_wait returns FTHMS_ENOCONV;
+ *              1 = fthms_wait then runs the whole job again in FP64 (precision 0) and returns its
+ *              status (the FP64 results replace the mixed ones; fthms_stats reports the fallback). */
 typedef struct {
   double W;
   int L;
@@ -121,6 +149,9 @@ typedef struct {
   int precision;
   int keep_densities;
   int cross_mode;
+  double refine_tol;
+  int refine_max;
+  int refine_fallback;
 } fthms_options;
 
 typedef struct {
@@ -137,9 +168,11 @@ typedef struct {
   double solve_flops;     /* 8 sum N^2 Q M: triangular solves of one run */
   double apply_flops;     /* 8 Q M (cross + observation entries): cross matvecs of one run */
   int precision;          /* the job's precision option */
-  double max_refine_resid; /* precision 1: max over systems and steps of the relative error estimated to
+  double max_refine_resid; /* mixed forms: max over systems and steps of the relative error estimated to
                               remain after the last correction (its size x the estimated contraction) */
-  double refine_passes;   /* precision 1: mean refinement passes (residual + correction) per system and step */
+  double refine_passes;   /* mixed forms: mean refinement passes (residual + correction) per system and step */
+  long long n_unconverged; /* mixed forms: (system, step) pairs whose estimate stayed above refine_tol */
+  int fallback_runs;      /* runs of the job repeated in FP64 by refine_fallback = 1 */
 } fthms_stats_t;
 
 /* Create a context on CUDA device `device` that enqueues all work on `cuda_stream` (a
@@ -185,7 +218,10 @@ fthms_status fthms_submit(fthms_ctx* ctx, const fthms_curve* curves, int ncurves
 /* *done = 1 when the last run finished (0 otherwise); never blocks. */
 fthms_status fthms_poll(fthms_req* req, int* done);
 /* Block until the last run finished or timeout_ms elapsed (negative = no limit):
- * FTHMS_ETIMEOUT on timeout, FTHMS_ECUDA if the device reported an error. */
+ * FTHMS_ETIMEOUT on timeout, FTHMS_ECUDA if the device reported an error, FTHMS_ENOCONV if the run
+ * finished but some system of a mixed-form job did not meet refine_tol within refine_max passes (its
+ * results stay readable; with refine_fallback = 1 the job is first run again in FP64, see
+ * fthms_options). */
 fthms_status fthms_wait(fthms_req* req, int timeout_ms);
 
 /* Output traces u_M(z_k, t_i) (eq. mult-scatt-int, evaluated directly at the output times),
@@ -208,6 +244,13 @@ fthms_status fthms_densities_dev(fthms_req* req, int arc, int m, int q, double* 
 fthms_status fthms_node_counts(fthms_req* req, int* out, size_t cap);
 
 fthms_status fthms_stats(fthms_req* req, fthms_stats_t* out);
+
+/* Per-result error statement of the mixed forms: out[j*(L-1) + l-1] = the relative error estimated to
+ * remain in the densities phi_{j,m,q}(omega_l) after refinement, maximised over the steps m and windows
+ * q (the estimate of refine_tol's stopping rule; the smooth densities of Algorithm 1's BIE solve).  0 for
+ * every system of an FP64 job (direct solve, no estimate) and of a job replaced by the FP64 fallback.
+ * cap >= narcs*(L-1).  Waits for the job. */
+fthms_status fthms_result_errors(fthms_req* req, double* out, size_t cap);
 
 /* Pipeline stages, in enqueue order, for the per-stage timers below. */
 enum {
@@ -287,26 +330,32 @@ fthms_status fthms_bessel0(const double* z_dev, double* j0_dev, double* y0_dev,
 
 /* Nystrom matrix of V_Gamma on one arc (eq. FDBIEk-interior with the log-split Chebyshev rule):
  * A[i + l*N] (column-major, interleaved complex, 2*N*N doubles in A_dev) for N first-kind nodes
- * at wavenumber kappa > 0.  Allocates and frees its own temporary tables. */
+ * at wavenumber kappa > 0.  Allocates and frees its own temporary tables and returns after the matrix
+ * is written (it synchronizes cuda_stream).  FTHMS_EINVAL for a NULL argument or coefficient array,
+ * curve degree < 1, N outside [2, 1024], kappa <= 0 or theta_b <= theta_a. */
 fthms_status fthms_assemble_self(const fthms_curve* curve, const fthms_arc* arc, int N,
                                  double kappa, double* A_dev, void* cuda_stream);
 
 /* Allocation-free variant of fthms_assemble_self (the paper has no counterpart; this is a library
- * convenience).  It is for callers that may not allocate device memory: code running inside a
- * stream capture or a memory-capped pool, or a host application whose own allocator owns all device
- * memory and forbids cudaMalloc/cudaFree from third-party code.  It computes the same matrix (same
- * kernels, same layout: A[i + l*N], interleaved complex, 2*N*N doubles in A_dev) but keeps its
- * temporary device data in a fixed ~534 KB static device array of the library instead of
- * allocating: every GPU that loads the library holds that array until the process exits.  The
- * caller still provides A_dev.
- *  - N must be in [2, 256] (the array's capacity); larger N returns FTHMS_EINVAL.
+ * convenience).  It is for callers that must not allocate device memory: a host application whose
+ * own allocator owns all device memory and forbids cudaMalloc/cudaFree from third-party code, a
+ * process running under a fixed memory cap, or a latency-bound pipeline that cannot accept the
+ * device-wide synchronisation that cudaFree implies.  It computes the same matrix (same kernels, same
+ * layout: A[i + l*N], interleaved complex, 2*N*N doubles in A_dev) but keeps its temporary device
+ * data in a fixed ~534 KB static device array of the library instead of allocating: every GPU that
+ * loads the library holds that array until the process exits.  The caller still provides A_dev.
+ *  - Arguments are checked as in fthms_assemble_self, except that N must lie in [2, 256] (the
+ *    array's capacity); N outside that range returns FTHMS_EINVAL.
  *  - The first call on each device (with that device current) looks up the array's device address
  *    and uploads the Bessel coefficient tables; make that first call before any stream capture.
+ *  - The call is asynchronous on cuda_stream: it returns with its copies and kernels queued.  A_dev
+ *    holds the matrix, and the static array is free for the next caller, only once that stream's
+ *    work has completed (synchronize the stream or order later work after it).
  *  - All calls share the one array and leave their data in it.  Calls whose work overlaps on the
  *    GPU (different streams or threads without ordering) race on it; calls on one stream are
  *    ordered.  Every call rewrites all of the array that it reads, so nothing needs clearing.
- *  - No cudaMalloc/cudaFree or other allocating routine is called; the upload is a cudaMemcpyAsync
- *    from host stack memory on cuda_stream. */
+ *  - No cudaMalloc/cudaFree or other allocating routine is called; the per-call tables go up with
+ *    cudaMemcpyAsync on cuda_stream. */
 fthms_status fthms_assemble_self_noalloc(const fthms_curve* curve, const fthms_arc* arc, int N,
                                          double kappa, double* A_dev, void* cuda_stream);
 

@@ -25,9 +25,41 @@ import numpy as np
 from .geometry import eta
 
 
-def signal_f(sig, t):
-    """f(t) = amp sin(carrier t) exp(-((t - centre)/width)^2)."""
+def sampled_signal(smp, t):
+    """Sampled signal f[i] = f(t0 + i dt) read between the samples (our reading of "a boundary time
+    signal" given as data; the paper's own signals are analytic): the degree-7 Lagrange interpolant through
+    the samples floor(s) - 3 .. floor(s) + 4, s = (t - t0)/dt, a sample index outside 0..n-1 counting as a
+    zero sample, and f = 0 outside [t0, t0 + (n-1) dt].  Weight of sample i0 + k at x = s - i0:
+    prod_{m != k} (x - m)/(k - m)."""
     t = np.asarray(t, dtype=np.float64)
+    f = np.asarray(smp["f"], dtype=np.float64)
+    n = f.size
+    t0, dt = float(smp["t0"]), float(smp["dt"])
+    tend = t0 + (n - 1) * dt
+    out = np.zeros(t.shape)
+    inside = (t >= t0) & (t <= tend)
+    s = (t[inside] - t0) / dt
+    fl = np.floor(s)
+    i0 = fl.astype(np.int64) - 3
+    x = s - fl + 3.0
+    acc = np.zeros(x.shape)
+    for k in range(8):
+        w = np.ones(x.shape)
+        for m in range(8):
+            if m != k:
+                w *= (x - m) / (k - m)
+        idx = i0 + k
+        ok = (idx >= 0) & (idx < n)
+        acc += w * np.where(ok, f[np.clip(idx, 0, n - 1)], 0.0)
+    out[inside] = acc
+    return out
+
+
+def signal_f(sig, t):
+    """f(t) = amp sin(carrier t) exp(-((t - centre)/width)^2), or the sampled signal of sig["samples"]."""
+    t = np.asarray(t, dtype=np.float64)
+    if sig.get("samples") is not None:
+        return sampled_signal(sig["samples"], t)
     return sig["amp"] * np.sin(sig["carrier"] * t) * np.exp(-((t - sig["centre"]) / sig["width"]) ** 2)
 
 
@@ -44,15 +76,27 @@ def signal_F(sig, omega):
 def point_source_rule(sig, r, t):
     """Integration range and node count of the trapezoid rule in v for the 2-D retarded field
     u(r, t) = (1/(2 pi)) int_0^inf f(t - r cosh v) dv (tau = r cosh v in the convolution of f with
-    H(t-r)/(2 pi sqrt(t^2 - r^2))).  f is below e^{-64} outside |tau - (t - centre)| <= 8 width.
-    Returns (v_lo, v_hi, n_intervals) or None when the integrand vanishes."""
-    tau_hi = t - sig["centre"] + 8.0 * sig["width"]
+    H(t-r)/(2 pi sqrt(t^2 - r^2))).  The analytic f is below e^{-64} outside |tau - (t - centre)| <=
+    8 width, with bandwidth B = |carrier| + 8/width; a sampled f vanishes outside its sample range and
+    carries its stated bandwidth B = band.  Returns (v_lo, v_hi, n_intervals) or None when the integrand
+    vanishes."""
+    smp = sig.get("samples")
+    if smp is not None:
+        tau_hi = t - smp["t0"]
+        tau_lo_c = t - (smp["t0"] + (len(smp["f"]) - 1) * smp["dt"])
+        band = smp["band"]
+    else:
+        tau_hi = t - sig["centre"] + 8.0 * sig["width"]
+        tau_lo_c = t - sig["centre"] - 8.0 * sig["width"]
+        band = abs(sig["carrier"]) + 8.0 / sig["width"]
     if tau_hi <= r:
         return None
-    tau_lo = max(r, t - sig["centre"] - 8.0 * sig["width"])
+    tau_lo = max(r, tau_lo_c)
+    if tau_lo >= tau_hi:
+        return None
     v_lo = math.acosh(tau_lo / r)
     v_hi = math.acosh(tau_hi / r)
-    rate = (abs(sig["carrier"]) + 8.0 / sig["width"]) * r * math.sinh(v_hi) + 1.0
+    rate = band * r * math.sinh(v_hi) + 1.0
     n = int(math.ceil((v_hi - v_lo) * (1.25 * rate + 24.0) / (2.0 * math.pi) * 2.0)) + 16
     return v_lo, v_hi, n
 

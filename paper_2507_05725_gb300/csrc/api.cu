@@ -106,6 +106,11 @@ struct fthms_req {
   double setup_ms = 0.0;
   bool use_graph = false;          // replay the captured pipeline instead of launching stage by stage
   cudaGraphExec_t graph = nullptr;
+  bool conv_checked = false;       // the last run's refinement counters have been read
+  fthms_status conv_status = FTHMS_OK;
+  std::string conv_msg;
+  int fallback_runs = 0;           // runs repeated in FP64 after a refinement that did not converge
+  bool plain_apply_fits = true;    // the FP64 stored-row apply fits shared memory (FP64 fallback possible)
 };
 
 namespace {
@@ -186,8 +191,10 @@ fthms_status upload_job(fthms_req* r) {
     J.row_cap = std::max(J.row_cap, rows);
     J.ph_cap = std::max(J.ph_cap, nsum);
   }
-  if (!J.mixed && p.opt.cross_mode == 0 &&
-      (size_t)J.Q * (J.acc_cap + J.row_cap + J.ph_cap) * 16 > (size_t)227 * 1024)
+  // The FP64 stored-row apply keeps a whole group in shared memory (the mixed form works in row slices).
+  r->plain_apply_fits = p.opt.cross_mode != 0 ||
+                        (size_t)J.Q * (J.acc_cap + J.row_cap + J.ph_cap) * 16 <= (size_t)227 * 1024;
+  if (p.opt.precision == 0 && !r->plain_apply_fits)
     return fail(FTHMS_EINVAL, "fthms_prepare: the stored cross rows of one (arc, frequency) group do not fit the "
                               "apply's shared memory; use cross_mode 1");
   J.h = p.h; J.dt = p.dt; J.sign = p.sig.sign;
@@ -195,10 +202,16 @@ fthms_status upload_job(fthms_req* r) {
   J.z0x = p.sig.z0[0]; J.z0y = p.sig.z0[1];
   J.dirx = p.sig.dir[0]; J.diry = p.sig.dir[1];
   J.amp = p.sig.amp; J.carrier = p.sig.carrier; J.centre = p.sig.centre; J.width = p.sig.width;
+  J.sig_nt = (int)p.sig_f.size();
+  J.sig_t0 = p.sig.t0; J.sig_dt = p.sig.dt; J.sig_band = p.sig.band;
   J.H = p.H; J.period = p.period;
   J.vec_total = p.vec_total;
-  J.mixed = p.opt.precision == 1 ? 1 : 0;
+  J.mixed = p.opt.precision >= 1 ? 1 : 0;
+  J.fp64keep = p.opt.precision == 2 ? 1 : 0;
+  J.refine_tol = p.opt.refine_tol;
+  J.refine_max = p.opt.refine_max;
   J.mat_total = p.mat_total;
+  TRY(dev_upload(r, p.sig_f, &J.sig_f));
 
   TRY(dev_upload(r, p.sys, &J.sys));
   TRY(dev_upload(r, p.sys_order, &J.sys_order));
@@ -216,7 +229,7 @@ fthms_status upload_job(fthms_req* r) {
   TRY(dev_upload(r, p.restr_off, &J.restr_off));
   TRY(dev_alloc(r, (size_t)p.restr_total, &J.restr));
   J.restr_df = nullptr;
-  if (p.opt.precision == 1) TRY(dev_alloc(r, (size_t)p.restr_total, &J.restr_df));
+  if (p.opt.precision >= 1) TRY(dev_alloc(r, (size_t)p.restr_total, &J.restr_df));
   TRY(dev_upload(r, p.restr_of_sys, &J.restr_of_sys));
   TRY(dev_upload(r, p.self_tiles, &J.tiles));
   TRY(dev_upload(r, p.tgts, &J.tgts));
@@ -274,8 +287,10 @@ fthms_status upload_job(fthms_req* r) {
   J.mrel = nullptr;
   J.rchunks = nullptr;
   J.n_rchunks = 0;
-  TRY(dev_alloc(r, 2, &J.refine_resid));          // [0] max estimated error left, [1] refinement passes (u64)
+  TRY(dev_alloc(r, 3, &J.refine_resid));          // [0] max estimated error left, [1] passes, [2] unconverged
+  J.sys_err = nullptr;
   if (J.mixed) {
+    TRY(dev_alloc(r, p.sys.size(), &J.sys_err));
     TRY(dev_alloc(r, (size_t)p.mat_total, &J.LU32));
     TRY(dev_alloc(r, (size_t)p.piv_total, &J.dinv32));
     TRY(dev_alloc(r, (size_t)p.vec_total, &J.rres));
@@ -293,6 +308,7 @@ fthms_status upload_job(fthms_req* r) {
   if (p.opt.keep_densities) TRY(dev_alloc(r, (size_t)p.vec_total * p.M, &J.phi_all));
   TRY(dev_alloc(r, (size_t)p.spec_total, &J.W));
   TRY(dev_alloc(r, (size_t)p.spec_total, &J.Gt));
+  TRY(dev_alloc(r, (size_t)p.act_idx.size() * p.NT, &J.ginc));
   J.E = nullptr;
   if (!J.otf) TRY(dev_alloc(r, (size_t)p.e_total, &J.E));
   TRY(dev_alloc(r, (size_t)std::max(1, p.n_obs * p.Q * p.L), &J.Vobs));
@@ -378,6 +394,7 @@ fthms_status enqueue(fthms_req* r) {
   CK(cudaGraphLaunch(r->graph, st));
   CK(cudaEventRecord(r->ev1, st));
   r->ran = true;
+  r->conv_checked = false;
   return FTHMS_OK;
 }
 
@@ -385,6 +402,7 @@ fthms_status enqueue_stages(fthms_req* r, bool bracket) {
   const DevJob& J = r->J;
   cudaStream_t st = r->stream;
   int nl = 0;
+  r->conv_checked = false;
   TRY(flush_marks(r));
   if (bracket) CK(cudaEventRecord(r->ev0, st));
   TRY(stage(r, FTHMS_STAGE_TABLES, st, &nl, [&] { return launch_tables(J, st, &nl); }));
@@ -396,7 +414,8 @@ fthms_status enqueue_stages(fthms_req* r, bool bracket) {
   CK(cudaMemsetAsync(J.Gt, 0, (size_t)r->plan.spec_total * sizeof(double2), st));
   CK(cudaMemsetAsync(J.W, 0, (size_t)r->plan.spec_total * sizeof(double2), st));
   CK(cudaMemsetAsync(J.Vobs, 0, (size_t)std::max(1, J.n_obs * J.Q * J.L) * sizeof(double2), st));
-  CK(cudaMemsetAsync(J.refine_resid, 0, 2 * sizeof(double), st));
+  CK(cudaMemsetAsync(J.refine_resid, 0, 3 * sizeof(double), st));
+  if (J.sys_err) CK(cudaMemsetAsync(J.sys_err, 0, (size_t)J.nsys * sizeof(float), st));
   TRY(stage(r, FTHMS_STAGE_INCIDENT, st, &nl, [&] { return launch_incident(J, st, &nl); }));
   TRY(stage(r, FTHMS_STAGE_RESTRICT, st, &nl, [&] { return launch_restrict(J, st, &nl); }));
   for (int m = 1; m <= J.M; ++m) {
@@ -583,11 +602,8 @@ fthms_status fthms_poll(fthms_req* req, int* done) {
   return cuda_fail(e, "fthms_poll");
 }
 
-fthms_status fthms_wait(fthms_req* req, int timeout_ms) {
-  if (!req) return fail(FTHMS_EINVAL, "fthms_wait: NULL job");
-  if (!req->ctx) return fail(FTHMS_EINVAL, "fthms_wait: the job's context was destroyed");
-  if (!req->ran) return fail(FTHMS_EINVAL, "fthms_wait: job was never run");
-  TRY(ensure_device(req->ctx->device));
+// Wait for the last run's completion event (no convergence check).
+static fthms_status wait_run(fthms_req* req, int timeout_ms) {
   auto t0 = std::chrono::steady_clock::now();
   for (;;) {
     cudaError_t e = cudaEventQuery(req->ev1);
@@ -601,12 +617,65 @@ fthms_status fthms_wait(fthms_req* req, int timeout_ms) {
   }
 }
 
+// After a finished run of a mixed-form job: read how many (system, step) refinements stayed above
+// refine_tol; with refine_fallback the whole job runs again in FP64 (every stage, on the job's stream).
+static fthms_status check_convergence(fthms_req* req) {
+  if (req->conv_checked) {
+    if (req->conv_status != FTHMS_OK) g_last_error = req->conv_msg;
+    return req->conv_status;
+  }
+  req->conv_checked = true;
+  req->conv_status = FTHMS_OK;
+  if (!req->J.mixed) return FTHMS_OK;
+  unsigned long long bad = 0;
+  CK(cudaMemcpyAsync(&bad, reinterpret_cast<const unsigned long long*>(req->J.refine_resid) + 2, sizeof bad,
+                     cudaMemcpyDeviceToHost, req->stream));
+  CK(cudaStreamSynchronize(req->stream));
+  if (bad == 0) return FTHMS_OK;
+  if (req->plan.opt.refine_fallback && req->plain_apply_fits) {
+    req->J.mixed = 0;
+    req->J.fp64keep = 0;
+    if (req->graph) {                  // the captured graph holds the mixed-form kernels
+      cudaGraphExecDestroy(req->graph);
+      req->graph = nullptr;
+    }
+    ++req->fallback_runs;
+    TRY(enqueue_stages(req));
+    TRY(wait_run(req, -1));
+    req->conv_checked = true;
+    return FTHMS_OK;
+  }
+  char buf[200];
+  snprintf(buf, sizeof buf, "fthms_wait: %llu (system, step) refinements stayed above refine_tol = %.3g after %d "
+           "passes%s", bad, req->plan.opt.refine_tol, req->plan.opt.refine_max,
+           req->plan.opt.refine_fallback ? " (no FP64 fallback: the stored cross rows exceed its apply)" : "");
+  req->conv_status = FTHMS_ENOCONV;
+  req->conv_msg = buf;
+  g_last_error = buf;
+  return FTHMS_ENOCONV;
+}
+
+fthms_status fthms_wait(fthms_req* req, int timeout_ms) {
+  if (!req) return fail(FTHMS_EINVAL, "fthms_wait: NULL job");
+  if (!req->ctx) return fail(FTHMS_EINVAL, "fthms_wait: the job's context was destroyed");
+  if (!req->ran) return fail(FTHMS_EINVAL, "fthms_wait: job was never run");
+  TRY(ensure_device(req->ctx->device));
+  TRY(wait_run(req, timeout_ms));
+  return check_convergence(req);
+}
+
+// Wait before reading results: a run whose refinement did not converge still has readable results.
+static fthms_status wait_results(fthms_req* req) {
+  fthms_status s = fthms_wait(req, -1);
+  return s == FTHMS_ENOCONV ? FTHMS_OK : s;
+}
+
 fthms_status fthms_traces(fthms_req* req, double* out, size_t cap) {
   if (!req || (!out && cap)) return fail(FTHMS_EINVAL, "fthms_traces: NULL argument");
   if (!req->ctx) return fail(FTHMS_EINVAL, "fthms_traces: the job's context was destroyed");
   size_t n = (size_t)req->plan.n_obs * req->plan.n_tout;
   if (cap < n) return fail(FTHMS_EINVAL, "fthms_traces: output buffer too small");
-  TRY(fthms_wait(req, -1));
+  TRY(wait_results(req));
   if (n) {
     CK(cudaMemcpyAsync(out, req->J.traces, n * sizeof(double), cudaMemcpyDeviceToHost, req->stream));
     CK(cudaStreamSynchronize(req->stream));
@@ -641,7 +710,7 @@ fthms_status fthms_densities(fthms_req* req, int arc, int m, int q, double* out,
   TRY(density_range(req, arc, m, q, &base, &first, &last, &n));
   if (needed) *needed = n;
   if (!out || cap < n) return fail(FTHMS_EINVAL, "fthms_densities: output buffer too small");
-  TRY(fthms_wait(req, -1));
+  TRY(wait_results(req));
   const Plan& p = req->plan;
   std::vector<double2> h((size_t)(last - first));
   CK(cudaMemcpyAsync(h.data(), base + first, h.size() * sizeof(double2), cudaMemcpyDeviceToHost, req->stream));
@@ -710,21 +779,46 @@ fthms_status fthms_stats(fthms_req* req, fthms_stats_t* out) {
   out->solve_flops = sv;
   out->apply_flops = 8.0 * p.Q * p.M * (double)p.e_total;
   out->precision = p.opt.precision;
+  out->fallback_runs = req->fallback_runs;
   if (req->ran) {
-    TRY(fthms_wait(req, -1));
+    TRY(wait_results(req));
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, req->ev0, req->ev1));
     out->gpu_ms = ms;
     if (req->J.mixed) {
-      double buf[2] = {0.0, 0.0};
-      CK(cudaMemcpyAsync(buf, req->J.refine_resid, 2 * sizeof(double), cudaMemcpyDeviceToHost, req->stream));
+      double buf[3] = {0.0, 0.0, 0.0};
+      CK(cudaMemcpyAsync(buf, req->J.refine_resid, 3 * sizeof(double), cudaMemcpyDeviceToHost, req->stream));
       CK(cudaStreamSynchronize(req->stream));
-      unsigned long long passes = 0;
+      unsigned long long passes = 0, bad = 0;
       std::memcpy(&passes, &buf[1], sizeof passes);
+      std::memcpy(&bad, &buf[2], sizeof bad);
       out->max_refine_resid = buf[0];
       out->refine_passes = (double)passes / ((double)req->J.nsys * p.M);
+      out->n_unconverged = (long long)bad;
     }
   }
+  return FTHMS_OK;
+}
+
+fthms_status fthms_result_errors(fthms_req* req, double* out, size_t cap) {
+  if (!req || !out) return fail(FTHMS_EINVAL, "fthms_result_errors: NULL argument");
+  if (!req->ctx) return fail(FTHMS_EINVAL, "fthms_result_errors: the job's context was destroyed");
+  const Plan& p = req->plan;
+  const size_t n = (size_t)p.P * (p.L - 1);
+  if (cap < n) return fail(FTHMS_EINVAL, "fthms_result_errors: buffer too small");
+  if (!req->ran || !req->J.mixed) {
+    for (size_t i = 0; i < n; ++i) out[i] = 0.0;
+    return req->ran ? FTHMS_OK : fail(FTHMS_EINVAL, "fthms_result_errors: job was never run");
+  }
+  TRY(wait_results(req));
+  if (!req->J.mixed) {                 // replaced by the FP64 fallback
+    for (size_t i = 0; i < n; ++i) out[i] = 0.0;
+    return FTHMS_OK;
+  }
+  std::vector<float> e(n);
+  CK(cudaMemcpyAsync(e.data(), req->J.sys_err, n * sizeof(float), cudaMemcpyDeviceToHost, req->stream));
+  CK(cudaStreamSynchronize(req->stream));
+  for (size_t i = 0; i < n; ++i) out[i] = e[i];     // systems are numbered j*(L-1) + l-1
   return FTHMS_OK;
 }
 
@@ -843,7 +937,8 @@ fthms_status fthms_bessel0(const double* z_dev, double* j0_dev, double* y0_dev, 
 
 fthms_status fthms_assemble_self(const fthms_curve* curve, const fthms_arc* arc, int N, double kappa,
                                  double* A_dev, void* cuda_stream) {
-  if (!curve || !arc || !A_dev || N < 2 || N > 1024 || !(kappa > 0) || !(arc->theta_b > arc->theta_a))
+  if (!curve || !arc || !A_dev || !curve->ax || !curve->bx || !curve->ay || !curve->by || curve->degree < 1 ||
+      N < 2 || N > 1024 || !(kappa > 0) || !(arc->theta_b > arc->theta_a))
     return fail(FTHMS_EINVAL, "fthms_assemble_self: bad arguments");
   int dev = 0;
   CK(cudaGetDevice(&dev));
@@ -917,6 +1012,7 @@ struct ServerReq {
   std::vector<fthms_curve> curves;
   std::vector<fthms_arc> arcs;
   fthms_signal sig{};
+  std::vector<double> sig_f;    // samples of a sampled signal
   fthms_options opt{};
   std::vector<double> obs;
   fthms_req* req = nullptr;
@@ -1088,6 +1184,10 @@ fthms_status fthms_server_submit(fthms_server* s, const fthms_curve* curves, int
   }
   q->arcs.assign(arcs, arcs + narcs);
   q->sig = *signal;
+  if (signal->n_t > 0 && signal->f) {
+    q->sig_f.assign(signal->f, signal->f + signal->n_t);
+    q->sig.f = q->sig_f.data();
+  }
   q->opt = *options;
   if (options->n_obs > 0 && options->obs_xy) q->obs.assign(options->obs_xy, options->obs_xy + 2 * options->n_obs);
   q->opt.obs_xy = q->obs.empty() ? nullptr : q->obs.data();

@@ -15,6 +15,7 @@
 //                  windowed slow transform (eq. Fourierk) -- one CTA per transfer node, in shared
 //                  memory, with a radix-2 FFT
 //   traces         u_M(z, t) at the output times (eq. mult-scatt-int)
+#include <algorithm>
 #include <cstdio>
 
 #include "bessel.cuh"
@@ -252,9 +253,13 @@ __device__ __forceinline__ void df_phase_seed(double theta, df& cx, df& sx) {
 }
 
 // A self-matrix entry: FP64, or (mixed form) the double-float pair the refinement reads plus its FP32
-// rounding for the FP32 factorisation -- what a separate split of the FP64 matrix would give.
+// rounding for the FP32 factorisation -- what a separate split of the FP64 matrix would give -- or (the
+// FP64-kept form) the FP64 value the FP64 residual reads plus its FP32 rounding.
 __device__ __forceinline__ void store_self(const DevJob& J, long long off, double2 v) {
-  if (J.mixed) {
+  if (J.fp64keep) {
+    J.A[off] = v;
+    J.LU32[off] = make_float2(__double2float_rn(v.x), __double2float_rn(v.y));
+  } else if (J.mixed) {
     const float4 d = df_split2(v);
     reinterpret_cast<float4*>(J.A)[off] = d;
     J.LU32[off] = make_float2(d.x, d.z);
@@ -367,7 +372,7 @@ __global__ void __launch_bounds__(256) k_assemble_self(DevJob J) {
   const int lend = s0.l + nb;
   const double zmin = (lsw * J.h) * R;
   const int kmax = hankel_terms((float)zmin);
-  if (J.mixed) {
+  if (J.mixed && !J.fp64keep) {
     // Mixed form, z < 20: the Taylor range in double-float, alpha = aw ln l + a0.
     const df R_d = df_from(R), qw_d = df_from(qw), aw_d = df_from(-0.5 * kInvPi * w),
              a0_d = df_from(-0.5 * kInvPi * fma(w, lratio, rl));
@@ -399,9 +404,10 @@ __global__ void __launch_bounds__(256) k_assemble_self(DevJob J) {
       store_self(J, mo + e2, v);
     }
   }
-  if (J.mixed && lsw < lend) {
+  if (J.mixed && !J.fp64keep && lsw < lend) {
     // Mixed form: the recurrence above z = 20 in double-float on the FP32 pipe (about 48 bits), stored
-    // as the pair and its FP32 rounding; FP64 only for the seeds.
+    // as the pair and its FP32 rounding; FP64 only for the seeds.  (The FP64-kept form assembles the
+    // whole self matrix in FP64, as the plain form does.)
     const df ampu_d = df_from(amp_u), invu_d = df_from(inv_u), alpha_d = df_from(alpha_a), qw_d = df_from(qw);
     df cu_d, su_d;
     if (hR <= 1.0) {
@@ -976,7 +982,7 @@ __global__ void __launch_bounds__(kAsmMaxThreads) k_cross_assemble(DevJob J) {
                                     t.near ? Wn[r * N + i] : 0.0, task.l0, w, invw, inv_h);
     double2* Ep = J.E + (long long)i * ld + task.row0 + r;
     const int lend = min(ps.lsw, task.l1 + 1);
-    if (J.mixed) {
+    if (J.mixed && !J.fp64keep) {
       // Mixed form, z < 20: the Taylor range in double-float, stored as double-float pairs.
       const df R_d = df_from(ps.R), A0_d = df_from(ps.A0), A1_d = df_from(A1), qw_d = df_from(qw);
       for (int l = task.l0; l < lend; ++l) {
@@ -1215,22 +1221,61 @@ __global__ void __launch_bounds__(kApplyThreads) k_cross_apply(DevJob J) {
 
 // ---------------------------------------------------------------------------------------------
 // Mixed-precision solve: an FP32 blocked solve with the FP32 factors, then refinement steps, each a
-// double-float residual r = G - A phi (A kept as double-float, about 48 bits) and an FP32 correction,
-// until the error estimated to remain is below kRefineTol, or kRefineMax steps.  Each step shrinks the
-// error by a factor rho (the FP32 solve's relative accuracy), so what remains after a correction of
-// relative size rel is about rho * rel; rho is estimated by the ratio of the last two corrections, or
-// after the first step by rel itself (that correction is the FP32 solution's own error, rho times the
-// solution for a generic right-hand side).  A step is two launches over the
+// residual r = G - A phi (A kept as double-float, about 48 bits; the residual in double-float, or in FP64
+// in the FP64-kept form) and an FP32 correction, until the error estimated to remain is below
+// J.refine_tol, or J.refine_max steps.  Each step shrinks the error by a factor rho (the FP32 solve's
+// relative accuracy), so what remains after a correction of relative size rel is about rho * rel; rho is
+// estimated by the ratio of the last two corrections, or after the first step by kFirstRhoSafety * rel
+// (that correction is the FP32 solution's own error, about rho times the solution for a generic
+// right-hand side; the factor covers large systems, where one right-hand side underestimates rho by up
+// to ~10x).  A system still above the tolerance after J.refine_max steps is counted as unconverged.
+// A step is two launches over the
 // systems still refining: k_mresid streams the double-float matrix with one thread per row (many
 // warps in flight per SM), k_msolve runs the triangular solves with one warp per system and little
 // register state.  Until a system finishes, its densities sit in its phi slots as double-float pairs
 // (16 bytes, the size of the FP64 value written there at the end).
-constexpr int kRefineMax = 3;
-constexpr double kRefineTol = 1e-12;
+constexpr int kRefineCap = 16;          // largest refine_max accepted
+constexpr double kFirstRhoSafety = 10.0;
 constexpr int kResidThreads = 128;
 
 // One thread per row (rows past N recompute the last row and store nothing), all Q windows of the row:
 // r_q = G_q - A phi_q with compensated double-float sums over the columns in order.
+template <int Q>
+__global__ void __launch_bounds__(kResidThreads) k_mresid(DevJob J);
+
+// The same residual in FP64 (FP64-kept form): the matrix kept in FP64, the densities (double-float pairs
+// in the phi slots, exact sums of two floats) converted to FP64 without rounding; FMA accumulation over the
+// columns in order.
+template <int Q>
+__global__ void __launch_bounds__(kResidThreads) k_mresid64(DevJob J) {
+  const int chunk = blockIdx.x * (kResidThreads / 32) + (threadIdx.x >> 5);
+  if (chunk >= J.n_rchunks) return;
+  const ResidChunk c = J.rchunks[chunk];
+  if (J.mdone[c.sys]) return;
+  const SysDesc s = J.sys[c.sys];
+  const int N = s.N;
+  const int i = c.row0 + (threadIdx.x & 31);
+  const int row = i < N ? i : N - 1;
+  const double2* __restrict__ A64 = J.A + s.mat_off;
+  const float4* __restrict__ ph = reinterpret_cast<const float4*>(J.phi + s.vec_off);
+  const double2* __restrict__ G = J.G + s.vec_off;
+  double2 acc[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) acc[q] = G[q * N + row];
+  constexpr int kUnroll = Q == 1 ? 8 : Q == 2 ? 4 : 2;
+#pragma unroll kUnroll
+  for (int j = 0; j < N; ++j) {
+    const double2 a = __ldg(&A64[(long long)j * N + row]);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) acc[q] = cfms(a, df_join2(ph[q * N + j]), acc[q]);
+  }
+  if (i < N) {
+#pragma unroll
+    for (int q = 0; q < Q; ++q)
+      J.rres[s.vec_off + q * N + i] = make_float2(__double2float_rn(acc[q].x), __double2float_rn(acc[q].y));
+  }
+}
+
 template <int Q>
 __global__ void __launch_bounds__(kResidThreads) k_mresid(DevJob J) {
   const int chunk = blockIdx.x * (kResidThreads / 32) + (threadIdx.x >> 5);
@@ -1289,7 +1334,7 @@ __global__ void __launch_bounds__(kResidThreads) k_mresid(DevJob J) {
 
 // pass 0: solve with FP32 G, store phi as double-float, mark the system as refining.  pass p >= 1:
 // solve for the correction from the residual, add it in double-float, and finish the system (FP64
-// densities, their running sum, the statistics) once the correction is small enough or p = kRefineMax.
+// densities, their running sum, the statistics) once the correction is small enough or p = J.refine_max.
 __global__ void __launch_bounds__(32 * kSolveWarps, 4) k_msolve(DevJob J, int m, int pass) {
   extern __shared__ __align__(16) unsigned char shm_raw[];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1340,16 +1385,19 @@ __global__ void __launch_bounds__(32 * kSolveWarps, 4) k_msolve(DevJob J, int m,
     pmax = fmaxf(pmax, __shfl_xor_sync(0xffffffffu, pmax, o));
   }
   const double rel = pmax > 0.f ? (double)dmax / (double)pmax : 0.0;
-  const double rho = pass == 1 ? rel : rel / (double)J.mrel[sidx];
+  const double rho = pass == 1 ? kFirstRhoSafety * rel : rel / fmax((double)J.mrel[sidx], 1e-300);
   const double left = rel * rho;
-  if (left >= kRefineTol && pass < kRefineMax) {
+  if (left >= J.refine_tol && pass < J.refine_max) {
     if (lane == 0) J.mrel[sidx] = (float)rel;
     return;
   }
   if (lane == 0) {
     J.mdone[sidx] = 1;
+    // non-negative doubles and floats order like their bit patterns
     atomicMax(reinterpret_cast<unsigned long long*>(J.refine_resid), (unsigned long long)__double_as_longlong(left));
     atomicAdd(reinterpret_cast<unsigned long long*>(J.refine_resid) + 1, (unsigned long long)pass);
+    if (!(left < J.refine_tol)) atomicAdd(reinterpret_cast<unsigned long long*>(J.refine_resid) + 2, 1ULL);
+    atomicMax(reinterpret_cast<int*>(J.sys_err) + sidx, __float_as_int(fminf((float)left, 3.0e38f)));
   }
   // Each lane reads back the double-float values it wrote itself, then replaces them by FP64.
   double2* out = J.phi + s.vec_off;
@@ -1559,7 +1607,37 @@ __device__ void forward_all(const DevJob& J, const double* g, double2* buf, doub
   }
 }
 
+// Sampled signal: the degree-7 Lagrange interpolant through the samples i0 .. i0 + 7, i0 = floor(s) - 3,
+// s = (t - t0)/dt (missing samples count as zero), and 0 outside [t0, t0 + (n_t - 1) dt].  With x = s - i0
+// in [3, 4), the weight of sample i0 + k is prod_{m != k} (x - m) / prod_{m != k} (k - m), the numerator
+// from prefix and suffix products.
+__device__ double sampled_f(const DevJob& J, double t) {
+  const double tend = J.sig_t0 + (double)(J.sig_nt - 1) * J.sig_dt;
+  if (!(t >= J.sig_t0 && t <= tend)) return 0.0;
+  const double s = (t - J.sig_t0) / J.sig_dt;
+  const double fl = floor(s);
+  const int i0 = (int)fl - 3;
+  const double x = s - fl + 3.0;
+  constexpr double kDen[8] = {-5040.0, 720.0, -240.0, 144.0, -144.0, 240.0, -720.0, 5040.0};
+  double pre[8], suf[8];
+  pre[0] = 1.0;
+#pragma unroll
+  for (int k = 1; k < 8; ++k) pre[k] = pre[k - 1] * (x - (double)(k - 1));
+  suf[7] = 1.0;
+#pragma unroll
+  for (int k = 6; k >= 0; --k) suf[k] = suf[k + 1] * (x - (double)(k + 1));
+  double acc = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int i = i0 + k;
+    const double fi = (i >= 0 && i < J.sig_nt) ? __ldg(&J.sig_f[i]) : 0.0;
+    acc = fma(pre[k] * suf[k] / kDen[k], fi, acc);
+  }
+  return acc;
+}
+
 __device__ __forceinline__ double signal_f(const DevJob& J, double t) {
+  if (J.sig_nt > 0) return sampled_f(J, t);
   const double a = (t - J.centre) / J.width;
   return J.amp * sin(J.carrier * t) * exp(-a * a);
 }
@@ -1569,11 +1647,16 @@ __device__ double incident_u(const DevJob& J, double X, double Y, double t) {
   if (J.sig_kind == 1) return signal_f(J, t - fma(Y, J.diry, X * J.dirx));
   const double dx = X - J.z0x, dy = Y - J.z0y;
   const double r = sqrt(fma(dx, dx, dy * dy));
-  const double tau_hi = t - J.centre + 8.0 * J.width;
+  // f(t - tau) can be nonzero for tau in [t - (end of f), t - (start of f)]
+  const bool smp = J.sig_nt > 0;
+  const double tau_hi = smp ? t - J.sig_t0 : t - J.centre + 8.0 * J.width;
   if (tau_hi <= r) return 0.0;
-  const double tau_lo = fmax(r, t - J.centre - 8.0 * J.width);
+  const double tau_lo = fmax(r, smp ? t - (J.sig_t0 + (double)(J.sig_nt - 1) * J.sig_dt)
+                                    : t - J.centre - 8.0 * J.width);
+  if (tau_lo >= tau_hi) return 0.0;
   const double v_lo = acosh(tau_lo / r), v_hi = acosh(tau_hi / r);
-  const double rate = (fabs(J.carrier) + 8.0 / J.width) * r * sinh(v_hi) + 1.0;
+  const double band = smp ? J.sig_band : fabs(J.carrier) + 8.0 / J.width;
+  const double rate = band * r * sinh(v_hi) + 1.0;
   const int n = (int)ceil((v_hi - v_lo) * (1.25 * rate + 24.0) / (2.0 * kPiD) * 2.0) + 16;
   const double dv = (v_hi - v_lo) / n;
   double acc = 0.5 * (signal_f(J, t - r * cosh(v_lo)) + signal_f(J, t - r * cosh(v_hi)));
@@ -1581,17 +1664,87 @@ __device__ double incident_u(const DevJob& J, double X, double Y, double t) {
   return acc * dv * (0.5 * kInvPi);
 }
 
+// Incident time samples g[a][n] = sign chi_k u^i(x, t_n) at the active transfer nodes, t_n = -H + n dt.
+// One thread per run of kIncRun consecutive samples.  Point source with the analytic signal: the
+// trapezoid rule in v on the run's common range [v_lo(t_first), v_hi(t_last)] (it contains every sample's
+// own range, outside of which f < e^{-64}) with the step of the run's largest rate, and each term of the
+// sum advanced from sample to sample by an exact recurrence: with rho = r cosh v and d = t - centre - rho,
+// T(t) = e^{i carrier (t - rho)} e^{-(d/width)^2} (so f = amp Im T) satisfies
+//   T(t_{j+1}) = T(t_j) u g_j,  u = e^{i carrier dt} e^{-(dt^2 + 2 dt d_0)/width^2},  g_j = e^{-2 j dt^2/width^2}
+// from the run's first sample (d_0 = t_first - centre - rho; |d_0| <= 10 width keeps u within e^{+-3}),
+// so a term costs one seed (sincos, exp) per run and a complex product per sample.  Runs whose Gaussian
+// factor could change by more than e^{-64} within the run (dt kIncRun > 2 width) and sampled signals
+// evaluate every sample directly (incident_u).
+constexpr int kIncRun = 16;
+constexpr int kIncThreads = 128;
+
+__global__ void __launch_bounds__(kIncThreads) k_incident_u(DevJob J) {
+  const int a = blockIdx.x;
+  const int n0 = (blockIdx.y * kIncThreads + threadIdx.x) * kIncRun;
+  if (n0 >= J.NT) return;
+  const int nr = min(kIncRun, J.NT - n0);
+  const int k = J.act_arc[a], x = J.act_idx[a];
+  const Panel pn = J.panels[J.tpanel[k]];
+  const double X = J.node_x[pn.off + x], Y = J.node_y[pn.off + x];
+  const double pref = J.sign * J.chi[J.tr_off[k] + x];
+  double* g = J.ginc + (long long)a * J.NT + n0;
+  const bool rec = J.sig_kind == 0 && J.sig_nt == 0 && J.dt * kIncRun <= 2.0 * J.width;
+  if (!rec) {
+    for (int j = 0; j < nr; ++j) g[j] = pref * incident_u(J, X, Y, -J.H + (n0 + j) * J.dt);
+    return;
+  }
+  const double dx = X - J.z0x, dy = Y - J.z0y;
+  const double r = sqrt(fma(dx, dx, dy * dy));
+  const double t_first = -J.H + n0 * J.dt, t_last = -J.H + (n0 + nr - 1) * J.dt;
+  double acc[kIncRun];
+#pragma unroll
+  for (int j = 0; j < kIncRun; ++j) acc[j] = 0.0;
+  const double tau_hi = t_last - J.centre + 8.0 * J.width;
+  const double tau_lo = fmax(r, t_first - J.centre - 8.0 * J.width);
+  if (tau_hi > r && tau_lo < tau_hi) {
+    const double v_lo = acosh(tau_lo / r), v_hi = acosh(tau_hi / r);
+    const double rate = (fabs(J.carrier) + 8.0 / J.width) * r * sinh(v_hi) + 1.0;
+    const int n = (int)ceil((v_hi - v_lo) * (1.25 * rate + 24.0) / (2.0 * kPiD) * 2.0) + 16;
+    const double dv = (v_hi - v_lo) / n;
+    const double iw2 = 1.0 / (J.width * J.width);
+    double sa, ca;
+    sincos(J.carrier * J.dt, &sa, &ca);
+    const double gam = exp(-2.0 * J.dt * J.dt * iw2);
+    for (int kk = 0; kk <= n; ++kk) {
+      const double rho = r * cosh(fma((double)kk, dv, v_lo));
+      const double wgt = (kk == 0 || kk == n) ? 0.5 : 1.0;
+      const double d0 = t_first - J.centre - rho;
+      double sp, cp;
+      sincos(J.carrier * (t_first - rho), &sp, &cp);
+      const double e0 = wgt * exp(-d0 * d0 * iw2);
+      double2 z = make_double2(e0 * cp, e0 * sp);
+      const double b = exp(-(J.dt * J.dt + 2.0 * J.dt * d0) * iw2);
+      const double2 u = make_double2(ca * b, sa * b);
+      double gj = 1.0;
+#pragma unroll
+      for (int j = 0; j < kIncRun; ++j) {
+        acc[j] += z.y;
+        z = cmul(z, make_double2(u.x * gj, u.y * gj));
+        gj *= gam;
+      }
+    }
+    const double sc = pref * J.amp * dv * (0.5 * kInvPi);
+#pragma unroll
+    for (int j = 0; j < kIncRun; ++j) acc[j] *= sc;
+  }
+  for (int j = 0; j < nr; ++j) g[j] = acc[j];
+}
+
+// Slow transforms of the incident samples of one active transfer node (eq. Fourierk per window).
 template <bool DF>
 __global__ void __launch_bounds__(kTimeMaxThreads) k_incident(DevJob J) {
   extern __shared__ double2 sht[];
   const int a = blockIdx.x;
   const int k = J.act_arc[a], x = J.act_idx[a];
-  const Panel pn = J.panels[J.tpanel[k]];
   double2* buf = sht;                               // K
   double* g = reinterpret_cast<double*>(sht + J.K); // NT
-  const double X = J.node_x[pn.off + x], Y = J.node_y[pn.off + x];
-  const double pref = J.sign * J.chi[J.tr_off[k] + x];
-  for (int n = threadIdx.x; n < J.NT; n += blockDim.x) g[n] = pref * incident_u(J, X, Y, -J.H + n * J.dt);
+  const double* src = J.ginc + (long long)a * J.NT;
+  for (int n = threadIdx.x; n < J.NT; n += blockDim.x) g[n] = src[n];
   __syncthreads();
   forward_all<DF>(J, g, buf, J.Gt + (J.tr_off[k] + x) * J.Q * J.L);
 }
@@ -1808,14 +1961,17 @@ static size_t time_smem(const DevJob& J) { return (size_t)J.K * sizeof(double2) 
 
 cudaError_t launch_incident(const DevJob& J, cudaStream_t st, int* launches) {
   if (J.n_act == 0) return cudaSuccess;
+  const int runs = (J.NT + kIncRun - 1) / kIncRun;
+  k_incident_u<<<dim3(J.n_act, (runs + kIncThreads - 1) / kIncThreads), kIncThreads, 0, st>>>(J);
   size_t sh = time_smem(J);
   const int nt = J.shape_time > 0 ? J.shape_time : kTimeThreads;
-  cudaError_t e = cudaFuncSetAttribute(J.mixed ? k_incident<true> : k_incident<false>,
+  const bool df = J.mixed && !J.fp64keep;   // double-float FFT butterflies
+  cudaError_t e = cudaFuncSetAttribute(df ? k_incident<true> : k_incident<false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
   if (e != cudaSuccess) return e;
-  if (J.mixed) k_incident<true><<<J.n_act, nt, sh, st>>>(J);
+  if (df) k_incident<true><<<J.n_act, nt, sh, st>>>(J);
   else k_incident<false><<<J.n_act, nt, sh, st>>>(J);
-  *launches += 1;
+  *launches += 2;
   return cudaGetLastError();
 }
 
@@ -1823,10 +1979,11 @@ cudaError_t launch_synth_fwd(const DevJob& J, cudaStream_t st, int* launches) {
   if (J.n_act == 0) return cudaSuccess;
   size_t sh = time_smem(J);
   const int nt = J.shape_time > 0 ? J.shape_time : kTimeThreads;
-  cudaError_t e = cudaFuncSetAttribute(J.mixed ? k_synth_fwd<true> : k_synth_fwd<false>,
+  const bool df = J.mixed && !J.fp64keep;   // double-float FFT butterflies
+  cudaError_t e = cudaFuncSetAttribute(df ? k_synth_fwd<true> : k_synth_fwd<false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
   if (e != cudaSuccess) return e;
-  if (J.mixed) k_synth_fwd<true><<<J.n_act, nt, sh, st>>>(J);
+  if (df) k_synth_fwd<true><<<J.n_act, nt, sh, st>>>(J);
   else k_synth_fwd<false><<<J.n_act, nt, sh, st>>>(J);
   *launches += 1;
   return cudaGetLastError();
@@ -1861,17 +2018,27 @@ cudaError_t launch_solve(const DevJob& J, int m, cudaStream_t st, int* launches)
     cudaError_t e = cudaFuncSetAttribute(k_msolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
     if (e != cudaSuccess) return e;
     const int grid = cdiv(J.nsys, nw), rgrid = cdiv(J.n_rchunks, kResidThreads / 32);
+    const int passes = std::min(std::max(J.refine_max, 1), kRefineCap);
     k_msolve<<<grid, 32 * nw, sh, st>>>(J, m, 0);
-    for (int pass = 1; pass <= kRefineMax && rgrid > 0; ++pass) {
-      switch (J.Q) {
-        case 1: k_mresid<1><<<rgrid, kResidThreads, 0, st>>>(J); break;
-        case 2: k_mresid<2><<<rgrid, kResidThreads, 0, st>>>(J); break;
-        case 3: k_mresid<3><<<rgrid, kResidThreads, 0, st>>>(J); break;
-        default: k_mresid<4><<<rgrid, kResidThreads, 0, st>>>(J); break;
+    for (int pass = 1; pass <= passes && rgrid > 0; ++pass) {
+      if (J.fp64keep) {
+        switch (J.Q) {
+          case 1: k_mresid64<1><<<rgrid, kResidThreads, 0, st>>>(J); break;
+          case 2: k_mresid64<2><<<rgrid, kResidThreads, 0, st>>>(J); break;
+          case 3: k_mresid64<3><<<rgrid, kResidThreads, 0, st>>>(J); break;
+          default: k_mresid64<4><<<rgrid, kResidThreads, 0, st>>>(J); break;
+        }
+      } else {
+        switch (J.Q) {
+          case 1: k_mresid<1><<<rgrid, kResidThreads, 0, st>>>(J); break;
+          case 2: k_mresid<2><<<rgrid, kResidThreads, 0, st>>>(J); break;
+          case 3: k_mresid<3><<<rgrid, kResidThreads, 0, st>>>(J); break;
+          default: k_mresid<4><<<rgrid, kResidThreads, 0, st>>>(J); break;
+        }
       }
       k_msolve<<<grid, 32 * nw, sh, st>>>(J, m, pass);
     }
-    *launches += 1 + 2 * kRefineMax;
+    *launches += 1 + 2 * passes;
     return cudaGetLastError();
   }
   const size_t per = (size_t)J.Q * J.max_n * sizeof(double2);

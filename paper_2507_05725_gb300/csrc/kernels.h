@@ -12,11 +12,18 @@ struct DevJob {
   int logK, max_nmax, max_n, acc_cap;
   int row_cap, ph_cap;           // max rows and max sum of source N over the cross groups
   int mixed;                     // 1: mixed-precision form (FP32 LU + double-float refinement/apply)
+  int fp64keep;                  // mixed form with FP64 kept for the small-argument Hankel series, the
+                                 // refinement residuals and the FFT butterflies (precision 2)
+  double refine_tol;             // stop refining once the estimated relative error left is below this
+  int refine_max;                // at most this many refinement passes per system and step
   long long mat_total;
   double h, dt, sign;
   // signal
   int sig_kind;
   double z0x, z0y, dirx, diry, amp, carrier, centre, width;
+  int sig_nt;                    // > 0: sampled signal f[0..sig_nt) at sig_t0 + i sig_dt
+  double sig_t0, sig_dt, sig_band;
+  const double* sig_f;
   // tables
   const SysDesc* sys;
   const int* sys_order;       // systems by decreasing N (launch order of k_lu and the solves)
@@ -65,7 +72,9 @@ struct DevJob {
   double2* A;                // LU factors (mixed form: the matrix itself, as double-float)
   float2* LU32;              // FP32 factors (mixed form)
   float2* dinv32;            // FP32 1 / U_kk (mixed form)
-  double* refine_resid;      // max over systems of the estimated error left, and the passes (mixed form)
+  double* refine_resid;      // [0] max estimated error left, [1] refinement passes, [2] unconverged
+                             // (system, step) pairs (64-bit integers in [1], [2]; mixed form)
+  float* sys_err;            // per system: max over steps of the estimated relative error left (mixed form)
   float2* rres;              // FP32-rounded refinement residuals, laid out like G (mixed form)
   int* mdone;                // per system: 1 once its refinement has finished this step (mixed form)
   float* mrel;               // per system: relative size of its last correction (mixed form)
@@ -80,6 +89,7 @@ struct DevJob {
   double2* phi_all;          // [m][...] or null
   double2* W;                // cross fields at transfer nodes [(tr_off+x)*Q+q]*L+l
   double2* Gt;               // transfer-node spectra (same layout)
+  double* ginc;              // m = 1 time samples sign chi_k u^i at the active transfer nodes [a][NT]
   double2* E;                // cross matrices
   double2* Vobs;             // [z][q][l]
   double* traces;            // [z][tout]

@@ -94,7 +94,9 @@ extern "C" fthms_status fthms_assemble_self_noalloc(const fthms_curve* curve, co
   if (s != FTHMS_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
 
-  // Host-side tables on the stack (no heap, no device allocation).
+  // Host-side tables on the stack (no heap, no device allocation).  A copy from pageable host memory
+  // has been staged by the time cudaMemcpyAsync returns, so these buffers may go out of scope after
+  // the loop below; the kernels stay queued on the stream.
   double nodes[4 * kNoallocMaxN];
   const double tc = 0.5 * (arc->theta_a + arc->theta_b), half = 0.5 * (arc->theta_b - arc->theta_a);
   for (int i = 0; i < N; ++i) {

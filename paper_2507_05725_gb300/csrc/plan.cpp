@@ -128,10 +128,18 @@ int build_plan(const fthms_curve* curves, int ncurves, const fthms_arc* arcs, in
     err = "cross_mode must be 0 (stored cross rows) or 1 (evaluated every step)";
     return FTHMS_EINVAL;
   }
-  if (opt->precision != 0 && opt->precision != 1) {
-    err = "precision must be 0 (FP64) or 1 (FP32 factors with double-float refinement and cross apply)";
+  if (opt->precision < 0 || opt->precision > 2) {
+    err = "precision must be 0 (FP64), 1 (FP32 factors with double-float refinement and cross apply) or 2 (the "
+          "same with FP64 small-argument Hankel series, refinement residuals and FFT butterflies)";
     return FTHMS_ENOTIMPL;
   }
+  if (!(opt->refine_tol >= 0.0) || opt->refine_max < 0 || opt->refine_max > 16 ||
+      (opt->refine_fallback != 0 && opt->refine_fallback != 1)) {
+    err = "refine_tol must be >= 0, refine_max in [0, 16] and refine_fallback 0 or 1";
+    return FTHMS_EINVAL;
+  }
+  if (p.opt.refine_tol == 0.0) p.opt.refine_tol = 1e-12;
+  if (p.opt.refine_max == 0) p.opt.refine_max = 3;
   if (opt->L < 3 || !(opt->W > 0) || opt->M < 1 || opt->Q < 1 || !(opt->H > 0) ||
       !is_pow2(opt->n_period) || opt->n_period < 16 || opt->n_period > 16384 || opt->n_obs < 0 ||
       opt->n_tout < 0 || (opt->n_obs > 0 && !opt->obs_xy)) {
@@ -150,10 +158,25 @@ int build_plan(const fthms_curve* curves, int ncurves, const fthms_arc* arcs, in
     err = "signal kind must be 0 (point source) or 1 (plane wave)";
     return FTHMS_EINVAL;
   }
-  if (!(sig->width > 0)) {
-    err = "signal width must be positive";
-    return FTHMS_EINVAL;
+  if (sig->n_t == 0) {
+    if (!(sig->width > 0)) {
+      err = "signal width must be positive";
+      return FTHMS_EINVAL;
+    }
+  } else {
+    if (sig->n_t < 8 || sig->n_t > (1 << 24) || !sig->f || !(sig->dt > 0) || !std::isfinite(sig->t0) ||
+        !(sig->band > 0) || !std::isfinite(sig->band)) {
+      err = "sampled signal needs n_t in [8, 2^24], samples, dt > 0, a finite t0 and band > 0";
+      return FTHMS_EINVAL;
+    }
+    p.sig_f.assign(sig->f, sig->f + sig->n_t);
+    for (double v : p.sig_f)
+      if (!std::isfinite(v)) {
+        err = "sampled signal has a non-finite sample";
+        return FTHMS_EINVAL;
+      }
   }
+  p.sig.f = nullptr;   // the samples live in p.sig_f (the caller's array may be freed)
   p.curves.resize(ncurves);
   for (int c = 0; c < ncurves; ++c) {
     const fthms_curve& cv = curves[c];
@@ -398,7 +421,7 @@ int build_plan(const fthms_curve* curves, int ncurves, const fthms_arc* arcs, in
   p.sys_order.resize(p.sys.size());
   for (size_t s = 0; s < p.sys.size(); ++s) p.sys_order[s] = (int)s;
   std::stable_sort(p.sys_order.begin(), p.sys_order.end(), [&](int a, int b) { return p.sys[a].N > p.sys[b].N; });
-  if (p.opt.precision == 1)
+  if (p.opt.precision >= 1)
     for (int s : p.sys_order)
       for (int r0 = 0; r0 < p.sys[s].N; r0 += 32) p.rchunks.push_back(ResidChunk{s, r0});
 
@@ -608,23 +631,25 @@ void arc_nodes(const Curve& c, double theta_a, double theta_b, int N, std::vecto
 size_t plan_device_bytes(const Plan& p) {
   size_t b = 0;
   b += (size_t)p.mat_total * 16;                 // A / LU
-  if (p.opt.precision == 1)                      // FP32 factors, FP32 residuals, refinement state
-    b += (size_t)p.mat_total * 8 + (size_t)p.piv_total * 8 + (size_t)p.vec_total * (8 + 16) + p.sys.size() * 8 +
+  if (p.opt.precision >= 1)                      // FP32 factors, FP32 residuals, refinement state
+    b += (size_t)p.mat_total * 8 + (size_t)p.piv_total * 8 + (size_t)p.vec_total * (8 + 16) + p.sys.size() * 12 +
          p.rchunks.size() * sizeof(ResidChunk);
+  b += p.sig_f.size() * 8;                       // samples of a sampled signal
   b += (size_t)p.piv_total * 4;                  // pivots
   b += (size_t)p.rlog_total * 8;                 // self log tables
   b += (size_t)p.vec_total * 16 * 3;             // G, phi (current), phi sum
   if (p.opt.keep_densities) b += (size_t)p.vec_total * 16 * p.M;
   b += (size_t)p.spec_total * 16 * 2;            // W and Gt on transfer meshes
+  b += p.act_idx.size() * (size_t)p.NT * 8;      // m = 1 time samples at the active transfer nodes
   if (p.opt.cross_mode == 0) b += (size_t)p.e_total * 16;   // stored cross matrices
-  b += (size_t)p.restr_total * (p.opt.precision == 1 ? 16 : 8);
+  b += (size_t)p.restr_total * (p.opt.precision >= 1 ? 16 : 8);
   b += (size_t)p.n_obs * p.Q * p.L * 16 + (size_t)p.n_obs * p.n_tout * 8;
   b += p.node_t.size() * 32 + p.tgts.size() * sizeof(CrossTgt) + p.blks.size() * sizeof(CrossBlk) +
        p.asms.size() * sizeof(CrossAsm) + p.self_tiles.size() * sizeof(SelfTile) + p.sys.size() * (sizeof(SysDesc) + sizeof(int)) + p.slices.size() * sizeof(ApplySlice) + p.grp_res_off.size() * 8;
-  if (p.opt.precision == 1 || p.opt.cross_mode == 1) b += (size_t)p.res_total * p.Q * 16;   // per-row cross sums
+  if (p.opt.precision >= 1 || p.opt.cross_mode == 1) b += (size_t)p.res_total * p.Q * 16;   // per-row cross sums
   if (p.opt.cross_mode == 1)
     b += (size_t)p.wn_total * 8 + p.otf.size() * sizeof(CrossOtf) + p.otf_res_off.size() * 8 + p.wn_off.size() * 8;
-  b += p.win.size() * 8 + (size_t)p.Q * p.L * 32 + (size_t)p.K * (p.opt.precision == 1 ? 16 : 8) + p.chi.size() * 8;
+  b += p.win.size() * 8 + (size_t)p.Q * p.L * 32 + (size_t)p.K * (p.opt.precision >= 1 ? 16 : 8) + p.chi.size() * 8;
   return b;
 }
 

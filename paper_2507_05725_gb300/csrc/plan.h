@@ -28,6 +28,7 @@ struct Plan {
   std::vector<Curve> curves;
   std::vector<ArcGeo> arcs;
   fthms_signal sig{};
+  std::vector<double> sig_f;  // samples of a sampled signal (copied from the caller)
   fthms_options opt{};
   std::vector<double> obs;  // 2 * n_obs
   int P = 0, L = 0, M = 0, Q = 0, K = 0, NT = 0, n_obs = 0, n_tout = 0;

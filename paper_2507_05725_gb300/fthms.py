@@ -35,7 +35,9 @@ class fthms_arc(C.Structure):
 
 class fthms_signal(C.Structure):
     _fields_ = [("kind", C.c_int), ("z0", C.c_double * 2), ("dir", C.c_double * 2), ("sign", C.c_double),
-                ("amp", C.c_double), ("carrier", C.c_double), ("centre", C.c_double), ("width", C.c_double)]
+                ("amp", C.c_double), ("carrier", C.c_double), ("centre", C.c_double), ("width", C.c_double),
+                ("n_t", C.c_int), ("t0", C.c_double), ("dt", C.c_double), ("f", C.POINTER(C.c_double)),
+                ("band", C.c_double)]
 
 
 class fthms_options(C.Structure):
@@ -43,7 +45,8 @@ class fthms_options(C.Structure):
                 ("N_ppw", C.c_double), ("M", C.c_int), ("Q", C.c_int), ("H", C.c_double), ("n_period", C.c_int),
                 ("interior", C.c_int), ("n_obs", C.c_int), ("obs_xy", C.POINTER(C.c_double)),
                 ("n_tout", C.c_int), ("tout0", C.c_double), ("dtout", C.c_double), ("precision", C.c_int),
-                ("keep_densities", C.c_int), ("cross_mode", C.c_int)]
+                ("keep_densities", C.c_int), ("cross_mode", C.c_int), ("refine_tol", C.c_double),
+                ("refine_max", C.c_int), ("refine_fallback", C.c_int)]
 
 
 class fthms_stats_t(C.Structure):
@@ -52,7 +55,7 @@ class fthms_stats_t(C.Structure):
                 ("cross_entries", C.c_double), ("hankel_evals", C.c_double), ("h2d_bytes", C.c_size_t),
                 ("lu_flops", C.c_double), ("solve_flops", C.c_double), ("apply_flops", C.c_double),
                 ("precision", C.c_int), ("max_refine_resid", C.c_double),
-                ("refine_passes", C.c_double)]
+                ("refine_passes", C.c_double), ("n_unconverged", C.c_longlong), ("fallback_runs", C.c_int)]
 
 
 STAGES = ["tables", "assemble_self", "lu", "cross_assemble", "incident", "restrict", "solve", "cross_apply",
@@ -81,6 +84,7 @@ def _load():
         "fthms_densities_dev": (st, [vp, C.c_int, C.c_int, C.c_int, vp, C.c_size_t]),
         "fthms_node_counts": (st, [vp, C.POINTER(C.c_int), C.c_size_t]),
         "fthms_stats": (st, [vp, C.POINTER(fthms_stats_t)]),
+        "fthms_result_errors": (st, [vp, C.POINTER(C.c_double), C.c_size_t]),
         "fthms_release": (st, [vp]),
         "fthms_last_error": (C.c_char_p, []),
         "fthms_bessel0": (st, [vp, vp, vp, vp, C.c_int, vp]),
@@ -116,7 +120,7 @@ EXPORTED = ["fthms_create", "fthms_destroy", "fthms_prepare", "fthms_run", "fthm
             "fthms_profile", "fthms_stage_times", "fthms_assemble_self_noalloc", "fthms_server_create",
             "fthms_server_submit", "fthms_server_poll", "fthms_server_wait", "fthms_server_result",
             "fthms_server_latency", "fthms_server_release", "fthms_server_destroy", "fthms_use_graph",
-            "fthms_autotune", "fthms_plan_info"]
+            "fthms_autotune", "fthms_plan_info", "fthms_result_errors"]
 
 
 def _check(status):
@@ -142,15 +146,24 @@ class Marshalled:
         arcs = problem["arcs"]
         self.arcs = (fthms_arc * len(arcs))(*[fthms_arc(int(c), float(a), float(b)) for c, a, b in arcs])
         s = problem["signal"]
+        smp = s.get("samples")
+        if smp is not None:
+            fs = np.ascontiguousarray(np.asarray(smp["f"], dtype=np.float64))
+            self._keep.append(fs)
+            sampled = (fs.size, float(smp["t0"]), float(smp["dt"]), _dptr(fs), float(smp["band"]))
+        else:
+            sampled = (0, 0.0, 0.0, None, 0.0)
         self.signal = fthms_signal(int(s["kind"]), (C.c_double * 2)(*s["z0"]), (C.c_double * 2)(*s["dir"]),
-                                   s["sign"], s["amp"], s["carrier"], s["centre"], s["width"])
+                                   s["sign"], s["amp"], s["carrier"], s["centre"], s["width"], *sampled)
         o = problem["options"]
         obs = np.ascontiguousarray(np.asarray(o["obs"], dtype=np.float64).reshape(-1))
         self._keep.append(obs)
         self.options = fthms_options(o["W"], o["L"], o["N_fixed"], o["N_min"], o["N_off"], o["N_ppw"], o["M"],
                                      o["Q"], o["H"], o["n_period"], o["interior"], obs.size // 2,
                                      _dptr(obs) if obs.size else None, o["n_tout"], o["tout0"], o["dtout"],
-                                     int(precision), int(keep_densities), int(o.get("cross_mode", 0)))
+                                     int(precision), int(keep_densities), int(o.get("cross_mode", 0)),
+                                     float(o.get("refine_tol", 0.0)), int(o.get("refine_max", 0)),
+                                     int(o.get("refine_fallback", 0)))
         self.ncurves, self.narcs = len(curves), len(arcs)
 
 
@@ -230,6 +243,13 @@ def fthms_stats(req):
     s = fthms_stats_t()
     _check(LIB.fthms_stats(req, C.byref(s)))
     return {k: getattr(s, k) for k, _ in fthms_stats_t._fields_}
+
+
+def fthms_result_errors(req, narcs, L):
+    """[narcs, L-1] estimated relative error left in each (arc, omega) result (mixed forms; 0 in FP64)."""
+    out = np.empty((narcs, L - 1), dtype=np.float64)
+    _check(LIB.fthms_result_errors(req, _dptr(out), out.size))
+    return out
 
 
 def fthms_autotune(req, reps=3):
@@ -321,6 +341,9 @@ class Job:
 
     def stats(self):
         return fthms_stats(self.req)
+
+    def result_errors(self):
+        return fthms_result_errors(self.req, self.P, self.L)
 
     def release(self):
         if self.req is not None:

@@ -51,7 +51,7 @@ def test_invalid_geometry_and_options(F):
     bad = copy.deepcopy(p)                          # unknown cross mode
     bad["options"]["cross_mode"] = 2
     assert _status(F, lambda: F.fthms_prepare(ctx, F.Marshalled(bad)))[0] == F.FTHMS_EINVAL
-    st, _ = _status(F, lambda: F.fthms_prepare(ctx, F.Marshalled(p, precision=2)))
+    st, _ = _status(F, lambda: F.fthms_prepare(ctx, F.Marshalled(p, precision=3)))
     assert st == F.FTHMS_ENOTIMPL
     F.fthms_destroy(ctx)
 

@@ -393,3 +393,37 @@ def test_autotune_keeps_results_bitwise(F, ctx, precision):
     finally:
         a.release()
         b.release()
+
+
+# ---- full-size third configuration (12-arc star cavity) against stored oracle values --------------
+
+def _golden_c3():
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "config3_m2.json")
+    with open(path) as f:
+        return json.load(f)
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_config3_full_size_second_step(F, ctx, precision):
+    """Full-size 12-arc star cavity (N 32..760, 2048 solved frequencies, Q = 4 windows, point-source data,
+    cross rows evaluated every step, in the bench's launch configuration): m = 2 densities of two receiving
+    arcs, all four windows, at six frequencies across (0, 200] including the largest system, against the
+    oracle values of tests/golden/make_config3_m2.py (every m = 1 density, the cross fields of all other
+    arcs, synthesis, windowed forward transform, restriction and solve)."""
+    gold = _golden_c3()
+    job = F.Job(ctx, wl.config3(M=2), precision=precision).run().wait()
+    num = den = 0.0
+    for key, v in gold["samples"].items():
+        k, l = (int(x) for x in key.split(":"))
+        ref = np.asarray(v["re"]) + 1j * np.asarray(v["im"])          # (Q, N)
+        for q in range(ref.shape[0]):
+            d = job.densities(k, 2, q)[l]
+            assert d.shape == ref[q].shape
+            num += float(np.sum(np.abs(d - ref[q]) ** 2))
+            den += float(np.sum(np.abs(ref[q]) ** 2))
+    st = job.stats()
+    job.release()
+    rel = math.sqrt(num / den)
+    assert rel < (DENSITY_TOL if precision == 0 else MIXED_TOL), rel
+    if precision:
+        assert st["n_unconverged"] == 0

@@ -307,3 +307,51 @@ def test_exterior_disk_mie_series():
     tout = np.arange(101) * 0.1
     ref = g.inverse_at(Vm, tout)
     assert np.max(np.abs(r.traces - ref)) < 2e-3 * np.max(np.abs(ref))
+
+
+# ---- Sampled signals ---------------------------------------------------------------------------
+
+def test_sampled_signal_reproduces_polynomials_of_degree_seven():
+    """The 8-point Lagrange reading is exact for polynomials of degree <= 7 wherever the stencil lies
+    inside the samples (a wrong weight, node offset or index shift fails this)."""
+    t0, dt, n = -1.3, 0.05, 200
+    ts = t0 + dt * np.arange(n)
+    p = np.polynomial.Polynomial([0.3, -1.1, 0.7, 0.25, -0.4, 0.05, 0.11, -0.02])
+    smp = {"t0": t0, "dt": dt, "f": p(ts), "band": 1.0}
+    t = np.linspace(t0 + 4 * dt, t0 + (n - 5) * dt, 777)
+    assert np.max(np.abs(tr.sampled_signal(smp, t) - p(t))) < 1e-11 * np.max(np.abs(p(ts)))
+    scale = np.max(np.abs(p(ts)))
+    assert np.max(np.abs(tr.sampled_signal(smp, ts[3:-4]) - p(ts[3:-4]))) < 1e-13 * scale   # samples kept
+    assert np.all(tr.sampled_signal(smp, np.array([t0 - 1e-9, t0 + n * dt])) == 0.0)         # zero outside
+
+
+def test_sampled_copy_of_the_analytic_signal():
+    """A sampled copy of f(t) = sin(10t) exp(-((t-6)/2)^2) (dt = 0.01) reproduces f to the interpolation
+    error max|f^(8)| dt^8 max|prod_m (x - m)| / 8! ~ 10^8 dt^8 36/40320 ~ 1e-11, and the point-source
+    field and plane wave built from the samples match the analytic ones."""
+    sig = {"kind": 0, "z0": [2.0, 0.5], "dir": [0.6, 0.8], "amp": 1.0, "carrier": 10.0, "centre": 6.0,
+           "width": 2.0}
+    dt = 0.01
+    ts = -10.0 + dt * np.arange(int(round(32.0 / dt)) + 1)          # [-10, 22]: 8 widths on either side
+    smp = {"t0": -10.0, "dt": dt, "f": tr.signal_f(sig, ts), "band": 10.0 + 8.0 / 2.0}
+    sigs = dict(sig, samples=smp)
+    t = np.linspace(-5.0, 18.0, 4001)
+    assert np.max(np.abs(tr.signal_f(sigs, t) - tr.signal_f(sig, t))) < 3e-11
+    x = np.array([[1.0, 0.0], [-0.5, 0.8]])
+    tt = np.array([3.0, 5.5, 7.25, 9.0, 14.0])
+    u_a = tr.incident_field(sig, x, tt)
+    u_s = tr.incident_field(sigs, x, tt)
+    assert np.max(np.abs(u_s - u_a)) < 1e-10 * np.max(np.abs(u_a))
+    sig_pw = dict(sig, kind=1)
+    assert np.max(np.abs(tr.incident_field(dict(sig_pw, samples=smp), x, tt) - tr.incident_field(sig_pw, x, tt))) < 3e-11
+
+
+def test_multipulse_samples_follow_the_pulse_formula():
+    """The multi-pulse profile (eq. multi) is five copies of the pulse of eq. planewave 10 apart."""
+    smp = wl.multipulse_samples(t0=0.0, dt=0.01, t_end=60.0)
+    sig = {"kind": 1, "samples": smp}
+    for j in range(5):
+        s = 2.0 + 10.0 * j + np.array([2.1, 3.0, 3.77])            # ell = s - 2 - 10 j near the pulse centre
+        ell = s - 2.0 - 10.0 * j
+        ref = -np.sin(4.0 * ell) * np.exp(-1.6 * (ell - 3.0) ** 2)
+        assert np.max(np.abs(tr.signal_f(sig, s) - ref)) < 1e-9

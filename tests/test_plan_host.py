@@ -3,6 +3,8 @@ device-memory accounting, without a GPU."""
 import copy
 import math
 
+import numpy as np
+
 import pytest
 
 import workloads as wl
@@ -63,4 +65,27 @@ def test_validation_without_a_gpu(F):
     bad = copy.deepcopy(p)                          # unknown cross mode
     bad["options"]["cross_mode"] = 2
     assert _status(F, bad)[0] == F.FTHMS_EINVAL
-    assert _status(F, p, precision=2)[0] == F.FTHMS_ENOTIMPL
+    assert _status(F, p, precision=3)[0] == F.FTHMS_ENOTIMPL
+    bad = copy.deepcopy(p)                          # refinement options out of range
+    bad["options"]["refine_max"] = 17
+    assert _status(F, bad, precision=1)[0] == F.FTHMS_EINVAL
+    bad["options"]["refine_max"] = 3
+    bad["options"]["refine_tol"] = -1.0
+    assert _status(F, bad, precision=1)[0] == F.FTHMS_EINVAL
+    smp = wl.multipulse_samples(t_end=20.0)          # sampled signals: too few samples, bad step or band
+    for key, val in (("f", smp["f"][:7]), ("dt", 0.0), ("band", 0.0)):
+        bad = wl.with_samples(p, dict(smp, **{key: val}))
+        st, msg = _status(F, bad)
+        assert st == F.FTHMS_EINVAL and "sampled" in msg
+    bad = wl.with_samples(p, dict(smp, f=np.where(np.arange(smp["f"].size) == 5, np.nan, smp["f"])))
+    assert _status(F, bad)[0] == F.FTHMS_EINVAL
+
+
+def test_sampled_signal_plans_like_the_analytic_one(F):
+    """A job whose signal is given by samples plans to the same systems; its device memory holds the
+    samples as well."""
+    p = wl.random_small(3, kind=1)
+    smp = wl.multipulse_samples(t_end=30.0)
+    b0, n0 = F.fthms_plan_info(F.Marshalled(p))
+    b1, n1 = F.fthms_plan_info(F.Marshalled(wl.with_samples(p, smp)))
+    assert n0 == n1 and b1 == b0 + 8 * smp["f"].size

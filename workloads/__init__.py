@@ -12,8 +12,9 @@ A problem is a plain dict:
 * ``arcs``: list of ``(curve_index, theta_a, theta_b)`` with ``theta_b > theta_a`` (may exceed 2 pi);
   consecutive arcs of one closed curve overlap their neighbours only (Section 3.1).
 * ``signal``: incident field ``u^i``; ``kind`` 0 = point source at ``z0``, 1 = plane wave along ``dir``;
-  time signal ``f(t) = amp sin(carrier t) exp(-((t - centre)/width)^2)``; boundary data is
-  ``sign * u^i`` (``sign = -1`` for scattering, ``+1`` when the boundary carries the field itself).
+  time signal ``f(t) = amp sin(carrier t) exp(-((t - centre)/width)^2)``, or samples of f given by an
+  optional ``samples`` entry ``{"t0", "dt", "f", "band"}``; boundary data is ``sign * u^i``
+  (``sign = -1`` for scattering, ``+1`` when the boundary carries the field itself).
 * ``options``: ``W`` (max frequency), ``L`` (frequencies ``omega_l = l W/(L-1)``, l = 0..L-1),
   the per-arc node-count rule ``N = N_fixed`` if nonzero else
   ``max(N_min, ceil(N_ppw * omega * arclength) + N_off)``, ``M`` multiple-scattering steps,
@@ -29,6 +30,7 @@ import numpy as np
 __all__ = [
     "circle", "ellipse", "kite", "star", "split_closed_curve", "config1", "config2",
     "config2_reduced", "config3", "config3_reduced", "random_small", "served_requests", "problem_summary",
+    "multipulse_samples", "with_samples",
 ]
 
 
@@ -248,6 +250,27 @@ def served_requests(seed, n, wmax=(20.0, 60.0)):
         out.append({"name": f"served-{seed}-{r}", "curves": curves, "arcs": arcs, "signal": signal,
                     "options": options})
     return out
+
+
+def multipulse_samples(t0=0.0, dt=0.01, t_end=60.0, t_lag=2.0, pulses=5, spacing=10.0):
+    """Samples of the multi-pulse time profile of Section 5 (eq. multi: five copies of the pulse u3 of eq.
+    planewave, 10 time units apart): f(s) = sum_j -sin(4 (s - t_lag - spacing j)) exp(-1.6 (s - t_lag -
+    spacing j - 3)^2) at s = t0 + i dt, for a plane wave u = f(t - x.d).  Returns the "samples" entry of a
+    signal dict; band = 4 + 8 sqrt(1.6) is the carrier plus eight Gaussian widths."""
+    n = int(round((t_end - t0) / dt)) + 1
+    s = t0 + dt * np.arange(n)
+    f = np.zeros(n)
+    for j in range(pulses):
+        ell = s - t_lag - spacing * j
+        f += -np.sin(4.0 * ell) * np.exp(-1.6 * (ell - 3.0) ** 2)
+    return {"t0": float(t0), "dt": float(dt), "f": f, "band": 4.0 + 8.0 * math.sqrt(1.6)}
+
+
+def with_samples(problem, samples):
+    """The same problem with its signal given by samples (the analytic parameters are then unused)."""
+    q = dict(problem)
+    q["signal"] = dict(problem["signal"], samples=samples)
+    return q
 
 
 def problem_summary(p):
