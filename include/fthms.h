@@ -132,7 +132,16 @@ typedef struct {
  *  refine_fallback : mixed forms: 0 = a job in which some system did not meet refine_tol within
  *              refine_max passes finishes with those results and fthms_wait returns FTHMS_ENOCONV;
  *              1 = fthms_wait then runs the whole job again in FP64 (precision 0) and returns its
- *              status (the FP64 results replace the mixed ones; fthms_stats reports the fallback). */
+ *              status (the FP64 results replace the mixed ones; fthms_stats reports the fallback).
+ *  omega_rank, omega_ranks : frequency partition of one job over omega_ranks ranks (one GPU each; 0 or 1
+ *              = no partition).  The per-frequency sub-problems of a step are independent (Section 3), so
+ *              rank r assembles, factors and solves only the solved frequencies l in
+ *              [1 + r (L-1)/R, 1 + (r+1)(L-1)/R) (R = omega_ranks), and holds only their device memory; the
+ *              one coupling, the omega -> t synthesis of every step (eq. TDsol), is a sum over all
+ *              frequencies, so the ranks add their partial time samples with the all-reduce given to
+ *              fthms_set_allreduce before the windowed forward transforms (eq. Fourierk) of their own
+ *              frequencies.  fthms_densities then covers the rank's frequencies only; the traces are
+ *              summed across ranks the same way. */
 typedef struct {
   double W;
   int L;
@@ -152,6 +161,7 @@ typedef struct {
   double refine_tol;
   int refine_max;
   int refine_fallback;
+  int omega_rank, omega_ranks;
 } fthms_options;
 
 typedef struct {
@@ -199,8 +209,8 @@ fthms_status fthms_prepare(fthms_ctx* ctx, const fthms_curve* curves, int ncurve
 /* Plan a job on the host only: the same validation as fthms_prepare (same status codes and
  * messages), without a device, allocation or upload.  *device_bytes receives the device memory the job
  * would hold (what fthms_prepare charges against a context budget) and *n_systems its number of
- * (arc, omega) systems; either pointer may be NULL.  For capacity planning (no counterpart in the
- * paper). */
+ * (arc, omega) systems (of this rank's frequencies for a partitioned job); either pointer may be NULL.
+ * For capacity planning (no counterpart in the paper). */
 fthms_status fthms_plan_info(const fthms_curve* curves, int ncurves, const fthms_arc* arcs, int narcs,
                              const fthms_signal* signal, const fthms_options* options,
                              size_t* device_bytes, int* n_systems);
@@ -229,7 +239,8 @@ fthms_status fthms_wait(fthms_req* req, int timeout_ms);
 fthms_status fthms_traces(fthms_req* req, double* out, size_t cap);
 
 /* Densities phi_{j,m,q}(omega_l)[i] of arc j: m in 1..M (requires keep_densities) or m = 0 for
- * the sum over m; q in 0..Q-1.  Layout: for l = 1..L-1, N_j(omega_l) complex values at the
+ * the sum over m; q in 0..Q-1.  Layout: for l = 1..L-1 (a frequency-partitioned job: the rank's own l,
+ * in increasing order), N_j(omega_l) complex values at the
  * first-kind nodes t_i = cos((2i+1) pi/(2N)), i = 0..N-1, where phi(t) = Psi(x(t)) |x'(t)|
  * sqrt(1 - t^2) is the smooth factor of eq. singularity.  Needs 2 sum_l N_j(omega_l) doubles;
  * the size is written to *needed (may be NULL).  Waits for the job. */
@@ -275,6 +286,17 @@ enum {
  * (NULL allowed) receives the four choices.  The job's earlier results are overwritten: call
  * fthms_run afterwards.  Not in the paper (a batching aid of this library). */
 fthms_status fthms_autotune(fthms_req* req, int reps, int* shapes);
+
+/* Sum across the ranks of a frequency-partitioned job (options omega_ranks > 1): called on the host from
+ * fthms_run, M times per run (after each step's partial synthesis, with buf_dev = the n_act x N_T time
+ * samples of the active transfer nodes, and for the traces, n_obs x n_tout), it must replace buf_dev
+ * (count doubles, device memory of the job) by its elementwise sum over all ranks, in order on
+ * cuda_stream (e.g. an in-place NCCL all-reduce enqueued on that stream) or before it returns.  user is
+ * passed through.  Every rank must call fthms_run the same number of times.  fthms_run returns
+ * FTHMS_EINVAL for a partitioned job without an all-reduce; a partitioned job is never captured into a
+ * CUDA graph (fthms_use_graph is ignored). */
+typedef void (*fthms_allreduce_fn)(double* buf_dev, size_t count, void* cuda_stream, void* user);
+fthms_status fthms_set_allreduce(fthms_req* req, fthms_allreduce_fn fn, void* user);
 
 /* enable != 0: fthms_run captures the job's whole pipeline (all stages and steps) into a CUDA graph on
  * its first run and replays it afterwards as one launch; the graph is rebuilt never (the job's inputs

@@ -86,11 +86,14 @@ class Setup:
         self.obs = np.asarray(o["obs"], dtype=np.float64).reshape(-1, 2)
 
 
-def run_oracle(problem, M=None, keep_G=False, cache_cross=True, arcs_phi=None):
+def run_oracle(problem, M=None, keep_G=False, cache_cross=True, arcs_phi=None, omega_part=None, allreduce=None):
     """Run Algorithm 1 on the discrete problem; returns an OracleResult.
 
     M overrides the number of multiple-scattering steps; ``arcs_phi`` limits which arcs' densities
-    are kept (all by default)."""
+    are kept (all by default).  ``omega_part = (r, R)`` runs rank r's share of a frequency partition: the
+    solved frequencies l in [1 + r (L-1)/R, 1 + (r+1)(L-1)/R) (the per-frequency sub-problems of a step
+    are independent, Section 3); the omega -> t synthesis of every step and the traces are then partial
+    sums over those frequencies, which ``allreduce(array) -> array`` must sum across the ranks."""
     S = Setup(problem)
     o = problem["options"]
     sig = problem["signal"]
@@ -99,11 +102,17 @@ def run_oracle(problem, M=None, keep_G=False, cache_cross=True, arcs_phi=None):
     M = o["M"] if M is None else M
     res = OracleResult(Ntab=S.Ntab, Nmax=S.Nmax, chi=S.chi, grid=tg)
     keep = set(range(P)) if arcs_phi is None else set(arcs_phi)
+    if omega_part is None:
+        own = range(1, L)
+    else:
+        r, R = omega_part
+        own = range(1 + r * (L - 1) // R, 1 + (r + 1) * (L - 1) // R)
+    total = (lambda a: a) if omega_part is None else allreduce
 
     # Self matrices, factored once per (arc, omega) and reused for every m and q (Alg. 1, line 8).
     lu = {}
     for j in range(P):
-        for l in range(1, L):
+        for l in own:
             A = ker.self_matrix(S.arcs[j], int(S.Ntab[j, l]), tg.omega[l])
             lu[(j, l)] = scipy.linalg.lu_factor(A)
 
@@ -113,7 +122,7 @@ def run_oracle(problem, M=None, keep_G=False, cache_cross=True, arcs_phi=None):
         """Gt [Nmax_k, Q, L] on the transfer mesh -> {l: (Q, N_k(l))} on the solve nodes."""
         out = {}
         nmax = int(S.Nmax[k])
-        for l in range(1, L):
+        for l in own:
             n = int(S.Ntab[k, l])
             if (n, nmax) not in Rcache:
                 Rcache[(n, nmax)] = ker.restriction(n, nmax)
@@ -154,7 +163,7 @@ def run_oracle(problem, M=None, keep_G=False, cache_cross=True, arcs_phi=None):
     for m in range(1, M + 1):
         phi = {}
         for j in range(P):
-            for l in range(1, L):
+            for l in own:
                 phi[(j, l)] = scipy.linalg.lu_solve(lu[(j, l)], G[(j, l)].T).T     # (Q, N)
                 if j in keep:
                     res.phi[(m, j, l)] = phi[(j, l)]
@@ -163,7 +172,7 @@ def run_oracle(problem, M=None, keep_G=False, cache_cross=True, arcs_phi=None):
         # Potentials of every arc at the other arcs' transfer nodes (masked per eq. vtilde) and at
         # the observation points (output sum of eq. mult-scatt-int, in the frequency domain).
         Wk = [np.zeros((int(S.Nmax[k]), Q, L), dtype=np.complex128) for k in range(P)]
-        for l in range(1, L):
+        for l in own:
             for j in range(P):
                 Vobs[:, :, l] += obs_block(l, j) @ phi[(j, l)].T
                 for k in range(P):
@@ -177,11 +186,11 @@ def run_oracle(problem, M=None, keep_G=False, cache_cross=True, arcs_phi=None):
         # g_{k,m+1} = -chi_k sum_j vtilde (eq. criterion_int2), back to the frequency domain.
         G = {}
         for k in range(P):
-            w = tg.inverse(Wk[k])
+            w = total(tg.inverse(Wk[k]))
             g = -S.chi[k][:, None] * w
             for l, v in restrict(k, tg.forward(g)).items():
                 G[(k, l)] = v
     res.Vobs = Vobs
     tout = o["tout0"] + o["dtout"] * np.arange(o["n_tout"])
-    res.traces = tg.inverse_at(Vobs, tout)
+    res.traces = total(tg.inverse_at(Vobs, tout))
     return res

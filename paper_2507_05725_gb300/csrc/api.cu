@@ -111,6 +111,8 @@ struct fthms_req {
   std::string conv_msg;
   int fallback_runs = 0;           // runs repeated in FP64 after a refinement that did not converge
   bool plain_apply_fits = true;    // the FP64 stored-row apply fits shared memory (FP64 fallback possible)
+  fthms_allreduce_fn allreduce = nullptr;   // sum across the ranks of a frequency-partitioned job
+  void* allreduce_user = nullptr;
 };
 
 namespace {
@@ -167,7 +169,7 @@ fthms_status upload_job(fthms_req* r) {
   DevJob& J = r->J;
   J.P = p.P; J.L = p.L; J.Q = p.Q; J.K = p.K; J.NT = p.NT; J.M = p.M;
   J.n_obs = p.n_obs; J.n_tout = p.n_tout;
-  J.nsys = (int)p.sys.size();
+  J.nsys = (int)p.sys_order.size();   // systems of this rank's frequencies (all, unpartitioned)
   J.n_act = (int)p.act_idx.size();
   J.n_grp = (int)p.grps.size();
   J.n_asm = (int)p.asms.size();
@@ -371,7 +373,9 @@ fthms_status enqueue_stages(fthms_req* r, bool bracket = true);
 // Run the pipeline: directly, or (use_graph, profiling off) through a CUDA graph captured on the first
 // run and replayed afterwards (one launch for the whole job).
 fthms_status enqueue(fthms_req* r) {
-  if (!r->use_graph || r->profiling) return enqueue_stages(r);
+  if (r->plan.ranks > 1 && !r->allreduce)
+    return fail(FTHMS_EINVAL, "fthms_run: a frequency-partitioned job needs fthms_set_allreduce");
+  if (!r->use_graph || r->profiling || r->plan.ranks > 1) return enqueue_stages(r);
   TRY(flush_marks(r));
   cudaStream_t st = r->stream;
   if (!r->graph) {
@@ -415,7 +419,7 @@ fthms_status enqueue_stages(fthms_req* r, bool bracket) {
   CK(cudaMemsetAsync(J.W, 0, (size_t)r->plan.spec_total * sizeof(double2), st));
   CK(cudaMemsetAsync(J.Vobs, 0, (size_t)std::max(1, J.n_obs * J.Q * J.L) * sizeof(double2), st));
   CK(cudaMemsetAsync(J.refine_resid, 0, 3 * sizeof(double), st));
-  if (J.sys_err) CK(cudaMemsetAsync(J.sys_err, 0, (size_t)J.nsys * sizeof(float), st));
+  if (J.sys_err) CK(cudaMemsetAsync(J.sys_err, 0, r->plan.sys.size() * sizeof(float), st));
   TRY(stage(r, FTHMS_STAGE_INCIDENT, st, &nl, [&] { return launch_incident(J, st, &nl); }));
   TRY(stage(r, FTHMS_STAGE_RESTRICT, st, &nl, [&] { return launch_restrict(J, st, &nl); }));
   for (int m = 1; m <= J.M; ++m) {
@@ -424,11 +428,20 @@ fthms_status enqueue_stages(fthms_req* r, bool bracket) {
       return J.otf ? launch_cross_otf(J, st, &nl) : launch_cross_apply(J, st, &nl);
     }));
     if (m < J.M) {
-      TRY(stage(r, FTHMS_STAGE_SYNTH_FWD, st, &nl, [&] { return launch_synth_fwd(J, st, &nl); }));
+      if (r->plan.ranks > 1) {
+        // partial synthesis over this rank's frequencies, the ranks' sum, then the rest of the step
+        TRY(stage(r, FTHMS_STAGE_SYNTH_FWD, st, &nl, [&] { return launch_synth_partial(J, st, &nl); }));
+        if (J.n_act > 0) r->allreduce(J.ginc, (size_t)J.n_act * J.NT, st, r->allreduce_user);
+        TRY(stage(r, FTHMS_STAGE_SYNTH_FWD, st, &nl, [&] { return launch_fwd_after_sum(J, st, &nl); }));
+      } else {
+        TRY(stage(r, FTHMS_STAGE_SYNTH_FWD, st, &nl, [&] { return launch_synth_fwd(J, st, &nl); }));
+      }
       TRY(stage(r, FTHMS_STAGE_RESTRICT, st, &nl, [&] { return launch_restrict(J, st, &nl); }));
     }
   }
   TRY(stage(r, FTHMS_STAGE_TRACES, st, &nl, [&] { return launch_traces(J, st, &nl); }));
+  if (r->plan.ranks > 1 && J.n_obs * J.n_tout > 0)
+    r->allreduce(J.traces, (size_t)J.n_obs * J.n_tout, st, r->allreduce_user);
   if (bracket) {
     CK(cudaEventRecord(r->ev1, st));
     r->ran = true;
@@ -514,7 +527,7 @@ fthms_status fthms_plan_info(const fthms_curve* curves, int ncurves, const fthms
   const int st = build_plan(curves, ncurves, arcs, narcs, signal, options, plan, err);
   if (st != FTHMS_OK) return fail((fthms_status)st, "fthms_prepare: " + err);
   if (device_bytes) *device_bytes = plan.device_bytes;
-  if (n_systems) *n_systems = (int)plan.sys.size();
+  if (n_systems) *n_systems = (int)plan.sys_order.size();   // this rank's systems
   return FTHMS_OK;
 }
 
@@ -632,7 +645,8 @@ static fthms_status check_convergence(fthms_req* req) {
                      cudaMemcpyDeviceToHost, req->stream));
   CK(cudaStreamSynchronize(req->stream));
   if (bad == 0) return FTHMS_OK;
-  if (req->plan.opt.refine_fallback && req->plain_apply_fits) {
+  // (a frequency-partitioned job never falls back alone: its ranks would stop meeting in the all-reduce)
+  if (req->plan.opt.refine_fallback && req->plain_apply_fits && req->plan.ranks <= 1) {
     req->J.mixed = 0;
     req->J.fp64keep = 0;
     if (req->graph) {                  // the captured graph holds the mixed-form kernels
@@ -691,10 +705,10 @@ static fthms_status density_range(fthms_req* req, int arc, int m, int q, const d
   if (m > 0 && !p.opt.keep_densities)
     return fail(FTHMS_EINVAL, "fthms_densities: per-step densities need keep_densities = 1");
   size_t n = 0;
-  for (int l = 1; l < p.L; ++l) n += 2 * (size_t)p.Ntab[(size_t)arc * p.L + l];
+  for (int l = p.lb; l < p.le; ++l) n += 2 * (size_t)p.Ntab[(size_t)arc * p.L + l];
   if (needed) *needed = n;
-  const SysDesc& s0 = p.sys[(size_t)arc * (p.L - 1)];
-  const SysDesc& s1 = p.sys[(size_t)arc * (p.L - 1) + p.L - 2];
+  const SysDesc& s0 = p.sys[(size_t)arc * (p.L - 1) + p.lb - 1];      // this rank's first and last frequency
+  const SysDesc& s1 = p.sys[(size_t)arc * (p.L - 1) + p.le - 2];
   *first = s0.vec_off;
   *last = s1.vec_off + (long long)p.Q * s1.N;
   *base = m == 0 ? req->J.phi_sum : req->J.phi_all + (long long)(m - 1) * p.vec_total;
@@ -716,7 +730,7 @@ fthms_status fthms_densities(fthms_req* req, int arc, int m, int q, double* out,
   CK(cudaMemcpyAsync(h.data(), base + first, h.size() * sizeof(double2), cudaMemcpyDeviceToHost, req->stream));
   CK(cudaStreamSynchronize(req->stream));
   size_t o = 0;
-  for (int l = 1; l < p.L; ++l) {
+  for (int l = p.lb; l < p.le; ++l) {
     const SysDesc& s = p.sys[(size_t)arc * (p.L - 1) + l - 1];
     const double2* src = h.data() + (s.vec_off - first) + (long long)q * s.N;
     for (int i = 0; i < s.N; ++i) {
@@ -738,7 +752,7 @@ fthms_status fthms_densities_dev(fthms_req* req, int arc, int m, int q, double* 
   TRY(ensure_device(req->ctx->device));
   const Plan& p = req->plan;
   size_t o = 0;
-  for (int l = 1; l < p.L; ++l) {
+  for (int l = p.lb; l < p.le; ++l) {
     const SysDesc& s = p.sys[(size_t)arc * (p.L - 1) + l - 1];
     CK(cudaMemcpyAsync(out_dev + o, base + s.vec_off + (long long)q * s.N, (size_t)s.N * sizeof(double2),
                        cudaMemcpyDeviceToDevice, req->stream));
@@ -763,8 +777,8 @@ fthms_status fthms_stats(fthms_req* req, fthms_stats_t* out) {
   const Plan& p = req->plan;
   std::memset(out, 0, sizeof *out);
   out->setup_ms = req->setup_ms;
-  out->systems = (long long)p.P * (p.L - 1);
-  out->solves = (long long)p.P * (p.L - 1) * p.M * p.Q;
+  out->systems = (long long)p.P * (p.le - p.lb);           // this rank's frequencies
+  out->solves = (long long)p.P * (p.le - p.lb) * p.M * p.Q;
   out->kernel_launches = req->launches;
   out->device_bytes = req->bytes;
   out->cross_entries = (double)p.e_total;
@@ -772,6 +786,7 @@ fthms_status fthms_stats(fthms_req* req, fthms_stats_t* out) {
   out->h2d_bytes = req->h2d;
   double lu = 0.0, sv = 0.0;
   for (const SysDesc& s : p.sys) {
+    if (!p.own(s.l)) continue;
     lu += (8.0 / 3.0) * (double)s.N * s.N * s.N;
     sv += 8.0 * (double)s.N * s.N * p.Q * p.M;
   }
@@ -819,6 +834,14 @@ fthms_status fthms_result_errors(fthms_req* req, double* out, size_t cap) {
   CK(cudaMemcpyAsync(e.data(), req->J.sys_err, n * sizeof(float), cudaMemcpyDeviceToHost, req->stream));
   CK(cudaStreamSynchronize(req->stream));
   for (size_t i = 0; i < n; ++i) out[i] = e[i];     // systems are numbered j*(L-1) + l-1
+  return FTHMS_OK;
+}
+
+fthms_status fthms_set_allreduce(fthms_req* req, fthms_allreduce_fn fn, void* user) {
+  if (!req || !fn) return fail(FTHMS_EINVAL, "fthms_set_allreduce: NULL argument");
+  if (!req->ctx) return fail(FTHMS_EINVAL, "fthms_set_allreduce: the job's context was destroyed");
+  req->allreduce = fn;
+  req->allreduce_user = user;
   return FTHMS_OK;
 }
 

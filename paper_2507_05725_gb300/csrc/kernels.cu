@@ -19,8 +19,10 @@
 #include <cstdio>
 
 #include "bessel.cuh"
+#include "cplx.cuh"
 #include "df64.cuh"
 #include "kernels.h"
+#include "lu_common.cuh"
 
 namespace fthms {
 
@@ -54,41 +56,6 @@ cudaError_t init_constants() {
 
 namespace {
 
-__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
-}
-// c + a * b
-__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c) {
-  return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
-}
-// c - a * b
-__device__ __forceinline__ double2 cfms(double2 a, double2 b, double2 c) {
-  return make_double2(fma(-a.x, b.x, fma(a.y, b.y, c.x)), fma(-a.x, b.y, fma(-a.y, b.x, c.y)));
-}
-__device__ __forceinline__ double2 crecip(double2 a) {
-  double d = 1.0 / fma(a.x, a.x, a.y * a.y);
-  return make_double2(a.x * d, -a.y * d);
-}
-__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
-
-// FP32 complex helpers (mixed-precision factorisation and solves)
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
-}
-__device__ __forceinline__ float2 cfms(float2 a, float2 b, float2 c) {
-  return make_float2(fmaf(-a.x, b.x, fmaf(a.y, b.y, c.x)), fmaf(-a.x, b.y, fmaf(-a.y, b.x, c.y)));
-}
-__device__ __forceinline__ float2 crecip(float2 a) {
-  float d = 1.0f / fmaf(a.x, a.x, a.y * a.y);
-  return make_float2(a.x * d, -a.y * d);
-}
-__device__ __forceinline__ double2 make_neg(double2 a) { return make_double2(-a.x, -a.y); }
-__device__ __forceinline__ float2 make_neg(float2 a) { return make_float2(-a.x, -a.y); }
-constexpr int kSB = 32;   // diagonal block of the blocked triangular solves
-template <class C> struct CTraits;
-template <> struct CTraits<double2> { using R = double; };
-template <> struct CTraits<float2> { using R = float; };
 
 // ---------------------------------------------------------------------------------------------
 // Bessel test kernel
@@ -496,7 +463,6 @@ constexpr int kLuThreads = 256;
 // C = double2 (plain form: factors J.A in place) or float2 (mixed form: factors J.LU32 in place).
 template <class C>
 __global__ void __launch_bounds__(kLuThreads) k_lu(DevJob J) {
-  using Real = typename CTraits<C>::R;
   extern __shared__ __align__(16) unsigned char shl_raw[];
   C* shl = reinterpret_cast<C*>(shl_raw);
   const SysDesc s = J.sys[J.sys_order[blockIdx.x]];
@@ -515,41 +481,11 @@ __global__ void __launch_bounds__(kLuThreads) k_lu(DevJob J) {
       Pn[r * kPS + c] = A[(long long)(k0 + c) * N + k0 + r];
     }
     __syncthreads();
-    // The panel's columns by one warp (warp barriers only): the pivot is the largest |re| + |im| with
-    // the lowest row among ties, then the row swap inside the panel and the rank-1 update.
+    // The panel's columns by one warp (warp barriers only).
     if (wid == 0) {
-      for (int c = 0; c < w; ++c) {
-        Real best = -1;
-        int bi = 0x7fffffff;
-        for (int r = c + lane; r < nr; r += 32) {
-          C v = Pn[r * kPS + c];
-          Real m = fabs(v.x) + fabs(v.y);
-          if (m > best) { best = m; bi = r; }
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-          Real ov = __shfl_xor_sync(0xffffffffu, best, o);
-          int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-          if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-        }
-        const int p = bi == 0x7fffffff ? c : bi;
-        if (lane == 0) {
-          spiv[c] = p;
-          piv[k0 + c] = k0 + p;
-        }
-        if (p != c && lane < w) {
-          C t = Pn[c * kPS + lane];
-          Pn[c * kPS + lane] = Pn[p * kPS + lane];
-          Pn[p * kPS + lane] = t;
-        }
-        __syncwarp();
-        const C inv = crecip(Pn[c * kPS + c]);
-        for (int r = c + 1 + lane; r < nr; r += 32) {
-          C lr = cmul(Pn[r * kPS + c], inv);
-          Pn[r * kPS + c] = lr;
-          for (int cc = c + 1; cc < w; ++cc) Pn[r * kPS + cc] = cfms(lr, Pn[c * kPS + cc], Pn[r * kPS + cc]);
-        }
-        __syncwarp();
-      }
+      panel_factor_warp<C>(Pn, kPS, nr, w, spiv, lane);
+      __syncwarp();
+      if (lane < w) piv[k0 + lane] = k0 + spiv[lane];
     }
     __syncthreads();
     for (int idx = tid; idx < nr * w; idx += kLuThreads) {
@@ -598,51 +534,10 @@ __global__ void __launch_bounds__(kLuThreads) k_lu(DevJob J) {
     }
     __syncthreads();
   }
-  // U = D U' with unit-diagonal U': keep 1/U_kk and scale row k of U (right of the diagonal).
-  C* dinv = (sizeof(C) == sizeof(double2) ? reinterpret_cast<C*>(J.dinv) : reinterpret_cast<C*>(J.dinv32)) + s.piv_off;
-  for (int k = tid; k < N; k += kLuThreads) dinv[k] = crecip(A[(long long)k * N + k]);
-  __syncthreads();
-  for (long long e = tid; e < (long long)N * N; e += kLuThreads) {
-    const int col = (int)(e / N), row = (int)(e % N);
-    if (col > row) A[e] = cmul(A[e], dinv[row]);
-  }
-  __syncthreads();
-  // Invert the kSB x kSB diagonal blocks of the unit-lower L and of the unit-upper U' in place (the
-  // strictly lower part of a block holds L^{-1}'s, the strictly upper part U'^{-1}'s), so that the
-  // triangular solves take ceil(N/kSB) dependent block steps.  Column c of the inverse of a unit
-  // triangular T: X[c][c] = 1, X[i][c] = -sum_k T[i][k] X[k][c] over k between c and i.
-  C* T = shl;                      // kSB x kSB block, column-major (reuses the panel space)
-  C* Xi = shl + kSB * kSB;
-  for (int r0 = 0; r0 < N; r0 += kSB) {
-    const int w = min(kSB, N - r0);
-    for (int e = tid; e < kSB * kSB; e += kLuThreads) {
-      const int c = e / kSB, i = e % kSB;
-      T[e] = (c < w && i < w) ? A[(long long)(r0 + c) * N + r0 + i] : C{};
-    }
-    __syncthreads();
-    // Xi <- identity; then step k: X[i][c] -= T[i][k] X[k][c] for i > k, c <= k (lower part) and,
-    // from the bottom, X[i][c] -= T[i][k'] X[k'][c] for i < k', c >= k' (upper part), k' = w-1-k:
-    // all (i, c) pairs of a step in parallel.
-    for (int e = tid; e < kSB * kSB; e += kLuThreads) Xi[e] = (e / kSB == e % kSB) ? C{1} : C{};
-    __syncthreads();
-    for (int kk = 0; kk < w - 1; ++kk) {
-      const int ku = w - 1 - kk;
-      for (int e = tid; e < 2 * kSB * kSB; e += kLuThreads) {
-        const int half = e / (kSB * kSB), f = e % (kSB * kSB), c = f / kSB, i = f % kSB;
-        if (half == 0) {
-          if (i > kk && i < w && c <= kk) Xi[c * kSB + i] = cfms(T[kk * kSB + i], Xi[c * kSB + kk], Xi[c * kSB + i]);
-        } else {
-          if (i < ku && c >= ku && c < w) Xi[c * kSB + i] = cfms(T[ku * kSB + i], Xi[c * kSB + ku], Xi[c * kSB + i]);
-        }
-      }
-      __syncthreads();
-    }
-    for (int e = tid; e < w * w; e += kLuThreads) {
-      const int c = e / w, i = e % w;
-      if (i != c) A[(long long)(r0 + c) * N + r0 + i] = Xi[c * kSB + i];
-    }
-    __syncthreads();
-  }
+  lu_finish<C, kLuThreads>(A, N,
+                           (sizeof(C) == sizeof(double2) ? reinterpret_cast<C*>(J.dinv) : reinterpret_cast<C*>(J.dinv32)) +
+                               s.piv_off,
+                           shl);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -1749,7 +1644,10 @@ __global__ void __launch_bounds__(kTimeMaxThreads) k_incident(DevJob J) {
   forward_all<DF>(J, g, buf, J.Gt + (J.tr_off[k] + x) * J.Q * J.L);
 }
 
-template <bool DF>
+// PART = 0: the whole step at one transfer node (synthesis, -chi_k, windowed forward transforms).  In a
+// frequency-partitioned job the synthesis sums only this rank's frequencies: PART = 1 writes those partial
+// samples to J.ginc, the ranks add them, and PART = 2 reads the sums back and finishes the step.
+template <bool DF, int PART>
 __global__ void __launch_bounds__(kTimeMaxThreads) k_synth_fwd(DevJob J) {
   extern __shared__ double2 sht[];
   const int a = blockIdx.x;
@@ -1758,23 +1656,32 @@ __global__ void __launch_bounds__(kTimeMaxThreads) k_synth_fwd(DevJob J) {
   double2* buf = sht;
   double* g = reinterpret_cast<double*>(sht + K);
   const long long base = (J.tr_off[k] + x) * J.Q * L;
-  for (int n = threadIdx.x; n < NT; n += blockDim.x) g[n] = 0.0;
-  for (int q = 0; q < J.Q; ++q) {
-    const double2* Wq = J.W + base + (long long)q * L;
-    const double2* st = J.syn_tw + (long long)q * L;
-    for (int b = threadIdx.x; b < K; b += blockDim.x) {
-      double2 acc = make_double2(0.0, 0.0);
-      for (int l = (b == 0 ? K : b); l < L; l += K) acc = cfma(st[l], Wq[l], acc);
-      fft_put<DF>(buf, bitrev(b, J.logK), acc);
+  double* gpart = J.ginc + (long long)a * NT;
+  if (PART == 2) {
+    for (int n = threadIdx.x; n < NT; n += blockDim.x) g[n] = gpart[n];
+  } else {
+    for (int n = threadIdx.x; n < NT; n += blockDim.x) g[n] = 0.0;
+    for (int q = 0; q < J.Q; ++q) {
+      const double2* Wq = J.W + base + (long long)q * L;
+      const double2* st = J.syn_tw + (long long)q * L;
+      for (int b = threadIdx.x; b < K; b += blockDim.x) {
+        double2 acc = make_double2(0.0, 0.0);
+        for (int l = (b == 0 ? K : b); l < L; l += K) acc = cfma(st[l], Wq[l], acc);
+        fft_put<DF>(buf, bitrev(b, J.logK), acc);
+      }
+      __syncthreads();
+      fft_in_place<DF>(J, buf);
+      const int n0 = J.nlo[q];
+      for (int r = threadIdx.x; r < K; r += blockDim.x) {
+        const int n = n0 + r;
+        if (n < NT) g[n] += fft_get<DF>(buf, r).x;
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    fft_in_place<DF>(J, buf);
-    const int n0 = J.nlo[q];
-    for (int r = threadIdx.x; r < K; r += blockDim.x) {
-      const int n = n0 + r;
-      if (n < NT) g[n] += fft_get<DF>(buf, r).x;
+    if (PART == 1) {
+      for (int n = threadIdx.x; n < NT; n += blockDim.x) gpart[n] = g[n];
+      return;
     }
-    __syncthreads();
   }
   const double mchi = -J.chi[J.tr_off[k] + x];
   for (int n = threadIdx.x; n < NT; n += blockDim.x) g[n] *= mchi;
@@ -1790,7 +1697,7 @@ constexpr int kRestrMaxThreads = 256;   // largest restriction block a tuned lau
 template <bool DF>
 __global__ void __launch_bounds__(kRestrMaxThreads) k_restrict(DevJob J) {
   extern __shared__ double2 shr[];
-  const int sidx = blockIdx.x;
+  const int sidx = J.sys_order[blockIdx.x];
   const SysDesc s = J.sys[sidx];
   const int k = s.arc, l = s.l, N = s.N, Q = J.Q, L = J.L;
   const long long base = J.tr_off[k];
@@ -1975,18 +1882,29 @@ cudaError_t launch_incident(const DevJob& J, cudaStream_t st, int* launches) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_synth_fwd(const DevJob& J, cudaStream_t st, int* launches) {
+template <int PART>
+static cudaError_t launch_synth_part(const DevJob& J, cudaStream_t st, int* launches) {
   if (J.n_act == 0) return cudaSuccess;
   size_t sh = time_smem(J);
   const int nt = J.shape_time > 0 ? J.shape_time : kTimeThreads;
   const bool df = J.mixed && !J.fp64keep;   // double-float FFT butterflies
-  cudaError_t e = cudaFuncSetAttribute(df ? k_synth_fwd<true> : k_synth_fwd<false>,
+  cudaError_t e = cudaFuncSetAttribute(df ? k_synth_fwd<true, PART> : k_synth_fwd<false, PART>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
   if (e != cudaSuccess) return e;
-  if (df) k_synth_fwd<true><<<J.n_act, nt, sh, st>>>(J);
-  else k_synth_fwd<false><<<J.n_act, nt, sh, st>>>(J);
+  if (df) k_synth_fwd<true, PART><<<J.n_act, nt, sh, st>>>(J);
+  else k_synth_fwd<false, PART><<<J.n_act, nt, sh, st>>>(J);
   *launches += 1;
   return cudaGetLastError();
+}
+
+cudaError_t launch_synth_fwd(const DevJob& J, cudaStream_t st, int* launches) {
+  return launch_synth_part<0>(J, st, launches);
+}
+cudaError_t launch_synth_partial(const DevJob& J, cudaStream_t st, int* launches) {
+  return launch_synth_part<1>(J, st, launches);
+}
+cudaError_t launch_fwd_after_sum(const DevJob& J, cudaStream_t st, int* launches) {
+  return launch_synth_part<2>(J, st, launches);
 }
 
 cudaError_t launch_restrict(const DevJob& J, cudaStream_t st, int* launches) {
@@ -1995,6 +1913,7 @@ cudaError_t launch_restrict(const DevJob& J, cudaStream_t st, int* launches) {
   cudaError_t e = cudaFuncSetAttribute(J.mixed ? k_restrict<true> : k_restrict<false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
   if (e != cudaSuccess) return e;
+  if (J.nsys == 0) return cudaSuccess;
   if (J.mixed) k_restrict<true><<<J.nsys, nt, sh, st>>>(J);
   else k_restrict<false><<<J.nsys, nt, sh, st>>>(J);
   *launches += 1;

@@ -120,6 +120,9 @@ cudaError_t launch_cross_apply(const DevJob& J, cudaStream_t st, int* launches);
 cudaError_t launch_near_weights(const DevJob& J, cudaStream_t st, int* launches);
 cudaError_t launch_cross_otf(const DevJob& J, cudaStream_t st, int* launches);
 cudaError_t launch_synth_fwd(const DevJob& J, cudaStream_t st, int* launches);
+// Frequency-partitioned jobs: the partial synthesis into J.ginc, then (after the ranks' sum) the rest.
+cudaError_t launch_synth_partial(const DevJob& J, cudaStream_t st, int* launches);
+cudaError_t launch_fwd_after_sum(const DevJob& J, cudaStream_t st, int* launches);
 cudaError_t launch_traces(const DevJob& J, cudaStream_t st, int* launches);
 
 }  // namespace fthms

@@ -294,6 +294,23 @@ int build_plan(const fthms_curve* curves, int ncurves, const fthms_arc* arcs, in
       double t = p.t0 + n * p.dt;
       p.win[(size_t)q * p.NT + n] = window(t - p.s_q[q], p.H);
     }
+  // Frequency partition (Section 3: the per-frequency sub-problems of a step are independent): rank r of R
+  // owns the solved frequencies l in [1 + r (L-1)/R, 1 + (r+1)(L-1)/R).
+  if (opt->omega_ranks > 1) {
+    if (opt->omega_rank < 0 || opt->omega_rank >= opt->omega_ranks || opt->omega_ranks > p.L - 1) {
+      err = "omega partition needs 0 <= omega_rank < omega_ranks <= L - 1";
+      return FTHMS_EINVAL;
+    }
+    p.ranks = opt->omega_ranks;
+  } else if (opt->omega_rank != 0 || opt->omega_ranks < 0) {
+    err = "omega_rank must be 0 without a frequency partition (omega_ranks <= 1)";
+    return FTHMS_EINVAL;
+  }
+  {
+    const long long ns = p.L - 1, R = p.ranks, r = p.ranks > 1 ? opt->omega_rank : 0;
+    p.lb = 1 + (int)(r * ns / R);
+    p.le = 1 + (int)((r + 1) * ns / R);
+  }
   p.wl.assign(p.L, p.h);
   p.wl[0] = 0.0;
   p.wl[p.L - 1] = 0.5 * p.h;
@@ -369,11 +386,16 @@ int build_plan(const fthms_curve* curves, int ncurves, const fthms_arc* arcs, in
       s.arc = j;
       s.l = l;
       s.N = N;
+      s.kappa = l * p.h;
+      if (!p.own(l)) {           // another rank's frequency: no storage here
+        s.panel = -1;
+        s.mat_off = s.vec_off = s.piv_off = s.rlog_off = -1;
+        continue;
+      }
       s.panel = get_panel(j, N, true);
       s.mat_off = p.mat_total;
       s.vec_off = p.vec_total;
       s.piv_off = p.piv_total;
-      s.kappa = l * p.h;
       p.mat_total += (long long)N * N;
       p.vec_total += (long long)p.Q * N;
       p.piv_total += N;
@@ -398,11 +420,11 @@ int build_plan(const fthms_curve* curves, int ncurves, const fthms_arc* arcs, in
   }
   // Self-assembly tiles over bands of consecutive frequencies with the same N.
   for (int j = 0; j < p.P; ++j) {
-    int l = 1;
-    while (l < p.L) {
+    int l = p.lb;
+    while (l < p.le) {
       int N = p.Ntab[(size_t)j * p.L + l];
       int l1 = l;
-      while (l1 + 1 < p.L && p.Ntab[(size_t)j * p.L + l1 + 1] == N && l1 + 1 - l < kSelfBand) ++l1;
+      while (l1 + 1 < p.le && p.Ntab[(size_t)j * p.L + l1 + 1] == N && l1 + 1 - l < kSelfBand) ++l1;
       int nt = (N + kSelfTile - 1) / kSelfTile;
       int sidx = j * (p.L - 1) + (l - 1);
       for (int a = 0; a < nt; ++a)
@@ -416,10 +438,11 @@ int build_plan(const fthms_curve* curves, int ncurves, const fthms_arc* arcs, in
     p.rlog_off_N.push_back(p.rlog_total);
     p.rlog_total += (long long)kv.first * kv.first;
   }
-  for (auto& s : p.sys) s.rlog_off = rlog_map[s.N];
+  for (auto& s : p.sys)
+    if (p.own(s.l)) s.rlog_off = rlog_map[s.N];
   // Largest systems first, so that the last wave of the per-system kernels holds the small ones.
-  p.sys_order.resize(p.sys.size());
-  for (size_t s = 0; s < p.sys.size(); ++s) p.sys_order[s] = (int)s;
+  for (size_t s = 0; s < p.sys.size(); ++s)
+    if (p.own(p.sys[s].l)) p.sys_order.push_back((int)s);
   std::stable_sort(p.sys_order.begin(), p.sys_order.end(), [&](int a, int b) { return p.sys[a].N > p.sys[b].N; });
   if (p.opt.precision >= 1)
     for (int s : p.sys_order)
@@ -482,7 +505,7 @@ int build_plan(const fthms_curve* curves, int ncurves, const fthms_arc* arcs, in
   for (int pi = 0; pi < npairs; ++pi) {
     const PairDesc& pd = p.pairs[pi];
     if (pd.nrows == 0) continue;
-    for (int l = 1; l < p.L; ++l) {
+    for (int l = p.lb; l < p.le; ++l) {
       int N = p.Ntab[(size_t)pd.j * p.L + l];
       p.e_off[(size_t)pi * p.L + l] = p.e_total;
       p.e_total += (long long)pd.nrows * N;
@@ -493,8 +516,8 @@ int build_plan(const fthms_curve* curves, int ncurves, const fthms_arc* arcs, in
   std::vector<std::vector<int>> pairs_of(p.P + 1);
   for (int pi = 0; pi < npairs; ++pi)
     if (p.pairs[pi].nrows > 0) pairs_of[p.pairs[pi].k].push_back(pi);
-  p.blks.reserve((size_t)npairs * (p.L - 1));
-  for (int l = 1; l < p.L; ++l)
+  p.blks.reserve((size_t)npairs * (p.le - p.lb));
+  for (int l = p.lb; l < p.le; ++l)
     for (int k = 0; k <= p.P; ++k) {
       CrossGrp g{l, k, (int)p.blks.size(), 0};
       for (int pi : pairs_of[k]) {
@@ -544,21 +567,21 @@ int build_plan(const fthms_curve* curves, int ncurves, const fthms_arc* arcs, in
   auto band_end = [&](int j, int l) {
     const int N = p.Ntab[(size_t)j * p.L + l];
     int l1 = l;
-    while (l1 + 1 < p.L && p.Ntab[(size_t)j * p.L + l1 + 1] == N && l1 + 1 - l < 64) ++l1;
+    while (l1 + 1 < p.le && p.Ntab[(size_t)j * p.L + l1 + 1] == N && l1 + 1 - l < 64) ++l1;
     return l1;
   };
   size_t n_asm = 0;
   for (int pi = 0; pi < npairs; ++pi) {
     const PairDesc& pd = p.pairs[pi];
     if (pd.nrows == 0) continue;
-    for (int l = 1; l < p.L; l = band_end(pd.j, l) + 1) n_asm += (pd.nrows + kRowChunk - 1) / kRowChunk;
+    for (int l = p.lb; l < p.le; l = band_end(pd.j, l) + 1) n_asm += (pd.nrows + kRowChunk - 1) / kRowChunk;
   }
   p.asms.reserve(n_asm);
   for (int pi = 0; pi < npairs; ++pi) {
     const PairDesc& pd = p.pairs[pi];
     if (pd.nrows == 0) continue;
-    int l = 1;
-    while (l < p.L) {
+    int l = p.lb;
+    while (l < p.le) {
       int N = p.Ntab[(size_t)pd.j * p.L + l];
       int l1 = band_end(pd.j, l);
       int panel = get_panel(pd.j, N);
@@ -600,7 +623,7 @@ int build_plan(const fthms_curve* curves, int ncurves, const fthms_arc* arcs, in
   p.restr_of_sys.assign(p.sys.size(), -1);
   for (size_t s = 0; s < p.sys.size(); ++s) {
     int N = p.sys[s].N, Nm = p.Nmax[p.sys[s].arc];
-    if (N == Nm) continue;
+    if (N == Nm || !p.own(p.sys[s].l)) continue;
     auto key = std::make_pair(N, Nm);
     auto it = rmap.find(key);
     if (it == rmap.end()) {

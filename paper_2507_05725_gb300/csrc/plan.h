@@ -32,6 +32,9 @@ struct Plan {
   fthms_options opt{};
   std::vector<double> obs;  // 2 * n_obs
   int P = 0, L = 0, M = 0, Q = 0, K = 0, NT = 0, n_obs = 0, n_tout = 0;
+  int lb = 1, le = 1;       // this rank's solved frequencies l in [lb, le) (all of 1..L-1 unpartitioned)
+  int ranks = 1;            // frequency partition of the job (1 = none)
+  bool own(int l) const { return l >= lb && l < le; }
   double h = 0, dt = 0, t0 = 0, H = 0, period = 0;
   std::vector<double> s_q, c_q;
   std::vector<int> nlo;
@@ -43,7 +46,7 @@ struct Plan {
   std::vector<int> panel_index;  // [P][max N + 1] -> panel id or -1
   int maxN = 0;
 
-  std::vector<SysDesc> sys;  // s = j*(L-1) + (l-1)
+  std::vector<SysDesc> sys;  // s = j*(L-1) + (l-1); systems of other ranks' frequencies have offsets -1
   std::vector<int> sys_order;  // systems by decreasing N: launch order of the per-system kernels
   long long mat_total = 0, vec_total = 0, piv_total = 0;
 

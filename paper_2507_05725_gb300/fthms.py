@@ -46,7 +46,8 @@ class fthms_options(C.Structure):
                 ("interior", C.c_int), ("n_obs", C.c_int), ("obs_xy", C.POINTER(C.c_double)),
                 ("n_tout", C.c_int), ("tout0", C.c_double), ("dtout", C.c_double), ("precision", C.c_int),
                 ("keep_densities", C.c_int), ("cross_mode", C.c_int), ("refine_tol", C.c_double),
-                ("refine_max", C.c_int), ("refine_fallback", C.c_int)]
+                ("refine_max", C.c_int), ("refine_fallback", C.c_int), ("omega_rank", C.c_int),
+                ("omega_ranks", C.c_int)]
 
 
 class fthms_stats_t(C.Structure):
@@ -57,6 +58,9 @@ class fthms_stats_t(C.Structure):
                 ("precision", C.c_int), ("max_refine_resid", C.c_double),
                 ("refine_passes", C.c_double), ("n_unconverged", C.c_longlong), ("fallback_runs", C.c_int)]
 
+
+# void (*)(double* buf_dev, size_t count, void* cuda_stream, void* user)
+ALLREDUCE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 
 STAGES = ["tables", "assemble_self", "lu", "cross_assemble", "incident", "restrict", "solve", "cross_apply",
           "synth_fwd", "traces"]
@@ -85,6 +89,7 @@ def _load():
         "fthms_node_counts": (st, [vp, C.POINTER(C.c_int), C.c_size_t]),
         "fthms_stats": (st, [vp, C.POINTER(fthms_stats_t)]),
         "fthms_result_errors": (st, [vp, C.POINTER(C.c_double), C.c_size_t]),
+        "fthms_set_allreduce": (st, [vp, ALLREDUCE_FN, vp]),
         "fthms_release": (st, [vp]),
         "fthms_last_error": (C.c_char_p, []),
         "fthms_bessel0": (st, [vp, vp, vp, vp, C.c_int, vp]),
@@ -120,7 +125,7 @@ EXPORTED = ["fthms_create", "fthms_destroy", "fthms_prepare", "fthms_run", "fthm
             "fthms_profile", "fthms_stage_times", "fthms_assemble_self_noalloc", "fthms_server_create",
             "fthms_server_submit", "fthms_server_poll", "fthms_server_wait", "fthms_server_result",
             "fthms_server_latency", "fthms_server_release", "fthms_server_destroy", "fthms_use_graph",
-            "fthms_autotune", "fthms_plan_info", "fthms_result_errors"]
+            "fthms_autotune", "fthms_plan_info", "fthms_result_errors", "fthms_set_allreduce"]
 
 
 def _check(status):
@@ -163,7 +168,8 @@ class Marshalled:
                                      _dptr(obs) if obs.size else None, o["n_tout"], o["tout0"], o["dtout"],
                                      int(precision), int(keep_densities), int(o.get("cross_mode", 0)),
                                      float(o.get("refine_tol", 0.0)), int(o.get("refine_max", 0)),
-                                     int(o.get("refine_fallback", 0)))
+                                     int(o.get("refine_fallback", 0)), int(o.get("omega_rank", 0)),
+                                     int(o.get("omega_ranks", 0)))
         self.ncurves, self.narcs = len(curves), len(arcs)
 
 
@@ -252,6 +258,79 @@ def fthms_result_errors(req, narcs, L):
     return out
 
 
+def fthms_set_allreduce(req, fn):
+    """Install fn(buf_dev, count, cuda_stream) as the cross-rank sum of a frequency-partitioned job; returns
+    the ctypes callback object, which the caller must keep alive while the job runs."""
+    cb = ALLREDUCE_FN(lambda buf, n, stream, user: fn(buf, n, stream))
+    _check(LIB.fthms_set_allreduce(req, cb, None))
+    return cb
+
+
+_CUDART = None
+
+
+def _cudart():
+    """The CUDA runtime (for the device <-> host copies of the all-reduce helpers below)."""
+    global _CUDART
+    if _CUDART is None:
+        home = os.environ.get("CUDA_HOME", "/usr/local/cuda")
+        for name in (os.path.join(home, "lib64", "libcudart.so"), "libcudart.so", "libcudart.so.13"):
+            try:
+                _CUDART = C.CDLL(name)
+                break
+            except OSError:
+                continue
+        if _CUDART is None:
+            raise OSError("libcudart not found")
+        _CUDART.cudaMemcpyAsync.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t, C.c_int, C.c_void_p]
+        _CUDART.cudaStreamSynchronize.argtypes = [C.c_void_p]
+    return _CUDART
+
+
+def _copy(dst, src, nbytes, kind, stream):
+    rt = _cudart()
+    if rt.cudaMemcpyAsync(dst, src, nbytes, kind, stream) != 0 or rt.cudaStreamSynchronize(stream) != 0:
+        raise RuntimeError("cudaMemcpyAsync failed")
+
+
+class HostAllreduce:
+    """All-reduce through host memory: the partial samples go to a host array, `reduce(array)` sums it
+    across ranks in place (e.g. torch.distributed.all_reduce on a CPU tensor with gloo), and the sum goes
+    back to the device."""
+
+    def __init__(self, reduce):
+        self.reduce = reduce
+
+    def __call__(self, buf, count, stream):
+        h = np.empty(count, dtype=np.float64)
+        _copy(h.ctypes.data, buf, count * 8, 2, stream)        # device -> host
+        self.reduce(h)
+        _copy(buf, h.ctypes.data, count * 8, 1, stream)        # host -> device
+
+
+class TorchAllreduce:
+    """All-reduce with torch.distributed on the device (NCCL): the partial samples are copied into a torch
+    tensor on the job's stream, summed across ranks there, and copied back."""
+
+    def __init__(self, device):
+        self.device = device
+        self.buf = None
+
+    def __call__(self, buf, count, stream):
+        import torch
+        import torch.distributed as dist
+        if self.buf is None or self.buf.numel() < count:
+            self.buf = torch.empty(count, dtype=torch.float64, device=self.device)
+        rt = _cudart()
+        t = self.buf[:count]
+        if rt.cudaMemcpyAsync(t.data_ptr(), buf, count * 8, 3, stream) != 0:
+            raise RuntimeError("cudaMemcpyAsync failed")
+        with torch.cuda.stream(torch.cuda.ExternalStream(stream, device=self.device)):
+            dist.all_reduce(t)
+        if rt.cudaMemcpyAsync(buf, t.data_ptr(), count * 8, 3, stream) != 0:
+            raise RuntimeError("cudaMemcpyAsync failed")
+
+
 def fthms_autotune(req, reps=3):
     """Launch shapes (solve warps, assembly threads, time threads, restriction threads) chosen for the job."""
     out = (C.c_int * 4)()
@@ -328,12 +407,12 @@ class Job:
         return fthms_traces(self.req, self.n_obs, self.n_tout)
 
     def densities(self, arc, m, q=0):
-        """{l: complex array (N_arc(omega_l),)} for l = 1..L-1."""
+        """{l: complex array (N_arc(omega_l),)} for l = 1..L-1 (the rank's own l for a partitioned job)."""
         flat = fthms_densities(self.req, arc, m, q)
         z = flat[0::2] + 1j * flat[1::2]
         Ns = self.node_counts()[arc]
         out, o = {}, 0
-        for l in range(1, self.L):
+        for l in self.own_frequencies():
             n = int(Ns[l - 1])
             out[l] = z[o:o + n]
             o += n
@@ -344,6 +423,16 @@ class Job:
 
     def result_errors(self):
         return fthms_result_errors(self.req, self.P, self.L)
+
+    def set_allreduce(self, fn):
+        self._allreduce = fthms_set_allreduce(self.req, fn)
+        return self
+
+    def own_frequencies(self):
+        """The solved frequency indices l of this job's rank (all of 1..L-1 without a partition)."""
+        o = self.problem["options"]
+        R, r, n = max(1, int(o.get("omega_ranks", 0))), int(o.get("omega_rank", 0)), self.L - 1
+        return range(1 + r * n // R, 1 + (r + 1) * n // R)
 
     def release(self):
         if self.req is not None:
