@@ -217,6 +217,12 @@ fthms_status upload_job(fthms_req* r) {
 
   TRY(dev_upload(r, p.sys, &J.sys));
   TRY(dev_upload(r, p.sys_order, &J.sys_order));
+  TRY(dev_upload(r, p.lu_small, &J.lu_small));
+  TRY(dev_upload(r, p.lu_big, &J.lu_big));
+  J.n_lu_small = (int)p.lu_small.size();
+  J.n_lu_big = (int)p.lu_big.size();
+  J.big_max_n = p.big_max_n;
+  TRY(dev_alloc(r, 1, &J.dev_err));
   TRY(dev_upload(r, p.panels, &J.panels));
   TRY(dev_upload(r, p.node_t, &J.node_t));
   TRY(dev_upload(r, p.node_x, &J.node_x));
@@ -419,6 +425,7 @@ fthms_status enqueue_stages(fthms_req* r, bool bracket) {
   CK(cudaMemsetAsync(J.W, 0, (size_t)r->plan.spec_total * sizeof(double2), st));
   CK(cudaMemsetAsync(J.Vobs, 0, (size_t)std::max(1, J.n_obs * J.Q * J.L) * sizeof(double2), st));
   CK(cudaMemsetAsync(J.refine_resid, 0, 3 * sizeof(double), st));
+  CK(cudaMemsetAsync(J.dev_err, 0, sizeof(int), st));
   if (J.sys_err) CK(cudaMemsetAsync(J.sys_err, 0, r->plan.sys.size() * sizeof(float), st));
   TRY(stage(r, FTHMS_STAGE_INCIDENT, st, &nl, [&] { return launch_incident(J, st, &nl); }));
   TRY(stage(r, FTHMS_STAGE_RESTRICT, st, &nl, [&] { return launch_restrict(J, st, &nl); }));
@@ -639,6 +646,15 @@ static fthms_status check_convergence(fthms_req* req) {
   }
   req->conv_checked = true;
   req->conv_status = FTHMS_OK;
+  int derr = 0;
+  CK(cudaMemcpyAsync(&derr, req->J.dev_err, sizeof derr, cudaMemcpyDeviceToHost, req->stream));
+  CK(cudaStreamSynchronize(req->stream));
+  if (derr) {
+    req->conv_status = FTHMS_ECUDA;
+    req->conv_msg = "fthms_wait: a tensor-core LU update did not complete within its bounded wait";
+    g_last_error = req->conv_msg;
+    return FTHMS_ECUDA;
+  }
   if (!req->J.mixed) return FTHMS_OK;
   unsigned long long bad = 0;
   CK(cudaMemcpyAsync(&bad, reinterpret_cast<const unsigned long long*>(req->J.refine_resid) + 2, sizeof bad,

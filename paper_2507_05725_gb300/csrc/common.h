@@ -104,6 +104,12 @@ struct SelfTile {
   int ti, tl;       // tile row / column (tile edge = kSelfTile)
 };
 
+// LU paths: one CTA per system in shared memory up to N = kLuSmallMax (FP64) / any N below kLuBigMin
+// (mixed forms); the mixed forms factor N >= kLuBigMin (up to kLuBigMax) with tensor-core updates.
+constexpr int kLuSmallMax = 800;
+constexpr int kLuBigMin = 801;
+constexpr int kLuBigMax = 2048;
+
 constexpr int kSelfTile = 16;
 constexpr int kSelfBand = 32;
 

@@ -465,7 +465,7 @@ template <class C>
 __global__ void __launch_bounds__(kLuThreads) k_lu(DevJob J) {
   extern __shared__ __align__(16) unsigned char shl_raw[];
   C* shl = reinterpret_cast<C*>(shl_raw);
-  const SysDesc s = J.sys[J.sys_order[blockIdx.x]];
+  const SysDesc s = J.sys[J.lu_small[blockIdx.x]];
   const int N = s.N;
   C* A = (sizeof(C) == sizeof(double2) ? reinterpret_cast<C*>(J.A) : reinterpret_cast<C*>(J.LU32)) + s.mat_off;
   int* piv = J.piv + s.piv_off;
@@ -1835,18 +1835,25 @@ cudaError_t launch_assemble_self(const DevJob& J, cudaStream_t st, int* launches
 
 cudaError_t launch_lu(const DevJob& J, cudaStream_t st, int* launches) {
   if (J.mixed) {
-    // k_assemble_self already wrote the FP32 matrix and the double-float pairs
-    size_t sh = std::max((size_t)J.max_n * (kNB + kPS), (size_t)2 * kSB * kSB) * sizeof(float2);
-    cudaError_t e = cudaFuncSetAttribute(k_lu<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
-    if (e != cudaSuccess) return e;
-    k_lu<float2><<<J.nsys, kLuThreads, sh, st>>>(J);
-    *launches += 1;
-    return cudaGetLastError();
+    // k_assemble_self already wrote the FP32 matrix and the double-float pairs (or FP64 values)
+    if (J.n_lu_small > 0) {
+      int small_max = 0;   // systems above kLuBigMin go to the tensor-core path; J.max_n bounds the rest
+      small_max = std::min(J.max_n, kLuBigMin - 1);
+      size_t sh = std::max((size_t)small_max * (kNB + kPS), (size_t)2 * kSB * kSB) * sizeof(float2);
+      cudaError_t e = cudaFuncSetAttribute(k_lu<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+      if (e != cudaSuccess) return e;
+      k_lu<float2><<<J.n_lu_small, kLuThreads, sh, st>>>(J);
+      *launches += 1;
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+    return launch_lu_large(J, st, launches);
   }
+  if (J.n_lu_small == 0) return cudaSuccess;
   size_t sh = std::max((size_t)J.max_n * (kNB + kPS), (size_t)2 * kSB * kSB) * sizeof(double2);
   cudaError_t e = cudaFuncSetAttribute(k_lu<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
   if (e != cudaSuccess) return e;
-  k_lu<double2><<<J.nsys, kLuThreads, sh, st>>>(J);
+  k_lu<double2><<<J.n_lu_small, kLuThreads, sh, st>>>(J);
   *launches += 1;
   return cudaGetLastError();
 }

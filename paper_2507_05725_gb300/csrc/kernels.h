@@ -26,7 +26,11 @@ struct DevJob {
   const double* sig_f;
   // tables
   const SysDesc* sys;
-  const int* sys_order;       // systems by decreasing N (launch order of k_lu and the solves)
+  const int* sys_order;       // systems by decreasing N (launch order of the solves and restriction)
+  const int* lu_small;        // systems factored by one CTA each (k_lu), decreasing N
+  const int* lu_big;          // mixed forms: systems above kLuBigMin, factored with tensor-core updates
+  int n_lu_small, n_lu_big, big_max_n;
+  int* dev_err;               // set by a kernel whose bounded wait ran out (reported by fthms_wait)
   const Panel* panels;
   const double *node_t, *node_x, *node_y, *node_sp;
   const int* rlogN;
@@ -112,6 +116,9 @@ cudaError_t launch_tables(const DevJob& J, cudaStream_t st, int* launches);
 cudaError_t launch_tables_rlog_only(const DevJob& J, cudaStream_t st, int* launches);
 cudaError_t launch_assemble_self(const DevJob& J, cudaStream_t st, int* launches);
 cudaError_t launch_lu(const DevJob& J, cudaStream_t st, int* launches);
+// Mixed forms, systems with N >= kLuBigMin: blocked LU with tcgen05 trailing updates (lu_large.cu).
+cudaError_t launch_lu_large(const DevJob& J, cudaStream_t st, int* launches);
+size_t lu_big_panel_smem(int maxN);
 cudaError_t launch_cross_assemble(const DevJob& J, cudaStream_t st, int* launches);
 cudaError_t launch_incident(const DevJob& J, cudaStream_t st, int* launches);
 cudaError_t launch_restrict(const DevJob& J, cudaStream_t st, int* launches);

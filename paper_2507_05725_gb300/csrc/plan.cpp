@@ -328,8 +328,11 @@ int build_plan(const fthms_curve* curves, int ncurves, const fthms_arc* arcs, in
       double omega = l * p.h;
       int N = opt->N_fixed > 0 ? opt->N_fixed
                                : std::max(opt->N_min, (int)std::ceil(opt->N_ppw * omega * p.arcs[j].length - 1e-9) + opt->N_off);
-      if (N < 2 || N > 800) {
-        snprintf(buf, sizeof buf, "arc %d omega index %d: node count %d outside [2, 800] (shared-memory panel of the LU)", j, l, N);
+      const int nmax = opt->precision == 0 ? kLuSmallMax : kLuBigMax;
+      if (N < 2 || N > nmax) {
+        snprintf(buf, sizeof buf, "arc %d omega index %d: node count %d outside [2, %d] (%s)", j, l, N, nmax,
+                 opt->precision == 0 ? "FP64: shared-memory panel of the LU; the mixed forms reach 2048"
+                                     : "largest tensor-core LU");
         err = buf;
         return FTHMS_EINVAL;
       }
@@ -444,6 +447,15 @@ int build_plan(const fthms_curve* curves, int ncurves, const fthms_arc* arcs, in
   for (size_t s = 0; s < p.sys.size(); ++s)
     if (p.own(p.sys[s].l)) p.sys_order.push_back((int)s);
   std::stable_sort(p.sys_order.begin(), p.sys_order.end(), [&](int a, int b) { return p.sys[a].N > p.sys[b].N; });
+  // LU paths: the mixed forms factor systems of kLuBigMin nodes or more with tensor-core trailing updates.
+  for (int s : p.sys_order) {
+    if (p.opt.precision >= 1 && p.sys[s].N >= kLuBigMin) {
+      p.lu_big.push_back(s);
+      p.big_max_n = std::max(p.big_max_n, p.sys[s].N);
+    } else {
+      p.lu_small.push_back(s);
+    }
+  }
   if (p.opt.precision >= 1)
     for (int s : p.sys_order)
       for (int r0 = 0; r0 < p.sys[s].N; r0 += 32) p.rchunks.push_back(ResidChunk{s, r0});
@@ -560,6 +572,12 @@ int build_plan(const fthms_curve* curves, int ncurves, const fthms_arc* arcs, in
       p.slices.push_back(sl);
       row0 = end;
     }
+  }
+  // Stored cross rows: the assembly keeps 4N + 2 kAsmRows N doubles and its band tables in shared memory.
+  if (p.opt.cross_mode == 0 && (size_t)(20 * p.maxN + 512) * 8 > (size_t)227 * 1024) {
+    snprintf(buf, sizeof buf, "stored cross rows (cross_mode 0) need N <= 1427 (largest N %d); use cross_mode 1", p.maxN);
+    err = buf;
+    return FTHMS_EINVAL;
   }
   const int kRowChunk = 8;
   // Assembly tasks: (pair, band of up to 64 equal-N frequencies, kRowChunk target rows); counted first so

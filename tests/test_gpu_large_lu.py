@@ -1,0 +1,68 @@
+"""Large systems (N up to 2048) in the mixed forms: FP32 LU with tensor-core (tcgen05, 3xTF32) trailing
+updates, refined against the kept matrix, through the C ABI against the FP64 oracle."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import workloads as wl
+from oracle import run_oracle
+
+pytestmark = pytest.mark.gpu
+
+MIXED_TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def F():
+    from paper_2507_05725_gb300 import fthms
+    return fthms
+
+
+@pytest.fixture(scope="module")
+def ctx(F):
+    torch.cuda.set_device(0)
+    c = F.fthms_create(0, 0, None)
+    yield c
+    F.fthms_destroy(c)
+
+
+def _problem(N, kind=1):
+    """Two overlapping arcs of one seeded curve, two solved frequencies (omega = 6 and 12), N nodes per arc,
+    cross rows evaluated every step (stored rows stop at N = 1427)."""
+    p = wl.random_small(13, n_arcs_per_curve=2, N_fixed=N, L=3, H=0.25, M=2, W=12.0, kind=kind, n_period=64)
+    p["options"]["cross_mode"] = 1
+    return p
+
+
+@pytest.mark.parametrize("N", [801, 1024, 2048])
+@pytest.mark.parametrize("precision", [1, 2])
+def test_large_system_parity(F, ctx, N, precision):
+    problem = _problem(N)
+    job = F.Job(ctx, problem, precision=precision).run().wait()
+    ref = run_oracle(problem)
+    num = den = 0.0
+    for m in (1, 2):
+        for j in range(2):
+            d = job.densities(j, m, 0)
+            for l in (1, 2):
+                r = ref.phi[(m, j, l)][0]
+                assert d[l].shape == r.shape
+                num += float(np.sum(np.abs(d[l] - r) ** 2))
+                den += float(np.sum(np.abs(r) ** 2))
+    st = job.stats()
+    tr = job.traces()
+    job.release()
+    rel = math.sqrt(num / den)
+    assert rel < MIXED_TOL, rel
+    assert st["n_unconverged"] == 0 and st["max_refine_resid"] < 1e-12
+    # an FP32-accurate factor needs about two refinement passes; a TF32-only one would need many more
+    assert st["refine_passes"] <= 3.0, st["refine_passes"]
+    assert np.max(np.abs(tr - ref.traces)) < 10 * MIXED_TOL * max(1e-300, np.max(np.abs(ref.traces)))
+
+
+def test_fp64_form_refuses_the_largest_systems(F, ctx):
+    with pytest.raises(F.FthmsError) as e:
+        F.Job(ctx, _problem(1024), precision=0)
+    assert e.value.status == F.FTHMS_EINVAL and "2048" in str(e.value)
