@@ -95,7 +95,8 @@ typedef struct {
 /* Discretisation and output options.
  *  W, L      : frequencies omega_l = l*(W/(L-1)), l = 0..L-1; l = 1..L-1 are solved.
  *  N rule    : nodes per arc N_j(omega) = N_fixed if > 0, else max(N_min, ceil(N_ppw*omega*len_j)
- *              + N_off), len_j the arc length; every N_j(omega) must lie in [2, 800].  The transfer
+ *              + N_off), len_j the arc length; every N_j(omega) must lie in [2, 800] (precision 0) or
+ *              [2, 2048] (precisions 1 and 2; stored cross rows, cross_mode 0, need N <= 1427).  The transfer
  *              mesh of arc j is its first-kind Chebyshev grid of size N_j(omega_{L-1}).
  *  M         : multiple-scattering steps (Algorithm 1's outer loop).
  *  Q, H      : 1 <= Q <= 4 time windows sqcap_q(t) = sqcap(t - s_q), s_q = 1.5 (q-1) H (Section 5).
@@ -112,8 +113,11 @@ typedef struct {
  *              refinement residuals, the FFT butterflies of the time transforms, the restriction and the
  *              cross apply in double-float on the FP32 pipe; diagonal self entries, per-pair setup,
  *              phase-seed reduction, log-singular corrections, transform folds and phase factors stay
- *              FP64.  The refinement solves the double-float matrix exactly; its rounding (~2^-44 of an
- *              entry) still reaches the densities through the matrix's conditioning.  2 = the mixed form
+ *              FP64; the self entries of systems with N > 800 (factored with tensor-core updates) are
+ *              assembled in FP64 and stored as their double-float rounding.  The refinement solves the
+ *              double-float matrix exactly; its rounding (~2^-44 of an entry) still reaches the densities
+ *              through the matrix's conditioning.  N > 800 (up to 2048): FP32 LU with tcgen05 (3xTF32)
+ *              trailing updates, precisions 1 and 2 only.  2 = the mixed form
  *              with FP64 kept where accuracy is decided: the self matrices assembled and kept in FP64 (the
  *              FP32 factor is their rounding) with FP64 refinement residuals, the small-argument (z < 20)
  *              Hankel series of the stored cross entries, and the FFT butterflies of the time transforms

@@ -37,6 +37,7 @@ class OracleResult:
     traces: np.ndarray = None        # [n_obs, n_tout]
     Vobs: np.ndarray = None          # [n_obs, Q, L] accumulated observation spectra
     G: dict = field(default_factory=dict)     # (m, j, l) -> complex (Q, N) BIE data (if kept)
+    g: dict = field(default_factory=dict)     # (m, k) -> real (Nmax_k, N_T) time-domain data g_{k,m} (if kept)
     chi: list = None                 # per arc chi at transfer nodes
     grid: TimeGrid = None
 
@@ -86,14 +87,16 @@ class Setup:
         self.obs = np.asarray(o["obs"], dtype=np.float64).reshape(-1, 2)
 
 
-def run_oracle(problem, M=None, keep_G=False, cache_cross=True, arcs_phi=None, omega_part=None, allreduce=None):
+def run_oracle(problem, M=None, keep_G=False, cache_cross=True, arcs_phi=None, omega_part=None, allreduce=None,
+               keep_g=False):
     """Run Algorithm 1 on the discrete problem; returns an OracleResult.
 
     M overrides the number of multiple-scattering steps; ``arcs_phi`` limits which arcs' densities
     are kept (all by default).  ``omega_part = (r, R)`` runs rank r's share of a frequency partition: the
     solved frequencies l in [1 + r (L-1)/R, 1 + (r+1)(L-1)/R) (the per-frequency sub-problems of a step
     are independent, Section 3); the omega -> t synthesis of every step and the traces are then partial
-    sums over those frequencies, which ``allreduce(array) -> array`` must sum across the ranks."""
+    sums over those frequencies, which ``allreduce(array) -> array`` must sum across the ranks.  ``keep_g``
+    keeps the time-domain data g_{k,m} on every transfer mesh (eqs. criterion_int1/2)."""
     S = Setup(problem)
     o = problem["options"]
     sig = problem["signal"]
@@ -133,6 +136,8 @@ def run_oracle(problem, M=None, keep_G=False, cache_cross=True, arcs_phi=None, o
     G = {}
     for k in range(P):
         g = sig["sign"] * S.chi[k][:, None] * incident_field(sig, S.X[k], tg.t)
+        if keep_g:
+            res.g[(1, k)] = g
         for l, v in restrict(k, tg.forward(g)).items():
             G[(k, l)] = v
 
@@ -188,6 +193,8 @@ def run_oracle(problem, M=None, keep_G=False, cache_cross=True, arcs_phi=None, o
         for k in range(P):
             w = total(tg.inverse(Wk[k]))
             g = -S.chi[k][:, None] * w
+            if keep_g:
+                res.g[(m + 1, k)] = g
             for l, v in restrict(k, tg.forward(g)).items():
                 G[(k, l)] = v
     res.Vobs = Vobs

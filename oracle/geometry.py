@@ -149,3 +149,25 @@ def node_count(problem, arc_len, omega):
     if o["N_fixed"] > 0:
         return int(o["N_fixed"])
     return max(int(o["N_min"]), int(math.ceil(o["N_ppw"] * omega * arc_len - 1e-9)) + int(o["N_off"]))
+
+
+def delta_min(problem, samples=4001):
+    """delta_min of eq. dist: the smallest distance between a truncated patch Gamma_j^tr (the points of
+    Gamma_j where chi_j > 0) and the rest of the boundary Gamma minus Gamma_j, over the patches of every
+    closed curve; by dense sampling of the curve (an upper bound within the sampling step)."""
+    arcs = build_arcs(problem)
+    best = math.inf
+    for a in arcs:
+        if a.next is None:
+            continue
+        theta = np.linspace(0.0, TWO_PI, samples, endpoint=False)
+        X = curve_eval(a.curve, theta)[0]
+        ts = a.local_param(theta)
+        inside = np.abs(ts) <= 1.0
+        tr = inside.copy()
+        tr[inside] = chi(a, ts[inside]) > 0.0
+        if not np.any(tr) or np.all(inside):
+            continue
+        d = np.linalg.norm(X[tr][:, None, :] - X[~inside][None, :, :], axis=-1)
+        best = min(best, float(np.min(d)))
+    return best

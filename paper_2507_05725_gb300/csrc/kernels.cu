@@ -339,7 +339,10 @@ __global__ void __launch_bounds__(256) k_assemble_self(DevJob J) {
   const int lend = s0.l + nb;
   const double zmin = (lsw * J.h) * R;
   const int kmax = hankel_terms((float)zmin);
-  if (J.mixed && !J.fp64keep) {
+  // Mixed form: double-float assembly for the systems of the one-CTA LU; the large systems (tensor-core LU,
+  // conditioning that grows with N) are assembled in FP64 and stored as the double-float rounding.
+  const bool df_asm = J.mixed && !J.fp64keep && N < kLuBigMin;
+  if (df_asm) {
     // Mixed form, z < 20: the Taylor range in double-float, alpha = aw ln l + a0.
     const df R_d = df_from(R), qw_d = df_from(qw), aw_d = df_from(-0.5 * kInvPi * w),
              a0_d = df_from(-0.5 * kInvPi * fma(w, lratio, rl));
@@ -371,7 +374,7 @@ __global__ void __launch_bounds__(256) k_assemble_self(DevJob J) {
       store_self(J, mo + e2, v);
     }
   }
-  if (J.mixed && !J.fp64keep && lsw < lend) {
+  if (df_asm && lsw < lend) {
     // Mixed form: the recurrence above z = 20 in double-float on the FP32 pipe (about 48 bits), stored
     // as the pair and its FP32 rounding; FP64 only for the seeds.  (The FP64-kept form assembles the
     // whole self matrix in FP64, as the plain form does.)
