@@ -282,12 +282,14 @@ enum {
   FTHMS_NSTAGES = 10
 };
 
-/* Pick launch shapes for this job's hardware and sizes: runs the job once, then times each tunable stage
- * `reps` times per candidate -- warps (systems) per solve block {4, 2, 1}, threads per cross-assembly block
- * {128, 64, 256} (stored rows only), per time-transform block {256, 128, 512} and per restriction block
- * {128, 64, 256} -- and keeps the fastest for later fthms_run calls (a captured graph is dropped and
- * re-captured).  Every candidate computes the same numbers, so results are bitwise unchanged.  shapes
- * (NULL allowed) receives the four choices.  The job's earlier results are overwritten: call
+/* Pick launch shapes and the LU path for this job's hardware and sizes: runs the job once, then times
+ * each tunable stage `reps` times per candidate -- warps (systems) per solve block {4, 2, 1}, threads per
+ * cross-assembly block {128, 64, 256} (stored rows only), per time-transform block {256, 128, 512}, per
+ * restriction block {128, 64, 256} and, in the mixed forms, the smallest N factored with tensor-core
+ * updates {801, 512, 384, 256} (below it the one-CTA LU) -- and keeps the fastest for later fthms_run
+ * calls (a captured graph is dropped and re-captured).  The launch shapes change no number; the LU path
+ * changes the FP32 factor's rounding only, which the refinement removes.  shapes (NULL allowed) receives
+ * the five choices (the last 0 for an FP64 job).  The job's earlier results are overwritten: call
  * fthms_run afterwards.  Not in the paper (a batching aid of this library). */
 fthms_status fthms_autotune(fthms_req* req, int reps, int* shapes);
 

@@ -111,6 +111,7 @@ struct fthms_req {
   std::string conv_msg;
   int fallback_runs = 0;           // runs repeated in FP64 after a refinement that did not converge
   bool plain_apply_fits = true;    // the FP64 stored-row apply fits shared memory (FP64 fallback possible)
+  int lu_min = kLuBigMin;          // smallest N factored with tensor-core updates (mixed forms)
   fthms_allreduce_fn allreduce = nullptr;   // sum across the ranks of a frequency-partitioned job
   void* allreduce_user = nullptr;
 };
@@ -163,6 +164,17 @@ void free_req(fthms_req* r) {
     fthms_status s__ = (x);            \
     if (s__ != FTHMS_OK) return s__;   \
   } while (0)
+
+// The first n_big systems of sys_order (the largest) take the tensor-core LU, the rest the one-CTA LU.
+void set_lu_split(fthms_req* r, int n_big) {
+  DevJob& J = r->J;
+  const Plan& p = r->plan;
+  J.lu_big = J.sys_order;
+  J.n_lu_big = n_big;
+  J.lu_small = J.sys_order ? J.sys_order + n_big : nullptr;
+  J.n_lu_small = (int)p.sys_order.size() - n_big;
+  J.big_max_n = n_big > 0 ? p.sys[p.sys_order[0]].N : 0;
+}
 
 fthms_status upload_job(fthms_req* r) {
   Plan& p = r->plan;
@@ -217,11 +229,7 @@ fthms_status upload_job(fthms_req* r) {
 
   TRY(dev_upload(r, p.sys, &J.sys));
   TRY(dev_upload(r, p.sys_order, &J.sys_order));
-  TRY(dev_upload(r, p.lu_small, &J.lu_small));
-  TRY(dev_upload(r, p.lu_big, &J.lu_big));
-  J.n_lu_small = (int)p.lu_small.size();
-  J.n_lu_big = (int)p.lu_big.size();
-  J.big_max_n = p.big_max_n;
+  set_lu_split(r, p.n_lu_big);
   TRY(dev_alloc(r, 1, &J.dev_err));
   TRY(dev_upload(r, p.panels, &J.panels));
   TRY(dev_upload(r, p.node_t, &J.node_t));
@@ -909,6 +917,28 @@ fthms_status fthms_autotune(fthms_req* req, int reps, int* shapes) {
   if (!J.otf) knobs.push_back({&J.shape_asm, {128, 64, 256}, [&] { return launch_cross_assemble(J, st, &nl); }});
   knobs.push_back({&J.shape_time, {256, 128, 512}, [&] { return launch_synth_fwd(J, st, &nl); }});
   knobs.push_back({&J.shape_restr, {128, 64, 256}, [&] { return launch_restrict(J, st, &nl); }});
+  // Mixed forms: the smallest N factored with tensor-core updates (candidates above 800 keep the default,
+  // the one-CTA LU cannot hold more); every candidate factors the same matrices, its time is compared.
+  int lu_min = kLuBigMin;
+  if (J.mixed) {
+    std::vector<int> cand{kLuBigMin};
+    for (int c : {512, 384, 256})
+      if (!req->plan.sys_order.empty() && req->plan.sys[req->plan.sys_order[0]].N >= c) cand.push_back(c);
+    if (cand.size() > 1) {
+      auto split_for = [&](int nmin) {
+        int nb = 0;
+        const Plan& p = req->plan;
+        while (nb < (int)p.sys_order.size() && p.sys[p.sys_order[nb]].N >= nmin) ++nb;
+        return nb;
+      };
+      knobs.push_back({&lu_min, cand, [&] {
+                         set_lu_split(req, split_for(lu_min));
+                         // the LU works in place: re-assemble the matrices before every factorisation
+                         cudaError_t e = launch_assemble_self(J, st, &nl);
+                         return e == cudaSuccess ? launch_lu(J, st, &nl) : e;
+                       }});
+    }
+  }
   for (Knob& k : knobs) {
     float best = 0.f;
     int pick = k.cand[0];
@@ -923,11 +953,20 @@ fthms_status fthms_autotune(fthms_req* req, int reps, int* shapes) {
     }
     *k.field = pick;
   }
+  {
+    int nb = 0;
+    const Plan& p = req->plan;
+    if (J.mixed)
+      while (nb < (int)p.sys_order.size() && p.sys[p.sys_order[nb]].N >= lu_min) ++nb;
+    set_lu_split(req, nb);
+    req->lu_min = lu_min;
+  }
   if (shapes) {
     shapes[0] = J.shape_solve;
     shapes[1] = J.shape_asm;
     shapes[2] = J.shape_time;
     shapes[3] = J.shape_restr;
+    shapes[4] = J.mixed ? req->lu_min : 0;
   }
   return FTHMS_OK;
 }

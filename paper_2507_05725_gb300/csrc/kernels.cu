@@ -1031,6 +1031,175 @@ __global__ void __launch_bounds__(kAsmThreads) k_cross_otf(DevJob J) {
   }
 }
 
+// Mixed forms, cross rows evaluated every step in double-float (on the FP32 pipe).  One CTA per (assembly
+// task of kAsmRows target rows, band of at most kOtfBandDf frequencies), kOtfDfThreads threads, sources in
+// tiles of kOtfDfSrc:
+//  1. thread (row r, source i of the tile): the pair's FP64 set-up once (pair_setup), then the entries of
+//     every frequency of the band -- below z = 20 the Taylor form (double-float; FP64 rounded to double-float
+//     in the FP64-kept form), above it Hankel's expansion with its phase advanced by the double-float
+//     rotation e^{i h R} (re-seeded every 16 steps), exactly as the mixed stored-row assembly -- into shared
+//     memory; the tile's double-float densities phi(omega_l) are staged beside them;
+//  2. thread (row, frequency): sum over the tile's sources of entry x density for every window, with
+//     compensated double-float accumulation in source order (deterministic), carried across the tiles.
+// The per-row sums go to the per-row results that k_cross_reduce adds per target in block order.
+constexpr int kOtfDfSrc = 16;
+constexpr int kOtfDfThreads = kAsmRows * kOtfDfSrc;   // 128
+
+// Double-float state of Hankel's expansion along a band (the mixed stored-row assembly's recurrence).
+struct AsymDf {
+  df cx, sx, cu, su, ampw, invu, beta;
+  int since, kmax;
+};
+
+__device__ __forceinline__ AsymDf asym_df_start(const PairSetup& ps, double lh_first, double camp) {
+  const AsymState as = asym_start(ps, lh_first, camp, false);
+  AsymDf a;
+  a.ampw = df_from(as.ampw);
+  a.invu = df_from(ps.inv_u);
+  a.beta = df_from(ps.beta);
+  a.kmax = as.kmax;
+  if (ps.hR <= 1.0) {
+    df_sincos_taylor(df_from(ps.hR), a.su, a.cu);
+  } else {
+    double su, cu;
+    sincos(ps.hR, &su, &cu);
+    a.su = df_from(su);
+    a.cu = df_from(cu);
+  }
+  a.cx = a.sx = df{0.f, 0.f};
+  a.since = 16;
+  return a;
+}
+
+__device__ __forceinline__ float4 asym_df_entry(AsymDf& a, double lhR, df invl, df rsql) {
+  if (a.since >= 16) {
+    df_phase_seed(lhR, a.cx, a.sx);
+    a.since = 0;
+  }
+  const df wz = df_mul(a.invu, invl);
+  const df w2 = df_neg(df_mul(wz, wz));
+  df P, Qa;
+  hankel_pq_df(a.kmax, w2, P, Qa);
+  Qa = df_mul(Qa, wz);
+  const df amp = df_mul(a.ampw, rsql);
+  const df t1 = df_dot2(P, a.cx, Qa, a.sx);
+  const df t2 = df_dot2(P, a.sx, df_neg(Qa), a.cx);
+  const df re = df_mul(amp, df_dot2(a.beta, t1, df{-1.f, 0.f}, t2));
+  const df im = df_mul(amp, t1);
+  const df cn = df_dot2(a.cx, a.cu, df_neg(a.sx), a.su);
+  a.sx = df_dot2(a.sx, a.cu, a.cx, a.su);
+  a.cx = cn;
+  ++a.since;
+  return make_float4(re.hi, re.lo, im.hi, im.lo);
+}
+
+template <int Q>
+__global__ void __launch_bounds__(kOtfDfThreads) k_cross_otf_df(DevJob J) {
+  constexpr int B = kOtfBandDf;
+  extern __shared__ __align__(16) unsigned char sho_raw[];
+  float4* Et = reinterpret_cast<float4*>(sho_raw);                 // [B][kAsmRows][kOtfDfSrc] entries
+  float4* Ps = Et + B * kAsmRows * kOtfDfSrc;                       // [B][Q][kOtfDfSrc] densities
+  __shared__ double tb[4][B];                                       // 1/l, 1/sqrt(l), ln l, l h
+  __shared__ df tbd[4][B];                                          // the same as double-float
+  __shared__ long long vo[B];                                       // density offsets of the band's systems
+  const CrossOtf ot = J.otf_tasks[blockIdx.x];
+  const CrossAsm task = J.asms[ot.task];
+  const PairDesc pr = J.pairs[task.pair];
+  const int N = task.N, nl = ot.l1 - ot.l0 + 1;
+  const Panel pn = J.panels[task.panel];
+  const CrossTgt* tg = J.tgts + pr.tgt_off + task.row0;
+  const long long woff = J.wn_off[ot.task];
+  const double* Wn = woff >= 0 ? J.wn + woff : nullptr;
+  const int tid = threadIdx.x;
+  if (tid < nl) {
+    const int l = ot.l0 + tid;
+    tb[0][tid] = 1.0 / l;
+    tb[1][tid] = rsqrt((double)l);
+    tb[2][tid] = log((double)l);
+    tb[3][tid] = l * J.h;
+    for (int k = 0; k < 4; ++k) tbd[k][tid] = df_from(tb[k][tid]);
+    vo[tid] = J.sys[(long long)pr.j * (J.L - 1) + (l - 1)].vec_off;
+  }
+  __syncthreads();
+  const double w = kPiD / N, qw = 0.25 * w, invw = N * kInvPi;
+  const double A1 = -0.5 * kInvPi * w;
+  const double camp = kSqrtTwoOverPi * qw;
+  const double inv_h = 1.0 / J.h;
+  const df A1_d = df_from(A1), qw_d = df_from(qw);
+  // phase-2 accumulators: thread owns (row, band) pairs p = tid, tid + kOtfDfThreads (row = p / B)
+  constexpr int kPairs = kAsmRows * B / kOtfDfThreads;
+  dfacc acc_re[kPairs][Q], acc_im[kPairs][Q];
+  const int r1 = tid / kOtfDfSrc, i1 = tid % kOtfDfSrc;            // phase-1 pair
+  for (int s0 = 0; s0 < N; s0 += kOtfDfSrc) {
+    const int i = s0 + i1;
+    float4* Ep = Et + r1 * kOtfDfSrc + i1;                          // + b * kAsmRows * kOtfDfSrc
+    if (r1 < task.nrows && i < N) {
+      const CrossTgt t = tg[r1];
+      const PairSetup ps = pair_setup(J, t, J.node_x[pn.off + i], J.node_y[pn.off + i], J.node_t[pn.off + i],
+                                      t.near ? Wn[r1 * N + i] : 0.0, ot.l0, w, invw, inv_h);
+      const int lend = min(ps.lsw, ot.l1 + 1);
+      const df R_d = df_from(ps.R), A0_d = df_from(ps.A0);
+      for (int l = ot.l0; l < lend; ++l) {                          // z < 20: Taylor form
+        const int b = l - ot.l0;
+        float4 e;
+        if (J.fp64keep) {
+          e = df_split2(taylor_entry(ps, tb[3][b], tb[2][b], A1, qw));
+        } else {
+          df J0, Yh;
+          bessel0_taylor_df(df_mul(tbd[3][b], R_d), J0, Yh);
+          const df alpha = df_add_fast(df_mul(A1_d, tbd[2][b]), A0_d);
+          const df re = df_dot2(alpha, J0, df_neg(qw_d), Yh);
+          const df im = df_mul(qw_d, J0);
+          e = make_float4(re.hi, re.lo, im.hi, im.lo);
+        }
+        Ep[b * kAsmRows * kOtfDfSrc] = e;
+      }
+      if (lend <= ot.l1) {
+        AsymDf as = asym_df_start(ps, tb[3][lend - ot.l0], camp);
+        for (int l = lend; l <= ot.l1; ++l) {
+          const int b = l - ot.l0;
+          Ep[b * kAsmRows * kOtfDfSrc] = asym_df_entry(as, tb[3][b] * ps.R, tbd[0][b], tbd[1][b]);
+        }
+      }
+    } else {
+      for (int b = 0; b < nl; ++b) Ep[b * kAsmRows * kOtfDfSrc] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    // the tile's densities phi_q(omega_l)[s0 .. s0 + kOtfDfSrc) (zero past N)
+    for (int e = tid; e < nl * Q * kOtfDfSrc; e += kOtfDfThreads) {
+      const int ii = e % kOtfDfSrc, q = (e / kOtfDfSrc) % Q, b = e / (kOtfDfSrc * Q);
+      Ps[e] = s0 + ii < N ? J.phi_df[vo[b] + (long long)q * N + s0 + ii] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kPairs; ++k) {
+      const int p = tid + k * kOtfDfThreads, r = p / B, b = p % B;
+      if (b < nl) {
+        const float4* Er = Et + (b * kAsmRows + r) * kOtfDfSrc;
+        const float4* Pb = Ps + b * Q * kOtfDfSrc;
+#pragma unroll 4
+        for (int ii = 0; ii < kOtfDfSrc; ++ii) {
+          const float4 e = Er[ii];
+#pragma unroll
+          for (int q = 0; q < Q; ++q) cdf_mac(acc_re[k][q], acc_im[k][q], e, Pb[q * kOtfDfSrc + ii]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int k = 0; k < kPairs; ++k) {
+    const int p = tid + k * kOtfDfThreads, r = p / B, b = p % B;
+    if (b < nl && r < task.nrows) {
+      const long long row = J.otf_res_off[(long long)task.pair * J.L + ot.l0 + b] + task.row0 + r;
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const df a = acc_re[k][q].value(), c = acc_im[k][q].value();
+        J.apply_res[row * Q + q] = make_double2((double)a.hi + (double)a.lo, (double)c.hi + (double)c.lo);
+      }
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------------------------
 // Cross apply: W_k(x, q, l) = sum_j sum_i E_{l,k,j}[i, r] phi_j[q, i]; observation sums accumulate.
 // One thread per target row, the rows of all source blocks of the group concatenated so that warps
@@ -2024,11 +2193,20 @@ cudaError_t launch_near_weights(const DevJob& J, cudaStream_t st, int* launches)
 template <int Q>
 static cudaError_t launch_cross_otf_q(const DevJob& J, cudaStream_t st) {
   constexpr int B = OtfBand<Q>::value;
-  const size_t sh = (size_t)kAsmThreads * Q * B * sizeof(double2);
   const size_t sh_red = (size_t)Q * J.acc_cap * sizeof(double2);
   cudaError_t e = cudaFuncSetAttribute(k_cross_reduce<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh_red);
   if (e != cudaSuccess) return e;
-  if (J.n_otf > 0) k_cross_otf<Q><<<J.n_otf, kAsmThreads, sh, st>>>(J);
+  if (J.n_otf > 0) {
+    if (J.mixed) {
+      const size_t sh = (size_t)kOtfBandDf * (kAsmRows + Q) * kOtfDfSrc * sizeof(float4);
+      e = cudaFuncSetAttribute(k_cross_otf_df<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+      if (e != cudaSuccess) return e;
+      k_cross_otf_df<Q><<<J.n_otf, kOtfDfThreads, sh, st>>>(J);
+    } else {
+      const size_t sh = (size_t)kAsmThreads * Q * B * sizeof(double2);
+      k_cross_otf<Q><<<J.n_otf, kAsmThreads, sh, st>>>(J);
+    }
+  }
   k_cross_reduce<Q><<<J.n_grp, kApplyThreads, sh_red, st>>>(J);
   return cudaGetLastError();
 }

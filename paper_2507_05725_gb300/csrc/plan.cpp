@@ -447,15 +447,11 @@ int build_plan(const fthms_curve* curves, int ncurves, const fthms_arc* arcs, in
   for (size_t s = 0; s < p.sys.size(); ++s)
     if (p.own(p.sys[s].l)) p.sys_order.push_back((int)s);
   std::stable_sort(p.sys_order.begin(), p.sys_order.end(), [&](int a, int b) { return p.sys[a].N > p.sys[b].N; });
-  // LU paths: the mixed forms factor systems of kLuBigMin nodes or more with tensor-core trailing updates.
-  for (int s : p.sys_order) {
-    if (p.opt.precision >= 1 && p.sys[s].N >= kLuBigMin) {
-      p.lu_big.push_back(s);
-      p.big_max_n = std::max(p.big_max_n, p.sys[s].N);
-    } else {
-      p.lu_small.push_back(s);
-    }
-  }
+  // LU paths: the mixed forms factor systems of kLuBigMin nodes or more with tensor-core trailing updates
+  // (a prefix of sys_order, which is sorted by decreasing N; fthms_autotune may move the threshold down).
+  p.n_lu_big = 0;
+  if (p.opt.precision >= 1)
+    while (p.n_lu_big < (int)p.sys_order.size() && p.sys[p.sys_order[p.n_lu_big]].N >= kLuBigMin) ++p.n_lu_big;
   if (p.opt.precision >= 1)
     for (int s : p.sys_order)
       for (int r0 = 0; r0 < p.sys[s].N; r0 += 32) p.rchunks.push_back(ResidChunk{s, r0});
@@ -621,7 +617,7 @@ int build_plan(const fthms_curve* curves, int ncurves, const fthms_arc* arcs, in
     }
     // Near weights once per job (they depend on the target and N only); tasks of at most
     // otf_band(Q) frequencies each.
-    const int band = otf_band(p.Q);
+    const int band = p.opt.precision >= 1 ? kOtfBandDf : otf_band(p.Q);
     p.wn_off.assign(p.asms.size(), -1);
     for (size_t a = 0; a < p.asms.size(); ++a) {
       const CrossAsm& t = p.asms[a];

@@ -48,8 +48,7 @@ struct Plan {
 
   std::vector<SysDesc> sys;  // s = j*(L-1) + (l-1); systems of other ranks' frequencies have offsets -1
   std::vector<int> sys_order;  // systems by decreasing N: launch order of the per-system kernels
-  std::vector<int> lu_small, lu_big;  // LU paths (one CTA per system / tensor-core updates), decreasing N
-  int big_max_n = 0;
+  int n_lu_big = 0;            // the first n_lu_big systems of sys_order take the tensor-core LU
   long long mat_total = 0, vec_total = 0, piv_total = 0;
 
   std::vector<int> rlogN;               // distinct N values

@@ -332,8 +332,9 @@ class TorchAllreduce:
 
 
 def fthms_autotune(req, reps=3):
-    """Launch shapes (solve warps, assembly threads, time threads, restriction threads) chosen for the job."""
-    out = (C.c_int * 4)()
+    """Choices for the job: solve warps, assembly threads, time threads, restriction threads and (mixed
+    forms) the smallest N factored with tensor-core updates (0 for FP64)."""
+    out = (C.c_int * 5)()
     _check(LIB.fthms_autotune(req, int(reps), out))
     return list(out)
 

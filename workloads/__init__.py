@@ -29,7 +29,7 @@ import numpy as np
 
 __all__ = [
     "circle", "ellipse", "kite", "star", "split_closed_curve", "config1", "config2",
-    "config2_reduced", "config3", "config3_reduced", "random_small", "served_requests", "problem_summary",
+    "config2_reduced", "config3", "config3_reduced", "config4", "random_small", "served_requests", "problem_summary",
     "multipulse_samples", "with_samples",
 ]
 
@@ -173,6 +173,43 @@ def config3_reduced(seed=3, L=129, M=2, W=16.0, Q=2, n_period=1024):
     into that band (sin(6t) exp(-((t-8)/3)^2)), Q = 2 windows."""
     return config3(seed=seed, L=L, M=M, W=W, Q=Q, H=12.0, n_period=n_period, carrier=6.0, centre=8.0,
                    width=3.0, n_tout=121, T=30.0)
+
+
+def config4(N=512, seed=4, L=1024, M=8, W=400.0, Q=2, H=4.0, n_period=4096, carrier=200.0, centre=3.0, width=0.5,
+            n_tout=201, T=8.0, cross_mode=None):
+    """Mixed-precision configuration: 6 arcs of a seeded exterior configuration of 5 ellipses with semi-axes
+    uniform in [0.4, 1.2] at seeded positions with pairwise gap >= 0.5 -- the first ellipse closed and split
+    into 2 overlapping arcs, the other four open elliptic-arc obstacles of 270 deg span at seeded
+    orientations (6 arcs cannot cover 5 closed curves) -- N nodes on every arc (512, 1024 or 2048 per batch),
+    1024 frequencies on [0, 400] (1023 solved), M = 8, Q = 2 windows with H = 4 on t in [0, 8] (dt = pi/800
+    internally), plane-wave pulse sin(200t) exp(-((t-3)/0.5)^2) at a seeded angle, 5 observation points on a
+    circle of radius 6.  Cross rows stored for N <= 512 (121 GB), evaluated every step above.  Up to 8
+    refinement passes: at N = 512 the top of the band has ~1.6 nodes per wavelength and a few of those
+    systems need more than 3."""
+    rng = np.random.default_rng(seed)
+    curves = []
+    for _ in range(5):
+        a, b = (float(v) for v in rng.uniform(0.4, 1.2, size=2))
+        for _ in range(10000):
+            cx, cy = rng.uniform(-3.0, 3.0, size=2)
+            c = ellipse(a, b, float(cx), float(cy))
+            if all(_min_gap(c, o) >= 0.5 for o in curves):
+                curves.append(c)
+                break
+        else:
+            raise RuntimeError("could not place obstacle")
+    arcs = split_closed_curve(0, 2, 1.25, 0.0)
+    for ci in range(1, 5):
+        c0 = float(rng.uniform(0.0, 2.0 * math.pi))
+        arcs.append((ci, c0 - 0.75 * math.pi, c0 + 0.75 * math.pi))
+    ang = float(rng.uniform(0.0, 2.0 * math.pi))
+    signal = _signal(1, -1.0, 1.0, carrier, centre, width, direction=(math.cos(ang), math.sin(ang)))
+    ph = float(rng.uniform(0.0, 2.0 * math.pi))
+    obs = [(6.0 * math.cos(ph + 2 * math.pi * k / 5), 6.0 * math.sin(ph + 2 * math.pi * k / 5)) for k in range(5)]
+    options = _options(W, L, M, Q, H, n_period, obs, 0.0, T / (n_tout - 1), n_tout, N_fixed=N, interior=0)
+    options["cross_mode"] = (0 if N <= 512 else 1) if cross_mode is None else cross_mode
+    options["refine_max"] = 8          # some systems at the band's top (~1.6 nodes per wavelength) converge slowly
+    return {"name": f"5ellipses6arcs-N{N}", "curves": curves, "arcs": arcs, "signal": signal, "options": options}
 
 
 def random_small(seed, n_arcs_per_curve=3, n_curves=1, L=33, M=2, Q=1, N_fixed=0, W=10.0, kind=None,
