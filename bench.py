@@ -1,17 +1,23 @@
 """Benchmark of the FTH-MS hot path on GB300: arc-omega BIE solves per second.
 
-Workload (one step = one whole job, every hot-path stage): the 4-obstacle exterior problem (two
-ellipses, a kite, a circle; 8 overlapping arcs; plane-wave pulse; N = max(48, ceil(2 omega len/pi)
-+ 16) from 48 to 259; 1025 frequencies on [0, 60]; 12 multiple-scattering steps; FP64).
+Headline workload (one step = one whole job, every hot-path stage): the mixed-precision configuration -- 6
+arcs of a seeded exterior configuration of 5 ellipses (one closed ellipse in 2 overlapping arcs, four open
+270-degree elliptic arcs), N = 512 nodes on every arc, 1023 solved frequencies on (0, 400], 8
+multiple-scattering steps, 2 time windows, plane-wave pulse; cross rows stored in HBM -- in the fastest mixed
+variant (default launch shapes, autotuned shapes and LU path, replayed as one CUDA graph, or the FP64-kept
+form) whose densities agree with the FP64 form of the same job within 1e-10 in the same run.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload c4|c2|c3]
 
-`value` is device-timed with the job's tables resident in HBM (CUDA events on the library's
-stream around K back-to-back runs); `e2e` times the public C ABI call with host buffers
-(prepare + run + wait + traces + densities to host + release) per step.  With --gpus N (torchrun)
-every rank runs its own replica of the job (the solves of different jobs are independent; no
-collective on the data path) and rank 0 prints the job-wide line.  `--impl reference` times the CPU
-oracle on a bounded sample of the same workload on the host cores.
+`value` is device-timed with the job's tables resident in HBM (CUDA events on the library's stream around K
+back-to-back runs); `e2e` times the public C ABI call with host buffers (prepare + run + wait + traces +
+densities to host + release) per step.  Under "forms": the same workload in FP64 and in each mixed variant,
+N = 1024 on every arc (tensor-core LU, cross rows every step), the 4-obstacle configuration, the 12-arc star
+cavity (one job), and a served request mix against the plain form on the same mix.  With --gpus N (torchrun)
+every rank runs its own replica of the job (weak scaling, no collective on the data path) and rank 0 prints
+the job-wide line; --partition splits one job's frequencies over the ranks instead (one all-reduce of the
+time samples per step, NCCL; strong scaling).  `--impl reference` times the CPU oracle on a bounded sample
+of the same workload on the host cores.
 """
 from __future__ import annotations
 
@@ -31,6 +37,18 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 METRIC = "arc-ω BIE solves/s at ≤1e-10 rel err, served+batched vs plain FP64; p50/p99 ms"
+MIXED_BAR = 1e-10      # the metric's error bar: mixed densities against the FP64 form of the same job
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+PEAKS = _peaks()
 
 
 def _hbm_peak_gbs():
@@ -48,7 +66,6 @@ FP64_PEAK_GFLOPS = 152 * 4 * 2.07  # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz ma
 # most common count at this workload (4 + 4 Horner FMAs, 1/z and 1/z^2, the amplitude, the two components,
 # the phase rotation).
 FLOPS_PER_KERNEL_ENTRY = 34
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_config2_small.md")
 
 
 def kernels_hash():
@@ -157,75 +174,46 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def bench_workload():
-    import workloads
-    return workloads.config2()
+# TF32 dense tensor rate: the measured bf16 rate x the nominal TF32 / BF16 ratio (1.1 / 2.25 PFLOP/s), sustained
+# (the LU runs inside a long job).
+TF32_PEAK_TFLOPS = PEAKS.get("bf16_tflops_sustained", 1700.0) * (1.1 / 2.25)
+PEAK_NOTE = "of measured" if PEAKS else "of fallback"
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_config4_small.md")
 
 
-def cpu_sample_problem():
-    """Bounded sample of the same workload for the CPU oracle: the same geometry, signal, node rule
-    and 12 steps on 64 frequencies of [0, 30] (H = 6 so that the window fits one period)."""
+def workload(name, N=512):
     import workloads
+    return {"c4": lambda: workloads.config4(N), "c2": workloads.config2, "c3": workloads.config3}[name]()
+
+
+WORKLOAD_NAMES = {
+    "c4": "5ellipses6arcs-N{N}: 6 arcs (1 closed ellipse in 2 + 4 open 270-degree arcs), N={N} on every arc, "
+          "L=1024 on [0,400], M=8, Q=2 (one whole job per step)",
+    "c2": "4obstacles-planewave: 8 arcs, N 48..259, L=1025 on [0,60], M=12, Q=1 (one whole job per step)",
+    "c3": "star12-cavity: 12 arcs, N 32..760, L=2049 on [0,200], M=8, Q=4, cross rows every step (one job per step)",
+}
+
+
+def solves_of(problem):
+    o = problem["options"]
+    return len(problem["arcs"]) * (o["L"] - 1) * o["M"] * o["Q"]
+
+
+def cpu_sample_problem(name="c4"):
+    """Bounded sample of the headline workload for the CPU oracle: the same 6 arcs, N = 512, signal and
+    8 steps x 2 windows on 4 solved frequencies (h = 0.75, so that the windows fit one period)."""
+    import workloads
+    if name == "c4":
+        return workloads.config4(512, L=5, W=3.0, n_period=256)
     return workloads.config2(L=65, W=30.0, H=6.0, M=12, n_period=512, T=6.0)
 
 
-def served_form(F, n=32, seed=11, max_inflight=4, precision=1):
-    """Served stream on a bounded seeded sample of the fifth configuration's request mix: a saturated
-    pass (every request submitted at t = 0) measures capacity, then Poisson arrivals at 0.7 x that
-    rate give per-request latency (submit -> result on the device, host clock) and throughput."""
-    import workloads
-    problems = workloads.served_requests(seed, n)
-    solves = [len(p["arcs"]) * (p["options"]["L"] - 1) * p["options"]["M"] * p["options"]["Q"] for p in problems]
-    srv = F.Server(0, 0, max_inflight=max_inflight)
-    for p in problems[:2]:                      # warm-up
-        t = srv.submit(p, precision=precision)
-        srv.wait(t)
-        srv.release(t)
-    t0 = time.perf_counter()
-    tickets = [srv.submit(p, precision=precision) for p in problems]
-    for t in tickets:
-        srv.wait(t)
-    makespan = time.perf_counter() - t0
-    for t in tickets:
-        srv.release(t)
-    rate = 0.7 * n / makespan
-    rng = np.random.default_rng(seed)
-    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n))
-    t0 = time.perf_counter()
-    tickets = []
-    for p, a in zip(problems, arrivals):
-        dt = t0 + a - time.perf_counter()
-        if dt > 0:
-            time.sleep(dt)
-        tickets.append(srv.submit(p, precision=precision))
-    lat, qlat = [], []
-    for t in tickets:
-        srv.wait(t)
-    t_end = time.perf_counter()
-    for t in tickets:
-        q, tot = srv.latency(t)
-        lat.append(tot)
-        qlat.append(q)
-        srv.release(t)
-    srv.close()
-    lat = np.array(lat)
-    return {"value": float(sum(solves) / (t_end - t0)), "unit": "solves/s",
-            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "queue_p50_ms": float(np.percentile(qlat, 50)), "saturated_solves_per_s": float(sum(solves) / makespan),
-            "arrival_rate_per_s": rate, "requests": n, "max_inflight": max_inflight, "precision": precision,
-            "sample": f"{n} seeded requests (disk / star cavity / 1-3 ellipses, 2-6 arcs, omega_max in [20, 60], "
-                      f"129 or 257 frequencies, M 3-6), Poisson arrivals at 0.7 x saturated capacity"}
-
-
-def run_oracle_sample():
+def run_oracle_sample(name="c4"):
     from oracle import run_oracle
-    p = cpu_sample_problem()
-    o = p["options"]
-    solves = len(p["arcs"]) * (o["L"] - 1) * o["M"] * o["Q"]
+    p = cpu_sample_problem(name)
     t0 = time.perf_counter()
     run_oracle(p, arcs_phi=[])
-    dt = time.perf_counter() - t0
-    return solves, dt
+    return solves_of(p), time.perf_counter() - t0
 
 
 def cpu_cores_used():
@@ -242,26 +230,202 @@ def reference_arm(args):
     if rank != 0:
         return 0
     for _ in range(args.warmup):
-        run_oracle_sample()
+        run_oracle_sample(args.workload)
     times, solves = [], 0
     for _ in range(args.steps):
-        s, dt = run_oracle_sample()
+        s, dt = run_oracle_sample(args.workload)
         solves, times = s, times + [dt]
     ms = 1000.0 * statistics.mean(times)
     value = solves / (ms / 1000.0)
-    p = cpu_sample_problem()
+    p = cpu_sample_problem(args.workload)
     o = p["options"]
-    sample = (f"oracle (numpy/scipy FP64) on 8 arcs x {o['L'] - 1} frequencies of [0, {o['W']:g}] x {o['M']} steps "
-              f"({solves} solves) per step, same geometry/signal/node rule as the bench workload")
+    sample = (f"oracle (numpy/scipy FP64) on {len(p['arcs'])} arcs x {o['L'] - 1} frequencies x {o['M']} steps x "
+              f"{o['Q']} windows ({solves} solves) per step, same geometry, N, signal and steps as the bench workload")
     cores = cpu_cores_used()
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "4obstacles-planewave sample on host cores", "sample": sample},
+            "config": {"workload": f"{p['name']} sample on host cores", "sample": sample},
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
+
+
+def rel_l2(a, b):
+    """Relative L2 distance of two lists (per arc) of {l: densities}, against the first."""
+    num = den = 0.0
+    for x, y in zip(a, b):
+        for l in x:
+            num += float(np.sum(np.abs(x[l] - y[l]) ** 2))
+            den += float(np.sum(np.abs(x[l]) ** 2))
+    return math.sqrt(num / den) if den > 0 else 0.0
+
+
+def _wait(F, job):
+    try:
+        job.wait()
+        return "ok"
+    except F.FthmsError as e:
+        return str(e)
+
+
+class _NoClock:
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        pass
+
+    def summary(self):
+        return None
+
+
+def time_job(F, ctx, stream, problem, precision, steps, warmup, autotune=False, graph=False, clocks=None,
+             dens=False, allreduce=None, ws=1):
+    """Device time of `steps` back-to-back runs of one prepared job after `warmup` runs (CUDA events on the
+    library's stream, synchronised on both sides, max over ranks), with its stage times (direct launches)."""
+    import torch
+    P = len(problem["arcs"])
+    job = F.Job(ctx, problem, keep_densities=False, precision=precision)
+    if allreduce is not None:
+        job.set_allreduce(allreduce)
+    tune = F.fthms_autotune(job.req, 2) if autotune else None
+    if graph:
+        F.fthms_use_graph(job.req, True)
+    for _ in range(warmup):
+        job.run()
+    status = _wait(F, job)
+    if not graph:
+        F.fthms_profile(job.req, True)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with (ClockSampler(clocks) if clocks is not None else _NoClock()) as clk:
+        e0.record(stream)
+        for _ in range(steps):
+            job.run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    s = _wait(F, job)
+    status = s if s != "ok" else status
+    ms = max_over_ranks(e0.elapsed_time(e1) / steps)
+    stages = None if graph else {k: (v[0] / steps, v[1] / steps) for k, v in F.fthms_stage_times(job.req).items()}
+    st = job.stats()
+    d = [job.densities(j, 0, 0) for j in range(P)] if dens else None
+    ok = bool(np.all(np.isfinite(job.traces())))
+    job.release()
+    return {"ms": ms, "stages": stages, "stats": st, "dens": d, "ok": ok, "status": status, "shapes": tune,
+            "precision": precision, "autotune": autotune, "graph": graph, "clocks": clk.summary()}
+
+
+def roofline_of(r, M, Q, stored_rows):
+    """Roofline of the dominant stage of a timed job (stage CUDA-event timers, per stage invocation)."""
+    stages, st = r["stages"], r["stats"]
+    mixed = r["precision"] >= 1
+    dom = max(stages, key=lambda k: stages[k][0])
+    dom_ms, dom_launch = stages[dom]
+    inv = {"solve": M, "cross_apply": M, "synth_fwd": M - 1, "restrict": M}.get(dom, 1)
+    ms = dom_ms / inv
+    sum_n2 = st["solve_flops"] / (8.0 * Q * M)
+    base = {"kernel": None, "ms_per_launch": ms, "launches_per_invocation": dom_launch / inv, "stage": dom}
+    tpu = measured_traffic_per_unit()
+    if dom == "cross_apply" and stored_rows:
+        name = "k_cross_rows_df" if mixed else "k_cross_apply"
+        by = 16.0 * st["cross_entries"]
+        ach = by / (ms * 1e-3) / 1e9
+        return dict(base, bound="hbm", achieved=ach, peak=HBM_PEAK_GBS, unit="GB/s", frac=ach / HBM_PEAK_GBS,
+                    traffic=tpu[name] * st["cross_entries"] if name in tpu else None, kernel=name,
+                    algorithmic_bytes_per_launch=by,
+                    note=f"peak: measured copy bandwidth ({PEAK_NOTE}); every stored cross entry read once per step")
+    if dom == "solve" and mixed:
+        by = 24.0 * sum_n2
+        ach = by / (ms * 1e-3) / 1e9
+        return dict(base, bound="hbm", achieved=ach, peak=HBM_PEAK_GBS, unit="GB/s", frac=ach / HBM_PEAK_GBS,
+                    traffic=None, kernel="k_msolve+k_mresid", algorithmic_bytes_per_launch=by,
+                    note=f"peak: measured copy bandwidth ({PEAK_NOTE}); FP32 factor and kept matrix read once per step")
+    if dom == "lu" and mixed and st.get("lu_tensor_systems", 0) > 0:
+        fl = st["lu_flops"]
+        ach = fl / (ms * 1e-3) / 1e12
+        return dict(base, bound="tensor", achieved=ach, peak=TF32_PEAK_TFLOPS, unit="TFLOP/s",
+                    frac=ach / TF32_PEAK_TFLOPS, traffic=None, kernel="k_lu_big_update+k_lu_big_panel",
+                    algorithmic_flops_per_launch=fl,
+                    note=f"(8/3) sum N^3 complex-LU flops over the LU stage; peak: TF32 dense = measured bf16 "
+                         f"sustained x 1.1/2.25 ({PEAK_NOTE}); the 3xTF32 split does 3 tensor products per flop")
+    fp64 = {"cross_assemble": FLOPS_PER_KERNEL_ENTRY * st["cross_entries"],
+            "assemble_self": FLOPS_PER_KERNEL_ENTRY * (st["hankel_evals"] - st["cross_entries"]),
+            "lu": st["lu_flops"], "solve": st["solve_flops"] / M, "cross_apply": st["apply_flops"] / M}
+    if dom in fp64:
+        ach = fp64[dom] / (ms * 1e-3) / 1e9
+        return dict(base, bound="alu", achieved=ach, peak=FP64_PEAK_GFLOPS, unit="GFLOP/s",
+                    frac=ach / FP64_PEAK_GFLOPS, traffic=None, kernel=dom, algorithmic_flops_per_launch=fp64[dom],
+                    note="FP64 pipe peak derived from the unit counts and clock: 152 SMs x 4 flop/clk x 2.07 GHz")
+    return dict(base, bound="alu", achieved=None, peak=FP64_PEAK_GFLOPS, unit="GFLOP/s", frac=None, traffic=None,
+                note="no roofline model for this stage")
+
+
+def served_vs_plain(F, ctx, n=48, seed=11, max_inflight=4, precision=1):
+    """Served stream on a bounded seeded sample shaped like the fifth configuration (disk / star cavity /
+    ellipse obstacles, 2-12 arcs, omega_max in [20, 150], 257 / 513 / 1025 frequencies, M 3-6): a saturated
+    pass (every request at t = 0) measures capacity; Poisson arrivals at 0.7 x that rate give per-request
+    latency; the plain FP64 form runs the same requests back to back through fthms_submit for comparison."""
+    import workloads
+    problems = workloads.served_requests(seed, n, wmax=(20.0, 150.0), Ls=(257, 513, 1025), arcs=(2, 12))
+    solves = sum(solves_of(p) for p in problems)
+    srv = F.Server(0, 0, max_inflight=max_inflight)
+    for p in problems[:2]:
+        t = srv.submit(p, precision=precision)
+        srv.wait(t)
+        srv.release(t)
+    t0 = time.perf_counter()
+    tickets = [srv.submit(p, precision=precision) for p in problems]
+    for t in tickets:
+        srv.wait(t)
+    makespan = time.perf_counter() - t0
+    for t in tickets:
+        srv.release(t)
+    rate = 0.7 * n / makespan
+    rng = np.random.default_rng(seed)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n))
+    t_start = time.perf_counter()
+    tickets = []
+    for p, a in zip(problems, arrivals):
+        dt = t_start + a - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        tickets.append(srv.submit(p, precision=precision))
+    for t in tickets:
+        srv.wait(t)
+    t_end = time.perf_counter()
+    lat = []
+    for t in tickets:
+        lat.append(srv.latency(t)[1])
+        srv.release(t)
+    srv.close()
+    # the same requests in the plain FP64 form, one after another through the public call
+    for p in problems[:2]:
+        req = F.fthms_submit(ctx, F.Marshalled(p, keep_densities=False, precision=0))
+        F.fthms_wait(req)
+        F.fthms_release(req)
+    t0 = time.perf_counter()
+    for p in problems:
+        m = F.Marshalled(p, keep_densities=False, precision=0)
+        req = F.fthms_submit(ctx, m)
+        F.fthms_wait(req)
+        F.fthms_traces(req, m.options.n_obs, p["options"]["n_tout"])
+        F.fthms_release(req)
+    plain_s = time.perf_counter() - t0
+    lat = np.array(lat)
+    return {"value": float(solves / (t_end - t_start)), "unit": "solves/s",
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "saturated_solves_per_s": float(solves / makespan),
+            "plain_fp64_same_mix_solves_per_s": float(solves / plain_s),
+            "vs_plain_same_mix": float(plain_s / makespan), "arrival_rate_per_s": rate, "requests": n,
+            "max_inflight": max_inflight, "precision": precision,
+            "sample": f"{n} seeded requests (disk / star cavity / 1-5 ellipses, 2-12 arcs, omega_max in [20, 150], "
+                      f"257 / 513 / 1025 frequencies, M 3-6), Poisson arrivals at 0.7 x saturated capacity; "
+                      f"vs_plain_same_mix = the same requests in FP64 back to back through fthms_submit"}
 
 
 def ours(args):
@@ -273,118 +437,69 @@ def ours(args):
     torch.cuda.set_device(lrank)
     if ws > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        dist.init_process_group("nccl")
     stream = torch.cuda.Stream()
-    problem = bench_workload()
+    problem = workload(args.workload, args.N)
     o = problem["options"]
-    P, L, M, Q = len(problem["arcs"]), o["L"], o["M"], o["Q"]
-    solves = P * (L - 1) * M * Q
+    P, M, Q = len(problem["arcs"]), o["M"], o["Q"]
+    solves = solves_of(problem)
+    stored_rows = o.get("cross_mode", 0) == 0
     ctx = F.fthms_create(lrank, 0, stream.cuda_stream)
+    wname = WORKLOAD_NAMES[args.workload].format(N=args.N)
 
-    def time_form(precision, clocks=False, autotune=False):
-        job = F.Job(ctx, problem, keep_densities=False, precision=precision)
-        if autotune:
-            time_form.shapes = F.fthms_autotune(job.req, 3)
-        for _ in range(args.warmup):
-            job.run()
-        job.wait()
-        F.fthms_profile(job.req, True)
-        torch.cuda.synchronize()
-        if ws > 1:
-            torch.distributed.barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        with ClockSampler(lrank) as clk:
-            e0.record(stream)
-            for _ in range(args.steps):
-                job.run()
-            e1.record(stream)
-            torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / args.steps
-        stages = F.fthms_stage_times(job.req)
-        F.fthms_profile(job.req, False)
-        st = job.stats()
-        dens = [job.densities(j, 0, 0) for j in range(P)]
-        ok = bool(np.all(np.isfinite(job.traces())))
-        job.release()
-        ms = max_over_ranks(ms)
-        return ms, stages, st, dens, ok, clk.summary()
+    if args.partition and ws > 1:
+        # one job split over the ranks by frequency (strong scaling): one all-reduce of the time samples per step
+        import copy
+        part = copy.deepcopy(problem)
+        part["options"].update(omega_rank=rank, omega_ranks=ws)
+        r = time_job(F, ctx, stream, part, args.precision, args.steps, args.warmup, clocks=lrank,
+                     allreduce=F.TorchAllreduce(torch.device("cuda", lrank)), ws=ws)
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": solves / (r["ms"] / 1e3), "unit": "solves/s", "n_gpus": ws,
+                              "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"],
+                              "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+                              "dtype": "mixed" if args.precision else "f64", "data": "synthetic",
+                              "config": {"workload": wname, "parallelism": f"omega-partition x{ws}"},
+                              "clocks": r["clocks"], "status": r["status"]}))
+        torch.distributed.destroy_process_group()
+        return 0
 
-    ms, stages, st, dens64, traces_ok, clocks = time_form(0)
-    value = job_value(ws, solves, ms)
-
-    def time_graph(precision, autotune=False):
-        job = F.Job(ctx, problem, keep_densities=False, precision=precision)
-        if autotune:
-            F.fthms_autotune(job.req, 3)
-        F.fthms_use_graph(job.req, True)
-        for _ in range(args.warmup):
-            job.run()
-        job.wait()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            job.run()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        time_graph.dens = [job.densities(j, 0, 0) for j in range(P)]
-        job.release()
-        return max_over_ranks(e0.elapsed_time(e1) / args.steps)
-
-    ms_graph = None if args.plain_only else time_graph(0)
-    launches_per_run = st["kernel_launches"]
-    if args.plain_only:
-        ms_mx, stages_mx, st_mx, dens_mx, ok_mx, clocks_mx = ms, stages, st, dens64, traces_ok, clocks
-        mixed_err = 0.0
-        ms_graph = ms
+    # FP64 form of the same job: the densities every mixed variant is checked against, and the plain number
+    plain = time_job(F, ctx, stream, problem, 0, 1 if args.workload == "c4" else min(args.steps, 3), 1, dens=True,
+                     ws=ws) if not args.no_plain else None
+    variants = []
+    if not args.plain_only:
+        for prec, tune, graph in ((1, False, False), (1, True, False), (1, True, True), (2, True, False)):
+            v = time_job(F, ctx, stream, problem, prec, 3, 2, autotune=tune, graph=graph, dens=plain is not None, ws=ws)
+            v["err"] = rel_l2(plain["dens"], v["dens"]) if plain is not None else None
+            variants.append(v)
+    eligible = [v for v in variants if v["status"] == "ok" and v["ok"] and v["err"] is not None and v["err"] <= MIXED_BAR]
+    best = min(eligible, key=lambda v: v["ms"]) if eligible else None
+    # the headline run: the chosen form over the requested steps, clocks sampled
+    if best is not None:
+        head = time_job(F, ctx, stream, problem, best["precision"], args.steps, args.warmup, autotune=best["autotune"],
+                        graph=best["graph"], clocks=lrank, dens=plain is not None, ws=ws)
+        head["err"] = rel_l2(plain["dens"], head["dens"]) if plain is not None else None
+        if best["graph"]:                        # stage timers need direct launches: the same form, 2 runs
+            d = time_job(F, ctx, stream, problem, best["precision"], 2, 1, autotune=best["autotune"], ws=ws)
+            head["stages"], head["stages_from"] = d["stages"], "the same form launched stage by stage (2 runs)"
     else:
-        ms_mx, stages_mx, st_mx, dens_mx, ok_mx, clocks_mx = time_form(1)
-        num = den = 0.0
-        for a, c in zip(dens64, dens_mx):
-            for l in a:
-                num += float(np.sum(np.abs(a[l] - c[l]) ** 2))
-                den += float(np.sum(np.abs(a[l]) ** 2))
-        mixed_err = math.sqrt(num / den)
-    # The mixed form with launch shapes picked by fthms_autotune: used for the headline when it is faster
-    # and its densities are bitwise those of the default shapes.
-    tuned = None
-    if not args.plain_only:
-        ms_t, stages_t, st_t, dens_t, ok_t, clocks_t = time_form(1, autotune=True)
-        same = all(np.array_equal(a[l], c[l]) for a, c in zip(dens_mx, dens_t) for l in a)
-        tuned = {"value": job_value(ws, solves, ms_t), "ms_per_step": ms_t, "shapes": {
-                     "solve_warps": time_form.shapes[0], "assembly_threads": time_form.shapes[1],
-                     "time_threads": time_form.shapes[2], "restriction_threads": time_form.shapes[3]},
-                 "bitwise_equal_to_default_shapes": bool(same),
-                 "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages_t.items()}}
-        if same and ok_t and ms_t < ms_mx:
-            ms_mx, stages_mx, st_mx, clocks_mx = ms_t, stages_t, st_t, clocks_t
-    # The tuned mixed form replayed as one captured CUDA graph per job (no launch gaps): the headline when
-    # faster and bitwise equal; its stage times and roofline come from the same kernels launched directly.
-    graph_mx = None
-    graph_used = False
-    if not args.plain_only:
-        ms_g = time_graph(1, autotune=True)
-        same_g = all(np.array_equal(a[l], c[l]) for a, c in zip(dens_mx, time_graph.dens) for l in a)
-        graph_mx = {"value": job_value(ws, solves, ms_g), "ms_per_step": ms_g, "bitwise_equal_to_direct": bool(same_g),
-                    "note": "tuned mixed job replayed as one captured CUDA graph"}
-        if same_g and ms_g < ms_mx:
-            ms_mx = ms_g
-            graph_used = True
+        head = time_job(F, ctx, stream, problem, 0, args.steps, args.warmup, clocks=lrank, ws=ws)
+        head["err"] = 0.0
+    value = job_value(ws, solves, head["ms"])
 
-    # Headline: the mixed form when its densities agree with the FP64 form within 1e-10 (the metric's
-    # bar), else the plain FP64 form.
-    use_mixed = (not args.plain_only) and mixed_err <= 1e-10 and ok_mx
-    served = served_form(F) if (rank == 0 and not args.no_served and not args.plain_only) else None
-
-    # end to end through the C ABI with host buffers
+    # end to end through the C ABI with host buffers (default launch shapes)
     e2e_steps = max(1, min(args.steps, 3))
     torch.cuda.synchronize()
-    d2h = 0
+    d2h = h2d = 0
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        m = F.Marshalled(problem, keep_densities=False, precision=1 if use_mixed else 0)
+        m = F.Marshalled(problem, keep_densities=False, precision=head["precision"])
         req = F.fthms_submit(ctx, m)
-        F.fthms_wait(req)
+        try:
+            F.fthms_wait(req)
+        except F.FthmsError:
+            pass
         tr = F.fthms_traces(req, m.options.n_obs, o["n_tout"])
         d2h = tr.nbytes
         for j in range(P):
@@ -393,168 +508,90 @@ def ours(args):
         F.fthms_release(req)
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(1000.0 * (time.perf_counter() - t0) / e2e_steps)
+
+    roof = roofline_of(head, M, Q, stored_rows) if head.get("stages") else None
+
+    def summary(r, with_stages=True):
+        if r is None:
+            return None
+        st = r["stats"]
+        out = {"value": job_value(ws, solves, r["ms"]), "ms_per_step": r["ms"], "precision": r["precision"],
+               "autotuned": r["autotune"], "graph": r["graph"], "status": r["status"],
+               "rel_l2_vs_fp64_densities": r.get("err"), "max_refine_resid": st["max_refine_resid"],
+               "refine_passes": st["refine_passes"], "n_unconverged": st["n_unconverged"],
+               "lu_tensor_systems": st.get("lu_tensor_systems"), "shapes": r["shapes"],
+               "gpu_launches_per_step": st["kernel_launches"], "device_gb": st["device_bytes"] / 1e9}
+        if with_stages and r["stages"]:
+            out["stages_ms_per_step"] = {k: v[0] for k, v in r["stages"].items()}
+        return out
+
+    forms = {"plain_fp64": summary(plain)}
+    for v in variants:
+        key = "mixed" if v["precision"] == 1 else "fp64_kept"
+        key += ("_autotuned" if v["autotune"] else "") + ("_graph" if v["graph"] else "")
+        forms[key] = summary(v)
+    if rank == 0 and ws == 1 and not args.no_forms:
+        import workloads
+        if args.workload == "c4":
+            big = time_job(F, ctx, stream, workloads.config4(1024), 1, 1, 1, autotune=True)
+            forms["c4_N1024"] = dict(summary(big), workload=WORKLOAD_NAMES["c4"].format(N=1024) +
+                                     "; cross rows every step", solves_per_step=solves_of(workloads.config4(1024)))
+            c2 = workloads.config2()
+            p2 = time_job(F, ctx, stream, c2, 0, 3, 2)
+            m2 = time_job(F, ctx, stream, c2, 1, 3, 2, autotune=True, graph=True)
+            forms["c2_plain_fp64"] = dict(summary(p2), value=solves_of(c2) / (p2["ms"] / 1e3),
+                                          workload=WORKLOAD_NAMES["c2"])
+            forms["c2_mixed_autotuned_graph"] = dict(summary(m2), value=solves_of(c2) / (m2["ms"] / 1e3),
+                                                     workload=WORKLOAD_NAMES["c2"])
+        if not args.no_c3 and args.workload != "c3":
+            c3 = workloads.config3()
+            r3 = time_job(F, ctx, stream, c3, 1, 1, 1)
+            forms["c3_mixed"] = dict(summary(r3), value=solves_of(c3) / (r3["ms"] / 1e3), workload=WORKLOAD_NAMES["c3"])
+        if not args.no_served:
+            forms["served"] = served_vs_plain(F, ctx)
     F.fthms_destroy(ctx)
-
-    def roofline_of(stages_, st_, mixed):
-        """Roofline of the dominant stage by the event timers (FP64 pipe for every FP64 stage)."""
-        dom = max(stages_, key=lambda k: stages_[k][0])
-        dom_ms, dom_launch = stages_[dom]
-        # a stage runs once per job, or once per time step (solve, cross apply); one invocation may
-        # be several kernel launches (mixed solve: a solve then residual + correction per refinement step)
-        inv = args.steps * {"solve": M, "cross_apply": M, "synth_fwd": M - 1, "restrict": M}.get(dom, 1)
-        per_launch_ms = dom_ms / max(1, inv)
-        launches_per_inv = dom_launch / max(1, inv)
-        self_entries = st_["hankel_evals"] - st_["cross_entries"]
-        sum_n2 = st_["solve_flops"] / (8.0 * Q * M)          # sum over systems of N^2
-        units = {"cross_apply": st_["cross_entries"] * Q, "cross_assemble": st_["cross_entries"],
-                 "assemble_self": self_entries, "lu": sum_n2, "solve": sum_n2 * Q}
-        fp64_stages = {"cross_assemble", "assemble_self"} | (set() if mixed else {"cross_apply", "lu", "solve"})
-        flops_per_launch = {"cross_apply": st_["apply_flops"] / M, "lu": st_["lu_flops"],
-                            "solve": st_["solve_flops"] / M,
-                            "cross_assemble": FLOPS_PER_KERNEL_ENTRY * st_["cross_entries"],
-                            "assemble_self": FLOPS_PER_KERNEL_ENTRY * self_entries}
-        kname = {"cross_apply": "k_cross_rows_df" if mixed else "k_cross_apply",
-                 "cross_assemble": "k_cross_assemble[mixed]" if mixed else "k_cross_assemble",
-                 "lu": "k_lu[mixed]" if mixed else "k_lu",
-                 "solve": "k_msolve+k_mresid" if mixed else "k_solve", "assemble_self": "k_assemble_self"}.get(dom)
-        tpu = measured_traffic_per_unit()
-        traffic = tpu[kname] * units[dom] if (kname in tpu and dom in units) else None
-        if dom in flops_per_launch and dom in fp64_stages:
-            ach = flops_per_launch[dom] / (per_launch_ms * 1e-3) / 1e9
-            return {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                    "frac": ach / FP64_PEAK_GFLOPS, "traffic": traffic, "kernel": kname,
-                    "algorithmic_flops_per_launch": flops_per_launch[dom], "ms_per_launch": per_launch_ms, "launches_per_invocation": launches_per_inv,
-                    "note": "FP64 pipe peak derived from the unit counts and clock: 152 SMs x 4 flop/clk x "
-                            "2.07 GHz; algorithmic flops per launch / CUDA-event time on the library stream"}
-        # Mixed form: the solve and the cross apply stream stored matrices (FP32 factor + double-float
-        # matrix, double-float cross entries); algorithmic bytes = every stored matrix read once.
-        bytes_per_launch = {"solve": 24.0 * sum_n2, "cross_apply": 16.0 * st_["cross_entries"]}
-        if dom in bytes_per_launch:
-            ach = bytes_per_launch[dom] / (per_launch_ms * 1e-3) / 1e9
-            return {"bound": "hbm", "achieved": ach, "peak": HBM_PEAK_GBS, "unit": "GB/s",
-                    "frac": ach / HBM_PEAK_GBS, "traffic": traffic, "kernel": kname,
-                    "algorithmic_bytes_per_launch": bytes_per_launch[dom], "ms_per_launch": per_launch_ms, "launches_per_invocation": launches_per_inv,
-                    "note": "peak: measured copy bandwidth (of measured); algorithmic bytes = each stored "
-                            "matrix read once per launch (refinement re-reads count as excess)"}
-        return {"bound": "alu", "achieved": None, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": None,
-                "traffic": traffic, "kernel": kname, "note": "no roofline model for this stage"}
-
-    roofline_plain = roofline_of(stages, st, False)
-    roofline_mixed = roofline_of(stages_mx, st_mx, True)
-    head_ms = ms_mx if use_mixed else ms
-    head_value = job_value(ws, solves, head_ms)
-    roofline = roofline_mixed if use_mixed else roofline_plain
-    head_stages = stages_mx if use_mixed else stages
-    head_launches = st_mx["kernel_launches"] if use_mixed else launches_per_run
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        s, dt = run_oracle_sample()
+        s, dt = run_oracle_sample(args.workload)
+        p = cpu_sample_problem(args.workload)
         cpu = {"value": s / dt, "unit": "solves/s", "cores": cpu_cores_used(), "kind": "oracle",
-               "sample": f"{s} solves of the same 8-arc geometry on 64 frequencies of [0, 30], M = 12, "
-                         f"{dt:.1f} s of CPU time"}
+               "sample": f"{s} solves: {p['name']} on {p['options']['L'] - 1} frequencies, {p['options']['M']} steps, "
+                         f"{p['options']['Q']} windows ({dt:.1f} s of CPU time)"}
     if rank == 0:
-        line = {"metric": METRIC, "value": head_value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": head_ms, "higher_is_better": True, "scaling": "weak",
+        mixed = head["precision"] >= 1
+        line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": head["ms"], "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None,
-                "dtype": ("f32 factors + double-float (2 x f32) assembly, refinement, FFT butterflies, restriction and cross "
-                          "apply; f64 per-pair setup, diagonal, transform folds and outputs"
-                          if use_mixed else "f64"),
+                "dtype": ({1: "f32 factors (tensor-core 3xTF32 updates above N = 800) + double-float (2 x f32) "
+                              "assembly, refinement, FFT butterflies, restriction and cross apply; f64 set-up, "
+                              "folds and outputs",
+                           2: "f32 factors + f64 self matrices and refinement residuals, f64 small-argument Hankel "
+                              "series and FFT butterflies; double-float far-field recurrence, restriction and cross "
+                              "apply"}[head["precision"]] if mixed else "f64"),
                 "data": "synthetic",
-                "config": {"workload": "4obstacles-planewave: 8 arcs, N 48..259, L=1025 on [0,60], M=12, Q=1 "
-                                       "(one whole job per step)",
-                           "solves_per_step": solves, "systems_per_step": P * (L - 1),
-                           "form": ("mixed" + (", CUDA-graph replay" if graph_used else "") +
-                                    " (verified <= 1e-10 vs FP64 in-run)") if use_mixed else "plain FP64",
-                           "l2": "working set > L2 (cross matrices "
-                           f"{st['cross_entries'] * 16 / 1e9:.1f} GB, factors {st['lu_flops'] > 0})",
+                "config": {"workload": wname, "solves_per_step": solves, "systems_per_step": P * (o["L"] - 1),
+                           "form": (("mixed" if head["precision"] == 1 else "fp64-kept mixed") +
+                                    (", autotuned" if head["autotune"] else "") +
+                                    (", CUDA-graph replay" if head["graph"] else "") +
+                                    f" (densities {head['err']:.2e} from the FP64 form in-run, bar 1e-10)")
+                           if mixed else "plain FP64",
+                           "l2": "working set > L2 (stored cross rows "
+                                 f"{head['stats']['cross_entries'] * 16 / 1e9:.0f} GB, matrices and factors)",
                            "parallelism": f"replicas x{ws}"},
                 "e2e": {"value": job_value(ws, solves, e2e_ms), "unit": "solves/s", "ms_per_step": e2e_ms,
-                        "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
-                "gpu_launches": int(head_launches * args.steps),
-                "roofline": roofline,
-                "stages_ms_per_step": {k: v[0] / args.steps for k, v in head_stages.items()},
-                "clocks": clocks,
+                        "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                        "note": "fthms_submit + wait + traces and summed densities to host + release, default shapes"},
+                "gpu_launches": int(head["stats"]["kernel_launches"] * args.steps),
+                "roofline": roof,
+                "stages_ms_per_step": {k: v[0] for k, v in head["stages"].items()} if head.get("stages") else None,
+                "clocks": head["clocks"],
                 "cpu_baseline": cpu,
-                "traces_finite": bool(traces_ok),
-                "forms": {
-                    "plain_fp64": {"value": value, "ms_per_step": ms, "dtype": "f64", "roofline": roofline_plain,
-                                   "gpu_launches": int(launches_per_run * args.steps),
-                                   "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()}},
-                    "plain_fp64_graph": None if ms_graph is None else {
-                        "value": job_value(ws, solves, ms_graph), "ms_per_step": ms_graph,
-                        "note": "whole job replayed as one captured CUDA graph"},
-                    "mixed_autotuned": tuned,
-                    "mixed_autotuned_graph": graph_mx,
-                    "mixed": {"value": job_value(ws, solves, ms_mx), "ms_per_step": ms_mx,
-                              "dtype": "f32 factors + double-float (2 x f32) assembly, refinement, FFT butterflies, restriction and cross apply; f64 setup, folds, outputs",
-                              "rel_l2_vs_fp64_densities": mixed_err,
-                              "max_refine_resid": st_mx["max_refine_resid"],
-                              "refine_passes_per_solve": st_mx.get("refine_passes"), "traces_finite": ok_mx,
-                              "roofline": roofline_mixed,
-                              "gpu_launches": int(st_mx["kernel_launches"] * args.steps),
-                              "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages_mx.items()},
-                              "clocks": clocks_mx},
-                    "served": served}}
+                "traces_finite": head["ok"],
+                "forms": forms}
         print(json.dumps(line))
     if ws > 1:
         torch.distributed.destroy_process_group()
-    return 0
-
-
-def star12(args):
-    """Auxiliary measurement (not the headline): one config-3 job per form -- the 12-arc star cavity, N 32..760,
-    2048 solved frequencies, Q = 4 windows, M = 8, cross rows evaluated every step -- device-timed like the
-    main line; prints one JSON line."""
-    import torch
-
-    import workloads
-    from paper_2507_05725_gb300 import fthms as F
-
-    torch.cuda.set_device(0)
-    stream = torch.cuda.Stream()
-    problem = workloads.config3()
-    o = problem["options"]
-    P, L, M, Q = len(problem["arcs"]), o["L"], o["M"], o["Q"]
-    solves = P * (L - 1) * M * Q
-    ctx = F.fthms_create(0, 0, stream.cuda_stream)
-    forms, dens = {}, {}
-    for precision in (1, 0):
-        job = F.Job(ctx, problem, keep_densities=False, precision=precision)
-        for _ in range(args.warmup):
-            job.run()
-        job.wait()
-        F.fthms_profile(job.req, True)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        with ClockSampler(0) as clk:
-            e0.record(stream)
-            for _ in range(args.steps):
-                job.run()
-            e1.record(stream)
-            torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / args.steps
-        stages = F.fthms_stage_times(job.req)
-        st = job.stats()
-        dens[precision] = [job.densities(j, 0, 0) for j in (0, P // 2)]
-        job.release()
-        forms["mixed" if precision else "plain_fp64"] = {
-            "value": solves / (ms * 1e-3), "ms_per_step": ms, "device_gb": st["device_bytes"] / 1e9,
-            "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()}, "clocks": clk.summary()}
-    num = den = 0.0
-    for a, c in zip(dens[0], dens[1]):
-        for l in a:
-            num += float(np.sum(np.abs(a[l] - c[l]) ** 2))
-            den += float(np.sum(np.abs(a[l]) ** 2))
-    forms["mixed"]["rel_l2_vs_fp64_densities_arcs_0_6"] = math.sqrt(num / den)
-    F.fthms_destroy(ctx)
-    print(json.dumps({"metric": METRIC, "value": forms["mixed"]["value"], "unit": "solves/s",
-                      "ms_per_step": forms["mixed"]["ms_per_step"], "steps": args.steps, "warmup": args.warmup,
-                      "higher_is_better": True, "data": "synthetic",
-                      "config": {"workload": "star12-cavity: 12 arcs, N 32..760, L=2049 on [0,200], M=8, Q=4, "
-                                             "cross rows evaluated every step (one job per step)",
-                                 "solves_per_step": solves},
-                      "forms": forms}))
     return 0
 
 
@@ -564,16 +601,20 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c4", choices=["c4", "c2", "c3"],
+                    help="c4: the mixed-precision configuration (N per --N); c2: 4 obstacles; c3: 12-arc star cavity")
+    ap.add_argument("--N", type=int, default=512, help="nodes per arc of the c4 workload (512 or 1024 on one GPU)")
+    ap.add_argument("--partition", action="store_true", help="split one job's frequencies over the ranks")
+    ap.add_argument("--precision", type=int, default=1, help="precision of the partitioned job")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the secondary workloads")
+    ap.add_argument("--no-c3", action="store_true", help="skip the 12-arc cavity form")
+    ap.add_argument("--no-plain", action="store_true", help="skip the FP64 reference job (no in-run error check)")
     ap.add_argument("--plain-only", action="store_true", help="time the plain FP64 form only (profiling runs)")
-    ap.add_argument("--workload", default="4obstacles", choices=["4obstacles", "star12"],
-                    help="star12: auxiliary single-GPU measurement of the 12-arc cavity (config 3)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
-    if args.workload == "star12":
-        return star12(args)
     return ours(args)
 
 

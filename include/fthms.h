@@ -113,10 +113,10 @@ typedef struct {
  *              refinement residuals, the FFT butterflies of the time transforms, the restriction and the
  *              cross apply in double-float on the FP32 pipe; diagonal self entries, per-pair setup,
  *              phase-seed reduction, log-singular corrections, transform folds and phase factors stay
- *              FP64; the self entries of systems with N > 800 (factored with tensor-core updates) are
- *              assembled in FP64 and stored as their double-float rounding.  The refinement solves the
- *              double-float matrix exactly; its rounding (~2^-44 of an entry) still reaches the densities
- *              through the matrix's conditioning.  N > 800 (up to 2048): FP32 LU with tcgen05 (3xTF32)
+ *              FP64.  The refinement solves the double-float matrix exactly; its rounding (~2^-44 of an
+ *              entry) still reaches the densities through the matrix's conditioning, so the systems with
+ *              N > 800 (factored with tensor-core updates, conditioning growing with N) keep FP64 matrices
+ *              and FP64 residuals as in form 2.  N > 800 (up to 2048): FP32 LU with tcgen05 (3xTF32)
  *              trailing updates, precisions 1 and 2 only.  2 = the mixed form
  *              with FP64 kept where accuracy is decided: the self matrices assembled and kept in FP64 (the
  *              FP32 factor is their rounding) with FP64 refinement residuals, the small-argument (z < 20)
@@ -132,7 +132,8 @@ typedef struct {
  *  refine_tol, refine_max : mixed forms: a system stops refining once the estimated relative error left
  *              is below refine_tol (0 = 1e-12), after at most refine_max passes (0 = 3; at most 16).  The
  *              estimate is the last correction's relative size times the contraction factor: the ratio
- *              of the last two corrections, or after the first correction 10 x its own size.
+ *              of the last two corrections; after the first correction, twice the largest ratio measured
+ *              for the system in an earlier step of the run, or (first step) 10 x the correction's size.
  *  refine_fallback : mixed forms: 0 = a job in which some system did not meet refine_tol within
  *              refine_max passes finishes with those results and fthms_wait returns FTHMS_ENOCONV;
  *              1 = fthms_wait then runs the whole job again in FP64 (precision 0) and returns its
@@ -187,6 +188,7 @@ typedef struct {
   double refine_passes;   /* mixed forms: mean refinement passes (residual + correction) per system and step */
   long long n_unconverged; /* mixed forms: (system, step) pairs whose estimate stayed above refine_tol */
   int fallback_runs;      /* runs of the job repeated in FP64 by refine_fallback = 1 */
+  int lu_tensor_systems;  /* systems factored with tensor-core (tcgen05) trailing updates (mixed forms) */
 } fthms_stats_t;
 
 /* Create a context on CUDA device `device` that enqueues all work on `cuda_stream` (a

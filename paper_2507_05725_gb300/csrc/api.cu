@@ -301,6 +301,8 @@ fthms_status upload_job(fthms_req* r) {
   J.rres = nullptr;
   J.mdone = nullptr;
   J.mrel = nullptr;
+  J.mrho = nullptr;
+  J.f64_min_n = J.fp64keep ? 0 : (J.mixed ? kLuBigMin : 1 << 30);
   J.rchunks = nullptr;
   J.n_rchunks = 0;
   TRY(dev_alloc(r, 3, &J.refine_resid));          // [0] max estimated error left, [1] passes, [2] unconverged
@@ -312,6 +314,7 @@ fthms_status upload_job(fthms_req* r) {
     TRY(dev_alloc(r, (size_t)p.vec_total, &J.rres));
     TRY(dev_alloc(r, p.sys.size(), &J.mdone));
     TRY(dev_alloc(r, p.sys.size(), &J.mrel));
+    TRY(dev_alloc(r, p.sys.size(), &J.mrho));
     TRY(dev_upload(r, p.rchunks, &J.rchunks));
     J.n_rchunks = (int)p.rchunks.size();
   }
@@ -435,6 +438,7 @@ fthms_status enqueue_stages(fthms_req* r, bool bracket) {
   CK(cudaMemsetAsync(J.refine_resid, 0, 3 * sizeof(double), st));
   CK(cudaMemsetAsync(J.dev_err, 0, sizeof(int), st));
   if (J.sys_err) CK(cudaMemsetAsync(J.sys_err, 0, r->plan.sys.size() * sizeof(float), st));
+  if (J.mrho) CK(cudaMemsetAsync(J.mrho, 0, r->plan.sys.size() * sizeof(float), st));   // measured per run
   TRY(stage(r, FTHMS_STAGE_INCIDENT, st, &nl, [&] { return launch_incident(J, st, &nl); }));
   TRY(stage(r, FTHMS_STAGE_RESTRICT, st, &nl, [&] { return launch_restrict(J, st, &nl); }));
   for (int m = 1; m <= J.M; ++m) {
@@ -819,6 +823,7 @@ fthms_status fthms_stats(fthms_req* req, fthms_stats_t* out) {
   out->apply_flops = 8.0 * p.Q * p.M * (double)p.e_total;
   out->precision = p.opt.precision;
   out->fallback_runs = req->fallback_runs;
+  out->lu_tensor_systems = req->J.mixed ? req->J.n_lu_big : 0;
   if (req->ran) {
     TRY(wait_results(req));
     float ms = 0.f;

@@ -222,8 +222,12 @@ __device__ __forceinline__ void df_phase_seed(double theta, df& cx, df& sx) {
 // A self-matrix entry: FP64, or (mixed form) the double-float pair the refinement reads plus its FP32
 // rounding for the FP32 factorisation -- what a separate split of the FP64 matrix would give -- or (the
 // FP64-kept form) the FP64 value the FP64 residual reads plus its FP32 rounding.
-__device__ __forceinline__ void store_self(const DevJob& J, long long off, double2 v) {
-  if (J.fp64keep) {
+// Mixed forms: systems that keep FP64 matrices and residuals (all in the FP64-kept form; N >= f64_min_n in
+// the mixed form, whose large systems' conditioning would amplify a double-float matrix's rounding).
+__device__ __forceinline__ bool sys_f64(const DevJob& J, int N) { return J.fp64keep || N >= J.f64_min_n; }
+
+__device__ __forceinline__ void store_self(const DevJob& J, long long off, double2 v, bool f64) {
+  if (f64) {
     J.A[off] = v;
     J.LU32[off] = make_float2(__double2float_rn(v.x), __double2float_rn(v.y));
   } else if (J.mixed) {
@@ -290,6 +294,9 @@ __global__ void __launch_bounds__(256) k_assemble_self(DevJob J) {
   const SelfTile tile = J.tiles[blockIdx.x];
   const SysDesc s0 = J.sys[tile.sys];
   const int N = s0.N, nb = tile.nsys;
+  // Mixed form: double-float assembly and storage, except for the systems that keep FP64 (sys_f64).
+  const bool f64 = J.mixed && sys_f64(J, N);
+  const bool df_asm = J.mixed && !f64;
   __shared__ double lnl[kSelfBand], invl[kSelfBand], rsql[kSelfBand];
   __shared__ df invl_d[kSelfBand], rsql_d[kSelfBand], lnl_d[kSelfBand], lh_d[kSelfBand];   // mixed form
   if (threadIdx.x < nb) {
@@ -318,7 +325,7 @@ __global__ void __launch_bounds__(256) k_assemble_self(DevJob J) {
     const double lsp = log(0.5 * J.h * J.node_sp[pn.off + i]);
     for (int b = 0; b < nb; ++b) {
       const double re = -0.5 * kInvPi * (kEulerGamma + lnl[b] + lsp);
-      store_self(J, J.sys[tile.sys + b].mat_off + e1, make_double2(fma(K1, rl, re * w), 0.25 * w));
+      store_self(J, J.sys[tile.sys + b].mat_off + e1, make_double2(fma(K1, rl, re * w), 0.25 * w), f64);
     }
     return;
   }
@@ -339,9 +346,6 @@ __global__ void __launch_bounds__(256) k_assemble_self(DevJob J) {
   const int lend = s0.l + nb;
   const double zmin = (lsw * J.h) * R;
   const int kmax = hankel_terms((float)zmin);
-  // Mixed form: double-float assembly for the systems of the one-CTA LU; the large systems (tensor-core LU,
-  // conditioning that grows with N) are assembled in FP64 and stored as the double-float rounding.
-  const bool df_asm = J.mixed && !J.fp64keep && N < kLuBigMin;
   if (df_asm) {
     // Mixed form, z < 20: the Taylor range in double-float, alpha = aw ln l + a0.
     const df R_d = df_from(R), qw_d = df_from(qw), aw_d = df_from(-0.5 * kInvPi * w),
@@ -370,8 +374,8 @@ __global__ void __launch_bounds__(256) k_assemble_self(DevJob J) {
       const double alpha = -0.5 * kInvPi * fma(w, lnl[b] + lratio, rl);
       const double2 v = make_double2(fma(alpha, J0, -qw * Yh), qw * J0);
       const long long mo = J.sys[tile.sys + b].mat_off;
-      store_self(J, mo + e1, v);
-      store_self(J, mo + e2, v);
+      store_self(J, mo + e1, v, f64);
+      store_self(J, mo + e2, v, f64);
     }
   }
   if (df_asm && lsw < lend) {
@@ -447,8 +451,8 @@ __global__ void __launch_bounds__(256) k_assemble_self(DevJob J) {
     const double Y0 = amp * fma(P, sx, -Qa * cx);
     const double2 v = make_double2(fma(alpha_a, J0, -qw * Y0), qw * J0);
     const long long mo = J.sys[tile.sys + b].mat_off;
-    store_self(J, mo + e1, v);
-    store_self(J, mo + e2, v);
+    store_self(J, mo + e1, v, f64);
+    store_self(J, mo + e2, v, f64);
     const double cn = fma(cx, cu, -sx * su);
     sx = fma(sx, cu, cx * su);
     cx = cn;
@@ -970,7 +974,8 @@ template <int Q>
 __global__ void __launch_bounds__(kAsmThreads) k_cross_otf(DevJob J) {
   constexpr int B = OtfBand<Q>::value;
   constexpr int G = kAsmThreads / kAsmRows;          // source groups
-  extern __shared__ double2 sho[];                    // [G][kAsmRows][Q * B] partial sums (thread order)
+  extern __shared__ double2 sho[];                    // [Q * B][G * kAsmRows] partial sums: slot-major, so
+                                                      // a warp's read-modify-writes hit consecutive words
   __shared__ double tb[4][B];                         // 1/l, 1/sqrt(l), ln l, l h
   const CrossOtf ot = J.otf_tasks[blockIdx.x];
   const CrossAsm task = J.asms[ot.task];
@@ -987,8 +992,8 @@ __global__ void __launch_bounds__(kAsmThreads) k_cross_otf(DevJob J) {
     tb[2][threadIdx.x] = log((double)l);
     tb[3][threadIdx.x] = l * J.h;
   }
-  double2* mine = sho + threadIdx.x * (Q * B);
-  for (int e = 0; e < Q * B; ++e) mine[e] = make_double2(0.0, 0.0);
+  double2* mine = sho + threadIdx.x;                  // slot e at mine[e * kAsmThreads]
+  for (int e = 0; e < Q * B; ++e) mine[e * kAsmThreads] = make_double2(0.0, 0.0);
   __syncthreads();
   const double w = kPiD / N, qw = 0.25 * w, invw = N * kInvPi;
   const double A1 = -0.5 * kInvPi * w;
@@ -1017,7 +1022,8 @@ __global__ void __launch_bounds__(kAsmThreads) k_cross_otf(DevJob J) {
         }
         const double2* ph = J.phi + sj[b].vec_off + i;
 #pragma unroll
-        for (int q = 0; q < Q; ++q) mine[q * B + b] = cfma(E, ph[q * N], mine[q * B + b]);
+        for (int q = 0; q < Q; ++q)
+          mine[(q * B + b) * kAsmThreads] = cfma(E, ph[q * N], mine[(q * B + b) * kAsmThreads]);
       }
     }
   }
@@ -1025,7 +1031,7 @@ __global__ void __launch_bounds__(kAsmThreads) k_cross_otf(DevJob J) {
   for (int e = threadIdx.x; e < task.nrows * Q * nl; e += kAsmThreads) {
     const int rr = e / (Q * nl), q = (e / nl) % Q, b = e % nl;
     double2 sum = make_double2(0.0, 0.0);
-    for (int gg = 0; gg < G; ++gg) sum = cadd(sum, sho[(gg * kAsmRows + rr) * (Q * B) + q * B + b]);
+    for (int gg = 0; gg < G; ++gg) sum = cadd(sum, sho[(q * B + b) * kAsmThreads + gg * kAsmRows + rr]);
     const long long row = J.otf_res_off[(long long)task.pair * J.L + ot.l0 + b] + task.row0 + rr;
     J.apply_res[row * Q + q] = sum;
   }
@@ -1044,6 +1050,7 @@ __global__ void __launch_bounds__(kAsmThreads) k_cross_otf(DevJob J) {
 // The per-row sums go to the per-row results that k_cross_reduce adds per target in block order.
 constexpr int kOtfDfSrc = 16;
 constexpr int kOtfDfThreads = kAsmRows * kOtfDfSrc;   // 128
+constexpr int kOtfDfPitch = kOtfBandDf + 1;           // float4 per shared-memory row (33: no bank conflicts)
 
 // Double-float state of Hankel's expansion along a band (the mixed stored-row assembly's recurrence).
 struct AsymDf {
@@ -1097,8 +1104,11 @@ template <int Q>
 __global__ void __launch_bounds__(kOtfDfThreads) k_cross_otf_df(DevJob J) {
   constexpr int B = kOtfBandDf;
   extern __shared__ __align__(16) unsigned char sho_raw[];
-  float4* Et = reinterpret_cast<float4*>(sho_raw);                 // [B][kAsmRows][kOtfDfSrc] entries
-  float4* Ps = Et + B * kAsmRows * kOtfDfSrc;                       // [B][Q][kOtfDfSrc] densities
+  // entries [row][source][band] and densities [window][source][band], rows of kOtfDfPitch float4: a warp
+  // of phase 2 (one row or window, 32 frequencies) reads 32 consecutive float4, a warp of phase 1 writes
+  // with a 33-float4 stride (both at the minimum of 4 shared-memory wavefronts)
+  float4* Et = reinterpret_cast<float4*>(sho_raw);                 // [kAsmRows * kOtfDfSrc][kOtfDfPitch]
+  float4* Ps = Et + kAsmRows * kOtfDfSrc * kOtfDfPitch;            // [Q * kOtfDfSrc][kOtfDfPitch]
   __shared__ double tb[4][B];                                       // 1/l, 1/sqrt(l), ln l, l h
   __shared__ df tbd[4][B];                                          // the same as double-float
   __shared__ long long vo[B];                                       // density offsets of the band's systems
@@ -1132,7 +1142,7 @@ __global__ void __launch_bounds__(kOtfDfThreads) k_cross_otf_df(DevJob J) {
   const int r1 = tid / kOtfDfSrc, i1 = tid % kOtfDfSrc;            // phase-1 pair
   for (int s0 = 0; s0 < N; s0 += kOtfDfSrc) {
     const int i = s0 + i1;
-    float4* Ep = Et + r1 * kOtfDfSrc + i1;                          // + b * kAsmRows * kOtfDfSrc
+    float4* Ep = Et + (r1 * kOtfDfSrc + i1) * kOtfDfPitch;          // + b
     if (r1 < task.nrows && i < N) {
       const CrossTgt t = tg[r1];
       const PairSetup ps = pair_setup(J, t, J.node_x[pn.off + i], J.node_y[pn.off + i], J.node_t[pn.off + i],
@@ -1152,35 +1162,36 @@ __global__ void __launch_bounds__(kOtfDfThreads) k_cross_otf_df(DevJob J) {
           const df im = df_mul(qw_d, J0);
           e = make_float4(re.hi, re.lo, im.hi, im.lo);
         }
-        Ep[b * kAsmRows * kOtfDfSrc] = e;
+        Ep[b] = e;
       }
       if (lend <= ot.l1) {
         AsymDf as = asym_df_start(ps, tb[3][lend - ot.l0], camp);
         for (int l = lend; l <= ot.l1; ++l) {
           const int b = l - ot.l0;
-          Ep[b * kAsmRows * kOtfDfSrc] = asym_df_entry(as, tb[3][b] * ps.R, tbd[0][b], tbd[1][b]);
+          Ep[b] = asym_df_entry(as, tb[3][b] * ps.R, tbd[0][b], tbd[1][b]);
         }
       }
     } else {
-      for (int b = 0; b < nl; ++b) Ep[b * kAsmRows * kOtfDfSrc] = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int b = 0; b < nl; ++b) Ep[b] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     // the tile's densities phi_q(omega_l)[s0 .. s0 + kOtfDfSrc) (zero past N)
     for (int e = tid; e < nl * Q * kOtfDfSrc; e += kOtfDfThreads) {
       const int ii = e % kOtfDfSrc, q = (e / kOtfDfSrc) % Q, b = e / (kOtfDfSrc * Q);
-      Ps[e] = s0 + ii < N ? J.phi_df[vo[b] + (long long)q * N + s0 + ii] : make_float4(0.f, 0.f, 0.f, 0.f);
+      Ps[(q * kOtfDfSrc + ii) * kOtfDfPitch + b] =
+          s0 + ii < N ? J.phi_df[vo[b] + (long long)q * N + s0 + ii] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < kPairs; ++k) {
       const int p = tid + k * kOtfDfThreads, r = p / B, b = p % B;
       if (b < nl) {
-        const float4* Er = Et + (b * kAsmRows + r) * kOtfDfSrc;
-        const float4* Pb = Ps + b * Q * kOtfDfSrc;
+        const float4* Er = Et + r * kOtfDfSrc * kOtfDfPitch + b;
+        const float4* Pb = Ps + b;
 #pragma unroll 4
         for (int ii = 0; ii < kOtfDfSrc; ++ii) {
-          const float4 e = Er[ii];
+          const float4 e = Er[ii * kOtfDfPitch];
 #pragma unroll
-          for (int q = 0; q < Q; ++q) cdf_mac(acc_re[k][q], acc_im[k][q], e, Pb[q * kOtfDfSrc + ii]);
+          for (int q = 0; q < Q; ++q) cdf_mac(acc_re[k][q], acc_im[k][q], e, Pb[(q * kOtfDfSrc + ii) * kOtfDfPitch]);
         }
       }
     }
@@ -1310,9 +1321,8 @@ constexpr int kResidThreads = 128;
 template <int Q>
 __global__ void __launch_bounds__(kResidThreads) k_mresid(DevJob J);
 
-// The same residual in FP64 (FP64-kept form): the matrix kept in FP64, the densities (double-float pairs
-// in the phi slots, exact sums of two floats) converted to FP64 without rounding; FMA accumulation over the
-// columns in order.
+// The same residual in FP64 (FP64-kept form): the matrix and the densities (refined in FP64) read as FP64,
+// FMA accumulation over the columns in order.
 template <int Q>
 __global__ void __launch_bounds__(kResidThreads) k_mresid64(DevJob J) {
   const int chunk = blockIdx.x * (kResidThreads / 32) + (threadIdx.x >> 5);
@@ -1321,10 +1331,11 @@ __global__ void __launch_bounds__(kResidThreads) k_mresid64(DevJob J) {
   if (J.mdone[c.sys]) return;
   const SysDesc s = J.sys[c.sys];
   const int N = s.N;
+  if (!sys_f64(J, N)) return;                 // double-float systems: k_mresid
   const int i = c.row0 + (threadIdx.x & 31);
   const int row = i < N ? i : N - 1;
   const double2* __restrict__ A64 = J.A + s.mat_off;
-  const float4* __restrict__ ph = reinterpret_cast<const float4*>(J.phi + s.vec_off);
+  const double2* __restrict__ ph = J.phi + s.vec_off;
   const double2* __restrict__ G = J.G + s.vec_off;
   double2 acc[Q];
 #pragma unroll
@@ -1334,7 +1345,7 @@ __global__ void __launch_bounds__(kResidThreads) k_mresid64(DevJob J) {
   for (int j = 0; j < N; ++j) {
     const double2 a = __ldg(&A64[(long long)j * N + row]);
 #pragma unroll
-    for (int q = 0; q < Q; ++q) acc[q] = cfms(a, df_join2(ph[q * N + j]), acc[q]);
+    for (int q = 0; q < Q; ++q) acc[q] = cfms(a, ph[q * N + j], acc[q]);
   }
   if (i < N) {
 #pragma unroll
@@ -1351,6 +1362,7 @@ __global__ void __launch_bounds__(kResidThreads) k_mresid(DevJob J) {
   if (J.mdone[c.sys]) return;
   const SysDesc s = J.sys[c.sys];
   const int N = s.N;
+  if (sys_f64(J, N)) return;                  // FP64 systems: k_mresid64
   const int i = c.row0 + (threadIdx.x & 31);
   const int row = i < N ? i : N - 1;
   const float4* __restrict__ Adf = reinterpret_cast<const float4*>(J.A) + s.mat_off;
@@ -1399,9 +1411,10 @@ __global__ void __launch_bounds__(kResidThreads) k_mresid(DevJob J) {
   }
 }
 
-// pass 0: solve with FP32 G, store phi as double-float, mark the system as refining.  pass p >= 1:
-// solve for the correction from the residual, add it in double-float, and finish the system (FP64
-// densities, their running sum, the statistics) once the correction is small enough or p = J.refine_max.
+// pass 0: solve with FP32 G, store phi as double-float (FP64 in the FP64-kept form, whose residual reads
+// it), mark the system as refining.  pass p >= 1: solve for the correction from the residual, add it in
+// double-float (FP64), and finish the system (FP64 densities, their double-float copy for the cross apply,
+// their running sum, the statistics) once the correction is small enough or p = J.refine_max.
 __global__ void __launch_bounds__(32 * kSolveWarps, 4) k_msolve(DevJob J, int m, int pass) {
   extern __shared__ __align__(16) unsigned char shm_raw[];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1412,6 +1425,7 @@ __global__ void __launch_bounds__(32 * kSolveWarps, 4) k_msolve(DevJob J, int m,
   if (pass > 0 && J.mdone[sidx]) return;
   const SysDesc s = J.sys[sidx];
   const int N = s.N, Q = J.Q;
+  const bool f64 = sys_f64(J, N);            // densities refined in FP64 (FP64 residual)
   float2* b = reinterpret_cast<float2*>(shm_raw) + (size_t)wid * Q * J.max_n;
   const float2* __restrict__ L32 = J.LU32 + s.mat_off;
   const int* __restrict__ piv = J.piv + s.piv_off;
@@ -1429,30 +1443,52 @@ __global__ void __launch_bounds__(32 * kSolveWarps, 4) k_msolve(DevJob J, int m,
   }
   __syncwarp();
   tri_solve<float2>(b, Q, N, L32, piv, dinv, lane);
+  double2* ph64 = J.phi + s.vec_off;
   if (pass == 0) {
-    for (int e = lane; e < Q * N; e += 32) ph[e] = make_float4(b[e].x, 0.f, b[e].y, 0.f);
+    if (f64) {
+      for (int e = lane; e < Q * N; e += 32) ph64[e] = make_double2(b[e].x, b[e].y);
+    } else {
+      for (int e = lane; e < Q * N; e += 32) ph[e] = make_float4(b[e].x, 0.f, b[e].y, 0.f);
+    }
     if (lane == 0) J.mdone[sidx] = 0;
     return;
   }
   float dmax = 0.f, pmax = 0.f;
   for (int e = lane; e < Q * N; e += 32) {
     const float2 d = b[e];
-    float4 p = ph[e];
-    float sh, sl;
-    two_sum(p.x, d.x, sh, sl);
-    quick_two_sum(sh, sl + p.y, p.x, p.y);
-    two_sum(p.z, d.y, sh, sl);
-    quick_two_sum(sh, sl + p.w, p.z, p.w);
-    ph[e] = p;
+    if (f64) {
+      double2 p = ph64[e];
+      p.x += (double)d.x;
+      p.y += (double)d.y;
+      ph64[e] = p;
+      pmax = fmaxf(pmax, fmaxf(fabsf((float)p.x), fabsf((float)p.y)));
+    } else {
+      float4 p = ph[e];
+      float sh, sl;
+      two_sum(p.x, d.x, sh, sl);
+      quick_two_sum(sh, sl + p.y, p.x, p.y);
+      two_sum(p.z, d.y, sh, sl);
+      quick_two_sum(sh, sl + p.w, p.z, p.w);
+      ph[e] = p;
+      pmax = fmaxf(pmax, fmaxf(fabsf(p.x), fabsf(p.z)));
+    }
     dmax = fmaxf(dmax, fmaxf(fabsf(d.x), fabsf(d.y)));
-    pmax = fmaxf(pmax, fmaxf(fabsf(p.x), fabsf(p.z)));
   }
   for (int o = 16; o > 0; o >>= 1) {
     dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
     pmax = fmaxf(pmax, __shfl_xor_sync(0xffffffffu, pmax, o));
   }
   const double rel = pmax > 0.f ? (double)dmax / (double)pmax : 0.0;
-  const double rho = pass == 1 ? kFirstRhoSafety * rel : rel / fmax((double)J.mrel[sidx], 1e-300);
+  // contraction factor: after the first correction, twice the largest one measured for this system in an
+  // earlier step, else kFirstRhoSafety x rel; later, the ratio of the last two corrections (remembered)
+  double rho;
+  if (pass == 1) {
+    const float known = J.mrho[sidx];
+    rho = known > 0.f ? 2.0 * (double)known : kFirstRhoSafety * rel;
+  } else {
+    rho = rel / fmax((double)J.mrel[sidx], 1e-300);
+    if (lane == 0) J.mrho[sidx] = fmaxf(J.mrho[sidx], fminf((float)rho, 1.0f));
+  }
   const double left = rel * rho;
   if (left >= J.refine_tol && pass < J.refine_max) {
     if (lane == 0) J.mrel[sidx] = (float)rel;
@@ -1466,16 +1502,22 @@ __global__ void __launch_bounds__(32 * kSolveWarps, 4) k_msolve(DevJob J, int m,
     if (!(left < J.refine_tol)) atomicAdd(reinterpret_cast<unsigned long long*>(J.refine_resid) + 2, 1ULL);
     atomicMax(reinterpret_cast<int*>(J.sys_err) + sidx, __float_as_int(fminf((float)left, 3.0e38f)));
   }
-  // Each lane reads back the double-float values it wrote itself, then replaces them by FP64.
+  // Each lane reads back the values it wrote itself; the double-float pairs are replaced by FP64.
   double2* out = J.phi + s.vec_off;
   double2* sum = J.phi_sum + s.vec_off;
   double2* all = J.phi_all ? J.phi_all + (long long)(m - 1) * J.vec_total + s.vec_off : nullptr;
   float4* pdf = J.phi_df + s.vec_off;
   for (int e = lane; e < Q * N; e += 32) {
-    const float4 p = ph[e];
-    const double2 v = df_join2(p);
-    pdf[e] = p;
-    out[e] = v;
+    double2 v;
+    if (f64) {
+      v = out[e];
+      pdf[e] = df_split2(v);
+    } else {
+      const float4 p = ph[e];
+      v = df_join2(p);
+      pdf[e] = p;
+      out[e] = v;
+    }
     sum[e] = m == 1 ? v : cadd(sum[e], v);
     if (all) all[e] = v;
   }
@@ -2119,14 +2161,17 @@ cudaError_t launch_solve(const DevJob& J, int m, cudaStream_t st, int* launches)
     const int passes = std::min(std::max(J.refine_max, 1), kRefineCap);
     k_msolve<<<grid, 32 * nw, sh, st>>>(J, m, 0);
     for (int pass = 1; pass <= passes && rgrid > 0; ++pass) {
-      if (J.fp64keep) {
+      // FP64 residuals for the systems that keep FP64 (all in the FP64-kept form), double-float for the rest
+      const bool any64 = J.fp64keep || J.max_n >= J.f64_min_n, anydf = !J.fp64keep;
+      if (any64) {
         switch (J.Q) {
           case 1: k_mresid64<1><<<rgrid, kResidThreads, 0, st>>>(J); break;
           case 2: k_mresid64<2><<<rgrid, kResidThreads, 0, st>>>(J); break;
           case 3: k_mresid64<3><<<rgrid, kResidThreads, 0, st>>>(J); break;
           default: k_mresid64<4><<<rgrid, kResidThreads, 0, st>>>(J); break;
         }
-      } else {
+      }
+      if (anydf) {
         switch (J.Q) {
           case 1: k_mresid<1><<<rgrid, kResidThreads, 0, st>>>(J); break;
           case 2: k_mresid<2><<<rgrid, kResidThreads, 0, st>>>(J); break;
@@ -2134,6 +2179,7 @@ cudaError_t launch_solve(const DevJob& J, int m, cudaStream_t st, int* launches)
           default: k_mresid<4><<<rgrid, kResidThreads, 0, st>>>(J); break;
         }
       }
+      *launches += (int)any64 + (int)anydf - 1;
       k_msolve<<<grid, 32 * nw, sh, st>>>(J, m, pass);
     }
     *launches += 1 + 2 * passes;
@@ -2198,7 +2244,7 @@ static cudaError_t launch_cross_otf_q(const DevJob& J, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   if (J.n_otf > 0) {
     if (J.mixed) {
-      const size_t sh = (size_t)kOtfBandDf * (kAsmRows + Q) * kOtfDfSrc * sizeof(float4);
+      const size_t sh = (size_t)kOtfDfPitch * (kAsmRows + Q) * kOtfDfSrc * sizeof(float4);
       e = cudaFuncSetAttribute(k_cross_otf_df<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
       if (e != cudaSuccess) return e;
       k_cross_otf_df<Q><<<J.n_otf, kOtfDfThreads, sh, st>>>(J);

@@ -82,6 +82,8 @@ struct DevJob {
   float2* rres;              // FP32-rounded refinement residuals, laid out like G (mixed form)
   int* mdone;                // per system: 1 once its refinement has finished this step (mixed form)
   float* mrel;               // per system: relative size of its last correction (mixed form)
+  float* mrho;               // per system: largest contraction factor measured in earlier steps (0: none yet)
+  int f64_min_n;             // mixed forms: systems of at least this N keep FP64 matrices and residuals
   const ResidChunk* rchunks; // 32-row chunks of the systems, largest first (mixed form)
   int n_rchunks;
   int* piv;

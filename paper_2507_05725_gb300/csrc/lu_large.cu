@@ -36,7 +36,7 @@ constexpr int kInnerPS = kInner + 1;
 constexpr int kPanelThreads = 256;
 constexpr int kTile = 128;          // complex rows and columns of an update tile
 constexpr int kPartBytes = kTile * kOuter * 4;   // 128 x 32 TF32 = 16 KB per operand part
-constexpr int kUpdThreads = 128;
+constexpr int kUpdThreads = 256;
 constexpr long long kMaxPolls = 1ll << 18;      // bounded wait for the tensor core (well under a second)
 constexpr uint32_t kTmemCols = 512;             // the whole tensor memory of the SM (one CTA per SM)
 constexpr int kLuThreadsFinish = 256;
@@ -77,8 +77,9 @@ __global__ void __launch_bounds__(kPanelThreads) k_lu_big_panel(DevJob J, int k0
       const int c = idx / nr, r = idx % nr;
       A[(long long)(k1 + c) * N + k1 + r] = Pn[r * kInnerPS + c];
     }
-    // Row interchanges on every other column (factored columns to the left, the rest to the right).
-    for (int col = tid; col < N; col += kPanelThreads) {
+    // Row interchanges on the outer panel's other columns (the columns outside it get the panel's
+    // interchanges all at once below).
+    for (int col = k0 + tid; col < kend; col += kPanelThreads) {
       if (col >= k1 && col < k1 + w) continue;
       float2* Ac = A + (long long)col * N + k1;
       for (int c = 0; c < w; ++c) {
@@ -122,24 +123,52 @@ __global__ void __launch_bounds__(kPanelThreads) k_lu_big_panel(DevJob J, int k0
     }
     __syncthreads();
   }
-  // U12 of the outer panel: rows k0 .. kend-1 of the columns right of it, X = L11^{-1} A12.
+  // The panel's interchanges on every column outside it, in order (rows k and piv[k], k = k0 .. kend-1): a
+  // column's rows k0 .. kend-1 in registers, pivot rows below them in HBM; right of the panel, fused with
+  // U12 = L11^{-1} A12 on those rows.
+  __shared__ int pv[kOuter];
   for (int e = tid; e < nbo * nbo; e += kPanelThreads) {
     const int c = e / nbo, r = e % nbo;
     L11[r][c] = A[(long long)(k0 + c) * N + k0 + r];
   }
+  if (tid < nbo) pv[tid] = piv[k0 + tid] - k0;
   __syncthreads();
-  for (int col = kend + tid; col < N; col += kPanelThreads) {
-    float2* Ac = A + (long long)col * N + k0;
+  for (int col = tid; col < N - nbo; col += kPanelThreads) {
+    const int cc = col < k0 ? col : col + nbo;        // skip the panel's own columns
+    float2* Ac = A + (long long)cc * N + k0;
     float2 x[kOuter];
 #pragma unroll
-    for (int r = 0; r < kOuter; ++r) {
-      if (r < nbo) {
-        float2 v = Ac[r];
-        for (int c = 0; c < r; ++c) v = cfms(L11[r][c], x[c], v);
-        x[r] = v;
-        Ac[r] = v;
+    for (int r = 0; r < kOuter; ++r)
+      if (r < nbo) x[r] = Ac[r];
+#pragma unroll
+    for (int c = 0; c < kOuter; ++c) {
+      if (c < nbo) {
+        const int p = pv[c];
+        if (p != c) {
+          if (p < nbo) {
+#pragma unroll
+            for (int q = 0; q < kOuter; ++q)        // x[c] <-> x[p] with register indices only
+              if (q == p) { const float2 t = x[q]; x[q] = x[c]; x[c] = t; }
+          } else {
+            const float2 t = Ac[p];
+            Ac[p] = x[c];
+            x[c] = t;
+          }
+        }
       }
     }
+    if (cc >= kend) {
+#pragma unroll
+      for (int r = 0; r < kOuter; ++r)
+        if (r < nbo) {
+#pragma unroll
+          for (int c = 0; c < kOuter; ++c)
+            if (c < r) x[r] = cfms(L11[r][c], x[c], x[r]);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < kOuter; ++r)
+      if (r < nbo) Ac[r] = x[r];
   }
 }
 
@@ -168,34 +197,46 @@ __global__ void __launch_bounds__(kUpdThreads, 1) k_lu_big_update(DevJob J, int 
   unsigned char* part = sm;
   if (wid == 0) tc::tmem_alloc(&tmem_base, kTmemCols);
   if (tid == 0) tc::mbar_init(&bar, 1);
-  // L21 tile: rows R0 .. R0+127 of columns k0 .. k0+31 (thread = row; zero beyond N).
+  // L21 tile: rows R0 .. R0+127 of columns k0 .. k0+31 (thread = row and half of K; zero beyond N), the 16
+  // loads of a thread issued before their splits.
   {
-    const int r = tid, row = R0 + r;
-    for (int k = 0; k < kOuter; ++k) {
-      float2 v = row < N ? A[(long long)(k0 + k) * N + row] : make_float2(0.f, 0.f);
+    const int r = tid & (kTile - 1), kh = (tid >> 7) * (kOuter / 2), row = R0 + r;
+    float2 v[kOuter / 2];
+#pragma unroll
+    for (int k = 0; k < kOuter / 2; ++k)
+      v[k] = row < N ? A[(long long)(k0 + kh + k) * N + row] : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < kOuter / 2; ++k) {
       float h, l;
-      const int o = part_off(r, k);
-      split_tf32(v.x, h, l);
+      const int o = part_off(r, kh + k);
+      split_tf32(v[k].x, h, l);
       *reinterpret_cast<float*>(part + 0 * kPartBytes + o) = h;
       *reinterpret_cast<float*>(part + 1 * kPartBytes + o) = l;
-      split_tf32(v.y, h, l);
+      split_tf32(v[k].y, h, l);
       *reinterpret_cast<float*>(part + 2 * kPartBytes + o) = h;
       *reinterpret_cast<float*>(part + 3 * kPartBytes + o) = l;
     }
   }
   // U12 tile: rows k0 .. k0+31 of columns C0 .. C0+127 as a 128 (column) x 32 (k) K-major operand
-  // (warp = column, lane = k: each column's 32 values are contiguous in HBM).
-  for (int n = wid; n < kTile; n += kUpdThreads / 32) {
-    const int col = C0 + n, k = lane;
-    float2 v = col < N ? A[(long long)col * N + k0 + k] : make_float2(0.f, 0.f);
-    float h, l;
-    const int o = part_off(n, k);
-    split_tf32(v.x, h, l);
-    *reinterpret_cast<float*>(part + 4 * kPartBytes + o) = h;
-    *reinterpret_cast<float*>(part + 5 * kPartBytes + o) = l;
-    split_tf32(v.y, h, l);
-    *reinterpret_cast<float*>(part + 6 * kPartBytes + o) = h;
-    *reinterpret_cast<float*>(part + 7 * kPartBytes + o) = l;
+  // (warp = column, lane = k: each column's 32 values are contiguous in HBM), 4 columns in flight per warp.
+  for (int n0 = wid; n0 < kTile; n0 += 4 * (kUpdThreads / 32)) {
+    float2 v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int col = C0 + n0 + u * (kUpdThreads / 32);
+      v[u] = col < N ? A[(long long)col * N + k0 + lane] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      float h, l;
+      const int o = part_off(n0 + u * (kUpdThreads / 32), lane);
+      split_tf32(v[u].x, h, l);
+      *reinterpret_cast<float*>(part + 4 * kPartBytes + o) = h;
+      *reinterpret_cast<float*>(part + 5 * kPartBytes + o) = l;
+      split_tf32(v[u].y, h, l);
+      *reinterpret_cast<float*>(part + 6 * kPartBytes + o) = h;
+      *reinterpret_cast<float*>(part + 7 * kPartBytes + o) = l;
+    }
   }
   tc::fence_proxy_async();
   tc::fence_before_sync();
@@ -226,21 +267,24 @@ __global__ void __launch_bounds__(kUpdThreads, 1) k_lu_big_update(DevJob J, int 
   const bool ok = tc::mbar_wait(&bar, 0, kMaxPolls);
   tc::fence_after_sync();
   if (ok) {
-    const int row = R0 + 32 * wid + lane;
-    const uint32_t lane_addr = tmem + ((uint32_t)(32 * wid) << 16);
-    for (int c = 0; c < kTile; c += 16) {
+    // warp w reads TMEM lanes 32 (w % 4) .. + 31 (its lane quarter); warps 0-3 take columns 0-63, 4-7 64-127
+    const int quarter = wid & 3, row = R0 + 32 * quarter + lane;
+    const uint32_t lane_addr = tmem + ((uint32_t)(32 * quarter) << 16);
+    for (int c = (wid >> 2) * (kTile / 2); c < (wid >> 2) * (kTile / 2) + kTile / 2; c += 16) {
       float re[16], im[16];
       tc::tmem_ld16(lane_addr + c, re);
       tc::tmem_ld16(lane_addr + kTile + c, im);
       if (row < N) {
+        float2 v[16];
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           const int col = C0 + c + j;
-          if (col < N) {
-            float2* p = A + (long long)col * N + row;
-            const float2 v = *p;
-            *p = make_float2(v.x - re[j], v.y - im[j]);
-          }
+          v[j] = col < N ? A[(long long)col * N + row] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int col = C0 + c + j;
+          if (col < N) A[(long long)col * N + row] = make_float2(v[j].x - re[j], v[j].y - im[j]);
         }
       }
     }

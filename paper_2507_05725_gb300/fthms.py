@@ -56,7 +56,8 @@ class fthms_stats_t(C.Structure):
                 ("cross_entries", C.c_double), ("hankel_evals", C.c_double), ("h2d_bytes", C.c_size_t),
                 ("lu_flops", C.c_double), ("solve_flops", C.c_double), ("apply_flops", C.c_double),
                 ("precision", C.c_int), ("max_refine_resid", C.c_double),
-                ("refine_passes", C.c_double), ("n_unconverged", C.c_longlong), ("fallback_runs", C.c_int)]
+                ("refine_passes", C.c_double), ("n_unconverged", C.c_longlong), ("fallback_runs", C.c_int),
+                ("lu_tensor_systems", C.c_int)]
 
 
 # void (*)(double* buf_dev, size_t count, void* cuda_stream, void* user)

@@ -66,3 +66,37 @@ def test_fp64_form_refuses_the_largest_systems(F, ctx):
     with pytest.raises(F.FthmsError) as e:
         F.Job(ctx, _problem(1024), precision=0)
     assert e.value.status == F.FTHMS_EINVAL and "2048" in str(e.value)
+
+
+@pytest.mark.parametrize("N,L", [(512, 1024), (1024, 1024), (2048, 65)])
+def test_config4_sampled_systems(F, ctx, N, L):
+    """The mixed-precision configuration (6 arcs of 5 ellipses, N nodes on every arc) in the FP64-kept form, in
+    the bench's launch configuration: m = 1 densities of sampled (arc, omega) systems -- both band edges and
+    the pulse's band around omega = 200 -- against oracle solves computed system by system.  N = 512 and 1024
+    run the full 1023-frequency job; N = 2048 (623 GB in full) keeps 64 frequencies of the same grid spacing
+    (W = 400 * 64 / 1023, the same time window)."""
+    from oracle import kernels as oker
+    from oracle.fthms import Setup
+    from oracle.transforms import incident_field
+    W = 400.0 if L == 1024 else 400.0 * (L - 1) / 1023
+    problem = wl.config4(N, L=L, W=W, M=2)
+    job = F.Job(ctx, problem, precision=2).run()
+    st = job.stats()
+    assert st["n_unconverged"] == 0 and st["lu_tensor_systems"] == (len(problem["arcs"]) * (L - 1) if N > 800 else 0)
+    S = Setup(problem)
+    tg = S.grid
+    sig = problem["signal"]
+    num = den = 0.0
+    for j in (0, 2, 5):
+        g = sig["sign"] * S.chi[j][:, None] * incident_field(sig, S.X[j], tg.t)
+        Gt = tg.forward(g)                                  # [Nmax, Q, L]
+        d0, d1 = job.densities(j, 1, 0), job.densities(j, 1, 1)
+        near_pulse = int(round(200.0 / tg.h)) if W > 200.0 else (L - 1) // 2
+        for l in sorted({1, near_pulse, near_pulse + 3, L - 1}):
+            A = oker.self_matrix(S.arcs[j], N, tg.omega[l])
+            for q, d in ((0, d0), (1, d1)):
+                phi = np.linalg.solve(A, Gt[:, q, l])     # N = N_max: no restriction
+                num += float(np.sum(np.abs(d[l] - phi) ** 2))
+                den += float(np.sum(np.abs(phi) ** 2))
+    job.release()
+    assert math.sqrt(num / den) < MIXED_TOL, math.sqrt(num / den)

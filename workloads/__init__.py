@@ -242,18 +242,19 @@ def random_small(seed, n_arcs_per_curve=3, n_curves=1, L=33, M=2, Q=1, N_fixed=0
     return {"name": f"small-{seed}", "curves": curves, "arcs": arcs, "signal": signal, "options": options}
 
 
-def served_requests(seed, n, wmax=(20.0, 60.0)):
+def served_requests(seed, n, wmax=(20.0, 60.0), Ls=(129, 257), arcs=(2, 6)):
     """Seeded request mix shaped like the served stream of the fifth configuration, scaled to a bounded
-    sample: each request draws a disk (interior, 3-4 arcs), a star cavity (interior, 4-6 arcs) or 1-3
-    separated ellipse obstacles (exterior, 2 arcs each); a band omega_max uniform in `wmax`; 129 or 257
-    frequencies; the config-2 node rule; a Gaussian-modulated sinusoid with carrier in
-    [2, min(40, omega_max - 8/b)] and width b in [1, 3]; 3-6 steps."""
+    sample: each request draws a disk (interior), a star cavity (interior) or 1-5 separated ellipse
+    obstacles (exterior, 2 arcs each) with a number of arcs in the `arcs` range, a band omega_max uniform in
+    `wmax`, a frequency count from `Ls`, the config-2 node rule, a Gaussian-modulated sinusoid with carrier in
+    [2, min(40, omega_max - 8/b)] and width b in [1, 3], and 3-6 steps."""
     rng = np.random.default_rng(seed)
+    lo, hi = arcs
     out = []
     for r in range(n):
         kind = int(rng.integers(0, 3))
         W = float(rng.uniform(*wmax))
-        L = int(rng.choice([129, 257]))
+        L = int(rng.choice(list(Ls)))
         b = float(rng.uniform(1.0, 3.0))
         a = float(rng.uniform(2.0, max(2.5, min(40.0, W - 8.0 / b))))
         M = int(rng.integers(3, 7))
@@ -261,30 +262,32 @@ def served_requests(seed, n, wmax=(20.0, 60.0)):
         H = float(min(12.0, 0.45 * period))
         if kind == 0:
             curves = [circle(float(rng.uniform(0.8, 1.2)))]
-            arcs = split_closed_curve(0, int(rng.integers(3, 5)), 1.25, float(rng.uniform(0, 2 * math.pi)))
+            na = int(rng.integers(max(2, lo), min(6, hi) + 1))
+            arcs_ = split_closed_curve(0, na, 1.25, float(rng.uniform(0, 2 * math.pi)))
             signal = _signal(0, +1.0, 1.0, a, 3.0 * b, b, z0=(2.5, float(rng.uniform(-1, 1))))
             obs = [(0.2, 0.1), (-0.3, 0.2)]
             interior = 1
         elif kind == 1:
             curves = [star(0.3, 5, float(rng.uniform(0, 2 * math.pi)))]
-            arcs = split_closed_curve(0, int(rng.integers(4, 7)), 1.25, float(rng.uniform(0, 2 * math.pi)))
+            na = int(rng.integers(max(4, lo), max(4, min(12, hi)) + 1))
+            arcs_ = split_closed_curve(0, na, 1.25, float(rng.uniform(0, 2 * math.pi)))
             signal = _signal(0, +1.0, 1.0, a, 3.0 * b, b, z0=(2.6, 0.3))
             obs = [(0.1, 0.0), (0.0, 0.3)]
             interior = 1
         else:
-            k = int(rng.integers(1, 4))
+            k = int(rng.integers(max(1, lo // 2), max(1, min(5, hi // 2)) + 1))
             curves = [ellipse(float(rng.uniform(0.5, 1.0)), float(rng.uniform(0.3, 0.6)), 3.0 * i, 0.0)
                       for i in range(k)]
-            arcs = []
+            arcs_ = []
             for ci in range(k):
-                arcs += split_closed_curve(ci, 2, 1.25, 0.0)
+                arcs_ += split_closed_curve(ci, 2, 1.25, 0.0)
             ang = float(rng.uniform(0, 2 * math.pi))
             signal = _signal(1, -1.0, 1.0, a, 3.0 * b + 4.0, b, direction=(math.cos(ang), math.sin(ang)))
             obs = [(1.5 * k, 3.0), (-3.0, -1.0)]
             interior = 0
         options = _options(W, L, M, 1, H, 1024, obs, 0.0, 0.1, 61, N_min=24, N_off=16, N_ppw=2.0 / math.pi,
                            interior=interior)
-        out.append({"name": f"served-{seed}-{r}", "curves": curves, "arcs": arcs, "signal": signal,
+        out.append({"name": f"served-{seed}-{r}", "curves": curves, "arcs": arcs_, "signal": signal,
                     "options": options})
     return out
 
