@@ -169,6 +169,7 @@ void free_req(fthms_req* r) {
 void set_lu_split(fthms_req* r, int n_big) {
   DevJob& J = r->J;
   const Plan& p = r->plan;
+  n_big = std::max(0, std::min(n_big, (int)p.sys_order.size()));
   J.lu_big = J.sys_order;
   J.n_lu_big = n_big;
   J.lu_small = J.sys_order ? J.sys_order + n_big : nullptr;
@@ -925,17 +926,19 @@ fthms_status fthms_autotune(fthms_req* req, int reps, int* shapes) {
   // Mixed forms: the smallest N factored with tensor-core updates (candidates above 800 keep the default,
   // the one-CTA LU cannot hold more); every candidate factors the same matrices, its time is compared.
   int lu_min = kLuBigMin;
+  // the number of systems (a prefix of sys_order, decreasing N) with at least nmin nodes; lives as long as
+  // the knobs that call it
+  const Plan& plan = req->plan;
+  auto split_for = [&plan](int nmin) {
+    int nb = 0;
+    while (nb < (int)plan.sys_order.size() && plan.sys[plan.sys_order[nb]].N >= nmin) ++nb;
+    return nb;
+  };
   if (J.mixed) {
     std::vector<int> cand{kLuBigMin};
     for (int c : {512, 384, 256})
-      if (!req->plan.sys_order.empty() && req->plan.sys[req->plan.sys_order[0]].N >= c) cand.push_back(c);
+      if (!plan.sys_order.empty() && plan.sys[plan.sys_order[0]].N >= c) cand.push_back(c);
     if (cand.size() > 1) {
-      auto split_for = [&](int nmin) {
-        int nb = 0;
-        const Plan& p = req->plan;
-        while (nb < (int)p.sys_order.size() && p.sys[p.sys_order[nb]].N >= nmin) ++nb;
-        return nb;
-      };
       knobs.push_back({&lu_min, cand, [&] {
                          set_lu_split(req, split_for(lu_min));
                          // the LU works in place: re-assemble the matrices before every factorisation
@@ -958,14 +961,8 @@ fthms_status fthms_autotune(fthms_req* req, int reps, int* shapes) {
     }
     *k.field = pick;
   }
-  {
-    int nb = 0;
-    const Plan& p = req->plan;
-    if (J.mixed)
-      while (nb < (int)p.sys_order.size() && p.sys[p.sys_order[nb]].N >= lu_min) ++nb;
-    set_lu_split(req, nb);
-    req->lu_min = lu_min;
-  }
+  set_lu_split(req, J.mixed ? split_for(lu_min) : 0);
+  req->lu_min = lu_min;
   if (shapes) {
     shapes[0] = J.shape_solve;
     shapes[1] = J.shape_asm;

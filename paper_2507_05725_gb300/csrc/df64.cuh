@@ -203,3 +203,30 @@ __device__ __forceinline__ void cdf_mac(dfacc& re, dfacc& im, float4 a, float4 b
 }
 
 }  // namespace fthms
+
+namespace fthms {
+
+// sqrt(a) for a > 0 in double-float: the FP32 root r corrected once by Newton's step with the exact
+// residual a - r^2 (two-product), error about 2^-46.
+__device__ __forceinline__ df df_sqrt(df a) {
+  const float r = sqrtf(a.hi);
+  const float p = __fmul_rn(r, r);
+  const float pe = fmaf(r, r, -p);                    // r^2 = p + pe exactly
+  const float d = __fadd_rn(__fadd_rn(__fsub_rn(a.hi, p), a.lo), -pe);
+  df out;
+  quick_two_sum(r, __fdiv_rn(d, __fmul_rn(2.f, r)), out.hi, out.lo);
+  return out;
+}
+
+// 1 / sqrt(a) for a > 0 in double-float: y = rsqrt(a.hi) refined by one Newton step y (3 - a y^2) / 2
+// with the product in double-float, error about 2^-46.
+__device__ __forceinline__ df df_rsqrt(df a) {
+  const float y = rsqrtf(a.hi);
+  const df y2 = df_mul(df{y, 0.f}, df{y, 0.f});
+  const df e = df_sub(df{1.f, 0.f}, df_mul(a, y2));   // 1 - a y^2, small
+  df out;
+  quick_two_sum(y, __fmul_rn(__fmul_rn(0.5f, y), e.hi), out.hi, out.lo);
+  return out;
+}
+
+}  // namespace fthms

@@ -1052,27 +1052,71 @@ constexpr int kOtfDfSrc = 16;
 constexpr int kOtfDfThreads = kAsmRows * kOtfDfSrc;   // 128
 constexpr int kOtfDfPitch = kOtfBandDf + 1;           // float4 per shared-memory row (33: no bank conflicts)
 
+// sin and cos of theta >= 0 (FP64, up to ~2e4) as double-float: theta reduced by n pi/2 in FP64 (pi/2 as the
+// sum of two doubles), the remainder's double-float Taylor series, the quadrant n mod 4.
+__device__ __forceinline__ void df_sincos_reduced(double theta, df& s, df& c) {
+  constexpr double kPio2Hi = 1.57079632679489661923, kPio2Lo = 6.123233995736766e-17;
+  const double n = rint(theta * kTwoOverPi);
+  const double r = fma(-n, kPio2Lo, fma(-n, kPio2Hi, theta));
+  df sr, cr;
+  df_sincos_taylor(df_from(r), sr, cr);
+  switch (((long long)n) & 3) {
+    case 0: s = sr; c = cr; break;
+    case 1: s = cr; c = df_neg(sr); break;
+    case 2: s = df_neg(sr); c = df_neg(cr); break;
+    default: s = df_neg(cr); c = sr; break;
+  }
+}
+
+// The per-pair quantities of pair_setup on the FP32 pipe (mixed forms, cross rows every step): the distance
+// R from the FP64 coordinate differences by a double-float square root, 1/(hR) and the amplitude
+// sqrt(2/(pi hR)) w/4 in double-float; FP64 only for the differences, the logarithms of the near rule and
+// of the Taylor range (present in the low-frequency bands only) and R itself for the phase reductions.
+struct PairDf {
+  df R, invu, A0, beta, ampw;
+  double R64;
+  float hR;
+  int lsw;
+};
+
+__device__ __forceinline__ PairDf pair_setup_df(const DevJob& J, const CrossTgt& t, double xi, double yi, double ti,
+                                                double wn, int l0, double w, double invw, df h_d, df camp_d) {
+  PairDf p;
+  const double dx = t.x - xi, dy = t.y - yi;
+  p.R = df_sqrt(df_from(fma(dx, dx, dy * dy)));
+  p.R64 = (double)p.R.hi + (double)p.R.lo;
+  const df hR = df_mul(h_d, p.R);
+  p.hR = hR.hi;
+  p.invu = df_div(df{1.f, 0.f}, hR);
+  p.lsw = max(l0, (int)ceilf(fminf((float)kBesselLarge * p.invu.hi, 1.0e9f)));
+  double lt = 0.0, beta = 0.0, A0 = 0.0;
+  if (t.near) {
+    lt = log(fabs(t.tstar - ti));
+    beta = -kTwoOverPi * fma(wn, invw, -lt);
+  } else {
+    wn = 0.0;
+  }
+  if (p.lsw > l0) A0 = -0.5 * kInvPi * fma(w, log(0.5 * J.h * p.R64) + kEulerGamma - lt, wn);
+  p.A0 = df_from(A0);
+  p.beta = df_from(beta);
+  p.ampw = df_mul(df_rsqrt(hR), camp_d);
+  return p;
+}
+
 // Double-float state of Hankel's expansion along a band (the mixed stored-row assembly's recurrence).
 struct AsymDf {
   df cx, sx, cu, su, ampw, invu, beta;
   int since, kmax;
 };
 
-__device__ __forceinline__ AsymDf asym_df_start(const PairSetup& ps, double lh_first, double camp) {
-  const AsymState as = asym_start(ps, lh_first, camp, false);
+__device__ __forceinline__ AsymDf asym_df_start(const PairDf& p, double lh_first, double h) {
   AsymDf a;
-  a.ampw = df_from(as.ampw);
-  a.invu = df_from(ps.inv_u);
-  a.beta = df_from(ps.beta);
-  a.kmax = as.kmax;
-  if (ps.hR <= 1.0) {
-    df_sincos_taylor(df_from(ps.hR), a.su, a.cu);
-  } else {
-    double su, cu;
-    sincos(ps.hR, &su, &cu);
-    a.su = df_from(su);
-    a.cu = df_from(cu);
-  }
+  a.ampw = p.ampw;
+  a.invu = p.invu;
+  a.beta = p.beta;
+  a.kmax = hankel_terms((float)(lh_first * p.R64));
+  if (p.hR <= 1.0f) df_sincos_taylor(df_from(h * p.R64), a.su, a.cu);
+  else df_sincos_reduced(h * p.R64, a.su, a.cu);
   a.cx = a.sx = df{0.f, 0.f};
   a.since = 16;
   return a;
@@ -1135,7 +1179,7 @@ __global__ void __launch_bounds__(kOtfDfThreads) k_cross_otf_df(DevJob J) {
   const double A1 = -0.5 * kInvPi * w;
   const double camp = kSqrtTwoOverPi * qw;
   const double inv_h = 1.0 / J.h;
-  const df A1_d = df_from(A1), qw_d = df_from(qw);
+  const df A1_d = df_from(A1), qw_d = df_from(qw), h_d = df_from(J.h), camp_d = df_from(camp);
   // phase-2 accumulators: thread owns (row, band) pairs p = tid, tid + kOtfDfThreads (row = p / B)
   constexpr int kPairs = kAsmRows * B / kOtfDfThreads;
   dfacc acc_re[kPairs][Q], acc_im[kPairs][Q];
@@ -1145,30 +1189,34 @@ __global__ void __launch_bounds__(kOtfDfThreads) k_cross_otf_df(DevJob J) {
     float4* Ep = Et + (r1 * kOtfDfSrc + i1) * kOtfDfPitch;          // + b
     if (r1 < task.nrows && i < N) {
       const CrossTgt t = tg[r1];
-      const PairSetup ps = pair_setup(J, t, J.node_x[pn.off + i], J.node_y[pn.off + i], J.node_t[pn.off + i],
-                                      t.near ? Wn[r1 * N + i] : 0.0, ot.l0, w, invw, inv_h);
-      const int lend = min(ps.lsw, ot.l1 + 1);
-      const df R_d = df_from(ps.R), A0_d = df_from(ps.A0);
-      for (int l = ot.l0; l < lend; ++l) {                          // z < 20: Taylor form
-        const int b = l - ot.l0;
-        float4 e;
-        if (J.fp64keep) {
-          e = df_split2(taylor_entry(ps, tb[3][b], tb[2][b], A1, qw));
-        } else {
-          df J0, Yh;
-          bessel0_taylor_df(df_mul(tbd[3][b], R_d), J0, Yh);
-          const df alpha = df_add_fast(df_mul(A1_d, tbd[2][b]), A0_d);
-          const df re = df_dot2(alpha, J0, df_neg(qw_d), Yh);
-          const df im = df_mul(qw_d, J0);
-          e = make_float4(re.hi, re.lo, im.hi, im.lo);
+      const double xi = J.node_x[pn.off + i], yi = J.node_y[pn.off + i], ti = J.node_t[pn.off + i];
+      const double wni = t.near ? Wn[r1 * N + i] : 0.0;
+      const PairDf pd = pair_setup_df(J, t, xi, yi, ti, wni, ot.l0, w, invw, h_d, camp_d);
+      const int lend = min(pd.lsw, ot.l1 + 1);
+      if (lend > ot.l0) {                                           // z < 20: Taylor form
+        PairSetup ps{};
+        if (J.fp64keep) ps = pair_setup(J, t, xi, yi, ti, wni, ot.l0, w, invw, inv_h);
+        for (int l = ot.l0; l < lend; ++l) {
+          const int b = l - ot.l0;
+          float4 e;
+          if (J.fp64keep) {
+            e = df_split2(taylor_entry(ps, tb[3][b], tb[2][b], A1, qw));
+          } else {
+            df J0, Yh;
+            bessel0_taylor_df(df_mul(tbd[3][b], pd.R), J0, Yh);
+            const df alpha = df_add_fast(df_mul(A1_d, tbd[2][b]), pd.A0);
+            const df re = df_dot2(alpha, J0, df_neg(qw_d), Yh);
+            const df im = df_mul(qw_d, J0);
+            e = make_float4(re.hi, re.lo, im.hi, im.lo);
+          }
+          Ep[b] = e;
         }
-        Ep[b] = e;
       }
       if (lend <= ot.l1) {
-        AsymDf as = asym_df_start(ps, tb[3][lend - ot.l0], camp);
+        AsymDf as = asym_df_start(pd, tb[3][lend - ot.l0], J.h);
         for (int l = lend; l <= ot.l1; ++l) {
           const int b = l - ot.l0;
-          Ep[b] = asym_df_entry(as, tb[3][b] * ps.R, tbd[0][b], tbd[1][b]);
+          Ep[b] = asym_df_entry(as, tb[3][b] * pd.R64, tbd[0][b], tbd[1][b]);
         }
       }
     } else {

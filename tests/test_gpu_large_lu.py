@@ -68,31 +68,39 @@ def test_fp64_form_refuses_the_largest_systems(F, ctx):
     assert e.value.status == F.FTHMS_EINVAL and "2048" in str(e.value)
 
 
-@pytest.mark.parametrize("N,L", [(512, 1024), (1024, 1024), (2048, 65)])
-def test_config4_sampled_systems(F, ctx, N, L):
-    """The mixed-precision configuration (6 arcs of 5 ellipses, N nodes on every arc) in the FP64-kept form, in
-    the bench's launch configuration: m = 1 densities of sampled (arc, omega) systems -- both band edges and
-    the pulse's band around omega = 200 -- against oracle solves computed system by system.  N = 512 and 1024
-    run the full 1023-frequency job; N = 2048 (623 GB in full) keeps 64 frequencies of the same grid spacing
-    (W = 400 * 64 / 1023, the same time window)."""
+@pytest.mark.parametrize("N,part", [(512, None), (1024, None), (2048, (7, 8))])
+def test_config4_sampled_systems(F, ctx, N, part):
+    """The mixed-precision configuration (6 arcs of 5 ellipses, N nodes on every arc, 1023 frequencies on
+    (0, 400]) in the FP64-kept form, in the bench's launch configuration: m = 1 densities of sampled (arc,
+    omega) systems -- the band's edges and the pulse's band around omega = 200 -- against oracle solves
+    computed system by system.  N = 2048 (623 GB in full) runs rank 7 of an 8-way frequency partition (its 128
+    frequencies at the top of the band, 77 GB): the m = 1 densities need no exchange between ranks."""
+    import copy
     from oracle import kernels as oker
     from oracle.fthms import Setup
     from oracle.transforms import incident_field
-    W = 400.0 if L == 1024 else 400.0 * (L - 1) / 1023
-    problem = wl.config4(N, L=L, W=W, M=2)
-    job = F.Job(ctx, problem, precision=2).run()
+    problem = wl.config4(N, M=1 if part else 2)
+    run_problem = copy.deepcopy(problem)
+    if part:
+        run_problem["options"].update(omega_rank=part[0], omega_ranks=part[1])
+    job = F.Job(ctx, run_problem, precision=2)
+    if part:
+        job.set_allreduce(lambda buf, n, stream: None)      # one rank alone: m = 1 is all that is checked
+    job.run()
     st = job.stats()
-    assert st["n_unconverged"] == 0 and st["lu_tensor_systems"] == (len(problem["arcs"]) * (L - 1) if N > 800 else 0)
+    own = list(job.own_frequencies())
+    assert st["n_unconverged"] == 0, st
+    assert st["lu_tensor_systems"] == (len(problem["arcs"]) * len(own) if N > 800 else 0)
     S = Setup(problem)
     tg = S.grid
     sig = problem["signal"]
     num = den = 0.0
+    picks = {own[0], own[-1], own[len(own) // 2]} if part else {1, 512, 515, tg.L - 1}
     for j in (0, 2, 5):
         g = sig["sign"] * S.chi[j][:, None] * incident_field(sig, S.X[j], tg.t)
         Gt = tg.forward(g)                                  # [Nmax, Q, L]
         d0, d1 = job.densities(j, 1, 0), job.densities(j, 1, 1)
-        near_pulse = int(round(200.0 / tg.h)) if W > 200.0 else (L - 1) // 2
-        for l in sorted({1, near_pulse, near_pulse + 3, L - 1}):
+        for l in sorted(picks):
             A = oker.self_matrix(S.arcs[j], N, tg.omega[l])
             for q, d in ((0, d0), (1, d1)):
                 phi = np.linalg.solve(A, Gt[:, q, l])     # N = N_max: no restriction
