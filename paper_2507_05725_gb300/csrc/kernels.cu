@@ -1385,9 +1385,13 @@ __global__ void __launch_bounds__(kResidThreads) k_mresid64(DevJob J) {
   const double2* __restrict__ A64 = J.A + s.mat_off;
   const double2* __restrict__ ph = J.phi + s.vec_off;
   const double2* __restrict__ G = J.G + s.vec_off;
+  const double isc = 1.0 / J.mscale[c.sys];   // a power of two: exact
   double2 acc[Q];
 #pragma unroll
-  for (int q = 0; q < Q; ++q) acc[q] = G[q * N + row];
+  for (int q = 0; q < Q; ++q) {
+    const double2 g = G[q * N + row];
+    acc[q] = make_double2(g.x * isc, g.y * isc);
+  }
   constexpr int kUnroll = Q == 1 ? 8 : Q == 2 ? 4 : 2;
 #pragma unroll kUnroll
   for (int j = 0; j < N; ++j) {
@@ -1416,10 +1420,12 @@ __global__ void __launch_bounds__(kResidThreads) k_mresid(DevJob J) {
   const float4* __restrict__ Adf = reinterpret_cast<const float4*>(J.A) + s.mat_off;
   const float4* __restrict__ ph = reinterpret_cast<const float4*>(J.phi + s.vec_off);
   const double2* __restrict__ G = J.G + s.vec_off;
+  const double isc = 1.0 / J.mscale[c.sys];   // a power of two: exact
   dfacc re[Q], im[Q];
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
-    const float4 gd = df_split2(G[q * N + row]);
+    const double2 g = G[q * N + row];
+    const float4 gd = df_split2(make_double2(g.x * isc, g.y * isc));
     re[q].add(gd.x, gd.y);
     im[q].add(gd.z, gd.w);
   }
@@ -1479,13 +1485,24 @@ __global__ void __launch_bounds__(32 * kSolveWarps, 4) k_msolve(DevJob J, int m,
   const int* __restrict__ piv = J.piv + s.piv_off;
   const float2* __restrict__ dinv = J.dinv32 + s.piv_off;
   float4* ph = reinterpret_cast<float4*>(J.phi + s.vec_off);
+  double scale;
   if (pass == 0) {
+    // the refinement runs in units of scale = 2^k >= max |G| (exact), so that no data underflow FP32
     const double2* __restrict__ G = J.G + s.vec_off;
+    double gmax = 0.0;
+    for (int e = lane; e < Q * N; e += 32) gmax = fmax(gmax, fmax(fabs(G[e].x), fabs(G[e].y)));
+    for (int o = 16; o > 0; o >>= 1) gmax = fmax(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
+    int ex = 0;
+    frexp(gmax, &ex);
+    scale = gmax > 0.0 ? ldexp(1.0, ex) : 1.0;
+    if (lane == 0) J.mscale[sidx] = scale;
+    const double isc = 1.0 / scale;
     for (int e = lane; e < Q * N; e += 32) {
       const double2 g = G[e];
-      b[e] = make_float2(__double2float_rn(g.x), __double2float_rn(g.y));
+      b[e] = make_float2(__double2float_rn(g.x * isc), __double2float_rn(g.y * isc));
     }
   } else {
+    scale = J.mscale[sidx];
     const float2* __restrict__ r = J.rres + s.vec_off;
     for (int e = lane; e < Q * N; e += 32) b[e] = r[e];
   }
@@ -1550,22 +1567,16 @@ __global__ void __launch_bounds__(32 * kSolveWarps, 4) k_msolve(DevJob J, int m,
     if (!(left < J.refine_tol)) atomicAdd(reinterpret_cast<unsigned long long*>(J.refine_resid) + 2, 1ULL);
     atomicMax(reinterpret_cast<int*>(J.sys_err) + sidx, __float_as_int(fminf((float)left, 3.0e38f)));
   }
-  // Each lane reads back the values it wrote itself; the double-float pairs are replaced by FP64.
+  // Each lane reads back the values it wrote itself (in units of scale) and replaces them by FP64.
   double2* out = J.phi + s.vec_off;
   double2* sum = J.phi_sum + s.vec_off;
   double2* all = J.phi_all ? J.phi_all + (long long)(m - 1) * J.vec_total + s.vec_off : nullptr;
   float4* pdf = J.phi_df + s.vec_off;
   for (int e = lane; e < Q * N; e += 32) {
-    double2 v;
-    if (f64) {
-      v = out[e];
-      pdf[e] = df_split2(v);
-    } else {
-      const float4 p = ph[e];
-      v = df_join2(p);
-      pdf[e] = p;
-      out[e] = v;
-    }
+    double2 v = f64 ? out[e] : df_join2(ph[e]);
+    v = make_double2(v.x * scale, v.y * scale);
+    pdf[e] = df_split2(v);
+    out[e] = v;
     sum[e] = m == 1 ? v : cadd(sum[e], v);
     if (all) all[e] = v;
   }

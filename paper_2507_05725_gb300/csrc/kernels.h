@@ -83,6 +83,7 @@ struct DevJob {
   int* mdone;                // per system: 1 once its refinement has finished this step (mixed form)
   float* mrel;               // per system: relative size of its last correction (mixed form)
   float* mrho;               // per system: largest contraction factor measured in earlier steps (0: none yet)
+  double* mscale;            // per system and step: power of two near max |G|; refinement runs in G / mscale
   int f64_min_n;             // mixed forms: systems of at least this N keep FP64 matrices and residuals
   const ResidChunk* rchunks; // 32-row chunks of the systems, largest first (mixed form)
   int n_rchunks;

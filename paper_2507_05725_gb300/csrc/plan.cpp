@@ -669,7 +669,7 @@ size_t plan_device_bytes(const Plan& p) {
   size_t b = 0;
   b += (size_t)p.mat_total * 16;                 // A / LU
   if (p.opt.precision >= 1)                      // FP32 factors, FP32 residuals, refinement state
-    b += (size_t)p.mat_total * 8 + (size_t)p.piv_total * 8 + (size_t)p.vec_total * (8 + 16) + p.sys.size() * 16 +
+    b += (size_t)p.mat_total * 8 + (size_t)p.piv_total * 8 + (size_t)p.vec_total * (8 + 16) + p.sys.size() * 24 +
          p.rchunks.size() * sizeof(ResidChunk);
   b += p.sig_f.size() * 8;                       // samples of a sampled signal
   b += (size_t)p.piv_total * 4;                  // pivots
