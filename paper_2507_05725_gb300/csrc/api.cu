@@ -429,6 +429,12 @@ fthms_status enqueue_stages(fthms_req* r, bool bracket) {
   r->conv_checked = false;
   TRY(flush_marks(r));
   if (bracket) CK(cudaEventRecord(r->ev0, st));
+  // Per-run flags and refinement state, cleared before the first kernel: the tensor-core LU reads
+  // dev_err (job memory may come back from the pool holding an earlier job's values).
+  CK(cudaMemsetAsync(J.dev_err, 0, sizeof(int), st));
+  CK(cudaMemsetAsync(J.refine_resid, 0, 3 * sizeof(double), st));
+  if (J.sys_err) CK(cudaMemsetAsync(J.sys_err, 0, r->plan.sys.size() * sizeof(float), st));
+  if (J.mrho) CK(cudaMemsetAsync(J.mrho, 0, r->plan.sys.size() * sizeof(float), st));   // measured per run
   TRY(stage(r, FTHMS_STAGE_TABLES, st, &nl, [&] { return launch_tables(J, st, &nl); }));
   TRY(stage(r, FTHMS_STAGE_ASSEMBLE, st, &nl, [&] { return launch_assemble_self(J, st, &nl); }));
   TRY(stage(r, FTHMS_STAGE_LU, st, &nl, [&] { return launch_lu(J, st, &nl); }));
@@ -438,10 +444,6 @@ fthms_status enqueue_stages(fthms_req* r, bool bracket) {
   CK(cudaMemsetAsync(J.Gt, 0, (size_t)r->plan.spec_total * sizeof(double2), st));
   CK(cudaMemsetAsync(J.W, 0, (size_t)r->plan.spec_total * sizeof(double2), st));
   CK(cudaMemsetAsync(J.Vobs, 0, (size_t)std::max(1, J.n_obs * J.Q * J.L) * sizeof(double2), st));
-  CK(cudaMemsetAsync(J.refine_resid, 0, 3 * sizeof(double), st));
-  CK(cudaMemsetAsync(J.dev_err, 0, sizeof(int), st));
-  if (J.sys_err) CK(cudaMemsetAsync(J.sys_err, 0, r->plan.sys.size() * sizeof(float), st));
-  if (J.mrho) CK(cudaMemsetAsync(J.mrho, 0, r->plan.sys.size() * sizeof(float), st));   // measured per run
   TRY(stage(r, FTHMS_STAGE_INCIDENT, st, &nl, [&] { return launch_incident(J, st, &nl); }));
   TRY(stage(r, FTHMS_STAGE_RESTRICT, st, &nl, [&] { return launch_restrict(J, st, &nl); }));
   for (int m = 1; m <= J.M; ++m) {
