@@ -488,13 +488,16 @@ def ours(args):
         head["err"] = 0.0
     value = job_value(ws, solves, head["ms"])
 
-    # end to end through the C ABI with host buffers (default launch shapes)
+    # end to end through the C ABI with host buffers, the headline form's tuned shapes given in the options
+    e2e_problem = dict(problem, options=dict(problem["options"]))
+    if head.get("shapes"):
+        e2e_problem["options"]["shapes"] = [int(v) for v in head["shapes"]]
     e2e_steps = max(1, min(args.steps, 3))
     torch.cuda.synchronize()
     d2h = h2d = 0
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        m = F.Marshalled(problem, keep_densities=False, precision=head["precision"])
+        m = F.Marshalled(e2e_problem, keep_densities=False, precision=head["precision"])
         req = F.fthms_submit(ctx, m)
         try:
             F.fthms_wait(req)
@@ -581,7 +584,8 @@ def ours(args):
                            "parallelism": f"replicas x{ws}"},
                 "e2e": {"value": job_value(ws, solves, e2e_ms), "unit": "solves/s", "ms_per_step": e2e_ms,
                         "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                        "note": "fthms_submit + wait + traces and summed densities to host + release, default shapes"},
+                        "note": "fthms_submit + wait + traces and summed densities to host + release, the headline "
+                                "form's shapes passed in fthms_options.shapes"},
                 "gpu_launches": int(head["stats"]["kernel_launches"] * args.steps),
                 "roofline": roof,
                 "stages_ms_per_step": {k: v[0] for k, v in head["stages"].items()} if head.get("stages") else None,

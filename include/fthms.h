@@ -146,7 +146,10 @@ typedef struct {
  *              frequencies, so the ranks add their partial time samples with the all-reduce given to
  *              fthms_set_allreduce before the windowed forward transforms (eq. Fourierk) of their own
  *              frequencies.  fthms_densities then covers the rank's frequencies only; the traces are
- *              summed across ranks the same way. */
+ *              summed across ranks the same way.
+ *  shapes    : launch shapes and LU path, the five choices fthms_autotune returns and fthms_set_shapes
+ *              takes (same candidates; all 0 = built-in defaults), applied from the job's first run: a job
+ *              submitted with fthms_submit runs tuned without an autotuning pass.  Others -> EINVAL. */
 typedef struct {
   double W;
   int L;
@@ -167,6 +170,7 @@ typedef struct {
   int refine_max;
   int refine_fallback;
   int omega_rank, omega_ranks;
+  int shapes[5];
 } fthms_options;
 
 typedef struct {
@@ -294,6 +298,14 @@ enum {
  * the five choices (the last 0 for an FP64 job).  The job's earlier results are overwritten: call
  * fthms_run afterwards.  Not in the paper (a batching aid of this library). */
 fthms_status fthms_autotune(fthms_req* req, int reps, int* shapes);
+
+/* Apply five choices as fthms_autotune returns them (e.g. tuned once on a job of the same sizes) without
+ * timing anything: shapes[0] warps per solve block {1, 2, 4}, [1] threads per cross-assembly block
+ * {64, 128, 256}, [2] per time-transform block {128, 256, 512}, [3] per restriction block {64, 128, 256},
+ * [4] the smallest N factored with tensor-core updates {256, 384, 512, 801} (mixed forms; must be 0 for an
+ * FP64 job); 0 anywhere keeps the built-in default.  FTHMS_EINVAL for any other value (nothing changes
+ * then).  A captured graph is dropped.  Later fthms_run calls use them. */
+fthms_status fthms_set_shapes(fthms_req* req, const int* shapes);
 
 /* Sum across the ranks of a frequency-partitioned job (options omega_ranks > 1): called on the host from
  * fthms_run, M times per run (after each step's partial synthesis, with buf_dev = the n_act x N_T time

@@ -177,6 +177,22 @@ void set_lu_split(fthms_req* r, int n_big) {
   J.big_max_n = n_big > 0 ? p.sys[p.sys_order[0]].N : 0;
 }
 
+// Launch shapes and LU split from five choices (validated): 0 keeps the built-in default.
+void apply_shapes(fthms_req* r, const int* shapes) {
+  DevJob& J = r->J;
+  J.shape_solve = shapes[0];
+  J.shape_asm = shapes[1];
+  J.shape_time = shapes[2];
+  J.shape_restr = shapes[3];
+  if (r->plan.opt.precision >= 1) {
+    const int lu_min = shapes[4] ? shapes[4] : kLuBigMin;
+    int nb = 0;
+    while (nb < (int)r->plan.sys_order.size() && r->plan.sys[r->plan.sys_order[nb]].N >= lu_min) ++nb;
+    set_lu_split(r, nb);
+    r->lu_min = lu_min;
+  }
+}
+
 fthms_status upload_job(fthms_req* r) {
   Plan& p = r->plan;
   DevJob& J = r->J;
@@ -261,7 +277,6 @@ fthms_status upload_job(fthms_req* r) {
   J.grp_res_off = nullptr;
   J.apply_res = nullptr;
   J.otf = p.opt.cross_mode == 1 ? 1 : 0;
-  J.shape_solve = J.shape_asm = J.shape_time = J.shape_restr = 0;
   J.n_otf = 0;
   J.otf_tasks = nullptr;
   J.wn_off = nullptr;
@@ -282,6 +297,7 @@ fthms_status upload_job(fthms_req* r) {
     TRY(dev_alloc(r, (size_t)p.wn_total, &J.wn));
     J.n_otf = (int)p.otf.size();
   }
+  apply_shapes(r, p.opt.shapes);       // launch shapes and LU split (fthms_options.shapes; 0 = default)
   TRY(dev_upload(r, p.tpanel, &J.tpanel));
   TRY(dev_upload(r, p.tr_off, &J.tr_off));
   TRY(dev_upload(r, p.chi, &J.chi));
@@ -300,6 +316,8 @@ fthms_status upload_job(fthms_req* r) {
   J.LU32 = nullptr;
   J.dinv32 = nullptr;
   J.rres = nullptr;
+  J.rres64 = nullptr;
+  J.dcorr = nullptr;
   J.mdone = nullptr;
   J.mrel = nullptr;
   J.mrho = nullptr;
@@ -314,6 +332,8 @@ fthms_status upload_job(fthms_req* r) {
     TRY(dev_alloc(r, (size_t)p.mat_total, &J.LU32));
     TRY(dev_alloc(r, (size_t)p.piv_total, &J.dinv32));
     TRY(dev_alloc(r, (size_t)p.vec_total, &J.rres));
+    TRY(dev_alloc(r, (size_t)p.vec_total, &J.rres64));
+    TRY(dev_alloc(r, (size_t)p.vec_total, &J.dcorr));
     TRY(dev_alloc(r, p.sys.size(), &J.mdone));
     TRY(dev_alloc(r, p.sys.size(), &J.mrel));
     TRY(dev_alloc(r, p.sys.size(), &J.mrho));
@@ -974,6 +994,19 @@ fthms_status fthms_autotune(fthms_req* req, int reps, int* shapes) {
     shapes[3] = J.shape_restr;
     shapes[4] = J.mixed ? req->lu_min : 0;
   }
+  return FTHMS_OK;
+}
+
+fthms_status fthms_set_shapes(fthms_req* req, const int* shapes) {
+  if (!req || !shapes) return fail(FTHMS_EINVAL, "fthms_set_shapes: NULL argument");
+  if (!req->ctx) return fail(FTHMS_EINVAL, "fthms_set_shapes: the job's context was destroyed");
+  if (!shapes_valid(shapes, req->plan.opt.precision >= 1))
+    return fail(FTHMS_EINVAL, "fthms_set_shapes: a choice outside its candidates");
+  if (req->graph) {                    // a captured graph holds the old launch shapes
+    cudaGraphExecDestroy(req->graph);
+    req->graph = nullptr;
+  }
+  apply_shapes(req, shapes);
   return FTHMS_OK;
 }
 

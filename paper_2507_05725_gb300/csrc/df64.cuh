@@ -229,4 +229,38 @@ __device__ __forceinline__ df df_rsqrt(df a) {
   return out;
 }
 
+
+// a ~ hi + lo for a double a with 2^-60 <= |a| < 2^100 by integer operations only (no FP64 instruction):
+// hi = a truncated to 24 significant bits, lo = the 29 fraction bits below them rounded to 24 bits (one
+// integer-to-float conversion, its exponent then shifted by that of a), so |a - hi - lo| <= 2^-47 |a|.
+// Outside that range (zero included) the FP64 conversions.
+__device__ __forceinline__ void split_f64_bits(double a, float& hi, float& lo) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(a);
+  const unsigned int uh = (unsigned int)(u >> 32), ul = (unsigned int)u;
+  const int e = (int)((uh >> 20) & 0x7FFu);                   // biased FP64 exponent
+  if (e < 1023 - 60 || e > 1023 + 100) {
+    hi = __double2float_rn(a);
+    lo = __double2float_rn(a - (double)hi);
+    return;
+  }
+  const unsigned int sign = uh & 0x80000000u;
+  const unsigned int frac23 = __funnelshift_l(ul, uh, 3) & 0x007FFFFFu;   // the top 23 fraction bits
+  hi = __uint_as_float(sign | ((unsigned int)(e - 1023 + 127) << 23) | frac23);
+  const unsigned int rem = ul & 0x1FFFFFFFu;                  // the 29 fraction bits below: rem 2^(e - 1075)
+  const float r = __uint2float_rn(rem);
+  lo = rem ? __uint_as_float(sign | (__float_as_uint(r) + ((unsigned int)(e - 1075) << 23))) : 0.f;
+}
+
+// acc += a * b for a = ah + al (double-float) and b a float: the exact error of ah b by the FMA
+// two-product, al b added to the low word.
+__device__ __forceinline__ void dfacc_mac1(dfacc& acc, float ah, float al, float b) {
+  const float p = __fmul_rn(ah, b);
+  float e = fmaf(ah, b, -p);
+  e = fmaf(al, b, e);
+  float s, t;
+  two_sum(acc.hi, p, s, t);
+  acc.hi = s;
+  acc.lo = __fadd_rn(acc.lo, __fadd_rn(t, e));
+}
+
 }  // namespace fthms

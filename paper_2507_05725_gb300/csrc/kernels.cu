@@ -555,16 +555,22 @@ __global__ void __launch_bounds__(kLuThreads) k_lu(DevJob J) {
 // and D^{-1} is applied between the sweeps).  C = double2 (FP64 factors) or float2 (FP32 factors).
 constexpr int kSolveWarps = 4;
 
-// Rows i0 and i0 + 32 of b -= T[:, r0..r0+w) x with x = b[r0..r0+w), column-major T of leading
-// dimension N.  Each batch of columns (8 for FP64 factors, 16 for FP32) issues the loads of both rows
-// before their FMAs, so a lane has 16 or 32 independent loads in flight instead of walking its rows one
-// after another.  A second row past
-// `end` is computed on the first and not stored.
-template <class C>
-__device__ __forceinline__ void tri_update2(C* bq, const C* __restrict__ A, int N, int r0, int w, int i0, int end) {
+// Rows i0 and i0 + 32 of every window's b_q -= T[:, r0..r0+w) x_q with x_q = b_q[r0..r0+w), column-major T
+// of leading dimension N: each factor entry is loaded once for all QT windows.  Each batch of columns
+// issues the loads of both rows before their FMAs, so a lane has 2 x kCols independent loads in flight
+// instead of walking its rows one after another.  A second row past `end` is computed on the first and
+// not stored.
+template <class C, int QT>
+__device__ __forceinline__ void tri_update2(C* b, int N, const C* __restrict__ A, int r0, int w, int i0, int end) {
   const int i1 = i0 + 32 < end ? i0 + 32 : i0;
-  constexpr int kCols = sizeof(C) == 8 ? 16 : 8;   // columns per load batch (FP32 factors: 16)
-  C a0 = bq[i0], a1 = bq[i1];
+  // columns per load batch: 16 FP32 or 8 FP64 entries per row, halved for 3-4 windows (registers)
+  constexpr int kCols = (sizeof(C) == 8 ? 16 : 8) / (QT > 2 ? 2 : 1);
+  C a0[QT], a1[QT];
+#pragma unroll
+  for (int q = 0; q < QT; ++q) {
+    a0[q] = b[q * N + i0];
+    a1[q] = b[q * N + i1];
+  }
 #pragma unroll 1
   for (int c0 = 0; c0 < kSB; c0 += kCols) {
     C v0[kCols], v1[kCols];
@@ -579,20 +585,62 @@ __device__ __forceinline__ void tri_update2(C* bq, const C* __restrict__ A, int 
 #pragma unroll
     for (int k = 0; k < kCols; ++k) {
       if (c0 + k < w) {
-        const C x = bq[r0 + c0 + k];
-        a0 = cfms(v0[k], x, a0);
-        a1 = cfms(v1[k], x, a1);
+#pragma unroll
+        for (int q = 0; q < QT; ++q) {
+          const C x = b[q * N + r0 + c0 + k];
+          a0[q] = cfms(v0[k], x, a0[q]);
+          a1[q] = cfms(v1[k], x, a1[q]);
+        }
       }
     }
   }
-  bq[i0] = a0;
-  if (i0 + 32 < end) bq[i0 + 32] = a1;
+#pragma unroll
+  for (int q = 0; q < QT; ++q) {
+    b[q * N + i0] = a0[q];
+    if (i0 + 32 < end) b[q * N + i0 + 32] = a1[q];
+  }
 }
 
-template <class C>
-__device__ void tri_solve(C* b, int Q, int N, const C* __restrict__ A, const int* __restrict__ piv,
+// x_q = T_kk^{-1} b_q on the block rows r0 .. r0+w (the diagonal block stored inverted, so a GEMV): lane =
+// row, the block's entries loaded once for all QT windows.  lower: the unit-lower block (entries left of
+// the diagonal); else the unit-upper one (right of it).
+template <class C, int QT>
+__device__ __forceinline__ void tri_diag(C* b, int N, const C* __restrict__ A, int r0, int w, int lane, bool lower) {
+  C x[QT];
+  if (lane < w) {
+#pragma unroll
+    for (int q = 0; q < QT; ++q) x[q] = b[q * N + r0 + lane];
+#pragma unroll 1
+    for (int h = 0; h < kSB; h += 16) {        // 16 loads in flight, then their FMAs
+      C v[16];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const bool use = lower ? h + k < lane : (h + k > lane && h + k < w);
+        if (use) v[k] = __ldg(&A[(long long)(r0 + h + k) * N + r0 + lane]);
+      }
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const bool use = lower ? h + k < lane : (h + k > lane && h + k < w);
+        if (use) {
+#pragma unroll
+          for (int q = 0; q < QT; ++q) x[q] = cfms(make_neg(v[k]), b[q * N + r0 + h + k], x[q]);
+        }
+      }
+    }
+  }
+  __syncwarp();
+  if (lane < w) {
+#pragma unroll
+    for (int q = 0; q < QT; ++q) b[q * N + r0 + lane] = x[q];
+  }
+  __syncwarp();
+}
+
+// Both triangular sweeps of one system for its QT windows b[q * N + i] (shared memory), one warp.
+template <class C, int QT>
+__device__ void tri_solve(C* b, int N, const C* __restrict__ A, const int* __restrict__ piv,
                           const C* __restrict__ dinv, int lane) {
-  if (lane < Q) {
+  if (lane < QT) {
     C* bq = b + lane * N;
     for (int k = 0; k < N; ++k) {
       const int p = __ldg(&piv[k]);
@@ -602,60 +650,23 @@ __device__ void tri_solve(C* b, int Q, int N, const C* __restrict__ A, const int
   __syncwarp();
   for (int r0 = 0; r0 < N; r0 += kSB) {           // forward, unit lower
     const int w = min(kSB, N - r0), r1 = r0 + w;
-    for (int q = 0; q < Q; ++q) {
-      C* bq = b + q * N;
-      C x = C{};
-      if (lane < w) {
-        x = bq[r0 + lane];
+    tri_diag<C, QT>(b, N, A, r0, w, lane, true);
 #pragma unroll 1
-        for (int h = 0; h < kSB; h += 16) {        // 16 loads in flight, then their FMAs
-          C v[16];
-#pragma unroll
-          for (int k = 0; k < 16; ++k)
-            if (h + k < lane) v[k] = __ldg(&A[(long long)(r0 + h + k) * N + r0 + lane]);
-#pragma unroll
-          for (int k = 0; k < 16; ++k)
-            if (h + k < lane) x = cfms(make_neg(v[k]), bq[r0 + h + k], x);
-        }
-      }
-      __syncwarp();
-      if (lane < w) bq[r0 + lane] = x;
-      __syncwarp();
-#pragma unroll 1
-      for (int i0 = r1 + lane; i0 < N; i0 += 64) tri_update2(bq, A, N, r0, w, i0, N);
-      __syncwarp();
-    }
+    for (int i0 = r1 + lane; i0 < N; i0 += 64) tri_update2<C, QT>(b, N, A, r0, w, i0, N);
+    __syncwarp();
   }
-  for (int e = lane; e < Q * N; e += 32) b[e] = cmul(b[e], __ldg(&dinv[e % N]));
+  for (int e = lane; e < QT * N; e += 32) b[e] = cmul(b[e], __ldg(&dinv[e % N]));
   __syncwarp();
   for (int r0 = ((N - 1) / kSB) * kSB; r0 >= 0; r0 -= kSB) {   // backward, unit upper
     const int w = min(kSB, N - r0);
-    for (int q = 0; q < Q; ++q) {
-      C* bq = b + q * N;
-      C x = C{};
-      if (lane < w) {
-        x = bq[r0 + lane];
+    tri_diag<C, QT>(b, N, A, r0, w, lane, false);
 #pragma unroll 1
-        for (int h = 0; h < kSB; h += 16) {
-          C v[16];
-#pragma unroll
-          for (int k = 0; k < 16; ++k)
-            if (h + k > lane && h + k < w) v[k] = __ldg(&A[(long long)(r0 + h + k) * N + r0 + lane]);
-#pragma unroll
-          for (int k = 0; k < 16; ++k)
-            if (h + k > lane && h + k < w) x = cfms(make_neg(v[k]), bq[r0 + h + k], x);
-        }
-      }
-      __syncwarp();
-      if (lane < w) bq[r0 + lane] = x;
-      __syncwarp();
-#pragma unroll 1
-      for (int i0 = lane; i0 < r0; i0 += 64) tri_update2(bq, A, N, r0, w, i0, r0);
-      __syncwarp();
-    }
+    for (int i0 = lane; i0 < r0; i0 += 64) tri_update2<C, QT>(b, N, A, r0, w, i0, r0);
+    __syncwarp();
   }
 }
 
+template <int QT>
 __global__ void __launch_bounds__(32 * kSolveWarps) k_solve(DevJob J, int m) {
   extern __shared__ double2 shs[];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -663,12 +674,12 @@ __global__ void __launch_bounds__(32 * kSolveWarps) k_solve(DevJob J, int m) {
   if (slot >= J.nsys) return;
   const int sidx = J.sys_order[slot];
   const SysDesc s = J.sys[sidx];
-  const int N = s.N, Q = J.Q;
+  const int N = s.N, Q = QT;
   double2* b = shs + (size_t)wid * Q * J.max_n;
   const double2* G = J.G + s.vec_off;
   for (int e = lane; e < Q * N; e += 32) b[e] = G[e];
   __syncwarp();
-  tri_solve<double2>(b, Q, N, J.A + s.mat_off, J.piv + s.piv_off, J.dinv + s.piv_off, lane);
+  tri_solve<double2, QT>(b, N, J.A + s.mat_off, J.piv + s.piv_off, J.dinv + s.piv_off, lane);
   double2* out = J.phi + s.vec_off;
   double2* sum = J.phi_sum + s.vec_off;
   double2* all = J.phi_all ? J.phi_all + (long long)(m - 1) * J.vec_total + s.vec_off : nullptr;
@@ -1401,8 +1412,65 @@ __global__ void __launch_bounds__(kResidThreads) k_mresid64(DevJob J) {
   }
   if (i < N) {
 #pragma unroll
-    for (int q = 0; q < Q; ++q)
+    for (int q = 0; q < Q; ++q) {
       J.rres[s.vec_off + q * N + i] = make_float2(__double2float_rn(acc[q].x), __double2float_rn(acc[q].y));
+      J.rres64[s.vec_off + q * N + i] = acc[q];
+    }
+  }
+}
+
+// Later passes of the systems that keep FP64: the residual of the previous pass updated with its
+// correction, r <- r - A d, instead of a new FP64 residual G - A phi (the same value: phi grew by d).  The
+// FP64 matrix is split into two floats by integer operations (split_f64_bits) and d is an FP32 vector, so
+// every product is formed to about 2^-47 on the FP32 pipe (FMA two-product) and summed with compensated
+// double-float sums over the columns in order.  The update's error, about 2^-47 |A| |d|, stays far below
+// the FP64 residual's 2^-53 |A| |phi| since the correction d is much smaller than phi; the FP64 pipe does
+// one conversion per row.
+template <int Q>
+__global__ void __launch_bounds__(kResidThreads) k_mresid_upd(DevJob J) {
+  const int chunk = blockIdx.x * (kResidThreads / 32) + (threadIdx.x >> 5);
+  if (chunk >= J.n_rchunks) return;
+  const ResidChunk c = J.rchunks[chunk];
+  if (J.mdone[c.sys]) return;
+  const SysDesc s = J.sys[c.sys];
+  const int N = s.N;
+  if (!sys_f64(J, N)) return;                 // double-float systems: k_mresid
+  const int i = c.row0 + (threadIdx.x & 31);
+  const int row = i < N ? i : N - 1;
+  const double2* __restrict__ A64 = J.A + s.mat_off;
+  const float2* __restrict__ d = J.dcorr + s.vec_off;
+  double2* r64 = J.rres64 + s.vec_off;
+  dfacc re[Q], im[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const float4 rd = df_split2(r64[q * N + row]);
+    re[q].add(rd.x, rd.y);
+    im[q].add(rd.z, rd.w);
+  }
+  constexpr int kUnroll = Q == 1 ? 8 : Q == 2 ? 4 : 2;
+#pragma unroll kUnroll
+  for (int j = 0; j < N; ++j) {
+    const double2 a = __ldg(&A64[(long long)j * N + row]);
+    float arh, arl, aih, ail;
+    split_f64_bits(a.x, arh, arl);
+    split_f64_bits(a.y, aih, ail);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const float2 dv = d[q * N + j];
+      // r -= a d:  Re -= ar dr - ai di,  Im -= ar di + ai dr
+      dfacc_mac1(re[q], -arh, -arl, dv.x);
+      dfacc_mac1(re[q], aih, ail, dv.y);
+      dfacc_mac1(im[q], -arh, -arl, dv.y);
+      dfacc_mac1(im[q], -aih, -ail, dv.x);
+    }
+  }
+  if (i < N) {
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const df rr = re[q].value(), ri = im[q].value();
+      J.rres[s.vec_off + q * N + i] = make_float2(rr.hi + rr.lo, ri.hi + ri.lo);
+      r64[q * N + i] = make_double2((double)rr.hi + (double)rr.lo, (double)ri.hi + (double)ri.lo);
+    }
   }
 }
 
@@ -1469,7 +1537,8 @@ __global__ void __launch_bounds__(kResidThreads) k_mresid(DevJob J) {
 // it), mark the system as refining.  pass p >= 1: solve for the correction from the residual, add it in
 // double-float (FP64), and finish the system (FP64 densities, their double-float copy for the cross apply,
 // their running sum, the statistics) once the correction is small enough or p = J.refine_max.
-__global__ void __launch_bounds__(32 * kSolveWarps, 4) k_msolve(DevJob J, int m, int pass) {
+template <int QT>
+__global__ void __launch_bounds__(32 * kSolveWarps, 3) k_msolve(DevJob J, int m, int pass) {
   extern __shared__ __align__(16) unsigned char shm_raw[];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nw = blockDim.x >> 5;
@@ -1478,7 +1547,7 @@ __global__ void __launch_bounds__(32 * kSolveWarps, 4) k_msolve(DevJob J, int m,
   const int sidx = J.sys_order[slot];
   if (pass > 0 && J.mdone[sidx]) return;
   const SysDesc s = J.sys[sidx];
-  const int N = s.N, Q = J.Q;
+  const int N = s.N, Q = QT;
   const bool f64 = sys_f64(J, N);            // densities refined in FP64 (FP64 residual)
   float2* b = reinterpret_cast<float2*>(shm_raw) + (size_t)wid * Q * J.max_n;
   const float2* __restrict__ L32 = J.LU32 + s.mat_off;
@@ -1507,7 +1576,7 @@ __global__ void __launch_bounds__(32 * kSolveWarps, 4) k_msolve(DevJob J, int m,
     for (int e = lane; e < Q * N; e += 32) b[e] = r[e];
   }
   __syncwarp();
-  tri_solve<float2>(b, Q, N, L32, piv, dinv, lane);
+  tri_solve<float2, QT>(b, N, L32, piv, dinv, lane);
   double2* ph64 = J.phi + s.vec_off;
   if (pass == 0) {
     if (f64) {
@@ -1519,9 +1588,11 @@ __global__ void __launch_bounds__(32 * kSolveWarps, 4) k_msolve(DevJob J, int m,
     return;
   }
   float dmax = 0.f, pmax = 0.f;
+  float2* dc = J.dcorr + s.vec_off;
   for (int e = lane; e < Q * N; e += 32) {
     const float2 d = b[e];
     if (f64) {
+      dc[e] = d;                              // the next pass updates the residual with it
       double2 p = ph64[e];
       p.x += (double)d.x;
       p.y += (double)d.y;
@@ -2209,49 +2280,47 @@ static int solve_warps(size_t bytes_per_warp, int wanted) {
   return nw;
 }
 
-cudaError_t launch_solve(const DevJob& J, int m, cudaStream_t st, int* launches) {
+template <int QT>
+static cudaError_t launch_solve_q(const DevJob& J, int m, cudaStream_t st, int* launches) {
   if (J.mixed) {
-    const size_t per = (size_t)J.Q * J.max_n * sizeof(float2);
+    const size_t per = (size_t)QT * J.max_n * sizeof(float2);
     const int nw = solve_warps(per, J.shape_solve);
     const size_t sh = (size_t)nw * per;
-    cudaError_t e = cudaFuncSetAttribute(k_msolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+    cudaError_t e = cudaFuncSetAttribute(k_msolve<QT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
     if (e != cudaSuccess) return e;
     const int grid = cdiv(J.nsys, nw), rgrid = cdiv(J.n_rchunks, kResidThreads / 32);
     const int passes = std::min(std::max(J.refine_max, 1), kRefineCap);
-    k_msolve<<<grid, 32 * nw, sh, st>>>(J, m, 0);
+    k_msolve<QT><<<grid, 32 * nw, sh, st>>>(J, m, 0);
     for (int pass = 1; pass <= passes && rgrid > 0; ++pass) {
       // FP64 residuals for the systems that keep FP64 (all in the FP64-kept form), double-float for the rest
       const bool any64 = J.fp64keep || J.max_n >= J.f64_min_n, anydf = !J.fp64keep;
-      if (any64) {
-        switch (J.Q) {
-          case 1: k_mresid64<1><<<rgrid, kResidThreads, 0, st>>>(J); break;
-          case 2: k_mresid64<2><<<rgrid, kResidThreads, 0, st>>>(J); break;
-          case 3: k_mresid64<3><<<rgrid, kResidThreads, 0, st>>>(J); break;
-          default: k_mresid64<4><<<rgrid, kResidThreads, 0, st>>>(J); break;
-        }
-      }
-      if (anydf) {
-        switch (J.Q) {
-          case 1: k_mresid<1><<<rgrid, kResidThreads, 0, st>>>(J); break;
-          case 2: k_mresid<2><<<rgrid, kResidThreads, 0, st>>>(J); break;
-          case 3: k_mresid<3><<<rgrid, kResidThreads, 0, st>>>(J); break;
-          default: k_mresid<4><<<rgrid, kResidThreads, 0, st>>>(J); break;
-        }
-      }
+      // (the first pass forms G - A phi in FP64; later passes update that residual with the correction)
+      if (any64 && pass == 1) k_mresid64<QT><<<rgrid, kResidThreads, 0, st>>>(J);
+      else if (any64) k_mresid_upd<QT><<<rgrid, kResidThreads, 0, st>>>(J);
+      if (anydf) k_mresid<QT><<<rgrid, kResidThreads, 0, st>>>(J);
       *launches += (int)any64 + (int)anydf - 1;
-      k_msolve<<<grid, 32 * nw, sh, st>>>(J, m, pass);
+      k_msolve<QT><<<grid, 32 * nw, sh, st>>>(J, m, pass);
     }
     *launches += 1 + 2 * passes;
     return cudaGetLastError();
   }
-  const size_t per = (size_t)J.Q * J.max_n * sizeof(double2);
+  const size_t per = (size_t)QT * J.max_n * sizeof(double2);
   const int nw = solve_warps(per, J.shape_solve);
   size_t sh = (size_t)nw * per;
-  cudaError_t e = cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+  cudaError_t e = cudaFuncSetAttribute(k_solve<QT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
   if (e != cudaSuccess) return e;
-  k_solve<<<cdiv(J.nsys, nw), 32 * nw, sh, st>>>(J, m);
+  k_solve<QT><<<cdiv(J.nsys, nw), 32 * nw, sh, st>>>(J, m);
   *launches += 1;
   return cudaGetLastError();
+}
+
+cudaError_t launch_solve(const DevJob& J, int m, cudaStream_t st, int* launches) {
+  switch (J.Q) {
+    case 1: return launch_solve_q<1>(J, m, st, launches);
+    case 2: return launch_solve_q<2>(J, m, st, launches);
+    case 3: return launch_solve_q<3>(J, m, st, launches);
+    default: return launch_solve_q<4>(J, m, st, launches);
+  }
 }
 
 template <int Q>

@@ -80,6 +80,8 @@ struct DevJob {
                              // (system, step) pairs (64-bit integers in [1], [2]; mixed form)
   float* sys_err;            // per system: max over steps of the estimated relative error left (mixed form)
   float2* rres;              // FP32-rounded refinement residuals, laid out like G (mixed form)
+  double2* rres64;           // FP64-kept systems: the residual the next pass updates, laid out like G
+  float2* dcorr;             // FP64-kept systems: the last FP32 correction, laid out like G
   int* mdone;                // per system: 1 once its refinement has finished this step (mixed form)
   float* mrel;               // per system: relative size of its last correction (mixed form)
   float* mrho;               // per system: largest contraction factor measured in earlier steps (0: none yet)

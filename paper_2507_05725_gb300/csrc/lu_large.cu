@@ -124,8 +124,9 @@ __global__ void __launch_bounds__(kPanelThreads) k_lu_big_panel(DevJob J, int k0
     __syncthreads();
   }
   // The panel's interchanges on every column outside it, in order (rows k and piv[k], k = k0 .. kend-1): a
-  // column's rows k0 .. kend-1 in registers, pivot rows below them in HBM; right of the panel, fused with
-  // U12 = L11^{-1} A12 on those rows.
+  // column's rows k0 .. kend-1 in a per-thread segment of shared memory (the inner-panel buffer, free
+  // now; element r of thread t at seg[r * kPanelThreads + t], conflict-free), pivot rows below them in
+  // HBM; then, right of the panel, U12 = L11^{-1} A12 on those rows in registers (static indices only).
   __shared__ int pv[kOuter];
   for (int e = tid; e < nbo * nbo; e += kPanelThreads) {
     const int c = e / nbo, r = e % nbo;
@@ -133,42 +134,34 @@ __global__ void __launch_bounds__(kPanelThreads) k_lu_big_panel(DevJob J, int k0
   }
   if (tid < nbo) pv[tid] = piv[k0 + tid] - k0;
   __syncthreads();
+  float2* seg = Pn;
   for (int col = tid; col < N - nbo; col += kPanelThreads) {
     const int cc = col < k0 ? col : col + nbo;        // skip the panel's own columns
     float2* Ac = A + (long long)cc * N + k0;
-    float2 x[kOuter];
-#pragma unroll
-    for (int r = 0; r < kOuter; ++r)
-      if (r < nbo) x[r] = Ac[r];
-#pragma unroll
-    for (int c = 0; c < kOuter; ++c) {
-      if (c < nbo) {
-        const int p = pv[c];
-        if (p != c) {
-          if (p < nbo) {
-#pragma unroll
-            for (int q = 0; q < kOuter; ++q)        // x[c] <-> x[p] with register indices only
-              if (q == p) { const float2 t = x[q]; x[q] = x[c]; x[c] = t; }
-          } else {
-            const float2 t = Ac[p];
-            Ac[p] = x[c];
-            x[c] = t;
-          }
-        }
-      }
+    for (int r = 0; r < nbo; ++r) seg[r * kPanelThreads + tid] = Ac[r];
+    for (int c = 0; c < nbo; ++c) {
+      const int p = pv[c];
+      if (p == c) continue;
+      const float2 t = p < nbo ? seg[p * kPanelThreads + tid] : Ac[p];
+      if (p < nbo) seg[p * kPanelThreads + tid] = seg[c * kPanelThreads + tid];
+      else Ac[p] = seg[c * kPanelThreads + tid];
+      seg[c * kPanelThreads + tid] = t;
     }
     if (cc >= kend) {
+      float2 x[kOuter];
+#pragma unroll
+      for (int r = 0; r < kOuter; ++r) x[r] = r < nbo ? seg[r * kPanelThreads + tid] : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int r = 1; r < kOuter; ++r) {
+#pragma unroll
+        for (int c = 0; c < r; ++c) x[r] = cfms(L11[r][c], x[c], x[r]);
+      }
 #pragma unroll
       for (int r = 0; r < kOuter; ++r)
-        if (r < nbo) {
-#pragma unroll
-          for (int c = 0; c < kOuter; ++c)
-            if (c < r) x[r] = cfms(L11[r][c], x[c], x[r]);
-        }
+        if (r < nbo) Ac[r] = x[r];
+    } else {
+      for (int r = 0; r < nbo; ++r) Ac[r] = seg[r * kPanelThreads + tid];
     }
-#pragma unroll
-    for (int r = 0; r < kOuter; ++r)
-      if (r < nbo) Ac[r] = x[r];
   }
 }
 
@@ -304,12 +297,19 @@ __global__ void __launch_bounds__(kLuThreadsFinish) k_lu_big_finish(DevJob J) {
 
 }  // namespace
 
-size_t lu_big_panel_smem(int maxN) { return (size_t)maxN * kInnerPS * sizeof(float2); }
+// The inner-panel rows (maxN x kInnerPS) or, later in the same buffer, the threads' 32-row column segments.
+size_t lu_big_panel_smem(int maxN) {
+  const size_t pn = (size_t)maxN * kInnerPS, segs = (size_t)kOuter * kPanelThreads;
+  return (pn > segs ? pn : segs) * sizeof(float2);
+}
 
 cudaError_t launch_lu_large(const DevJob& J, cudaStream_t st, int* launches) {
   if (J.n_lu_big == 0) return cudaSuccess;
   const size_t sh_p = lu_big_panel_smem(J.big_max_n);
   cudaError_t e = cudaFuncSetAttribute(k_lu_big_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh_p);
+  if (e != cudaSuccess) return e;
+  // the largest shared-memory carveout, so that two panel CTAs (128 registers a thread) share an SM
+  e = cudaFuncSetAttribute(k_lu_big_panel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e != cudaSuccess) return e;
   const size_t sh_u = (size_t)8 * kPartBytes;
   e = cudaFuncSetAttribute(k_lu_big_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh_u);

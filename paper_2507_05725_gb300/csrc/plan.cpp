@@ -113,7 +113,19 @@ double chi_at(const Plan& p, int j, double t) {
 
 bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
+
 }  // namespace
+
+bool shapes_valid(const int* sh, bool mixed) {
+  auto one_of = [](int v, std::initializer_list<int> ok) {
+    if (v == 0) return true;
+    for (int o : ok)
+      if (v == o) return true;
+    return false;
+  };
+  return one_of(sh[0], {1, 2, 4}) && one_of(sh[1], {64, 128, 256}) && one_of(sh[2], {128, 256, 512}) &&
+         one_of(sh[3], {64, 128, 256}) && (mixed ? one_of(sh[4], {256, 384, 512, kLuBigMin}) : sh[4] == 0);
+}
 
 int build_plan(const fthms_curve* curves, int ncurves, const fthms_arc* arcs, int narcs,
                const fthms_signal* sig, const fthms_options* opt, Plan& p, std::string& err) {
@@ -136,6 +148,12 @@ int build_plan(const fthms_curve* curves, int ncurves, const fthms_arc* arcs, in
   if (!(opt->refine_tol >= 0.0) || opt->refine_max < 0 || opt->refine_max > 16 ||
       (opt->refine_fallback != 0 && opt->refine_fallback != 1)) {
     err = "refine_tol must be >= 0, refine_max in [0, 16] and refine_fallback 0 or 1";
+    return FTHMS_EINVAL;
+  }
+  if (!shapes_valid(opt->shapes, opt->precision >= 1)) {
+    err = "shapes: a choice outside its candidates (solve warps {1, 2, 4}, assembly threads {64, 128, 256}, "
+          "time threads {128, 256, 512}, restriction threads {64, 128, 256}, LU {256, 384, 512, 801} in the mixed "
+          "forms and 0 in FP64; 0 = default)";
     return FTHMS_EINVAL;
   }
   if (p.opt.refine_tol == 0.0) p.opt.refine_tol = 1e-12;
@@ -668,9 +686,9 @@ void arc_nodes(const Curve& c, double theta_a, double theta_b, int N, std::vecto
 size_t plan_device_bytes(const Plan& p) {
   size_t b = 0;
   b += (size_t)p.mat_total * 16;                 // A / LU
-  if (p.opt.precision >= 1)                      // FP32 factors, FP32 residuals, refinement state
-    b += (size_t)p.mat_total * 8 + (size_t)p.piv_total * 8 + (size_t)p.vec_total * (8 + 16) + p.sys.size() * 24 +
-         p.rchunks.size() * sizeof(ResidChunk);
+  if (p.opt.precision >= 1)                      // FP32 factors, residuals and corrections, refinement state
+    b += (size_t)p.mat_total * 8 + (size_t)p.piv_total * 8 + (size_t)p.vec_total * (8 + 16 + 16 + 8) +
+         p.sys.size() * 24 + p.rchunks.size() * sizeof(ResidChunk);
   b += p.sig_f.size() * 8;                       // samples of a sampled signal
   b += (size_t)p.piv_total * 4;                  // pivots
   b += (size_t)p.rlog_total * 8;                 // self log tables

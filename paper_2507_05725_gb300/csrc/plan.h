@@ -98,6 +98,9 @@ struct Plan {
 int build_plan(const fthms_curve* curves, int ncurves, const fthms_arc* arcs, int narcs,
                const fthms_signal* sig, const fthms_options* opt, Plan& plan, std::string& err);
 
+// The five launch choices (fthms_options.shapes, fthms_set_shapes) are among their candidates.
+bool shapes_valid(const int* shapes, bool mixed);
+
 // Offsets of the device arrays for a plan (bytes are accumulated into plan.device_bytes).
 size_t plan_device_bytes(const Plan& p);
 

@@ -47,7 +47,7 @@ class fthms_options(C.Structure):
                 ("n_tout", C.c_int), ("tout0", C.c_double), ("dtout", C.c_double), ("precision", C.c_int),
                 ("keep_densities", C.c_int), ("cross_mode", C.c_int), ("refine_tol", C.c_double),
                 ("refine_max", C.c_int), ("refine_fallback", C.c_int), ("omega_rank", C.c_int),
-                ("omega_ranks", C.c_int)]
+                ("omega_ranks", C.c_int), ("shapes", C.c_int * 5)]
 
 
 class fthms_stats_t(C.Structure):
@@ -108,6 +108,7 @@ def _load():
         "fthms_server_destroy": (st, [vp]),
         "fthms_use_graph": (st, [vp, C.c_int]),
         "fthms_autotune": (st, [vp, C.c_int, C.POINTER(C.c_int)]),
+        "fthms_set_shapes": (st, [vp, C.POINTER(C.c_int)]),
         "fthms_profile": (st, [vp, C.c_int]),
         "fthms_stage_times": (st, [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
     }
@@ -126,7 +127,7 @@ EXPORTED = ["fthms_create", "fthms_destroy", "fthms_prepare", "fthms_run", "fthm
             "fthms_profile", "fthms_stage_times", "fthms_assemble_self_noalloc", "fthms_server_create",
             "fthms_server_submit", "fthms_server_poll", "fthms_server_wait", "fthms_server_result",
             "fthms_server_latency", "fthms_server_release", "fthms_server_destroy", "fthms_use_graph",
-            "fthms_autotune", "fthms_plan_info", "fthms_result_errors", "fthms_set_allreduce"]
+            "fthms_autotune", "fthms_plan_info", "fthms_result_errors", "fthms_set_allreduce", "fthms_set_shapes"]
 
 
 def _check(status):
@@ -170,7 +171,8 @@ class Marshalled:
                                      int(precision), int(keep_densities), int(o.get("cross_mode", 0)),
                                      float(o.get("refine_tol", 0.0)), int(o.get("refine_max", 0)),
                                      int(o.get("refine_fallback", 0)), int(o.get("omega_rank", 0)),
-                                     int(o.get("omega_ranks", 0)))
+                                     int(o.get("omega_ranks", 0)),
+                                     (C.c_int * 5)(*[int(v) for v in o.get("shapes", (0, 0, 0, 0, 0))]))
         self.ncurves, self.narcs = len(curves), len(arcs)
 
 
@@ -338,6 +340,12 @@ def fthms_autotune(req, reps=3):
     out = (C.c_int * 5)()
     _check(LIB.fthms_autotune(req, int(reps), out))
     return list(out)
+
+
+def fthms_set_shapes(req, shapes):
+    """Apply five choices as fthms_autotune returns them, without timing."""
+    arr = (C.c_int * 5)(*[int(v) for v in shapes])
+    _check(LIB.fthms_set_shapes(req, arr))
 
 
 def fthms_use_graph(req, enable=True):

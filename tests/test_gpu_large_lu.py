@@ -1,5 +1,6 @@
 """Large systems (N up to 2048) in the mixed forms: FP32 LU with tensor-core (tcgen05, 3xTF32) trailing
 updates, refined against the kept matrix, through the C ABI against the FP64 oracle."""
+import copy
 import math
 
 import numpy as np
@@ -60,6 +61,49 @@ def test_large_system_parity(F, ctx, N, precision):
     # an FP32-accurate factor needs about two refinement passes; a TF32-only one would need many more
     assert st["refine_passes"] <= 3.0, st["refine_passes"]
     assert np.max(np.abs(tr - ref.traces)) < 10 * MIXED_TOL * max(1e-300, np.max(np.abs(ref.traces)))
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_set_shapes_moves_systems_to_the_tensor_core_lu(F, ctx, precision):
+    """fthms_set_shapes (or fthms_options.shapes at prepare) with the LU choice 256 factors N = 300 systems
+    with tensor-core updates instead of the one-CTA LU; both paths refine to the FP64 oracle's densities."""
+    problem = _problem(300)
+    ref = run_oracle(problem)
+    in_options = copy.deepcopy(problem)
+    in_options["options"]["shapes"] = [2, 128, 256, 128, 256]   # the same choices given at prepare
+    for prob, shapes, n_tensor in ((problem, [0, 0, 0, 0, 0], 0), (problem, [2, 128, 256, 128, 256], 4),
+                                   (in_options, None, 4)):
+        job = F.Job(ctx, prob, precision=precision)
+        if shapes is not None:
+            F.fthms_set_shapes(job.req, shapes)
+        job.run().wait()
+        num = den = 0.0
+        for m in (1, 2):
+            for j in range(2):
+                d = job.densities(j, m, 0)
+                for l in (1, 2):
+                    r = ref.phi[(m, j, l)][0]
+                    num += float(np.sum(np.abs(d[l] - r) ** 2))
+                    den += float(np.sum(np.abs(r) ** 2))
+        st = job.stats()
+        job.release()
+        assert st["lu_tensor_systems"] == n_tensor
+        assert st["n_unconverged"] == 0
+        assert math.sqrt(num / den) < MIXED_TOL
+
+
+def test_set_shapes_rejects_choices_outside_the_candidates(F, ctx):
+    job = F.Job(ctx, _problem(300), precision=1)
+    for bad in ([3, 0, 0, 0, 0], [0, 96, 0, 0, 0], [0, 0, 0, 0, 100], [0, 0, 0, 0, 1024]):
+        with pytest.raises(F.FthmsError) as e:
+            F.fthms_set_shapes(job.req, bad)
+        assert e.value.status == F.FTHMS_EINVAL
+    job.release()
+    plain = F.Job(ctx, _problem(300), precision=0)
+    with pytest.raises(F.FthmsError):
+        F.fthms_set_shapes(plain.req, [0, 0, 0, 0, 256])   # the FP64 form has one LU path
+    F.fthms_set_shapes(plain.req, [2, 0, 256, 0, 0])
+    plain.release()
 
 
 def test_fp64_form_refuses_the_largest_systems(F, ctx):

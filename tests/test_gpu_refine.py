@@ -127,6 +127,21 @@ def test_tighter_refinement_tolerance_is_met(F, ctx):
     assert rel < DENSITY_TOL
 
 
+def test_fp64_kept_residual_updates_meet_a_tighter_tolerance(F, ctx):
+    """FP64-kept form with refine_tol = 1e-14 and up to 6 passes: the first residual in FP64, every later
+    one (at least the second pass's) updated with the last correction (r <- r - A d on the FP32 pipe); the
+    updated residual must stay accurate, so the densities land on the FP64 oracle well inside the mixed
+    form's bar."""
+    problem = wl.random_small(2, n_arcs_per_curve=3, kind=0, M=3)
+    problem["options"].update(refine_tol=1e-14, refine_max=6)
+    job = F.Job(ctx, problem, precision=2).run().wait()
+    st = job.stats()
+    assert st["n_unconverged"] == 0 and st["max_refine_resid"] < 1e-14 and st["refine_passes"] >= 2.0
+    rel = _rel_vs_oracle(job, run_oracle(problem), problem)
+    job.release()
+    assert rel < DENSITY_TOL
+
+
 # ---- sampled signals ---------------------------------------------------------------------------------
 
 def _sampled_problem(kind):

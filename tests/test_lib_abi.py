@@ -46,6 +46,7 @@ def test_host_validation_without_gpu():
     assert F.LIB.fthms_bessel0(None, None, None, None, -1, None) == F.FTHMS_EINVAL
     assert F.LIB.fthms_release(None) == F.FTHMS_EINVAL
     assert F.LIB.fthms_wait(None, 0) == F.FTHMS_EINVAL
+    assert F.LIB.fthms_set_shapes(None, None) == F.FTHMS_EINVAL
     d = C.c_int()
     assert F.LIB.fthms_poll(None, C.byref(d)) == F.FTHMS_EINVAL
 

@@ -81,6 +81,23 @@ def test_validation_without_a_gpu(F):
     assert _status(F, bad)[0] == F.FTHMS_EINVAL
 
 
+def test_launch_shapes_in_the_options_are_validated(F):
+    """fthms_options.shapes: the autotuner's candidates (0 = default) pass; anything else, and an LU choice in
+    the FP64 form (one LU path), is EINVAL; the choices change no device memory."""
+    p = wl.random_small(0)
+    ok = copy.deepcopy(p)
+    ok["options"]["shapes"] = [1, 256, 512, 64, 256]
+    assert F.fthms_plan_info(F.Marshalled(ok, precision=1)) == F.fthms_plan_info(F.Marshalled(p, precision=1))
+    ok["options"]["shapes"] = [4, 128, 256, 128, 0]
+    F.fthms_plan_info(F.Marshalled(ok, precision=0))
+    for bad_shapes, prec in (([3, 0, 0, 0, 0], 1), ([0, 32, 0, 0, 0], 1), ([0, 0, 1024, 0, 0], 1),
+                             ([0, 0, 0, 512, 0], 1), ([0, 0, 0, 0, 100], 1), ([0, 0, 0, 0, 256], 0)):
+        bad = copy.deepcopy(p)
+        bad["options"]["shapes"] = bad_shapes
+        st, msg = _status(F, bad, precision=prec)
+        assert st == F.FTHMS_EINVAL and "shapes" in msg
+
+
 def test_sampled_signal_plans_like_the_analytic_one(F):
     """A job whose signal is given by samples plans to the same systems; its device memory holds the
     samples as well."""
