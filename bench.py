@@ -320,49 +320,85 @@ def time_job(F, ctx, stream, problem, precision, steps, warmup, autotune=False, 
             "precision": precision, "autotune": autotune, "graph": graph, "clocks": clk.summary()}
 
 
-def roofline_of(r, M, Q, stored_rows):
-    """Roofline of the dominant stage of a timed job (stage CUDA-event timers, per stage invocation)."""
+def lu_update_flops(problem, n_tensor):
+    """Algorithmic tensor flops of the tcgen05 trailing updates of one job: per system and 32-column panel,
+    8 x 32 x T^2 real flops (T = trailing size), times 3 for the three-term TF32 split (N fixed per batch)."""
+    N = int(problem["options"].get("N_fixed") or 0)
+    per = sum(8.0 * 32 * (N - 32 * (k + 1)) ** 2 for k in range(N // 32 + 1) if N - 32 * (k + 1) > 0)
+    return 3.0 * per * n_tensor
+
+
+def stage_rooflines(r, problem, stored_rows):
+    """Per stage with a model (stage CUDA-event timers over the timed region; each stage below is one kernel,
+    or one kernel and a small companion named in its note): algorithmic bytes or flops per job over the
+    stage's device time per job."""
     stages, st = r["stages"], r["stats"]
-    mixed = r["precision"] >= 1
-    dom = max(stages, key=lambda k: stages[k][0])
-    dom_ms, dom_launch = stages[dom]
-    inv = {"solve": M, "cross_apply": M, "synth_fwd": M - 1, "restrict": M}.get(dom, 1)
-    ms = dom_ms / inv
+    o = problem["options"]
+    M, Q = o["M"], o["Q"]
+    prec = r["precision"]
     sum_n2 = st["solve_flops"] / (8.0 * Q * M)
-    base = {"kernel": None, "ms_per_launch": ms, "launches_per_invocation": dom_launch / inv, "stage": dom}
+    passes = st["refine_passes"]
     tpu = measured_traffic_per_unit()
-    if dom == "cross_apply" and stored_rows:
-        name = "k_cross_rows_df" if mixed else "k_cross_apply"
-        by = 16.0 * st["cross_entries"]
-        ach = by / (ms * 1e-3) / 1e9
-        return dict(base, bound="hbm", achieved=ach, peak=HBM_PEAK_GBS, unit="GB/s", frac=ach / HBM_PEAK_GBS,
-                    traffic=tpu[name] * st["cross_entries"] if name in tpu else None, kernel=name,
-                    algorithmic_bytes_per_launch=by,
-                    note=f"peak: measured copy bandwidth ({PEAK_NOTE}); every stored cross entry read once per step")
-    if dom == "solve" and mixed:
-        by = 24.0 * sum_n2
-        ach = by / (ms * 1e-3) / 1e9
-        return dict(base, bound="hbm", achieved=ach, peak=HBM_PEAK_GBS, unit="GB/s", frac=ach / HBM_PEAK_GBS,
-                    traffic=None, kernel="k_msolve+k_mresid", algorithmic_bytes_per_launch=by,
-                    note=f"peak: measured copy bandwidth ({PEAK_NOTE}); FP32 factor and kept matrix read once per step")
-    if dom == "lu" and mixed and st.get("lu_tensor_systems", 0) > 0:
-        fl = st["lu_flops"]
-        ach = fl / (ms * 1e-3) / 1e12
-        return dict(base, bound="tensor", achieved=ach, peak=TF32_PEAK_TFLOPS, unit="TFLOP/s",
-                    frac=ach / TF32_PEAK_TFLOPS, traffic=None, kernel="k_lu_big_update+k_lu_big_panel",
-                    algorithmic_flops_per_launch=fl,
-                    note=f"(8/3) sum N^3 complex-LU flops over the LU stage; peak: TF32 dense = measured bf16 "
-                         f"sustained x 1.1/2.25 ({PEAK_NOTE}); the 3xTF32 split does 3 tensor products per flop")
-    fp64 = {"cross_assemble": FLOPS_PER_KERNEL_ENTRY * st["cross_entries"],
-            "assemble_self": FLOPS_PER_KERNEL_ENTRY * (st["hankel_evals"] - st["cross_entries"]),
-            "lu": st["lu_flops"], "solve": st["solve_flops"] / M, "cross_apply": st["apply_flops"] / M}
-    if dom in fp64:
-        ach = fp64[dom] / (ms * 1e-3) / 1e9
-        return dict(base, bound="alu", achieved=ach, peak=FP64_PEAK_GFLOPS, unit="GFLOP/s",
-                    frac=ach / FP64_PEAK_GFLOPS, traffic=None, kernel=dom, algorithmic_flops_per_launch=fp64[dom],
-                    note="FP64 pipe peak derived from the unit counts and clock: 152 SMs x 4 flop/clk x 2.07 GHz")
-    return dict(base, bound="alu", achieved=None, peak=FP64_PEAK_GFLOPS, unit="GFLOP/s", frac=None, traffic=None,
-                note="no roofline model for this stage")
+    out = {}
+
+    def add(stage, kernel, bound, amount, peak, unit, note, traffic=None):
+        ms, launches = stages.get(stage, (0.0, 0))
+        if ms <= 0 or amount <= 0:
+            return
+        ach = amount / (ms * 1e-3) / (1e12 if unit == "TFLOP/s" else 1e9)
+        out[stage] = {"kernel": kernel, "bound": bound, "achieved": ach, "peak": peak, "unit": unit,
+                      "frac": ach / peak, "traffic": traffic, "ms_per_job": ms, "launches_per_job": launches,
+                      "ms_per_launch": ms / max(launches, 1),
+                      ("algorithmic_flops_per_launch" if unit.endswith("FLOP/s") else "algorithmic_bytes_per_launch"):
+                          amount / max(launches, 1),
+                      "note": note}
+
+    hbm = f"peak: measured copy bandwidth ({PEAK_NOTE})"
+    fp64 = "peak: FP64 pipe derived from the unit counts and clock: 152 SMs x 4 flop/clk x 2.07 GHz"
+    if stored_rows:
+        name = "k_cross_rows_df" if prec >= 1 else "k_cross_apply"
+        by = 16.0 * st["cross_entries"] * M
+        tr = tpu[name] * st["cross_entries"] * M if name in tpu else None
+        add("cross_apply", name, "hbm", by, HBM_PEAK_GBS, "GB/s",
+            f"every stored cross entry (16 B) read once per step{', then an ordered per-group reduce (~1% of the stage)' if prec else ''}; {hbm}",
+            traffic=tr)
+    if prec >= 1:
+        add("solve", "k_msolve", "hbm", 8.0 * sum_n2 * M * (1.0 + passes), HBM_PEAK_GBS, "GB/s",
+            f"the FP32 factor (8 B per entry) read once per solve pass, 1 + {passes:.3f} passes per system and step; {hbm}")
+        if prec == 2:
+            add("resid", "k_mresid64", "alu", 8.0 * Q * sum_n2 * M, FP64_PEAK_GFLOPS, "GFLOP/s",
+                f"first-pass residual in FP64: 8 flops per complex multiply-add per window; {fp64}")
+            add("resid_upd", "k_mresid_upd", "hbm", 16.0 * sum_n2 * M * max(passes - 1.0, 0.0), HBM_PEAK_GBS,
+                "GB/s", f"later-pass residual updates: the FP64 matrix (16 B per entry) read once per pass, "
+                        f"{max(passes - 1.0, 0.0):.3f} passes per system and step; {hbm}")
+        else:
+            add("resid", "k_mresid", "hbm", 16.0 * sum_n2 * M, HBM_PEAK_GBS, "GB/s",
+                f"first-pass double-float residual: the kept matrix (16 B per entry) read once; {hbm}")
+            add("resid_upd", "k_mresid", "hbm", 16.0 * sum_n2 * M * max(passes - 1.0, 0.0), HBM_PEAK_GBS, "GB/s",
+                f"later-pass residuals: the kept matrix read once per pass; {hbm}")
+        if st.get("lu_tensor_systems", 0) > 0:
+            add("lu_update", "k_lu_big_update", "tensor", lu_update_flops(problem, st["lu_tensor_systems"]),
+                TF32_PEAK_TFLOPS, "TFLOP/s",
+                f"tcgen05 kind::tf32 trailing updates, 3 TF32 products per FP32 product (8 x 32 x T^2 real flops "
+                f"per panel); peak: TF32 dense = measured bf16 sustained x 1.1/2.25 ({PEAK_NOTE})")
+    else:
+        add("solve", "k_solve", "alu", st["solve_flops"], FP64_PEAK_GFLOPS, "GFLOP/s", fp64)
+        add("lu", "k_lu<double2>", "alu", st["lu_flops"], FP64_PEAK_GFLOPS, "GFLOP/s", "(8/3) sum N^3; " + fp64)
+        if stored_rows:
+            add("cross_assemble", "k_cross_assemble", "alu", FLOPS_PER_KERNEL_ENTRY * st["cross_entries"],
+                FP64_PEAK_GFLOPS, "GFLOP/s", "34-flop model of one far-field Hankel step per entry; " + fp64)
+    return out
+
+
+def roofline_of(r, problem, stored_rows):
+    """The dominant stage's roofline (largest device time per job among the stage timers)."""
+    stages = r["stages"]
+    dom = max(stages, key=lambda k: stages[k][0])
+    rl = stage_rooflines(r, problem, stored_rows)
+    if dom in rl:
+        return dict(rl[dom], stage=dom)
+    return {"stage": dom, "kernel": None, "bound": "alu", "achieved": None, "peak": FP64_PEAK_GFLOPS,
+            "unit": "GFLOP/s", "frac": None, "traffic": None, "note": "no roofline model for this stage"}
 
 
 def served_vs_plain(F, ctx, n=48, seed=11, max_inflight=4, precision=1):
@@ -512,7 +548,8 @@ def ours(args):
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(1000.0 * (time.perf_counter() - t0) / e2e_steps)
 
-    roof = roofline_of(head, M, Q, stored_rows) if head.get("stages") else None
+    roof = roofline_of(head, problem, stored_rows) if head.get("stages") else None
+    stage_roofs = stage_rooflines(head, problem, stored_rows) if head.get("stages") else None
 
     def summary(r, with_stages=True):
         if r is None:
@@ -588,6 +625,7 @@ def ours(args):
                                 "form's shapes passed in fthms_options.shapes"},
                 "gpu_launches": int(head["stats"]["kernel_launches"] * args.steps),
                 "roofline": roof,
+                "stage_rooflines": stage_roofs,
                 "stages_ms_per_step": {k: v[0] for k, v in head["stages"].items()} if head.get("stages") else None,
                 "clocks": head["clocks"],
                 "cpu_baseline": cpu,

@@ -277,15 +277,18 @@ fthms_status fthms_result_errors(fthms_req* req, double* out, size_t cap);
 enum {
   FTHMS_STAGE_TABLES = 0,      /* FFT twiddles, recentring phases, log and restriction tables */
   FTHMS_STAGE_ASSEMBLE = 1,    /* self matrices (eq. FDBIEk-interior, log-split rule) */
-  FTHMS_STAGE_LU = 2,          /* LU factorisation of every (arc, omega) matrix */
+  FTHMS_STAGE_LU = 2,          /* LU factorisation of every (arc, omega) matrix (large systems: the panels) */
   FTHMS_STAGE_CROSS_ASM = 3,   /* stored cross-arc single-layer rows (eq. FDsolk-interior) */
   FTHMS_STAGE_INCIDENT = 4,    /* g_{k,1} and its slow transform (eqs. criterion_int1, Fourierk) */
   FTHMS_STAGE_RESTRICT = 5,    /* transfer mesh -> solve nodes */
-  FTHMS_STAGE_SOLVE = 6,       /* triangular solves (Algorithm 1, BIE solve) */
+  FTHMS_STAGE_SOLVE = 6,       /* triangular solves (Algorithm 1, BIE solve; mixed forms: every pass's) */
   FTHMS_STAGE_CROSS_APPLY = 7, /* cross-arc and observation potentials */
   FTHMS_STAGE_SYNTH_FWD = 8,   /* eq. TDsol, eq. criterion_int2, eq. Fourierk */
   FTHMS_STAGE_TRACES = 9,      /* eq. mult-scatt-int at the output times */
-  FTHMS_NSTAGES = 10
+  FTHMS_STAGE_RESID = 10,      /* mixed forms: refinement residuals G - A phi of the first pass */
+  FTHMS_STAGE_RESID_UPD = 11,  /* mixed forms: residuals of later passes (updated with the last correction) */
+  FTHMS_STAGE_LU_UPDATE = 12,  /* mixed forms: tensor-core trailing updates of the large-system LU */
+  FTHMS_NSTAGES = 13
 };
 
 /* Pick launch shapes and the LU path for this job's hardware and sizes: runs the job once, then times

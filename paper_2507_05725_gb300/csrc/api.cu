@@ -457,7 +457,14 @@ fthms_status enqueue_stages(fthms_req* r, bool bracket) {
   if (J.mrho) CK(cudaMemsetAsync(J.mrho, 0, r->plan.sys.size() * sizeof(float), st));   // measured per run
   TRY(stage(r, FTHMS_STAGE_TABLES, st, &nl, [&] { return launch_tables(J, st, &nl); }));
   TRY(stage(r, FTHMS_STAGE_ASSEMBLE, st, &nl, [&] { return launch_assemble_self(J, st, &nl); }));
-  TRY(stage(r, FTHMS_STAGE_LU, st, &nl, [&] { return launch_lu(J, st, &nl); }));
+  TRY(stage(r, FTHMS_STAGE_LU, st, &nl, [&] { return launch_lu_small(J, st, &nl); }));
+  if (J.mixed) {              // large systems: panels (LU stage) and tensor-core trailing updates, in turn
+    for (int k = 0; k < lu_big_panels(J); ++k) {
+      TRY(stage(r, FTHMS_STAGE_LU, st, &nl, [&] { return launch_lu_big_panel(J, k, st, &nl); }));
+      TRY(stage(r, FTHMS_STAGE_LU_UPDATE, st, &nl, [&] { return launch_lu_big_update(J, k, st, &nl); }));
+    }
+    TRY(stage(r, FTHMS_STAGE_LU, st, &nl, [&] { return launch_lu_big_finish(J, st, &nl); }));
+  }
   TRY(stage(r, FTHMS_STAGE_CROSS_ASM, st, &nl, [&] {
     return J.otf ? launch_near_weights(J, st, &nl) : launch_cross_assemble(J, st, &nl);
   }));
@@ -467,7 +474,16 @@ fthms_status enqueue_stages(fthms_req* r, bool bracket) {
   TRY(stage(r, FTHMS_STAGE_INCIDENT, st, &nl, [&] { return launch_incident(J, st, &nl); }));
   TRY(stage(r, FTHMS_STAGE_RESTRICT, st, &nl, [&] { return launch_restrict(J, st, &nl); }));
   for (int m = 1; m <= J.M; ++m) {
-    TRY(stage(r, FTHMS_STAGE_SOLVE, st, &nl, [&] { return launch_solve(J, m, st, &nl); }));
+    if (J.mixed) {            // the FP32 solve, then refinement passes (residuals, correction solves)
+      TRY(stage(r, FTHMS_STAGE_SOLVE, st, &nl, [&] { return launch_msolve(J, m, 0, st, &nl); }));
+      for (int pass = 1; pass <= refine_passes(J); ++pass) {
+        TRY(stage(r, pass == 1 ? FTHMS_STAGE_RESID : FTHMS_STAGE_RESID_UPD, st, &nl,
+                  [&] { return launch_resid(J, pass, st, &nl); }));
+        TRY(stage(r, FTHMS_STAGE_SOLVE, st, &nl, [&] { return launch_msolve(J, m, pass, st, &nl); }));
+      }
+    } else {
+      TRY(stage(r, FTHMS_STAGE_SOLVE, st, &nl, [&] { return launch_solve(J, m, st, &nl); }));
+    }
     TRY(stage(r, FTHMS_STAGE_CROSS_APPLY, st, &nl, [&] {
       return J.otf ? launch_cross_otf(J, st, &nl) : launch_cross_apply(J, st, &nl);
     }));

@@ -2178,6 +2178,12 @@ cudaError_t launch_assemble_self(const DevJob& J, cudaStream_t st, int* launches
 }
 
 cudaError_t launch_lu(const DevJob& J, cudaStream_t st, int* launches) {
+  cudaError_t e = launch_lu_small(J, st, launches);
+  if (e != cudaSuccess || !J.mixed) return e;
+  return launch_lu_large(J, st, launches);
+}
+
+cudaError_t launch_lu_small(const DevJob& J, cudaStream_t st, int* launches) {
   if (J.mixed) {
     // k_assemble_self already wrote the FP32 matrix and the double-float pairs (or FP64 values)
     if (J.n_lu_small > 0) {
@@ -2188,10 +2194,9 @@ cudaError_t launch_lu(const DevJob& J, cudaStream_t st, int* launches) {
       if (e != cudaSuccess) return e;
       k_lu<float2><<<J.n_lu_small, kLuThreads, sh, st>>>(J);
       *launches += 1;
-      e = cudaGetLastError();
-      if (e != cudaSuccess) return e;
+      return cudaGetLastError();
     }
-    return launch_lu_large(J, st, launches);
+    return cudaSuccess;
   }
   if (J.n_lu_small == 0) return cudaSuccess;
   size_t sh = std::max((size_t)J.max_n * (kNB + kPS), (size_t)2 * kSB * kSB) * sizeof(double2);
@@ -2280,29 +2285,48 @@ static int solve_warps(size_t bytes_per_warp, int wanted) {
   return nw;
 }
 
+int refine_passes(const DevJob& J) {
+  return J.mixed && J.n_rchunks > 0 ? std::min(std::max(J.refine_max, 1), kRefineCap) : 0;
+}
+
+// Mixed forms: the triangular solves of refinement pass `pass` (0: the FP32 solution) for every system
+// still refining.
+template <int QT>
+static cudaError_t launch_msolve_q(const DevJob& J, int m, int pass, cudaStream_t st, int* launches) {
+  const size_t per = (size_t)QT * J.max_n * sizeof(float2);
+  const int nw = solve_warps(per, J.shape_solve);
+  const size_t sh = (size_t)nw * per;
+  cudaError_t e = cudaFuncSetAttribute(k_msolve<QT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+  if (e != cudaSuccess) return e;
+  k_msolve<QT><<<cdiv(J.nsys, nw), 32 * nw, sh, st>>>(J, m, pass);
+  *launches += 1;
+  return cudaGetLastError();
+}
+
+// Mixed forms: the residuals before refinement pass `pass` >= 1: FP64 for the systems that keep FP64 at
+// the first pass, updated with the last correction at later ones (reading of the FP64 residual), double-float
+// for the others.
+template <int QT>
+static cudaError_t launch_resid_q(const DevJob& J, int pass, cudaStream_t st, int* launches) {
+  const int rgrid = cdiv(J.n_rchunks, kResidThreads / 32);
+  if (rgrid == 0) return cudaSuccess;
+  const bool any64 = J.fp64keep || J.max_n >= J.f64_min_n, anydf = !J.fp64keep;
+  if (any64 && pass == 1) k_mresid64<QT><<<rgrid, kResidThreads, 0, st>>>(J);
+  else if (any64) k_mresid_upd<QT><<<rgrid, kResidThreads, 0, st>>>(J);
+  if (anydf) k_mresid<QT><<<rgrid, kResidThreads, 0, st>>>(J);
+  *launches += (int)any64 + (int)anydf;
+  return cudaGetLastError();
+}
+
 template <int QT>
 static cudaError_t launch_solve_q(const DevJob& J, int m, cudaStream_t st, int* launches) {
   if (J.mixed) {
-    const size_t per = (size_t)QT * J.max_n * sizeof(float2);
-    const int nw = solve_warps(per, J.shape_solve);
-    const size_t sh = (size_t)nw * per;
-    cudaError_t e = cudaFuncSetAttribute(k_msolve<QT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
-    if (e != cudaSuccess) return e;
-    const int grid = cdiv(J.nsys, nw), rgrid = cdiv(J.n_rchunks, kResidThreads / 32);
-    const int passes = std::min(std::max(J.refine_max, 1), kRefineCap);
-    k_msolve<QT><<<grid, 32 * nw, sh, st>>>(J, m, 0);
-    for (int pass = 1; pass <= passes && rgrid > 0; ++pass) {
-      // FP64 residuals for the systems that keep FP64 (all in the FP64-kept form), double-float for the rest
-      const bool any64 = J.fp64keep || J.max_n >= J.f64_min_n, anydf = !J.fp64keep;
-      // (the first pass forms G - A phi in FP64; later passes update that residual with the correction)
-      if (any64 && pass == 1) k_mresid64<QT><<<rgrid, kResidThreads, 0, st>>>(J);
-      else if (any64) k_mresid_upd<QT><<<rgrid, kResidThreads, 0, st>>>(J);
-      if (anydf) k_mresid<QT><<<rgrid, kResidThreads, 0, st>>>(J);
-      *launches += (int)any64 + (int)anydf - 1;
-      k_msolve<QT><<<grid, 32 * nw, sh, st>>>(J, m, pass);
+    cudaError_t e = launch_msolve_q<QT>(J, m, 0, st, launches);
+    for (int pass = 1; pass <= refine_passes(J) && e == cudaSuccess; ++pass) {
+      e = launch_resid_q<QT>(J, pass, st, launches);
+      if (e == cudaSuccess) e = launch_msolve_q<QT>(J, m, pass, st, launches);
     }
-    *launches += 1 + 2 * passes;
-    return cudaGetLastError();
+    return e;
   }
   const size_t per = (size_t)QT * J.max_n * sizeof(double2);
   const int nw = solve_warps(per, J.shape_solve);
@@ -2320,6 +2344,24 @@ cudaError_t launch_solve(const DevJob& J, int m, cudaStream_t st, int* launches)
     case 2: return launch_solve_q<2>(J, m, st, launches);
     case 3: return launch_solve_q<3>(J, m, st, launches);
     default: return launch_solve_q<4>(J, m, st, launches);
+  }
+}
+
+cudaError_t launch_msolve(const DevJob& J, int m, int pass, cudaStream_t st, int* launches) {
+  switch (J.Q) {
+    case 1: return launch_msolve_q<1>(J, m, pass, st, launches);
+    case 2: return launch_msolve_q<2>(J, m, pass, st, launches);
+    case 3: return launch_msolve_q<3>(J, m, pass, st, launches);
+    default: return launch_msolve_q<4>(J, m, pass, st, launches);
+  }
+}
+
+cudaError_t launch_resid(const DevJob& J, int pass, cudaStream_t st, int* launches) {
+  switch (J.Q) {
+    case 1: return launch_resid_q<1>(J, pass, st, launches);
+    case 2: return launch_resid_q<2>(J, pass, st, launches);
+    case 3: return launch_resid_q<3>(J, pass, st, launches);
+    default: return launch_resid_q<4>(J, pass, st, launches);
   }
 }
 

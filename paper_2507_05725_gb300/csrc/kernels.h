@@ -121,13 +121,25 @@ cudaError_t launch_tables(const DevJob& J, cudaStream_t st, int* launches);
 cudaError_t launch_tables_rlog_only(const DevJob& J, cudaStream_t st, int* launches);
 cudaError_t launch_assemble_self(const DevJob& J, cudaStream_t st, int* launches);
 cudaError_t launch_lu(const DevJob& J, cudaStream_t st, int* launches);
-// Mixed forms, systems with N >= kLuBigMin: blocked LU with tcgen05 trailing updates (lu_large.cu).
+// The one-CTA LU of the systems below the tensor-core split (all systems in the FP64 form).
+cudaError_t launch_lu_small(const DevJob& J, cudaStream_t st, int* launches);
+// Mixed forms, systems above the split: blocked LU with tcgen05 trailing updates (lu_large.cu), as one
+// sequence or panel by panel (panel k: columns 32k .. 32k+31, then the trailing update; then the finish).
 cudaError_t launch_lu_large(const DevJob& J, cudaStream_t st, int* launches);
+int lu_big_panels(const DevJob& J);
+cudaError_t launch_lu_big_panel(const DevJob& J, int panel, cudaStream_t st, int* launches);
+cudaError_t launch_lu_big_update(const DevJob& J, int panel, cudaStream_t st, int* launches);
+cudaError_t launch_lu_big_finish(const DevJob& J, cudaStream_t st, int* launches);
 size_t lu_big_panel_smem(int maxN);
 cudaError_t launch_cross_assemble(const DevJob& J, cudaStream_t st, int* launches);
 cudaError_t launch_incident(const DevJob& J, cudaStream_t st, int* launches);
 cudaError_t launch_restrict(const DevJob& J, cudaStream_t st, int* launches);
 cudaError_t launch_solve(const DevJob& J, int m, cudaStream_t st, int* launches);
+// Mixed forms, the same step piece by piece: launch_msolve(pass 0), then for pass = 1 .. refine_passes(J)
+// launch_resid(pass) and launch_msolve(pass).
+int refine_passes(const DevJob& J);
+cudaError_t launch_msolve(const DevJob& J, int m, int pass, cudaStream_t st, int* launches);
+cudaError_t launch_resid(const DevJob& J, int pass, cudaStream_t st, int* launches);
 cudaError_t launch_cross_apply(const DevJob& J, cudaStream_t st, int* launches);
 cudaError_t launch_near_weights(const DevJob& J, cudaStream_t st, int* launches);
 cudaError_t launch_cross_otf(const DevJob& J, cudaStream_t st, int* launches);

@@ -303,30 +303,51 @@ size_t lu_big_panel_smem(int maxN) {
   return (pn > segs ? pn : segs) * sizeof(float2);
 }
 
-cudaError_t launch_lu_large(const DevJob& J, cudaStream_t st, int* launches) {
-  if (J.n_lu_big == 0) return cudaSuccess;
+// Kernel attributes of the large-system LU (once per launch sequence).
+static cudaError_t lu_big_attributes(const DevJob& J) {
   const size_t sh_p = lu_big_panel_smem(J.big_max_n);
   cudaError_t e = cudaFuncSetAttribute(k_lu_big_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh_p);
   if (e != cudaSuccess) return e;
   // the largest shared-memory carveout, so that two panel CTAs (128 registers a thread) share an SM
   e = cudaFuncSetAttribute(k_lu_big_panel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e != cudaSuccess) return e;
-  const size_t sh_u = (size_t)8 * kPartBytes;
-  e = cudaFuncSetAttribute(k_lu_big_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh_u);
+  return cudaFuncSetAttribute(k_lu_big_update, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * kPartBytes);
+}
+
+int lu_big_panels(const DevJob& J) { return J.n_lu_big > 0 ? (J.big_max_n + kOuter - 1) / kOuter : 0; }
+
+cudaError_t launch_lu_big_panel(const DevJob& J, int panel, cudaStream_t st, int* launches) {
+  if (J.n_lu_big == 0) return cudaSuccess;
+  cudaError_t e = panel == 0 ? lu_big_attributes(J) : cudaSuccess;
   if (e != cudaSuccess) return e;
-  for (int k0 = 0; k0 < J.big_max_n; k0 += kOuter) {
-    k_lu_big_panel<<<J.n_lu_big, kPanelThreads, sh_p, st>>>(J, k0);
-    const int T = J.big_max_n - k0 - kOuter;
-    *launches += 1;
-    if (T > 0) {
-      const int tm = (T + kTile - 1) / kTile;
-      k_lu_big_update<<<dim3(J.n_lu_big, tm * tm), kUpdThreads, sh_u, st>>>(J, k0);
-      *launches += 1;
-    }
-  }
+  k_lu_big_panel<<<J.n_lu_big, kPanelThreads, lu_big_panel_smem(J.big_max_n), st>>>(J, panel * kOuter);
+  *launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lu_big_update(const DevJob& J, int panel, cudaStream_t st, int* launches) {
+  const int k0 = panel * kOuter, T = J.big_max_n - k0 - kOuter;
+  if (J.n_lu_big == 0 || T <= 0) return cudaSuccess;
+  const int tm = (T + kTile - 1) / kTile;
+  k_lu_big_update<<<dim3(J.n_lu_big, tm * tm), kUpdThreads, 8 * kPartBytes, st>>>(J, k0);
+  *launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lu_big_finish(const DevJob& J, cudaStream_t st, int* launches) {
+  if (J.n_lu_big == 0) return cudaSuccess;
   k_lu_big_finish<<<J.n_lu_big, kLuThreadsFinish, 0, st>>>(J);
   *launches += 1;
   return cudaGetLastError();
+}
+
+cudaError_t launch_lu_large(const DevJob& J, cudaStream_t st, int* launches) {
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < lu_big_panels(J) && e == cudaSuccess; ++k) {
+    e = launch_lu_big_panel(J, k, st, launches);
+    if (e == cudaSuccess) e = launch_lu_big_update(J, k, st, launches);
+  }
+  return e == cudaSuccess ? launch_lu_big_finish(J, st, launches) : e;
 }
 
 }  // namespace fthms

@@ -64,7 +64,7 @@ class fthms_stats_t(C.Structure):
 ALLREDUCE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 
 STAGES = ["tables", "assemble_self", "lu", "cross_assemble", "incident", "restrict", "solve", "cross_apply",
-          "synth_fwd", "traces"]
+          "synth_fwd", "traces", "resid", "resid_upd", "lu_update"]
 
 
 def _load():

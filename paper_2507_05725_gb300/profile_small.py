@@ -1,6 +1,6 @@
 """Small jobs for ncu captures.  Prints each job's statistics as one JSON line.
 
-  python -m paper_2507_05725_gb300.profile_small [c2|c4|c4s|c4-launches]
+  python -m paper_2507_05725_gb300.profile_small [c2|c4|c4s|c4r|c4-launches]
 
 c2: the 4-obstacle configuration's geometry, signal and node rule on 512 frequencies of [0, 30] with M = 4
     (about 1.8 GB on the device, cross matrices 1.4 GB, above L2), in the plain FP64 and the mixed form.
@@ -12,6 +12,8 @@ c4s: the mixed-precision configuration at N = 512 on 128 frequencies of the same
     50), M = 2, cross rows evaluated every step, in the FP64-kept form with the bench's tuned shapes
     (tensor-core LU at N = 512): 768 systems, about 5 GB on the device; the launches of interest are k_lu_big_update, k_lu_big_panel,
     k_msolve, k_mresid64 and k_cross_otf_df.
+c4r: the same at N = 512 on 16 frequencies (omega up to 6.3), M = 2, stored cross rows (1.75 GB of them, far
+    above L2), FP64-kept form with the tuned shapes: the launch of interest is k_cross_rows_df.
 c4-launches: one full-size job of the mixed-precision configuration at N = 512 (1023 frequencies, M = 8,
     the bench's headline workload) in the FP64-kept form with the bench's tuned shapes and the tensor-core
     LU, for a launch list.
@@ -33,6 +35,8 @@ def main():
         runs = [(wl.config2(L=513, W=30.0, M=4), 0), (wl.config2(L=513, W=30.0, M=4), 1)]
     elif which == "c4":
         runs = [(wl.config4(1024, L=65, W=400.0 * 64 / 1023, M=2), 2)]
+    elif which == "c4r":
+        runs = [(wl.config4(512, L=17, W=400.0 * 16 / 1023, M=2), 2)]
     elif which == "c4s":
         p = wl.config4(512, L=129, W=400.0 * 128 / 1023, M=2)
         p["options"]["cross_mode"] = 1
