@@ -199,18 +199,19 @@ def solves_of(problem):
     return len(problem["arcs"]) * (o["L"] - 1) * o["M"] * o["Q"]
 
 
-def cpu_sample_problem(name="c4"):
+def cpu_sample_problem(name="c4", n_freq=16):
     """Bounded sample of the headline workload for the CPU oracle: the same 6 arcs, N = 512, signal and
-    8 steps x 2 windows on 4 solved frequencies (h = 0.75, so that the windows fit one period)."""
+    8 steps x 2 windows on n_freq solved frequencies (spacing h = 0.75, so that the windows fit one period):
+    about 14 s of CPU time at 16 frequencies (the cpu_baseline), 7 s at 8 (one step of the reference arm)."""
     import workloads
     if name == "c4":
-        return workloads.config4(512, L=5, W=3.0, n_period=256)
+        return workloads.config4(512, L=n_freq + 1, W=0.75 * n_freq, n_period=256)
     return workloads.config2(L=65, W=30.0, H=6.0, M=12, n_period=512, T=6.0)
 
 
-def run_oracle_sample(name="c4"):
+def run_oracle_sample(name="c4", n_freq=16):
     from oracle import run_oracle
-    p = cpu_sample_problem(name)
+    p = cpu_sample_problem(name, n_freq)
     t0 = time.perf_counter()
     run_oracle(p, arcs_phi=[])
     return solves_of(p), time.perf_counter() - t0
@@ -230,14 +231,14 @@ def reference_arm(args):
     if rank != 0:
         return 0
     for _ in range(args.warmup):
-        run_oracle_sample(args.workload)
+        run_oracle_sample(args.workload, 8)
     times, solves = [], 0
     for _ in range(args.steps):
-        s, dt = run_oracle_sample(args.workload)
+        s, dt = run_oracle_sample(args.workload, 8)
         solves, times = s, times + [dt]
     ms = 1000.0 * statistics.mean(times)
     value = solves / (ms / 1000.0)
-    p = cpu_sample_problem(args.workload)
+    p = cpu_sample_problem(args.workload, 8)
     o = p["options"]
     sample = (f"oracle (numpy/scipy FP64) on {len(p['arcs'])} arcs x {o['L'] - 1} frequencies x {o['M']} steps x "
               f"{o['Q']} windows ({solves} solves) per step, same geometry, N, signal and steps as the bench workload")
