@@ -1447,23 +1447,31 @@ __global__ void __launch_bounds__(kResidThreads) k_mresid_upd(DevJob J) {
     re[q].add(rd.x, rd.y);
     im[q].add(rd.z, rd.w);
   }
-  constexpr int kUnroll = Q == 1 ? 8 : Q == 2 ? 4 : 2;
-#pragma unroll kUnroll
-  for (int j = 0; j < N; ++j) {
-    const double2 a = __ldg(&A64[(long long)j * N + row]);
+  // r -= a d:  Re -= ar dr - ai di,  Im -= ar di + ai dr; kB matrix entries of the row loaded before their sums
+  constexpr int kB = Q <= 2 ? 8 : 4;
+  auto step = [&](const double2 a, int j) {
     float arh, arl, aih, ail;
     split_f64_bits(a.x, arh, arl);
     split_f64_bits(a.y, aih, ail);
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
       const float2 dv = d[q * N + j];
-      // r -= a d:  Re -= ar dr - ai di,  Im -= ar di + ai dr
       dfacc_mac1(re[q], -arh, -arl, dv.x);
       dfacc_mac1(re[q], aih, ail, dv.y);
       dfacc_mac1(im[q], -arh, -arl, dv.y);
       dfacc_mac1(im[q], -aih, -ail, dv.x);
     }
+  };
+  int j0 = 0;
+#pragma unroll 1
+  for (; j0 + kB <= N; j0 += kB) {
+    double2 a[kB];
+#pragma unroll
+    for (int k = 0; k < kB; ++k) a[k] = __ldg(&A64[(long long)(j0 + k) * N + row]);
+#pragma unroll
+    for (int k = 0; k < kB; ++k) step(a[k], j0 + k);
   }
+  for (; j0 < N; ++j0) step(__ldg(&A64[(long long)j0 * N + row]), j0);
   if (i < N) {
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
@@ -1659,54 +1667,51 @@ __global__ void __launch_bounds__(32 * kSolveWarps, 3) k_msolve(DevJob J, int m,
 // barrier after the density staging, and many small CTAs per SM keep enough loads in flight.
 template <int Q>
 __global__ void __launch_bounds__(kApplySlice, 3) k_cross_rows_df(DevJob J) {
-  extern __shared__ __align__(16) unsigned char shd_raw[];
-  float4* ph = reinterpret_cast<float4*>(shd_raw);        // df64 densities of the overlapped blocks
   const ApplySlice sl = J.slices[blockIdx.x];
-  const int nb = sl.b1 - sl.b0 + 1;
-  __shared__ int s_row0[kApplyMaxBlk + 1], s_ph0[kApplyMaxBlk + 1];
-  if (threadIdx.x == 0) {
-    int r = sl.rowb0, p = 0;
-    for (int b = 0; b < nb; ++b) {
-      s_row0[b] = r;
-      s_ph0[b] = p;
-      r += J.blks[sl.b0 + b].nrows;
-      p += Q * J.blks[sl.b0 + b].N;
-    }
-    s_row0[nb] = r;
-    s_ph0[nb] = p;
-  }
-  __syncthreads();
-  for (int b = 0; b < nb; ++b) {
-    const CrossBlk B = J.blks[sl.b0 + b];
-    const float4* p = J.phi_df + J.sys[B.sys].vec_off;
-    for (int e = threadIdx.x; e < Q * B.N; e += kApplySlice) ph[s_ph0[b] + e] = p[e];
-  }
-  __syncthreads();
   if ((int)threadIdx.x >= sl.nrows) return;
   const int row = sl.row0 + threadIdx.x;
-  int b = 0;
-  while (row >= s_row0[b + 1]) ++b;
-  const CrossBlk B = J.blks[sl.b0 + b];
-  const int N = B.N, nr = B.nrows, r = row - s_row0[b];
-  const float4* phb = ph + s_ph0[b];
+  // the thread's source block: the slice's blocks hold consecutive rows of the group
+  int b = sl.b0, r = row - sl.rowb0;
+  while (r >= J.blks[b].nrows) {
+    r -= J.blks[b].nrows;
+    ++b;
+  }
+  const CrossBlk B = J.blks[b];
+  const int N = B.N, nr = B.nrows;
+  // the block's double-float densities, the same for every row: one cached load per warp and column
+  const float4* __restrict__ phb = J.phi_df + J.sys[B.sys].vec_off;
   dfacc sr[Q], si[Q], tr[Q], ti[Q];
   const float4* __restrict__ Er = reinterpret_cast<const float4*>(J.E + B.e_off) + r;
   int i = 0;
-  constexpr int kUnroll = Q <= 2 ? 4 : 2;   // independent loads in flight without spilling
-#pragma unroll kUnroll
+  // kB entries of the row loaded before their sums (two alternating accumulator sets)
+  constexpr int kB = Q == 1 ? 8 : Q == 2 ? 6 : 4;
+#pragma unroll 1
+  for (; i + kB <= N; i += kB) {
+    float4 e[kB];
+#pragma unroll
+    for (int k = 0; k < kB; ++k) e[k] = __ldg(&Er[(long long)(i + k) * nr]);
+#pragma unroll
+    for (int k = 0; k < kB; k += 2) {
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        cdf_mac(sr[q], si[q], e[k], __ldg(&phb[q * N + i + k]));
+        cdf_mac(tr[q], ti[q], e[k + 1], __ldg(&phb[q * N + i + k + 1]));
+      }
+    }
+  }
   for (; i + 1 < N; i += 2) {
     const float4 e0 = __ldg(&Er[(long long)i * nr]);
     const float4 e1 = __ldg(&Er[(long long)(i + 1) * nr]);
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-      cdf_mac(sr[q], si[q], e0, phb[q * N + i]);
-      cdf_mac(tr[q], ti[q], e1, phb[q * N + i + 1]);
+      cdf_mac(sr[q], si[q], e0, __ldg(&phb[q * N + i]));
+      cdf_mac(tr[q], ti[q], e1, __ldg(&phb[q * N + i + 1]));
     }
   }
   if (i < N) {
     const float4 e0 = __ldg(&Er[(long long)i * nr]);
 #pragma unroll
-    for (int q = 0; q < Q; ++q) cdf_mac(sr[q], si[q], e0, phb[q * N + i]);
+    for (int q = 0; q < Q; ++q) cdf_mac(sr[q], si[q], e0, __ldg(&phb[q * N + i]));
   }
   double2* out = J.apply_res + (J.grp_res_off[sl.grp] + row) * Q;
 #pragma unroll
@@ -2368,7 +2373,7 @@ cudaError_t launch_resid(const DevJob& J, int pass, cudaStream_t st, int* launch
 template <int Q>
 static cudaError_t launch_cross_apply_q(const DevJob& J, size_t sh, cudaStream_t st) {
   if (J.mixed) {
-    const size_t sh_rows = (size_t)Q * J.slice_ph_cap * sizeof(float4);
+    const size_t sh_rows = 0;   // the row kernel reads the densities through the L1 cache
     const size_t sh_red = (size_t)Q * J.acc_cap * sizeof(double2);
     cudaError_t e = cudaFuncSetAttribute(k_cross_rows_df<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh_rows);
     if (e != cudaSuccess) return e;
