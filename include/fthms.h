@@ -288,7 +288,8 @@ enum {
   FTHMS_STAGE_RESID = 10,      /* mixed forms: refinement residuals G - A phi of the first pass */
   FTHMS_STAGE_RESID_UPD = 11,  /* mixed forms: residuals of later passes (updated with the last correction) */
   FTHMS_STAGE_LU_UPDATE = 12,  /* mixed forms: tensor-core trailing updates of the large-system LU */
-  FTHMS_NSTAGES = 13
+  FTHMS_STAGE_FUSED = 13,      /* FP64 form with fthms_use_fused: assembly + LU + step-1 solve in one launch */
+  FTHMS_NSTAGES = 14
 };
 
 /* Pick launch shapes and the LU path for this job's hardware and sizes: runs the job once, then times
@@ -320,6 +321,14 @@ fthms_status fthms_set_shapes(fthms_req* req, const int* shapes);
  * CUDA graph (fthms_use_graph is ignored). */
 typedef void (*fthms_allreduce_fn)(double* buf_dev, size_t count, void* cuda_stream, void* user);
 fthms_status fthms_set_allreduce(fthms_req* req, fthms_allreduce_fn fn, void* user);
+
+/* enable != 0 (FP64 form only; FTHMS_EINVAL for a mixed form): later runs assemble, factor and solve (step 1)
+ * every (arc, omega) system in one persistent launch -- each CTA takes the next system (largest N first) from a
+ * work counter and carries it through its self matrix (the same rule as the staged assembly, evaluated per
+ * system), its LU and its step-1 solve -- instead of three launches over all systems; the incident field and
+ * the restriction to the solve nodes run first.  Densities agree with the staged path to rounding (the
+ * assembly's operation order differs).  Algorithm 1 lines 7-9 per (arc, omega); not a paper form (batching). */
+fthms_status fthms_use_fused(fthms_req* req, int enable);
 
 /* enable != 0: fthms_run captures the job's whole pipeline (all stages and steps) into a CUDA graph on
  * its first run and replays it afterwards as one launch; the graph is rebuilt never (the job's inputs

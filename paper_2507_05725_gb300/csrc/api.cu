@@ -105,6 +105,7 @@ struct fthms_req {
   int launches = 0;
   double setup_ms = 0.0;
   bool use_graph = false;          // replay the captured pipeline instead of launching stage by stage
+  bool use_fused = false;          // FP64 form: assembly + LU + step-1 solve in one persistent launch
   cudaGraphExec_t graph = nullptr;
   bool conv_checked = false;       // the last run's refinement counters have been read
   fthms_status conv_status = FTHMS_OK;
@@ -248,6 +249,7 @@ fthms_status upload_job(fthms_req* r) {
   TRY(dev_upload(r, p.sys_order, &J.sys_order));
   set_lu_split(r, p.n_lu_big);
   TRY(dev_alloc(r, 1, &J.dev_err));
+  TRY(dev_alloc(r, 1, &J.work_counter));
   TRY(dev_upload(r, p.panels, &J.panels));
   TRY(dev_upload(r, p.node_t, &J.node_t));
   TRY(dev_upload(r, p.node_x, &J.node_x));
@@ -455,9 +457,12 @@ fthms_status enqueue_stages(fthms_req* r, bool bracket) {
   CK(cudaMemsetAsync(J.refine_resid, 0, 3 * sizeof(double), st));
   if (J.sys_err) CK(cudaMemsetAsync(J.sys_err, 0, r->plan.sys.size() * sizeof(float), st));
   if (J.mrho) CK(cudaMemsetAsync(J.mrho, 0, r->plan.sys.size() * sizeof(float), st));   // measured per run
+  const bool fused = r->use_fused && !J.mixed;   // assembly, LU and step-1 solve in the fused launch below
   TRY(stage(r, FTHMS_STAGE_TABLES, st, &nl, [&] { return launch_tables(J, st, &nl); }));
-  TRY(stage(r, FTHMS_STAGE_ASSEMBLE, st, &nl, [&] { return launch_assemble_self(J, st, &nl); }));
-  TRY(stage(r, FTHMS_STAGE_LU, st, &nl, [&] { return launch_lu_small(J, st, &nl); }));
+  if (!fused) {
+    TRY(stage(r, FTHMS_STAGE_ASSEMBLE, st, &nl, [&] { return launch_assemble_self(J, st, &nl); }));
+    TRY(stage(r, FTHMS_STAGE_LU, st, &nl, [&] { return launch_lu_small(J, st, &nl); }));
+  }
   if (J.mixed) {              // large systems: panels (LU stage) and tensor-core trailing updates, in turn
     for (int k = 0; k < lu_big_panels(J); ++k) {
       TRY(stage(r, FTHMS_STAGE_LU, st, &nl, [&] { return launch_lu_big_panel(J, k, st, &nl); }));
@@ -481,6 +486,8 @@ fthms_status enqueue_stages(fthms_req* r, bool bracket) {
                   [&] { return launch_resid(J, pass, st, &nl); }));
         TRY(stage(r, FTHMS_STAGE_SOLVE, st, &nl, [&] { return launch_msolve(J, m, pass, st, &nl); }));
       }
+    } else if (fused && m == 1) {
+      TRY(stage(r, FTHMS_STAGE_FUSED, st, &nl, [&] { return launch_fused_asf(J, J.work_counter, st, &nl); }));
     } else {
       TRY(stage(r, FTHMS_STAGE_SOLVE, st, &nl, [&] { return launch_solve(J, m, st, &nl); }));
     }
@@ -1023,6 +1030,19 @@ fthms_status fthms_set_shapes(fthms_req* req, const int* shapes) {
     req->graph = nullptr;
   }
   apply_shapes(req, shapes);
+  return FTHMS_OK;
+}
+
+fthms_status fthms_use_fused(fthms_req* req, int enable) {
+  if (!req) return fail(FTHMS_EINVAL, "fthms_use_fused: NULL job");
+  if (!req->ctx) return fail(FTHMS_EINVAL, "fthms_use_fused: the job's context was destroyed");
+  if (enable && req->plan.opt.precision != 0)
+    return fail(FTHMS_EINVAL, "fthms_use_fused: the fused kernel is the FP64 form's (precision 0)");
+  if (req->graph) {                    // a captured graph holds the other stage sequence
+    cudaGraphExecDestroy(req->graph);
+    req->graph = nullptr;
+  }
+  req->use_fused = enable != 0;
   return FTHMS_OK;
 }
 

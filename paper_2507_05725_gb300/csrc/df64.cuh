@@ -263,4 +263,50 @@ __device__ __forceinline__ void dfacc_mac1(dfacc& acc, float ah, float al, float
   acc.lo = __fadd_rn(acc.lo, __fadd_rn(t, e));
 }
 
+// a = a1 + a2 + a3 exactly for a double a with 2^-60 <= |a| < 2^100, by integer operations only: a1 = a truncated
+// to 24 significant bits, a2 = the next 24 bits, a3 = the last 5 (integers below 2^24 convert to float exactly,
+// then their exponents are shifted by that of a).  Outside that range (zero included; |a| below 2^128) by FP64
+// operations.
+__device__ __forceinline__ void split3_f64_bits(double a, float& a1, float& a2, float& a3) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(a);
+  const unsigned int uh = (unsigned int)(u >> 32), ul = (unsigned int)u;
+  const int e = (int)((uh >> 20) & 0x7FFu);
+  if (e < 1023 - 60 || e > 1023 + 100) {
+    a1 = __double2float_rn(a);
+    const double r = a - (double)a1;
+    a2 = __double2float_rn(r);
+    a3 = __double2float_rn(r - (double)a2);
+    return;
+  }
+  const unsigned int sign = uh & 0x80000000u;
+  a1 = __uint_as_float(sign | ((unsigned int)(e - 1023 + 127) << 23) | (__funnelshift_l(ul, uh, 3) & 0x007FFFFFu));
+  const unsigned int rem = ul & 0x1FFFFFFFu;            // the 29 fraction bits below a1: rem 2^(e - 1075)
+  const unsigned int top = rem >> 5, low = rem & 31u;
+  a2 = top ? __uint_as_float(sign | (__float_as_uint(__uint2float_rn(top)) + ((unsigned int)(e - 1070) << 23))) : 0.f;
+  a3 = low ? __uint_as_float(sign | (__float_as_uint(__uint2float_rn(low)) + ((unsigned int)(e - 1075) << 23))) : 0.f;
+}
+
+// A sum of products a x (a = a1 + a2 + a3 from split3_f64_bits, x a float) kept exactly in three float levels:
+// h collects the rounded leading products by Knuth's two-sum, m collects (again by two-sums) h's errors and
+// the next-order terms (the exact error of a1 x by the FMA two-product, a2 x), l the rest with plain adds
+// (terms ~2^-48 of a product, so its rounding stays near 2^-70 of the sum of |products|): more accurate than an
+// FP64 accumulation, on the FP32 pipe.
+struct xacc {
+  float h = 0.f, m = 0.f, l = 0.f;
+  __device__ __forceinline__ void add_prod(float a1, float a2, float a3, float x) {
+    const float p1 = __fmul_rn(a1, x), e1 = fmaf(a1, x, -p1);
+    const float p2 = __fmul_rn(a2, x), e2 = fmaf(a2, x, -p2);
+    const float p3 = __fmul_rn(a3, x);
+    float s, t0, u1, u2, u3;
+    two_sum(h, p1, s, t0);
+    h = s;
+    two_sum(m, t0, s, u1);
+    two_sum(s, e1, m, u2);
+    two_sum(m, p2, s, u3);
+    m = s;
+    l = __fadd_rn(l, __fadd_rn(__fadd_rn(u1, u2), __fadd_rn(u3, __fadd_rn(e2, p3))));
+  }
+  __device__ __forceinline__ double value() const { return ((double)l + (double)m) + (double)h; }
+};
+
 }  // namespace fthms

@@ -467,12 +467,12 @@ constexpr int kNB = 8;
 constexpr int kPS = kNB + 1;   // padded panel row stride (bank-conflict-free column access)
 constexpr int kLuThreads = 256;
 
-// C = double2 (plain form: factors J.A in place) or float2 (mixed form: factors J.LU32 in place).
+// C = double2 (plain form: factors J.A in place) or float2 (mixed form: factors J.LU32 in place).  One system
+// by the whole CTA (kLuThreads threads); shl_raw: max(N (kNB + kPS), 2 kSB^2) elements of shared memory.
 template <class C>
-__global__ void __launch_bounds__(kLuThreads) k_lu(DevJob J) {
-  extern __shared__ __align__(16) unsigned char shl_raw[];
+__device__ void lu_one(const DevJob& J, int sidx, unsigned char* shl_raw) {
   C* shl = reinterpret_cast<C*>(shl_raw);
-  const SysDesc s = J.sys[J.lu_small[blockIdx.x]];
+  const SysDesc s = J.sys[sidx];
   const int N = s.N;
   C* A = (sizeof(C) == sizeof(double2) ? reinterpret_cast<C*>(J.A) : reinterpret_cast<C*>(J.LU32)) + s.mat_off;
   int* piv = J.piv + s.piv_off;
@@ -547,6 +547,12 @@ __global__ void __launch_bounds__(kLuThreads) k_lu(DevJob J) {
                            shl);
 }
 
+template <class C>
+__global__ void __launch_bounds__(kLuThreads) k_lu(DevJob J) {
+  extern __shared__ __align__(16) unsigned char shl_raw[];
+  lu_one<C>(J, J.lu_small[blockIdx.x], shl_raw);
+}
+
 // ---------------------------------------------------------------------------------------------
 // Triangular solves, one warp per system, all Q right-hand sides together, in blocks of kSB = 32
 // rows: x_b = T_b^{-1} b_b with the inverted diagonal block (a 32 x 32 GEMV, lane = row), then the
@@ -560,11 +566,12 @@ constexpr int kSolveWarps = 4;
 // issues the loads of both rows before their FMAs, so a lane has 2 x kCols independent loads in flight
 // instead of walking its rows one after another.  A second row past `end` is computed on the first and
 // not stored.
-template <class C, int QT>
+template <class C, int QT, bool kLean>
 __device__ __forceinline__ void tri_update2(C* b, int N, const C* __restrict__ A, int r0, int w, int i0, int end) {
   const int i1 = i0 + 32 < end ? i0 + 32 : i0;
-  // columns per load batch: 16 FP32 or 8 FP64 entries per row, halved for 3-4 windows (registers)
-  constexpr int kCols = (sizeof(C) == 8 ? 16 : 8) / (QT > 2 ? 2 : 1);
+  // columns per load batch: 16 FP32 or 8 FP64 entries per row, halved for 3-4 windows and in lean builds
+  // (registers)
+  constexpr int kCols = (sizeof(C) == 8 ? 16 : 8) / (QT > 2 ? 2 : 1) / (kLean ? 2 : 1);
   C a0[QT], a1[QT];
 #pragma unroll
   for (int q = 0; q < QT; ++q) {
@@ -604,22 +611,23 @@ __device__ __forceinline__ void tri_update2(C* b, int N, const C* __restrict__ A
 // x_q = T_kk^{-1} b_q on the block rows r0 .. r0+w (the diagonal block stored inverted, so a GEMV): lane =
 // row, the block's entries loaded once for all QT windows.  lower: the unit-lower block (entries left of
 // the diagonal); else the unit-upper one (right of it).
-template <class C, int QT>
+template <class C, int QT, bool kLean>
 __device__ __forceinline__ void tri_diag(C* b, int N, const C* __restrict__ A, int r0, int w, int lane, bool lower) {
+  constexpr int kH = kLean ? 8 : 16;
   C x[QT];
   if (lane < w) {
 #pragma unroll
     for (int q = 0; q < QT; ++q) x[q] = b[q * N + r0 + lane];
 #pragma unroll 1
-    for (int h = 0; h < kSB; h += 16) {        // 16 loads in flight, then their FMAs
-      C v[16];
+    for (int h = 0; h < kSB; h += kH) {        // kH loads in flight, then their FMAs
+      C v[kH];
 #pragma unroll
-      for (int k = 0; k < 16; ++k) {
+      for (int k = 0; k < kH; ++k) {
         const bool use = lower ? h + k < lane : (h + k > lane && h + k < w);
         if (use) v[k] = __ldg(&A[(long long)(r0 + h + k) * N + r0 + lane]);
       }
 #pragma unroll
-      for (int k = 0; k < 16; ++k) {
+      for (int k = 0; k < kH; ++k) {
         const bool use = lower ? h + k < lane : (h + k > lane && h + k < w);
         if (use) {
 #pragma unroll
@@ -636,8 +644,9 @@ __device__ __forceinline__ void tri_diag(C* b, int N, const C* __restrict__ A, i
   __syncwarp();
 }
 
-// Both triangular sweeps of one system for its QT windows b[q * N + i] (shared memory), one warp.
-template <class C, int QT>
+// Both triangular sweeps of one system for its QT windows b[q * N + i] (shared memory), one warp (kLean:
+// smaller load batches, for kernels with a tighter register budget).
+template <class C, int QT, bool kLean = false>
 __device__ void tri_solve(C* b, int N, const C* __restrict__ A, const int* __restrict__ piv,
                           const C* __restrict__ dinv, int lane) {
   if (lane < QT) {
@@ -650,19 +659,40 @@ __device__ void tri_solve(C* b, int N, const C* __restrict__ A, const int* __res
   __syncwarp();
   for (int r0 = 0; r0 < N; r0 += kSB) {           // forward, unit lower
     const int w = min(kSB, N - r0), r1 = r0 + w;
-    tri_diag<C, QT>(b, N, A, r0, w, lane, true);
+    tri_diag<C, QT, kLean>(b, N, A, r0, w, lane, true);
 #pragma unroll 1
-    for (int i0 = r1 + lane; i0 < N; i0 += 64) tri_update2<C, QT>(b, N, A, r0, w, i0, N);
+    for (int i0 = r1 + lane; i0 < N; i0 += 64) tri_update2<C, QT, kLean>(b, N, A, r0, w, i0, N);
     __syncwarp();
   }
   for (int e = lane; e < QT * N; e += 32) b[e] = cmul(b[e], __ldg(&dinv[e % N]));
   __syncwarp();
   for (int r0 = ((N - 1) / kSB) * kSB; r0 >= 0; r0 -= kSB) {   // backward, unit upper
     const int w = min(kSB, N - r0);
-    tri_diag<C, QT>(b, N, A, r0, w, lane, false);
+    tri_diag<C, QT, kLean>(b, N, A, r0, w, lane, false);
 #pragma unroll 1
-    for (int i0 = lane; i0 < r0; i0 += 64) tri_update2<C, QT>(b, N, A, r0, w, i0, r0);
+    for (int i0 = lane; i0 < r0; i0 += 64) tri_update2<C, QT, kLean>(b, N, A, r0, w, i0, r0);
     __syncwarp();
+  }
+}
+
+// Both sweeps of one system's FP64 factors for all QT windows of step m, by one warp (b: QT x N double2 of
+// shared memory), then its densities, their running sum and (kept densities) step m's copy.
+template <int QT, bool kLean = false>
+__device__ void solve_one(const DevJob& J, int sidx, int m, double2* b, int lane) {
+  const SysDesc s = J.sys[sidx];
+  const int N = s.N;
+  const double2* G = J.G + s.vec_off;
+  for (int e = lane; e < QT * N; e += 32) b[e] = G[e];
+  __syncwarp();
+  tri_solve<double2, QT, kLean>(b, N, J.A + s.mat_off, J.piv + s.piv_off, J.dinv + s.piv_off, lane);
+  double2* out = J.phi + s.vec_off;
+  double2* sum = J.phi_sum + s.vec_off;
+  double2* all = J.phi_all ? J.phi_all + (long long)(m - 1) * J.vec_total + s.vec_off : nullptr;
+  for (int e = lane; e < QT * N; e += 32) {
+    double2 v = b[e];
+    out[e] = v;
+    sum[e] = m == 1 ? v : cadd(sum[e], v);
+    if (all) all[e] = v;
   }
 }
 
@@ -672,22 +702,83 @@ __global__ void __launch_bounds__(32 * kSolveWarps) k_solve(DevJob J, int m) {
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int slot = blockIdx.x * (blockDim.x >> 5) + wid;
   if (slot >= J.nsys) return;
-  const int sidx = J.sys_order[slot];
+  solve_one<QT>(J, J.sys_order[slot], m, shs + (size_t)wid * QT * J.max_n, lane);
+}
+
+// The FP64 self matrix of one system (plain form) by one CTA: every entry of the upper triangle (diagonal
+// included) evaluated for the system's own frequency and stored at both mirror positions -- the same
+// log-split rule, Taylor range below z = 20 and Hankel asymptotics above as k_assemble_self, without its
+// sharing of the per-pair terms across a band of frequencies.
+__device__ void assemble_one(const DevJob& J, int sidx) {
   const SysDesc s = J.sys[sidx];
-  const int N = s.N, Q = QT;
-  double2* b = shs + (size_t)wid * Q * J.max_n;
-  const double2* G = J.G + s.vec_off;
-  for (int e = lane; e < Q * N; e += 32) b[e] = G[e];
-  __syncwarp();
-  tri_solve<double2, QT>(b, N, J.A + s.mat_off, J.piv + s.piv_off, J.dinv + s.piv_off, lane);
-  double2* out = J.phi + s.vec_off;
-  double2* sum = J.phi_sum + s.vec_off;
-  double2* all = J.phi_all ? J.phi_all + (long long)(m - 1) * J.vec_total + s.vec_off : nullptr;
-  for (int e = lane; e < Q * N; e += 32) {
-    double2 v = b[e];
-    out[e] = v;
-    sum[e] = m == 1 ? v : cadd(sum[e], v);
-    if (all) all[e] = v;
+  const int N = s.N;
+  const Panel pn = J.panels[s.panel];
+  const double l = (double)s.l, lnl = log(l);
+  const double w = kPiD / N, qw = 0.25 * w;
+  const long long ntri = (long long)N * (N + 1) / 2;
+  for (long long t = threadIdx.x; t < ntri; t += blockDim.x) {
+    // t -> (i, c) with i <= c, column by column: c (c + 1) / 2 <= t < (c + 1) (c + 2) / 2
+    int c = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    while ((long long)(c + 1) * (c + 2) / 2 <= t) ++c;
+    while ((long long)c * (c + 1) / 2 > t) --c;
+    const int i = (int)(t - (long long)c * (c + 1) / 2);
+    const double rl = J.rlog[s.rlog_off + (long long)i * N + c];
+    const long long e1 = (long long)c * N + i, e2 = (long long)i * N + c;
+    double2 v;
+    if (i == c) {
+      const double lsp = log(0.5 * J.h * J.node_sp[pn.off + i]);
+      v = make_double2(fma(-0.5 * kInvPi, rl, -0.5 * kInvPi * (kEulerGamma + lnl + lsp) * w), qw);
+    } else {
+      const double dx = J.node_x[pn.off + i] - J.node_x[pn.off + c];
+      const double dy = J.node_y[pn.off + i] - J.node_y[pn.off + c];
+      const double R = sqrt(fma(dx, dx, dy * dy));
+      const double dts = fabs(J.node_t[pn.off + i] - J.node_t[pn.off + c]);
+      const double hR = J.h * R, z = l * hR;
+      if (z < kBesselLarge) {
+        double J0, Yh;
+        bessel0_taylor(z, J0, Yh);
+        const double alpha = -0.5 * kInvPi * fma(w, lnl + log(hR / (2.0 * dts)) + kEulerGamma, rl);
+        v = make_double2(fma(alpha, J0, -qw * Yh), qw * J0);
+      } else {
+        double J0, Y0;
+        bessel0_asym(z, J0, Y0);
+        const double alpha = -0.5 * kInvPi * (rl - w * log(dts));
+        v = make_double2(fma(alpha, J0, -qw * Y0), qw * J0);
+      }
+    }
+    J.A[s.mat_off + e1] = v;
+    J.A[s.mat_off + e2] = v;
+  }
+}
+
+// The fused kernel's phases as separate calls, so that each keeps its own register allocation.
+template <int QT>
+__device__ __noinline__ void fused_solve(const DevJob& J, int sidx, double2* b, int lane) {
+  solve_one<QT, true>(J, sidx, 1, b, lane);
+}
+__device__ __noinline__ void fused_assemble(const DevJob& J, int sidx) { assemble_one(J, sidx); }
+__device__ __noinline__ void fused_lu(const DevJob& J, int sidx, unsigned char* sh) { lu_one<double2>(J, sidx, sh); }
+
+// Batching form, plain FP64: one persistent launch assembles, factors and solves (step 1) every (arc, omega)
+// system.  Each CTA takes the next system from a work counter (systems by decreasing N, so the largest start
+// first and the small ones fill the tail), assembles its matrix, factors it (lu_one) and solves its step-1
+// windows with one warp; the counter is reset by the host before the launch.
+template <int QT>
+__global__ void __launch_bounds__(kLuThreads, 1) k_fused_asf(DevJob J, int* counter) {
+  extern __shared__ __align__(16) unsigned char shf_raw[];
+  __shared__ int s_item;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int item = s_item;
+    if (item >= J.nsys) return;
+    const int sidx = J.sys_order[item];
+    fused_assemble(J, sidx);
+    __syncthreads();
+    fused_lu(J, sidx, shf_raw);
+    __syncthreads();
+    if (threadIdx.x < 32) fused_solve<QT>(J, sidx, reinterpret_cast<double2*>(shf_raw), threadIdx.x);
+    __syncthreads();
   }
 }
 
@@ -1380,8 +1471,12 @@ constexpr int kResidThreads = 128;
 template <int Q>
 __global__ void __launch_bounds__(kResidThreads) k_mresid(DevJob J);
 
-// The same residual in FP64 (FP64-kept form): the matrix and the densities (refined in FP64) read as FP64,
-// FMA accumulation over the columns in order.
+// The first-pass residual of the systems that keep FP64 (all in the FP64-kept form), to FP64 accuracy on both
+// arithmetic pipes at once: phi_0 is the FP32 solution (exactly a float), so every product a_ij phi_j can be
+// formed exactly from a three-float split of the FP64 entry.  A warp sums its rows either through FP64 FMAs
+// (acc) or through exact products and exact two-level sums on the FP32 pipe (xacc); the FP64 pipe, which alone
+// would bound the kernel at 8 DFMA per entry and two windows, and the FP32 pipe then work side by side.
+// The result, G - A phi_0, is as accurate as an all-FP64 accumulation or more.
 template <int Q>
 __global__ void __launch_bounds__(kResidThreads) k_mresid64(DevJob J) {
   const int chunk = blockIdx.x * (kResidThreads / 32) + (threadIdx.x >> 5);
@@ -1394,27 +1489,66 @@ __global__ void __launch_bounds__(kResidThreads) k_mresid64(DevJob J) {
   const int i = c.row0 + (threadIdx.x & 31);
   const int row = i < N ? i : N - 1;
   const double2* __restrict__ A64 = J.A + s.mat_off;
-  const double2* __restrict__ ph = J.phi + s.vec_off;
+  const double2* __restrict__ ph = J.phi + s.vec_off;       // phi_0 as FP64 (exact)
+  const float2* __restrict__ ph32 = J.dcorr + s.vec_off;    // the same values as floats (pass-0 solve)
   const double2* __restrict__ G = J.G + s.vec_off;
   const double isc = 1.0 / J.mscale[c.sys];   // a power of two: exact
   double2 acc[Q];
+  xacc sr[Q], si[Q];
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
     const double2 g = G[q * N + row];
     acc[q] = make_double2(g.x * isc, g.y * isc);
   }
-  constexpr int kUnroll = Q == 1 ? 8 : Q == 2 ? 4 : 2;
-#pragma unroll kUnroll
-  for (int j = 0; j < N; ++j) {
-    const double2 a = __ldg(&A64[(long long)j * N + row]);
+  auto col64 = [&](const double2 a, int j) {
 #pragma unroll
     for (int q = 0; q < Q; ++q) acc[q] = cfms(a, ph[q * N + j], acc[q]);
+  };
+  auto colx = [&](const double2 a, int j) {
+    float r1, r2, r3, i1, i2, i3;
+    split3_f64_bits(a.x, r1, r2, r3);
+    split3_f64_bits(a.y, i1, i2, i3);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const float2 x = ph32[q * N + j];
+      sr[q].add_prod(r1, r2, r3, x.x);          // Re a phi = ar phr - ai phi
+      sr[q].add_prod(-i1, -i2, -i3, x.y);
+      si[q].add_prod(r1, r2, r3, x.y);          // Im a phi = ar phi + ai phr
+      si[q].add_prod(i1, i2, i3, x.x);
+    }
+  };
+  // warps specialise: every other 32-row chunk sums in FP64, the rest on the FP32 pipe, so that warps waiting
+  // on the FP64 pipe and warps issuing FP32 work share each SM (measured per job: 4 of 7 chunks in FP64 122 ms,
+  // 5 of 8 128 ms, all 166 ms)
+  const bool on_fp32 = (chunk & 1) != 0;
+  int j0 = 0;
+  if (on_fp32) {
+#pragma unroll 1
+    for (; j0 + 4 <= N; j0 += 4) {             // four entries of the row loaded before their sums
+      double2 a[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) a[k] = __ldg(&A64[(long long)(j0 + k) * N + row]);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) colx(a[k], j0 + k);
+    }
+    for (; j0 < N; ++j0) colx(__ldg(&A64[(long long)j0 * N + row]), j0);
+  } else {
+#pragma unroll 1
+    for (; j0 + 8 <= N; j0 += 8) {
+      double2 a[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) a[k] = __ldg(&A64[(long long)(j0 + k) * N + row]);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) col64(a[k], j0 + k);
+    }
+    for (; j0 < N; ++j0) col64(__ldg(&A64[(long long)j0 * N + row]), j0);
   }
   if (i < N) {
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-      J.rres[s.vec_off + q * N + i] = make_float2(__double2float_rn(acc[q].x), __double2float_rn(acc[q].y));
-      J.rres64[s.vec_off + q * N + i] = acc[q];
+      const double2 r = make_double2(acc[q].x - sr[q].value(), acc[q].y - si[q].value());
+      J.rres[s.vec_off + q * N + i] = make_float2(__double2float_rn(r.x), __double2float_rn(r.y));
+      J.rres64[s.vec_off + q * N + i] = r;
     }
   }
 }
@@ -1586,9 +1720,13 @@ __global__ void __launch_bounds__(32 * kSolveWarps, 3) k_msolve(DevJob J, int m,
   __syncwarp();
   tri_solve<float2, QT>(b, N, L32, piv, dinv, lane);
   double2* ph64 = J.phi + s.vec_off;
+  float2* dc = J.dcorr + s.vec_off;
   if (pass == 0) {
     if (f64) {
-      for (int e = lane; e < Q * N; e += 32) ph64[e] = make_double2(b[e].x, b[e].y);
+      for (int e = lane; e < Q * N; e += 32) {
+        ph64[e] = make_double2(b[e].x, b[e].y);
+        dc[e] = b[e];                         // phi_0 as floats for the first residual's FP32-pipe columns
+      }
     } else {
       for (int e = lane; e < Q * N; e += 32) ph[e] = make_float4(b[e].x, 0.f, b[e].y, 0.f);
     }
@@ -1596,7 +1734,6 @@ __global__ void __launch_bounds__(32 * kSolveWarps, 3) k_msolve(DevJob J, int m,
     return;
   }
   float dmax = 0.f, pmax = 0.f;
-  float2* dc = J.dcorr + s.vec_off;
   for (int e = lane; e < Q * N; e += 32) {
     const float2 d = b[e];
     if (f64) {
@@ -2210,6 +2347,34 @@ cudaError_t launch_lu_small(const DevJob& J, cudaStream_t st, int* launches) {
   k_lu<double2><<<J.n_lu_small, kLuThreads, sh, st>>>(J);
   *launches += 1;
   return cudaGetLastError();
+}
+
+template <int QT>
+static cudaError_t launch_fused_q(const DevJob& J, int* counter, size_t sh, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(k_fused_asf<QT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per_sm = 0;
+  e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_asf<QT>, kLuThreads, sh);
+  if (e != cudaSuccess) return e;
+  const int grid = std::max(1, std::min(J.nsys, sms * std::max(per_sm, 1)));
+  e = cudaMemsetAsync(counter, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  k_fused_asf<QT><<<grid, kLuThreads, sh, st>>>(J, counter);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fused_asf(const DevJob& J, int* counter, cudaStream_t st, int* launches) {
+  if (J.nsys == 0) return cudaSuccess;
+  const size_t sh = std::max((size_t)J.max_n * (kNB + kPS), (size_t)2 * kSB * kSB) * sizeof(double2);
+  *launches += 1;
+  switch (J.Q) {
+    case 1: return launch_fused_q<1>(J, counter, sh, st);
+    case 2: return launch_fused_q<2>(J, counter, sh, st);
+    case 3: return launch_fused_q<3>(J, counter, sh, st);
+    default: return launch_fused_q<4>(J, counter, sh, st);
+  }
 }
 
 cudaError_t launch_cross_assemble(const DevJob& J, cudaStream_t st, int* launches) {

@@ -31,6 +31,7 @@ struct DevJob {
   const int* lu_big;          // mixed forms: systems above kLuBigMin, factored with tensor-core updates
   int n_lu_small, n_lu_big, big_max_n;
   int* dev_err;               // set by a kernel whose bounded wait ran out (reported by fthms_wait)
+  int* work_counter;          // the fused kernel's next-system counter
   const Panel* panels;
   const double *node_t, *node_x, *node_y, *node_sp;
   const int* rlogN;
@@ -131,6 +132,9 @@ cudaError_t launch_lu_big_panel(const DevJob& J, int panel, cudaStream_t st, int
 cudaError_t launch_lu_big_update(const DevJob& J, int panel, cudaStream_t st, int* launches);
 cudaError_t launch_lu_big_finish(const DevJob& J, cudaStream_t st, int* launches);
 size_t lu_big_panel_smem(int maxN);
+// Plain FP64 form, batching: self assembly, LU and the step-1 solve of every system in one persistent launch
+// (counter: one device int, reset on the stream before the launch).
+cudaError_t launch_fused_asf(const DevJob& J, int* counter, cudaStream_t st, int* launches);
 cudaError_t launch_cross_assemble(const DevJob& J, cudaStream_t st, int* launches);
 cudaError_t launch_incident(const DevJob& J, cudaStream_t st, int* launches);
 cudaError_t launch_restrict(const DevJob& J, cudaStream_t st, int* launches);

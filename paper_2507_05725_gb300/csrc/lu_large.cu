@@ -11,13 +11,14 @@
 //    minus sign by the instruction descriptor's B negation;
 //  - FP32 accuracy from TF32 by the three-term split x = x_hi + x_lo (x_hi = tf32(x), x_lo = tf32(x - x_hi)):
 //    A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi, FP32 accumulation;
-//  - 8 operand parts (Ar, Ai, Br, Bi) x (hi, lo) of 128 rows x 32 K in shared memory, K-major without
-//    swizzle: element (r, k) at byte (r % 8) 16 + (r / 8) 1024 + (k % 4) 4 + (k / 4) 128, so a core matrix
-//    (8 rows x 16 bytes) is contiguous, K-adjacent core matrices are 128 bytes apart (leading byte offset)
-//    and 8-row groups 1024 bytes apart (stride byte offset); 48 MMAs of 128 x 128 x 8 per tile;
-//  - Re D and Im D in TMEM columns [0, 128) and [128, 256) (the CTA holds all 512 columns: one CTA per SM);
-//    lane = tile row; the epilogue reads 16 columns at a time and subtracts them from the FP32 factor in
-//    HBM (a warp's rows are contiguous there);
+//  - K in two stages of 16: 8 operand parts (Ar, Ai, Br, Bi) x (hi, lo) of 128 rows x 16 K in 64 KB of shared
+//    memory, K-major without swizzle: element (r, k) at byte (r % 8) 16 + (r / 8) 512 + (k % 4) 4 + (k / 4) 128,
+//    so a core matrix (8 rows x 16 bytes) is contiguous, K-adjacent core matrices are 128 bytes apart (leading
+//    byte offset) and 8-row groups 512 bytes apart (stride byte offset); 24 MMAs of 128 x 128 x 8 per stage;
+//    the second stage's HBM loads are in flight while the first stage's MMAs run;
+//  - Re D and Im D in TMEM columns [0, 128) and [128, 256) of the CTA's 256 (two CTAs per SM); lane = tile
+//    row; the epilogue reads 16 columns at a time and subtracts them from the FP32 factor in HBM (a warp's rows
+//    are contiguous there);
 //  - the wait for the MMAs is bounded: when it runs out the CTA flags J.dev_err (fthms_wait reports it),
 //    frees its tensor memory and returns, and later CTAs return at once.
 #include <cstdint>
@@ -35,15 +36,17 @@ constexpr int kInner = 8;           // inner panel width (one warp)
 constexpr int kInnerPS = kInner + 1;
 constexpr int kPanelThreads = 256;
 constexpr int kTile = 128;          // complex rows and columns of an update tile
-constexpr int kPartBytes = kTile * kOuter * 4;   // 128 x 32 TF32 = 16 KB per operand part
+constexpr int kStageK = 16;                       // K per operand stage (two stages per 32-column panel)
+constexpr int kPartBytes = kTile * kStageK * 4;   // 128 x 16 TF32 = 8 KB per operand part and stage
+constexpr int kSBO = (kStageK / 4) * 128;         // bytes between 8-row groups of a part (K-major, no swizzle)
 constexpr int kUpdThreads = 256;
 constexpr long long kMaxPolls = 1ll << 18;      // bounded wait for the tensor core (well under a second)
-constexpr uint32_t kTmemCols = 512;             // the whole tensor memory of the SM (one CTA per SM)
+constexpr uint32_t kTmemCols = 256;             // Re and Im accumulators, 128 columns each (two CTAs per SM)
 constexpr int kLuThreadsFinish = 256;
 
-// Byte offset of element (r, k) of a 128 x 32 K-major part (see the file comment).
+// Byte offset of element (r, k) of a 128 x 16 K-major part (see the file comment).
 __device__ __forceinline__ int part_off(int r, int k) {
-  return (r & 7) * 16 + (r >> 3) * 1024 + (k & 3) * 4 + (k >> 2) * 128;
+  return (r & 7) * 16 + (r >> 3) * kSBO + (k & 3) * 4 + (k >> 2) * 128;
 }
 
 // Outer panel k0 of every large system with N > k0 (kPanelThreads threads per system).
@@ -165,14 +168,86 @@ __global__ void __launch_bounds__(kPanelThreads) k_lu_big_panel(DevJob J, int k0
   }
 }
 
-// One operand part element: the TF32 value and its TF32 remainder.
+// One operand stage (K = 16 of the panel, from column k0 + kk0): the L21 tile (rows R0 .. R0+127) and the U12
+// tile (columns C0 .. C0+127), both read from HBM into registers (zero beyond N).
+struct StageRegs {
+  float2 l[8];   // L21: row tid % 128, k = kk0 + 8 (tid / 128) + 0..7
+  float2 u[8];   // U12: k = kk0 + tid % 16, column tid / 16 + 16 j, j = 0..7
+};
+
+__device__ __forceinline__ void load_stage(const float2* A, int N, int k0, int kk0, int R0, int C0, int tid,
+                                           StageRegs& g) {
+  const int r = tid & (kTile - 1), kh = (tid >> 7) * 8, row = R0 + r;
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    g.l[k] = row < N ? A[(long long)(k0 + kk0 + kh + k) * N + row] : make_float2(0.f, 0.f);
+  const int kk = tid & 15;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int col = C0 + (tid >> 4) + 16 * j;
+    g.u[j] = col < N ? A[(long long)col * N + k0 + kk0 + kk] : make_float2(0.f, 0.f);
+  }
+}
+
+// One operand element: the TF32 value and its TF32 remainder.
 __device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
   hi = tc::to_tf32(x);
   lo = tc::to_tf32(x - hi);
 }
 
-// Trailing update A22 -= L21 U12 after outer panel k0: blockIdx.x = large system, blockIdx.y = tile.
-__global__ void __launch_bounds__(kUpdThreads, 1) k_lu_big_update(DevJob J, int k0) {
+// The stage's registers as the 8 K-major parts 0 Ar_hi, 1 Ar_lo, 2 Ai_hi, 3 Ai_lo, 4 Br_hi, 5 Br_lo,
+// 6 Bi_hi, 7 Bi_lo in shared memory.
+__device__ __forceinline__ void store_stage(unsigned char* part, int tid, const StageRegs& g) {
+  const int r = tid & (kTile - 1), kh = (tid >> 7) * 8;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    float h, l;
+    const int o = part_off(r, kh + k);
+    split_tf32(g.l[k].x, h, l);
+    *reinterpret_cast<float*>(part + 0 * kPartBytes + o) = h;
+    *reinterpret_cast<float*>(part + 1 * kPartBytes + o) = l;
+    split_tf32(g.l[k].y, h, l);
+    *reinterpret_cast<float*>(part + 2 * kPartBytes + o) = h;
+    *reinterpret_cast<float*>(part + 3 * kPartBytes + o) = l;
+  }
+  const int kk = tid & 15;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    float h, l;
+    const int o = part_off((tid >> 4) + 16 * j, kk);
+    split_tf32(g.u[j].x, h, l);
+    *reinterpret_cast<float*>(part + 4 * kPartBytes + o) = h;
+    *reinterpret_cast<float*>(part + 5 * kPartBytes + o) = l;
+    split_tf32(g.u[j].y, h, l);
+    *reinterpret_cast<float*>(part + 6 * kPartBytes + o) = h;
+    *reinterpret_cast<float*>(part + 7 * kPartBytes + o) = l;
+  }
+}
+
+// The MMAs of one stage (issued by one thread): complex as four real products, each as the three TF32 products
+// hi hi, hi lo, lo hi; the first stage's first products overwrite the accumulators.
+__device__ __forceinline__ void mma_stage(uint32_t base, uint32_t d_re, uint32_t d_im, bool first) {
+  constexpr uint32_t id_pos = tc::idesc_tf32(kTile, kTile, false), id_neg = tc::idesc_tf32(kTile, kTile, true);
+  const int xa[3] = {0, 0, 1}, xb[3] = {0, 1, 0};
+  for (int t = 0; t < 3; ++t) {
+    for (int ks = 0; ks < kStageK / 8; ++ks) {
+      const uint32_t ko = ks * 256;    // 8 TF32 of K = two 16-byte core-matrix columns
+      auto desc = [&](int p) { return tc::smem_desc(base + p * kPartBytes + ko, 128, kSBO); };
+      const uint64_t ar = desc(0 + xa[t]), ai = desc(2 + xa[t]), br = desc(4 + xb[t]), bi = desc(6 + xb[t]);
+      tc::mma_tf32(d_re, ar, br, id_pos, !first);
+      tc::mma_tf32(d_re, ai, bi, id_neg, true);
+      tc::mma_tf32(d_im, ar, bi, id_pos, !first);
+      tc::mma_tf32(d_im, ai, br, id_pos, true);
+      first = false;
+    }
+  }
+}
+
+// Trailing update A22 -= L21 U12 after outer panel k0: blockIdx.x = large system, blockIdx.y = tile.  K = 32 in
+// two stages of 16 through one 64 KB operand buffer: the second stage's HBM loads are issued before the wait for
+// the first stage's MMAs (which read the buffer), then written over it.  64 KB of shared memory and 256 tensor-
+// memory columns per CTA, so two CTAs share an SM and overlap one's epilogue with the other's loads.
+__global__ void __launch_bounds__(kUpdThreads, 2) k_lu_big_update(DevJob J, int k0) {
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ __align__(8) uint64_t bar;
   __shared__ uint32_t tmem_base;
@@ -186,79 +261,41 @@ __global__ void __launch_bounds__(kUpdThreads, 1) k_lu_big_update(DevJob J, int 
   const int R0 = k0 + kOuter + kTile * ((int)blockIdx.y / tm), C0 = k0 + kOuter + kTile * ((int)blockIdx.y % tm);
   float2* A = J.LU32 + s.mat_off;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  // parts: 0 Ar_hi, 1 Ar_lo, 2 Ai_hi, 3 Ai_lo, 4 Br_hi, 5 Br_lo, 6 Bi_hi, 7 Bi_lo
   unsigned char* part = sm;
   if (wid == 0) tc::tmem_alloc(&tmem_base, kTmemCols);
   if (tid == 0) tc::mbar_init(&bar, 1);
-  // L21 tile: rows R0 .. R0+127 of columns k0 .. k0+31 (thread = row and half of K; zero beyond N), the 16
-  // loads of a thread issued before their splits.
-  {
-    const int r = tid & (kTile - 1), kh = (tid >> 7) * (kOuter / 2), row = R0 + r;
-    float2 v[kOuter / 2];
-#pragma unroll
-    for (int k = 0; k < kOuter / 2; ++k)
-      v[k] = row < N ? A[(long long)(k0 + kh + k) * N + row] : make_float2(0.f, 0.f);
-#pragma unroll
-    for (int k = 0; k < kOuter / 2; ++k) {
-      float h, l;
-      const int o = part_off(r, kh + k);
-      split_tf32(v[k].x, h, l);
-      *reinterpret_cast<float*>(part + 0 * kPartBytes + o) = h;
-      *reinterpret_cast<float*>(part + 1 * kPartBytes + o) = l;
-      split_tf32(v[k].y, h, l);
-      *reinterpret_cast<float*>(part + 2 * kPartBytes + o) = h;
-      *reinterpret_cast<float*>(part + 3 * kPartBytes + o) = l;
-    }
-  }
-  // U12 tile: rows k0 .. k0+31 of columns C0 .. C0+127 as a 128 (column) x 32 (k) K-major operand
-  // (warp = column, lane = k: each column's 32 values are contiguous in HBM), 4 columns in flight per warp.
-  for (int n0 = wid; n0 < kTile; n0 += 4 * (kUpdThreads / 32)) {
-    float2 v[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int col = C0 + n0 + u * (kUpdThreads / 32);
-      v[u] = col < N ? A[(long long)col * N + k0 + lane] : make_float2(0.f, 0.f);
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      float h, l;
-      const int o = part_off(n0 + u * (kUpdThreads / 32), lane);
-      split_tf32(v[u].x, h, l);
-      *reinterpret_cast<float*>(part + 4 * kPartBytes + o) = h;
-      *reinterpret_cast<float*>(part + 5 * kPartBytes + o) = l;
-      split_tf32(v[u].y, h, l);
-      *reinterpret_cast<float*>(part + 6 * kPartBytes + o) = h;
-      *reinterpret_cast<float*>(part + 7 * kPartBytes + o) = l;
-    }
-  }
+  StageRegs g;
+  load_stage(A, N, k0, 0, R0, C0, tid, g);
+  store_stage(part, tid, g);
+  load_stage(A, N, k0, kStageK, R0, C0, tid, g);  // in flight during the first stage's MMAs
   tc::fence_proxy_async();
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = tmem_base;
+  const uint32_t base = tc::smem_addr(part);
   if (tid == 0) {
-    const uint32_t base = tc::smem_addr(part);
-    constexpr uint32_t id_pos = tc::idesc_tf32(kTile, kTile, false), id_neg = tc::idesc_tf32(kTile, kTile, true);
-    const uint32_t d_re = tmem, d_im = tmem + kTile;
-    // (A part, B part) pairs of the three-term split: hi hi, hi lo, lo hi
-    const int xa[3] = {0, 0, 1}, xb[3] = {0, 1, 0};
-    bool first = true;
-    for (int t = 0; t < 3; ++t) {
-      for (int ks = 0; ks < kOuter / 8; ++ks) {
-        const uint32_t ko = ks * 256;    // 8 TF32 of K = two 16-byte core-matrix columns
-        auto desc = [&](int p) { return tc::smem_desc(base + p * kPartBytes + ko, 128, 1024); };
-        const uint64_t ar = desc(0 + xa[t]), ai = desc(2 + xa[t]), br = desc(4 + xb[t]), bi = desc(6 + xb[t]);
-        tc::mma_tf32(d_re, ar, br, id_pos, !first);
-        tc::mma_tf32(d_re, ai, bi, id_neg, true);
-        tc::mma_tf32(d_im, ar, bi, id_pos, !first);
-        tc::mma_tf32(d_im, ai, br, id_pos, true);
-        first = false;
-      }
-    }
+    mma_stage(base, tmem, tmem + kTile, true);
     tc::mma_commit(&bar);
   }
-  const bool ok = tc::mbar_wait(&bar, 0, kMaxPolls);
+  bool ok = tc::mbar_wait(&bar, 0, kMaxPolls);   // the buffer is free once the first stage's MMAs are done
   tc::fence_after_sync();
+  if (ok) {
+    store_stage(part, tid, g);
+    tc::fence_proxy_async();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  ok = __syncthreads_and(ok) != 0;
+  if (ok) {
+    if (tid == 0) {
+      mma_stage(base, tmem, tmem + kTile, false);
+      tc::mma_commit(&bar);
+    }
+    ok = tc::mbar_wait(&bar, 1, kMaxPolls);
+    tc::fence_after_sync();
+  }
   if (ok) {
     // warp w reads TMEM lanes 32 (w % 4) .. + 31 (its lane quarter); warps 0-3 take columns 0-63, 4-7 64-127
     const int quarter = wid & 3, row = R0 + 32 * quarter + lane;
@@ -311,7 +348,9 @@ static cudaError_t lu_big_attributes(const DevJob& J) {
   // the largest shared-memory carveout, so that two panel CTAs (128 registers a thread) share an SM
   e = cudaFuncSetAttribute(k_lu_big_panel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_lu_big_update, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * kPartBytes);
+  e = cudaFuncSetAttribute(k_lu_big_update, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * kPartBytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_lu_big_update, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
 }
 
 int lu_big_panels(const DevJob& J) { return J.n_lu_big > 0 ? (J.big_max_n + kOuter - 1) / kOuter : 0; }

@@ -64,7 +64,7 @@ class fthms_stats_t(C.Structure):
 ALLREDUCE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 
 STAGES = ["tables", "assemble_self", "lu", "cross_assemble", "incident", "restrict", "solve", "cross_apply",
-          "synth_fwd", "traces", "resid", "resid_upd", "lu_update"]
+          "synth_fwd", "traces", "resid", "resid_upd", "lu_update", "fused"]
 
 
 def _load():
@@ -109,6 +109,7 @@ def _load():
         "fthms_use_graph": (st, [vp, C.c_int]),
         "fthms_autotune": (st, [vp, C.c_int, C.POINTER(C.c_int)]),
         "fthms_set_shapes": (st, [vp, C.POINTER(C.c_int)]),
+        "fthms_use_fused": (st, [vp, C.c_int]),
         "fthms_profile": (st, [vp, C.c_int]),
         "fthms_stage_times": (st, [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
     }
@@ -127,7 +128,8 @@ EXPORTED = ["fthms_create", "fthms_destroy", "fthms_prepare", "fthms_run", "fthm
             "fthms_profile", "fthms_stage_times", "fthms_assemble_self_noalloc", "fthms_server_create",
             "fthms_server_submit", "fthms_server_poll", "fthms_server_wait", "fthms_server_result",
             "fthms_server_latency", "fthms_server_release", "fthms_server_destroy", "fthms_use_graph",
-            "fthms_autotune", "fthms_plan_info", "fthms_result_errors", "fthms_set_allreduce", "fthms_set_shapes"]
+            "fthms_autotune", "fthms_plan_info", "fthms_result_errors", "fthms_set_allreduce", "fthms_set_shapes",
+            "fthms_use_fused"]
 
 
 def _check(status):
@@ -346,6 +348,10 @@ def fthms_set_shapes(req, shapes):
     """Apply five choices as fthms_autotune returns them, without timing."""
     arr = (C.c_int * 5)(*[int(v) for v in shapes])
     _check(LIB.fthms_set_shapes(req, arr))
+
+
+def fthms_use_fused(req, enable=True):
+    _check(LIB.fthms_use_fused(req, int(bool(enable))))
 
 
 def fthms_use_graph(req, enable=True):
