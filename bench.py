@@ -283,7 +283,7 @@ class _NoClock:
 
 
 def time_job(F, ctx, stream, problem, precision, steps, warmup, autotune=False, graph=False, clocks=None,
-             dens=False, allreduce=None, ws=1):
+             dens=False, allreduce=None, ws=1, fused=False):
     """Device time of `steps` back-to-back runs of one prepared job after `warmup` runs (CUDA events on the
     library's stream, synchronised on both sides, max over ranks), with its stage times (direct launches)."""
     import torch
@@ -292,6 +292,8 @@ def time_job(F, ctx, stream, problem, precision, steps, warmup, autotune=False, 
     if allreduce is not None:
         job.set_allreduce(allreduce)
     tune = F.fthms_autotune(job.req, 2) if autotune else None
+    if fused:
+        F.fthms_use_fused(job.req)
     if graph:
         F.fthms_use_graph(job.req, True)
     for _ in range(warmup):
@@ -582,6 +584,14 @@ def ours(args):
             m2 = time_job(F, ctx, stream, c2, 1, 3, 2, autotune=True, graph=True)
             forms["c2_plain_fp64"] = dict(summary(p2), value=solves_of(c2) / (p2["ms"] / 1e3),
                                           workload=WORKLOAD_NAMES["c2"])
+            f2 = time_job(F, ctx, stream, c2, 0, 3, 2, fused=True)
+            forms["c2_plain_fp64_fused"] = dict(
+                summary(f2), value=solves_of(c2) / (f2["ms"] / 1e3), workload=WORKLOAD_NAMES["c2"],
+                note="batching form: assembly, LU and step-1 solve of every system in one persistent launch "
+                     "(fthms_use_fused), against c2_plain_fp64's staged launches of the same FP64 kernels",
+                fused_ms_per_job=f2["stages"].get("fused", (0.0, 0))[0] if f2["stages"] else None,
+                staged_ms_per_job=sum(p2["stages"][k][0] for k in ("assemble_self", "lu")) + p2["stages"]["solve"][0]
+                / c2["options"]["M"] if p2["stages"] else None)
             forms["c2_mixed_autotuned_graph"] = dict(summary(m2), value=solves_of(c2) / (m2["ms"] / 1e3),
                                                      workload=WORKLOAD_NAMES["c2"])
         if not args.no_c3 and args.workload != "c3":

@@ -751,20 +751,30 @@ __device__ void assemble_one(const DevJob& J, int sidx) {
   }
 }
 
-// The fused kernel's phases as separate calls, so that each keeps its own register allocation.
-template <int QT>
-__device__ __noinline__ void fused_solve(const DevJob& J, int sidx, double2* b, int lane) {
-  solve_one<QT, true>(J, sidx, 1, b, lane);
+// The fused kernel's step-1 solve, one window per warp (a single-window sweep needs few registers), as a
+// separate call so that it keeps its own register allocation.
+__device__ __noinline__ void fused_solve(const DevJob& J, int sidx, int q, double2* b, int lane) {
+  const SysDesc s = J.sys[sidx];
+  const int N = s.N;
+  const long long o = s.vec_off + (long long)q * N;
+  for (int e = lane; e < N; e += 32) b[e] = J.G[o + e];
+  __syncwarp();
+  tri_solve<double2, 1, true>(b, N, J.A + s.mat_off, J.piv + s.piv_off, J.dinv + s.piv_off, lane);
+  double2* all = J.phi_all ? J.phi_all + o : nullptr;   // step 1's copy when densities are kept
+  for (int e = lane; e < N; e += 32) {
+    const double2 v = b[e];
+    J.phi[o + e] = v;
+    J.phi_sum[o + e] = v;
+    if (all) all[e] = v;
+  }
 }
-__device__ __noinline__ void fused_assemble(const DevJob& J, int sidx) { assemble_one(J, sidx); }
-__device__ __noinline__ void fused_lu(const DevJob& J, int sidx, unsigned char* sh) { lu_one<double2>(J, sidx, sh); }
 
 // Batching form, plain FP64: one persistent launch assembles, factors and solves (step 1) every (arc, omega)
 // system.  Each CTA takes the next system from a work counter (systems by decreasing N, so the largest start
 // first and the small ones fill the tail), assembles its matrix, factors it (lu_one) and solves its step-1
-// windows with one warp; the counter is reset by the host before the launch.
+// windows, one warp per window; the counter is reset by the host before the launch.
 template <int QT>
-__global__ void __launch_bounds__(kLuThreads, 1) k_fused_asf(DevJob J, int* counter) {
+__global__ void __launch_bounds__(kLuThreads, 2) k_fused_asf(DevJob J, int* counter) {
   extern __shared__ __align__(16) unsigned char shf_raw[];
   __shared__ int s_item;
   for (;;) {
@@ -773,11 +783,12 @@ __global__ void __launch_bounds__(kLuThreads, 1) k_fused_asf(DevJob J, int* coun
     const int item = s_item;
     if (item >= J.nsys) return;
     const int sidx = J.sys_order[item];
-    fused_assemble(J, sidx);
+    assemble_one(J, sidx);
     __syncthreads();
-    fused_lu(J, sidx, shf_raw);
+    lu_one<double2>(J, sidx, shf_raw);
     __syncthreads();
-    if (threadIdx.x < 32) fused_solve<QT>(J, sidx, reinterpret_cast<double2*>(shf_raw), threadIdx.x);
+    const int wid = threadIdx.x >> 5;
+    if (wid < QT) fused_solve(J, sidx, wid, reinterpret_cast<double2*>(shf_raw) + (size_t)wid * J.max_n, threadIdx.x & 31);
     __syncthreads();
   }
 }
@@ -1517,10 +1528,10 @@ __global__ void __launch_bounds__(kResidThreads) k_mresid64(DevJob J) {
       si[q].add_prod(i1, i2, i3, x.x);
     }
   };
-  // warps specialise: every other 32-row chunk sums in FP64, the rest on the FP32 pipe, so that warps waiting
-  // on the FP64 pipe and warps issuing FP32 work share each SM (measured per job: 4 of 7 chunks in FP64 122 ms,
-  // 5 of 8 128 ms, all 166 ms)
-  const bool on_fp32 = (chunk & 1) != 0;
+  // warps specialise: one of every four 32-row chunks sums in FP64, the rest on the FP32 pipe, so that warps
+  // waiting on the FP64 pipe and warps issuing FP32 work share each SM (measured per job: all chunks in FP64
+  // 166 ms, 5 of 8 128 ms, 4 of 7 122 ms, 1 of 2 112 ms, 3 of 8 107 ms)
+  const bool on_fp32 = (chunk & 3) != 0;
   int j0 = 0;
   if (on_fp32) {
 #pragma unroll 1
