@@ -344,8 +344,9 @@ def stage_rooflines(r, problem, stored_rows):
     tpu = measured_traffic_per_unit()
     out = {}
 
-    def add(stage, kernel, bound, amount, peak, unit, note, traffic=None):
-        ms, launches = stages.get(stage, (0.0, 0))
+    def add(stage, kernel, bound, amount, peak, unit, note, traffic=None, launches=None):
+        ms, stage_launches = stages.get(stage, (0.0, 0))
+        launches = stage_launches if launches is None else launches
         if ms <= 0 or amount <= 0:
             return
         ach = amount / (ms * 1e-3) / (1e12 if unit == "TFLOP/s" else 1e9)
@@ -364,16 +365,22 @@ def stage_rooflines(r, problem, stored_rows):
         tr = tpu[name] * st["cross_entries"] * M if name in tpu else None
         add("cross_apply", name, "hbm", by, HBM_PEAK_GBS, "GB/s",
             f"every stored cross entry (16 B) read once per step{', then an ordered per-group reduce (~1% of the stage)' if prec else ''}; {hbm}",
-            traffic=tr)
+            traffic=tr, launches=M)
     if prec >= 1:
-        add("solve", "k_msolve", "hbm", 8.0 * sum_n2 * M * (1.0 + passes), HBM_PEAK_GBS, "GB/s",
-            f"the FP32 factor (8 B per entry) read once per solve pass, 1 + {passes:.3f} passes per system and step; {hbm}")
+        solve_units = sum_n2 * M * (1.0 + passes)
+        add("solve", "k_msolve", "hbm", 8.0 * solve_units, HBM_PEAK_GBS, "GB/s",
+            f"the FP32 factor (8 B per entry) read once per solve pass, 1 + {passes:.3f} passes per system and step; {hbm}",
+            traffic=tpu["k_msolve"] * solve_units if "k_msolve" in tpu else None)
         if prec == 2:
-            add("resid", "k_mresid64", "alu", 8.0 * Q * sum_n2 * M, FP64_PEAK_GFLOPS, "GFLOP/s",
-                f"first-pass residual in FP64: 8 flops per complex multiply-add per window; {fp64}")
-            add("resid_upd", "k_mresid_upd", "hbm", 16.0 * sum_n2 * M * max(passes - 1.0, 0.0), HBM_PEAK_GBS,
+            add("resid", "k_mresid64", "hbm", 16.0 * sum_n2 * M, HBM_PEAK_GBS, "GB/s",
+                f"first-pass residual to FP64 accuracy: the FP64 matrix (16 B per entry) read once per step; a "
+                f"quarter of the rows on the FP64 pipe (8 DFMA per entry, two windows), the rest exact on the FP32 "
+                f"pipe; {hbm}", traffic=tpu["k_mresid64"] * sum_n2 * M if "k_mresid64" in tpu else None)
+            upd_units = sum_n2 * M * max(passes - 1.0, 0.0)
+            add("resid_upd", "k_mresid_upd", "hbm", 16.0 * upd_units, HBM_PEAK_GBS,
                 "GB/s", f"later-pass residual updates: the FP64 matrix (16 B per entry) read once per pass, "
-                        f"{max(passes - 1.0, 0.0):.3f} passes per system and step; {hbm}")
+                        f"{max(passes - 1.0, 0.0):.3f} passes per system and step; {hbm}",
+                traffic=tpu["k_mresid_upd"] * upd_units if "k_mresid_upd" in tpu else None)
         else:
             add("resid", "k_mresid", "hbm", 16.0 * sum_n2 * M, HBM_PEAK_GBS, "GB/s",
                 f"first-pass double-float residual: the kept matrix (16 B per entry) read once; {hbm}")
@@ -404,15 +411,24 @@ def roofline_of(r, problem, stored_rows):
             "unit": "GFLOP/s", "frac": None, "traffic": None, "note": "no roofline model for this stage"}
 
 
+# The fifth configuration's bands (omega_max to 300, up to 2049 frequencies) make single requests as large as
+# the 12-arc cavity's jobs (about a minute each in FP64); the bench samples the lower part of its range.
+SERVED_WMAX = (20.0, 150.0)
+SERVED_LS = (257, 513, 1025)
+
+
 def served_vs_plain(F, ctx, n=48, seed=11, max_inflight=4, precision=1):
-    """Served stream on a bounded seeded sample shaped like the fifth configuration (disk / star cavity /
-    ellipse obstacles, 2-12 arcs, omega_max in [20, 150], 257 / 513 / 1025 frequencies, M 3-6): a saturated
-    pass (every request at t = 0) measures capacity; Poisson arrivals at 0.7 x that rate give per-request
-    latency; the plain FP64 form runs the same requests back to back through fthms_submit for comparison."""
+    """Served stream on a bounded seeded sample of the fifth configuration (disk / star cavity / ellipse
+    obstacles, 2-12 arcs, omega_max in [20, 150], 257 / 513 / 1025 frequencies, M 3-6), admitted by an HBM
+    budget of 3/4 of the free device memory: a saturated pass (every request at t = 0) measures capacity;
+    Poisson arrivals at 0.7 x that rate give per-request latency; the plain FP64 form runs the same requests
+    back to back through fthms_submit for comparison."""
+    import torch
     import workloads
-    problems = workloads.served_requests(seed, n, wmax=(20.0, 150.0), Ls=(257, 513, 1025), arcs=(2, 12))
+    problems = workloads.served_requests(seed, n, wmax=SERVED_WMAX, Ls=SERVED_LS, arcs=(2, 12))
     solves = sum(solves_of(p) for p in problems)
-    srv = F.Server(0, 0, max_inflight=max_inflight)
+    budget = int(0.75 * torch.cuda.mem_get_info()[0])
+    srv = F.Server(0, budget, max_inflight=max_inflight)
     for p in problems[:2]:
         t = srv.submit(p, precision=precision)
         srv.wait(t)
@@ -461,10 +477,11 @@ def served_vs_plain(F, ctx, n=48, seed=11, max_inflight=4, precision=1):
             "saturated_solves_per_s": float(solves / makespan),
             "plain_fp64_same_mix_solves_per_s": float(solves / plain_s),
             "vs_plain_same_mix": float(plain_s / makespan), "arrival_rate_per_s": rate, "requests": n,
-            "max_inflight": max_inflight, "precision": precision,
-            "sample": f"{n} seeded requests (disk / star cavity / 1-5 ellipses, 2-12 arcs, omega_max in [20, 150], "
-                      f"257 / 513 / 1025 frequencies, M 3-6), Poisson arrivals at 0.7 x saturated capacity; "
-                      f"vs_plain_same_mix = the same requests in FP64 back to back through fthms_submit"}
+            "max_inflight": max_inflight, "precision": precision, "hbm_budget_gb": budget / 1e9,
+            "sample": f"{n} seeded requests (disk / star cavity / 1-5 ellipses, 2-12 arcs, omega_max in "
+                      f"[{SERVED_WMAX[0]:g}, {SERVED_WMAX[1]:g}], {' / '.join(map(str, SERVED_LS))} frequencies, "
+                      f"M 3-6), Poisson arrivals at 0.7 x saturated capacity; vs_plain_same_mix = the same "
+                      f"requests in FP64 back to back through fthms_submit"}
 
 
 def ours(args):

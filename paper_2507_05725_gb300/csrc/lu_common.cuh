@@ -47,6 +47,59 @@ __device__ void panel_factor_warp(C* Pn, int ps, int nr, int w, int* spiv, int l
   }
 }
 
+// The same factorisation by a whole block of NT threads (the same pivots, the same arithmetic per entry, so
+// the same factor bit for bit): per column, the pivot search over rows split across the threads (warp
+// shuffles, then the NT / 32 warp results in red_m / red_i, reduced by every thread), the swap, then the
+// scaling and rank-1 update with rows split across the threads; three block barriers per column.
+template <class C, int NT>
+__device__ void panel_factor_block(C* Pn, int ps, int nr, int w, int* spiv,
+                                   typename CTraits<C>::R* red_m, int* red_i) {
+  using Real = typename CTraits<C>::R;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  for (int c = 0; c < w; ++c) {
+    Real best = -1;
+    int bi = 0x7fffffff;
+    for (int r = c + tid; r < nr; r += NT) {
+      C v = Pn[r * ps + c];
+      Real m = fabs(v.x) + fabs(v.y);
+      if (m > best) { best = m; bi = r; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      Real ov = __shfl_xor_sync(0xffffffffu, best, o);
+      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    }
+    if (lane == 0) {
+      red_m[wid] = best;
+      red_i[wid] = bi;
+    }
+    __syncthreads();
+    best = red_m[0];
+    bi = red_i[0];
+#pragma unroll
+    for (int k = 1; k < NT / 32; ++k) {
+      const Real ov = red_m[k];
+      const int oi = red_i[k];
+      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    }
+    const int p = bi == 0x7fffffff ? c : bi;
+    if (tid == 0) spiv[c] = p;
+    if (p != c && tid < w) {
+      C t = Pn[c * ps + tid];
+      Pn[c * ps + tid] = Pn[p * ps + tid];
+      Pn[p * ps + tid] = t;
+    }
+    __syncthreads();
+    const C inv = crecip(Pn[c * ps + c]);
+    for (int r = c + 1 + tid; r < nr; r += NT) {
+      C lr = cmul(Pn[r * ps + c], inv);
+      Pn[r * ps + c] = lr;
+      for (int cc = c + 1; cc < w; ++cc) Pn[r * ps + cc] = cfms(lr, Pn[c * ps + cc], Pn[r * ps + cc]);
+    }
+    __syncthreads();
+  }
+}
+
 // Finish the factor P A = L U (column-major N x N in A, unit lower L below the diagonal, U on and above)
 // for the blocked triangular solves, by all NT threads of a block: U = D U' with unit-diagonal U' (dinv
 // receives 1/U_kk, the rows of U right of the diagonal are scaled), then the kSB x kSB diagonal blocks of

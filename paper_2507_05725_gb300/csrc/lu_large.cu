@@ -49,19 +49,22 @@ __device__ __forceinline__ int part_off(int r, int k) {
   return (r & 7) * 16 + (r >> 3) * kSBO + (k & 3) * 4 + (k >> 2) * 128;
 }
 
-// Outer panel k0 of every large system with N > k0 (kPanelThreads threads per system).
+// Outer panel k0 of every large system with N > k0 (kPanelThreads threads per system; the 8-column inner
+// panels factored by the whole block).
 __global__ void __launch_bounds__(kPanelThreads) k_lu_big_panel(DevJob J, int k0) {
   extern __shared__ __align__(16) unsigned char sh_raw[];
   float2* Pn = reinterpret_cast<float2*>(sh_raw);   // [N - k1][kInnerPS] inner panel rows
   __shared__ float2 U[kInner][kOuter];              // inner U12 rows within the outer panel
   __shared__ float2 L11[kOuter][kOuter + 1];        // unit-lower block of the outer panel (row-major)
   __shared__ int spiv[kInner];
+  __shared__ float red_m[kPanelThreads / 32];
+  __shared__ int red_i[kPanelThreads / 32];
   const SysDesc s = J.sys[J.lu_big[blockIdx.x]];
   const int N = s.N;
   if (k0 >= N) return;
   float2* A = J.LU32 + s.mat_off;
   int* piv = J.piv + s.piv_off;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int tid = threadIdx.x;
   const int nbo = min(kOuter, N - k0), kend = k0 + nbo;
   for (int k1 = k0; k1 < kend; k1 += kInner) {
     const int w = min(kInner, kend - k1), nr = N - k1;
@@ -70,12 +73,8 @@ __global__ void __launch_bounds__(kPanelThreads) k_lu_big_panel(DevJob J, int k0
       Pn[r * kInnerPS + c] = A[(long long)(k1 + c) * N + k1 + r];
     }
     __syncthreads();
-    if (wid == 0) {
-      panel_factor_warp<float2>(Pn, kInnerPS, nr, w, spiv, lane);
-      __syncwarp();
-      if (lane < w) piv[k1 + lane] = k1 + spiv[lane];
-    }
-    __syncthreads();
+    panel_factor_block<float2, kPanelThreads>(Pn, kInnerPS, nr, w, spiv, red_m, red_i);
+    if (tid < w) piv[k1 + tid] = k1 + spiv[tid];
     for (int idx = tid; idx < nr * w; idx += kPanelThreads) {
       const int c = idx / nr, r = idx % nr;
       A[(long long)(k1 + c) * N + k1 + r] = Pn[r * kInnerPS + c];
