@@ -91,8 +91,9 @@ constexpr int kOtfBand = 16;
 template <int Q> struct OtfBand { static constexpr int value = kOtfBand / Q > 4 ? kOtfBand / Q : 4; };
 inline int otf_band(int Q) { return kOtfBand / Q > 4 ? kOtfBand / Q : 4; }   // host side of OtfBand
 // Mixed forms: the double-float every-step kernel evaluates a (row, source) pair for bands of up to
-// kOtfBandDf frequencies (its per-pair FP64 set-up amortised over the band).
-constexpr int kOtfBandDf = 32;
+// kOtfBandDf frequencies (its per-pair set-up amortised over the band; 16 rather than 32 leaves room for more
+// CTAs per SM).
+constexpr int kOtfBandDf = 16;
 struct CrossOtf {
   int task;
   int l0, l1;

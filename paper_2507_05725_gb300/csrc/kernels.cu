@@ -1163,7 +1163,7 @@ __global__ void __launch_bounds__(kAsmThreads) k_cross_otf(DevJob J) {
 // The per-row sums go to the per-row results that k_cross_reduce adds per target in block order.
 constexpr int kOtfDfSrc = 16;
 constexpr int kOtfDfThreads = kAsmRows * kOtfDfSrc;   // 128
-constexpr int kOtfDfPitch = kOtfBandDf + 1;           // float4 per shared-memory row (33: no bank conflicts)
+constexpr int kOtfDfPitch = kOtfBandDf + 1;           // float4 per shared-memory row (odd: no bank conflicts)
 
 // sin and cos of theta >= 0 (FP64, up to ~2e4) as double-float: theta reduced by n pi/2 in FP64 (pi/2 as the
 // sum of two doubles), the remainder's double-float Taylor series, the quadrant n mod 4.
