@@ -417,7 +417,7 @@ SERVED_WMAX = (20.0, 150.0)
 SERVED_LS = (257, 513, 1025)
 
 
-def served_vs_plain(F, ctx, n=48, seed=11, max_inflight=4, precision=1):
+def served_vs_plain(F, ctx, n=48, seed=11, max_inflight=4, precision=1, wmax=None, Ls=None):
     """Served stream on a bounded seeded sample of the fifth configuration (disk / star cavity / ellipse
     obstacles, 2-12 arcs, omega_max in [20, 150], 257 / 513 / 1025 frequencies, M 3-6), admitted by an HBM
     budget of 3/4 of the free device memory: a saturated pass (every request at t = 0) measures capacity;
@@ -425,7 +425,8 @@ def served_vs_plain(F, ctx, n=48, seed=11, max_inflight=4, precision=1):
     back to back through fthms_submit for comparison."""
     import torch
     import workloads
-    problems = workloads.served_requests(seed, n, wmax=SERVED_WMAX, Ls=SERVED_LS, arcs=(2, 12))
+    wmax, Ls = wmax or SERVED_WMAX, Ls or SERVED_LS
+    problems = workloads.served_requests(seed, n, wmax=wmax, Ls=Ls, arcs=(2, 12))
     solves = sum(solves_of(p) for p in problems)
     budget = int(0.75 * torch.cuda.mem_get_info()[0])
     srv = F.Server(0, budget, max_inflight=max_inflight)
@@ -479,7 +480,7 @@ def served_vs_plain(F, ctx, n=48, seed=11, max_inflight=4, precision=1):
             "vs_plain_same_mix": float(plain_s / makespan), "arrival_rate_per_s": rate, "requests": n,
             "max_inflight": max_inflight, "precision": precision, "hbm_budget_gb": budget / 1e9,
             "sample": f"{n} seeded requests (disk / star cavity / 1-5 ellipses, 2-12 arcs, omega_max in "
-                      f"[{SERVED_WMAX[0]:g}, {SERVED_WMAX[1]:g}], {' / '.join(map(str, SERVED_LS))} frequencies, "
+                      f"[{wmax[0]:g}, {wmax[1]:g}], {' / '.join(map(str, Ls))} frequencies, "
                       f"M 3-6), Poisson arrivals at 0.7 x saturated capacity; vs_plain_same_mix = the same "
                       f"requests in FP64 back to back through fthms_submit"}
 
@@ -682,10 +683,33 @@ def main():
     ap.add_argument("--no-c3", action="store_true", help="skip the 12-arc cavity form")
     ap.add_argument("--no-plain", action="store_true", help="skip the FP64 reference job (no in-run error check)")
     ap.add_argument("--plain-only", action="store_true", help="time the plain FP64 form only (profiling runs)")
+    ap.add_argument("--served-only", action="store_true",
+                    help="only the served stream against the plain FP64 form on the same requests, one JSON line")
+    ap.add_argument("--served-n", type=int, default=48, help="requests of --served-only")
+    ap.add_argument("--served-wmax", type=float, default=SERVED_WMAX[1],
+                    help="largest omega_max of --served-only (the fifth configuration's range ends at 300)")
+    ap.add_argument("--served-ls", default=",".join(map(str, SERVED_LS)),
+                    help="frequency counts of --served-only (the fifth configuration's: 257,513,1025,2049)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.served_only:
+        return served_only(args)
     return ours(args)
+
+
+def served_only(args):
+    """The served stream on a chosen sample of the fifth configuration's ranges (bounded by the time a GPU run
+    may take: its plain FP64 pass runs the requests one after another)."""
+    import torch
+    from paper_2507_05725_gb300 import fthms as F
+    torch.cuda.set_device(0)
+    ctx = F.fthms_create(0, 0, None)
+    r = served_vs_plain(F, ctx, n=args.served_n, wmax=(SERVED_WMAX[0], args.served_wmax),
+                        Ls=tuple(int(v) for v in args.served_ls.split(",")))
+    F.fthms_destroy(ctx)
+    print(json.dumps({"metric": METRIC, "served": r}))
+    return 0
 
 
 if __name__ == "__main__":
