@@ -942,6 +942,10 @@ __device__ __forceinline__ double2 asym_entry(AsymState& a, const PairSetup& s, 
   return make_double2(amp * fma(s.beta, t1, -t2), amp * t1);
 }
 
+// kNear: the launch over the tasks with near rows (shared memory for their product-integration weights);
+// otherwise over the far-only tasks, which need only the band tables (more CTAs per SM).  Each launch skips
+// the other kind of task.
+template <bool kNear>
 __global__ void __launch_bounds__(kAsmMaxThreads) k_cross_assemble(DevJob J) {
   extern __shared__ double sha[];
   const CrossAsm task = J.asms[blockIdx.x];
@@ -949,9 +953,9 @@ __global__ void __launch_bounds__(kAsmMaxThreads) k_cross_assemble(DevJob J) {
   const int N = task.N;
   const Panel pn = J.panels[task.panel];
   const CrossTgt* tg = J.tgts + pr.tgt_off + task.row0;
-  double* ctab = sha;                       // 4N: cospi(r/(2N))
-  double* lam = sha + 4 * N;                // kAsmRows x N
-  double* Wn = lam + kAsmRows * N;          // kAsmRows x N near weights
+  double* ctab = sha;                                // 4N: cospi(r/(2N))
+  double* lam = sha + 4 * N;                         // kAsmRows x N
+  double* Wn = kNear ? lam + kAsmRows * N : sha;     // kAsmRows x N near weights (near launch only)
   __shared__ int any_near;
   if (threadIdx.x == 0) {
     int a = 0;
@@ -959,7 +963,8 @@ __global__ void __launch_bounds__(kAsmMaxThreads) k_cross_assemble(DevJob J) {
     any_near = a;
   }
   __syncthreads();
-  if (any_near) near_weights_block(tg, task.nrows, N, ctab, lam, Wn);
+  if ((any_near != 0) != kNear) return;
+  if (kNear) near_weights_block(tg, task.nrows, N, ctab, lam, Wn);
   const double w = kPiD / N, qw = 0.25 * w, invw = N * kInvPi;
   const double A1 = -0.5 * kInvPi * w;          // coefficient of ln l below z = 20
   const double camp = kSqrtTwoOverPi * qw;      // sqrt(2/pi) w/4
@@ -967,7 +972,7 @@ __global__ void __launch_bounds__(kAsmMaxThreads) k_cross_assemble(DevJob J) {
   const int ld = pr.nrows;   // blocks are stored source-major: E[i * nrows + row]
   const int nl = task.l1 - task.l0 + 1;
   // per-band tables: 1/l, 1/sqrt(l), ln l and omega_l = l h
-  double* invl = Wn + kAsmRows * N;          // <= kAsmBand each
+  double* invl = kNear ? Wn + kAsmRows * N : sha;    // <= kAsmBand each
   double* rsql = invl + kAsmBand;
   double* lnl = rsql + kAsmBand;
   double* lh = lnl + kAsmBand;
@@ -994,7 +999,7 @@ __global__ void __launch_bounds__(kAsmMaxThreads) k_cross_assemble(DevJob J) {
     const int r = e % task.nrows, i = e / task.nrows;
     const CrossTgt t = tg[r];
     const PairSetup ps = pair_setup(J, t, J.node_x[pn.off + i], J.node_y[pn.off + i], J.node_t[pn.off + i],
-                                    t.near ? Wn[r * N + i] : 0.0, task.l0, w, invw, inv_h);
+                                    kNear && t.near ? Wn[r * N + i] : 0.0, task.l0, w, invw, inv_h);
     double2* Ep = J.E + (long long)i * ld + task.row0 + r;
     const int lend = min(ps.lsw, task.l1 + 1);
     if (J.mixed && !J.fp64keep) {
@@ -2393,11 +2398,15 @@ cudaError_t launch_cross_assemble(const DevJob& J, cudaStream_t st, int* launche
   // Shared layout of k_cross_assemble, in 8-byte words: ctab 4N, lam kAsmRows N, Wn kAsmRows N, then
   // band tables invl, rsql, lnl, lh (doubles) and invl_d, rsql_d, lnl_d, lh_d (double-float pairs),
   // kAsmBand each.
-  size_t sh = ((size_t)(4 + 2 * kAsmRows) * J.max_n + 8 * kAsmBand) * sizeof(double);
-  cudaError_t e = cudaFuncSetAttribute(k_cross_assemble, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+  // (the far-only launch: the band tables alone)
+  const size_t sh = ((size_t)(4 + 2 * kAsmRows) * J.max_n + 8 * kAsmBand) * sizeof(double);
+  const size_t sh_far = (size_t)8 * kAsmBand * sizeof(double);
+  const int nt = J.shape_asm > 0 ? J.shape_asm : kAsmThreads;
+  cudaError_t e = cudaFuncSetAttribute(k_cross_assemble<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
   if (e != cudaSuccess) return e;
-  k_cross_assemble<<<J.n_asm, J.shape_asm > 0 ? J.shape_asm : kAsmThreads, sh, st>>>(J);
-  *launches += 1;
+  k_cross_assemble<true><<<J.n_asm, nt, sh, st>>>(J);
+  k_cross_assemble<false><<<J.n_asm, nt, sh_far, st>>>(J);
+  *launches += 2;
   return cudaGetLastError();
 }
 
