@@ -1814,12 +1814,31 @@ __global__ void __launch_bounds__(32 * kSolveWarps, 3) k_msolve(DevJob J, int m,
   }
 }
 
+// Asynchronous 16-byte copies global -> shared (bypassing L1), for streams whose loads would otherwise
+// occupy registers until they land.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int kPending>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(kPending) : "memory");
+}
+
+// Entries of a row per batch of the mixed-form cross apply (even: two alternating accumulator sets).
+__host__ __device__ constexpr int apply_batch(int Q) { return Q == 1 ? 8 : Q == 2 ? 6 : 4; }
+constexpr int kApplyStages = 2;   // batches per thread in shared memory: one summed while the next lands
+
 // Cross apply in double-float on the FP32 pipe (mixed form): E and phi as df64, compensated sums.
 // Mixed form, first half: one CTA per slice of kApplySlice rows of a group, one thread per row, the
-// row's double-float sum over its block's sources (E and phi as df64, two compensated sums).  No
-// barrier after the density staging, and many small CTAs per SM keep enough loads in flight.
+// row's double-float sum over its block's sources (E and phi as df64, two compensated sums).  The row's
+// entries stream through a per-thread ring of kApplyStages batches in shared memory (cp.async): batch
+// b + 1 is in flight while batch b is summed, so the loads never wait for the FP32 pipe and hold no
+// registers.  A thread reads only the slots it filled itself (no barrier).
 template <int Q>
 __global__ void __launch_bounds__(kApplySlice, 3) k_cross_rows_df(DevJob J) {
+  extern __shared__ __align__(16) float4 she[];     // [kApplyStages][kB][kApplySlice]
   const ApplySlice sl = J.slices[blockIdx.x];
   if ((int)threadIdx.x >= sl.nrows) return;
   const int row = sl.row0 + threadIdx.x;
@@ -1835,23 +1854,38 @@ __global__ void __launch_bounds__(kApplySlice, 3) k_cross_rows_df(DevJob J) {
   const float4* __restrict__ phb = J.phi_df + J.sys[B.sys].vec_off;
   dfacc sr[Q], si[Q], tr[Q], ti[Q];
   const float4* __restrict__ Er = reinterpret_cast<const float4*>(J.E + B.e_off) + r;
-  int i = 0;
-  // kB entries of the row loaded before their sums (two alternating accumulator sets)
-  constexpr int kB = Q == 1 ? 8 : Q == 2 ? 6 : 4;
-#pragma unroll 1
-  for (; i + kB <= N; i += kB) {
-    float4 e[kB];
+  constexpr int kB = apply_batch(Q);
+  const int nbat = N / kB;
+  float4* mine = she + threadIdx.x;
+  auto issue = [&](int bi) {
+    float4* dst = mine + (bi % kApplyStages) * kB * kApplySlice;
+    const float4* src = Er + (long long)bi * kB * nr;
 #pragma unroll
-    for (int k = 0; k < kB; ++k) e[k] = __ldg(&Er[(long long)(i + k) * nr]);
+    for (int k = 0; k < kB; ++k) cp_async16(dst + k * kApplySlice, src + (long long)k * nr);
+  };
+#pragma unroll
+  for (int bi = 0; bi < kApplyStages - 1; ++bi) {
+    if (bi < nbat) issue(bi);
+    cp_async_commit();
+  }
+#pragma unroll 1
+  for (int bi = 0; bi < nbat; ++bi) {
+    if (bi + kApplyStages - 1 < nbat) issue(bi + kApplyStages - 1);
+    cp_async_commit();                          // (empty near the end: keeps the group count uniform)
+    cp_async_wait<kApplyStages - 1>();          // batch bi has landed
+    const float4* src = mine + (bi % kApplyStages) * kB * kApplySlice;
+    const int i = bi * kB;
 #pragma unroll
     for (int k = 0; k < kB; k += 2) {
+      const float4 e0 = src[k * kApplySlice], e1 = src[(k + 1) * kApplySlice];
 #pragma unroll
       for (int q = 0; q < Q; ++q) {
-        cdf_mac(sr[q], si[q], e[k], __ldg(&phb[q * N + i + k]));
-        cdf_mac(tr[q], ti[q], e[k + 1], __ldg(&phb[q * N + i + k + 1]));
+        cdf_mac(sr[q], si[q], e0, __ldg(&phb[q * N + i + k]));
+        cdf_mac(tr[q], ti[q], e1, __ldg(&phb[q * N + i + k + 1]));
       }
     }
   }
+  int i = nbat * kB;
   for (; i + 1 < N; i += 2) {
     const float4 e0 = __ldg(&Er[(long long)i * nr]);
     const float4 e1 = __ldg(&Er[(long long)(i + 1) * nr]);
@@ -2558,7 +2592,8 @@ cudaError_t launch_resid(const DevJob& J, int pass, cudaStream_t st, int* launch
 template <int Q>
 static cudaError_t launch_cross_apply_q(const DevJob& J, size_t sh, cudaStream_t st) {
   if (J.mixed) {
-    const size_t sh_rows = 0;   // the row kernel reads the densities through the L1 cache
+    // the row kernel's ring of entry batches (the densities come through the L1 cache)
+    const size_t sh_rows = (size_t)kApplyStages * apply_batch(Q) * kApplySlice * sizeof(float4);
     const size_t sh_red = (size_t)Q * J.acc_cap * sizeof(double2);
     cudaError_t e = cudaFuncSetAttribute(k_cross_rows_df<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh_rows);
     if (e != cudaSuccess) return e;
