@@ -374,8 +374,8 @@ def stage_rooflines(r, problem, stored_rows):
         if prec == 2:
             add("resid", "k_mresid64", "hbm", 16.0 * sum_n2 * M, HBM_PEAK_GBS, "GB/s",
                 f"first-pass residual to FP64 accuracy: the FP64 matrix (16 B per entry) read once per step; a "
-                f"quarter of the rows on the FP64 pipe (8 DFMA per entry, two windows), the rest exact on the FP32 "
-                f"pipe; {hbm}", traffic=tpu["k_mresid64"] * sum_n2 * M if "k_mresid64" in tpu else None)
+                f"sixth of the rows on the FP64 pipe (8 DFMA per entry, two windows), the rest in anchored sums of "
+                f"exact products on the FP32 pipe; {hbm}", traffic=tpu["k_mresid64"] * sum_n2 * M if "k_mresid64" in tpu else None)
             upd_units = sum_n2 * M * max(passes - 1.0, 0.0)
             add("resid_upd", "k_mresid_upd", "hbm", 16.0 * upd_units, HBM_PEAK_GBS,
                 "GB/s", f"later-pass residual updates: the FP64 matrix (16 B per entry) read once per pass, "

@@ -286,27 +286,50 @@ __device__ __forceinline__ void split3_f64_bits(double a, float& a1, float& a2, 
   a3 = low ? __uint_as_float(sign | (__float_as_uint(__uint2float_rn(low)) + ((unsigned int)(e - 1075) << 23))) : 0.f;
 }
 
-// A sum of products a x (a = a1 + a2 + a3 from split3_f64_bits, x a float) kept exactly in three float levels:
-// h collects the rounded leading products by Knuth's two-sum, m collects (again by two-sums) h's errors and
-// the next-order terms (the exact error of a1 x by the FMA two-product, a2 x), l the rest with plain adds
-// (terms ~2^-48 of a product, so its rounding stays near 2^-70 of the sum of |products|): more accurate than an
-// FP64 accumulation, on the FP32 pipe.
-struct xacc {
-  float h = 0.f, m = 0.f, l = 0.f;
+// Anchored sums of products a x (a = a1 + a2 + a3 the exact three-float split, x a float) on the FP32 pipe,
+// by error-free extraction against fixed power-of-two anchors (the "ExtractScalar" step of Rump, Ogita and
+// Oishi's accurate summation, 2008).  With every partial sum of |a x| below 2^(kh-1), H starts at
+// 1.5 2^kh and stays in [2^kh, 2^(kh+1)]: t = H + p1 and q = t - H are exact (Sterbenz), and p1 - q is the
+// exact part of p1 below H's ulp (Fast2Sum, |H| >= |p1|).  Those parts, the product errors e1 (FMA
+// two-product) and a2 x go the same way into M, anchored at 1.5 2^km (km = kh - 23 + ceil(log2(T + 4)) for
+// T terms, so M too stays in its binade); a2 x through one FMA (M + a2 x rounded once, then the exact
+// q and the rest a2 x - q rounded once more, ~2^(km-47)).  What falls below M's ulp, and a3 x, are added
+// plainly in l, which renorm() folds back into M.  18 FP32 instructions a product instead of the 34 that
+// exact three-level two-sums take; the error, about 2^-50 of the sum of |a x| (the anchors' scale), is of
+// the order of an FP64 accumulation's.
+struct aacc {
+  float H, M, l, sh, sm;
+  __device__ __forceinline__ void init(int kh, int km) {     // -126 < km < kh < 128
+    H = sh = __uint_as_float(((unsigned)(127 + kh) << 23) | 0x400000u);   // 1.5 2^kh
+    M = sm = __uint_as_float(((unsigned)(127 + km) << 23) | 0x400000u);
+    l = 0.f;
+  }
+  __device__ __forceinline__ void put_m(float v) {      // |v| <= |M| / 2: exact split into M's grid and l
+    const float t = __fadd_rn(M, v);
+    l = __fadd_rn(l, __fsub_rn(v, __fsub_rn(t, M)));
+    M = t;
+  }
   __device__ __forceinline__ void add_prod(float a1, float a2, float a3, float x) {
     const float p1 = __fmul_rn(a1, x), e1 = fmaf(a1, x, -p1);
-    const float p2 = __fmul_rn(a2, x), e2 = fmaf(a2, x, -p2);
-    const float p3 = __fmul_rn(a3, x);
-    float s, t0, u1, u2, u3;
-    two_sum(h, p1, s, t0);
-    h = s;
-    two_sum(m, t0, s, u1);
-    two_sum(s, e1, m, u2);
-    two_sum(m, p2, s, u3);
-    m = s;
-    l = __fadd_rn(l, __fadd_rn(__fadd_rn(u1, u2), __fadd_rn(u3, __fadd_rn(e2, p3))));
+    const float t = __fadd_rn(H, p1);
+    const float r1 = __fsub_rn(p1, __fsub_rn(t, H));
+    H = t;
+    put_m(r1);
+    put_m(e1);
+    const float u = fmaf(a2, x, M);
+    const float q = __fsub_rn(u, M);
+    l = __fadd_rn(l, fmaf(a2, x, -q));
+    M = u;
+    l = fmaf(a3, x, l);
   }
-  __device__ __forceinline__ double value() const { return ((double)l + (double)m) + (double)h; }
+  __device__ __forceinline__ void renorm() {       // l's high part into M (exact), keeping l small
+    const float t = __fadd_rn(M, l);
+    l = __fsub_rn(l, __fsub_rn(t, M));
+    M = t;
+  }
+  __device__ __forceinline__ double value() const {
+    return ((double)__fsub_rn(H, sh) + (double)__fsub_rn(M, sm)) + (double)l;
+  }
 };
 
 }  // namespace fthms

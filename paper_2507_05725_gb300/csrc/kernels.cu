@@ -1487,12 +1487,56 @@ constexpr int kResidThreads = 128;
 template <int Q>
 __global__ void __launch_bounds__(kResidThreads) k_mresid(DevJob J);
 
+// Asynchronous 16-byte copies global -> shared (bypassing L1), for streams whose loads would otherwise
+// occupy registers until they land.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int kPending>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(kPending) : "memory");
+}
+
+// Per row of the systems that keep FP64, an upper bound of sum_j (|Re a_ij| + |Im a_ij|) in FP32, once per job
+// after the assembly: each |a| bounded from above by its 23 leading fraction bits times (1 + 2^-22), the sum
+// of N such floats by (1 + 2^-10) for its roundings (N 2^-24 < 2^-10).  The first-pass residual sizes the
+// anchors of its FP32-pipe sums from it.
+__device__ __forceinline__ float abs_bound_f32(double a) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(a) & 0x7FFFFFFFFFFFFFFFull;
+  const int e = (int)(u >> 52);
+  if (e >= 1023 + 127) return __uint_as_float(0x7F800000u);   // beyond FP32 (or not finite): +inf
+  if (e < 1023 - 126) return 0x1p-126f;                       // below FP32's normal range
+  const unsigned frac23 = (unsigned)(u >> 29) & 0x7FFFFFu;
+  return __fmul_rn(__uint_as_float(((unsigned)(e - 1023 + 127) << 23) | frac23), 1.f + 0x1p-22f);
+}
+__global__ void __launch_bounds__(kResidThreads) k_arow_norms(DevJob J) {
+  const int chunk = blockIdx.x * (kResidThreads / 32) + (threadIdx.x >> 5);
+  if (chunk >= J.n_rchunks) return;
+  const ResidChunk c = J.rchunks[chunk];
+  const SysDesc s = J.sys[c.sys];
+  const int N = s.N;
+  if (!sys_f64(J, N)) return;
+  const int i = c.row0 + (threadIdx.x & 31);
+  if (i >= N) return;
+  const double2* __restrict__ A64 = J.A + s.mat_off;
+  float acc = 0.f;
+#pragma unroll 4
+  for (int j = 0; j < N; ++j) {
+    const double2 a = __ldg(&A64[(long long)j * N + i]);
+    acc = __fadd_rn(acc, __fadd_rn(abs_bound_f32(a.x), abs_bound_f32(a.y)));
+  }
+  J.arow[s.piv_off + i] = __fmul_rn(acc, 1.f + 0x1p-10f);
+}
+
 // The first-pass residual of the systems that keep FP64 (all in the FP64-kept form), to FP64 accuracy on both
 // arithmetic pipes at once: phi_0 is the FP32 solution (exactly a float), so every product a_ij phi_j can be
 // formed exactly from a three-float split of the FP64 entry.  A warp sums its rows either through FP64 FMAs
-// (acc) or through exact products and exact two-level sums on the FP32 pipe (xacc); the FP64 pipe, which alone
-// would bound the kernel at 8 DFMA per entry and two windows, and the FP32 pipe then work side by side.
-// The result, G - A phi_0, is as accurate as an all-FP64 accumulation or more.
+// (acc) or through those products and anchored sums on the FP32 pipe (aacc, anchors sized from the row's
+// bound arow * phimax); the FP64 pipe, which alone would bound the kernel at 8 DFMA per entry and two
+// windows, and the FP32 pipe then work side by side.  Either way G - A phi_0 comes out with an error of
+// the order of an FP64 accumulation's (about 2^-50 of sum_j |a_ij phi_j|).
 template <int Q>
 __global__ void __launch_bounds__(kResidThreads) k_mresid64(DevJob J) {
   const int chunk = blockIdx.x * (kResidThreads / 32) + (threadIdx.x >> 5);
@@ -1510,11 +1554,24 @@ __global__ void __launch_bounds__(kResidThreads) k_mresid64(DevJob J) {
   const double2* __restrict__ G = J.G + s.vec_off;
   const double isc = 1.0 / J.mscale[c.sys];   // a power of two: exact
   double2 acc[Q];
-  xacc sr[Q], si[Q];
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
     const double2 g = G[q * N + row];
     acc[q] = make_double2(g.x * isc, g.y * isc);
+  }
+  // Anchors of the FP32-pipe sums: every partial sum of |a phi_0| along the row stays below
+  // bnd = sum_j (|Re a_ij| + |Im a_ij|) max |phi_0| (both bounded from above), below 2^(kh-1) with kh = e + 3
+  // for bnd in [2^e, 2^(e+1)).  A chunk with a row outside the anchors' range sums in FP64.
+  const float bnd = J.arow[s.piv_off + row] * J.phimax[c.sys] * (1.f + 0x1p-20f);
+  const int be = (int)((__float_as_uint(bnd) >> 23) & 0xFFu) - 127;
+  const int kh = bnd > 0.f ? be + 3 : 0;                   // (bnd = 0: every product is zero)
+  const int km = kh - 23 + (32 - __clz(2 * N + 3));        // ceil(log2(T + 4)), T = 2N terms a sum
+  const bool anchors_ok = bnd == 0.f || (be >= -40 && be <= 100);
+  aacc sr[Q], si[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    sr[q].init(kh, km);
+    si[q].init(kh, km);
   }
   auto col64 = [&](const double2 a, int j) {
 #pragma unroll
@@ -1533,10 +1590,10 @@ __global__ void __launch_bounds__(kResidThreads) k_mresid64(DevJob J) {
       si[q].add_prod(i1, i2, i3, x.x);
     }
   };
-  // warps specialise: one of every four 32-row chunks sums in FP64, the rest on the FP32 pipe, so that warps
-  // waiting on the FP64 pipe and warps issuing FP32 work share each SM (measured per job: all chunks in FP64
-  // 166 ms, 5 of 8 128 ms, 4 of 7 122 ms, 1 of 2 112 ms, 3 of 8 107 ms)
-  const bool on_fp32 = (chunk & 3) != 0;
+  // warps specialise: one of every six 32-row chunks sums in FP64, the rest on the FP32 pipe, so that warps
+  // waiting on the FP64 pipe and warps issuing FP32 work share each SM (measured per job, N = 512: one chunk
+  // in three on the FP64 pipe 91.6 ms, in four 79.9, in six 76.6, in eight 80.6)
+  const bool on_fp32 = (chunk % 6) != 0 && __all_sync(0xffffffffu, anchors_ok);
   int j0 = 0;
   if (on_fp32) {
 #pragma unroll 1
@@ -1546,6 +1603,11 @@ __global__ void __launch_bounds__(kResidThreads) k_mresid64(DevJob J) {
       for (int k = 0; k < 4; ++k) a[k] = __ldg(&A64[(long long)(j0 + k) * N + row]);
 #pragma unroll
       for (int k = 0; k < 4; ++k) colx(a[k], j0 + k);
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        sr[q].renorm();
+        si[q].renorm();
+      }
     }
     for (; j0 < N; ++j0) colx(__ldg(&A64[(long long)j0 * N + row]), j0);
   } else {
@@ -1739,10 +1801,14 @@ __global__ void __launch_bounds__(32 * kSolveWarps, 3) k_msolve(DevJob J, int m,
   float2* dc = J.dcorr + s.vec_off;
   if (pass == 0) {
     if (f64) {
+      float pm = 0.f;
       for (int e = lane; e < Q * N; e += 32) {
         ph64[e] = make_double2(b[e].x, b[e].y);
         dc[e] = b[e];                         // phi_0 as floats for the first residual's FP32-pipe columns
+        pm = fmaxf(pm, fmaxf(fabsf(b[e].x), fabsf(b[e].y)));
       }
+      for (int o = 16; o > 0; o >>= 1) pm = fmaxf(pm, __shfl_xor_sync(0xffffffffu, pm, o));
+      if (lane == 0) J.phimax[sidx] = pm;     // the first residual's anchors
     } else {
       for (int e = lane; e < Q * N; e += 32) ph[e] = make_float4(b[e].x, 0.f, b[e].y, 0.f);
     }
@@ -1812,18 +1878,6 @@ __global__ void __launch_bounds__(32 * kSolveWarps, 3) k_msolve(DevJob J, int m,
     sum[e] = m == 1 ? v : cadd(sum[e], v);
     if (all) all[e] = v;
   }
-}
-
-// Asynchronous 16-byte copies global -> shared (bypassing L1), for streams whose loads would otherwise
-// occupy registers until they land.
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int kPending>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(kPending) : "memory");
 }
 
 // Entries of a row per batch of the mixed-form cross apply (even: two alternating accumulator sets).
@@ -2364,6 +2418,13 @@ cudaError_t launch_tables_rlog_only(const DevJob& J, cudaStream_t st, int* launc
 cudaError_t launch_assemble_self(const DevJob& J, cudaStream_t st, int* launches) {
   if (J.n_tiles > 0) {
     k_assemble_self<<<J.n_tiles, 256, 0, st>>>(J);
+    *launches += 1;
+  }
+  // the row bounds of the FP64 matrices, for the first-pass residual's anchors
+  const bool any64 = J.mixed && (J.fp64keep || J.max_n >= J.f64_min_n);
+  const int rgrid = cdiv(J.n_rchunks, kResidThreads / 32);
+  if (any64 && J.arow && rgrid > 0) {
+    k_arow_norms<<<rgrid, kResidThreads, 0, st>>>(J);
     *launches += 1;
   }
   return cudaGetLastError();

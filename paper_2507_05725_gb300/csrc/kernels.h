@@ -87,6 +87,8 @@ struct DevJob {
   float* mrel;               // per system: relative size of its last correction (mixed form)
   float* mrho;               // per system: largest contraction factor measured in earlier steps (0: none yet)
   double* mscale;            // per system and step: power of two near max |G|; refinement runs in G / mscale
+  float* arow;               // FP64-kept systems: per row, an upper bound of sum_j |Re a_ij| + |Im a_ij| (once per job)
+  float* phimax;             // FP64-kept systems: per system, max |component| of the pass-0 FP32 solution (per step)
   int f64_min_n;             // mixed forms: systems of at least this N keep FP64 matrices and residuals
   const ResidChunk* rchunks; // 32-row chunks of the systems, largest first (mixed form)
   int n_rchunks;

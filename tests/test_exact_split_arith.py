@@ -3,8 +3,9 @@ the same bit operations and float32 roundings (numpy), against exact rational ar
 
 - the three-float split of a double (a = a1 + a2 + a3 exactly, a1 the 24-bit truncation, a2 the next 24 bits,
   a3 the last 5), built from the exponent and fraction bits and integer-to-float conversions;
-- the three-level sum of products (Knuth two-sums for the leading and the next-order level, the FMA two-product
-  for the product errors), whose error must stay far below an FP64 accumulation's.
+- the anchored sums of products (error-free extraction against power-of-two anchors sized from a bound of the
+  sum of |a x|, the FMA two-product for the product errors), whose error must be of the order of an FP64
+  accumulation's, with both anchored levels staying in their binades.
 """
 from fractions import Fraction
 
@@ -41,35 +42,23 @@ def split3(a):
     return a1, a2, a3
 
 
-def two_sum(a, b):
-    s = F32(a + b)
-    v = F32(s - a)
-    return s, F32(F32(a - F32(s - v)) + F32(b - v))
+def split2(a):
+    """The two-float split of the later-pass residual updates (hi the 24-bit truncation, lo the 29 bits below
+    rounded once by an integer-to-float conversion, then scaled), as the device code forms it."""
+    u = int(np.array([a], dtype=np.float64).view(np.uint64)[0])
+    uh, ul = u >> 32, u & 0xFFFFFFFF
+    e = (uh >> 20) & 0x7FF
+    sign = uh & 0x80000000
+    frac23 = ((uh << 3) | (ul >> 29)) & 0x007FFFFF
+    hi = _bits_to_f32(sign | ((e - 1023 + 127) << 23) | frac23)
+    rem = ul & 0x1FFFFFFF
+    lo = _bits_to_f32(sign | (_f32_bits(F32(rem)) + ((e - 1075) << 23))) if rem else F32(0.0)
+    return hi, lo, rem
 
 
 def fma32(a, b, c):
     # float32 operands: a * b is exact in FP64 (48 bits); the uses below are exact in float32 as well
     return F32(float(a) * float(b) + float(c))
-
-
-class XAcc:
-    def __init__(self):
-        self.h = self.m = self.l = F32(0.0)
-
-    def add_prod(self, a1, a2, a3, x):
-        p1 = F32(a1 * x)
-        e1 = fma32(a1, x, -p1)
-        p2 = F32(a2 * x)
-        e2 = fma32(a2, x, -p2)
-        p3 = F32(a3 * x)
-        self.h, t0 = two_sum(self.h, p1)
-        s, u1 = two_sum(self.m, t0)
-        m, u2 = two_sum(s, e1)
-        self.m, u3 = two_sum(m, p2)
-        self.l = F32(self.l + F32(F32(u1 + u2) + F32(u3 + F32(e2 + p3))))
-
-    def value(self):
-        return (float(self.l) + float(self.m)) + float(self.h)
 
 
 def test_three_float_split_is_exact():
@@ -84,25 +73,109 @@ def test_three_float_split_is_exact():
             assert abs(float(a2)) <= 2.0 ** -23 * abs(a) and abs(float(a3)) <= 2.0 ** -47 * abs(a)
 
 
-def test_three_level_sum_of_products_beats_fp64():
-    """Residual-like sums with heavy cancellation: sum_j a_j x_j - g with a FP64, x float32; the three-level
-    sum's error against exact arithmetic stays below 2^-60 of sum |a_j x_j|, well under the FP64 FMA
-    accumulation's (about N 2^-53 at worst, measured here too)."""
-    rng = np.random.default_rng(7)
-    worst = worst64 = 0.0
-    for trial in range(6):
-        n = 300
-        a = rng.standard_normal(n) * np.exp(rng.uniform(-3, 3, n))
+def test_two_float_split_rounds_once():
+    """lo is the 29 fraction bits below hi rounded once to float32 (what a conversion of that integer gives):
+    |a - hi - lo| <= 2^-47 |a| and lo equals the correctly rounded remainder."""
+    rng = np.random.default_rng(9)
+    vals = rng.standard_normal(3000) * 10.0 ** rng.uniform(-15, 25, 3000)
+    for a in vals:
+        a = float(a)
+        hi, lo, rem = split2(a)
+        exact_rem = Fraction(a) - Fraction(float(hi))
+        assert float(lo) == float(F32(float(exact_rem)))          # one rounding of the exact remainder
+        assert abs(Fraction(a) - Fraction(float(hi)) - Fraction(float(lo))) <= Fraction(2) ** -47 * abs(Fraction(a))
+
+
+class AAcc:
+    """The anchored sums of the first-pass residual (anchors 1.5 2^kh and 1.5 2^km), float32 step by step."""
+
+    def __init__(self, kh, km):
+        self.H = self.sh = F32(1.5 * 2.0 ** kh)
+        self.M = self.sm = F32(1.5 * 2.0 ** km)
+        self.l = F32(0.0)
+
+    def put_m(self, v):
+        t = F32(self.M + v)
+        self.l = F32(self.l + F32(v - F32(t - self.M)))
+        self.M = t
+
+    def add_prod(self, a1, a2, a3, x):
+        p1 = F32(a1 * x)
+        e1 = fma32(a1, x, -p1)
+        t = F32(self.H + p1)
+        r1 = F32(p1 - F32(t - self.H))
+        self.H = t
+        self.put_m(r1)
+        self.put_m(e1)
+        u = fma32_round(a2, x, self.M)
+        q = F32(u - self.M)
+        self.l = F32(self.l + fma32_round(a2, x, -q))
+        self.M = u
+        self.l = fma32_round(a3, x, self.l)
+
+    def renorm(self):
+        t = F32(self.M + self.l)
+        self.l = F32(self.l - F32(t - self.M))
+        self.M = t
+
+    def value(self):
+        return (float(F32(self.H - self.sh)) + float(F32(self.M - self.sm))) + float(self.l)
+
+
+def fma32_round(a, b, c):
+    """fmaf: a * b + c rounded once to float32 (exact rational arithmetic, then one rounding)."""
+    return F32(float(Fraction(float(a)) * Fraction(float(b)) + Fraction(float(c))))
+
+
+def _anchors(bound, n_terms):
+    # as the kernel: bnd in [2^e, 2^(e+1)) -> kh = e + 3; km = kh - 23 + ceil(log2(T + 4))
+    e = int(np.floor(np.log2(bound)))
+    kh = e + 3
+    km = kh - 23 + int(np.ceil(np.log2(n_terms + 4)))
+    return kh, km
+
+
+def _check_anchored(a, x, renorm_every=4):
+    """Sum a_j x_j by the anchored sums; returns (error, bound) against exact rational arithmetic, after
+    checking that H and M never leave their binades."""
+    n = len(a)
+    bound = float(np.sum(np.abs(a) * np.abs(x.astype(np.float64)))) * (1 + 2 ** -20)
+    kh, km = _anchors(bound, n)
+    acc = AAcc(kh, km)
+    for j, (aj, xj) in enumerate(zip(a, x)):
+        acc.add_prod(*split3(float(aj)), xj)
+        assert 2.0 ** kh <= float(acc.H) <= 2.0 ** (kh + 1)
+        assert 2.0 ** km <= float(acc.M) <= 2.0 ** (km + 1)
+        if (j + 1) % renorm_every == 0:
+            acc.renorm()
+    exact = sum(Fraction(float(ai)) * Fraction(float(xi)) for ai, xi in zip(a, x))
+    return abs(float(Fraction(acc.value()) - exact)), bound
+
+
+def test_anchored_sums_fp64_grade():
+    """Residual-like sums (FP64 entries times float32 values): cancelling, same-sign (every partial sum near
+    the bound) and mixed-magnitude cases; the error stays below 2^-48 of the bound sum |a x| (2^-51 to 2^-55
+    measured; an FP64 accumulation of the same sums, 2^-49 to 2^-54)."""
+    rng = np.random.default_rng(11)
+    worst = 0.0
+    for trial in range(8):
+        n = (64, 300, 1024)[trial % 3]
+        a = rng.standard_normal(n) * np.exp(rng.uniform(-4, 4, n))
+        if trial % 4 == 1:
+            a = np.abs(a)                                     # same sign: partial sums up to the bound
         x = rng.standard_normal(n).astype(np.float32)
-        x[-1] = np.float32(-(np.dot(a[:-1], x[:-1].astype(np.float64)) / a[-1]))   # near-cancelling sum
-        exact = sum(Fraction(float(ai)) * Fraction(float(xi)) for ai, xi in zip(a, x))
-        acc = XAcc()
-        s64 = 0.0
-        for ai, xi in zip(a, x):
-            acc.add_prod(*split3(float(ai)), xi)
-            s64 = float(np.fma(ai, float(xi), s64)) if hasattr(np, "fma") else s64 + ai * float(xi)
-        scale = float(sum(abs(Fraction(float(ai)) * Fraction(float(xi))) for ai, xi in zip(a, x)))
-        worst = max(worst, abs(float(Fraction(acc.value()) - exact)) / scale)
-        worst64 = max(worst64, abs(float(Fraction(s64) - exact)) / scale)
-    assert worst < 2.0 ** -60, worst
-    assert worst < worst64 or worst64 == 0.0
+        if trial % 4 == 1:
+            x = np.abs(x)
+        if trial % 4 == 2:
+            x[-1] = np.float32(-(np.dot(a[:-1], x[:-1].astype(np.float64)) / a[-1]))   # near-cancelling
+        err, bound = _check_anchored(a, x)
+        worst = max(worst, err / bound)
+    assert worst < 2.0 ** -48, worst
+
+
+def test_anchored_sums_zero_and_tiny_terms():
+    # zero entries and exactly representable values: the sum is exact
+    a = np.array([0.0, 1.0, -0.5, 0.25, 0.0, 3.0])
+    x = np.array([1.0, 2.0, 4.0, -8.0, 5.0, 0.5], dtype=np.float32)
+    err, bound = _check_anchored(a, x)
+    assert err == 0.0
