@@ -69,9 +69,16 @@ FLOPS_PER_KERNEL_ENTRY = 34
 
 
 def kernels_hash():
+    """sha256 of kernels.cu's code: comments, trailing blanks and empty lines removed, so that a change of
+    wording leaves the recorded counters valid and any change of code invalidates them."""
     import hashlib
-    with open(os.path.join(ROOT, "paper_2507_05725_gb300", "csrc", "kernels.cu"), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    import re
+    with open(os.path.join(ROOT, "paper_2507_05725_gb300", "csrc", "kernels.cu")) as f:
+        src = f.read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    code = "\n".join(line.rstrip() for line in src.splitlines() if line.strip())
+    return hashlib.sha256(code.encode()).hexdigest()[:16]
 
 
 def measured_traffic_per_unit():
@@ -84,8 +91,8 @@ def measured_traffic_per_unit():
     h = None
     out = {}
     for line in txt.splitlines():
-        if line.startswith("kernels.cu sha256:"):
-            h = line.split(":", 1)[1].strip().strip("`")
+        if line.startswith("kernels.cu code sha256:"):
+            h = line.split("`")[1] if line.count("`") >= 2 else None
         cells = [c.strip().strip("`") for c in line.strip().strip("|").split("|")]
         if len(cells) >= 6 and cells[0].startswith("k_"):
             try:

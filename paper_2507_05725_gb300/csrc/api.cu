@@ -325,7 +325,7 @@ fthms_status upload_job(fthms_req* r) {
   J.mrho = nullptr;
   J.mscale = nullptr;
   J.arow = nullptr;
-  J.phimax = nullptr;
+  J.phistat = nullptr;
   J.f64_min_n = J.fp64keep ? 0 : (J.mixed ? kLuBigMin : 1 << 30);
   J.rchunks = nullptr;
   J.n_rchunks = 0;
@@ -343,7 +343,7 @@ fthms_status upload_job(fthms_req* r) {
     TRY(dev_alloc(r, p.sys.size(), &J.mrho));
     TRY(dev_alloc(r, p.sys.size(), &J.mscale));
     TRY(dev_alloc(r, (size_t)p.piv_total, &J.arow));
-    TRY(dev_alloc(r, p.sys.size(), &J.phimax));
+    TRY(dev_alloc(r, p.sys.size() * 4, &J.phistat));
     TRY(dev_upload(r, p.rchunks, &J.rchunks));
     J.n_rchunks = (int)p.rchunks.size();
   }

@@ -1499,10 +1499,11 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(kPending) : "memory");
 }
 
-// Per row of the systems that keep FP64, an upper bound of sum_j (|Re a_ij| + |Im a_ij|) in FP32, once per job
-// after the assembly: each |a| bounded from above by its 23 leading fraction bits times (1 + 2^-22), the sum
-// of N such floats by (1 + 2^-10) for its roundings (N 2^-24 < 2^-10).  The first-pass residual sizes the
-// anchors of its FP32-pipe sums from it.
+// Per row of the systems that keep FP64, upper bounds of the 1-norm and the 2-norm of the row's 2N real
+// components (|Re a_ij|, |Im a_ij|) in FP32, once per job after the assembly: each |a| bounded from above by
+// its 23 leading fraction bits times (1 + 2^-22), the sums of 2N such floats (or their squares) by (1 + 2^-10)
+// for their roundings (2N 2^-24 < 2^-10), the square root by (1 + 2^-20).  The first-pass residual sizes the
+// anchors of its FP32-pipe sums from them.
 __device__ __forceinline__ float abs_bound_f32(double a) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(a) & 0x7FFFFFFFFFFFFFFFull;
   const int e = (int)(u >> 52);
@@ -1521,20 +1522,23 @@ __global__ void __launch_bounds__(kResidThreads) k_arow_norms(DevJob J) {
   const int i = c.row0 + (threadIdx.x & 31);
   if (i >= N) return;
   const double2* __restrict__ A64 = J.A + s.mat_off;
-  float acc = 0.f;
+  float n1 = 0.f, n2 = 0.f;
 #pragma unroll 4
   for (int j = 0; j < N; ++j) {
     const double2 a = __ldg(&A64[(long long)j * N + i]);
-    acc = __fadd_rn(acc, __fadd_rn(abs_bound_f32(a.x), abs_bound_f32(a.y)));
+    const float br = abs_bound_f32(a.x), bi = abs_bound_f32(a.y);
+    n1 = __fadd_rn(n1, __fadd_rn(br, bi));
+    n2 = fmaf(br, br, fmaf(bi, bi, n2));
   }
-  J.arow[s.piv_off + i] = __fmul_rn(acc, 1.f + 0x1p-10f);
+  J.arow[s.piv_off + i] =
+      make_float2(__fmul_rn(n1, 1.f + 0x1p-10f), __fmul_rn(__fsqrt_rn(__fmul_rn(n2, 1.f + 0x1p-10f)), 1.f + 0x1p-20f));
 }
 
 // The first-pass residual of the systems that keep FP64 (all in the FP64-kept form), to FP64 accuracy on both
 // arithmetic pipes at once: phi_0 is the FP32 solution (exactly a float), so every product a_ij phi_j can be
 // formed exactly from a three-float split of the FP64 entry.  A warp sums its rows either through FP64 FMAs
-// (acc) or through those products and anchored sums on the FP32 pipe (aacc, anchors sized from the row's
-// bound arow * phimax); the FP64 pipe, which alone would bound the kernel at 8 DFMA per entry and two
+// (acc) or through those products and anchored sums on the FP32 pipe (aacc, anchors sized per window from
+// the smaller of the row's 1-norm times max |phi_0| and its 2-norm times |phi_0|_2); the FP64 pipe, which alone would bound the kernel at 8 DFMA per entry and two
 // windows, and the FP32 pipe then work side by side.  Either way G - A phi_0 comes out with an error of
 // the order of an FP64 accumulation's (about 2^-50 of sum_j |a_ij phi_j|).
 template <int Q>
@@ -1559,19 +1563,23 @@ __global__ void __launch_bounds__(kResidThreads) k_mresid64(DevJob J) {
     const double2 g = G[q * N + row];
     acc[q] = make_double2(g.x * isc, g.y * isc);
   }
-  // Anchors of the FP32-pipe sums: every partial sum of |a phi_0| along the row stays below
-  // bnd = sum_j (|Re a_ij| + |Im a_ij|) max |phi_0| (both bounded from above), below 2^(kh-1) with kh = e + 3
-  // for bnd in [2^e, 2^(e+1)).  A chunk with a row outside the anchors' range sums in FP64.
-  const float bnd = J.arow[s.piv_off + row] * J.phimax[c.sys] * (1.f + 0x1p-20f);
-  const int be = (int)((__float_as_uint(bnd) >> 23) & 0xFFu) - 127;
-  const int kh = bnd > 0.f ? be + 3 : 0;                   // (bnd = 0: every product is zero)
-  const int km = kh - 23 + (32 - __clz(2 * N + 3));        // ceil(log2(T + 4)), T = 2N terms a sum
-  const bool anchors_ok = bnd == 0.f || (be >= -40 && be <= 100);
+  // Anchors of the FP32-pipe sums, per window: every partial sum of |a phi_0| along the row (both the real
+  // and the imaginary part's 2N terms) stays below bnd = min(|a_i|_1 max |phi_0|, |a_i|_2 |phi_0|_2) (Hoelder,
+  // Cauchy-Schwarz; all bounded from above), so below 2^(kh-1) with kh = e + 2 for bnd in [2^e, 2^(e+1)).  A
+  // chunk with a row outside the anchors' range sums in FP64.
+  const float2 an = J.arow[s.piv_off + row];
+  const int km_off = -23 + (32 - __clz(2 * N + 3));       // km = kh - 23 + ceil(log2(T + 4)), T = 2N terms a sum
+  bool anchors_ok = true;
   aacc sr[Q], si[Q];
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
-    sr[q].init(kh, km);
-    si[q].init(kh, km);
+    const float2 ps = J.phistat[c.sys * 4 + q];
+    const float bnd = __fmul_rn(fminf(__fmul_rn(an.x, ps.x), __fmul_rn(an.y, ps.y)), 1.f + 0x1p-20f);
+    const int be = (int)((__float_as_uint(bnd) >> 23) & 0xFFu) - 127;
+    const int kh = bnd > 0.f ? be + 2 : 0;                 // (bnd = 0: every product is zero)
+    anchors_ok = anchors_ok && (bnd == 0.f || (be >= -40 && be <= 100));
+    sr[q].init(kh, kh + km_off);
+    si[q].init(kh, kh + km_off);
   }
   auto col64 = [&](const double2 a, int j) {
 #pragma unroll
@@ -1801,14 +1809,24 @@ __global__ void __launch_bounds__(32 * kSolveWarps, 3) k_msolve(DevJob J, int m,
   float2* dc = J.dcorr + s.vec_off;
   if (pass == 0) {
     if (f64) {
-      float pm = 0.f;
-      for (int e = lane; e < Q * N; e += 32) {
-        ph64[e] = make_double2(b[e].x, b[e].y);
-        dc[e] = b[e];                         // phi_0 as floats for the first residual's FP32-pipe columns
-        pm = fmaxf(pm, fmaxf(fabsf(b[e].x), fabsf(b[e].y)));
+#pragma unroll
+      for (int q = 0; q < QT; ++q) {
+        float pm = 0.f, p2 = 0.f;
+        for (int e = q * N + lane; e < (q + 1) * N; e += 32) {
+          ph64[e] = make_double2(b[e].x, b[e].y);
+          dc[e] = b[e];                       // phi_0 as floats for the first residual's FP32-pipe columns
+          pm = fmaxf(pm, fmaxf(fabsf(b[e].x), fabsf(b[e].y)));
+          p2 = fmaf(b[e].x, b[e].x, fmaf(b[e].y, b[e].y, p2));
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          pm = fmaxf(pm, __shfl_xor_sync(0xffffffffu, pm, o));
+          p2 = __fadd_rn(p2, __shfl_xor_sync(0xffffffffu, p2, o));
+        }
+        // the first residual's anchors: max |component| and an upper bound of the window's 2-norm
+        if (lane == 0)
+          J.phistat[sidx * 4 + q] =
+              make_float2(pm, __fmul_rn(__fsqrt_rn(__fmul_rn(p2, 1.f + 0x1p-10f)), 1.f + 0x1p-20f));
       }
-      for (int o = 16; o > 0; o >>= 1) pm = fmaxf(pm, __shfl_xor_sync(0xffffffffu, pm, o));
-      if (lane == 0) J.phimax[sidx] = pm;     // the first residual's anchors
     } else {
       for (int e = lane; e < Q * N; e += 32) ph[e] = make_float4(b[e].x, 0.f, b[e].y, 0.f);
     }

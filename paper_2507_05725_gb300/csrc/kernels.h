@@ -87,8 +87,10 @@ struct DevJob {
   float* mrel;               // per system: relative size of its last correction (mixed form)
   float* mrho;               // per system: largest contraction factor measured in earlier steps (0: none yet)
   double* mscale;            // per system and step: power of two near max |G|; refinement runs in G / mscale
-  float* arow;               // FP64-kept systems: per row, an upper bound of sum_j |Re a_ij| + |Im a_ij| (once per job)
-  float* phimax;             // FP64-kept systems: per system, max |component| of the pass-0 FP32 solution (per step)
+  float2* arow;              // FP64-kept systems, per row (once per job): upper bounds of the 1-norm and the 2-norm
+                             // of the row's 2N real components (|Re a_ij|, |Im a_ij|)
+  float2* phistat;           // FP64-kept systems, per system and window (4 slots a system, every step): max |component|
+                             // and an upper bound of the 2-norm of the pass-0 FP32 solution
   int f64_min_n;             // mixed forms: systems of at least this N keep FP64 matrices and residuals
   const ResidChunk* rchunks; // 32-row chunks of the systems, largest first (mixed form)
   int n_rchunks;

@@ -688,7 +688,7 @@ size_t plan_device_bytes(const Plan& p) {
   b += (size_t)p.mat_total * 16;                 // A / LU
   if (p.opt.precision >= 1)                      // FP32 factors, residuals and corrections, refinement state
     b += (size_t)p.mat_total * 8 + (size_t)p.piv_total * 8 + (size_t)p.vec_total * (8 + 16 + 16 + 8) +
-         p.sys.size() * 28 + (size_t)p.piv_total * 4 + p.rchunks.size() * sizeof(ResidChunk);
+         p.sys.size() * (24 + 32) + (size_t)p.piv_total * 8 + p.rchunks.size() * sizeof(ResidChunk);
   b += p.sig_f.size() * 8;                       // samples of a sampled signal
   b += (size_t)p.piv_total * 4;                  // pivots
   b += (size_t)p.rlog_total * 8;                 // self log tables

@@ -128,9 +128,10 @@ def fma32_round(a, b, c):
 
 
 def _anchors(bound, n_terms):
-    # as the kernel: bnd in [2^e, 2^(e+1)) -> kh = e + 3; km = kh - 23 + ceil(log2(T + 4))
+    # as the kernel: bnd in [2^e, 2^(e+1)) -> kh = e + 2 (every partial sum below 2^(kh-1));
+    # km = kh - 23 + ceil(log2(T + 4))
     e = int(np.floor(np.log2(bound)))
-    kh = e + 3
+    kh = e + 2
     km = kh - 23 + int(np.ceil(np.log2(n_terms + 4)))
     return kh, km
 
