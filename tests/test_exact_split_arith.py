@@ -180,3 +180,59 @@ def test_anchored_sums_zero_and_tiny_terms():
     x = np.array([1.0, 2.0, 4.0, -8.0, 5.0, 0.5], dtype=np.float32)
     err, bound = _check_anchored(a, x)
     assert err == 0.0
+
+
+def _abs_bound_f32(a):
+    """|a| bounded from above in float32 as the row-norm kernel does: the 23 leading fraction bits times
+    (1 + 2^-22)."""
+    u = int(np.array([abs(a)], dtype=np.float64).view(np.uint64)[0])
+    e = u >> 52
+    if e >= 1023 + 127:
+        return F32(np.inf)
+    if e < 1023 - 126:
+        return F32(2.0 ** -126)
+    frac23 = (u >> 29) & 0x7FFFFF
+    return F32(_bits_to_f32(((e - 1023 + 127) << 23) | frac23) * F32(1 + 2.0 ** -22))
+
+
+def _fma32(a, b, c):
+    return F32(float(Fraction(float(a)) * Fraction(float(b)) + Fraction(float(c))))
+
+
+def test_anchor_bounds_hold():
+    """The first-pass residual's anchors: per row the FP32 bounds of the 1-norm and 2-norm of the row's 2N real
+    components, per window max |phi| and the 2-norm bound, bnd = min(n1 max|phi|, n2 |phi|_2) (1 + 2^-20), all
+    with the kernels' float32 roundings, must bound both accumulators' sums of |a x| (real and imaginary part
+    pairings); kh = e + 2 for bnd in [2^e, 2^(e+1)) then keeps every partial sum below 2^(kh-1)."""
+    rng = np.random.default_rng(21)
+    for trial in range(6):
+        n = (40, 200, 513)[trial % 3]
+        ar = rng.standard_normal(n) * np.exp(rng.uniform(-6, 2, n))
+        ai = rng.standard_normal(n) * np.exp(rng.uniform(-6, 2, n))
+        ar[trial % n] *= 1e3                                    # a dominant (diagonal-like) entry
+        pr = (rng.standard_normal(n) * np.exp(rng.uniform(-3, 3, n))).astype(np.float32)
+        pi = (rng.standard_normal(n) * np.exp(rng.uniform(-3, 3, n))).astype(np.float32)
+        n1 = n2 = F32(0.0)
+        for x, y in zip(ar, ai):
+            br, bi = _abs_bound_f32(float(x)), _abs_bound_f32(float(y))
+            n1 = F32(n1 + F32(br + bi))
+            n2 = _fma32(br, br, _fma32(bi, bi, n2))
+        n1 = F32(n1 * F32(1 + 2.0 ** -10))
+        n2 = F32(F32(np.sqrt(F32(n2 * F32(1 + 2.0 ** -10)))) * F32(1 + 2.0 ** -20))
+        pm = F32(max(np.max(np.abs(pr)), np.max(np.abs(pi))))
+        p2 = F32(0.0)
+        for x, y in zip(pr, pi):
+            p2 = _fma32(x, x, _fma32(y, y, p2))
+        p2 = F32(F32(np.sqrt(F32(p2 * F32(1 + 2.0 ** -10)))) * F32(1 + 2.0 ** -20))
+        bnd = F32(min(F32(n1 * pm), F32(n2 * p2)) * F32(1 + 2.0 ** -20))
+        fr = [Fraction(float(v)) for v in pr]
+        fi = [Fraction(float(v)) for v in pi]
+        far = [Fraction(float(v)) for v in ar]
+        fai = [Fraction(float(v)) for v in ai]
+        s_re = sum(abs(a) * abs(x) + abs(b) * abs(y) for a, b, x, y in zip(far, fai, fr, fi))
+        s_im = sum(abs(a) * abs(y) + abs(b) * abs(x) for a, b, x, y in zip(far, fai, fr, fi))
+        assert Fraction(float(bnd)) >= max(s_re, s_im)
+        e = int(np.floor(np.log2(float(bnd))))
+        kh = e + 2
+        # the leading products p1 = fl(a1 x) add up to at most (1 + 2^-24) sum |a x|
+        assert max(s_re, s_im) * (1 + Fraction(1, 2 ** 24)) < Fraction(2) ** (kh - 1)
