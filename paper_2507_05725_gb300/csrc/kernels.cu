@@ -1538,9 +1538,10 @@ __global__ void __launch_bounds__(kResidThreads) k_arow_norms(DevJob J) {
 // arithmetic pipes at once: phi_0 is the FP32 solution (exactly a float), so every product a_ij phi_j can be
 // formed exactly from a three-float split of the FP64 entry.  A warp sums its rows either through FP64 FMAs
 // (acc) or through those products and anchored sums on the FP32 pipe (aacc, anchors sized per window from
-// the smaller of the row's 1-norm times max |phi_0| and its 2-norm times |phi_0|_2); the FP64 pipe, which alone would bound the kernel at 8 DFMA per entry and two
-// windows, and the FP32 pipe then work side by side.  Either way G - A phi_0 comes out with an error of
-// the order of an FP64 accumulation's (about 2^-50 of sum_j |a_ij phi_j|).
+// the smaller of the row's 1-norm times max |phi_0| and its 2-norm times |phi_0|_2); the FP64 pipe, which
+// alone would bound the kernel at 8 DFMA per entry and two windows, and the FP32 pipe then work side by
+// side.  Either way G - A phi_0 comes out with an error of the order of an FP64 accumulation's (about 2^-50
+// of sum_j |a_ij phi_j|).
 template <int Q>
 __global__ void __launch_bounds__(kResidThreads) k_mresid64(DevJob J) {
   const int chunk = blockIdx.x * (kResidThreads / 32) + (threadIdx.x >> 5);
